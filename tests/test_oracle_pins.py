@@ -1,0 +1,477 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics, independent
+of the oracle's own formulas: library routines (numpy Gauss rule, scipy B-splines,
+scipy adaptive quadrature, dense LAPACK solves and eigendecompositions), closed forms,
+the paper's printed amplification blocks and characteristic polynomials
+(tests/golden/), a textbook special case (Hulbert-Chung explicit generalized-alpha)
+and brute force on tiny meshes."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.interpolate
+import scipy.linalg
+
+import oracle
+import workloads as W
+from conftest import read_golden
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+
+
+# ----------------------------------------------------------------------------- quadrature, basis
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8])
+def test_gauss_legendre_matches_numpy_and_is_exact(n):
+    x, w = oracle.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(x, xr, atol=1e-14, rtol=0) and np.allclose(w, wr, atol=1e-14, rtol=0)
+    for deg in range(2 * n):
+        exact = (1 - (-1) ** (deg + 1)) / (deg + 1)
+        assert abs(np.sum(w * x ** deg) - exact) < 1e-13
+
+
+def _knot_cases():
+    yield 1, W.open_uniform_knots(5, 1)
+    yield 2, W.open_uniform_knots(6, 2)
+    yield 3, W.open_uniform_knots(7, 3)
+    yield 4, W.open_uniform_knots(5, 4)
+    yield 3, np.array([0, 0, 0, 0, 0.1, 0.35, 0.35, 0.6, 0.9, 1, 1, 1, 1.0])  # non-uniform, repeated knot
+    yield 2, np.array([0, 0, 0, 0.2, 0.2, 0.5, 0.7, 1, 1, 1.0])
+
+
+@pytest.mark.parametrize("case", list(range(6)))
+def test_basis_matches_scipy_bspline(case):
+    p, U = list(_knot_cases())[case]
+    m = len(U) - p - 1
+    xs = np.random.default_rng(case).uniform(0, 1, 25)
+    for x in xs:
+        val, der = oracle.basis(p, U, x)
+        for i in range(m):
+            c = np.zeros(m)
+            c[i] = 1.0
+            spl = scipy.interpolate.BSpline(U, c, p, extrapolate=False)
+            assert abs(val[i] - spl(x)) < 1e-13
+            if p > 0:
+                assert abs(der[i] - spl.derivative()(x)) < 1e-11
+        assert abs(val.sum() - 1.0) < 1e-14  # partition of unity (eq. partition_unity)
+        assert abs(der.sum()) < 1e-10
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_greville_reproduces_linear(p):
+    U = W.open_uniform_knots(6, p)
+    g = W.greville(U, p)
+    for x in np.linspace(0, 1, 13):
+        val, der = oracle.basis(p, U, x)
+        assert abs(val @ g - x) < 1e-14
+        assert abs(der @ g - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------- 1-D matrices
+def test_mass_1d_p1_closed_form():
+    nel = 8
+    q = oracle.Quad1D(1, W.open_uniform_knots(nel, 1), 2)
+    h = 1.0 / nel
+    M = q.mass_interior()
+    n = nel - 1
+    ref = h / 6 * (4 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1))
+    assert np.abs(M - ref).max() < 1e-15
+
+
+def _scipy_gram(p, U, deriv):
+    m = len(U) - p - 1
+    spl = []
+    for i in range(1, m - 1):
+        c = np.zeros(m)
+        c[i] = 1
+        s = scipy.interpolate.BSpline(U, c, p, extrapolate=False)
+        spl.append(s.derivative() if deriv else s)
+    n = len(spl)
+    breaks = np.unique(U)
+    G = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - p), min(n, i + p + 1)):
+            tot = 0.0
+            for a, b in zip(breaks[:-1], breaks[1:]):
+                tot += scipy.integrate.quad(lambda x: np.nan_to_num(spl[i](x)) * np.nan_to_num(spl[j](x)), a, b,
+                                            epsabs=1e-15, epsrel=1e-13)[0]
+            G[i, j] = tot
+    return G
+
+
+@pytest.mark.parametrize("case", [1, 2, 3, 4])
+def test_mass_and_stiffness_1d_match_adaptive_quadrature(case):
+    p, U = list(_knot_cases())[case]
+    q = oracle.Quad1D(p, U, p + 1)
+    assert np.abs(q.mass_interior() - _scipy_gram(p, U, False)).max() < 1e-13
+    assert np.abs(q.stiffness_interior() - _scipy_gram(p, U, True)).max() < 1e-10
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_interior_mass_stencil_is_cardinal_spline_autocorrelation(p):
+    # int N_p(x) N_p(x + k) dx = N_{2p+1}(p + 1 + k) for the cardinal B-spline N_p on [0, p+1]
+    nel = 4 * p + 8
+    h = 1.0 / nel
+    q = oracle.Quad1D(p, W.open_uniform_knots(nel, p), p + 1)
+    M = q.mass_interior()
+    Kst = q.stiffness_interior()
+    N2 = scipy.interpolate.BSpline.basis_element(np.arange(2 * p + 3), extrapolate=False)
+    i = M.shape[0] // 2
+    for k in range(0, p + 1):
+        assert abs(M[i, i + k] / h - N2(p + 1 + k)) < 1e-13
+        assert abs(Kst[i, i + k] * h + N2.derivative(2)(p + 1 + k)) < 1e-11
+
+
+# ----------------------------------------------------------------------------- 2-D/3-D operators
+def _patch(w):
+    return oracle.Patch(w.p, w.knots, w.ctrl())
+
+
+@pytest.mark.parametrize("d,nel,p", [(2, (4, 5), (2, 3)), (3, (3, 4, 3), (2, 2, 3)), (3, (3, 3, 3), (1, 1, 1))])
+def test_identity_map_is_kronecker(d, nel, p):
+    w = W.Workload("t", d, nel, p, 0.0, 1, 0.5, 1)
+    P = _patch(w)
+    M, K = P.assemble()
+    Md, Kd = P.band_to_dense(M), P.band_to_dense(K)
+    Mh = [q.mass_interior() for q in P.q1]
+    Kh = [q.stiffness_interior() for q in P.q1]
+    kron = lambda mats: mats[0] if len(mats) == 1 else np.kron(kron(mats[1:]), mats[0])  # co-lex
+    Mref = kron(Mh)
+    Kref = np.zeros_like(Mref)
+    for a in range(d):
+        Kref += kron([Kh[b] if b == a else Mh[b] for b in range(d)])
+    assert np.abs(Md - Mref).max() < 1e-14 * np.abs(Mref).max() * 10
+    assert np.abs(Kd - Kref).max() < 1e-12 * np.abs(Kref).max()
+
+
+def _brute_entries(w, pairs):
+    """M_ij and K_ij recomputed in numpy from scipy B-splines, same Gauss rule (brute force)."""
+    d = w.d
+    knots = w.knots
+    ctrl = w.ctrl()
+    mfull = w.m
+    xg, wg = np.polynomial.legendre.leggauss(max(w.p) + 1)
+    pts, wts = [], []
+    for a in range(d):
+        br = np.unique(knots[a])
+        xa, wa = [], []
+        for lo, hi in zip(br[:-1], br[1:]):
+            xa += list(lo + (hi - lo) * (xg + 1) / 2)
+            wa += list((hi - lo) / 2 * wg)
+        pts.append(np.array(xa))
+        wts.append(np.array(wa))
+    tabs = []
+    for a in range(d):
+        B = np.zeros((len(pts[a]), mfull[a]))
+        dB = np.zeros_like(B)
+        for i in range(mfull[a]):
+            c = np.zeros(mfull[a])
+            c[i] = 1
+            s = scipy.interpolate.BSpline(knots[a], c, w.p[a])
+            B[:, i] = s(pts[a])
+            dB[:, i] = s.derivative()(pts[a])
+        tabs.append((B, dB))
+    grid = ctrl.reshape(tuple(reversed(mfull)) + (d,))  # [i_{d-1}..i_0, coord]
+    # DF at every quadrature point: DF[c, b] = sum_i C_ic dB_i/dxi_b
+    out = []
+    for (i, j) in pairs:
+        ni = np.unravel_index(i, tuple(reversed(w.n)))[::-1]
+        nj = np.unravel_index(j, tuple(reversed(w.n)))[::-1]
+        Mij = 0.0
+        Kij = 0.0
+        for qs in np.ndindex(*[len(pts[a]) for a in range(d)]):
+            vals_i = [tabs[a][0][qs[a], ni[a] + 1] for a in range(d)]
+            vals_j = [tabs[a][0][qs[a], nj[a] + 1] for a in range(d)]
+            if np.prod(vals_i) == 0 and all(tabs[a][1][qs[a], ni[a] + 1] == 0 for a in range(d)):
+                continue
+            J = np.zeros((d, d))
+            for b in range(d):
+                fac = [tabs[a][1][qs[a]] if a == b else tabs[a][0][qs[a]] for a in range(d)]
+                for c in range(d):
+                    t = grid[..., c]
+                    for a in range(d):  # the last axis is i_0, then i_1, ...
+                        t = t @ fac[a]
+                    J[c, b] = t
+            wq = np.prod([wts[a][qs[a]] for a in range(d)])
+            det = np.linalg.det(J)
+            gi = np.array([np.prod([tabs[a][1 if a == b else 0][qs[a], ni[a] + 1] for a in range(d)]) for b in range(d)])
+            gj = np.array([np.prod([tabs[a][1 if a == b else 0][qs[a], nj[a] + 1] for a in range(d)]) for b in range(d)])
+            Ji = np.linalg.inv(J)
+            Mij += np.prod(vals_i) * np.prod(vals_j) * abs(det) * wq
+            Kij += gi @ (Ji @ Ji.T) @ gj * abs(det) * wq
+        out.append((Mij, Kij))
+    return out
+
+
+def test_deformed_entries_match_brute_force():
+    w = W.Workload("t", 3, (3, 3, 3), (2, 2, 2), 0.12, 1, 0.5, 1)
+    P = _patch(w)
+    M, K = P.assemble()
+    Md, Kd = P.band_to_dense(M), P.band_to_dense(K)
+    rng = np.random.default_rng(3)
+    pairs = [(0, 0), (P.N - 1, P.N - 1), (0, 1), (5, 13)]
+    pairs += [tuple(int(v) for v in rng.integers(0, P.N, 2)) for _ in range(4)]
+    ref = _brute_entries(w, pairs)
+    for (i, j), (m_ref, k_ref) in zip(pairs, ref):
+        assert abs(Md[i, j] - m_ref) < 1e-14 + 1e-12 * abs(m_ref)
+        assert abs(Kd[i, j] - k_ref) < 1e-12 + 1e-10 * abs(k_ref)
+    # symmetric positive definite
+    assert np.abs(Md - Md.T).max() < 1e-16 + 1e-14 * np.abs(Md).max()
+    assert np.linalg.eigvalsh(Md).min() > 0 and np.linalg.eigvalsh(Kd).min() > 0
+
+
+def test_deformed_2d_entries_match_brute_force():
+    w = W.Workload("t", 2, (4, 3), (3, 2), 0.1, 1, 0.5, 1)
+    P = _patch(w)
+    M, K = P.assemble()
+    Md, Kd = P.band_to_dense(M), P.band_to_dense(K)
+    pairs = [(0, 0), (1, 6), (P.N - 1, P.N - 2), (7, 7)]
+    for (i, j), (m_ref, k_ref) in zip(pairs, _brute_entries(w, pairs)):
+        assert abs(Md[i, j] - m_ref) < 1e-14 + 1e-12 * abs(m_ref)
+        assert abs(Kd[i, j] - k_ref) < 1e-12 + 1e-10 * abs(k_ref)
+
+
+def test_sampled_rows_equal_full_assembly():
+    w = W.small(d=3, nel=4, p=3, amp=0.1)
+    P = _patch(w)
+    M, K = P.assemble()
+    rows = W.sample_indices(P.N, 9, seed=1)
+    Ms, Ks = P.assemble(rows)
+    assert np.array_equal(Ms, M[rows]) and np.array_equal(Ks, K[rows])
+
+
+def test_rejects_folded_geometry():
+    w = W.Workload("t", 3, (3, 3, 3), (2, 2, 2), 2.5, 1, 0.5, 1)
+    with pytest.raises(ValueError):
+        _patch(w)
+
+
+def test_band_matvec_equals_dense():
+    w = W.small(d=3, nel=(3, 4, 5), p=(2, 3, 2), amp=0.1)
+    P = _patch(w)
+    M, K = P.assemble()
+    x = np.random.default_rng(0).standard_normal(P.N)
+    assert np.allclose(P.band_matvec(M, x), P.band_to_dense(M) @ x, rtol=0, atol=1e-15)
+    assert np.allclose(P.band_matvec(K, x), P.band_to_dense(K) @ x, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- preconditioner, PCG
+def test_preconditioner_is_inverse_of_dense_definition():
+    w = W.small(d=3, nel=(3, 4, 3), p=(2, 3, 2), amp=0.1)
+    P = _patch(w)
+    ops = oracle.Operators(P)
+    Mh = [q.mass_interior() for q in P.q1]
+    Mhat = np.kron(np.kron(Mh[2], Mh[1]), Mh[0])
+    Dhat = np.diag(np.diag(Mhat))
+    D = np.diag(np.diag(P.band_to_dense(ops.M)))
+    s = lambda A, e: np.diag(np.diag(A) ** e)
+    Pm = s(D, .5) @ s(Dhat, -.5) @ Mhat @ s(Dhat, -.5) @ s(D, .5)  # def:single_patch_prec
+    r = np.random.default_rng(1).standard_normal(P.N)
+    assert np.allclose(ops.apply_Pinv(r), np.linalg.solve(Pm, r), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("d,p", [(2, 2), (3, 3), (3, 4)])
+def test_identity_map_pcg_converges_in_one_iteration(d, p):
+    # F = identity => D = Dhat and M = Mhat, so the preconditioner is M itself: one PCG
+    # iteration leaves only rounding (about eps * cond(M), cond ~ 2e5 for p = 4 in 3-D),
+    # while on a deformed map one iteration is far from converged.
+    b = np.random.default_rng(2).standard_normal(int(np.prod([5 + p - 2] * d)))
+    rr = {}
+    for amp in (0.0, 0.1):
+        ops = oracle.Operators(_patch(W.small(d=d, nel=5, p=p, amp=amp)))
+        _, it, rr[amp] = oracle.pcg(ops.apply_M, ops.apply_Pinv, b, tol=0.0, max_iter=1)
+        assert it == 1
+    assert rr[0.0] < 1e-10 and rr[0.1] > 1e-4
+
+
+def test_pcg_matches_dense_solve():
+    w = W.small(d=3, nel=4, p=2, amp=0.15)
+    ops = oracle.Operators(_patch(w))
+    Md = ops.patch.band_to_dense(ops.M)
+    b = np.random.default_rng(5).standard_normal(ops.N)
+    x, it, rr = oracle.pcg(ops.apply_M, ops.apply_Pinv, b, tol=1e-14)
+    xr = scipy.linalg.solve(Md, b, assume_a="pos")
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-12
+    assert 1 < it < 30
+
+
+# ----------------------------------------------------------------------------- time scheme
+def _eval(expr, a, b, g, T):
+    return eval(expr, {"a": a, "b": b, "g": g, "T": T})
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_amplification_blocks_match_printed(k):
+    gold = read_golden("amplification_blocks.txt")
+    rng = np.random.default_rng(k)
+    for _ in range(5):
+        prm = [(rng.uniform(0.5, 2), rng.uniform(0, 1), rng.uniform(0, 2), 0.0) for _ in range(k)]
+        T = rng.uniform(0.1, 3)
+        G = oracle.scalar_amplification(k, 0.0, T, params=prm)
+        for j in range(k):
+            a, b, g, _ = prm[j]
+            sec = "block j=k" if j == k - 1 else "block j<k"
+            ref = np.array([[_eval(e, a, b, g, T) for e in row] for row in gold[sec]]) / a
+            assert np.abs(G[3 * j:3 * j + 3, 3 * j:3 * j + 3] - ref).max() < 1e-13
+            assert np.abs(G[3 * j + 3:, 3 * j:3 * j + 3]).max() == 0.0 if j < k - 1 else True  # block upper-triangular
+
+
+def test_characteristic_polynomials_match_printed():
+    gold = read_golden("characteristic_polynomials.txt")
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        prm = [(rng.uniform(0.5, 2), rng.uniform(0, 1), rng.uniform(0, 2), 0.0) for _ in range(2)]
+        T = rng.uniform(0.1, 3)
+        G = oracle.scalar_amplification(2, 0.0, T, params=prm)
+        for j, sec in enumerate(["block j<k", "block j=k"]):
+            a, b, g, _ = prm[j]
+            c = np.array([_eval(e, a, b, g, T) for e in gold[sec][0]])
+            ev = np.linalg.eigvals(G[3 * j:3 * j + 3, 3 * j:3 * j + 3])
+            assert np.abs(np.polyval(c / c[0], ev)).max() < 1e-10
+
+
+def test_last_block_is_hulbert_chung():
+    # Hulbert-Chung explicit generalized-alpha (textbook): alpha_m = (2 rho - 1)/(1 + rho),
+    # beta = (5 - 3 rho)/((1 + rho)^2 (2 - rho)), gamma = 3/2 - alpha_m; the paper's
+    # alpha = 1 - alpha_m (it weights the new acceleration).
+    for rho in [0.0, 0.3, 0.5, 0.8, 1.0]:
+        a, b, g, af = oracle.galpha_params(1, rho)[0]
+        am = (2 * rho - 1) / (1 + rho)
+        assert abs(a - (1 - am)) < 1e-15
+        assert abs(b - (5 - 3 * rho) / ((1 + rho) ** 2 * (2 - rho))) < 1e-15
+        assert abs(g - (1.5 - am)) < 1e-15 and af == 0.0
+
+
+def test_k1_trajectory_equals_hulbert_chung():
+    w = W.small(d=2, nel=4, p=2, amp=0.1, k=1)
+    ops = oracle.Operators(_patch(w))
+    Md, Kd = ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K)
+    U0, V0 = w.initial()
+    rho, tau = 0.4, 0.002
+    st = oracle.Stepper(ops, 1, rho, tol=1e-15)
+    X = st.init(U0, V0)
+    am = (2 * rho - 1) / (1 + rho)
+    beta = (5 - 3 * rho) / ((1 + rho) ** 2 * (2 - rho))
+    gam = 1.5 - am
+    d, v = U0.copy(), V0.copy()
+    a = np.linalg.solve(Md, -Kd @ d)
+    for _ in range(20):
+        X = st.step(X, tau)
+        # M ((1 - am) a1 + am a0) = -K d_n
+        a1 = (np.linalg.solve(Md, -Kd @ d) - am * a) / (1 - am)
+        d = d + tau * v + tau ** 2 * ((0.5 - beta) * a + beta * a1)
+        v = v + tau * ((1 - gam) * a + gam * a1)
+        a = a1
+    assert np.linalg.norm(X[0] - d) / np.linalg.norm(d) < 1e-12
+    assert np.linalg.norm(X[1] - v) / np.linalg.norm(v) < 1e-11
+
+
+def test_theta_crit_is_the_minus_one_root_of_printed_polynomial():
+    gold = read_golden("characteristic_polynomials.txt")
+    for rho in [0.0, 0.25, 0.5, 0.75, 1.0]:
+        a, b, g, _ = oracle.galpha_params(1, rho)[0]
+        T = oracle.theta_crit(rho)
+        c = np.array([_eval(e, a, b, g, T) for e in gold["block j=k"][0]])
+        assert abs(np.polyval(c, -1.0)) < 1e-12
+    assert abs(oracle.theta_crit(1.0) - 4.0) < 1e-15  # central-difference limit (Sec. 3.2)
+    assert abs(oracle.theta_crit(0.0) - 2.4) < 1e-15
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9, 1.0])
+def test_stability_limit_independent_of_k(rho):
+    Tc = oracle.theta_crit(rho)
+    for k in (1, 2, 3):
+        sr_in = max(abs(np.linalg.eigvals(oracle.scalar_amplification(k, rho, Tc * 0.999))))
+        sr_out = max(abs(np.linalg.eigvals(oracle.scalar_amplification(k, rho, Tc * 1.01))))
+        assert sr_in <= 1 + 1e-6 and sr_out > 1 + 1e-4
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.8])
+def test_spectral_radius_at_bifurcation_equals_rho(rho):
+    # Omega_b = 2 + 2 rho_b + rho_s - rho_s rho_b^2 (boxed formulas) at rho_b = rho_s = rho:
+    # all roots of each block equal -rho there, so the spectral radius is rho for every k.
+    Ob = 2 + 3 * rho - rho ** 3
+    for k in (1, 2, 3):
+        G = oracle.scalar_amplification(k, rho, Ob)
+        for j in range(k):
+            ev = np.linalg.eigvals(G[3 * j:3 * j + 3, 3 * j:3 * j + 3])
+            assert abs(max(abs(ev)) - rho) < 2e-5
+
+
+def _modal_error(k, rho, n, lam=1.0, T=1.0):
+    st = oracle.Stepper(oracle.ScalarOps(lam), k, rho, tol=0.0)
+    w = math.sqrt(lam)
+    X = np.zeros((3 * k, 1))
+    for r in range(3 * k):  # derivatives of cos(w t) at 0
+        X[r, 0] = (-1) ** (r // 2) * w ** r if r % 2 == 0 else 0.0
+    eu = ev = 0.0
+    for s in range(1, n + 1):  # max over the time grid (robust to zero crossings of the error)
+        X = st.step(X, T / n)
+        t = s * T / n
+        eu = max(eu, abs(X[0, 0] - math.cos(w * t)))
+        ev = max(ev, abs(X[1, 0] + w * math.sin(w * t)))
+    return eu, ev
+
+
+@pytest.mark.parametrize("k,ns,minorder", [(1, (40, 80), 1.9), (2, (20, 40), 3.85), (3, (16, 32), 5.5)])
+@pytest.mark.parametrize("rho", [0.0, 0.5, 1.0])
+def test_modal_order_is_2k(k, ns, minorder, rho):
+    e1 = _modal_error(k, rho, ns[0], lam=4.0)
+    e2 = _modal_error(k, rho, ns[1], lam=4.0)
+    for a, b in zip(e1, e2):
+        assert math.log2(a / b) > minorder
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_semidiscrete_temporal_order(k):
+    w = W.small(d=3, nel=3, p=2, amp=0.1, k=k)
+    ops = oracle.Operators(_patch(w))
+    Md, Kd = ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K)
+    U0, V0 = w.initial()
+    lmax = oracle.lambda_max_dense(Md, Kd)
+    tau0 = 0.4 * math.sqrt(oracle.theta_crit(0.5) / lmax)
+    errs = []
+    for n in (16, 32):
+        T = 16 * tau0
+        st = oracle.Stepper(ops, k, 0.5, tol=1e-15)
+        X = st.init(U0, V0)
+        for _ in range(n):
+            X = st.step(X, T / n)
+        Ue, Ve = oracle.exact_semidiscrete(Md, Kd, U0, V0, T)
+        errs.append(np.linalg.norm(X[0] - Ue) / np.linalg.norm(Ue))
+    order = math.log2(errs[0] / errs[1])
+    assert order > 2 * k - 0.35, (errs, order)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_cfl_limit_independent_of_k_on_mesh(k):
+    w = W.small(d=2, nel=6, p=2, amp=0.1, k=k)
+    ops = oracle.Operators(_patch(w))
+    Md, Kd = ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K)
+    lmax = oracle.lambda_max_dense(Md, Kd)
+    rho = 0.5
+    tc = math.sqrt(oracle.theta_crit(rho) / lmax)
+    U0 = np.random.default_rng(0).standard_normal(ops.N)
+    V0 = np.zeros(ops.N)
+
+    def energy(X):
+        return 0.5 * X[1] @ Md @ X[1] + 0.5 * X[0] @ Kd @ X[0]
+
+    # The block upper-triangular amplification matrix is non-normal, so the energy can
+    # rise transiently (by a few times for k = 3) before the dissipative decay; stability
+    # means no sustained growth.
+    out = []
+    for frac in (0.98, 1.03):
+        st = oracle.Stepper(ops, k, rho, tol=1e-14)
+        X = st.init(U0, V0)
+        e0 = energy(X)
+        hist = []
+        for _ in range(800):
+            X = st.step(X, frac * tc)
+            hist.append(energy(X) / e0)
+        out.append(hist)
+    stable, unstable = out
+    mid = lambda h: max(h[200:400])
+    late = lambda h: max(h[600:800])
+    assert late(stable) <= mid(stable) * 1.001
+    assert late(unstable) > 1e2 * mid(unstable)
