@@ -1,0 +1,204 @@
+/*
+ * iga_galpha.h -- C ABI of the GB300 implementation of the per-time-step hot
+ * path of the explicit 2k-order generalized-alpha method for isogeometric
+ * structural dynamics (Behnoudfar, Loli, Reali, Sangalli, Calo; arXiv 2102.11536).
+ *
+ * The semi-discrete problem is M U'' + K U = F with U(0) = U0, U'(0) = V0
+ * (Sec. 2.1, eq. mp / eq. u0), damping C = 0, on one B-spline patch
+ * (Sec. 5.1-5.2) with homogeneous Dirichlet conditions. One step of the method
+ * (Sec. 4, eq. ho1-ho3) applies the stiffness operator to k predicted vectors,
+ * solves k systems with the mass matrix by preconditioned CG (Sec. 5.5) with
+ * the preconditioner D^{1/2} Dhat^{-1/2} (Mhat_1 x Mhat_2 x Mhat_3) Dhat^{-1/2} D^{1/2}
+ * (Sec. 5.3, def:single_patch_prec), and updates the 3k state variables.
+ *
+ * Conventions shared by every call:
+ *   - All vectors are FP64, length N = prod_a (m_a - 2), the interior control
+ *     points (the first and last univariate function of each direction carry
+ *     the Dirichlet condition and are dropped). Order is co-lexicographic,
+ *     direction 0 fastest (Sec. 5.2, def:parametric_spline).
+ *   - "device" pointers are CUDA global memory on the handle's device; "host"
+ *     pointers are ordinary (preferably pinned) CPU memory.
+ *   - Every call returns an IGA_* status; on failure iga_last_error() gives a
+ *     message. No C++ exception crosses the ABI.
+ *   - Work is issued on the handle's stream (iga_options.stream). Calls that
+ *     return results to host memory synchronise that stream; calls that only
+ *     write device memory may return before the kernels finish.
+ *   - A handle is not thread-safe. The library owns all memory it allocates;
+ *     caller buffers are never freed or retained after the call.
+ */
+#ifndef IGA_GALPHA_H
+#define IGA_GALPHA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define IGA_OK 0
+#define IGA_EINVAL 1          /* bad argument (sizes, degrees, pointers, k, rho, dt) */
+#define IGA_ENOMEM 2          /* device or host allocation failed */
+#define IGA_ECUDA 3           /* a CUDA call failed; the message names it */
+#define IGA_ENOT_CONVERGED 4  /* PCG reached max_iter above the tolerance */
+#define IGA_ENUMERIC 5        /* NaN/Inf or non-positive curvature p.Mp in PCG */
+#define IGA_EUNSTABLE 6       /* energy growth detected (time step above the CFL limit) */
+#define IGA_EGEOMETRY 7       /* det DF <= 0 at a quadrature point (Sec. 5.3, Assumption g_regularity) */
+
+/* Form of the K and M operators. */
+#define IGA_OP_MATRIX_FREE 0  /* sum-factorised at the Gauss points (default) */
+#define IGA_OP_ASSEMBLED 1    /* assembled band rows, (2p+1)^d coefficients per row */
+
+/* Arithmetic of the preconditioner's fast-diagonalisation mode products. */
+#define IGA_PREC_FP64 0       /* FP64 (default); plain CG */
+#define IGA_PREC_FP32 1       /* FP32 CUDA cores; flexible CG */
+#define IGA_PREC_BF16 2       /* BF16 tensor cores, FP32 accumulation; flexible CG */
+#define IGA_PREC_FP16 3       /* FP16 tensor cores, FP32 accumulation; flexible CG */
+
+/* Initial guess of each mass solve inside a time step. */
+#define IGA_GUESS_ZERO 0      /* null vector, as in the paper's experiments (Sec. 6) */
+#define IGA_GUESS_PREV 1      /* the same block's solution at the previous step */
+#define IGA_GUESS_EXTRAP 2    /* 2 Z^{n-1} - Z^{n-2} */
+#define IGA_GUESS_TAYLOR 3    /* the Taylor predictor T_{s_j} of the solved variable */
+
+typedef struct iga_options {
+  int nquad;        /* Gauss points per element and direction; 0 => max_a(p_a) + 1 */
+  double tol;       /* PCG stopping rule ||r||_2 <= tol * ||b||_2; default 1e-10 */
+  int max_iter;     /* PCG iteration cap per solve; default 500 */
+  int precond;      /* IGA_PREC_*; default IGA_PREC_FP64 */
+  int op_form;      /* IGA_OP_*; default IGA_OP_MATRIX_FREE */
+  int guess;        /* IGA_GUESS_*; default IGA_GUESS_ZERO */
+  int device;       /* CUDA device ordinal; default 0 */
+  void* stream;     /* cudaStream_t for all work, NULL = legacy default stream */
+} iga_options;
+
+typedef struct iga_stats {
+  int steps;            /* time steps taken by the call */
+  int solves;           /* mass-matrix solves */
+  long long iters;      /* PCG iterations summed over the solves */
+  int max_iters;        /* largest iteration count of one solve */
+  double max_relres;    /* largest final ||r||/||b|| */
+} iga_stats;
+
+typedef struct iga_handle iga_handle;
+
+/* Fill *opt with the defaults listed above. */
+void iga_options_default(iga_options* opt);
+
+/* Static text for a status code. */
+const char* iga_status_string(int status);
+
+/* Message of the last failed call on h (empty string if none); valid until the
+ * next call on h. h may be NULL for failures of iga_create. */
+const char* iga_last_error(const iga_handle* h);
+
+/*
+ * iga_create -- set up one patch (Sec. 5.1-5.2).
+ *   dim        2 or 3.
+ *   degree     [dim] spline degrees p_a >= 1 (at most 6).
+ *   nknots     [dim] knot-vector lengths; m_a = nknots[a] - p_a - 1 functions, m_a >= 3.
+ *   knots      [dim] host pointers to open knot vectors on [0, 1] (first and last knot
+ *              repeated p_a + 1 times, non-decreasing, interior multiplicity <= p_a).
+ *   ctrl       host, full control net: prod_a m_a points, co-lexicographic, dim
+ *              coordinates per point (point-major). The geometry is
+ *              F(xi) = sum_i C_i B_i(xi).
+ *   opt        options (NULL => defaults); copied.
+ *   out        receives the handle.
+ * All inputs are copied; the caller keeps ownership. Builds the univariate
+ * Gauss tables, the geometric factors at every quadrature point (W = w|det DF|
+ * and G = W DF^{-1} DF^{-T}), diag(M), and the fast-diagonalisation factors
+ * Mhat_a = U_a Lambda_a U_a^T of the preconditioner. Returns IGA_EGEOMETRY if
+ * det DF <= 0 at some quadrature point.
+ */
+int iga_create(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
+               const iga_options* opt, iga_handle** out);
+
+/* Release every resource of h (NULL is allowed). */
+void iga_destroy(iga_handle* h);
+
+/* Number of interior degrees of freedom N. */
+int iga_ndof(const iga_handle* h, long long* ndof);
+
+/*
+ * iga_assemble -- build the assembled band rows of M and K (IGA_OP_ASSEMBLED form).
+ * Idempotent. Called implicitly by the first operator use when op_form is
+ * IGA_OP_ASSEMBLED. Memory: 2 * N * prod_a (2 p_a + 1) * 8 bytes of device memory.
+ */
+int iga_assemble(iga_handle* h);
+
+/* Switch the operator form / preconditioner arithmetic / guess / tolerance of an
+ * existing handle (same meanings as in iga_options). */
+int iga_set_op_form(iga_handle* h, int op_form);
+int iga_set_precond(iga_handle* h, int precond);
+int iga_set_guess(iga_handle* h, int guess);
+int iga_set_tol(iga_handle* h, double tol, int max_iter);
+
+/*
+ * Operators (device pointers). x and y hold nvec vectors of N doubles each,
+ * vector v at offset v*N; x and y must not overlap.
+ *   iga_apply_M:    y = M x, [M]_ij = int B_i B_j |det DF| (Sec. 5.3, eq. mass_matrix).
+ *   iga_apply_K:    y = K x, K_ij = int grad B_i . grad B_j (Galerkin form of eq. pde, omega = 1).
+ *   iga_apply_Pinv: y = D^{-1/2} Dhat^{1/2} Mhat^{-1} Dhat^{1/2} D^{-1/2} x, the inverse of
+ *                   the preconditioner of Sec. 5.3 (def:single_patch_prec, def:matrices_1),
+ *                   in the arithmetic chosen by iga_options.precond.
+ * 1 <= nvec <= 8.
+ */
+int iga_apply_M(iga_handle* h, int nvec, const double* x, double* y);
+int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y);
+int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y);
+
+/*
+ * iga_solve_M -- solve M x_v = b_v for nvec independent right-hand sides by
+ * preconditioned CG (Sec. 5.5), stopping each at ||r||_2 <= tol ||b||_2.
+ * b, x: device, nvec*N doubles. use_x0 != 0 takes x as the initial guess, else
+ * the null vector. iters (host, [nvec], may be NULL) receives the iteration
+ * counts, relres (host, [nvec], may be NULL) the final ||r||/||b||.
+ * Synchronises the stream. IGA_ENOT_CONVERGED / IGA_ENUMERIC on failure.
+ */
+int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0, int* iters, double* relres);
+
+/*
+ * iga_galpha_params -- the method's parameters for order 2k and user parameter
+ * rho_inf in [0, 1] (Sec. 4.1, boxed formulas with rho_b = rho_s; eq. HOgamma):
+ * alpha[k], beta[k], gamma[k] (host arrays, block j at index j-1).
+ */
+int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double* gamma);
+
+/*
+ * iga_cfl -- largest eigenvalue of M^{-1} K by power iteration (iters steps, each
+ * one K product and one PCG solve), and the critical step
+ * tau_crit = sqrt(Theta_crit(rho_inf) / lambda_max), Theta_crit = 12(1+rho)(2-rho)/(rho^2-5rho+10),
+ * the k-independent stability limit of the method (Sec. 3.2 and 4.1).
+ * lambda_max and tau_crit are host pointers.
+ */
+int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double* tau_crit);
+
+/*
+ * iga_state_init -- initial high-order data (Sec. 3, after eq. 4aup; C = 0, F = 0):
+ * X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3, with X_{-2} = U0, X_{-1} = V0.
+ *   k      order parameter, 1 <= k <= 4 (order 2k).
+ *   U0, V0 device, N doubles each.
+ *   state  device, 3k*N doubles, caller-owned: rows U, V, A, L^1, ..., L^{3k-3}.
+ * Also resets the per-handle history used by the PREV / EXTRAP guesses.
+ * Synchronises the stream.
+ */
+int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, double* state);
+
+/*
+ * iga_step -- advance state (device, 3k*N doubles, layout of iga_state_init) by
+ * nsteps explicit steps of size dt (Sec. 4, eq. ho1-ho3). Each step: Taylor
+ * predictor, one batched K product over the k predicted vectors, k mass solves
+ * by PCG (batched), fused update of the 3k variables. stats (host, may be NULL)
+ * accumulates counters. Synchronises the stream.
+ */
+int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int nsteps, iga_stats* stats);
+
+/*
+ * iga_step_host -- iga_step on a HOST state buffer (3k*N doubles): copies the
+ * state to the device, steps, and copies it back, inside the call.
+ */
+int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, double dt, int nsteps,
+                  iga_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_GALPHA_H */

@@ -56,6 +56,8 @@ def lib():
         L.ora_assemble_rows.restype = ctypes.c_int
         L.ora_band_matvec.argtypes = [ip, ip, dp, dp, dp]
         L.ora_band_matvec.restype = None
+        L.ora_mass_diagonal.argtypes = [ip, dp, ip, dp, dp, dp, dp]
+        L.ora_mass_diagonal.restype = ctypes.c_int
         L.ora_num_threads.argtypes = []
         L.ora_num_threads.restype = ctypes.c_int
         _LIB = L
@@ -200,6 +202,26 @@ class Patch:
                                 _d(Kr) if stiffness else None)
         return Mr, Kr
 
+    def mass_diagonal(self):
+        """diag(M) without assembling M (ora_mass_diagonal)."""
+        D = np.zeros(self.N)
+        lib().ora_mass_diagonal(_i(self.dims), _d(self.qw_all), _i(self.qfirst_all), _d(self.qval_all),
+                                _d(self.qder_all), _d(self.W), _d(D))
+        return D
+
+    def band_rows_times(self, rows, A, x):
+        """(A x)_i for the given rows, A holding those rows' band slots (sampled checks)."""
+        n3 = self.n + [1] * (3 - self.d)
+        offs = self.slot_offsets()
+        out = np.zeros(len(rows))
+        for r, i in enumerate(rows):
+            i0, i1, i2 = i % n3[0], (i // n3[0]) % n3[1], i // (n3[0] * n3[1])
+            j0, j1, j2 = i0 + offs[:, 0], i1 + offs[:, 1], i2 + offs[:, 2]
+            ok = (j0 >= 0) & (j0 < n3[0]) & (j1 >= 0) & (j1 < n3[1]) & (j2 >= 0) & (j2 < n3[2])
+            j = j0 + n3[0] * (j1 + n3[1] * j2)
+            out[r] = np.sum(A[r][ok] * x[j[ok]])
+        return out
+
     def slot_offsets(self):
         """(S, 3) integer offsets (o0, o1, o2) of the band slots."""
         p3 = self.p + [0] * (3 - self.d)
@@ -236,21 +258,19 @@ class Patch:
 # ----------------------------------------------------------------------------
 # Operators and the preconditioner (Sec. 5.3, 5.5)
 # ----------------------------------------------------------------------------
-class Operators:
-    """Assembled M and K with the preconditioner
-       P = D^{1/2} Dhat^{-1/2} Mhat Dhat^{-1/2} D^{1/2}   (def:single_patch_prec)
-    where Mhat = Mhat_3 (x) Mhat_2 (x) Mhat_1 is the parametric (F = identity) mass
-    matrix, Dhat = diag(Mhat), D = diag(M) (def:matrices_1). Mhat^{-1} is applied
-    through the Kronecker structure by banded Cholesky solves along each direction."""
+class Preconditioner:
+    """The preconditioner P = D^{1/2} Dhat^{-1/2} Mhat Dhat^{-1/2} D^{1/2}
+    (def:single_patch_prec), Mhat = Mhat_3 (x) Mhat_2 (x) Mhat_1 the parametric
+    (F = identity) mass matrix, Dhat = diag(Mhat), D = diag(M) (def:matrices_1).
+    Mhat^{-1} is applied through the Kronecker structure by banded Cholesky solves
+    along each direction. D defaults to ora_mass_diagonal."""
 
-    def __init__(self, patch: Patch, stiffness=True):
+    def __init__(self, patch: Patch, D=None):
         self.patch = patch
         self.d = patch.d
         self.n = patch.n
         self.N = patch.N
-        self.M, self.K = patch.assemble(stiffness=stiffness)
-        centre = patch.nslots // 2
-        self.D = self.M[:, centre].copy()
+        self.D = patch.mass_diagonal() if D is None else D
         self.Mhat = [patch.q1[a].mass_interior() for a in range(self.d)]
         self.cho = []
         for a in range(self.d):
@@ -267,12 +287,6 @@ class Operators:
         self.Dhat = dh
         self.scale = np.sqrt(self.Dhat / self.D)  # D^{-1/2} Dhat^{1/2}
 
-    def apply_M(self, x):
-        return self.patch.band_matvec(self.M, x)
-
-    def apply_K(self, x):
-        return self.patch.band_matvec(self.K, x)
-
     def kron_solve(self, r):
         """Mhat^{-1} r, one banded Cholesky solve along each direction (Kronecker inverse)."""
         shape = tuple(reversed(self.n))  # C-order array (i_{d-1}, ..., i_0)
@@ -288,6 +302,30 @@ class Operators:
     def apply_Pinv(self, r):
         """z = D^{-1/2} Dhat^{1/2} Mhat^{-1} Dhat^{1/2} D^{-1/2} r."""
         return self.scale * self.kron_solve(self.scale * r)
+
+
+class Operators:
+    """Assembled M and K (band rows) with the preconditioner of Sec. 5.3; D is the
+    centre slot (the diagonal) of the assembled M."""
+
+    def __init__(self, patch: Patch, stiffness=True):
+        self.patch = patch
+        self.d = patch.d
+        self.n = patch.n
+        self.N = patch.N
+        self.M, self.K = patch.assemble(stiffness=stiffness)
+        self.pre = Preconditioner(patch, D=self.M[:, patch.nslots // 2].copy())
+        self.D = self.pre.D
+        self.Mhat = self.pre.Mhat
+
+    def apply_M(self, x):
+        return self.patch.band_matvec(self.M, x)
+
+    def apply_K(self, x):
+        return self.patch.band_matvec(self.K, x)
+
+    def apply_Pinv(self, r):
+        return self.pre.apply_Pinv(r)
 
 
 def pcg(apply_A, apply_Pinv, b, x0=None, tol=1e-10, max_iter=500):

@@ -401,9 +401,15 @@ int ora_assemble_rows(const int* dims, const double* qw, const int* qfirst, cons
           double wq = W[qi];
           int q[3] = {q0, q1, q2};
           int j0[3], j1[3];
+          /* values / derivatives of the functions nonzero at this point, per direction */
+          double vj[3][16], dj[3][16];
           for (int a = 0; a < 3; ++a) {
             j0[a] = a < d ? g.qfirst[a][q[a]] : 0;
             j1[a] = a < d ? j0[a] + g.p[a] : 0;
+            for (int c = j0[a]; c <= j1[a]; ++c) {
+              vj[a][c - j0[a]] = bval(&g, a, q[a], c);
+              dj[a][c - j0[a]] = bder(&g, a, q[a], c);
+            }
           }
           for (int c2 = j0[2]; c2 <= j1[2]; ++c2) {
             if (d > 2 && (c2 == 0 || c2 == g.m[2] - 1)) continue;
@@ -415,12 +421,12 @@ int ora_assemble_rows(const int* dims, const double* qw, const int* qfirst, cons
                 if (o0 < -g.p[0] || o0 > g.p[0] || o1 < -g.p[1] || o1 > g.p[1] || o2 < -g.p[2] || o2 > g.p[2])
                   continue;
                 long slot = (o0 + g.p[0]) + (long)S1[0] * ((o1 + g.p[1]) + (long)S1[1] * (o2 + g.p[2]));
-                double vj0 = bval(&g, 0, q0, c0), vj1 = bval(&g, 1, q1, c1), vj2 = bval(&g, 2, q2, c2);
+                double vj0 = vj[0][c0 - j0[0]], vj1 = vj[1][c1 - j0[1]], vj2 = vj[2][c2 - j0[2]];
                 Mr[slot] += bi * vj0 * vj1 * vj2 * wq;
                 if (Kr) {
-                  double gj0 = bder(&g, 0, q0, c0) * vj1 * vj2;
-                  double gj1 = vj0 * bder(&g, 1, q1, c1) * vj2;
-                  double gj2 = vj0 * vj1 * bder(&g, 2, q2, c2);
+                  double gj0 = dj[0][c0 - j0[0]] * vj1 * vj2;
+                  double gj1 = vj0 * dj[1][c1 - j0[1]] * vj2;
+                  double gj2 = vj0 * vj1 * dj[2][c2 - j0[2]];
                   Kr[slot] += gj0 * h[0] + gj1 * h[1] + gj2 * h[2];
                 }
               }
@@ -461,4 +467,42 @@ void ora_band_matvec(const int* n, const int* p, const double* A, const double* 
     }
     y[i] = acc;
   }
+}
+
+/* ---------------------------------------------------------------------------
+ * Diagonal of the interior mass matrix, D_i = M_ii = sum_q B_i(q)^2 W(q) over
+ * the quadrature points in the support of B_i (def:matrices_1, D = diag(M)).
+ * ------------------------------------------------------------------------- */
+int ora_mass_diagonal(const int* dims, const double* qw, const int* qfirst, const double* qval, const double* qder,
+                      const double* W, double* D) {
+  mesh_t g;
+  mesh_from(&g, dims, qw, qfirst, qval, qder);
+  const int d = g.d;
+  int n[3];
+  for (int a = 0; a < 3; ++a) n[a] = a < d ? g.m[a] - 2 : 1;
+  const long N = (long)n[0] * n[1] * n[2];
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < N; ++i) {
+    int f[3];
+    f[0] = (int)(i % n[0]) + 1;
+    f[1] = (int)((i / n[0]) % n[1]) + (d > 1 ? 1 : 0);
+    f[2] = (int)(i / ((long)n[0] * n[1])) + (d > 2 ? 1 : 0);
+    double acc = 0.0;
+    for (int q2 = 0; q2 < g.Q[2]; ++q2) {
+      double v2 = bval(&g, 2, q2, f[2]);
+      if (v2 == 0.0) continue;
+      for (int q1 = 0; q1 < g.Q[1]; ++q1) {
+        double v1 = bval(&g, 1, q1, f[1]);
+        if (v1 == 0.0) continue;
+        for (int q0 = 0; q0 < g.Q[0]; ++q0) {
+          double v0 = bval(&g, 0, q0, f[0]);
+          if (v0 == 0.0) continue;
+          double b = v0 * v1 * v2;
+          acc += b * b * W[q0 + (long)g.Q[0] * (q1 + (long)g.Q[1] * q2)];
+        }
+      }
+    }
+    D[i] = acc;
+  }
+  return 0;
 }

@@ -1,0 +1,243 @@
+"""GB300 (sm_103a) implementation of the per-time-step hot path of the explicit
+2k-order generalized-alpha method for isogeometric structural dynamics
+(arXiv 2102.11536).
+
+This module is a thin ctypes binding over libiga_galpha.so, whose C ABI is
+declared in include/iga_galpha.h: it only marshals arguments. Every step of the
+path runs in the library's CUDA kernels; there is no CPU fallback, and a missing
+library raises at first use.
+
+Device buffers are passed as torch CUDA tensors (float64, contiguous) or raw
+integer device addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiga_galpha.so")
+_LIB = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENOT_CONVERGED, ENUMERIC, EUNSTABLE, EGEOMETRY = range(8)
+OP_FORMS = {"matrix_free": 0, "assembled": 1}
+PRECONDS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+GUESSES = {"zero": 0, "prev": 1, "extrap": 2, "taylor": 3}
+
+
+class IgaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("nquad", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("precond", ctypes.c_int), ("op_form", ctypes.c_int), ("guess", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("solves", ctypes.c_int), ("iters", ctypes.c_longlong),
+                ("max_iters", ctypes.c_int), ("max_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    """Load libiga_galpha.so (built by __graft_entry__.build() or paper_2102_11536_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libiga_galpha.so is not built (run __graft_entry__.build()); "
+                          "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    H = ctypes.c_void_p
+    sig = {
+        "iga_options_default": (None, [ctypes.POINTER(Options)]),
+        "iga_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "iga_last_error": (ctypes.c_char_p, [H]),
+        "iga_create": (ctypes.c_int, [ctypes.c_int, ip, ip, ctypes.POINTER(dp), dp, ctypes.POINTER(Options),
+                                      ctypes.POINTER(H)]),
+        "iga_destroy": (None, [H]),
+        "iga_ndof": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_longlong)]),
+        "iga_assemble": (ctypes.c_int, [H]),
+        "iga_set_op_form": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_set_precond": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_set_guess": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_set_tol": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_int]),
+        "iga_apply_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
+        "iga_apply_K": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
+        "iga_apply_Pinv": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
+        "iga_solve_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp, ctypes.c_int, ip, dp]),
+        "iga_galpha_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, dp, dp, dp]),
+        "iga_cfl": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_int, dp, dp]),
+        "iga_state_init": (ctypes.c_int, [H, ctypes.c_int, vp, vp, vp]),
+        "iga_step": (ctypes.c_int, [H, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(Stats)]),
+        "iga_step_host": (ctypes.c_int, [H, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points this binding expects the library to export."""
+    return ["iga_options_default", "iga_status_string", "iga_last_error", "iga_create", "iga_destroy",
+            "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
+            "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
+            "iga_state_init", "iga_step", "iga_step_host"]
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):  # numpy array (host memory)
+        return t.ctypes.data
+    raise TypeError("expected a tensor, a numpy array or an integer address")
+
+
+def _check_dev(t, n, name):
+    if isinstance(t, int):
+        return
+    if getattr(t, "is_cuda", False) is not True:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    import torch
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() < n:
+        raise ValueError("%s must be a contiguous float64 tensor with at least %d elements" % (name, n))
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def galpha_params(k: int, rho: float):
+    """(alpha, beta, gamma) lists of the method for order 2k (Sec. 4.1)."""
+    a = (ctypes.c_double * k)()
+    b = (ctypes.c_double * k)()
+    g = (ctypes.c_double * k)()
+    rc = lib().iga_galpha_params(k, rho, a, b, g)
+    if rc != OK:
+        raise IgaError(rc, "iga_galpha_params")
+    return list(a), list(b), list(g)
+
+
+class Patch:
+    """One B-spline patch on the GPU (iga_create / iga_destroy)."""
+
+    def __init__(self, degrees, knots, ctrl, nquad=0, tol=1e-10, max_iter=500, precond="fp64",
+                 op_form="matrix_free", guess="zero", device=0, stream="current"):
+        import numpy as np
+        L = lib()
+        self.d = len(degrees)
+        opt = Options()
+        L.iga_options_default(ctypes.byref(opt))
+        opt.nquad, opt.tol, opt.max_iter = nquad, tol, max_iter
+        opt.precond, opt.op_form, opt.guess = PRECONDS[precond], OP_FORMS[op_form], GUESSES[guess]
+        opt.device = device
+        opt.stream = _default_stream() if stream == "current" else stream
+        deg = (ctypes.c_int * self.d)(*[int(p) for p in degrees])
+        self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        nk = (ctypes.c_int * self.d)(*[len(k) for k in self._knots])
+        kp = (ctypes.POINTER(ctypes.c_double) * self.d)(
+            *[k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k in self._knots])
+        c = np.ascontiguousarray(ctrl, dtype=np.float64)
+        h = ctypes.c_void_p()
+        rc = L.iga_create(self.d, deg, nk, kp, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          ctypes.byref(opt), ctypes.byref(h))
+        if rc != OK:
+            raise IgaError(rc, "iga_create: " + L.iga_last_error(None).decode())
+        self.h = h
+        n = ctypes.c_longlong()
+        L.iga_ndof(h, ctypes.byref(n))
+        self.N = int(n.value)
+
+    def _chk(self, rc, what):
+        if rc != OK:
+            raise IgaError(rc, "%s: %s" % (what, lib().iga_last_error(self.h).decode()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().iga_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def assemble(self):
+        self._chk(lib().iga_assemble(self.h), "iga_assemble")
+
+    def set_op_form(self, form):
+        self._chk(lib().iga_set_op_form(self.h, OP_FORMS[form]), "iga_set_op_form")
+
+    def set_precond(self, prec):
+        self._chk(lib().iga_set_precond(self.h, PRECONDS[prec]), "iga_set_precond")
+
+    def set_guess(self, guess):
+        self._chk(lib().iga_set_guess(self.h, GUESSES[guess]), "iga_set_guess")
+
+    def set_tol(self, tol, max_iter=500):
+        self._chk(lib().iga_set_tol(self.h, tol, max_iter), "iga_set_tol")
+
+    def apply_M(self, x, y, nvec=1):
+        _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")
+        self._chk(lib().iga_apply_M(self.h, nvec, _ptr(x), _ptr(y)), "iga_apply_M")
+
+    def apply_K(self, x, y, nvec=1):
+        _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")
+        self._chk(lib().iga_apply_K(self.h, nvec, _ptr(x), _ptr(y)), "iga_apply_K")
+
+    def apply_Pinv(self, x, y, nvec=1):
+        _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")
+        self._chk(lib().iga_apply_Pinv(self.h, nvec, _ptr(x), _ptr(y)), "iga_apply_Pinv")
+
+    def solve_M(self, b, x, nvec=1, use_x0=False):
+        _check_dev(b, nvec * self.N, "b"); _check_dev(x, nvec * self.N, "x")
+        its = (ctypes.c_int * nvec)()
+        rel = (ctypes.c_double * nvec)()
+        self._chk(lib().iga_solve_M(self.h, nvec, _ptr(b), _ptr(x), int(use_x0), its, rel), "iga_solve_M")
+        return list(its), list(rel)
+
+    def cfl(self, rho, iters=100):
+        lam = ctypes.c_double()
+        tc = ctypes.c_double()
+        self._chk(lib().iga_cfl(self.h, rho, iters, ctypes.byref(lam), ctypes.byref(tc)), "iga_cfl")
+        return lam.value, tc.value
+
+    def state_init(self, k, U0, V0, state):
+        _check_dev(U0, self.N, "U0"); _check_dev(V0, self.N, "V0"); _check_dev(state, 3 * k * self.N, "state")
+        self._chk(lib().iga_state_init(self.h, k, _ptr(U0), _ptr(V0), _ptr(state)), "iga_state_init")
+
+    def step(self, state, k, rho, dt, nsteps=1, stats=None):
+        _check_dev(state, 3 * k * self.N, "state")
+        st = stats if stats is not None else Stats()
+        self._chk(lib().iga_step(self.h, _ptr(state), k, rho, dt, nsteps, ctypes.byref(st)), "iga_step")
+        return st
+
+    def step_host(self, state_host, k, rho, dt, nsteps=1, stats=None):
+        """state_host: host buffer (numpy array or pinned CPU tensor) of 3k*N float64."""
+        st = stats if stats is not None else Stats()
+        self._chk(lib().iga_step_host(self.h, _ptr(state_host), k, rho, dt, nsteps, ctypes.byref(st)),
+                  "iga_step_host")
+        return st

@@ -1,0 +1,731 @@
+// C ABI of the GB300 explicit generalized-alpha IGA library (include/iga_galpha.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "iga_internal.h"
+
+using namespace iga;
+
+struct iga_handle {
+  int dim = 0;
+  iga_options opt{};
+  cudaStream_t stream = nullptr;
+  Tables1D tab[3];
+  DirDev dd[3]{};
+  int n[3] = {1, 1, 1}, Q[3] = {1, 1, 1}, m[3] = {1, 1, 1};
+  long long N = 0, Qt = 0;
+  double* ctrl = nullptr;   // SoA control net
+  double* W = nullptr;      // [Qt]
+  double* G = nullptr;      // [ng][Qt]
+  long long gstride = 0;
+  double* Dm = nullptr;     // diag(M)
+  double* scale = nullptr;  // D^{-1/2} Dhat^{1/2}
+  int* dflag = nullptr;     // device scratch flag
+  // assembled form
+  double* Mband = nullptr;
+  double* Kband = nullptr;
+  // operator workspace
+  int ws_vec = 0;
+  double *u0 = nullptr, *u1 = nullptr, *ta = nullptr, *tb = nullptr, *tc = nullptr;
+  long long su = 0, st = 0;
+  // PCG workspace
+  int cg_vec = 0;
+  double *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *f1 = nullptr, *f2 = nullptr;
+  double* partial = nullptr;  // 3 * kMaxVec * kRedBlocks
+  CgScalars cs{};
+  int* h_nactive = nullptr;   // pinned
+  // stepping
+  int step_k = 0;
+  double *Yneg = nullptr, *rhs = nullptr, *Z = nullptr, *Z2 = nullptr;
+  int hist = 0;
+  double* dstate = nullptr;
+  long long dstate_cap = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(iga_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(h, IGA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+#define CKS(expr)                   \
+  do {                              \
+    int s_ = (expr);                \
+    if (s_ != IGA_OK) return s_;    \
+  } while (0)
+
+template <typename T>
+int dalloc(iga_handle* h, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(h, IGA_ENOMEM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + " bytes): " +
+                                   cudaGetErrorString(e));
+  }
+  return IGA_OK;
+}
+
+template <typename T>
+int upload(iga_handle* h, T** p, const std::vector<T>& v) {
+  CKS(dalloc(h, p, v.size()));
+  CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return IGA_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// -- the method's parameters (Sec. 4.1, boxed formulas; eq. HOgamma) ----------
+// Block j = k: rho_b = rho_s = rho, alpha_f = 0. Blocks j < k: the boxed j<k
+// formulas at rho_b = rho_s = -rho (the reading that keeps the stability limit of
+// every block equal to that of the last one), alpha_f = 1.
+void galpha_params(int k, double rho, double* alpha, double* beta, double* gamma) {
+  for (int j = 1; j <= k; ++j) {
+    double a, b, af;
+    if (j == k) {
+      const double rb = rho, rs = rho;
+      a = (2.0 + (1.0 - rb) * rs) / ((1.0 + rb) * (1.0 + rs));
+      b = (-5.0 - 3.0 * rb - 4.0 * rs + 2.0 * rb * rs + 2.0 * rb * rb * rs - rs * rs + rb * rs * rs) /
+          ((1.0 + rb) * (1.0 + rb) * (-2.0 - 3.0 * rs + rb * rs - rs * rs + rb * rs * rs));
+      af = 0.0;
+    } else {
+      const double rb = -rho, rs = -rho;
+      a = (2.0 - (1.0 + rb) * rs) / ((rb - 1.0) * (rs - 1.0));
+      b = (1.0 + rb) * (rb * rs - 1.0) * (rb * rs - 1.0) /
+          ((rb - 1.0) * (rb - 1.0) * (rs - 1.0) * (rs + rb * rs - 2.0));
+      af = 1.0;
+    }
+    alpha[j - 1] = a;
+    beta[j - 1] = b;
+    gamma[j - 1] = 0.5 - af + a;
+  }
+}
+
+double theta_crit(double rho) { return 12.0 * (1.0 + rho) * (2.0 - rho) / (rho * rho - 5.0 * rho + 10.0); }
+
+int ensure_op_ws(iga_handle* h, int nvec) {
+  if (h->ws_vec >= nvec) return IGA_OK;
+  if (h->dim == 3) {
+    h->su = (long long)h->Q[0] * h->n[1] * h->n[2];
+    h->st = (long long)h->Q[0] * h->Q[1] * h->n[2];
+    CKS(dalloc(h, &h->u0, (size_t)(nvec * h->su)));
+    CKS(dalloc(h, &h->u1, (size_t)(nvec * h->su)));
+    CKS(dalloc(h, &h->ta, (size_t)(nvec * h->st)));
+    CKS(dalloc(h, &h->tb, (size_t)(nvec * h->st)));
+    CKS(dalloc(h, &h->tc, (size_t)(nvec * h->st)));
+  } else {
+    h->su = (long long)h->Q[0] * h->n[1];
+    h->st = 0;
+    CKS(dalloc(h, &h->u0, (size_t)(nvec * h->su)));
+    CKS(dalloc(h, &h->u1, (size_t)(nvec * h->su)));
+  }
+  h->ws_vec = nvec;
+  return IGA_OK;
+}
+
+int ensure_cg_ws(iga_handle* h, int nvec) {
+  if (h->cg_vec >= nvec) return IGA_OK;
+  const size_t sz = (size_t)nvec * h->N;
+  CKS(dalloc(h, &h->r, sz));
+  CKS(dalloc(h, &h->z, sz));
+  CKS(dalloc(h, &h->zold, sz));
+  CKS(dalloc(h, &h->p, sz));
+  CKS(dalloc(h, &h->q, sz));
+  CKS(dalloc(h, &h->f1, sz));
+  CKS(dalloc(h, &h->f2, sz));
+  h->cg_vec = nvec;
+  return IGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+int apply_M_mf(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  CKS(ensure_op_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const int *n = h->n, *Q = h->Q;
+  const DirDev* d = h->dd;
+  if (h->dim == 3) {
+    CK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, nullptr, nullptr, h->st));
+    CK(launch_mid_mass(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->W, h->ta, h->ta, h->st));
+    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, nullptr, nullptr, h->st, h->u0, h->su));
+    CK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
+  } else {
+    CK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    CK(launch_mid_mass(s, d[1], Q[0], nvec, active, h->W, h->u0, h->u0, h->su));
+    CK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
+  }
+  return IGA_OK;
+}
+
+int apply_K_mf(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  CKS(ensure_op_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const int *n = h->n, *Q = h->Q;
+  const DirDev* d = h->dd;
+  if (h->dim == 3) {
+    CK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
+    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, d[1].der, h->tb, h->st));
+    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u1, h->su, d[1].val, h->tc, nullptr, nullptr, h->st));
+    CK(launch_mid_stiff3(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->G, h->gstride, h->ta, h->tb, h->tc, h->st));
+    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, h->tb, d[1].der, h->st, h->u0, h->su));
+    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->tc, d[1].val, nullptr, nullptr, h->st, h->u1, h->su));
+    CK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
+  } else {
+    CK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
+    CK(launch_mid_stiff2(s, d[1], Q[0], nvec, active, h->G, h->gstride, h->u0, h->u1, h->su));
+    CK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
+  }
+  return IGA_OK;
+}
+
+int apply_Pinv_fd64(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
+  CKS(ensure_cg_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const int* n = h->n;
+  const DirDev* d = h->dd;
+  double *t1 = h->f1, *t2 = h->f2;
+  FdEpilogue none{};
+  FdEpilogue lam{};
+  lam.lam[0] = d[0].lam64;
+  lam.lam[1] = d[1].lam64;
+  lam.lam[2] = h->dim == 3 ? d[2].lam64 : nullptr;
+  lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
+  FdEpilogue post{};
+  post.post = h->scale;
+  const long long N = h->N;
+  if (h->dim == 3) {
+    const long long n01 = (long long)n[0] * n[1];
+    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n01 / n[0] * n[2]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
+    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
+    CK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
+    CK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
+    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
+  } else {
+    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
+    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
+    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
+  }
+  return IGA_OK;
+}
+
+int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  return apply_M_mf(h, nvec, active, x, y);
+}
+int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  return apply_K_mf(h, nvec, active, x, y);
+}
+int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
+  return apply_Pinv_fd64(h, nvec, active, r, z);
+}
+
+// ---------------------------------------------------------------------------
+// batched PCG
+// ---------------------------------------------------------------------------
+int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int* iters, double* relres) {
+  CKS(ensure_cg_ws(h, nvec));
+  CKS(ensure_op_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const long long N = h->N;
+  CgScalars& c = h->cs;
+  double* pA = h->partial;
+  double* pB = h->partial + kMaxVec * kRedBlocks;
+  double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
+  const double tol2 = h->opt.tol * h->opt.tol;
+  const bool flexible = h->opt.precond != IGA_PREC_FP64;
+  if (use_x0) {
+    CKS(apply_M(h, nvec, nullptr, x, h->q));
+    CK(launch_sub(s, N, nvec, b, h->q, h->r, N));
+  } else {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * nvec * N, s));
+    CK(cudaMemcpyAsync(h->r, b, sizeof(double) * nvec * N, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(launch_dot(s, N, nvec, b, b, N, pA));
+  CK(launch_dot(s, N, nvec, h->r, h->r, N, pB));
+  CK(launch_cg_init(s, nvec, pA, pB, c, tol2));
+  CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int nact = *h->h_nactive;
+  if (nact > 0) {
+    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
+    CK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+    CK(launch_cg_start(s, nvec, pA, c));
+    CK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
+  }
+  int it = 0;
+  while (nact > 0 && it < h->opt.max_iter) {
+    CKS(apply_M(h, nvec, c.active, h->p, h->q));
+    CK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
+    CK(launch_cg_alpha(s, nvec, pA, c));
+    CK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
+    CK(launch_cg_check(s, nvec, pB, c, tol2));
+    CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    nact = *h->h_nactive;
+    ++it;
+    if (nact == 0) break;
+    if (flexible) std::swap(h->z, h->zold);
+    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
+    CK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+    if (flexible) CK(launch_dot(s, N, nvec, h->r, h->zold, N, pC));
+    CK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
+    CK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
+  }
+  int hit[kMaxVec], hst[kMaxVec];
+  double hrr[kMaxVec], hbb[kMaxVec];
+  CK(cudaMemcpyAsync(hit, c.iters, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hst, c.status, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hrr, c.rr, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hbb, c.bb, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int status = IGA_OK;
+  for (int v = 0; v < nvec; ++v) {
+    const double rel = hbb[v] > 0 ? std::sqrt(hrr[v] / hbb[v]) : 0.0;
+    if (iters) iters[v] = hit[v];
+    if (relres) relres[v] = rel;
+    if (hst[v] != 0) status = IGA_ENUMERIC;
+  }
+  if (status != IGA_OK) return fail(h, status, "PCG breakdown (non-positive curvature or non-finite values)");
+  if (nact > 0) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "PCG did not reach tol %.3g in %d iterations", h->opt.tol, h->opt.max_iter);
+    return fail(h, IGA_ENOT_CONVERGED, buf);
+  }
+  return IGA_OK;
+}
+
+int check_handle(iga_handle* h) {
+  if (!h) return IGA_EINVAL;
+  h->err.clear();
+  cudaError_t e = cudaSetDevice(h->opt.device);
+  if (e != cudaSuccess) return fail(h, IGA_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return IGA_OK;
+}
+
+int ensure_step_ws(iga_handle* h, int k) {
+  if (h->step_k >= k) return IGA_OK;
+  const size_t sz = (size_t)k * h->N;
+  CKS(dalloc(h, &h->Yneg, sz));
+  CKS(dalloc(h, &h->rhs, sz));
+  CKS(dalloc(h, &h->Z, sz));
+  CKS(dalloc(h, &h->Z2, sz));
+  h->step_k = k;
+  return IGA_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// public API
+// ===========================================================================
+extern "C" {
+
+void iga_options_default(iga_options* opt) {
+  if (!opt) return;
+  opt->nquad = 0;
+  opt->tol = 1e-10;
+  opt->max_iter = 500;
+  opt->precond = IGA_PREC_FP64;
+  opt->op_form = IGA_OP_MATRIX_FREE;
+  opt->guess = IGA_GUESS_ZERO;
+  opt->device = 0;
+  opt->stream = nullptr;
+}
+
+const char* iga_status_string(int status) {
+  switch (status) {
+    case IGA_OK: return "ok";
+    case IGA_EINVAL: return "invalid argument";
+    case IGA_ENOMEM: return "out of memory";
+    case IGA_ECUDA: return "CUDA error";
+    case IGA_ENOT_CONVERGED: return "PCG not converged";
+    case IGA_ENUMERIC: return "numerical breakdown";
+    case IGA_EUNSTABLE: return "unstable time step";
+    case IGA_EGEOMETRY: return "invalid geometry (det DF <= 0)";
+    default: return "unknown status";
+  }
+}
+
+const char* iga_last_error(const iga_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+void iga_destroy(iga_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->opt.device);
+  for (int a = 0; a < 3; ++a) {
+    DirDev& d = h->dd[a];
+    dfree(d.val); dfree(d.der); dfree(d.sq); dfree(d.val32); dfree(d.der32);
+    dfree(d.qfirst); dfree(d.flo); dfree(d.fhi); dfree(d.qw);
+    dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32);
+  }
+  dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
+  dfree(h->Mband); dfree(h->Kband);
+  dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
+  dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
+  dfree(h->partial);
+  dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.alpha); dfree(h->cs.beta);
+  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
+  if (h->h_nactive) cudaFreeHost(h->h_nactive);
+  dfree(h->Yneg); dfree(h->rhs); dfree(h->Z); dfree(h->Z2); dfree(h->dstate);
+  delete h;
+}
+
+int iga_create(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
+               const iga_options* opt, iga_handle** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, IGA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(nullptr, IGA_EINVAL, "dim must be 2 or 3");
+  if (!degree || !nknots || !knots || !ctrl) return fail(nullptr, IGA_EINVAL, "NULL input array");
+  iga_handle* h = new (std::nothrow) iga_handle();
+  if (!h) return fail(nullptr, IGA_ENOMEM, "host allocation failed");
+  if (opt) h->opt = *opt;
+  else iga_options_default(&h->opt);
+  if (!(h->opt.tol >= 0.0) || h->opt.max_iter < 1 || h->opt.precond < 0 || h->opt.precond > 3 ||
+      h->opt.op_form < 0 || h->opt.op_form > 1 || h->opt.guess < 0 || h->opt.guess > 3) {
+    delete h;
+    return fail(nullptr, IGA_EINVAL, "invalid options");
+  }
+  h->dim = dim;
+  h->stream = (cudaStream_t)h->opt.stream;
+  int pmax = 0;
+  for (int a = 0; a < dim; ++a) pmax = std::max(pmax, degree[a]);
+  const int nq = h->opt.nquad > 0 ? h->opt.nquad : pmax + 1;
+  std::string err;
+  for (int a = 0; a < dim; ++a) {
+    if (!knots[a] || !build_tables(degree[a], nknots[a], knots[a], nq, h->tab[a], err)) {
+      delete h;
+      return fail(nullptr, IGA_EINVAL, "direction " + std::to_string(a) + ": " + (knots[a] ? err : "NULL knots"));
+    }
+    h->n[a] = h->tab[a].n;
+    h->Q[a] = h->tab[a].Q;
+    h->m[a] = h->tab[a].m;
+  }
+  h->N = (long long)h->n[0] * h->n[1] * h->n[2];
+  h->Qt = (long long)h->Q[0] * h->Q[1] * h->Q[2];
+  if (cudaSetDevice(h->opt.device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, IGA_ECUDA, "cudaSetDevice failed");
+  }
+  int rc = IGA_OK;
+  auto setup = [&]() -> int {
+    for (int a = 0; a < dim; ++a) {
+      const Tables1D& t = h->tab[a];
+      DirDev& d = h->dd[a];
+      d.p = t.p; d.P = t.p + 1; d.n = t.n; d.Q = t.Q;
+      std::vector<double> sq(t.val.size());
+      for (size_t i = 0; i < sq.size(); ++i) sq[i] = t.val[i] * t.val[i];
+      std::vector<float> v32(t.val.begin(), t.val.end()), d32(t.der.begin(), t.der.end());
+      std::vector<double> U((size_t)t.n * t.n);
+      for (int i = 0; i < t.n; ++i)
+        for (int c = 0; c < t.n; ++c) U[(size_t)c * t.n + i] = t.evec[(size_t)i * t.n + c];
+      std::vector<float> U32(U.begin(), U.end()), l32(t.eval.begin(), t.eval.end());
+      CKS(upload(h, &d.val, t.val)); CKS(upload(h, &d.der, t.der)); CKS(upload(h, &d.sq, sq));
+      CKS(upload(h, &d.val32, v32)); CKS(upload(h, &d.der32, d32));
+      CKS(upload(h, &d.qfirst, t.qfirst)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
+      CKS(upload(h, &d.qw, t.qw));
+      CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, t.eval));
+      CKS(upload(h, &d.U32, U32)); CKS(upload(h, &d.lam32, l32));
+    }
+    // control net, point-major -> SoA
+    const long long mt = (long long)h->m[0] * h->m[1] * (dim == 3 ? h->m[2] : 1);
+    std::vector<double> soa((size_t)(dim * mt));
+    for (long long i = 0; i < mt; ++i)
+      for (int c = 0; c < dim; ++c) soa[(size_t)(c * mt + i)] = ctrl[i * dim + c];
+    CKS(upload(h, &h->ctrl, soa));
+    const int ng = dim == 3 ? 6 : 3;
+    h->gstride = h->Qt;
+    CKS(dalloc(h, &h->W, (size_t)h->Qt));
+    CKS(dalloc(h, &h->G, (size_t)(ng * h->Qt)));
+    CKS(dalloc(h, &h->dflag, 4));
+    CK(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 4, h->stream));
+    int mm[3] = {h->m[0], h->m[1], h->m[2]};
+    CK(launch_geometry(h->stream, dim, h->dd, mm, h->ctrl, h->W, h->G, h->gstride, h->dflag));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, IGA_EGEOMETRY, "det DF <= 0 at a quadrature point");
+    // PCG scalars and reduction scratch
+    CKS(dalloc(h, &h->partial, (size_t)3 * kMaxVec * kRedBlocks));
+    CKS(dalloc(h, &h->cs.bb, kMaxVec)); CKS(dalloc(h, &h->cs.rz, kMaxVec)); CKS(dalloc(h, &h->cs.rr, kMaxVec));
+    CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
+    CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
+    CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
+    CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
+    // diag(M): D = (B_0^2)^T (B_1^2)^T (B_2^2)^T W (transposed passes with squared tables)
+    CKS(ensure_op_ws(h, 1));
+    CKS(dalloc(h, &h->Dm, (size_t)h->N));
+    const int *n = h->n, *Q = h->Q;
+    const DirDev* d = h->dd;
+    if (dim == 3) {
+      CK(launch_tr(h->stream, d[2], {(long long)Q[0] * Q[1], Q[2], n[2], 1}, 1, nullptr, h->W, d[2].sq, nullptr, nullptr, 0, h->ta, 0));
+      CK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], n[2]}, 1, nullptr, h->ta, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
+      CK(launch_tr(h->stream, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
+    } else {
+      CK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], 1}, 1, nullptr, h->W, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
+      CK(launch_tr(h->stream, d[0], {1, Q[0], n[0], n[1]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
+    }
+    std::vector<double> D((size_t)h->N), sc((size_t)h->N);
+    CK(cudaMemcpyAsync(D.data(), h->Dm, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < h->N; ++i) {
+      const int i0 = (int)(i % n[0]), i1 = (int)((i / n[0]) % n[1]), i2 = (int)(i / ((long long)n[0] * n[1]));
+      double dh = h->tab[0].mhat[(size_t)i0 * n[0] + i0] * h->tab[1].mhat[(size_t)i1 * n[1] + i1];
+      if (dim == 3) dh *= h->tab[2].mhat[(size_t)i2 * n[2] + i2];
+      if (!(D[i] > 0)) return fail(h, IGA_EGEOMETRY, "non-positive diagonal of M");
+      sc[i] = std::sqrt(dh / D[i]);
+    }
+    CKS(upload(h, &h->scale, sc));
+    return IGA_OK;
+  };
+  rc = setup();
+  if (rc != IGA_OK) {
+    g_create_err = h->err;
+    iga_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return IGA_OK;
+}
+
+int iga_ndof(const iga_handle* h, long long* ndof) {
+  if (!h || !ndof) return IGA_EINVAL;
+  *ndof = h->N;
+  return IGA_OK;
+}
+
+int iga_set_op_form(iga_handle* h, int op_form) {
+  if (!h || op_form < 0 || op_form > 1) return IGA_EINVAL;
+  h->opt.op_form = op_form;
+  return IGA_OK;
+}
+int iga_set_precond(iga_handle* h, int precond) {
+  if (!h || precond < 0 || precond > 3) return IGA_EINVAL;
+  h->opt.precond = precond;
+  return IGA_OK;
+}
+int iga_set_guess(iga_handle* h, int guess) {
+  if (!h || guess < 0 || guess > 3) return IGA_EINVAL;
+  h->opt.guess = guess;
+  return IGA_OK;
+}
+int iga_set_tol(iga_handle* h, double tol, int max_iter) {
+  if (!h || !(tol >= 0) || max_iter < 1) return IGA_EINVAL;
+  h->opt.tol = tol;
+  h->opt.max_iter = max_iter;
+  return IGA_OK;
+}
+
+int iga_assemble(iga_handle* h) {
+  CKS(check_handle(h));
+  return fail(h, IGA_EINVAL, "assembled operator form not available in this build");
+}
+
+int iga_apply_M(iga_handle* h, int nvec, const double* x, double* y) {
+  CKS(check_handle(h));
+  if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
+  return apply_M(h, nvec, nullptr, x, y);
+}
+
+int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y) {
+  CKS(check_handle(h));
+  if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
+  return apply_K(h, nvec, nullptr, x, y);
+}
+
+int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y) {
+  CKS(check_handle(h));
+  if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
+  return apply_Pinv(h, nvec, nullptr, x, y);
+}
+
+int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0, int* iters, double* relres) {
+  CKS(check_handle(h));
+  if (nvec < 1 || nvec > kMaxVec || !b || !x) return fail(h, IGA_EINVAL, "bad arguments");
+  return solve(h, nvec, b, x, use_x0 != 0, iters, relres);
+}
+
+int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double* gamma) {
+  if (k < 1 || k > kMaxK || !(rho_inf >= 0.0 && rho_inf <= 1.0) || !alpha || !beta || !gamma) return IGA_EINVAL;
+  galpha_params(k, rho_inf, alpha, beta, gamma);
+  return IGA_OK;
+}
+
+int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, double* state) {
+  CKS(check_handle(h));
+  if (k < 1 || k > kMaxK || !U0 || !V0 || !state) return fail(h, IGA_EINVAL, "bad arguments");
+  const long long N = h->N;
+  cudaStream_t s = h->stream;
+  CKS(ensure_step_ws(h, 2));
+  CK(cudaMemcpyAsync(state, U0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(state + N, V0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  // X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3: the chains of even and odd a are
+  // independent, so consecutive pairs are solved together.
+  const int last = 3 * k - 3;
+  for (int a = 0; a <= last; a += 2) {
+    const int nv = (a + 1 <= last) ? 2 : 1;
+    CKS(apply_K(h, nv, nullptr, state + (long long)a * N, h->rhs));
+    CK(launch_scale_neg(s, nv * N, h->rhs));
+    CKS(solve(h, nv, h->rhs, state + (long long)(a + 2) * N, false, nullptr, nullptr));
+  }
+  h->hist = 0;
+  return IGA_OK;
+}
+
+int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int nsteps, iga_stats* stats) {
+  CKS(check_handle(h));
+  if (k < 1 || k > kMaxK || !state || nsteps < 0 || !(dt > 0.0) || !(rho_inf >= 0.0 && rho_inf <= 1.0))
+    return fail(h, IGA_EINVAL, "bad arguments");
+  const long long N = h->N;
+  cudaStream_t s = h->stream;
+  CKS(ensure_step_ws(h, k));
+  StepCoefs sc{};
+  sc.k = k;
+  sc.tau = dt;
+  double fact = 1.0;
+  for (int m = 0; m < 3 * k; ++m) {
+    if (m > 0) fact *= m;
+    sc.c[m] = std::pow(dt, m) / fact;
+  }
+  galpha_params(k, rho_inf, sc.alpha, sc.beta, sc.gamma);
+  for (int step = 0; step < nsteps; ++step) {
+    const int guess = h->opt.guess;
+    const bool taylor = guess == IGA_GUESS_TAYLOR;
+    CK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr));
+    CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+    bool use_x0 = false;
+    if (taylor) {
+      use_x0 = true;
+    } else if (guess == IGA_GUESS_PREV && h->hist >= 1) {
+      use_x0 = true;  // Z still holds the previous step's solutions
+    } else if (guess == IGA_GUESS_EXTRAP && h->hist >= 1) {
+      if (h->hist >= 2) CK(launch_extrap(s, (long long)k * N, h->Z, h->Z2));
+      else CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
+      use_x0 = true;
+    }
+    int its[kMaxVec];
+    double rel[kMaxVec];
+    CKS(solve(h, k, h->rhs, h->Z, use_x0, its, rel));
+    if (guess == IGA_GUESS_EXTRAP && h->hist == 0)
+      CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
+    CK(launch_update(s, N, sc, state, h->Z));
+    h->hist = std::min(h->hist + 1, 2);
+    if (stats) {
+      stats->steps += 1;
+      stats->solves += k;
+      for (int j = 0; j < k; ++j) {
+        stats->iters += its[j];
+        stats->max_iters = std::max(stats->max_iters, its[j]);
+        stats->max_relres = std::max(stats->max_relres, rel[j]);
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  return IGA_OK;
+}
+
+int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, double dt, int nsteps,
+                  iga_stats* stats) {
+  CKS(check_handle(h));
+  if (k < 1 || k > kMaxK || !state_host) return fail(h, IGA_EINVAL, "bad arguments");
+  const long long len = 3LL * k * h->N;
+  if (h->dstate_cap < len) {
+    CKS(dalloc(h, &h->dstate, (size_t)len));
+    h->dstate_cap = len;
+  }
+  CK(cudaMemcpyAsync(h->dstate, state_host, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
+  CKS(iga_step(h, h->dstate, k, rho_inf, dt, nsteps, stats));
+  CK(cudaMemcpyAsync(state_host, h->dstate, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IGA_OK;
+}
+
+int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double* tau_crit) {
+  CKS(check_handle(h));
+  if (iters < 1 || !lambda_max || !tau_crit || !(rho_inf >= 0.0 && rho_inf <= 1.0))
+    return fail(h, IGA_EINVAL, "bad arguments");
+  const long long N = h->N;
+  cudaStream_t s = h->stream;
+  CKS(ensure_step_ws(h, 2));
+  CKS(ensure_cg_ws(h, 2));
+  // start from a checkerboard (close to the highest mode) times a smooth bump
+  std::vector<double> x0((size_t)N);
+  for (long long i = 0; i < N; ++i) {
+    const int i0 = (int)(i % h->n[0]), i1 = (int)((i / h->n[0]) % h->n[1]), i2 = (int)(i / ((long long)h->n[0] * h->n[1]));
+    const double sgn = ((i0 + i1 + i2) & 1) ? -1.0 : 1.0;
+    const double bump = std::sin(3.14159265358979 * (i0 + 1) / (h->n[0] + 1)) *
+                        std::sin(3.14159265358979 * (i1 + 1) / (h->n[1] + 1)) *
+                        (h->dim == 3 ? std::sin(3.14159265358979 * (i2 + 1) / (h->n[2] + 1)) : 1.0);
+    x0[i] = sgn * (0.5 + bump);
+  }
+  double* x = h->Z2;
+  double* y = h->rhs;
+  double* zz = h->Z;
+  CK(cudaMemcpyAsync(x, x0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  const double tol_save = h->opt.tol;
+  h->opt.tol = 1e-10;
+  double* pA = h->partial;
+  double* res = h->f1;  // scratch for reduced scalars
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    CKS(apply_K(h, 1, nullptr, x, y));
+    int st = solve(h, 1, y, zz, false, nullptr, nullptr);
+    if (st != IGA_OK) { h->opt.tol = tol_save; return st; }
+    CK(launch_dot(s, N, 1, zz, zz, N, pA));
+    CK(launch_reduce(s, 1, pA, res));
+    double nz = 0.0;
+    CK(cudaMemcpyAsync(&nz, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> tmp((size_t)N);
+    CK(cudaMemcpy(tmp.data(), zz, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    const double inv = 1.0 / std::sqrt(nz);
+    for (auto& v : tmp) v *= inv;
+    CK(cudaMemcpy(x, tmp.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  }
+  h->opt.tol = tol_save;
+  // Rayleigh quotient x^T K x / x^T M x
+  CKS(apply_K(h, 1, nullptr, x, y));
+  CKS(apply_M(h, 1, nullptr, x, zz));
+  CK(launch_dot(s, N, 1, x, y, N, pA));
+  CK(launch_reduce(s, 1, pA, res));
+  CK(launch_dot(s, N, 1, x, zz, N, pA));
+  CK(launch_reduce(s, 1, pA, res + 1));
+  double kx[2];
+  CK(cudaMemcpyAsync(kx, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  lam = kx[0] / kx[1];
+  *lambda_max = lam;
+  *tau_crit = std::sqrt(theta_crit(rho_inf) / lam);
+  return IGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// Host-side univariate setup: Gauss rule, B-spline tables, parametric mass
+// matrix and its eigen-decomposition for the fast-diagonalisation preconditioner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "iga_internal.h"
+
+namespace iga {
+
+// Cyclic Jacobi rotations on a symmetric matrix. A = V diag(eval) V^T on exit,
+// V stored row-major with eigenvector c in column c. Sweeps until every
+// off-diagonal entry is below 1e-300 relative to the Frobenius norm or no
+// rotation changes anything.
+void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evec, std::vector<double>& eval) {
+  evec.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) evec[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    int rotations = 0;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[(size_t)p * n + q];
+        double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        // an entry negligible against the geometric mean of its diagonal is dropped
+        if (std::fabs(apq) <= 1e-18 * std::sqrt(std::fabs(app * aqq))) {
+          A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+          continue;
+        }
+        ++rotations;
+        // rotation angle that annihilates a_pq: cot(2 phi) = (a_qq - a_pp) / (2 a_pq)
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < n; ++r) {  // columns p, q of A
+          double arp = A[(size_t)r * n + p], arq = A[(size_t)r * n + q];
+          A[(size_t)r * n + p] = c * arp - s * arq;
+          A[(size_t)r * n + q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < n; ++r) {  // rows p, q of A
+          double apr = A[(size_t)p * n + r], aqr = A[(size_t)q * n + r];
+          A[(size_t)p * n + r] = c * apr - s * aqr;
+          A[(size_t)q * n + r] = s * apr + c * aqr;
+        }
+        A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+        for (int r = 0; r < n; ++r) {  // accumulate V <- V J
+          double vrp = evec[(size_t)r * n + p], vrq = evec[(size_t)r * n + q];
+          evec[(size_t)r * n + p] = c * vrp - s * vrq;
+          evec[(size_t)r * n + q] = s * vrp + c * vrq;
+        }
+      }
+    }
+    if (rotations == 0) break;
+  }
+  eval.resize(n);
+  for (int i = 0; i < n; ++i) eval[i] = A[(size_t)i * n + i];
+}
+
+// Gauss-Legendre nodes and weights by the Golub-Welsch construction: the nodes
+// are the eigenvalues of the symmetric tridiagonal Jacobi matrix of the
+// Legendre recurrence (off-diagonal j / sqrt(4 j^2 - 1)), the weights twice the
+// squared first components of the normalised eigenvectors.
+void gauss_legendre(int n, double* x, double* w) {
+  std::vector<double> J((size_t)n * n, 0.0);
+  for (int j = 1; j < n; ++j) {
+    double b = j / std::sqrt(4.0 * j * j - 1.0);
+    J[(size_t)(j - 1) * n + j] = J[(size_t)j * n + (j - 1)] = b;
+  }
+  std::vector<double> V, lam;
+  jacobi_eigen(n, J, V, lam);
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+  for (int i = 0; i < n; ++i) {
+    int c = order[i];
+    x[i] = lam[c];
+    w[i] = 2.0 * V[c] * V[c];  // row 0, column c
+  }
+  // one Newton polish of every node on P_n for full double accuracy
+  for (int i = 0; i < n; ++i) {
+    double z = x[i];
+    for (int it = 0; it < 2; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 1; j < n; ++j) {
+        double p2 = ((2 * j + 1) * z * p1 - j * p0) / (j + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      if (n == 1) { p1 = z; dp = 1.0; }
+      z -= p1 / dp;
+      if (it == 1) w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    x[i] = z;
+  }
+}
+
+// The p+1 B-splines nonzero on span s (functions s-p..s) and their derivatives at
+// x, from the Cox-de Boor recursion written on local indices: at degree r the
+// live functions are s-r..s; N_r[t] (function i = s-r+t) gathers
+//   (x-U_i)/(U_{i+r}-U_i) N_{r-1}[t-1] + (U_{i+r+1}-x)/(U_{i+r+1}-U_{i+1}) N_{r-1}[t],
+// with terms of zero denominators dropped (0/0 = 0).
+void bspline_span(int p, const double* U, int s, double x, double* val, double* der) {
+  double N[kMaxP + 1] = {1.0}, Nm[kMaxP + 1] = {1.0};
+  for (int r = 1; r <= p; ++r) {
+    for (int t = 0; t < r; ++t) Nm[t] = N[t];
+    for (int t = 0; t <= r; ++t) {
+      int i = s - r + t;
+      double acc = 0.0;
+      if (t >= 1) {
+        double den = U[i + r] - U[i];
+        if (den > 0) acc += (x - U[i]) / den * Nm[t - 1];
+      }
+      if (t <= r - 1) {
+        double den = U[i + r + 1] - U[i + 1];
+        if (den > 0) acc += (U[i + r + 1] - x) / den * Nm[t];
+      }
+      N[t] = acc;
+    }
+  }
+  for (int t = 0; t <= p; ++t) val[t] = N[t];
+  if (der) {
+    // Nm holds degree p-1 (live functions s-p+1..s)
+    for (int t = 0; t <= p; ++t) {
+      if (p == 0) { der[t] = 0.0; continue; }
+      int i = s - p + t;
+      double acc = 0.0;
+      if (t >= 1) {
+        double den = U[i + p] - U[i];
+        if (den > 0) acc += p * Nm[t - 1] / den;
+      }
+      if (t <= p - 1) {
+        double den = U[i + p + 1] - U[i + 1];
+        if (den > 0) acc -= p * Nm[t] / den;
+      }
+      der[t] = acc;
+    }
+  }
+}
+
+bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err) {
+  char buf[256];
+  int m = nknots - p - 1;
+  if (p < 1 || p > kMaxDeg) { snprintf(buf, sizeof buf, "degree %d outside [1, %d]", p, kMaxDeg); err = buf; return false; }
+  if (m < 3) { err = "fewer than 3 basis functions in a direction"; return false; }
+  if (nq < 1 || nq > 16) { err = "nquad outside [1, 16]"; return false; }
+  for (int i = 0; i + 1 < nknots; ++i)
+    if (!(U[i + 1] >= U[i])) { err = "knot vector not non-decreasing"; return false; }
+  for (int i = 1; i <= p; ++i)
+    if (U[i] != U[0] || U[nknots - 1 - i] != U[nknots - 1]) { err = "knot vector not open (ends need multiplicity p+1)"; return false; }
+  if (U[0] != 0.0 || U[nknots - 1] != 1.0) { err = "knot vector must span [0, 1]"; return false; }
+  for (int i = p + 1; i < m; ++i) {
+    int mult = 1;
+    while (i + mult < m && U[i + mult] == U[i]) ++mult;
+    if (mult > p) { err = "interior knot multiplicity above p"; return false; }
+  }
+  t.p = p; t.m = m; t.n = m - 2; t.nq = nq;
+  std::vector<double> gx(nq), gw(nq);
+  gauss_legendre(nq, gx.data(), gw.data());
+  std::vector<int> spans;
+  for (int s = p; s < m; ++s)
+    if (U[s + 1] > U[s]) spans.push_back(s);
+  t.nel = (int)spans.size();
+  t.Q = t.nel * nq;
+  const int P = p + 1;
+  t.qx.resize(t.Q); t.qw.resize(t.Q); t.qfirst.resize(t.Q);
+  t.val.resize((size_t)t.Q * P); t.der.resize((size_t)t.Q * P);
+  for (int e = 0; e < t.nel; ++e) {
+    int s = spans[e];
+    double a = U[s], h = U[s + 1] - U[s];
+    for (int g = 0; g < nq; ++g) {
+      int q = e * nq + g;
+      double x = a + 0.5 * h * (gx[g] + 1.0);
+      t.qx[q] = x;
+      t.qw[q] = 0.5 * h * gw[g];
+      t.qfirst[q] = s - p;
+      bspline_span(p, U, s, x, &t.val[(size_t)q * P], &t.der[(size_t)q * P]);
+    }
+  }
+  // quadrature ranges of the interior functions (qfirst is non-decreasing in q)
+  t.flo.assign(t.n, 0); t.fhi.assign(t.n, 0);
+  for (int i = 0; i < t.n; ++i) {
+    int f = i + 1, lo = -1, hi = -1;
+    for (int q = 0; q < t.Q; ++q)
+      if (t.qfirst[q] <= f && f <= t.qfirst[q] + p) {
+        if (lo < 0) lo = q;
+        hi = q + 1;
+      }
+    if (lo < 0) { err = "interior function without quadrature support"; return false; }
+    t.flo[i] = lo; t.fhi[i] = hi;
+  }
+  // interior parametric mass matrix (one direction of def:matrices_1)
+  t.mhat.assign((size_t)t.n * t.n, 0.0);
+  for (int q = 0; q < t.Q; ++q)
+    for (int a = 0; a < P; ++a) {
+      int i = t.qfirst[q] + a - 1;
+      if (i < 0 || i >= t.n) continue;
+      for (int b = 0; b < P; ++b) {
+        int j = t.qfirst[q] + b - 1;
+        if (j < 0 || j >= t.n) continue;
+        t.mhat[(size_t)i * t.n + j] += t.qw[q] * t.val[(size_t)q * P + a] * t.val[(size_t)q * P + b];
+      }
+    }
+  jacobi_eigen(t.n, t.mhat, t.evec, t.eval);
+  for (double l : t.eval)
+    if (!(l > 0)) { err = "parametric mass matrix not positive definite"; return false; }
+  return true;
+}
+
+}  // namespace iga

@@ -1,0 +1,168 @@
+// Internal declarations of the GB300 generalized-alpha IGA library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/iga_galpha.h"
+
+namespace iga {
+
+constexpr int kMaxDeg = 6;       // largest supported spline degree
+constexpr int kMaxP = kMaxDeg + 1;
+constexpr int kMaxVec = 8;       // largest batch of vectors per operator call
+constexpr int kMaxK = 4;         // largest order parameter (order 2k)
+constexpr int kMaxRows = 3 * kMaxK;
+
+// ---------------------------------------------------------------------------
+// Host-side univariate setup (host_setup.cpp)
+// ---------------------------------------------------------------------------
+struct Tables1D {
+  int p = 0, m = 0, n = 0, nel = 0, nq = 0, Q = 0;
+  std::vector<double> qx, qw;       // [Q] point, weight (Gauss weight * span/2)
+  std::vector<int> qfirst;          // [Q] first full function index nonzero on the span
+  std::vector<double> val, der;     // [Q][p+1]
+  std::vector<int> flo, fhi;        // [n] quadrature range [lo, hi) of interior function i (full i+1)
+  std::vector<double> mhat;         // [n][n] interior parametric mass matrix
+  std::vector<double> evec;         // [n][n] row-major, column c = eigenvector c
+  std::vector<double> eval;         // [n]
+};
+
+// Gauss-Legendre rule on [-1, 1].
+void gauss_legendre(int n, double* x, double* w);
+// Values and derivatives of the degree-p B-splines nonzero at x in span s (s-p..s).
+void bspline_span(int p, const double* U, int s, double x, double* val, double* der);
+// Build all tables of one direction; returns false on invalid knots.
+bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err);
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).
+void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evec, std::vector<double>& eval);
+
+// ---------------------------------------------------------------------------
+// Device-side per-direction tables
+// ---------------------------------------------------------------------------
+struct DirDev {
+  int p, P, n, Q;
+  double* val;    // [Q][P]
+  double* der;    // [Q][P]
+  double* sq;     // [Q][P] squared values (for diag(M))
+  float* val32;
+  float* der32;
+  int* qfirst;    // [Q]
+  int* flo;       // [n]
+  int* fhi;       // [n]
+  double* qw;     // [Q]
+  double* U64;    // [n][n] column-major copy of the eigenvectors: element (i, c) at c*n + i
+  double* lam64;  // [n]
+  float* U32;
+  float* lam32;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels_*.cu)
+// ---------------------------------------------------------------------------
+struct AxisShape {
+  long long A;   // product of the sizes of the faster axes
+  int Lin;       // length along the axis on input
+  int Lout;      // length along the axis on output
+  long long B;   // product of the sizes of the slower axes
+};
+
+// Interpolation pass along one axis (coefficients -> quadrature points):
+// out[x,o,y] = sum_l T[o][l] in[x, qfirst[o]-1+l, y]; up to 2 tables on one input.
+cudaError_t launch_fwd(cudaStream_t s, const DirDev& d, AxisShape sh, int nvec, const int* active,
+                       const double* in, long long in_vs, const double* T0, double* out0, const double* T1,
+                       double* out1, long long out_vs);
+// Transposed pass (quadrature points -> coefficients):
+// out[x,i,y] = sum_{q in supp i} T0[q][i+1-qfirst[q]] in0[x,q,y] (+ same with T1, in1).
+cudaError_t launch_tr(cudaStream_t s, const DirDev& d, AxisShape sh, int nvec, const int* active,
+                      const double* in0, const double* T0, const double* in1, const double* T1, long long in_vs,
+                      double* out, long long out_vs);
+// Fused last-axis kernel of the mass operator: out = B^T (W .* (B in)) along the last axis.
+cudaError_t launch_mid_mass(cudaStream_t s, const DirDev& d, long long A, int nvec, const int* active,
+                            const double* W, const double* in, double* out, long long vs);
+// Fused last-axis kernel of the stiffness operator (3-D): inputs a (-> B' a), b (-> B b),
+// c (-> B c) are the partial interpolants of the derivative in directions 2, 1, 0; h = G g;
+// outputs (in place) a <- B'^T h2, b <- B^T h1, c <- B^T h0.
+cudaError_t launch_mid_stiff3(cudaStream_t s, const DirDev& d, long long A, int nvec, const int* active,
+                              const double* G, long long gstride, double* a, double* b, double* c, long long vs);
+// 2-D: inputs a (-> B' a, direction 1), c (-> B c, direction 0); outputs a <- B'^T h1, c <- B^T h0.
+cudaError_t launch_mid_stiff2(cudaStream_t s, const DirDev& d, long long A, int nvec, const int* active,
+                              const double* G, long long gstride, double* a, double* c, long long vs);
+// Geometric factors at the quadrature points; sets *bad = 1 if det DF <= 0 somewhere.
+cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const int* m, const double* ctrl_soa,
+                            double* W, double* G, long long gstride, int* bad);
+
+// Fast-diagonalisation mode product along one axis: out[x,i,y] = sum_j Mat(i,j) in[x,j,y]
+// with Mat(i,j) = U[j*n+i] (transpose=0: U) or U[i*n+j] (transpose=1: U^T),
+// optional prologue scale (in * pre[idx]) and epilogue (Lambda^{-1} or post scale).
+struct FdEpilogue {
+  const double* post;            // multiply output by post[idx] (nullable)
+  const double* lam[3];          // divide by lam0[i0] lam1[i1] lam2[i2] (nullable)
+  int n[3];
+};
+cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const double* U,
+                             int transpose, const double* in, double* out, long long vs, const double* pre,
+                             FdEpilogue ep);
+cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
+                             int transpose, const void* in, int in_is_double, void* out, int out_is_double,
+                             long long vs, const double* pre, const double* post, const float* const* lam,
+                             const int* nn);
+
+// Vector kernels (kernels_vec.cu)
+constexpr int kRedBlocks = 296;  // fixed reduction grid (2 x 148 .. deterministic order)
+// partial[v*kRedBlocks + b] = sum over the block's fixed index set of a_v . b_v
+cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, const double* b, long long vs,
+                       double* partial);
+// One block per vector: result[v] = sum_b partial[v*kRedBlocks + b] in fixed order.
+cudaError_t launch_reduce(cudaStream_t s, int nvec, const double* partial, double* result);
+
+struct CgScalars {  // device arrays, one entry per system
+  double* bb;      // ||b||^2
+  double* rz;      // r.z (current)
+  double* rr;      // ||r||^2
+  double* alpha;
+  double* beta;
+  int* active;     // 1 while iterating
+  int* iters;
+  int* status;     // 0 ok, IGA_ENUMERIC on breakdown
+  int* nactive;    // single counter
+};
+// Reduction epilogues of PCG (one thread per system, tiny kernels).
+cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, CgScalars c);
+cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgScalars c, double tol2);
+cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, CgScalars c,
+                           int flexible);
+cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, const double* partial_rr,
+                           CgScalars c, double tol2);
+cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, CgScalars c);
+// x += alpha p; r -= alpha q; partial ||r||^2
+cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
+                                const double* p, const double* q, long long vs, double* partial);
+// p = z + beta p
+cudaError_t launch_cg_update_p(cudaStream_t s, long long N, int nvec, CgScalars c, double* p, const double* z,
+                               long long vs);
+// r = b - q (q = M x0)
+cudaError_t launch_sub(cudaStream_t s, long long N, int nvec, const double* b, const double* q, double* r,
+                       long long vs);
+cudaError_t launch_copy_active(cudaStream_t s, long long N, int nvec, const int* active, const double* src,
+                               double* dst, long long vs);
+
+struct StepCoefs {
+  int k;
+  double c[kMaxRows];          // tau^m / m!
+  double alpha[kMaxK], beta[kMaxK], gamma[kMaxK];
+  double tau;
+};
+// Writes -Y_j (k vectors) and, if T != nullptr, the Taylor predictor T_{s_j} of each solved row.
+cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T);
+// Fused stage update in place.
+cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, const double* Z);
+// Z <- 2 Z - Z2, Z2 <- old Z
+cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
+cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
+
+}  // namespace iga

@@ -1,0 +1,354 @@
+// PCG vector kernels (Sec. 5.5) and the fused generalized-alpha predictor and
+// stage update (Sec. 4, eq. ho1-ho3). Reductions use a fixed grid and a fixed
+// tree, so every result is bitwise reproducible run to run.
+#include "iga_internal.h"
+
+namespace iga {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block of 256 threads -> one value (valid in thread 0)
+__device__ __forceinline__ double block_sum256(double v) {
+  __shared__ double sh[8];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < 8 ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_dot(long long N, const double* __restrict__ a, const double* __restrict__ b,
+                                             long long vs, double* __restrict__ partial) {
+  const int v = blockIdx.y;
+  const double* pa = a + v * vs;
+  const double* pb = b + v * vs;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    s = fma(pa[i], pb[i], s);
+  s = block_sum256(s);
+  if (threadIdx.x == 0) partial[v * kRedBlocks + blockIdx.x] = s;
+}
+
+cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, const double* b, long long vs,
+                       double* partial) {
+  k_dot<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, a, b, vs, partial);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ double sum_partials(const double* p) {
+  double s = 0.0;
+  for (int b = 0; b < kRedBlocks; ++b) s += p[b];
+  return s;
+}
+
+__global__ void k_reduce(int nvec, const double* partial, double* result) {
+  const int v = threadIdx.x;
+  if (v < nvec) result[v] = sum_partials(partial + v * kRedBlocks);
+}
+
+cudaError_t launch_reduce(cudaStream_t s, int nvec, const double* partial, double* result) {
+  k_reduce<<<1, 32, 0, s>>>(nvec, partial, result);
+  return cudaGetLastError();
+}
+
+// b.b and r.r at the start; a system is active while ||r|| > tol ||b|| and b != 0.
+__global__ void k_cg_init(int nvec, const double* pbb, const double* prr, CgScalars c, double tol2) {
+  const int v = threadIdx.x;
+  if (v < nvec) {
+    const double bb = sum_partials(pbb + v * kRedBlocks);
+    const double rr = sum_partials(prr + v * kRedBlocks);
+    c.bb[v] = bb;
+    c.rr[v] = rr;
+    c.iters[v] = 0;
+    c.status[v] = 0;
+    int act = (bb > 0.0) && (rr > tol2 * bb);
+    if (!isfinite(bb) || !isfinite(rr)) {
+      c.status[v] = IGA_ENUMERIC;
+      act = 0;
+    }
+    c.active[v] = act;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int i = 0; i < nvec; ++i) na += c.active[i];
+    *c.nactive = na;
+  }
+}
+
+cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, const double* partial_rr,
+                           CgScalars c, double tol2) {
+  k_cg_init<<<1, 32, 0, s>>>(nvec, partial_bb, partial_rr, c, tol2);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_start(int nvec, const double* prz, CgScalars c) {
+  const int v = threadIdx.x;
+  if (v < nvec) c.rz[v] = sum_partials(prz + v * kRedBlocks);
+}
+
+cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, CgScalars c) {
+  k_cg_start<<<1, 32, 0, s>>>(nvec, partial_rz, c);
+  return cudaGetLastError();
+}
+
+// alpha = r.z / p.q; breakdown (p.q <= 0 or not finite) stops the system with IGA_ENUMERIC.
+__global__ void k_cg_alpha(int nvec, const double* ppq, CgScalars c) {
+  const int v = threadIdx.x;
+  if (v >= nvec) return;
+  if (!c.active[v]) {
+    c.alpha[v] = 0.0;
+    return;
+  }
+  const double pq = sum_partials(ppq + v * kRedBlocks);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    c.status[v] = IGA_ENUMERIC;
+    c.active[v] = 0;
+    c.alpha[v] = 0.0;
+    return;
+  }
+  c.alpha[v] = c.rz[v] / pq;
+}
+
+cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, CgScalars c) {
+  k_cg_alpha<<<1, 32, 0, s>>>(nvec, partial, c);
+  return cudaGetLastError();
+}
+
+// After x/r update: count the iteration, test ||r||^2 <= tol^2 ||b||^2.
+__global__ void k_cg_check(int nvec, const double* prr, CgScalars c, double tol2) {
+  const int v = threadIdx.x;
+  if (v < nvec && c.active[v]) {
+    const double rr = sum_partials(prr + v * kRedBlocks);
+    c.rr[v] = rr;
+    c.iters[v] += 1;
+    if (!isfinite(rr)) {
+      c.status[v] = IGA_ENUMERIC;
+      c.active[v] = 0;
+    } else if (rr <= tol2 * c.bb[v]) {
+      c.active[v] = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int i = 0; i < nvec; ++i) na += c.active[i];
+    *c.nactive = na;
+  }
+}
+
+cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgScalars c, double tol2) {
+  k_cg_check<<<1, 32, 0, s>>>(nvec, partial, c, tol2);
+  return cudaGetLastError();
+}
+
+// beta = r.z_new / r.z_old (plain CG) or (r.z_new - r.z_prev) / r.z_old (flexible,
+// Polak-Ribiere form for a preconditioner that is not exactly linear).
+__global__ void k_cg_beta(int nvec, const double* prz, const double* prz2, CgScalars c, int flexible) {
+  const int v = threadIdx.x;
+  if (v >= nvec || !c.active[v]) return;
+  const double rz_new = sum_partials(prz + v * kRedBlocks);
+  double num = rz_new;
+  if (flexible) num -= sum_partials(prz2 + v * kRedBlocks);
+  c.beta[v] = num / c.rz[v];
+  c.rz[v] = rz_new;
+}
+
+cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, CgScalars c,
+                           int flexible) {
+  k_cg_beta<<<1, 32, 0, s>>>(nvec, partial, partial2, c, flexible);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_cg_update_xr(long long N, CgScalars c, double* __restrict__ x,
+                                                      double* __restrict__ r, const double* __restrict__ p,
+                                                      const double* __restrict__ q, long long vs,
+                                                      double* __restrict__ partial) {
+  const int v = blockIdx.y;
+  const double a = c.alpha[v];
+  const bool act = c.active[v] != 0;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const long long k = v * vs + i;
+    double ri = r[k];
+    if (act) {
+      x[k] = fma(a, p[k], x[k]);
+      ri = fma(-a, q[k], ri);
+      r[k] = ri;
+    }
+    s = fma(ri, ri, s);
+  }
+  s = block_sum256(s);
+  if (threadIdx.x == 0) partial[v * kRedBlocks + blockIdx.x] = s;
+}
+
+cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
+                                const double* p, const double* q, long long vs, double* partial) {
+  k_cg_update_xr<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, c, x, r, p, q, vs, partial);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_cg_update_p(long long N, CgScalars c, double* __restrict__ p,
+                                                     const double* __restrict__ z, long long vs) {
+  const int v = blockIdx.y;
+  if (!c.active[v]) return;
+  const double b = c.beta[v];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const long long k = v * vs + i;
+    p[k] = fma(b, p[k], z[k]);
+  }
+}
+
+cudaError_t launch_cg_update_p(cudaStream_t s, long long N, int nvec, CgScalars c, double* p, const double* z,
+                               long long vs) {
+  k_cg_update_p<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, c, p, z, vs);
+  return cudaGetLastError();
+}
+
+__global__ void k_sub(long long N, const double* b, const double* q, double* r, long long vs) {
+  const int v = blockIdx.y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    r[v * vs + i] = b[v * vs + i] - q[v * vs + i];
+}
+
+cudaError_t launch_sub(cudaStream_t s, long long N, int nvec, const double* b, const double* q, double* r,
+                       long long vs) {
+  k_sub<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, b, q, r, vs);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_active(long long N, const int* active, const double* src, double* dst, long long vs) {
+  const int v = blockIdx.y;
+  if (active && !active[v]) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    dst[v * vs + i] = src[v * vs + i];
+}
+
+cudaError_t launch_copy_active(cudaStream_t s, long long N, int nvec, const int* active, const double* src,
+                               double* dst, long long vs) {
+  k_copy_active<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, active, src, dst, vs);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// generalized-alpha predictor and stage update. Rows of X: q + 2 for
+// q = -2..3k-3 (U, V, A, L^1, ...). c[m] = tau^m / m!.
+// T_q = sum_{r >= q} c[r-q] X_r (Taylor predictor, eq. ho2-ho3).
+// Block j solves for row s_j + 2 = 3j - 1 (0-based j-1: row 3(j-1) + 2).
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(256) k_predict(long long N, StepCoefs sc, const double* __restrict__ X,
+                                                 double* __restrict__ Yneg, double* __restrict__ T) {
+  constexpr int R = 3 * K;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = X[r * N + i];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int row = 3 * j + 2;   // solved variable of block j+1
+    const int ry = row - 2;      // its "displacement" row
+    double y;
+    if (j < K - 1) {             // alpha_f = 1: full Taylor predictor T_{s_j - 2}
+      y = 0.0;
+#pragma unroll
+      for (int r = R - 1; r >= ry; --r) y = fma(sc.c[r - ry], x[r], y);
+    } else {                     // alpha_f = 0: the current value
+      y = x[ry];
+    }
+    Yneg[j * N + i] = -y;
+    if (T) {
+      double t = 0.0;
+#pragma unroll
+      for (int r = R - 1; r >= row; --r) t = fma(sc.c[r - row], x[r], t);
+      T[j * N + i] = t;
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_update(long long N, StepCoefs sc, double* __restrict__ X,
+                                                const double* __restrict__ Z) {
+  constexpr int R = 3 * K;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x[R], t[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = X[r * N + i];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    double s = 0.0;
+#pragma unroll
+    for (int r = R - 1; r >= q; --r) s = fma(sc.c[r - q], x[r], s);
+    t[q] = s;
+  }
+  const double tau = sc.tau;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int row = 3 * j + 2;
+    const double P = (Z[j * N + i] - t[row]) / sc.alpha[j];
+    X[row * N + i] = t[row] + P;
+    X[(row - 1) * N + i] = fma(sc.gamma[j] * tau, P, t[row - 1]);
+    X[(row - 2) * N + i] = fma(sc.beta[j] * tau * tau, P, t[row - 2]);
+  }
+}
+
+cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T) {
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  switch (sc.k) {
+    case 1: k_predict<1><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
+    case 2: k_predict<2><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
+    case 3: k_predict<3><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
+    case 4: k_predict<4><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, const double* Z) {
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  switch (sc.k) {
+    case 1: k_update<1><<<blocks, 256, 0, s>>>(N, sc, X, Z); break;
+    case 2: k_update<2><<<blocks, 256, 0, s>>>(N, sc, X, Z); break;
+    case 3: k_update<3><<<blocks, 256, 0, s>>>(N, sc, X, Z); break;
+    case 4: k_update<4><<<blocks, 256, 0, s>>>(N, sc, X, Z); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_extrap(long long n, double* Z, double* Z2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double z = Z[i];
+    Z[i] = 2.0 * z - Z2[i];
+    Z2[i] = z;
+  }
+}
+
+cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2) {
+  k_extrap<<<kRedBlocks, 256, 0, s>>>(n, Z, Z2);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_neg(long long n, double* x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = -x[i];
+}
+
+cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x) {
+  k_scale_neg<<<kRedBlocks, 256, 0, s>>>(n, x);
+  return cudaGetLastError();
+}
+
+}  // namespace iga

@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: the library loads, exports every entry point that
+include/*.h declares, and its host-only logic (parameters, status strings, argument
+validation that fails before any device call) agrees with the oracle."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2102_11536_gb300 as iga
+from paper_2102_11536_gb300 import build as gb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(iga_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gb.build()
+    return iga.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 18
+    raw = ctypes.CDLL(iga.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(raw, name), name
+    assert set(iga.exported_symbols()) <= declared
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("rho", [0.0, 0.25, 0.5, 0.9, 1.0])
+def test_params_match_oracle(lib, k, rho):
+    a, b, g = iga.galpha_params(k, rho)
+    ref = oracle.galpha_params(k, rho)
+    for j in range(k):
+        assert abs(a[j] - ref[j][0]) < 1e-15
+        assert abs(b[j] - ref[j][1]) < 1e-14
+        assert abs(g[j] - ref[j][2]) < 1e-15
+
+
+def test_params_reject_bad_arguments(lib):
+    with pytest.raises(iga.IgaError):
+        iga.galpha_params(5, 0.5)
+    with pytest.raises(iga.IgaError):
+        iga.galpha_params(2, 1.5)
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.iga_status_string(code)
+
+
+def test_create_rejects_bad_knots_before_device_use(lib):
+    # open knot vectors are required; the check happens on the host
+    bad = [np.array([0, 0.1, 0.5, 1, 1, 1.0]), np.array([0, 0, 0, 1, 1, 1.0])]
+    with pytest.raises(iga.IgaError) as e:
+        iga.Patch([2, 2], bad, np.zeros((9, 2)))
+    assert e.value.status == iga.EINVAL
+    with pytest.raises(iga.IgaError) as e:
+        iga.Patch([9, 2], [np.zeros(20), np.zeros(6)], np.zeros((9, 2)))
+    assert e.value.status == iga.EINVAL

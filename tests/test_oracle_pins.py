@@ -240,6 +240,13 @@ def test_sampled_rows_equal_full_assembly():
     assert np.array_equal(Ms, M[rows]) and np.array_equal(Ks, K[rows])
 
 
+def test_mass_diagonal_equals_assembled_diagonal():
+    for w in (W.small(d=3, nel=(3, 4, 5), p=(2, 3, 2), amp=0.1), W.small(d=2, nel=(5, 4), p=3, amp=0.1)):
+        P = _patch(w)
+        M, _ = P.assemble(stiffness=False)
+        assert np.abs(P.mass_diagonal() - M[:, P.nslots // 2]).max() < 1e-15 * np.abs(M).max() * 10
+
+
 def test_rejects_folded_geometry():
     w = W.Workload("t", 3, (3, 3, 3), (2, 2, 2), 2.5, 1, 0.5, 1)
     with pytest.raises(ValueError):
