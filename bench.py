@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark: time steps per second of the explicit 2k-order generalized-alpha
+isogeometric step on GB300, with PCG iterations per step.
+
+Workload (default): 3-D unit cube mapped by x + 0.1 sin(pi x) sin(pi y) sin(pi z)
+in each coordinate, B-splines p = 3 (C^2) on 64^3 elements (N = 274625 interior
+dofs), k = 2 (4th order), rho_inf = 0.5, dt = 0.5 tau_crit, standing-wave initial
+data, FP64 PCG to relative residual 1e-10 with the fast-diagonalisation
+preconditioner. One "step" is one time step of the method: Taylor predictor,
+batched K product over the k vectors, k mass solves by PCG, fused stage update.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/sec and PCG iters/step, FP64 vs mixed/learned, at ≤1e-8 rel. error"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clock (2 FMA) x 2.07 GHz. The
+# per-SM unit count is inferred from an FMA-chain microbenchmark that reached
+# 1.201 TFLOP/s at ~1.98 GHz (profiles/fp64_peak_probe.md).
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture, valid only
+# for the kernel source it was taken on (sha256 of kernels_ops.cu, first 16 hex).
+NCU_TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cube64_p3")
+    ap.add_argument("--rho", type=float, default=0.5)
+    ap.add_argument("--cfl-iters", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_desc(w):
+    return ("%s: %dD unit %s, %s, p=%d C^%d, %s elements, N=%d, k=%d (order %d), rho_inf=%g, "
+            "dt=%.2f tau_crit, PCG tol %g" % (
+                w.name, w.d, "cube" if w.d == 3 else "square",
+                "deformed x+%g prod sin(pi x_i)" % w.amp if w.amp else "identity map", w.p[0], w.p[0] - 1,
+                "x".join(str(v) for v in w.nel), w.ndof, w.k, 2 * w.k, w.rho, w.cfl_fraction, w.tol))
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p.strip() for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts) and parts[local_rank].isdigit():
+            return int(parts[local_rank])
+    return local_rank
+
+
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_sha():
+    with open(os.path.join(ROOT, "paper_2102_11536_gb300", "csrc", "kernels_ops.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------- oracle (CPU)
+def oracle_setup(w, dt):
+    import oracle
+    t0 = time.perf_counter()
+    P = oracle.Patch(w.p, w.knots, w.ctrl())
+    ops = oracle.Operators(P)
+    setup_s = time.perf_counter() - t0
+    st = oracle.Stepper(ops, w.k, w.rho, tol=w.tol)
+    U0, V0 = w.initial()
+    X = st.init(U0, V0)
+    return st, X, setup_s, oracle.num_threads()
+
+
+def run_cpu_baseline(w, dt, target_s):
+    """The oracle as it stands on the host cores: M and K assembled once (not
+    timed), then whole time steps timed until about target_s seconds."""
+    st, X, setup_s, cores = oracle_setup(w, dt)
+    X0 = X.copy()
+    t0 = time.perf_counter()
+    X = st.step(X, dt)
+    first = time.perf_counter() - t0
+    nsteps = max(1, min(50, int(target_s / max(first, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        X = st.step(X, dt)
+    el = time.perf_counter() - t0
+    return {"value": nsteps / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d time steps of %s on %d host threads after one warm-up step; M and K assembled once "
+                      "(%.0f s, not timed)" % (nsteps, w.name, cores, setup_s),
+            "iters_per_step": sum(sum(i) for i in st.iters[1:]) / nsteps}, X0, X, nsteps + 1
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2102_11536_gb300 as iga
+    import workloads
+    from paper_2102_11536_gb300 import build as gb
+
+    rank, world, local_rank = dist_env()
+    gb.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    w = workloads.config(args.config)
+    w.rho = args.rho
+    k = w.k
+    U0, V0 = w.initial()
+    patch = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, device=local_rank)
+    N = patch.N
+    t0 = time.perf_counter()
+    lam, tc = patch.cfl(w.rho, iters=args.cfl_iters)
+    cfl_s = time.perf_counter() - t0
+    dt = w.cfl_fraction * tc
+    state = torch.empty(3 * k * N, dtype=torch.float64, device=dev)
+    u0 = torch.from_numpy(U0).to(dev)
+    v0 = torch.from_numpy(V0).to(dev)
+    patch.state_init(k, u0, v0, state)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        patch.step(state, k, w.rho, dt, 1)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(gpu_index_for(local_rank))
+    sampler.start()
+    patch.profile("mass")
+    stats = iga.Stats()
+    total_ms = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        flush.add_(1.0)  # evict L2 between timed steps (not timed)
+        e0.record(stream)
+        patch.step(state, k, w.rho, dt, 1, stats)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
+    prof_ms, prof_n, prof_flops, prof_bytes = patch.profile_read()
+    patch.profile("off")
+    clocks = sampler.stop()
+    t_local = total_ms / 1000.0
+    if pg:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+        pg.barrier()
+    else:
+        t_max = t_local
+    steps_per_s = world * args.steps / t_max
+
+    # end to end through the public C API on host memory: every step copies the
+    # state in from pinned host memory and the new state back out.
+    host = torch.empty(3 * k * N, dtype=torch.float64, pin_memory=True)
+    host.copy_(state)
+    st_e2e = iga.Stats()
+    patch.step_host(host, k, w.rho, dt, 1, st_e2e)  # warm
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        patch.step_host(host, k, w.rho, dt, 1, st_e2e)
+    e2e_s = time.perf_counter() - t0
+    e2e_rate = args.steps / e2e_s
+    if pg:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_rate = world * args.steps / float(tt.item())
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    hbm, hbm_kind = hbm_peak()
+    avg_ms = prof_ms / max(prof_n, 1)
+    achieved_tf = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
+    sha = kernel_sha()
+    traffic = NCU_TRAFFIC.get(sha)
+    result = {
+        "metric": METRIC,
+        "value": steps_per_s,
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": workload_desc(w),
+            "ndof": N,
+            "k": k,
+            "rho_inf": w.rho,
+            "dt": dt,
+            "lambda_max": lam,
+            "form": "FP64 matrix-free sum-factorised K and M, FP64 fast-diagonalisation preconditioner, "
+                    "zero initial guess (the paper's PCG setting)",
+            "l2": "L2 flushed (256 MB write) before every timed step; geometric factors (%.0f MB) exceed L2"
+                  % (7 * 8 * (w.nel[0] * (w.p[0] + 1)) ** 3 / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "pcg_iters_per_step": stats.iters / args.steps,
+        "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
+        "dof_updates_per_s": steps_per_s * N,
+        "gpu_launches": int(stats.launches),
+        "roofline": {
+            "kernel": "k_mid_mass (fused last-axis mass kernel: interpolate, x W, integrate)",
+            "bound": "alu",
+            "achieved": achieved_tf,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved_tf / FP64_PEAK_TFLOPS,
+            "traffic": traffic,
+            "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
+            "launches": prof_n,
+            "avg_launch_ms": avg_ms,
+            "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
+            "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
+            "hbm_view": {"achieved_gbs": prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0,
+                         "peak_gbs": hbm, "peak_kind": hbm_kind},
+        },
+        "e2e": {"value": e2e_rate, "unit": "steps/s", "h2d_bytes_per_step": 3 * k * N * 8,
+                "d2h_bytes_per_step": 3 * k * N * 8,
+                "api": "iga_step_host (state in pinned host memory, copied in and out every step)"},
+        "clocks": clocks,
+        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        base, X0, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
+        result["cpu_baseline"] = base
+        # full-size parity: the same number of steps on the GPU from the same initial state
+        g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, device=local_rank)
+        s2 = torch.empty_like(state)
+        g.state_init(k, u0, v0, s2)
+        g.step(s2, k, w.rho, dt, nst)
+        Xg = s2.view(3 * k, N).cpu().numpy()
+        result["parity_vs_oracle"] = {
+            "steps": nst,
+            "rel_l2_U": float(np.linalg.norm(Xg[0] - Xo[0]) / np.linalg.norm(Xo[0])),
+            "rel_l2_V": float(np.linalg.norm(Xg[1] - Xo[1]) / np.linalg.norm(Xo[1])),
+        }
+        g.close()
+    print(json.dumps(result), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: same workload, metric and unit."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+
+    w = workloads.config(args.config)
+    w.rho = args.rho
+    # lambda_max by the oracle's own power iteration (each iteration one PCG solve;
+    # capped at 20 on the CPU), dt = 0.5 tau_crit as on the GPU arm
+    st, X, setup_s, cores = oracle_setup(w, None)
+    lam = oracle.lambda_max_power(st.ops, iters=min(args.cfl_iters, 20), tol=1e-8)
+    dt = w.cfl_fraction * math.sqrt(oracle.theta_crit(w.rho) / lam)
+    for _ in range(args.warmup):
+        X = st.step(X, dt)
+    n0 = len(st.iters)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X = st.step(X, dt)
+    el = time.perf_counter() - t0
+    val = args.steps / el
+    iters = sum(sum(i) for i in st.iters[n0:]) / args.steps
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "ndof": w.ndof, "k": w.k, "rho_inf": w.rho, "dt": dt,
+                   "lambda_max": lam},
+        "pcg_iters_per_step": iters,
+        "cpu_baseline": {"value": val, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d whole time steps of %s after %d warm-up steps; M and K assembled once "
+                                   "(%.0f s, not timed)" % (args.steps, w.name, args.warmup, setup_s)},
+        "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -76,7 +76,15 @@ typedef struct iga_stats {
   long long iters;      /* PCG iterations summed over the solves */
   int max_iters;        /* largest iteration count of one solve */
   double max_relres;    /* largest final ||r||/||b|| */
+  long long launches;   /* CUDA kernel launches issued by the call */
 } iga_stats;
+
+/* Kernel classes that iga_profile can time (see iga_profile). */
+#define IGA_PROF_OFF 0
+#define IGA_PROF_MASS 1       /* the fused last-axis kernel of the matrix-free mass operator */
+#define IGA_PROF_STIFF 2      /* the fused last-axis kernel of the matrix-free stiffness operator */
+#define IGA_PROF_PRECOND 3    /* one whole preconditioner application (all mode products) */
+#define IGA_PROF_MASS_APPLY 4 /* one whole mass-operator application (all passes) */
 
 typedef struct iga_handle iga_handle;
 
@@ -197,6 +205,19 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
  */
 int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, double dt, int nsteps,
                   iga_stats* stats);
+
+/*
+ * Profiling of one kernel class (no counterpart in the paper; measurement aid).
+ * iga_profile(h, cls) brackets every later launch of that class on the handle's
+ * stream with a pair of CUDA events (IGA_PROF_OFF stops). iga_profile_read
+ * synchronises the stream and returns, since the last read: the summed device
+ * time in ms, the number of timed launches, and the ALGORITHMIC floating-point
+ * operations and DRAM bytes of those launches (the minimum work of the
+ * operation, counted by the library from the sizes; not hardware counters).
+ * All outputs are host pointers; any may be NULL.
+ */
+int iga_profile(iga_handle* h, int kernel_class);
+int iga_profile_read(iga_handle* h, double* total_ms, long long* launches, double* flops, double* bytes);
 
 #ifdef __cplusplus
 }

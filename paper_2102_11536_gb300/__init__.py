@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("solves", ctypes.c_int), ("iters", ctypes.c_longlong),
-                ("max_iters", ctypes.c_int), ("max_relres", ctypes.c_double)]
+                ("max_iters", ctypes.c_int), ("max_relres", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,6 +80,8 @@ def lib():
                                     ctypes.POINTER(Stats)]),
         "iga_step_host": (ctypes.c_int, [H, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(Stats)]),
+        "iga_profile": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_profile_read": (ctypes.c_int, [H, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -94,7 +96,10 @@ def exported_symbols():
     return ["iga_options_default", "iga_status_string", "iga_last_error", "iga_create", "iga_destroy",
             "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
             "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
-            "iga_state_init", "iga_step", "iga_step_host"]
+            "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read"]
+
+
+PROFILE_CLASSES = {"off": 0, "mass": 1, "stiff": 2, "precond": 3, "mass_apply": 4}
 
 
 def _ptr(t):
@@ -234,6 +239,21 @@ class Patch:
         st = stats if stats is not None else Stats()
         self._chk(lib().iga_step(self.h, _ptr(state), k, rho, dt, nsteps, ctypes.byref(st)), "iga_step")
         return st
+
+    def profile(self, kernel_class):
+        """Time every later launch of one kernel class ('mass', 'stiff', 'precond',
+        'mass_apply' or 'off') with CUDA events on the handle's stream."""
+        self._chk(lib().iga_profile(self.h, PROFILE_CLASSES[kernel_class]), "iga_profile")
+
+    def profile_read(self):
+        """(total_ms, launches, algorithmic_flops, algorithmic_bytes) since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        fl = ctypes.c_double()
+        by = ctypes.c_double()
+        self._chk(lib().iga_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                         ctypes.byref(by)), "iga_profile_read")
+        return ms.value, n.value, fl.value, by.value
 
     def step_host(self, state_host, k, rho, dt, nsteps=1, stats=None):
         """state_host: host buffer (numpy array or pinned CPU tensor) of 3k*N float64."""

@@ -45,6 +45,13 @@ struct iga_handle {
   int hist = 0;
   double* dstate = nullptr;
   long long dstate_cap = 0;
+  // launch counting and profiling of one kernel class
+  long long nlaunch = 0;
+  int cur_active = 0;  // host-known number of active systems of the running PCG
+  int prof_class = IGA_PROF_OFF;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
+  double prof_flops = 0.0, prof_bytes = 0.0;
   std::string err;
 };
 
@@ -70,6 +77,39 @@ int fail(iga_handle* h, int code, const std::string& msg) {
     int s_ = (expr);                \
     if (s_ != IGA_OK) return s_;    \
   } while (0)
+
+// a kernel launch: checked and counted
+#define LK(call)     \
+  do {               \
+    CK(call);        \
+    ++h->nlaunch;    \
+  } while (0)
+
+// Event bracket around the launches of one profiled kernel class.
+int prof_begin(iga_handle* h, int cls, cudaEvent_t* e1) {
+  *e1 = nullptr;
+  if (h->prof_class != cls) return IGA_OK;
+  cudaEvent_t a, b;
+  if (h->prof_pool.size() >= 2) {
+    a = h->prof_pool.back(); h->prof_pool.pop_back();
+    b = h->prof_pool.back(); h->prof_pool.pop_back();
+  } else {
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+  }
+  CK(cudaEventRecord(a, h->stream));
+  h->prof_pending.push_back({a, b});
+  *e1 = b;
+  return IGA_OK;
+}
+
+int prof_end(iga_handle* h, cudaEvent_t e1, double flops, double bytes) {
+  if (!e1) return IGA_OK;
+  CK(cudaEventRecord(e1, h->stream));
+  h->prof_flops += flops;
+  h->prof_bytes += bytes;
+  return IGA_OK;
+}
 
 template <typename T>
 int dalloc(iga_handle* h, T** p, size_t count) {
@@ -166,22 +206,51 @@ int ensure_cg_ws(iga_handle* h, int nvec) {
 // ---------------------------------------------------------------------------
 // operators
 // ---------------------------------------------------------------------------
+// Algorithmic work of the last-axis kernels per vector (FMA = 2 flops):
+// mass: interpolate (p+1 FMA), scale by W (1 mul), integrate (p+1 FMA) per point;
+// stiffness: 3 interpolations, the symmetric 3x3 product (9 mul + 6 add), 3 integrations.
+double mass_last_flops(const iga_handle* h) { return (4.0 * h->dd[h->dim - 1].P + 1.0) * (double)h->Qt; }
+double stiff_last_flops(const iga_handle* h) {
+  const double P = h->dd[h->dim - 1].P;
+  return h->dim == 3 ? (12.0 * P + 15.0) * (double)h->Qt : (8.0 * P + 6.0) * (double)h->Qt;
+}
+// whole mass application: banded passes of every axis, forward and transposed
+double mass_apply_flops(const iga_handle* h) {
+  const int *n = h->n, *Q = h->Q;
+  double f = mass_last_flops(h);
+  if (h->dim == 3) {
+    f += 2 * 2.0 * h->dd[0].P * (double)Q[0] * n[1] * n[2];
+    f += 2 * 2.0 * h->dd[1].P * (double)Q[0] * Q[1] * n[2];
+  } else {
+    f += 2 * 2.0 * h->dd[0].P * (double)Q[0] * n[1];
+  }
+  return f;
+}
+
 int apply_M_mf(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
   CKS(ensure_op_ws(h, nvec));
   cudaStream_t s = h->stream;
   const int *n = h->n, *Q = h->Q;
   const DirDev* d = h->dd;
+  const int nact = active ? h->cur_active : nvec;
+  cudaEvent_t ea = nullptr, em = nullptr;
+  CKS(prof_begin(h, IGA_PROF_MASS_APPLY, &ea));
   if (h->dim == 3) {
-    CK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
-    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, nullptr, nullptr, h->st));
-    CK(launch_mid_mass(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->W, h->ta, h->ta, h->st));
-    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, nullptr, nullptr, h->st, h->u0, h->su));
-    CK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, nullptr, nullptr, h->st));
+    CKS(prof_begin(h, IGA_PROF_MASS, &em));
+    LK(launch_mid_mass(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->W, h->ta, h->ta, h->st));
+    CKS(prof_end(h, em, nact * mass_last_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->st)));
+    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, nullptr, nullptr, h->st, h->u0, h->su));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
   } else {
-    CK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
-    CK(launch_mid_mass(s, d[1], Q[0], nvec, active, h->W, h->u0, h->u0, h->su));
-    CK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    CKS(prof_begin(h, IGA_PROF_MASS, &em));
+    LK(launch_mid_mass(s, d[1], Q[0], nvec, active, h->W, h->u0, h->u0, h->su));
+    CKS(prof_end(h, em, nact * mass_last_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->su)));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
   }
+  CKS(prof_end(h, ea, nact * mass_apply_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->N)));
   return IGA_OK;
 }
 
@@ -190,18 +259,24 @@ int apply_K_mf(iga_handle* h, int nvec, const int* active, const double* x, doub
   cudaStream_t s = h->stream;
   const int *n = h->n, *Q = h->Q;
   const DirDev* d = h->dd;
+  const int nact = active ? h->cur_active : nvec;
+  cudaEvent_t ek = nullptr;
   if (h->dim == 3) {
-    CK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
-    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, d[1].der, h->tb, h->st));
-    CK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u1, h->su, d[1].val, h->tc, nullptr, nullptr, h->st));
-    CK(launch_mid_stiff3(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->G, h->gstride, h->ta, h->tb, h->tc, h->st));
-    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, h->tb, d[1].der, h->st, h->u0, h->su));
-    CK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->tc, d[1].val, nullptr, nullptr, h->st, h->u1, h->su));
-    CK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
+    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, d[1].der, h->tb, h->st));
+    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u1, h->su, d[1].val, h->tc, nullptr, nullptr, h->st));
+    CKS(prof_begin(h, IGA_PROF_STIFF, &ek));
+    LK(launch_mid_stiff3(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->G, h->gstride, h->ta, h->tb, h->tc, h->st));
+    CKS(prof_end(h, ek, nact * stiff_last_flops(h), 8.0 * (6.0 * h->Qt + 6.0 * nact * h->st)));
+    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, h->tb, d[1].der, h->st, h->u0, h->su));
+    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->tc, d[1].val, nullptr, nullptr, h->st, h->u1, h->su));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
   } else {
-    CK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
-    CK(launch_mid_stiff2(s, d[1], Q[0], nvec, active, h->G, h->gstride, h->u0, h->u1, h->su));
-    CK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
+    CKS(prof_begin(h, IGA_PROF_STIFF, &ek));
+    LK(launch_mid_stiff2(s, d[1], Q[0], nvec, active, h->G, h->gstride, h->u0, h->u1, h->su));
+    CKS(prof_end(h, ek, nact * stiff_last_flops(h), 8.0 * (3.0 * h->Qt + 4.0 * nact * h->su)));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
   }
   return IGA_OK;
 }
@@ -223,17 +298,17 @@ int apply_Pinv_fd64(iga_handle* h, int nvec, const int* active, const double* r,
   const long long N = h->N;
   if (h->dim == 3) {
     const long long n01 = (long long)n[0] * n[1];
-    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n01 / n[0] * n[2]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
-    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
-    CK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
-    CK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
-    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
+    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n01 / n[0] * n[2]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
+    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
+    LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
+    LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
+    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
   } else {
-    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
-    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
-    CK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-    CK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
+    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
+    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
+    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
   }
   return IGA_OK;
 }
@@ -245,7 +320,14 @@ int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double*
   return apply_K_mf(h, nvec, active, x, y);
 }
 int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
-  return apply_Pinv_fd64(h, nvec, active, r, z);
+  const int nact = active ? h->cur_active : nvec;
+  double modes = 0.0;  // sum_a n_a: one mode product costs 2 n_a flops per entry, done twice
+  for (int a = 0; a < h->dim; ++a) modes += h->n[a];
+  cudaEvent_t e = nullptr;
+  CKS(prof_begin(h, IGA_PROF_PRECOND, &e));
+  CKS(apply_Pinv_fd64(h, nvec, active, r, z));
+  CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
+  return IGA_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -264,41 +346,43 @@ int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int*
   const bool flexible = h->opt.precond != IGA_PREC_FP64;
   if (use_x0) {
     CKS(apply_M(h, nvec, nullptr, x, h->q));
-    CK(launch_sub(s, N, nvec, b, h->q, h->r, N));
+    LK(launch_sub(s, N, nvec, b, h->q, h->r, N));
   } else {
     CK(cudaMemsetAsync(x, 0, sizeof(double) * nvec * N, s));
     CK(cudaMemcpyAsync(h->r, b, sizeof(double) * nvec * N, cudaMemcpyDeviceToDevice, s));
   }
-  CK(launch_dot(s, N, nvec, b, b, N, pA));
-  CK(launch_dot(s, N, nvec, h->r, h->r, N, pB));
-  CK(launch_cg_init(s, nvec, pA, pB, c, tol2));
+  LK(launch_dot(s, N, nvec, b, b, N, pA));
+  LK(launch_dot(s, N, nvec, h->r, h->r, N, pB));
+  LK(launch_cg_init(s, nvec, pA, pB, c, tol2));
   CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int nact = *h->h_nactive;
+  h->cur_active = nact;
   if (nact > 0) {
     CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-    CK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-    CK(launch_cg_start(s, nvec, pA, c));
-    CK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
+    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+    LK(launch_cg_start(s, nvec, pA, c));
+    LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
   }
   int it = 0;
   while (nact > 0 && it < h->opt.max_iter) {
     CKS(apply_M(h, nvec, c.active, h->p, h->q));
-    CK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
-    CK(launch_cg_alpha(s, nvec, pA, c));
-    CK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
-    CK(launch_cg_check(s, nvec, pB, c, tol2));
+    LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
+    LK(launch_cg_alpha(s, nvec, pA, c));
+    LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
+    LK(launch_cg_check(s, nvec, pB, c, tol2));
     CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     nact = *h->h_nactive;
+    h->cur_active = nact;
     ++it;
     if (nact == 0) break;
     if (flexible) std::swap(h->z, h->zold);
     CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-    CK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-    if (flexible) CK(launch_dot(s, N, nvec, h->r, h->zold, N, pC));
-    CK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
-    CK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
+    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+    if (flexible) LK(launch_dot(s, N, nvec, h->r, h->zold, N, pC));
+    LK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
+    LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
   }
   int hit[kMaxVec], hst[kMaxVec];
   double hrr[kMaxVec], hbb[kMaxVec];
@@ -394,6 +478,8 @@ void iga_destroy(iga_handle* h) {
   dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.alpha); dfree(h->cs.beta);
   dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
   if (h->h_nactive) cudaFreeHost(h->h_nactive);
+  for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
   dfree(h->Yneg); dfree(h->rhs); dfree(h->Z); dfree(h->Z2); dfree(h->dstate);
   delete h;
 }
@@ -469,7 +555,7 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
     CKS(dalloc(h, &h->dflag, 4));
     CK(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 4, h->stream));
     int mm[3] = {h->m[0], h->m[1], h->m[2]};
-    CK(launch_geometry(h->stream, dim, h->dd, mm, h->ctrl, h->W, h->G, h->gstride, h->dflag));
+    LK(launch_geometry(h->stream, dim, h->dd, mm, h->ctrl, h->W, h->G, h->gstride, h->dflag));
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -487,12 +573,12 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
     const int *n = h->n, *Q = h->Q;
     const DirDev* d = h->dd;
     if (dim == 3) {
-      CK(launch_tr(h->stream, d[2], {(long long)Q[0] * Q[1], Q[2], n[2], 1}, 1, nullptr, h->W, d[2].sq, nullptr, nullptr, 0, h->ta, 0));
-      CK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], n[2]}, 1, nullptr, h->ta, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
-      CK(launch_tr(h->stream, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
+      LK(launch_tr(h->stream, d[2], {(long long)Q[0] * Q[1], Q[2], n[2], 1}, 1, nullptr, h->W, d[2].sq, nullptr, nullptr, 0, h->ta, 0));
+      LK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], n[2]}, 1, nullptr, h->ta, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
+      LK(launch_tr(h->stream, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
     } else {
-      CK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], 1}, 1, nullptr, h->W, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
-      CK(launch_tr(h->stream, d[0], {1, Q[0], n[0], n[1]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
+      LK(launch_tr(h->stream, d[1], {Q[0], Q[1], n[1], 1}, 1, nullptr, h->W, d[1].sq, nullptr, nullptr, 0, h->u0, 0));
+      LK(launch_tr(h->stream, d[0], {1, Q[0], n[0], n[1]}, 1, nullptr, h->u0, d[0].sq, nullptr, nullptr, 0, h->Dm, 0));
     }
     std::vector<double> D((size_t)h->N), sc((size_t)h->N);
     CK(cudaMemcpyAsync(D.data(), h->Dm, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
@@ -594,7 +680,7 @@ int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, dou
   for (int a = 0; a <= last; a += 2) {
     const int nv = (a + 1 <= last) ? 2 : 1;
     CKS(apply_K(h, nv, nullptr, state + (long long)a * N, h->rhs));
-    CK(launch_scale_neg(s, nv * N, h->rhs));
+    LK(launch_scale_neg(s, nv * N, h->rhs));
     CKS(solve(h, nv, h->rhs, state + (long long)(a + 2) * N, false, nullptr, nullptr));
   }
   h->hist = 0;
@@ -617,10 +703,11 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
     sc.c[m] = std::pow(dt, m) / fact;
   }
   galpha_params(k, rho_inf, sc.alpha, sc.beta, sc.gamma);
+  const long long launches0 = h->nlaunch;
   for (int step = 0; step < nsteps; ++step) {
     const int guess = h->opt.guess;
     const bool taylor = guess == IGA_GUESS_TAYLOR;
-    CK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr));
+    LK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr));
     CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
     bool use_x0 = false;
     if (taylor) {
@@ -628,7 +715,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
     } else if (guess == IGA_GUESS_PREV && h->hist >= 1) {
       use_x0 = true;  // Z still holds the previous step's solutions
     } else if (guess == IGA_GUESS_EXTRAP && h->hist >= 1) {
-      if (h->hist >= 2) CK(launch_extrap(s, (long long)k * N, h->Z, h->Z2));
+      if (h->hist >= 2) LK(launch_extrap(s, (long long)k * N, h->Z, h->Z2));
       else CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
       use_x0 = true;
     }
@@ -637,7 +724,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
     CKS(solve(h, k, h->rhs, h->Z, use_x0, its, rel));
     if (guess == IGA_GUESS_EXTRAP && h->hist == 0)
       CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
-    CK(launch_update(s, N, sc, state, h->Z));
+    LK(launch_update(s, N, sc, state, h->Z));
     h->hist = std::min(h->hist + 1, 2);
     if (stats) {
       stats->steps += 1;
@@ -649,6 +736,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
       }
     }
   }
+  if (stats) stats->launches += h->nlaunch - launches0;
   CK(cudaStreamSynchronize(s));
   return IGA_OK;
 }
@@ -666,6 +754,33 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
   CKS(iga_step(h, h->dstate, k, rho_inf, dt, nsteps, stats));
   CK(cudaMemcpyAsync(state_host, h->dstate, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return IGA_OK;
+}
+
+int iga_profile(iga_handle* h, int kernel_class) {
+  CKS(check_handle(h));
+  if (kernel_class < IGA_PROF_OFF || kernel_class > IGA_PROF_MASS_APPLY) return fail(h, IGA_EINVAL, "bad kernel class");
+  h->prof_class = kernel_class;
+  return IGA_OK;
+}
+
+int iga_profile_read(iga_handle* h, double* total_ms, long long* launches, double* flops, double* bytes) {
+  CKS(check_handle(h));
+  CK(cudaStreamSynchronize(h->stream));
+  double ms = 0.0;
+  for (auto& pr : h->prof_pending) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+    ms += t;
+    h->prof_pool.push_back(pr.first);
+    h->prof_pool.push_back(pr.second);
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = (long long)h->prof_pending.size();
+  if (flops) *flops = h->prof_flops;
+  if (bytes) *bytes = h->prof_bytes;
+  h->prof_pending.clear();
+  h->prof_flops = h->prof_bytes = 0.0;
   return IGA_OK;
 }
 
@@ -700,8 +815,8 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
     CKS(apply_K(h, 1, nullptr, x, y));
     int st = solve(h, 1, y, zz, false, nullptr, nullptr);
     if (st != IGA_OK) { h->opt.tol = tol_save; return st; }
-    CK(launch_dot(s, N, 1, zz, zz, N, pA));
-    CK(launch_reduce(s, 1, pA, res));
+    LK(launch_dot(s, N, 1, zz, zz, N, pA));
+    LK(launch_reduce(s, 1, pA, res));
     double nz = 0.0;
     CK(cudaMemcpyAsync(&nz, res, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -715,10 +830,10 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
   // Rayleigh quotient x^T K x / x^T M x
   CKS(apply_K(h, 1, nullptr, x, y));
   CKS(apply_M(h, 1, nullptr, x, zz));
-  CK(launch_dot(s, N, 1, x, y, N, pA));
-  CK(launch_reduce(s, 1, pA, res));
-  CK(launch_dot(s, N, 1, x, zz, N, pA));
-  CK(launch_reduce(s, 1, pA, res + 1));
+  LK(launch_dot(s, N, 1, x, y, N, pA));
+  LK(launch_reduce(s, 1, pA, res));
+  LK(launch_dot(s, N, 1, x, zz, N, pA));
+  LK(launch_reduce(s, 1, pA, res + 1));
   double kx[2];
   CK(cudaMemcpyAsync(kx, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
