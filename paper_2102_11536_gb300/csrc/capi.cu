@@ -313,6 +313,34 @@ int apply_Pinv_fd64(iga_handle* h, int nvec, const int* active, const double* r,
   return IGA_OK;
 }
 
+// FP32 form: the same six mode products in FP32 on the CUDA cores, FP32
+// intermediates (stored in the FP64 scratch buffers), FP64 input and output.
+int apply_Pinv_fd32(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
+  CKS(ensure_cg_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const int* n = h->n;
+  const DirDev* d = h->dd;
+  float* t1 = reinterpret_cast<float*>(h->f1);
+  float* t2 = reinterpret_cast<float*>(h->f2);
+  const float* lam[3] = {d[0].lam32, d[1].lam32, h->dim == 3 ? d[2].lam32 : nullptr};
+  const long long N = h->N;
+  if (h->dim == 3) {
+    const long long n01 = (long long)n[0] * n[1];
+    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U32, 1, r, 1, t1, 0, N, h->scale, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, t1, 0, t2, 0, N, nullptr, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, t2, 0, t1, 0, N, nullptr, nullptr, lam, n));
+    LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, t1, 0, t2, 0, N, nullptr, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, t2, 0, t1, 0, N, nullptr, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U32, 0, t1, 0, z, 1, N, nullptr, h->scale, nullptr, n));
+  } else {
+    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, r, 1, t1, 0, N, h->scale, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, t1, 0, t2, 0, N, nullptr, nullptr, lam, n));
+    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, t2, 0, t1, 0, N, nullptr, nullptr, nullptr, n));
+    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, t1, 0, z, 1, N, nullptr, h->scale, nullptr, n));
+  }
+  return IGA_OK;
+}
+
 int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
   return apply_M_mf(h, nvec, active, x, y);
 }
@@ -325,7 +353,11 @@ int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, doub
   for (int a = 0; a < h->dim; ++a) modes += h->n[a];
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, IGA_PROF_PRECOND, &e));
-  CKS(apply_Pinv_fd64(h, nvec, active, r, z));
+  switch (h->opt.precond) {
+    case IGA_PREC_FP64: CKS(apply_Pinv_fd64(h, nvec, active, r, z)); break;
+    case IGA_PREC_FP32: CKS(apply_Pinv_fd32(h, nvec, active, r, z)); break;
+    default: return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
+  }
   CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
   return IGA_OK;
 }

@@ -435,6 +435,49 @@ __global__ void __launch_bounds__(256) k_fd64(int n, int A, const int* __restric
 }
 
 // ----------------------------------------------------------------------------
+// FP32 fast-diagonalisation mode product (CUDA cores): FP64 or FP32 in/out,
+// FP32 arithmetic and factors. The first mode reads the FP64 residual and
+// applies the FP64 scaling before rounding; the last mode rescales in FP64.
+// ----------------------------------------------------------------------------
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_fd32(int n, int A, const int* __restrict__ active, const float* __restrict__ U,
+                                              int transpose, const TI* __restrict__ in, TO* __restrict__ out,
+                                              long long vs, const double* __restrict__ pre,
+                                              const double* __restrict__ post, const float* __restrict__ lam0,
+                                              const float* __restrict__ lam1, const float* __restrict__ lam2, int n0,
+                                              int n1) {
+  const int v = blockIdx.z;
+  if (active && !active[v]) return;
+  const int y = blockIdx.y;
+  const int flat = blockIdx.x * blockDim.x + threadIdx.x;
+  if (flat >= A * n) return;
+  const int i = flat / A;
+  const int x = flat - i * A;
+  const long long rowbase = (long long)y * n * A + x;
+  const TI* src = in + v * vs + rowbase;
+  float acc = 0.0f;
+  for (int j = 0; j < n; ++j) {
+    const long long o = (long long)j * A;
+    float u;
+    if (pre) u = (float)((double)src[o] * pre[rowbase + o]);
+    else u = (float)src[o];
+    const float m = transpose ? U[(long long)i * n + j] : U[(long long)j * n + i];
+    acc = fmaf(m, u, acc);
+  }
+  const long long idx = rowbase + (long long)i * A;
+  if (lam0) {
+    const int i0 = (int)(idx % n0);
+    const int i1 = (int)((idx / n0) % n1);
+    const int i2 = (int)(idx / ((long long)n0 * n1));
+    float l = lam0[i0] * lam1[i1];
+    if (lam2) l *= lam2[i2];
+    acc = acc / l;
+  }
+  if (post) out[v * vs + idx] = (TO)((double)acc * post[idx]);
+  else out[v * vs + idx] = (TO)acc;
+}
+
+// ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
 #define IGA_DISPATCH_P(P, ...)                              \
@@ -541,6 +584,28 @@ cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, cons
   if (sh.B > 65535 || sh.A * n > 0x7fffffffLL) return cudaErrorInvalidValue;
   dim3 grid = plane_grid(sh.A * n, sh.B, nvec, 256);
   k_fd64<<<grid, 256, 0, s>>>(n, (int)sh.A, active, U, transpose, in, out, vs, pre, ep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
+                             int transpose, const void* in, int in_is_double, void* out, int out_is_double,
+                             long long vs, const double* pre, const double* post, const float* const* lam,
+                             const int* nn) {
+  if (sh.B > 65535 || sh.A * n > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid = plane_grid(sh.A * n, sh.B, nvec, 256);
+  const float* l0 = lam ? lam[0] : nullptr;
+  const float* l1 = lam ? lam[1] : nullptr;
+  const float* l2 = lam ? lam[2] : nullptr;
+  const int n0 = nn ? nn[0] : 1, n1 = nn ? nn[1] : 1;
+  const int A = (int)sh.A;
+  if (in_is_double && !out_is_double)
+    k_fd32<double, float><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const double*)in, (float*)out, vs, pre, post, l0, l1, l2, n0, n1);
+  else if (!in_is_double && !out_is_double)
+    k_fd32<float, float><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const float*)in, (float*)out, vs, pre, post, l0, l1, l2, n0, n1);
+  else if (!in_is_double && out_is_double)
+    k_fd32<float, double><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const float*)in, (double*)out, vs, pre, post, l0, l1, l2, n0, n1);
+  else
+    k_fd32<double, double><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const double*)in, (double*)out, vs, pre, post, l0, l1, l2, n0, n1);
   return cudaGetLastError();
 }
 
