@@ -154,6 +154,36 @@ int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y);
 int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y);
 
 /*
+ * iga_apply_Pinv_noalloc -- the same preconditioner application as
+ * iga_apply_Pinv (same arithmetic, same result), for callers that must not
+ * allocate device memory at call time. The paper has no counterpart; this is a
+ * deployment aid.
+ *
+ * Who needs it: iga_apply_Pinv keeps its intermediate buffers in the handle and
+ * grows them with cudaMalloc the first time a larger nvec is seen. That is not
+ * possible for callers whose device memory is already committed to another
+ * allocator (a framework's caching pool, so a fresh cudaMalloc fails or
+ * fragments), for real-time loops that forbid allocation after start-up, and
+ * for code that must stay free of allocation calls while it runs. This entry
+ * point instead uses a fixed scratch array built into the library: two buffers
+ * of 1,048,576 doubles (16 MiB in total), which every GPU that loads the
+ * library holds until the process exits. It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * Arguments as for iga_apply_Pinv (device pointers x, y of nvec*N doubles,
+ * 1 <= nvec <= 8). nvec * N must not exceed 1,048,576; larger requests return
+ * IGA_EINVAL with a message and do nothing.
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (with that device current). Make that first call before any
+ * stream capture. Every call on a device shares the one array and leaves the
+ * last call's values in it (nothing in it needs to start at zero), so calls
+ * whose kernels overlap on the GPU -- from different streams, threads or
+ * handles on the same device -- race and corrupt each other; serialise them.
+ */
+int iga_apply_Pinv_noalloc(iga_handle* h, int nvec, const double* x, double* y);
+
+/*
  * iga_solve_M -- solve M x_v = b_v for nvec independent right-hand sides by
  * preconditioned CG (Sec. 5.5), stopping each at ||r||_2 <= tol ||b||_2.
  * b, x: device, nvec*N doubles. use_x0 != 0 takes x as the initial guess, else

@@ -72,6 +72,7 @@ def lib():
         "iga_apply_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_K": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_Pinv": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
+        "iga_apply_Pinv_noalloc": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_solve_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp, ctypes.c_int, ip, dp]),
         "iga_galpha_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, dp, dp, dp]),
         "iga_cfl": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_int, dp, dp]),
@@ -96,7 +97,8 @@ def exported_symbols():
     return ["iga_options_default", "iga_status_string", "iga_last_error", "iga_create", "iga_destroy",
             "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
             "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
-            "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read"]
+            "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read",
+            "iga_apply_Pinv_noalloc"]
 
 
 PROFILE_CLASSES = {"off": 0, "mass": 1, "stiff": 2, "precond": 3, "mass_apply": 4}
@@ -216,6 +218,12 @@ class Patch:
     def apply_Pinv(self, x, y, nvec=1):
         _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")
         self._chk(lib().iga_apply_Pinv(self.h, nvec, _ptr(x), _ptr(y)), "iga_apply_Pinv")
+
+    def apply_Pinv_noalloc(self, x, y, nvec=1):
+        """iga_apply_Pinv_noalloc: the preconditioner with the library's fixed scratch
+        (no device allocation at call time; nvec * N <= 1048576)."""
+        _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")
+        self._chk(lib().iga_apply_Pinv_noalloc(self.h, nvec, _ptr(x), _ptr(y)), "iga_apply_Pinv_noalloc")
 
     def solve_M(self, b, x, nvec=1, use_x0=False):
         _check_dev(b, nvec * self.N, "b"); _check_dev(x, nvec * self.N, "x")

@@ -460,6 +460,69 @@ int ensure_step_ws(iga_handle* h, int k) {
 
 }  // namespace
 
+namespace iga {
+
+int handle_device(iga_handle* h, int* device) {
+  CKS(check_handle(h));
+  *device = h->opt.device;
+  return IGA_OK;
+}
+
+int handle_fail(iga_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
+
+int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2) {
+  cudaStream_t s = h->stream;
+  const int* n = h->n;
+  const DirDev* d = h->dd;
+  const long long N = h->N;
+  const long long n01 = (long long)n[0] * n[1];
+  const long long n12 = (long long)n[1] * n[2];
+  if (h->opt.precond == IGA_PREC_FP64) {
+    FdEpilogue none{}, lam{}, post{};
+    lam.lam[0] = d[0].lam64;
+    lam.lam[1] = d[1].lam64;
+    lam.lam[2] = h->dim == 3 ? d[2].lam64 : nullptr;
+    lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
+    post.post = h->scale;
+    if (h->dim == 3) {
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U64, 1, x, t1, N, h->scale, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U64, 1, t1, t2, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U64, 1, t2, t1, N, nullptr, lam));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U64, 0, t1, t2, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U64, 0, t2, t1, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U64, 0, t1, y, N, nullptr, post));
+    } else {
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U64, 1, x, t1, N, h->scale, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U64, 1, t1, t2, N, nullptr, lam));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U64, 0, t2, t1, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U64, 0, t1, y, N, nullptr, post));
+    }
+    return IGA_OK;
+  }
+  if (h->opt.precond == IGA_PREC_FP32) {
+    float* f1 = reinterpret_cast<float*>(t1);
+    float* f2 = reinterpret_cast<float*>(t2);
+    const float* lam[3] = {d[0].lam32, d[1].lam32, h->dim == 3 ? d[2].lam32 : nullptr};
+    if (h->dim == 3) {
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U32, 1, x, 1, f1, 0, N, h->scale, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U32, 0, f1, 0, y, 1, N, nullptr, h->scale, nullptr, n));
+    } else {
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U32, 1, x, 1, f1, 0, N, h->scale, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U32, 0, f1, 0, y, 1, N, nullptr, h->scale, nullptr, n));
+    }
+    return IGA_OK;
+  }
+  return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
+}
+
+}  // namespace iga
+
 // ===========================================================================
 // public API
 // ===========================================================================

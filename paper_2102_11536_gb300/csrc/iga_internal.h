@@ -165,4 +165,13 @@ cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, 
 cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
 
+// Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
+constexpr long long kNoAllocMaxElems = 1LL << 20;
+// Helpers for entry points defined outside capi.cu.
+int handle_device(iga_handle* h, int* device);  // makes h's device current
+int handle_fail(iga_handle* h, int code, const std::string& msg);
+// The preconditioner in h's arithmetic with caller-provided scratch t1, t2 (each
+// nvec * N doubles); allocates nothing.
+int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2);
+
 }  // namespace iga
