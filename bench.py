@@ -1,13 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark: time steps per second of the explicit 2k-order generalized-alpha
-isogeometric step on GB300, with PCG iterations per step.
+isogeometric step on GB300, with PCG iterations per step, for the FP64 form of
+the method and its faster forms, at <= 1e-8 relative error.
 
 Workload (default): 3-D unit cube mapped by x + 0.1 sin(pi x) sin(pi y) sin(pi z)
 in each coordinate, B-splines p = 3 (C^2) on 64^3 elements (N = 274625 interior
 dofs), k = 2 (4th order), rho_inf = 0.5, dt = 0.5 tau_crit, standing-wave initial
-data, FP64 PCG to relative residual 1e-10 with the fast-diagonalisation
+data, PCG to relative residual 1e-10 with the fast-diagonalisation
 preconditioner. One "step" is one time step of the method: Taylor predictor,
 batched K product over the k vectors, k mass solves by PCG, fused stage update.
+
+Forms measured (all FP64 state, FP64 PCG residuals and dot products, same tol):
+  fp64_paper      matrix-free sum-factorised K, M; FP64 preconditioner; zero guess
+                  (the paper's PCG setting)
+  fp64_assembled  assembled band K, M; FP64 preconditioner; zero guess
+  mixed_fp32      assembled band K, M; FP32 preconditioner (flexible PCG); zero guess
+  mixed_taylor    as mixed_fp32 with the Taylor predictor as initial guess
+The headline value is the fastest form whose U and V stay within 1e-8 (relative
+L2) of the fp64_paper run after the same steps from the same initial state.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -34,21 +44,35 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 1.201 TFLOP/s at ~1.98 GHz (profiles/fp64_peak_probe.md).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
+ERR_LIMIT = 1e-8
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture, valid only
-# for the kernel source it was taken on (sha256 of kernels_ops.cu, first 16 hex).
+FORMS = [
+    ("fp64_paper", dict(op_form="matrix_free", precond="fp64", guess="zero"), "mass",
+     "k_mid_mass (fused last-axis mass kernel: interpolate, x W, integrate)"),
+    ("fp64_assembled", dict(op_form="assembled", precond="fp64", guess="zero"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+    ("mixed_fp32", dict(op_form="assembled", precond="fp32", guess="zero"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+    ("mixed_taylor", dict(op_form="assembled", precond="fp32", guess="taylor"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+]
+
+# DRAM traffic per launch of a profiled kernel from an ncu capture, keyed by
+# (kernel, sha256 of the kernel's source file, first 16 hex): a capture only
+# counts while the source it was taken on is unchanged.
 NCU_TRAFFIC = {}
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cube64_p3")
     ap.add_argument("--rho", type=float, default=0.5)
     ap.add_argument("--cfl-iters", type=int, default=60)
+    ap.add_argument("--forms", default=",".join(f[0] for f in FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -132,13 +156,16 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_sha():
-    with open(os.path.join(ROOT, "paper_2102_11536_gb300", "csrc", "kernels_ops.cu"), "rb") as f:
+def source_sha(name):
+    with open(os.path.join(ROOT, "paper_2102_11536_gb300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+KERNEL_SOURCE = {"mass": "kernels_ops.cu", "band_mass": "kernels_band.cu"}
+
+
 # ---------------------------------------------------------------------------- oracle (CPU)
-def oracle_setup(w, dt):
+def oracle_setup(w):
     import oracle
     t0 = time.perf_counter()
     P = oracle.Patch(w.p, w.knots, w.ctrl())
@@ -153,8 +180,7 @@ def oracle_setup(w, dt):
 def run_cpu_baseline(w, dt, target_s):
     """The oracle as it stands on the host cores: M and K assembled once (not
     timed), then whole time steps timed until about target_s seconds."""
-    st, X, setup_s, cores = oracle_setup(w, dt)
-    X0 = X.copy()
+    st, X, setup_s, cores = oracle_setup(w)
     t0 = time.perf_counter()
     X = st.step(X, dt)
     first = time.perf_counter() - t0
@@ -166,10 +192,35 @@ def run_cpu_baseline(w, dt, target_s):
     return {"value": nsteps / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
             "sample": "%d time steps of %s on %d host threads after one warm-up step; M and K assembled once "
                       "(%.0f s, not timed)" % (nsteps, w.name, cores, setup_s),
-            "iters_per_step": sum(sum(i) for i in st.iters[1:]) / nsteps}, X0, X, nsteps + 1
+            "iters_per_step": sum(sum(i) for i in st.iters[1:]) / nsteps}, X, nsteps + 1
 
 
 # ---------------------------------------------------------------------------- GPU arm
+def time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class):
+    k = w.k
+    for _ in range(args.warmup):
+        patch.step(state, k, w.rho, dt, 1)
+    torch.cuda.synchronize()
+    patch.profile(prof_class)
+    stats = iga.Stats()
+    total_ms = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        flush.add_(1.0)  # evict L2 between timed steps (not timed)
+        e0.record(stream)
+        patch.step(state, k, w.rho, dt, 1, stats)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    prof = patch.profile_read()
+    patch.profile("off")
+    return total_ms, stats, prof
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -198,50 +249,84 @@ def run_ours(args):
     lam, tc = patch.cfl(w.rho, iters=args.cfl_iters)
     cfl_s = time.perf_counter() - t0
     dt = w.cfl_fraction * tc
+    t0 = time.perf_counter()
+    patch.assemble()
+    assemble_s = time.perf_counter() - t0
     state = torch.empty(3 * k * N, dtype=torch.float64, device=dev)
     u0 = torch.from_numpy(U0).to(dev)
     v0 = torch.from_numpy(V0).to(dev)
-    patch.state_init(k, u0, v0, state)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    hbm, hbm_kind = hbm_peak()
 
-    for _ in range(args.warmup):
-        patch.step(state, k, w.rho, dt, 1)
-    torch.cuda.synchronize(dev)
-    if pg:
-        pg.barrier()
+    wanted = args.forms.split(",")
+    results = {}
+    finals = {}
     sampler = ClockSampler(gpu_index_for(local_rank))
-    sampler.start()
-    patch.profile("mass")
-    stats = iga.Stats()
-    total_ms = 0.0
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
-    for _ in range(args.steps):
-        flush.add_(1.0)  # evict L2 between timed steps (not timed)
-        e0.record(stream)
-        patch.step(state, k, w.rho, dt, 1, stats)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize(dev)
-    torch.cuda.nvtx.range_pop()
-    prof_ms, prof_n, prof_flops, prof_bytes = patch.profile_read()
-    patch.profile("off")
-    clocks = sampler.stop()
-    t_local = total_ms / 1000.0
     if pg:
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
         pg.barrier()
-    else:
-        t_max = t_local
-    steps_per_s = world * args.steps / t_max
+    sampler.start()
+    for name, opts, prof_class, kdesc in FORMS:
+        if name not in wanted:
+            continue
+        patch.set_op_form(opts["op_form"])
+        patch.set_precond(opts["precond"])
+        patch.set_guess(opts["guess"])
+        patch.state_init(k, u0, v0, state)
+        total_ms, stats, prof = time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class)
+        t_local = total_ms / 1000.0
+        if pg:
+            tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            t_max = float(tt.item())
+        else:
+            t_max = t_local
+        finals[name] = state.view(3 * k, N)[:2].cpu().numpy()
+        prof_ms, prof_n, prof_flops, prof_bytes = prof
+        achieved = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
+        sha = source_sha(KERNEL_SOURCE[prof_class])
+        results[name] = {
+            "options": opts,
+            "value": world * args.steps / t_max,
+            "ms_per_step": total_ms / args.steps,
+            "pcg_iters_per_step": stats.iters / args.steps,
+            "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
+            "gpu_launches": int(stats.launches),
+            "roofline": {
+                "kernel": kdesc,
+                "bound": "alu",
+                "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": NCU_TRAFFIC.get((prof_class, sha)),
+                "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
+                "launches": prof_n,
+                "avg_launch_ms": prof_ms / max(prof_n, 1),
+                "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
+                "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
+                "hbm_view": {"achieved_gbs": prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0,
+                             "peak_gbs": hbm, "peak_kind": hbm_kind},
+            },
+        }
+    clocks = sampler.stop()
+    ref = finals.get("fp64_paper")
+    for name, r in results.items():
+        if ref is not None:
+            r["rel_err_vs_fp64_paper"] = {
+                "U": float(np.linalg.norm(finals[name][0] - ref[0]) / np.linalg.norm(ref[0])),
+                "V": float(np.linalg.norm(finals[name][1] - ref[1]) / np.linalg.norm(ref[1]))}
+    ok = [n for n, r in results.items()
+          if "rel_err_vs_fp64_paper" not in r or max(r["rel_err_vs_fp64_paper"].values()) <= ERR_LIMIT]
+    head = max(ok, key=lambda n: results[n]["value"])
+    hopts = results[head]["options"]
 
-    # end to end through the public C API on host memory: every step copies the
-    # state in from pinned host memory and the new state back out.
+    # end to end through the public C API on host memory, headline form: every step
+    # copies the state in from pinned host memory and the new state back out.
+    patch.set_op_form(hopts["op_form"])
+    patch.set_precond(hopts["precond"])
+    patch.set_guess(hopts["guess"])
+    patch.state_init(k, u0, v0, state)
     host = torch.empty(3 * k * N, dtype=torch.float64, pin_memory=True)
     host.copy_(state)
     st_e2e = iga.Stats()
@@ -251,30 +336,27 @@ def run_ours(args):
     for _ in range(args.steps):
         patch.step_host(host, k, w.rho, dt, 1, st_e2e)
     e2e_s = time.perf_counter() - t0
-    e2e_rate = args.steps / e2e_s
     if pg:
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_rate = world * args.steps / float(tt.item())
+        e2e_s = float(tt.item())
+        pg.barrier()
+    e2e_rate = world * args.steps / e2e_s
 
     if rank != 0:
         if pg:
             pg.destroy_process_group()
         return
 
-    hbm, hbm_kind = hbm_peak()
-    avg_ms = prof_ms / max(prof_n, 1)
-    achieved_tf = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
-    sha = kernel_sha()
-    traffic = NCU_TRAFFIC.get(sha)
+    h = results[head]
     result = {
         "metric": METRIC,
-        "value": steps_per_s,
+        "value": h["value"],
         "unit": "steps/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps,
+        "ms_per_step": h["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -287,53 +369,40 @@ def run_ours(args):
             "rho_inf": w.rho,
             "dt": dt,
             "lambda_max": lam,
-            "form": "FP64 matrix-free sum-factorised K and M, FP64 fast-diagonalisation preconditioner, "
-                    "zero initial guess (the paper's PCG setting)",
+            "form": head,
+            "form_options": hopts,
             "l2": "L2 flushed (256 MB write) before every timed step; geometric factors (%.0f MB) exceed L2"
                   % (7 * 8 * (w.nel[0] * (w.p[0] + 1)) ** 3 / 1e6),
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
-        "pcg_iters_per_step": stats.iters / args.steps,
-        "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
-        "dof_updates_per_s": steps_per_s * N,
-        "gpu_launches": int(stats.launches),
-        "roofline": {
-            "kernel": "k_mid_mass (fused last-axis mass kernel: interpolate, x W, integrate)",
-            "bound": "alu",
-            "achieved": achieved_tf,
-            "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s",
-            "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": traffic,
-            "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
-            "launches": prof_n,
-            "avg_launch_ms": avg_ms,
-            "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
-            "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
-            "hbm_view": {"achieved_gbs": prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0,
-                         "peak_gbs": hbm, "peak_kind": hbm_kind},
-        },
+        "pcg_iters_per_step": h["pcg_iters_per_step"],
+        "pcg_iters_per_solve": h["pcg_iters_per_solve"],
+        "dof_updates_per_s": h["value"] * N,
+        "gpu_launches": h["gpu_launches"],
+        "roofline": h["roofline"],
+        "forms": results,
         "e2e": {"value": e2e_rate, "unit": "steps/s", "h2d_bytes_per_step": 3 * k * N * 8,
                 "d2h_bytes_per_step": 3 * k * N * 8,
-                "api": "iga_step_host (state in pinned host memory, copied in and out every step)"},
+                "api": "iga_step_host (state in pinned host memory, copied in and out every step), form " + head},
         "clocks": clocks,
-        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s},
+        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s},
     }
     if not args.no_cpu_baseline and world == 1:
-        base, X0, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
+        base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
         result["cpu_baseline"] = base
-        # full-size parity: the same number of steps on the GPU from the same initial state
-        g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, device=local_rank)
-        s2 = torch.empty_like(state)
-        g.state_init(k, u0, v0, s2)
-        g.step(s2, k, w.rho, dt, nst)
-        Xg = s2.view(3 * k, N).cpu().numpy()
+        # full-size parity: the same number of steps on the GPU (FP64 form) from the same initial state
+        patch.set_op_form("matrix_free")
+        patch.set_precond("fp64")
+        patch.set_guess("zero")
+        patch.state_init(k, u0, v0, state)
+        patch.step(state, k, w.rho, dt, nst)
+        Xg = state.view(3 * k, N).cpu().numpy()
         result["parity_vs_oracle"] = {
             "steps": nst,
+            "form": "fp64_paper",
             "rel_l2_U": float(np.linalg.norm(Xg[0] - Xo[0]) / np.linalg.norm(Xo[0])),
             "rel_l2_V": float(np.linalg.norm(Xg[1] - Xo[1]) / np.linalg.norm(Xo[1])),
         }
-        g.close()
     print(json.dumps(result), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -352,7 +421,7 @@ def run_reference(args):
     w.rho = args.rho
     # lambda_max by the oracle's own power iteration (each iteration one PCG solve;
     # capped at 20 on the CPU), dt = 0.5 tau_crit as on the GPU arm
-    st, X, setup_s, cores = oracle_setup(w, None)
+    st, X, setup_s, cores = oracle_setup(w)
     lam = oracle.lambda_max_power(st.ops, iters=min(args.cfl_iters, 20), tol=1e-8)
     dt = w.cfl_fraction * math.sqrt(oracle.theta_crit(w.rho) / lam)
     for _ in range(args.warmup):

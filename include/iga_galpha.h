@@ -85,6 +85,8 @@ typedef struct iga_stats {
 #define IGA_PROF_STIFF 2      /* the fused last-axis kernel of the matrix-free stiffness operator */
 #define IGA_PROF_PRECOND 3    /* one whole preconditioner application (all mode products) */
 #define IGA_PROF_MASS_APPLY 4 /* one whole mass-operator application (all passes) */
+#define IGA_PROF_BAND_MASS 5  /* the band product of the assembled mass matrix */
+#define IGA_PROF_BAND_STIFF 6 /* the band product of the assembled stiffness matrix */
 
 typedef struct iga_handle iga_handle;
 

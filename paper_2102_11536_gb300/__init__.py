@@ -101,7 +101,7 @@ def exported_symbols():
             "iga_apply_Pinv_noalloc"]
 
 
-PROFILE_CLASSES = {"off": 0, "mass": 1, "stiff": 2, "precond": 3, "mass_apply": 4}
+PROFILE_CLASSES = {"off": 0, "mass": 1, "stiff": 2, "precond": 3, "mass_apply": 4, "band_mass": 5, "band_stiff": 6}
 
 
 def _ptr(t):

@@ -29,6 +29,10 @@ struct iga_handle {
   // assembled form
   double* Mband = nullptr;
   double* Kband = nullptr;
+  long long* band_off = nullptr;  // [H] linear offsets of the stored slots
+  int band_H = 0;
+  bool band_ready = false;
+  double band_nnz = 0.0;          // nonzero couplings (for algorithmic flop counts)
   // operator workspace
   int ws_vec = 0;
   double *u0 = nullptr, *u1 = nullptr, *ta = nullptr, *tb = nullptr, *tc = nullptr;
@@ -281,70 +285,127 @@ int apply_K_mf(iga_handle* h, int nvec, const int* active, const double* x, doub
   return IGA_OK;
 }
 
-int apply_Pinv_fd64(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
-  CKS(ensure_cg_ws(h, nvec));
+// The preconditioner of Sec. 5.3 by fast diagonalisation with scratch t1, t2
+// (nvec*N doubles each): t = S r (S = D^{-1/2} Dhat^{1/2}), then U^T along each
+// axis, division by Lambda_0(i0) Lambda_1(i1) Lambda_2(i2), U along each axis, S.
+// FP64 form: all in FP64. FP32 form: the scaled residual is rounded to FP32,
+// mode products and Lambda in FP32, final rescale in FP64.
+int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* t1, double* t2) {
   cudaStream_t s = h->stream;
   const int* n = h->n;
   const DirDev* d = h->dd;
-  double *t1 = h->f1, *t2 = h->f2;
-  FdEpilogue none{};
-  FdEpilogue lam{};
-  lam.lam[0] = d[0].lam64;
-  lam.lam[1] = d[1].lam64;
-  lam.lam[2] = h->dim == 3 ? d[2].lam64 : nullptr;
-  lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
-  FdEpilogue post{};
-  post.post = h->scale;
   const long long N = h->N;
-  if (h->dim == 3) {
-    const long long n01 = (long long)n[0] * n[1];
-    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n01 / n[0] * n[2]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
-    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
-    LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
-    LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
-    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
-  } else {
-    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, h->scale, none));
-    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
-    LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-    LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
+  const long long n01 = (long long)n[0] * n[1];
+  const long long n12 = (long long)n[1] * n[2];
+  const bool d3 = h->dim == 3;
+  if (h->opt.precond == IGA_PREC_FP64) {
+    FdEpilogue none{}, lam{}, post{};
+    lam.lam[0] = d[0].lam64;
+    lam.lam[1] = d[1].lam64;
+    lam.lam[2] = d3 ? d[2].lam64 : nullptr;
+    lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
+    post.post = h->scale;
+    LK(launch_scale(s, N, nvec, r, h->scale, t1, 0, N));
+    if (d3) {
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 1, t1, t2, N, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t2, t1, N, none));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t1, t2, N, lam));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t2, t1, N, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t1, t2, N, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 0, t2, z, N, post));
+    } else {
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, t1, t2, N, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t2, t1, N, lam));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t1, t2, N, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t2, z, N, post));
+    }
+    return IGA_OK;
   }
+  if (h->opt.precond == IGA_PREC_FP32) {
+    float* f1 = reinterpret_cast<float*>(t1);
+    float* f2 = reinterpret_cast<float*>(t2);
+    const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
+    LK(launch_scale(s, N, nvec, r, h->scale, f1, 1, N));
+    if (d3) {
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, f1, 0, f2, 0, N, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 0, f2, 0, z, 1, N, h->scale, nullptr, n));
+    } else {
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, f2, 0, f1, 0, N, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, f2, 0, z, 1, N, h->scale, nullptr, n));
+    }
+    return IGA_OK;
+  }
+  return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
+}
+
+// Assembled band rows of M and K by probing the matrix-free operators with the
+// (2p+1)^d colour vectors, 8 colours per application (kernels_band.cu).
+int assemble_band(iga_handle* h) {
+  if (h->band_ready) return IGA_OK;
+  cudaStream_t s = h->stream;
+  int p3[3] = {0, 0, 0};
+  for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
+  int S = 1;
+  for (int a = 0; a < 3; ++a) S *= 2 * p3[a] + 1;
+  const int centre = S / 2, H = S - centre;
+  std::vector<long long> off(H);
+  for (int hh = 0; hh < H; ++hh) {
+    const int sl = centre + hh;
+    const int m0 = 2 * p3[0] + 1, m1 = 2 * p3[1] + 1;
+    const int o0 = sl % m0 - p3[0], o1 = (sl / m0) % m1 - p3[1], o2 = sl / (m0 * m1) - p3[2];
+    off[hh] = o0 + (long long)h->n[0] * (o1 + (long long)h->n[1] * o2);
+  }
+  double nnz = 1.0;
+  for (int a = 0; a < 3; ++a) nnz *= (double)h->n[a] * (2 * p3[a] + 1) - (double)p3[a] * (p3[a] + 1);
+  CKS(upload(h, &h->band_off, off));
+  CKS(dalloc(h, &h->Mband, (size_t)H * h->N));
+  CKS(dalloc(h, &h->Kband, (size_t)H * h->N));
+  CK(cudaMemsetAsync(h->Mband, 0, sizeof(double) * H * h->N, s));
+  CK(cudaMemsetAsync(h->Kband, 0, sizeof(double) * H * h->N, s));
+  constexpr int kBatch = 8;
+  CKS(ensure_cg_ws(h, kBatch));
+  for (int first = 0; first < S; first += kBatch) {
+    const int nv = std::min(kBatch, S - first);
+    LK(launch_probe_gen(s, h->N, h->n, p3, first, S, nv, h->r, h->N));
+    CKS(apply_M_mf(h, nv, nullptr, h->r, h->z));
+    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, h->z, h->N, h->Mband));
+    CKS(apply_K_mf(h, nv, nullptr, h->r, h->z));
+    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, h->z, h->N, h->Kband));
+  }
+  CK(cudaStreamSynchronize(s));
+  h->band_H = H;
+  h->band_nnz = nnz;
+  h->band_ready = true;
   return IGA_OK;
 }
 
-// FP32 form: the same six mode products in FP32 on the CUDA cores, FP32
-// intermediates (stored in the FP64 scratch buffers), FP64 input and output.
-int apply_Pinv_fd32(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
-  CKS(ensure_cg_ws(h, nvec));
-  cudaStream_t s = h->stream;
-  const int* n = h->n;
-  const DirDev* d = h->dd;
-  float* t1 = reinterpret_cast<float*>(h->f1);
-  float* t2 = reinterpret_cast<float*>(h->f2);
-  const float* lam[3] = {d[0].lam32, d[1].lam32, h->dim == 3 ? d[2].lam32 : nullptr};
-  const long long N = h->N;
-  if (h->dim == 3) {
-    const long long n01 = (long long)n[0] * n[1];
-    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U32, 1, r, 1, t1, 0, N, h->scale, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, t1, 0, t2, 0, N, nullptr, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, t2, 0, t1, 0, N, nullptr, nullptr, lam, n));
-    LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, t1, 0, t2, 0, N, nullptr, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, t2, 0, t1, 0, N, nullptr, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], (long long)n[1] * n[2]}, nvec, active, d[0].U32, 0, t1, 0, z, 1, N, nullptr, h->scale, nullptr, n));
-  } else {
-    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, r, 1, t1, 0, N, h->scale, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, t1, 0, t2, 0, N, nullptr, nullptr, lam, n));
-    LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, t2, 0, t1, 0, N, nullptr, nullptr, nullptr, n));
-    LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, t1, 0, z, 1, N, nullptr, h->scale, nullptr, n));
-  }
+int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* active, const double* x, double* y) {
+  const int nact = active ? h->cur_active : nvec;
+  cudaEvent_t e = nullptr;
+  CKS(prof_begin(h, cls, &e));
+  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, A, active, nvec, x, y, h->N));
+  CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
 
 int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  if (h->opt.op_form == IGA_OP_ASSEMBLED) {
+    CKS(assemble_band(h));
+    return apply_band(h, h->Mband, IGA_PROF_BAND_MASS, nvec, active, x, y);
+  }
   return apply_M_mf(h, nvec, active, x, y);
 }
 int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  if (h->opt.op_form == IGA_OP_ASSEMBLED) {
+    CKS(assemble_band(h));
+    return apply_band(h, h->Kband, IGA_PROF_BAND_STIFF, nvec, active, x, y);
+  }
   return apply_K_mf(h, nvec, active, x, y);
 }
 int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
@@ -353,11 +414,8 @@ int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, doub
   for (int a = 0; a < h->dim; ++a) modes += h->n[a];
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, IGA_PROF_PRECOND, &e));
-  switch (h->opt.precond) {
-    case IGA_PREC_FP64: CKS(apply_Pinv_fd64(h, nvec, active, r, z)); break;
-    case IGA_PREC_FP32: CKS(apply_Pinv_fd32(h, nvec, active, r, z)); break;
-    default: return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
-  }
+  CKS(ensure_cg_ws(h, nvec));
+  CKS(fd_apply(h, nvec, active, r, z, h->f1, h->f2));
   CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
   return IGA_OK;
 }
@@ -471,54 +529,7 @@ int handle_device(iga_handle* h, int* device) {
 int handle_fail(iga_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
 
 int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2) {
-  cudaStream_t s = h->stream;
-  const int* n = h->n;
-  const DirDev* d = h->dd;
-  const long long N = h->N;
-  const long long n01 = (long long)n[0] * n[1];
-  const long long n12 = (long long)n[1] * n[2];
-  if (h->opt.precond == IGA_PREC_FP64) {
-    FdEpilogue none{}, lam{}, post{};
-    lam.lam[0] = d[0].lam64;
-    lam.lam[1] = d[1].lam64;
-    lam.lam[2] = h->dim == 3 ? d[2].lam64 : nullptr;
-    lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
-    post.post = h->scale;
-    if (h->dim == 3) {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U64, 1, x, t1, N, h->scale, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U64, 1, t1, t2, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U64, 1, t2, t1, N, nullptr, lam));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U64, 0, t1, t2, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U64, 0, t2, t1, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U64, 0, t1, y, N, nullptr, post));
-    } else {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U64, 1, x, t1, N, h->scale, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U64, 1, t1, t2, N, nullptr, lam));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U64, 0, t2, t1, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U64, 0, t1, y, N, nullptr, post));
-    }
-    return IGA_OK;
-  }
-  if (h->opt.precond == IGA_PREC_FP32) {
-    float* f1 = reinterpret_cast<float*>(t1);
-    float* f2 = reinterpret_cast<float*>(t2);
-    const float* lam[3] = {d[0].lam32, d[1].lam32, h->dim == 3 ? d[2].lam32 : nullptr};
-    if (h->dim == 3) {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U32, 1, x, 1, f1, 0, N, h->scale, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, nullptr, d[2].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, nullptr, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, nullptr, d[0].U32, 0, f1, 0, y, 1, N, nullptr, h->scale, nullptr, n));
-    } else {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U32, 1, x, 1, f1, 0, N, h->scale, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, nullptr, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, nullptr, d[0].U32, 0, f1, 0, y, 1, N, nullptr, h->scale, nullptr, n));
-    }
-    return IGA_OK;
-  }
-  return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
+  return fd_apply(h, nvec, nullptr, x, y, t1, t2);
 }
 
 }  // namespace iga
@@ -566,7 +577,7 @@ void iga_destroy(iga_handle* h) {
     dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32);
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
-  dfree(h->Mband); dfree(h->Kband);
+  dfree(h->Mband); dfree(h->Kband); dfree(h->band_off);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial);
@@ -626,9 +637,12 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
       std::vector<double> sq(t.val.size());
       for (size_t i = 0; i < sq.size(); ++i) sq[i] = t.val[i] * t.val[i];
       std::vector<float> v32(t.val.begin(), t.val.end()), d32(t.der.begin(), t.der.end());
-      std::vector<double> U((size_t)t.n * t.n);
+      // [U | U^T], both column-major: element (i, j) of the applied matrix at j*n + i
+      const size_t nn = (size_t)t.n * t.n;
+      std::vector<double> U(2 * nn);
       for (int i = 0; i < t.n; ++i)
         for (int c = 0; c < t.n; ++c) U[(size_t)c * t.n + i] = t.evec[(size_t)i * t.n + c];
+      for (size_t e = 0; e < nn; ++e) U[nn + e] = t.evec[e];
       std::vector<float> U32(U.begin(), U.end()), l32(t.eval.begin(), t.eval.end());
       CKS(upload(h, &d.val, t.val)); CKS(upload(h, &d.der, t.der)); CKS(upload(h, &d.sq, sq));
       CKS(upload(h, &d.val32, v32)); CKS(upload(h, &d.der32, d32));
@@ -728,7 +742,7 @@ int iga_set_tol(iga_handle* h, double tol, int max_iter) {
 
 int iga_assemble(iga_handle* h) {
   CKS(check_handle(h));
-  return fail(h, IGA_EINVAL, "assembled operator form not available in this build");
+  return assemble_band(h);
 }
 
 int iga_apply_M(iga_handle* h, int nvec, const double* x, double* y) {
@@ -854,7 +868,7 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
 
 int iga_profile(iga_handle* h, int kernel_class) {
   CKS(check_handle(h));
-  if (kernel_class < IGA_PROF_OFF || kernel_class > IGA_PROF_MASS_APPLY) return fail(h, IGA_EINVAL, "bad kernel class");
+  if (kernel_class < IGA_PROF_OFF || kernel_class > IGA_PROF_BAND_STIFF) return fail(h, IGA_EINVAL, "bad kernel class");
   h->prof_class = kernel_class;
   return IGA_OK;
 }

@@ -55,7 +55,7 @@ struct DirDev {
   int* flo;       // [n]
   int* fhi;       // [n]
   double* qw;     // [Q]
-  double* U64;    // [n][n] column-major copy of the eigenvectors: element (i, c) at c*n + i
+  double* U64;    // [2][n][n]: U then U^T, each column-major (element (i, j) at j*n + i)
   double* lam64;  // [n]
   float* U32;
   float* lam32;
@@ -97,20 +97,21 @@ cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const i
                             double* W, double* G, long long gstride, int* bad);
 
 // Fast-diagonalisation mode product along one axis: out[x,i,y] = sum_j Mat(i,j) in[x,j,y]
-// with Mat(i,j) = U[j*n+i] (transpose=0: U) or U[i*n+j] (transpose=1: U^T),
-// optional prologue scale (in * pre[idx]) and epilogue (Lambda^{-1} or post scale).
+// with Mat = U (transpose=0) or U^T (transpose=1), U holding [U | U^T] column-major,
+// and an optional epilogue (Lambda^{-1} or post scale).
 struct FdEpilogue {
   const double* post;            // multiply output by post[idx] (nullable)
   const double* lam[3];          // divide by lam0[i0] lam1[i1] lam2[i2] (nullable)
   int n[3];
 };
 cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const double* U,
-                             int transpose, const double* in, double* out, long long vs, const double* pre,
-                             FdEpilogue ep);
+                             int transpose, const double* in, double* out, long long vs, FdEpilogue ep);
 cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
                              int transpose, const void* in, int in_is_double, void* out, int out_is_double,
-                             long long vs, const double* pre, const double* post, const float* const* lam,
-                             const int* nn);
+                             long long vs, const double* post, const float* const* lam, const int* nn);
+// out = scale .* in, elementwise per vector (FP64 product, FP64 or FP32 result)
+cudaError_t launch_scale(cudaStream_t s, long long N, int nvec, const double* in, const double* scale, void* out,
+                         int out_is_float, long long vs);
 
 // Vector kernels (kernels_vec.cu)
 constexpr int kRedBlocks = 296;  // fixed reduction grid (2 x 148 .. deterministic order)
@@ -164,6 +165,15 @@ cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, 
 // Z <- 2 Z - Z2, Z2 <- old Z
 cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
+
+// Assembled band form (kernels_band.cu): H stored slots (centre + upper half),
+// off[h] the linear offset of slot h, A [H][N].
+cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
+                             const int* active, int nvec, const double* x, double* y, long long vs);
+cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
+                             double* x, long long vs);
+cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,
+                                 int nvec, const double* y, long long vs, double* A);
 
 // Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
 constexpr long long kNoAllocMaxElems = 1LL << 20;

@@ -1,0 +1,152 @@
+// Assembled band form of the isogeometric mass and stiffness matrices.
+//
+// Storage: the symmetric band is kept as its centre and upper half. With
+// S = prod_a (2 p_a + 1) offsets o = (o0, o1, o2), |o_a| <= p_a, in co-lexicographic
+// slot order, slot S-1-s holds -o(s); the stored slots are h = 0 (the diagonal,
+// slot S/2) and h = 1..H-1 (slots S/2 + h). A[h][i] = A_{i, i+o} (zero where i+o
+// leaves the interior), structure of arrays [H][N] so that a warp of consecutive
+// rows reads consecutive words.
+//
+// Product: y_i = A[0][i] x_i + sum_h ( A[h][i] x_{i+L_h} + A[h][i-L_h] x_{i-L_h} ),
+// L_h the linear offset of o(h). The second term is the lower half by symmetry.
+// Where i +- L_h wraps around an edge of the grid the stored coefficient is zero,
+// so only the array bounds are checked.
+//
+// Assembly by probing: for a colour c in prod_a [0, 2 p_a + 1), the probe vector
+// is 1 at the dofs with i_a = c_a (mod 2 p_a + 1) for all a, else 0. Row i of
+// A x_c is then the single coefficient A_{i,j} whose column j = i + o has that
+// colour (o_a = c_a - i_a mod 2 p_a + 1 folded into [-p_a, p_a]). Every band
+// entry is recovered exactly from the operator's own Gauss quadrature.
+#include "iga_internal.h"
+
+namespace iga {
+
+template <int NV>
+__global__ void __launch_bounds__(256) k_band_spmv(long long N, int H, const long long* __restrict__ off,
+                                                   const double* __restrict__ A, const int* __restrict__ active,
+                                                   int nvec, const double* __restrict__ x, double* __restrict__ y,
+                                                   long long vs) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  // up to NV vectors per thread share every coefficient load
+  const int v0 = blockIdx.y * NV;
+  bool on[NV];
+  double acc[NV];
+  const double a0 = A[i];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int vv = v0 + v;
+    on[v] = vv < nvec && (!active || active[vv]);
+    acc[v] = on[v] ? a0 * x[vv * vs + i] : 0.0;
+  }
+  for (int h = 1; h < H; ++h) {
+    const long long L = off[h];
+    const long long jp = i + L, jm = i - L;
+    const double* Ah = A + (long long)h * N;
+    if (jp >= 0 && jp < N) {
+      const double a = Ah[i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (on[v]) acc[v] = fma(a, x[(v0 + v) * vs + jp], acc[v]);
+    }
+    if (jm >= 0 && jm < N) {
+      const double a = Ah[jm];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (on[v]) acc[v] = fma(a, x[(v0 + v) * vs + jm], acc[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    if (on[v]) y[(v0 + v) * vs + i] = acc[v];
+}
+
+struct BandGeom {
+  int n[3];
+  int p[3];
+  int m[3];     // 2p+1 per direction
+  int centre;   // S / 2
+};
+
+__device__ __forceinline__ void idx3(long long i, const BandGeom& g, int* ia) {
+  ia[0] = (int)(i % g.n[0]);
+  ia[1] = (int)((i / g.n[0]) % g.n[1]);
+  ia[2] = (int)(i / ((long long)g.n[0] * g.n[1]));
+}
+
+// probe vectors for colours first..first+nvec-1 (colour index co-lex over m[0], m[1], m[2])
+__global__ void k_probe_gen(long long N, BandGeom g, int first, int ncol, double* __restrict__ x, long long vs) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (i >= N) return;
+  int ia[3];
+  idx3(i, g, ia);
+  const int c = first + v;
+  const int c0 = c % g.m[0], c1 = (c / g.m[0]) % g.m[1], c2 = c / (g.m[0] * g.m[1]);
+  const bool hit = c < ncol && ia[0] % g.m[0] == c0 && ia[1] % g.m[1] == c1 && ia[2] % g.m[2] == c2;
+  x[v * vs + i] = hit ? 1.0 : 0.0;
+}
+
+__global__ void k_probe_extract(long long N, BandGeom g, int first, int ncol, const double* __restrict__ y,
+                                long long vs, double* __restrict__ A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  const int c = first + v;
+  if (i >= N || c >= ncol) return;
+  int ia[3];
+  idx3(i, g, ia);
+  const int cc[3] = {c % g.m[0], (c / g.m[0]) % g.m[1], c / (g.m[0] * g.m[1])};
+  int o[3];
+  for (int a = 0; a < 3; ++a) {
+    int r = (cc[a] - ia[a] % g.m[a] + g.m[a]) % g.m[a];  // o_a mod (2p+1)
+    if (r > g.p[a]) r -= g.m[a];
+    o[a] = r;
+    const int j = ia[a] + r;
+    if (j < 0 || j >= g.n[a]) return;  // neighbour outside the interior: coefficient stays 0
+  }
+  const int slot = (o[0] + g.p[0]) + g.m[0] * ((o[1] + g.p[1]) + g.m[1] * (o[2] + g.p[2]));
+  if (slot < g.centre) return;  // lower half: taken from the symmetric partner
+  A[(long long)(slot - g.centre) * N + i] = y[v * vs + i];
+}
+
+static BandGeom make_geom(const int* n, const int* p) {
+  BandGeom g;
+  int S = 1;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = n[a];
+    g.p[a] = p[a];
+    g.m[a] = 2 * p[a] + 1;
+    S *= g.m[a];
+  }
+  g.centre = S / 2;
+  return g;
+}
+
+cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
+                             const int* active, int nvec, const double* x, double* y, long long vs) {
+  const unsigned bx = (unsigned)((N + 255) / 256);
+  if (nvec <= 1) {
+    k_band_spmv<1><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
+  } else if (nvec == 2) {
+    k_band_spmv<2><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
+  } else if (nvec == 3) {
+    k_band_spmv<3><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
+  } else {
+    k_band_spmv<4><<<dim3(bx, (unsigned)((nvec + 3) / 4)), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
+                             double* x, long long vs) {
+  k_probe_gen<<<dim3((unsigned)((N + 255) / 256), nvec), 256, 0, s>>>(N, make_geom(n, p), first, ncol, x, vs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,
+                                 int nvec, const double* y, long long vs, double* A) {
+  k_probe_extract<<<dim3((unsigned)((N + 255) / 256), nvec), 256, 0, s>>>(N, make_geom(n, p), first, ncol, y, vs, A);
+  return cudaGetLastError();
+}
+
+}  // namespace iga

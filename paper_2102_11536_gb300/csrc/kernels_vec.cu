@@ -45,28 +45,43 @@ cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, c
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ double sum_partials(const double* p) {
-  double s = 0.0;
-  for (int b = 0; b < kRedBlocks; ++b) s += p[b];
-  return s;
+// Warp w of a 256-thread block sums vector w's kRedBlocks partials (lane stride 32,
+// then a shuffle tree): a fixed order, so the result is reproducible, and 32
+// lanes instead of one serial FP64 chain.
+__device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < nvec) {
+    double s = 0.0;
+    for (int b = lane; b < kRedBlocks; b += 32) s += partial[w * kRedBlocks + b];
+    s = warp_sum(s);
+    if (lane == 0) out[w] = s;
+  }
+  __syncthreads();
 }
 
-__global__ void k_reduce(int nvec, const double* partial, double* result) {
+constexpr int kEpiThreads = 32 * kMaxVec;
+
+__global__ void __launch_bounds__(kEpiThreads) k_reduce(int nvec, const double* partial, double* result) {
+  __shared__ double sa[kMaxVec];
+  reduce_partials(nvec, partial, sa);
   const int v = threadIdx.x;
-  if (v < nvec) result[v] = sum_partials(partial + v * kRedBlocks);
+  if (v < nvec) result[v] = sa[v];
 }
 
 cudaError_t launch_reduce(cudaStream_t s, int nvec, const double* partial, double* result) {
-  k_reduce<<<1, 32, 0, s>>>(nvec, partial, result);
+  k_reduce<<<1, kEpiThreads, 0, s>>>(nvec, partial, result);
   return cudaGetLastError();
 }
 
 // b.b and r.r at the start; a system is active while ||r|| > tol ||b|| and b != 0.
-__global__ void k_cg_init(int nvec, const double* pbb, const double* prr, CgScalars c, double tol2) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_init(int nvec, const double* pbb, const double* prr, CgScalars c,
+                                                         double tol2) {
+  __shared__ double sb[kMaxVec], sr[kMaxVec];
+  reduce_partials(nvec, pbb, sb);
+  reduce_partials(nvec, prr, sr);
   const int v = threadIdx.x;
   if (v < nvec) {
-    const double bb = sum_partials(pbb + v * kRedBlocks);
-    const double rr = sum_partials(prr + v * kRedBlocks);
+    const double bb = sb[v], rr = sr[v];
     c.bb[v] = bb;
     c.rr[v] = rr;
     c.iters[v] = 0;
@@ -88,29 +103,33 @@ __global__ void k_cg_init(int nvec, const double* pbb, const double* prr, CgScal
 
 cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, const double* partial_rr,
                            CgScalars c, double tol2) {
-  k_cg_init<<<1, 32, 0, s>>>(nvec, partial_bb, partial_rr, c, tol2);
+  k_cg_init<<<1, kEpiThreads, 0, s>>>(nvec, partial_bb, partial_rr, c, tol2);
   return cudaGetLastError();
 }
 
-__global__ void k_cg_start(int nvec, const double* prz, CgScalars c) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_start(int nvec, const double* prz, CgScalars c) {
+  __shared__ double sz[kMaxVec];
+  reduce_partials(nvec, prz, sz);
   const int v = threadIdx.x;
-  if (v < nvec) c.rz[v] = sum_partials(prz + v * kRedBlocks);
+  if (v < nvec) c.rz[v] = sz[v];
 }
 
 cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, CgScalars c) {
-  k_cg_start<<<1, 32, 0, s>>>(nvec, partial_rz, c);
+  k_cg_start<<<1, kEpiThreads, 0, s>>>(nvec, partial_rz, c);
   return cudaGetLastError();
 }
 
 // alpha = r.z / p.q; breakdown (p.q <= 0 or not finite) stops the system with IGA_ENUMERIC.
-__global__ void k_cg_alpha(int nvec, const double* ppq, CgScalars c) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double* ppq, CgScalars c) {
+  __shared__ double sq[kMaxVec];
+  reduce_partials(nvec, ppq, sq);
   const int v = threadIdx.x;
   if (v >= nvec) return;
   if (!c.active[v]) {
     c.alpha[v] = 0.0;
     return;
   }
-  const double pq = sum_partials(ppq + v * kRedBlocks);
+  const double pq = sq[v];
   if (!(pq > 0.0) || !isfinite(pq)) {
     c.status[v] = IGA_ENUMERIC;
     c.active[v] = 0;
@@ -121,15 +140,17 @@ __global__ void k_cg_alpha(int nvec, const double* ppq, CgScalars c) {
 }
 
 cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, CgScalars c) {
-  k_cg_alpha<<<1, 32, 0, s>>>(nvec, partial, c);
+  k_cg_alpha<<<1, kEpiThreads, 0, s>>>(nvec, partial, c);
   return cudaGetLastError();
 }
 
 // After x/r update: count the iteration, test ||r||^2 <= tol^2 ||b||^2.
-__global__ void k_cg_check(int nvec, const double* prr, CgScalars c, double tol2) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_check(int nvec, const double* prr, CgScalars c, double tol2) {
+  __shared__ double sr[kMaxVec];
+  reduce_partials(nvec, prr, sr);
   const int v = threadIdx.x;
   if (v < nvec && c.active[v]) {
-    const double rr = sum_partials(prr + v * kRedBlocks);
+    const double rr = sr[v];
     c.rr[v] = rr;
     c.iters[v] += 1;
     if (!isfinite(rr)) {
@@ -148,25 +169,29 @@ __global__ void k_cg_check(int nvec, const double* prr, CgScalars c, double tol2
 }
 
 cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgScalars c, double tol2) {
-  k_cg_check<<<1, 32, 0, s>>>(nvec, partial, c, tol2);
+  k_cg_check<<<1, kEpiThreads, 0, s>>>(nvec, partial, c, tol2);
   return cudaGetLastError();
 }
 
 // beta = r.z_new / r.z_old (plain CG) or (r.z_new - r.z_prev) / r.z_old (flexible,
 // Polak-Ribiere form for a preconditioner that is not exactly linear).
-__global__ void k_cg_beta(int nvec, const double* prz, const double* prz2, CgScalars c, int flexible) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_beta(int nvec, const double* prz, const double* prz2, CgScalars c,
+                                                         int flexible) {
+  __shared__ double sz[kMaxVec], sz2[kMaxVec];
+  reduce_partials(nvec, prz, sz);
+  if (flexible) reduce_partials(nvec, prz2, sz2);
   const int v = threadIdx.x;
   if (v >= nvec || !c.active[v]) return;
-  const double rz_new = sum_partials(prz + v * kRedBlocks);
+  const double rz_new = sz[v];
   double num = rz_new;
-  if (flexible) num -= sum_partials(prz2 + v * kRedBlocks);
+  if (flexible) num -= sz2[v];
   c.beta[v] = num / c.rz[v];
   c.rz[v] = rz_new;
 }
 
 cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, CgScalars c,
                            int flexible) {
-  k_cg_beta<<<1, 32, 0, s>>>(nvec, partial, partial2, c, flexible);
+  k_cg_beta<<<1, kEpiThreads, 0, s>>>(nvec, partial, partial2, c, flexible);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,28 @@ def test_operators_match_oracle(case):
         assert _maxrel(Y[v], ops.apply_Pinv(X[v])) < 1e-12
 
 
+def test_assembled_operators_match_oracle(case):
+    """The assembled band form (probed from the matrix-free operators) against the
+    oracle's Gauss-quadrature band rows."""
+    w, ops, g = case
+    g.set_op_form("assembled")
+    try:
+        N = ops.N
+        X = np.random.default_rng(8).standard_normal((3, N))
+        x = _t(X)
+        y = torch.empty_like(x)
+        g.apply_M(x, y, 3)
+        Y = _np(y).reshape(3, N)
+        for v in range(3):
+            assert _maxrel(Y[v], ops.apply_M(X[v])) < 1e-12
+        g.apply_K(x, y, 3)
+        Y = _np(y).reshape(3, N)
+        for v in range(3):
+            assert _maxrel(Y[v], ops.apply_K(X[v])) < 1e-11
+    finally:
+        g.set_op_form("matrix_free")
+
+
 def test_pcg_matches_oracle(case):
     w, ops, g = case
     N = ops.N
@@ -118,9 +140,9 @@ def _oracle_run(w, ops, steps, dt, tol, guess="zero"):
     return X, st.iters
 
 
-def _gpu_run(w, steps, dt, tol, guess="zero", precond="fp64"):
+def _gpu_run(w, steps, dt, tol, guess="zero", precond="fp64", op_form="matrix_free"):
     U0, V0 = w.initial()
-    g = _gpu(w, tol=tol, guess=guess, precond=precond)
+    g = _gpu(w, tol=tol, guess=guess, precond=precond, op_form=op_form)
     state = torch.zeros(3 * w.k * g.N, dtype=torch.float64, device=DEV)
     g.state_init(w.k, _t(U0), _t(V0), state)
     st = g.step(state, w.k, w.rho, dt, steps)
@@ -147,6 +169,19 @@ def test_step_matches_oracle(k, rho):
     for row in (0, 1):
         err = np.linalg.norm(Xg[row] - Xo[row]) / np.linalg.norm(Xo[row])
         assert err < 1e-10, (row, err)
+
+
+@pytest.mark.parametrize("precond", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [2, 3])
+def test_assembled_step_matches_oracle(k, precond):
+    w = W.small(d=3, nel=(5, 4, 6), p=3, amp=0.1, k=k, rho=0.5, init="random")
+    ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+    dt = _dt(ops, w.rho)
+    Xo, _ = _oracle_run(w, ops, 10, dt, 1e-12)
+    Xg, _ = _gpu_run(w, 10, dt, 1e-12, precond=precond, op_form="assembled")
+    for row in (0, 1):
+        err = np.linalg.norm(Xg[row] - Xo[row]) / np.linalg.norm(Xo[row])
+        assert err < 1e-9, (row, err)
 
 
 @pytest.mark.parametrize("guess", ["prev", "extrap", "taylor"])
