@@ -305,19 +305,19 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     lam.lam[2] = d3 ? d[2].lam64 : nullptr;
     lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
     post.post = h->scale;
-    LK(launch_scale(s, N, nvec, r, h->scale, t1, 0, N));
+    const double* sc = h->scale;
     if (d3) {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 1, t1, t2, N, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t2, t1, N, none));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t1, t2, N, lam));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t2, t1, N, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t1, t2, N, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 0, t2, z, N, post));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 1, r, t1, N, sc, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
+      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
     } else {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, t1, t2, N, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t2, t1, N, lam));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t1, t2, N, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t2, z, N, post));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, sc, none));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
+      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
+      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
     }
     return IGA_OK;
   }
@@ -325,19 +325,19 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     float* f1 = reinterpret_cast<float*>(t1);
     float* f2 = reinterpret_cast<float*>(t2);
     const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
-    LK(launch_scale(s, N, nvec, r, h->scale, f1, 1, N));
+    const double* sc = h->scale;
     if (d3) {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, f1, 0, f2, 0, N, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 0, f2, 0, z, 1, N, h->scale, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 1, r, 1, f1, 0, N, sc, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 0, f1, 0, z, 1, N, nullptr, sc, nullptr, n));
     } else {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, f2, 0, f1, 0, N, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, f2, 0, z, 1, N, h->scale, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, r, 1, f1, 0, N, sc, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, lam, n));
+      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
+      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, f1, 0, z, 1, N, nullptr, sc, nullptr, n));
     }
     return IGA_OK;
   }
@@ -637,12 +637,15 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
       std::vector<double> sq(t.val.size());
       for (size_t i = 0; i < sq.size(); ++i) sq[i] = t.val[i] * t.val[i];
       std::vector<float> v32(t.val.begin(), t.val.end()), d32(t.der.begin(), t.der.end());
-      // [U | U^T], both column-major: element (i, j) of the applied matrix at j*n + i
-      const size_t nn = (size_t)t.n * t.n;
-      std::vector<double> U(2 * nn);
+      // [U | U^T]: element (i, j) of the applied matrix at j*np + i, rows padded to np
+      const int np = (t.n + 7) & ~7;
+      const size_t blk = (size_t)t.n * np;
+      std::vector<double> U(2 * blk, 0.0);
       for (int i = 0; i < t.n; ++i)
-        for (int c = 0; c < t.n; ++c) U[(size_t)c * t.n + i] = t.evec[(size_t)i * t.n + c];
-      for (size_t e = 0; e < nn; ++e) U[nn + e] = t.evec[e];
+        for (int j = 0; j < t.n; ++j) {
+          U[(size_t)j * np + i] = t.evec[(size_t)i * t.n + j];        // U(i, j)
+          U[blk + (size_t)j * np + i] = t.evec[(size_t)j * t.n + i];  // U^T(i, j) = U(j, i)
+        }
       std::vector<float> U32(U.begin(), U.end()), l32(t.eval.begin(), t.eval.end());
       CKS(upload(h, &d.val, t.val)); CKS(upload(h, &d.der, t.der)); CKS(upload(h, &d.sq, sq));
       CKS(upload(h, &d.val32, v32)); CKS(upload(h, &d.der32, d32));

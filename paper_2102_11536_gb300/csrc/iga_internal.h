@@ -55,7 +55,7 @@ struct DirDev {
   int* flo;       // [n]
   int* fhi;       // [n]
   double* qw;     // [Q]
-  double* U64;    // [2][n][n]: U then U^T, each column-major (element (i, j) at j*n + i)
+  double* U64;    // [2][n][np]: U then U^T, element (i, j) at j*np + i, np = n rounded up to 8
   double* lam64;  // [n]
   float* U32;
   float* lam32;
@@ -104,14 +104,15 @@ struct FdEpilogue {
   const double* lam[3];          // divide by lam0[i0] lam1[i1] lam2[i2] (nullable)
   int n[3];
 };
+// (kernels_fd.cu) U holds [U | U^T], each Mat(i, j) at j*np + i, np = n rounded up
+// to 8; pre (axis 0 only, nullable) multiplies the inputs in FP64 before rounding.
 cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const double* U,
-                             int transpose, const double* in, double* out, long long vs, FdEpilogue ep);
+                             int transpose, const double* in, double* out, long long vs, const double* pre,
+                             FdEpilogue ep);
 cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
                              int transpose, const void* in, int in_is_double, void* out, int out_is_double,
-                             long long vs, const double* post, const float* const* lam, const int* nn);
-// out = scale .* in, elementwise per vector (FP64 product, FP64 or FP32 result)
-cudaError_t launch_scale(cudaStream_t s, long long N, int nvec, const double* in, const double* scale, void* out,
-                         int out_is_float, long long vs);
+                             long long vs, const double* pre, const double* post, const float* const* lam,
+                             const int* nn);
 
 // Vector kernels (kernels_vec.cu)
 constexpr int kRedBlocks = 296;  // fixed reduction grid (2 x 148 .. deterministic order)

@@ -389,87 +389,6 @@ __global__ void k_geometry(GeoDir g0, GeoDir g1, GeoDir g2, const double* __rest
 }
 
 // ----------------------------------------------------------------------------
-// FP64 fast-diagonalisation mode product (one axis). U holds [U | U^T], each
-// column-major, so the applied matrix's element (i, j) sits at j*n + i: a warp
-// reads consecutive entries (axis 0, consecutive i) or one broadcast entry.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_fd64(int n, int A, const int* __restrict__ active,
-                                              const double* __restrict__ U, int transpose,
-                                              const double* __restrict__ in, double* __restrict__ out, long long vs,
-                                              FdEpilogue ep) {
-  const int v = blockIdx.z;
-  if (active && !active[v]) return;
-  const int y = blockIdx.y;
-  const int flat = blockIdx.x * blockDim.x + threadIdx.x;
-  if (flat >= A * n) return;
-  const int i = flat / A;
-  const int x = flat - i * A;
-  const long long rowbase = (long long)y * n * A + x;
-  const double* src = in + v * vs + rowbase;
-  const double* Mc = U + (transpose ? (long long)n * n : 0LL) + i;
-  double acc = 0.0;
-  for (int j = 0; j < n; ++j) acc = fma(Mc[(long long)j * n], src[(long long)j * A], acc);
-  const long long idx = rowbase + (long long)i * A;
-  if (ep.lam[0]) {
-    const long long n01 = (long long)ep.n[0] * ep.n[1];
-    const int i0 = (int)(idx % ep.n[0]);
-    const int i1 = (int)((idx / ep.n[0]) % ep.n[1]);
-    const int i2 = (int)(idx / n01);
-    double l = ep.lam[0][i0] * ep.lam[1][i1];
-    if (ep.lam[2]) l *= ep.lam[2][i2];
-    acc /= l;
-  }
-  if (ep.post) acc *= ep.post[idx];
-  out[v * vs + idx] = acc;
-}
-
-// out = scale .* in (FP64 product, stored as FP64 or rounded to FP32)
-template <typename TO>
-__global__ void k_scale(long long N, const double* __restrict__ in, const double* __restrict__ scale,
-                        TO* __restrict__ out, long long vs) {
-  const int v = blockIdx.y;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    out[v * vs + i] = (TO)(in[v * vs + i] * scale[i]);
-}
-
-// ----------------------------------------------------------------------------
-// FP32 fast-diagonalisation mode product (CUDA cores): FP32 arithmetic and
-// factors ([U | U^T] column-major as for FP64), FP32 or FP64 in/out; the last
-// mode rescales in FP64.
-// ----------------------------------------------------------------------------
-template <typename TI, typename TO>
-__global__ void __launch_bounds__(256) k_fd32(int n, int A, const int* __restrict__ active, const float* __restrict__ U,
-                                              int transpose, const TI* __restrict__ in, TO* __restrict__ out,
-                                              long long vs, const double* __restrict__ post,
-                                              const float* __restrict__ lam0,
-                                              const float* __restrict__ lam1, const float* __restrict__ lam2, int n0,
-                                              int n1) {
-  const int v = blockIdx.z;
-  if (active && !active[v]) return;
-  const int y = blockIdx.y;
-  const int flat = blockIdx.x * blockDim.x + threadIdx.x;
-  if (flat >= A * n) return;
-  const int i = flat / A;
-  const int x = flat - i * A;
-  const long long rowbase = (long long)y * n * A + x;
-  const TI* src = in + v * vs + rowbase;
-  const float* Mc = U + (transpose ? (long long)n * n : 0LL) + i;
-  float acc = 0.0f;
-  for (int j = 0; j < n; ++j) acc = fmaf(Mc[(long long)j * n], (float)src[(long long)j * A], acc);
-  const long long idx = rowbase + (long long)i * A;
-  if (lam0) {
-    const int i0 = (int)(idx % n0);
-    const int i1 = (int)((idx / n0) % n1);
-    const int i2 = (int)(idx / ((long long)n0 * n1));
-    float l = lam0[i0] * lam1[i1];
-    if (lam2) l *= lam2[i2];
-    acc = acc / l;
-  }
-  if (post) out[v * vs + idx] = (TO)((double)acc * post[idx]);
-  else out[v * vs + idx] = (TO)acc;
-}
-
-// ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
 #define IGA_DISPATCH_P(P, ...)                              \
@@ -567,43 +486,6 @@ cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const i
     k_geometry<3><<<blocks, 256, 0, s>>>(g[0], g[1], g[2], ctrl_soa, ctrl_soa + mt, ctrl_soa + 2 * mt, W, G, gstride, bad);
   else
     k_geometry<2><<<blocks, 256, 0, s>>>(g[0], g[1], g[2], ctrl_soa, ctrl_soa + mt, nullptr, W, G, gstride, bad);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const double* U,
-                             int transpose, const double* in, double* out, long long vs, FdEpilogue ep) {
-  if (sh.B > 65535 || sh.A * n > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dim3 grid = plane_grid(sh.A * n, sh.B, nvec, 256);
-  k_fd64<<<grid, 256, 0, s>>>(n, (int)sh.A, active, U, transpose, in, out, vs, ep);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scale(cudaStream_t s, long long N, int nvec, const double* in, const double* scale, void* out,
-                         int out_is_float, long long vs) {
-  dim3 grid(kRedBlocks, nvec);
-  if (out_is_float) k_scale<float><<<grid, 256, 0, s>>>(N, in, scale, (float*)out, vs);
-  else k_scale<double><<<grid, 256, 0, s>>>(N, in, scale, (double*)out, vs);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
-                             int transpose, const void* in, int in_is_double, void* out, int out_is_double,
-                             long long vs, const double* post, const float* const* lam, const int* nn) {
-  if (sh.B > 65535 || sh.A * n > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dim3 grid = plane_grid(sh.A * n, sh.B, nvec, 256);
-  const float* l0 = lam ? lam[0] : nullptr;
-  const float* l1 = lam ? lam[1] : nullptr;
-  const float* l2 = lam ? lam[2] : nullptr;
-  const int n0 = nn ? nn[0] : 1, n1 = nn ? nn[1] : 1;
-  const int A = (int)sh.A;
-  if (in_is_double && !out_is_double)
-    k_fd32<double, float><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const double*)in, (float*)out, vs, post, l0, l1, l2, n0, n1);
-  else if (!in_is_double && !out_is_double)
-    k_fd32<float, float><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const float*)in, (float*)out, vs, post, l0, l1, l2, n0, n1);
-  else if (!in_is_double && out_is_double)
-    k_fd32<float, double><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const float*)in, (double*)out, vs, post, l0, l1, l2, n0, n1);
-  else
-    k_fd32<double, double><<<grid, 256, 0, s>>>(n, A, active, U, transpose, (const double*)in, (double*)out, vs, post, l0, l1, l2, n0, n1);
   return cudaGetLastError();
 }
 
