@@ -20,7 +20,7 @@
 namespace iga {
 
 constexpr int kFdR = 8;     // outputs per thread on strided axes
-constexpr int kFdRMax = 6;  // outputs per lane on axis 0: n <= 192
+constexpr int kFdRMax = 6;  // outputs per lane per output block on axis 0
 
 __host__ __device__ inline int fd_np(int n) { return (n + 7) & ~7; }
 
@@ -97,24 +97,26 @@ __global__ void __launch_bounds__(256) k_fd_axis0(FdArgs<TC> a, long long nlines
       line[j] = (TC)u;
     }
     __syncwarp();
-    TC acc[kFdRMax];
+    for (int ib = 0; ib < n; ib += 32 * kFdRMax) {  // blocks of 32 * kFdRMax outputs
+      TC acc[kFdRMax];
 #pragma unroll
-    for (int r = 0; r < kFdRMax; ++r) acc[r] = (TC)0;
-    for (int j = 0; j < n; ++j) {
-      const TC u = line[j];
-      const TC* mj = a.mat + (long long)j * a.np;
+      for (int r = 0; r < kFdRMax; ++r) acc[r] = (TC)0;
+      for (int j = 0; j < n; ++j) {
+        const TC u = line[j];
+        const TC* mj = a.mat + (long long)j * a.np + ib;
+#pragma unroll
+        for (int r = 0; r < kFdRMax; ++r) {
+          const int i = lane + 32 * r;
+          if (ib + i < n) acc[r] = fma(__ldg(mj + i), u, acc[r]);
+        }
+      }
 #pragma unroll
       for (int r = 0; r < kFdRMax; ++r) {
-        const int i = lane + 32 * r;
-        if (i < n) acc[r] = fma(__ldg(mj + i), u, acc[r]);
+        const int i = ib + lane + 32 * r;
+        if (i < n) fd_store(a, dst, base + i, acc[r]);
       }
     }
     __syncwarp();
-#pragma unroll
-    for (int r = 0; r < kFdRMax; ++r) {
-      const int i = lane + 32 * r;
-      if (i < n) fd_store(a, dst, base + i, acc[r]);
-    }
   }
 }
 
@@ -155,7 +157,6 @@ __global__ void __launch_bounds__(256) k_fd_axisN(FdArgs<TC> a, int A, const int
 template <typename TI, typename TC, typename TO>
 static cudaError_t fd_launch(cudaStream_t s, const FdArgs<TC>& a, AxisShape sh, int nvec, const int* active,
                              const TI* in, TO* out, long long vs) {
-  if (a.n > 32 * kFdRMax) return cudaErrorInvalidValue;
   if (sh.A == 1) {
     const long long nlines = sh.B;
     const int warps = 8;
