@@ -106,13 +106,22 @@ __global__ void __launch_bounds__(256) k_fd_lines(FdArgs<TC> a, const int* __res
 template <typename TI, typename TC, typename TO, int G, int R>
 static cudaError_t fd_run(cudaStream_t s, const FdArgs<TC>& a, int nvec, const int* active, const TI* in, TO* out,
                           long long vs) {
-  constexpr int threads = 256;
-  constexpr int groups = threads / G;
+  // lines per block: up to 256 threads, within 48 KB of line buffers (whole warps)
+  constexpr int per_warp = 32 / G;
+  const size_t line_bytes = sizeof(TC) * (size_t)a.np;
+  int groups = 256 / G;
+  while (groups > per_warp && groups * line_bytes > 48 * 1024) groups -= per_warp;
+  const size_t smem = groups * line_bytes;
+  if (smem > 48 * 1024) {  // one warp's lines exceed the default: raise the limit (up to 227 KB)
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_fd_lines<TI, TC, TO, G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   long long blocks = (a.nlines + groups - 1) / groups;
   const long long cap = 152LL * 16;  // at most 16 resident-size waves of blocks; the rest loop
   if (blocks > cap) blocks = cap;
-  const size_t smem = sizeof(TC) * (size_t)groups * a.np;
-  k_fd_lines<TI, TC, TO, G, R><<<dim3((unsigned)blocks, nvec), threads, smem, s>>>(a, active, in, out, vs);
+  k_fd_lines<TI, TC, TO, G, R><<<dim3((unsigned)blocks, nvec), groups * G, smem, s>>>(a, active, in, out, vs);
   return cudaGetLastError();
 }
 
