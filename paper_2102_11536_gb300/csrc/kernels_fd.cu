@@ -3,24 +3,32 @@
 // co-lexicographic tensor, Mat = U_a or U_a^T (U_a the orthonormal eigenvectors of
 // the univariate parametric mass matrix Mhat_a).
 //
+// Each mode product is the small GEMM Y (R x n) = X (R x n) Mat^T over the
+// R = N / n lines ("rows") of the tensor along the axis; row r is the line at
+// x = r mod A, y = r div A (A = stride of the axis), element j at x + A (j + n y).
+//
 // Matrix layout: [U | U^T], each stored as Mat(i, j) at j*np + i, np = n rounded
 // up to 8 (zero padding).
 //
-// One kernel for every axis. A line is the n values along the axis at fixed
-// (x, y); a group of G lanes (G = 8, 16 or 32, so 32/G lines per warp) gathers
-// its line into shared memory (for axis 0 a contiguous read; otherwise a
-// strided gather, served from L2 where the whole tensor of a preconditioner
-// application resides) and lane l of the group accumulates the outputs
-// i = l, l+G, l+2G, ... with coefficient reads Mat(l + G r, j) that are
-// contiguous within the group. Smaller G wastes fewer lanes when n is not a
-// multiple of 32 (what matters for FP64, whose pipe is 1/64 of FP32); G = 32
-// gives the fewest instructions per output (FP32).
-// Epilogue: optional division by Lambda_0(i0) Lambda_1(i1) Lambda_2(i2), optional
-// FP64 rescaling, conversion to the output type. An optional FP64 prologue
-// scaling multiplies the inputs before they are rounded to the compute type.
+// A block takes a tile of kTileRows consecutive rows: it first stages the whole
+// tile in shared memory with one wide, coalesced load (a contiguous block for
+// axis 0, and for the strided axes kTileRows consecutive rows of every j, which
+// are consecutive addresses), so the load latency is paid once per tile rather
+// than once per term; then thread (row t, group g) accumulates the np/8
+// consecutive outputs i = g np/8 ... of its row from shared memory, with the
+// coefficients Mat(i, j) being the same for the whole warp (broadcast loads).
+// Outputs of the strided axes are written directly (consecutive rows are
+// consecutive addresses); axis-0 outputs are staged back through shared memory
+// and written as one contiguous block. Epilogue: optional division by
+// Lambda_0(i0) Lambda_1(i1) Lambda_2(i2) and optional FP64 rescaling; an optional
+// FP64 prologue scaling multiplies the inputs before they are rounded.
 #include "iga_internal.h"
 
 namespace iga {
+
+constexpr int kTileRows = 32;   // rows per block (one warp-width)
+constexpr int kGroups = 8;      // output groups per row (warps per block)
+// outputs per thread per chunk (template kMaxRI): 9 for np <= 72, else 17 (chunks of 136 outputs)
 
 __host__ __device__ inline int fd_np(int n) { return (n + 7) & ~7; }
 
@@ -35,11 +43,11 @@ struct FdArgs {
   const TC* lam2;
   int n0, n1;           // tensor sizes for the index decomposition of the epilogue
   long long A;          // stride of the axis (product of the faster sizes)
-  long long nlines;     // A * B
+  long long R;          // rows = A * B
 };
 
-template <typename TC, typename TO>
-__device__ __forceinline__ void fd_store(const FdArgs<TC>& a, TO* out, long long idx, TC acc) {
+template <typename TC>
+__device__ __forceinline__ TC fd_lambda(const FdArgs<TC>& a, long long idx, TC acc) {
   if (a.lam0) {
     const int i0 = (int)(idx % a.n0);
     const int i1 = (int)((idx / a.n0) % a.n1);
@@ -48,111 +56,154 @@ __device__ __forceinline__ void fd_store(const FdArgs<TC>& a, TO* out, long long
     if (a.lam2) l *= a.lam2[i2];
     acc = acc / l;
   }
-  if (a.post) out[idx] = (TO)((double)acc * a.post[idx]);
-  else out[idx] = (TO)acc;
+  return acc;
 }
 
-// G lanes per line, R outputs per lane per output block (G * R outputs per block)
-template <typename TI, typename TC, typename TO, int G, int R>
-__global__ void __launch_bounds__(256) k_fd_lines(FdArgs<TC> a, const int* __restrict__ active,
-                                                  const TI* __restrict__ in, TO* __restrict__ out, long long vs) {
+template <typename TC, typename TO>
+__device__ __forceinline__ void fd_put(const FdArgs<TC>& a, TO* out, long long idx, TC val) {
+  if (a.post) out[idx] = (TO)((double)val * a.post[idx]);
+  else out[idx] = (TO)val;
+}
+
+template <typename TI, typename TC, typename TO, bool AXIS0, int kMaxRI>
+__global__ void __launch_bounds__(kTileRows* kGroups) k_fd_tile(FdArgs<TC> a, const int* __restrict__ active,
+                                                                const TI* __restrict__ in, TO* __restrict__ out,
+                                                                long long vs) {
   extern __shared__ unsigned char fd_smem[];
+  TC* Xs = reinterpret_cast<TC*>(fd_smem);  // [kTileRows][ld]
   const int v = blockIdx.y;
   if (active && !active[v]) return;
-  const int lane = threadIdx.x & (G - 1);
-  const int grp = threadIdx.x / G;  // line slot of this group within the block
-  const int ngrp = blockDim.x / G;
-  TC* line = reinterpret_cast<TC*>(fd_smem) + grp * a.np;
+  const int n = a.n, np = a.np, ld = np + 1;  // odd row stride: conflict-free column reads
+  const long long A = a.A;
+  const long long r0 = (long long)blockIdx.x * kTileRows;
+  const int rows = (int)min((long long)kTileRows, a.R - r0);
   const TI* src = in + v * vs;
   TO* dst = out + v * vs;
-  const int n = a.n;
-  const long long A = a.A;
-  for (long long L = (long long)blockIdx.x * ngrp + grp; L < a.nlines; L += (long long)gridDim.x * ngrp) {
-    // line L = x + A * y, element j at x + A * (j + n * y)
-    const long long y = L / A;
-    const long long x = L - y * A;
-    const long long base = x + A * n * y;
-    for (int j = lane; j < n; j += G) {
-      const long long idx = base + (long long)j * A;
-      double u = (double)src[idx];
-      if (a.pre) u *= a.pre[idx];
-      line[j] = (TC)u;
+  const int tid = threadIdx.x;
+  // ---- stage the tile
+  if (AXIS0) {
+    const long long base = r0 * n;
+    const int cnt = rows * n;
+    for (int f = tid; f < cnt; f += blockDim.x) {
+      const int rr = f / n, j = f - rr * n;
+      double u = (double)src[base + f];
+      if (a.pre) u *= a.pre[base + f];
+      Xs[rr * ld + j] = (TC)u;
     }
-    __syncwarp();
-    for (int ib = 0; ib < n; ib += G * R) {
-      TC acc[R];
+  } else {
+    for (int e = tid; e < kTileRows * n; e += blockDim.x) {
+      const int j = e / kTileRows, rr = e - j * kTileRows;
+      TC val = (TC)0;
+      if (rr < rows) {
+        const long long r = r0 + rr;
+        const long long y = r / A, x = r - y * A;
+        const long long idx = x + A * (j + (long long)n * y);
+        double u = (double)src[idx];
+        if (a.pre) u *= a.pre[idx];
+        val = (TC)u;
+      }
+      Xs[rr * ld + j] = val;
+    }
+  }
+  __syncthreads();
+  // ---- compute: thread (row t, group g)
+  const int t = tid % kTileRows;
+  const int g = tid / kTileRows;
+  const TC* xr = Xs + t * ld;
+  TC outv[kMaxRI];
+  for (int ic = 0; ic < np; ic += kGroups * kMaxRI) {
+    const int span = min(np - ic, kGroups * kMaxRI);  // multiple of 8
+    const int RI = span / kGroups;
+    const int i0 = ic + g * RI;
+    TC acc[kMaxRI];
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = (TC)0;
-#pragma unroll 4
-      for (int j = 0; j < n; ++j) {
-        const TC u = line[j];
-        const TC* mj = a.mat + (long long)j * a.np + ib + lane;
+    for (int b = 0; b < kMaxRI; ++b) acc[b] = (TC)0;
+#pragma unroll 2
+    for (int j = 0; j < n; ++j) {
+      const TC u = xr[j];
+      const TC* mj = a.mat + (long long)j * np + i0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (ib + G * r >= a.np) break;  // uniform across the warp: rounds past the padded row
-          if (ib + lane + G * r < a.np) acc[r] = fma(__ldg(mj + G * r), u, acc[r]);
+      for (int b = 0; b < kMaxRI; ++b)
+        if (b < RI) acc[b] = fma(__ldg(mj + b), u, acc[b]);
+    }
+    if (AXIS0) {
+      // keep the results (after Lambda) to stage through shared memory
+#pragma unroll
+      for (int b = 0; b < kMaxRI; ++b)
+        if (b < RI) outv[b] = fd_lambda(a, (r0 + t) * n + i0 + b, acc[b]);
+      __syncthreads();  // every thread has finished reading Xs
+#pragma unroll
+      for (int b = 0; b < kMaxRI; ++b)
+        if (b < RI && i0 + b < n && t < rows) Xs[t * ld + i0 + b] = outv[b];
+      __syncthreads();
+      const long long base = r0 * n;
+      for (int f = tid; f < rows * n; f += blockDim.x) {
+        const int rr = f / n, i = f - rr * n;
+        if (i >= ic && i < ic + span) fd_put(a, dst, base + f, Xs[rr * ld + i]);
+      }
+      __syncthreads();
+      if (ic + kGroups * kMaxRI < np) {
+        // a further chunk needs the input tile again: restage it
+        for (int f = tid; f < rows * n; f += blockDim.x) {
+          const int rr = f / n, j = f - rr * n;
+          double u = (double)src[base + f];
+          if (a.pre) u *= a.pre[base + f];
+          Xs[rr * ld + j] = (TC)u;
+        }
+        __syncthreads();
+      }
+    } else {
+      if (t < rows) {
+        const long long r = r0 + t;
+        const long long y = r / A, x = r - y * A;
+#pragma unroll
+        for (int b = 0; b < kMaxRI; ++b) {
+          const int i = i0 + b;
+          if (b < RI && i < n) {
+            const long long idx = x + A * (i + (long long)n * y);
+            fd_put(a, dst, idx, fd_lambda(a, idx, acc[b]));
+          }
         }
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = ib + lane + G * r;
-        if (i < n) fd_store(a, dst, base + (long long)i * A, acc[r]);
-      }
     }
-    __syncwarp();
   }
 }
 
-template <typename TI, typename TC, typename TO, int G, int R>
-static cudaError_t fd_run(cudaStream_t s, const FdArgs<TC>& a, int nvec, const int* active, const TI* in, TO* out,
-                          long long vs) {
-  // lines per block: up to 256 threads, within 48 KB of line buffers (whole warps)
-  constexpr int per_warp = 32 / G;
-  const size_t line_bytes = sizeof(TC) * (size_t)a.np;
-  int groups = 256 / G;
-  while (groups > per_warp && groups * line_bytes > 48 * 1024) groups -= per_warp;
-  const size_t smem = groups * line_bytes;
-  if (smem > 48 * 1024) {  // one warp's lines exceed the default: raise the limit (up to 227 KB)
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_fd_lines<TI, TC, TO, G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename TI, typename TC, typename TO, bool AX0, int RI>
+static cudaError_t fd_go(cudaStream_t s, const FdArgs<TC>& a, int nvec, const int* active, const TI* in, TO* out,
+                         long long vs, size_t smem, dim3 grid) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fd_tile<TI, TC, TO, AX0, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  long long blocks = (a.nlines + groups - 1) / groups;
-  const long long cap = 152LL * 16;  // at most 16 resident-size waves of blocks; the rest loop
-  if (blocks > cap) blocks = cap;
-  k_fd_lines<TI, TC, TO, G, R><<<dim3((unsigned)blocks, nvec), groups * G, smem, s>>>(a, active, in, out, vs);
+  k_fd_tile<TI, TC, TO, AX0, RI><<<grid, kTileRows * kGroups, smem, s>>>(a, active, in, out, vs);
   return cudaGetLastError();
 }
 
-// FP64: the lane group that wastes the fewest FP64 slots on the last output block
-template <typename TI, typename TO>
-static cudaError_t fd_launch64(cudaStream_t s, const FdArgs<double>& a, int nvec, const int* active, const TI* in,
-                               TO* out, long long vs) {
-  auto waste = [&](int G) { return (G - a.n % G) % G; };
-  int best = 8;
-  if (waste(16) < waste(best)) best = 16;
-  if (waste(32) < waste(best)) best = 32;
-  if (best == 32) return fd_run<TI, double, TO, 32, 4>(s, a, nvec, active, in, out, vs);
-  if (best == 16) return fd_run<TI, double, TO, 16, 8>(s, a, nvec, active, in, out, vs);
-  return fd_run<TI, double, TO, 8, 16>(s, a, nvec, active, in, out, vs);
-}
-
-static FdArgs<double> args64(int n, AxisShape sh, const double* U, int transpose) {
-  FdArgs<double> a{};
-  a.n = n;
-  a.np = fd_np(n);
-  a.mat = U + (transpose ? (long long)n * a.np : 0LL);
-  a.A = sh.A;
-  a.nlines = sh.A * sh.B;
-  a.n0 = a.n1 = 1;
-  return a;
+template <typename TI, typename TC, typename TO>
+static cudaError_t fd_launch(cudaStream_t s, const FdArgs<TC>& a, int nvec, const int* active, const TI* in, TO* out,
+                             long long vs) {
+  const size_t smem = sizeof(TC) * (size_t)kTileRows * (a.np + 1);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const long long blocks = (a.R + kTileRows - 1) / kTileRows;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)blocks, nvec);
+  const bool small = a.np <= kGroups * 9;
+  if (a.A == 1)
+    return small ? fd_go<TI, TC, TO, true, 9>(s, a, nvec, active, in, out, vs, smem, grid)
+                 : fd_go<TI, TC, TO, true, 17>(s, a, nvec, active, in, out, vs, smem, grid);
+  return small ? fd_go<TI, TC, TO, false, 9>(s, a, nvec, active, in, out, vs, smem, grid)
+               : fd_go<TI, TC, TO, false, 17>(s, a, nvec, active, in, out, vs, smem, grid);
 }
 
 cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const double* U,
                              int transpose, const double* in, double* out, long long vs, const double* pre,
                              FdEpilogue ep) {
-  FdArgs<double> a = args64(n, sh, U, transpose);
+  FdArgs<double> a{};
+  a.n = n;
+  a.np = fd_np(n);
+  a.mat = U + (transpose ? (long long)n * a.np : 0LL);
   a.pre = pre;
   a.post = ep.post;
   a.lam0 = ep.lam[0];
@@ -160,7 +211,9 @@ cudaError_t launch_fd_mode64(cudaStream_t s, int n, AxisShape sh, int nvec, cons
   a.lam2 = ep.lam[2];
   a.n0 = ep.n[0] > 0 ? ep.n[0] : 1;
   a.n1 = ep.n[1] > 0 ? ep.n[1] : 1;
-  return fd_launch64<double, double>(s, a, nvec, active, in, out, vs);
+  a.A = sh.A;
+  a.R = sh.A * sh.B;
+  return fd_launch<double, double, double>(s, a, nvec, active, in, out, vs);
 }
 
 cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const float* U,
@@ -179,14 +232,14 @@ cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, cons
   a.n0 = nn ? nn[0] : 1;
   a.n1 = nn ? nn[1] : 1;
   a.A = sh.A;
-  a.nlines = sh.A * sh.B;
+  a.R = sh.A * sh.B;
   if (in_is_double && !out_is_double)
-    return fd_run<double, float, float, 32, 4>(s, a, nvec, active, (const double*)in, (float*)out, vs);
+    return fd_launch<double, float, float>(s, a, nvec, active, (const double*)in, (float*)out, vs);
   if (!in_is_double && !out_is_double)
-    return fd_run<float, float, float, 32, 4>(s, a, nvec, active, (const float*)in, (float*)out, vs);
+    return fd_launch<float, float, float>(s, a, nvec, active, (const float*)in, (float*)out, vs);
   if (!in_is_double && out_is_double)
-    return fd_run<float, float, double, 32, 4>(s, a, nvec, active, (const float*)in, (double*)out, vs);
-  return fd_run<double, float, double, 32, 4>(s, a, nvec, active, (const double*)in, (double*)out, vs);
+    return fd_launch<float, float, double>(s, a, nvec, active, (const float*)in, (double*)out, vs);
+  return fd_launch<double, float, double>(s, a, nvec, active, (const double*)in, (double*)out, vs);
 }
 
 }  // namespace iga
