@@ -646,12 +646,15 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
           U[(size_t)j * np + i] = t.evec[(size_t)i * t.n + j];        // U(i, j)
           U[blk + (size_t)j * np + i] = t.evec[(size_t)j * t.n + i];  // U^T(i, j) = U(j, i)
         }
-      std::vector<float> U32(U.begin(), U.end()), l32(t.eval.begin(), t.eval.end());
+      // inverse eigenvalues 1/Lambda_a (the epilogue multiplies)
+      std::vector<double> linv(t.n);
+      for (int i = 0; i < t.n; ++i) linv[i] = 1.0 / t.eval[i];
+      std::vector<float> U32(U.begin(), U.end()), l32(linv.begin(), linv.end());
       CKS(upload(h, &d.val, t.val)); CKS(upload(h, &d.der, t.der)); CKS(upload(h, &d.sq, sq));
       CKS(upload(h, &d.val32, v32)); CKS(upload(h, &d.der32, d32));
       CKS(upload(h, &d.qfirst, t.qfirst)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
       CKS(upload(h, &d.qw, t.qw));
-      CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, t.eval));
+      CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, linv));
       CKS(upload(h, &d.U32, U32)); CKS(upload(h, &d.lam32, l32));
     }
     // control net, point-major -> SoA

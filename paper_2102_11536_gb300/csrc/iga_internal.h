@@ -56,7 +56,7 @@ struct DirDev {
   int* fhi;       // [n]
   double* qw;     // [Q]
   double* U64;    // [2][n][np]: U then U^T, element (i, j) at j*np + i, np = n rounded up to 8
-  double* lam64;  // [n]
+  double* lam64;  // [n] inverse eigenvalues 1 / Lambda_a of Mhat_a
   float* U32;
   float* lam32;
 };
@@ -101,7 +101,7 @@ cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const i
 // and an optional epilogue (Lambda^{-1} or post scale).
 struct FdEpilogue {
   const double* post;            // multiply output by post[idx] (nullable)
-  const double* lam[3];          // divide by lam0[i0] lam1[i1] lam2[i2] (nullable)
+  const double* lam[3];          // multiply by lam0[i0] lam1[i1] lam2[i2], the inverse eigenvalues (nullable)
   int n[3];
 };
 // (kernels_fd.cu) U holds [U | U^T], each Mat(i, j) at j*np + i, np = n rounded up

@@ -26,8 +26,9 @@
 
 namespace iga {
 
-constexpr int kTileRows = 32;   // rows per block (one warp-width)
-constexpr int kGroups = 8;      // output groups per row (warps per block)
+constexpr int kTileRows = 16;   // rows per block
+constexpr int kGroups = 8;      // output groups per row (128 threads per block)
+constexpr int kStage = 8;       // staged loads in flight per thread
 // outputs per thread per chunk (template kMaxRI): 9 for np <= 72, else 17 (chunks of 136 outputs)
 
 __host__ __device__ inline int fd_np(int n) { return (n + 7) & ~7; }
@@ -38,7 +39,7 @@ struct FdArgs {
   const TC* mat;        // the applied matrix, Mat(i, j) at j*np + i
   const double* pre;    // multiply inputs by pre[idx] in FP64 before rounding (nullable)
   const double* post;   // multiply outputs by post[idx] (nullable)
-  const TC* lam0;       // divide by lam0[i0] lam1[i1] lam2[i2] (nullable)
+  const TC* lam0;       // multiply by lam0[i0] lam1[i1] lam2[i2], inverse eigenvalues (nullable)
   const TC* lam1;
   const TC* lam2;
   int n0, n1;           // tensor sizes for the index decomposition of the epilogue
@@ -52,9 +53,9 @@ __device__ __forceinline__ TC fd_lambda(const FdArgs<TC>& a, long long idx, TC a
     const int i0 = (int)(idx % a.n0);
     const int i1 = (int)((idx / a.n0) % a.n1);
     const int i2 = (int)(idx / ((long long)a.n0 * a.n1));
-    TC l = a.lam0[i0] * a.lam1[i1];
+    TC l = a.lam0[i0] * a.lam1[i1];  // inverse eigenvalues
     if (a.lam2) l *= a.lam2[i2];
-    acc = acc / l;
+    acc = acc * l;
   }
   return acc;
 }
@@ -80,29 +81,52 @@ __global__ void __launch_bounds__(kTileRows* kGroups) k_fd_tile(FdArgs<TC> a, co
   const TI* src = in + v * vs;
   TO* dst = out + v * vs;
   const int tid = threadIdx.x;
-  // ---- stage the tile
+  // ---- stage the tile: kStage independent loads per thread in flight, then the stores
   if (AXIS0) {
     const long long base = r0 * n;
     const int cnt = rows * n;
-    for (int f = tid; f < cnt; f += blockDim.x) {
-      const int rr = f / n, j = f - rr * n;
-      double u = (double)src[base + f];
-      if (a.pre) u *= a.pre[base + f];
-      Xs[rr * ld + j] = (TC)u;
+    for (int f0 = 0; f0 < cnt; f0 += kStage * blockDim.x) {
+      double u[kStage];
+#pragma unroll
+      for (int k = 0; k < kStage; ++k) {
+        const int f = f0 + k * blockDim.x + tid;
+        u[k] = f < cnt ? (double)src[base + f] : 0.0;
+        if (a.pre && f < cnt) u[k] *= a.pre[base + f];
+      }
+#pragma unroll
+      for (int k = 0; k < kStage; ++k) {
+        const int f = f0 + k * blockDim.x + tid;
+        if (f < cnt) {
+          const int rr = f / n, j = f - rr * n;
+          Xs[rr * ld + j] = (TC)u[k];
+        }
+      }
     }
   } else {
-    for (int e = tid; e < kTileRows * n; e += blockDim.x) {
-      const int j = e / kTileRows, rr = e - j * kTileRows;
-      TC val = (TC)0;
-      if (rr < rows) {
-        const long long r = r0 + rr;
-        const long long y = r / A, x = r - y * A;
-        const long long idx = x + A * (j + (long long)n * y);
-        double u = (double)src[idx];
-        if (a.pre) u *= a.pre[idx];
-        val = (TC)u;
+    const int cnt = kTileRows * n;
+    for (int e0 = 0; e0 < cnt; e0 += kStage * blockDim.x) {
+      double u[kStage];
+#pragma unroll
+      for (int k = 0; k < kStage; ++k) {
+        const int e = e0 + k * blockDim.x + tid;
+        const int j = e / kTileRows, rr = e - j * kTileRows;
+        u[k] = 0.0;
+        if (e < cnt && rr < rows) {
+          const long long r = r0 + rr;
+          const long long y = r / A, x = r - y * A;
+          const long long idx = x + A * (j + (long long)n * y);
+          u[k] = (double)src[idx];
+          if (a.pre) u[k] *= a.pre[idx];
+        }
       }
-      Xs[rr * ld + j] = val;
+#pragma unroll
+      for (int k = 0; k < kStage; ++k) {
+        const int e = e0 + k * blockDim.x + tid;
+        if (e < cnt) {
+          const int j = e / kTileRows, rr = e - j * kTileRows;
+          Xs[rr * ld + j] = (TC)u[k];
+        }
+      }
     }
   }
   __syncthreads();
