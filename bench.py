@@ -349,6 +349,11 @@ def run_ours(args):
         return
 
     h = results[head]
+    try:
+        probe_tf, probe_ghz = iga.fp64_fma_probe(local_rank)
+    except Exception:
+        probe_tf, probe_ghz = None, None
+    h["roofline"]["fp64_fma_probe_tflops"] = probe_tf
     result = {
         "metric": METRIC,
         "value": h["value"],

@@ -251,6 +251,15 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
 int iga_profile(iga_handle* h, int kernel_class);
 int iga_profile_read(iga_handle* h, double* total_ms, long long* launches, double* flops, double* bytes);
 
+/*
+ * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in
+ * the paper; measurement aid): 8 independent FMA chains per thread, 4 blocks of 256
+ * threads per SM, 2^14 iterations, averaged over 5 timed launches after 2
+ * warm-up launches. tflops (host) receives the rate; sm_clock_ghz (host, may be
+ * NULL) the device's nominal maximum SM clock. Allocates and frees a small buffer.
+ */
+int iga_probe_fp64_fma(int device, double* tflops, double* sm_clock_ghz);
+
 #ifdef __cplusplus
 }
 #endif

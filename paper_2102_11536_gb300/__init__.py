@@ -82,6 +82,7 @@ def lib():
         "iga_step_host": (ctypes.c_int, [H, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(Stats)]),
         "iga_profile": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_probe_fp64_fma": (ctypes.c_int, [ctypes.c_int, dp, dp]),
         "iga_profile_read": (ctypes.c_int, [H, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
     }
     for name, (res, args) in sig.items():
@@ -98,7 +99,17 @@ def exported_symbols():
             "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
             "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
             "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read",
-            "iga_apply_Pinv_noalloc"]
+            "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma"]
+
+
+def fp64_fma_probe(device=0):
+    """(TFLOP/s, nominal max SM clock GHz) of the FP64 FMA-chain probe on `device`."""
+    tf = ctypes.c_double()
+    ghz = ctypes.c_double()
+    rc = lib().iga_probe_fp64_fma(device, ctypes.byref(tf), ctypes.byref(ghz))
+    if rc != OK:
+        raise IgaError(rc, "iga_probe_fp64_fma")
+    return tf.value, ghz.value
 
 
 PROFILE_CLASSES = {"off": 0, "mass": 1, "stiff": 2, "precond": 3, "mass_apply": 4, "band_mass": 5, "band_stiff": 6}
