@@ -341,7 +341,45 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     }
     return IGA_OK;
   }
+  if (h->opt.precond == IGA_PREC_BF16) {
+    // the same sequence on the tensor cores: BF16 operands, FP32 accumulation and intermediates
+    for (int a = 0; a < h->dim; ++a)
+      if (!d[a].Btc[0])
+        return fail(h, IGA_EINVAL, "BF16 preconditioner needs at most 256 interior functions per direction");
+    float* f1 = reinterpret_cast<float*>(t1);
+    float* f2 = reinterpret_cast<float*>(t2);
+    const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
+    const double* sc = h->scale;
+    int* err = h->dflag + 1;
+    if (d3) {
+      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].Btc[1], r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].Btc[1], f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].Btc[1], f2, 0, f1, 0, N, nullptr, nullptr, lam, n, err));
+      LK(launch_fd_mode_tc(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].Btc[0], f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].Btc[0], f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].Btc[0], f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
+    } else {
+      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].Btc[1], r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].Btc[1], f1, 0, f2, 0, N, nullptr, nullptr, lam, n, err));
+      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].Btc[0], f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].Btc[0], f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
+    }
+    return IGA_OK;
+  }
   return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
+}
+
+// The tensor-core kernels set dflag[1] when an mbarrier wait runs out.
+int check_tc_error(iga_handle* h) {
+  if (h->opt.precond != IGA_PREC_BF16) return IGA_OK;
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e) {
+    CK(cudaMemsetAsync(h->dflag + 1, 0, sizeof(int), h->stream));
+    return fail(h, IGA_ECUDA, "tensor-core mode product: mbarrier wait timed out");
+  }
+  return IGA_OK;
 }
 
 // Assembled band rows of M and K by probing the matrix-free operators with the
@@ -488,6 +526,7 @@ int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int*
     if (relres) relres[v] = rel;
     if (hst[v] != 0) status = IGA_ENUMERIC;
   }
+  CKS(check_tc_error(h));
   if (status != IGA_OK) return fail(h, status, "PCG breakdown (non-positive curvature or non-finite values)");
   if (nact > 0) {
     char buf[160];
@@ -575,6 +614,8 @@ void iga_destroy(iga_handle* h) {
     dfree(d.val); dfree(d.der); dfree(d.sq); dfree(d.val32); dfree(d.der32);
     dfree(d.qfirst); dfree(d.flo); dfree(d.fhi); dfree(d.qw);
     dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32);
+    for (int t = 0; t < 2; ++t)
+      if (d.Btc[t]) { cudaFree(d.Btc[t]); d.Btc[t] = nullptr; }
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off);
@@ -655,6 +696,23 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
       CKS(upload(h, &d.qfirst, t.qfirst)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
       CKS(upload(h, &d.qw, t.qw));
       CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, linv));
+      if (tc_pad(t.n) <= 256) {  // BF16 tensor-core operands: Mat = U and Mat = U^T, (i, j) row-major
+        std::vector<double> Mu((size_t)t.n * t.n), Mt((size_t)t.n * t.n);
+        for (int i = 0; i < t.n; ++i)
+          for (int j = 0; j < t.n; ++j) {
+            Mu[(size_t)i * t.n + j] = t.evec[(size_t)i * t.n + j];
+            Mt[(size_t)i * t.n + j] = t.evec[(size_t)j * t.n + i];
+          }
+        std::vector<uint16_t> bits;
+        tc_arrange_bf16(t.n, Mu.data(), bits);
+        uint16_t* p0 = nullptr;
+        CKS(upload(h, &p0, bits));
+        d.Btc[0] = p0;
+        tc_arrange_bf16(t.n, Mt.data(), bits);
+        uint16_t* p1 = nullptr;
+        CKS(upload(h, &p1, bits));
+        d.Btc[1] = p1;
+      }
       CKS(upload(h, &d.U32, U32)); CKS(upload(h, &d.lam32, l32));
     }
     // control net, point-major -> SoA
@@ -766,7 +824,8 @@ int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y) {
 int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y) {
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
-  return apply_Pinv(h, nvec, nullptr, x, y);
+  CKS(apply_Pinv(h, nvec, nullptr, x, y));
+  return check_tc_error(h);
 }
 
 int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0, int* iters, double* relres) {

@@ -59,6 +59,7 @@ struct DirDev {
   double* lam64;  // [n] inverse eigenvalues 1 / Lambda_a of Mhat_a
   float* U32;
   float* lam32;
+  void* Btc[2];   // BF16 U and U^T in the tensor-core operand layout (kernels_tc.cu)
 };
 
 // ---------------------------------------------------------------------------
@@ -166,6 +167,16 @@ cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, 
 // Z <- 2 Z - Z2, Z2 <- old Z
 cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
+
+// BF16 tensor-core mode product (kernels_tc.cu): B is the BF16 matrix arranged by
+// tc_arrange_bf16; err (device int) is set to 1 if an mbarrier wait times out.
+cudaError_t launch_fd_mode_tc(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const void* B,
+                              const void* in, int in_is_double, void* out, int out_is_double, long long vs,
+                              const double* pre, const double* post, const float* const* lam, const int* nn,
+                              int* err);
+int tc_pad(int n);
+// Mat(i, j) row-major n x n (i output, j summed) -> BF16 bits in the K-major core-matrix layout
+void tc_arrange_bf16(int n, const double* Mat_ij, std::vector<uint16_t>& outbits);
 
 // Assembled band form (kernels_band.cu): H stored slots (centre + upper half),
 // off[h] the linear offset of slot h, A [H][N].

@@ -257,35 +257,58 @@ def test_max_iter_reports_not_converged():
     g.close()
 
 
-@pytest.mark.parametrize("name", ["3d_mixed_p", "3d_ragged_p3", "2d_square32_p2"])
-def test_fp32_preconditioner_close_to_oracle(name):
-    """FP32 mode products: norm-wise relative error of P^{-1} r at FP32 level (<= 1e-5)."""
+# FP32 mode products: FP32 rounding; BF16 (tensor cores): 8-bit mantissa operands,
+# FP32 accumulation over six mode products -> about 1e-2 norm-wise.
+PRECOND_TOL = {"fp32": 1e-5, "bf16": 5e-2}
+
+
+@pytest.mark.parametrize("precond", ["fp32", "bf16"])
+@pytest.mark.parametrize("name", ["3d_mixed_p", "3d_ragged_p3", "2d_square32_p2", "3d_p4"])
+def test_low_precision_preconditioner_close_to_oracle(name, precond):
+    """Norm-wise relative error of P^{-1} r against the FP64 oracle at the arithmetic's level."""
     w = OPERATOR_CASES[name]
     pre = oracle.Preconditioner(oracle.Patch(w.p, w.knots, w.ctrl()))
-    g = _gpu(w, precond="fp32")
+    g = _gpu(w, precond=precond)
     X = np.random.default_rng(2).standard_normal((2, pre.N))
     y = torch.empty(2 * pre.N, dtype=torch.float64, device=DEV)
     g.apply_Pinv(_t(X), y, 2)
     Y = _np(y).reshape(2, pre.N)
     for v in range(2):
         ref = pre.apply_Pinv(X[v])
-        assert np.linalg.norm(Y[v] - ref) / np.linalg.norm(ref) < 1e-5
+        err = np.linalg.norm(Y[v] - ref) / np.linalg.norm(ref)
+        assert err < PRECOND_TOL[precond], err
     g.close()
 
 
+def test_bf16_preconditioner_cube64():
+    """The tensor-core form at full size (n = 65 per direction, 34 row tiles per mode)."""
+    w = W.config("cube64_p3")
+    P = oracle.Patch(w.p, w.knots, w.ctrl())
+    pre = oracle.Preconditioner(P)
+    g = _gpu(w, precond="bf16")
+    X = np.random.default_rng(6).standard_normal(P.N)
+    y = torch.empty(P.N, dtype=torch.float64, device=DEV)
+    g.apply_Pinv(_t(X), y)
+    ref = pre.apply_Pinv(X)
+    assert np.linalg.norm(_np(y) - ref) / np.linalg.norm(ref) < PRECOND_TOL["bf16"]
+    g.close()
+
+
+@pytest.mark.parametrize("precond", ["fp32", "bf16"])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_step_with_fp32_preconditioner_matches_fp64_oracle(k):
-    """Flexible PCG with the FP32 preconditioner reaches the same FP64 tolerance, so the
-    trajectory matches the FP64 oracle to the solver tolerance."""
+def test_step_with_low_precision_preconditioner_matches_fp64_oracle(k, precond):
+    """Flexible PCG with an FP32 or BF16 preconditioner reaches the same FP64 tolerance, so
+    the trajectory matches the FP64 oracle to the solver tolerance."""
     w = W.small(d=3, nel=(5, 4, 6), p=3, amp=0.1, k=k, rho=0.5, init="random")
     ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
     dt = _dt(ops, w.rho)
     Xo, it_o = _oracle_run(w, ops, 10, dt, 1e-12)
-    Xg, st = _gpu_run(w, 10, dt, 1e-12, precond="fp32")
+    Xg, st = _gpu_run(w, 10, dt, 1e-12, precond=precond)
     for row in (0, 1):
         err = np.linalg.norm(Xg[row] - Xo[row]) / np.linalg.norm(Xo[row])
         assert err < 1e-9, (row, err)
-    assert st.iters <= sum(sum(i) for i in it_o) + 2 * st.solves  # at most 2 extra iterations per solve
+    extra = 2 if precond == "fp32" else 6
+    assert st.iters <= sum(sum(i) for i in it_o) + extra * st.solves
 
 
 def test_cube64_sampled_rows_and_preconditioner():
