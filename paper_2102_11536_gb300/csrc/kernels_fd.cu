@@ -193,6 +193,95 @@ __global__ void __launch_bounds__(kTileRows* kGroups) k_fd_tile(FdArgs<TC> a, co
   }
 }
 
+// FP32 variant with one output per thread: the whole matrix (n x np floats) and a
+// tile of TR = 512 / np rows live in shared memory; thread (t, i) forms
+// sum_j X(t, j) Mat(i, j) from a broadcast (X) and a conflict-free (Mat) read.
+// Many resident warps hide the latency that limits the register-tiled form when
+// there are only a few thousand rows.
+template <typename TI, typename TO, bool AXIS0>
+__global__ void __launch_bounds__(512) k_fd_smem32(FdArgs<float> a, int TR, const int* __restrict__ active,
+                                                   const TI* __restrict__ in, TO* __restrict__ out, long long vs) {
+  extern __shared__ __align__(16) float fsm[];
+  const int v = blockIdx.y;
+  if (active && !active[v]) return;
+  const int n = a.n, np = a.np, ldx = n + 1;
+  float* Ms = fsm;             // Mat(i, j) at j*np + i
+  float* Xs = fsm + n * np;    // [TR][n+1]
+  const long long A = a.A;
+  const long long r0 = (long long)blockIdx.x * TR;
+  const int rows = (int)min((long long)TR, a.R - r0);
+  const TI* src = in + v * vs;
+  TO* dst = out + v * vs;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  {
+    const float4* m4 = reinterpret_cast<const float4*>(a.mat);
+    float4* s4 = reinterpret_cast<float4*>(Ms);
+    for (int e = tid; e < n * np / 4; e += nt) s4[e] = __ldg(m4 + e);
+  }
+  if (AXIS0) {
+    const long long base = r0 * n;
+    for (int f = tid; f < rows * n; f += nt) {
+      const int rr = f / n, j = f - rr * n;
+      double u = (double)src[base + f];
+      if (a.pre) u *= a.pre[base + f];
+      Xs[rr * ldx + j] = (float)u;
+    }
+  } else {
+    for (int e = tid; e < rows * n; e += nt) {
+      const int j = e / rows, rr = e - j * rows;
+      const long long r = r0 + rr;
+      const long long y = r / A, x = r - y * A;
+      const long long idx = x + A * (j + (long long)n * y);
+      double u = (double)src[idx];
+      if (a.pre) u *= a.pre[idx];
+      Xs[rr * ldx + j] = (float)u;
+    }
+  }
+  __syncthreads();
+  const int t = tid / np, i = tid - t * np;
+  if (t >= rows || i >= n) return;
+  const float* xr = Xs + t * ldx;
+  float acc = 0.0f;
+#pragma unroll 8
+  for (int j = 0; j < n; ++j) acc = fmaf(xr[j], Ms[j * np + i], acc);
+  const long long r = r0 + t;
+  long long idx;
+  if (AXIS0) {
+    idx = r * n + i;
+  } else {
+    const long long y = r / A, x = r - y * A;
+    idx = x + A * (i + (long long)n * y);
+  }
+  fd_put(a, dst, idx, fd_lambda(a, idx, acc));
+}
+
+template <typename TI, typename TO>
+static bool fd_smem32(cudaStream_t s, const FdArgs<float>& a, int nvec, const int* active, const TI* in, TO* out,
+                      long long vs, cudaError_t* err) {
+  if (a.np > 512) return false;
+  const int TR = 512 / a.np;
+  const size_t smem = sizeof(float) * ((size_t)a.n * a.np + (size_t)TR * (a.n + 1));
+  if (smem > 160 * 1024) return false;
+  const long long blocks = (a.R + TR - 1) / TR;
+  const dim3 grid((unsigned)blocks, nvec);
+  const int threads = ((TR * a.np + 31) / 32) * 32;
+  if (a.A == 1) {
+    if (smem > 48 * 1024 &&
+        (*err = cudaFuncSetAttribute(k_fd_smem32<TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem)) != cudaSuccess)
+      return true;
+    k_fd_smem32<TI, TO, true><<<grid, threads, smem, s>>>(a, TR, active, in, out, vs);
+  } else {
+    if (smem > 48 * 1024 &&
+        (*err = cudaFuncSetAttribute(k_fd_smem32<TI, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem)) != cudaSuccess)
+      return true;
+    k_fd_smem32<TI, TO, false><<<grid, threads, smem, s>>>(a, TR, active, in, out, vs);
+  }
+  *err = cudaGetLastError();
+  return true;
+}
+
 template <typename TI, typename TC, typename TO, bool AX0, int RI>
 static cudaError_t fd_go(cudaStream_t s, const FdArgs<TC>& a, int nvec, const int* active, const TI* in, TO* out,
                          long long vs, size_t smem, dim3 grid) {
@@ -257,6 +346,16 @@ cudaError_t launch_fd_mode32(cudaStream_t s, int n, AxisShape sh, int nvec, cons
   a.n1 = nn ? nn[1] : 1;
   a.A = sh.A;
   a.R = sh.A * sh.B;
+  cudaError_t e = cudaSuccess;
+  if (in_is_double && !out_is_double) {
+    if (fd_smem32(s, a, nvec, active, (const double*)in, (float*)out, vs, &e)) return e;
+  } else if (!in_is_double && !out_is_double) {
+    if (fd_smem32(s, a, nvec, active, (const float*)in, (float*)out, vs, &e)) return e;
+  } else if (!in_is_double && out_is_double) {
+    if (fd_smem32(s, a, nvec, active, (const float*)in, (double*)out, vs, &e)) return e;
+  } else {
+    if (fd_smem32(s, a, nvec, active, (const double*)in, (double*)out, vs, &e)) return e;
+  }
   if (in_is_double && !out_is_double)
     return fd_launch<double, float, float>(s, a, nvec, active, (const double*)in, (float*)out, vs);
   if (!in_is_double && !out_is_double)
