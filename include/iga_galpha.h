@@ -142,6 +142,18 @@ int iga_set_guess(iga_handle* h, int guess);
 int iga_set_tol(iga_handle* h, double tol, int max_iter);
 
 /*
+ * iga_set_graphs -- on (default) lets iga_step replay one captured CUDA graph per
+ * time step, whose PCG loop runs on the device (a conditional while node tests
+ * convergence after every iteration): no host synchronisation inside a step. The
+ * graph is captured on the first step of a configuration and re-captured when the
+ * state buffer, k, dt, rho_inf, tolerance, max_iter, operator form, preconditioner
+ * or guess change. Results are identical to the host-driven loop (off). Steps taken
+ * while a kernel class is being profiled, and the first two steps of the PREV and
+ * EXTRAP guesses, always use the host-driven loop.
+ */
+int iga_set_graphs(iga_handle* h, int on);
+
+/*
  * Operators (device pointers). x and y hold nvec vectors of N doubles each,
  * vector v at offset v*N; x and y must not overlap.
  *   iga_apply_M:    y = M x, [M]_ij = int B_i B_j |det DF| (Sec. 5.3, eq. mass_matrix).

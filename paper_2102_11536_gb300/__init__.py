@@ -69,6 +69,7 @@ def lib():
         "iga_set_precond": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_set_guess": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_set_tol": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_int]),
+        "iga_set_graphs": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_apply_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_K": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_Pinv": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
@@ -99,7 +100,7 @@ def exported_symbols():
             "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
             "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
             "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read",
-            "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma"]
+            "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma", "iga_set_graphs"]
 
 
 def fp64_fma_probe(device=0):
@@ -214,6 +215,10 @@ class Patch:
 
     def set_guess(self, guess):
         self._chk(lib().iga_set_guess(self.h, GUESSES[guess]), "iga_set_guess")
+
+    def set_graphs(self, on):
+        """Replay one captured CUDA graph per step (device-side PCG loop) or use the host loop."""
+        self._chk(lib().iga_set_graphs(self.h, 1 if on else 0), "iga_set_graphs")
 
     def set_tol(self, tol, max_iter=500):
         self._chk(lib().iga_set_tol(self.h, tol, max_iter), "iga_set_tol")

@@ -56,6 +56,23 @@ struct iga_handle {
   std::vector<cudaEvent_t> prof_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
   double prof_flops = 0.0, prof_bytes = 0.0;
+  // captured step graph with the PCG loop on the device (conditional while node)
+  bool use_graphs = true;
+  cudaStream_t gs = nullptr, gbody = nullptr;  // non-default streams for capture and replay
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool gvalid = false;
+  struct GraphKey {
+    const double* state;
+    int k, op, prec, guess, max_iter;
+    double dt, rho, tol;
+  } gkey{};
+  long long g_pro = 0, g_body = 0, g_epi = 0;  // kernel launches captured before / in / after the loop
+  int* d_loop = nullptr;       // [2] iterations of the current solve, body executions since reset
+  long long* d_tot = nullptr;  // [kMaxVec] iterations per system slot, summed over solves
+  int* d_max = nullptr;        // [kMaxVec] largest count of one solve
+  int* d_stat = nullptr;       // [2] first error status, any unconverged solve
   std::string err;
 };
 
@@ -461,17 +478,16 @@ int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, doub
 // ---------------------------------------------------------------------------
 // batched PCG
 // ---------------------------------------------------------------------------
-int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int* iters, double* relres) {
-  CKS(ensure_cg_ws(h, nvec));
-  CKS(ensure_op_ws(h, nvec));
+// PCG (Sec. 5.5), split into launch-only pieces so that the same kernels serve the
+// host-driven loop and the captured graph (whose loop runs on the device).
+// solve_begin: r = b - M x0 (or x = 0, r = b), ||b||^2, ||r||^2, activity flags.
+int solve_begin(iga_handle* h, int nvec, const double* b, double* x, bool use_x0) {
   cudaStream_t s = h->stream;
   const long long N = h->N;
   CgScalars& c = h->cs;
   double* pA = h->partial;
   double* pB = h->partial + kMaxVec * kRedBlocks;
-  double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
   const double tol2 = h->opt.tol * h->opt.tol;
-  const bool flexible = h->opt.precond != IGA_PREC_FP64;
   if (use_x0) {
     CKS(apply_M(h, nvec, nullptr, x, h->q));
     LK(launch_sub(s, N, nvec, b, h->q, h->r, N));
@@ -482,35 +498,77 @@ int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int*
   LK(launch_dot(s, N, nvec, b, b, N, pA));
   LK(launch_dot(s, N, nvec, h->r, h->r, N, pB));
   LK(launch_cg_init(s, nvec, pA, pB, c, tol2));
-  CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int nact = *h->h_nactive;
-  h->cur_active = nact;
-  if (nact > 0) {
-    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-    LK(launch_cg_start(s, nvec, pA, c));
-    LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
-  }
+  return IGA_OK;
+}
+
+// solve_prime: z = P^{-1} r, r.z, p = z (active systems).
+int solve_prime(iga_handle* h, int nvec) {
+  cudaStream_t s = h->stream;
+  const long long N = h->N;
+  CgScalars& c = h->cs;
+  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
+  LK(launch_dot(s, N, nvec, h->r, h->z, N, h->partial));
+  LK(launch_cg_start(s, nvec, h->partial, c));
+  LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
+  return IGA_OK;
+}
+
+// solve_iter_a: q = M p, alpha = r.z / p.q, x += alpha p, r -= alpha q, convergence test.
+int solve_iter_a(iga_handle* h, int nvec, double* x) {
+  cudaStream_t s = h->stream;
+  const long long N = h->N;
+  CgScalars& c = h->cs;
+  double* pA = h->partial;
+  double* pB = h->partial + kMaxVec * kRedBlocks;
+  CKS(apply_M(h, nvec, c.active, h->p, h->q));
+  LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
+  LK(launch_cg_alpha(s, nvec, pA, c));
+  LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
+  LK(launch_cg_check(s, nvec, pB, c, h->opt.tol * h->opt.tol));
+  return IGA_OK;
+}
+
+// solve_iter_b: [flexible: r.z_old] z = P^{-1} r, beta, p = z + beta p.
+int solve_iter_b(iga_handle* h, int nvec) {
+  cudaStream_t s = h->stream;
+  const long long N = h->N;
+  CgScalars& c = h->cs;
+  double* pA = h->partial;
+  double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
+  const bool flexible = h->opt.precond != IGA_PREC_FP64;
+  if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
+  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
+  LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+  LK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
+  LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
+  return IGA_OK;
+}
+
+int read_nactive(iga_handle* h, int* nact) {
+  CK(cudaMemcpyAsync(h->h_nactive, h->cs.nactive, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *nact = *h->h_nactive;
+  h->cur_active = *nact;
+  return IGA_OK;
+}
+
+// Host-driven batched PCG: one host synchronisation per iteration to test convergence.
+int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int* iters, double* relres) {
+  CKS(ensure_cg_ws(h, nvec));
+  CKS(ensure_op_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  CgScalars& c = h->cs;
+  CKS(solve_begin(h, nvec, b, x, use_x0));
+  int nact = 0;
+  CKS(read_nactive(h, &nact));
+  if (nact > 0) CKS(solve_prime(h, nvec));
   int it = 0;
   while (nact > 0 && it < h->opt.max_iter) {
-    CKS(apply_M(h, nvec, c.active, h->p, h->q));
-    LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
-    LK(launch_cg_alpha(s, nvec, pA, c));
-    LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
-    LK(launch_cg_check(s, nvec, pB, c, tol2));
-    CK(cudaMemcpyAsync(h->h_nactive, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    nact = *h->h_nactive;
-    h->cur_active = nact;
+    CKS(solve_iter_a(h, nvec, x));
+    CKS(read_nactive(h, &nact));
     ++it;
     if (nact == 0) break;
-    if (flexible) std::swap(h->z, h->zold);
-    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-    if (flexible) LK(launch_dot(s, N, nvec, h->r, h->zold, N, pC));
-    LK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
-    LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
+    CKS(solve_iter_b(h, nvec));
   }
   int hit[kMaxVec], hst[kMaxVec];
   double hrr[kMaxVec], hbb[kMaxVec];
@@ -552,6 +610,185 @@ int ensure_step_ws(iga_handle* h, int k) {
   CKS(dalloc(h, &h->Z, sz));
   CKS(dalloc(h, &h->Z2, sz));
   h->step_k = k;
+  return IGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one time step as a CUDA graph, the PCG loop running on the device
+// ---------------------------------------------------------------------------
+void drop_step_graph(iga_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->gvalid = false;
+}
+
+// Capture one step on h->gs: Taylor predictor, batched K, the solve's set-up, a
+// conditional while node whose body is one PCG iteration followed by the loop test
+// (k_set_cond: some system active and fewer than max_iter iterations), the
+// iteration statistics, and the stage update. Every buffer is sized beforehand:
+// nothing is allocated while capturing.
+int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
+  drop_step_graph(h);
+  if (!h->gs) {
+    CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->gbody, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  }
+  if (!h->d_loop) {
+    CKS(dalloc(h, &h->d_loop, 2));
+    CKS(dalloc(h, &h->d_tot, kMaxVec));
+    CKS(dalloc(h, &h->d_max, kMaxVec));
+    CKS(dalloc(h, &h->d_stat, 2));
+  }
+  CKS(ensure_step_ws(h, k));
+  CKS(ensure_cg_ws(h, k));
+  CKS(ensure_op_ws(h, k));
+  if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
+  const long long N = h->N;
+  const int guess = h->opt.guess;
+  cudaStream_t user = h->stream;
+  h->stream = h->gs;
+  cudaError_t e0 = cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal);
+  if (e0 != cudaSuccess) {
+    h->stream = user;
+    return fail(h, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e0));
+  }
+  auto capture = [&]() -> int {
+    const long long l0 = h->nlaunch;
+    LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr));
+    CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+    if (guess == IGA_GUESS_EXTRAP) LK(launch_extrap(h->gs, (long long)k * N, h->Z, h->Z2));
+    CKS(solve_begin(h, k, h->rhs, h->Z, guess != IGA_GUESS_ZERO));
+    CKS(solve_prime(h, k));  // masked: no work for systems that start converged
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle hc;
+    CK(cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
+    LK(launch_set_cond(h->gs, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 1));
+    CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    h->g_pro = h->nlaunch - l0;
+    const long long l1 = h->nlaunch;
+    h->stream = h->gbody;
+    CK(cudaStreamBeginCaptureToGraph(h->gbody, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int brc = solve_iter_a(h, k, h->Z);
+    if (brc == IGA_OK) brc = solve_iter_b(h, k);
+    if (brc == IGA_OK) {
+      const cudaError_t be = launch_set_cond(h->gbody, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 0);
+      if (be != cudaSuccess) brc = fail(h, IGA_ECUDA, std::string("loop test: ") + cudaGetErrorString(be));
+      else ++h->nlaunch;
+    }
+    cudaGraph_t bout = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->gbody, &bout);
+    h->stream = h->gs;
+    if (brc != IGA_OK) return brc;
+    if (ee != cudaSuccess) return fail(h, IGA_ECUDA, std::string("loop body capture: ") + cudaGetErrorString(ee));
+    h->g_body = h->nlaunch - l1;
+    CK(cudaStreamUpdateCaptureDependencies(h->gs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const long long l2 = h->nlaunch;
+    LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_stat));
+    LK(launch_update(h->gs, N, sc, state, h->Z));
+    h->g_epi = h->nlaunch - l2;
+    return IGA_OK;
+  };
+  const int rc = capture();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->gs, &g);
+  h->stream = user;
+  if (rc != IGA_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  }
+  if (ee != cudaSuccess) return fail(h, IGA_ECUDA, std::string("step capture: ") + cudaGetErrorString(ee));
+  cudaGraphExec_t ge = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+  if (ie != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(h, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+  }
+  h->graph = g;
+  h->gexec = ge;
+  h->gvalid = true;
+  return IGA_OK;
+}
+
+bool same_key(const iga_handle::GraphKey& a, const iga_handle::GraphKey& b) {
+  return a.state == b.state && a.k == b.k && a.op == b.op && a.prec == b.prec && a.guess == b.guess &&
+         a.max_iter == b.max_iter && a.dt == b.dt && a.rho == b.rho && a.tol == b.tol;
+}
+
+// nsteps replays of the captured step on h->gs, ordered after earlier work on the
+// caller's stream and before later work on it; one host synchronisation at the end.
+int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCoefs& sc, int nsteps,
+                   iga_stats* stats) {
+  iga_handle::GraphKey key{};
+  key.state = state;
+  key.k = k;
+  key.op = h->opt.op_form;
+  key.prec = h->opt.precond;
+  key.guess = h->opt.guess;
+  key.max_iter = h->opt.max_iter;
+  key.dt = sc.tau;
+  key.rho = rho;
+  key.tol = h->opt.tol;
+  if (!h->gvalid || !same_key(key, h->gkey)) {
+    CKS(build_step_graph(h, state, k, sc));
+    h->gkey = key;
+  }
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->d_tot, 0, sizeof(long long) * kMaxVec, s));
+  CK(cudaMemsetAsync(h->d_max, 0, sizeof(int) * kMaxVec, s));
+  CK(cudaMemsetAsync(h->d_stat, 0, sizeof(int) * 2, s));
+  CK(cudaMemsetAsync(h->d_loop, 0, sizeof(int) * 2, s));
+  CK(cudaEventRecord(h->ev_in, s));
+  CK(cudaStreamWaitEvent(h->gs, h->ev_in, 0));
+  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(h->gexec, h->gs));
+  CK(cudaEventRecord(h->ev_out, h->gs));
+  CK(cudaStreamWaitEvent(s, h->ev_out, 0));
+  long long tot[kMaxVec];
+  int mx[kMaxVec], st[2], loop[2];
+  double rr[kMaxVec], bb[kMaxVec];
+  CK(cudaMemcpyAsync(tot, h->d_tot, sizeof(tot), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(mx, h->d_max, sizeof(mx), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(st, h->d_stat, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(loop, h->d_loop, sizeof(loop), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rr, h->cs.rr, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(bb, h->cs.bb, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->nlaunch += (long long)nsteps * (h->g_pro + h->g_epi) + (long long)loop[1] * h->g_body;
+  h->hist = std::min(h->hist + nsteps, 2);
+  if (stats) {
+    stats->steps += nsteps;
+    stats->solves += k * nsteps;
+    for (int j = 0; j < k; ++j) {
+      stats->iters += tot[j];
+      stats->max_iters = std::max(stats->max_iters, mx[j]);
+      const double rel = bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0;  // last step's solves
+      stats->max_relres = std::max(stats->max_relres, rel);
+    }
+  }
+  CKS(check_tc_error(h));
+  if (st[0] != 0) return fail(h, IGA_ENUMERIC, "PCG breakdown (non-positive curvature or non-finite values)");
+  if (st[1] != 0) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "PCG did not reach tol %.3g in %d iterations", h->opt.tol, h->opt.max_iter);
+    return fail(h, IGA_ENOT_CONVERGED, buf);
+  }
   return IGA_OK;
 }
 
@@ -628,6 +865,12 @@ void iga_destroy(iga_handle* h) {
   for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
   dfree(h->Yneg); dfree(h->rhs); dfree(h->Z); dfree(h->Z2); dfree(h->dstate);
+  drop_step_graph(h);
+  if (h->gs) cudaStreamDestroy(h->gs);
+  if (h->gbody) cudaStreamDestroy(h->gbody);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_stat);
   delete h;
 }
 
@@ -797,6 +1040,12 @@ int iga_set_guess(iga_handle* h, int guess) {
   h->opt.guess = guess;
   return IGA_OK;
 }
+int iga_set_graphs(iga_handle* h, int on) {
+  if (!h) return IGA_EINVAL;
+  h->use_graphs = on != 0;
+  return IGA_OK;
+}
+
 int iga_set_tol(iga_handle* h, double tol, int max_iter) {
   if (!h || !(tol >= 0) || max_iter < 1) return IGA_EINVAL;
   h->opt.tol = tol;
@@ -880,6 +1129,27 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
   const long long launches0 = h->nlaunch;
   for (int step = 0; step < nsteps; ++step) {
     const int guess = h->opt.guess;
+    // steady state: replay the captured step (device-side PCG loop) for the remaining steps
+    const bool graph_ok = h->use_graphs && h->prof_class == IGA_PROF_OFF &&
+                          (guess == IGA_GUESS_ZERO || guess == IGA_GUESS_TAYLOR || h->hist >= 2);
+    if (graph_ok) {
+      iga_handle::GraphKey key{};
+      key.state = state; key.k = k; key.op = h->opt.op_form; key.prec = h->opt.precond; key.guess = guess;
+      key.max_iter = h->opt.max_iter; key.dt = dt; key.rho = rho_inf; key.tol = h->opt.tol;
+      if (!h->gvalid || !same_key(key, h->gkey)) {
+        if (build_step_graph(h, state, k, sc) != IGA_OK) {
+          h->use_graphs = false;  // capture refused: keep the host-driven loop for this handle
+          h->err.clear();
+        } else {
+          h->gkey = key;
+        }
+      }
+      if (h->use_graphs) {
+        CKS(run_step_graph(h, state, k, rho_inf, sc, nsteps - step, stats));
+        if (stats) stats->launches += h->nlaunch - launches0;
+        return IGA_OK;
+      }
+    }
     const bool taylor = guess == IGA_GUESS_TAYLOR;
     LK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr));
     CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));

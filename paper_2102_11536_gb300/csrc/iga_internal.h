@@ -166,6 +166,10 @@ cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const doub
 cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, const double* Z);
 // Z <- 2 Z - Z2, Z2 <- old Z
 cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
+// device-side loop control of the captured PCG (kernels_vec.cu)
+cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const int* nactive, int* loop, int max_iter,
+                            int reset);
+cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, int* stat);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
 
 // BF16 tensor-core mode product (kernels_tc.cu): B is the BF16 matrix arranged by

@@ -376,4 +376,43 @@ cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x) {
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// device-side PCG loop of the captured step graph
+// ----------------------------------------------------------------------------
+// loop[0]: iterations of the current solve, loop[1]: body executions summed over
+// the solves since the last reset. The while node runs its body as long as the
+// value set here is non-zero: some system still active and max_iter not reached.
+__global__ void k_set_cond(cudaGraphConditionalHandle hc, const int* nactive, int* loop, int max_iter, int reset) {
+  if (reset) {
+    loop[0] = 0;
+  } else {
+    loop[0] += 1;
+    loop[1] += 1;
+  }
+  cudaGraphSetConditional(hc, (*nactive > 0 && loop[0] < max_iter) ? 1u : 0u);
+}
+
+cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const int* nactive, int* loop, int max_iter,
+                            int reset) {
+  k_set_cond<<<1, 1, 0, s>>>(hc, nactive, loop, max_iter, reset);
+  return cudaGetLastError();
+}
+
+// After a solve: total and largest iteration counts per system slot, the first
+// error status, and whether any system stopped unconverged.
+__global__ void k_accum(int nvec, CgScalars c, long long* tot, int* mx, int* stat) {
+  const int v = threadIdx.x;
+  if (v < nvec) {
+    tot[v] += c.iters[v];
+    if (c.iters[v] > mx[v]) mx[v] = c.iters[v];
+    if (c.status[v] != 0) atomicCAS(stat, 0, c.status[v]);
+  }
+  if (v == 0 && *c.nactive > 0) stat[1] = 1;
+}
+
+cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, int* stat) {
+  k_accum<<<1, 32, 0, s>>>(nvec, c, tot, mx, stat);
+  return cudaGetLastError();
+}
+
 }  // namespace iga

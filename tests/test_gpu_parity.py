@@ -230,6 +230,30 @@ def test_nonuniform_repeated_knots():
     g.close()
 
 
+@pytest.mark.parametrize("form", [("matrix_free", "fp64", "zero"), ("assembled", "fp32", "zero"),
+                                  ("assembled", "fp64", "extrap"), ("assembled", "bf16", "taylor")])
+def test_graph_replay_equals_host_loop(form):
+    """The captured step (PCG loop on the device) and the host-driven loop run the same
+    kernels in the same order: bitwise equal states and equal iteration counts."""
+    op, prec, guess = form
+    w = W.small(d=3, nel=(6, 5, 7), p=3, amp=0.1, k=2, rho=0.5, init="random")
+    ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+    dt = _dt(ops, w.rho)
+    U0, V0 = w.initial()
+    out = []
+    for graphs in (False, True):
+        g = _gpu(w, tol=1e-11, op_form=op, precond=prec, guess=guess)
+        g.set_graphs(graphs)
+        state = torch.zeros(3 * w.k * g.N, dtype=torch.float64, device=DEV)
+        g.state_init(w.k, _t(U0), _t(V0), state)
+        st = g.step(state, w.k, w.rho, dt, 4)
+        st = g.step(state, w.k, w.rho, dt, 6, st)  # a second call replays the cached graph
+        out.append((_np(state), st.iters, st.max_iters, st.steps))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+
+
 def test_deterministic_bitwise():
     w = W.small(d=3, nel=(6, 5, 4), p=3, amp=0.1, k=2)
     ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
