@@ -70,17 +70,23 @@ def test_cube128_forms_agree(c3):
     state = torch.empty(3 * k * g.N, dtype=torch.float64, device=DEV)
     steps = 6
     finals = {}
-    for name, op, prec, graphs in [("fp64", "assembled", "fp64", True), ("fp32", "assembled", "fp32", True),
-                                   ("fp32_host", "assembled", "fp32", False), ("bf16", "assembled", "bf16", True),
-                                   ("mf", "matrix_free", "fp64", True)]:
+    # The BF16 preconditioner stops PCG at points farther apart within the same
+    # tolerance; at tol 1e-10 its velocity sits at 1.5e-8 from the FP64 form here, so
+    # that form runs at tol 1e-11 to meet 1e-8.
+    for name, op, prec, graphs, tol in [("fp64", "assembled", "fp64", True, w.tol),
+                                        ("fp32", "assembled", "fp32", True, w.tol),
+                                        ("fp32_host", "assembled", "fp32", False, w.tol),
+                                        ("bf16", "assembled", "bf16", True, 1e-11),
+                                        ("mf", "matrix_free", "fp64", True, w.tol)]:
         g.set_op_form(op)
         g.set_precond(prec)
         g.set_graphs(graphs)
+        g.set_tol(tol, 500)
         g.state_init(k, u0, v0, state)
         if name == "fp64":
             e0 = _energy(g, state.view(3 * k, g.N)[:2].cpu().numpy())
         st = g.step(state, k, rho, dt, steps)
-        assert st.max_relres <= w.tol
+        assert st.max_relres <= tol
         finals[name] = state.view(3 * k, g.N)[:2].cpu().numpy()
     ref = finals["fp64"]
     for name in ("fp32", "bf16", "mf"):
@@ -90,5 +96,6 @@ def test_cube128_forms_agree(c3):
     assert np.array_equal(finals["fp32"], finals["fp32_host"])
     g.set_op_form("assembled")
     g.set_precond("fp64")
+    g.set_tol(w.tol, 500)
     e1 = _energy(g, ref)
     assert e1 <= e0 * (1 + 1e-4)
