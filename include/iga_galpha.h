@@ -58,6 +58,11 @@ extern "C" {
 #define IGA_GUESS_PREV 1      /* the same block's solution at the previous step */
 #define IGA_GUESS_EXTRAP 2    /* 2 Z^{n-1} - Z^{n-2} */
 #define IGA_GUESS_TAYLOR 3    /* the Taylor predictor T_{s_j} of the solved variable */
+#define IGA_GUESS_LEARNED 4   /* 2 Z^{n-1} - Z^{n-2} plus the learned network's correction
+                                 (iga_ws_*; no counterpart in the paper) */
+
+/* Parameters of the warm-start network: W1 [16][3][27], b1 [16], W2 [16][27], b2 [1]. */
+#define IGA_NET_NPARAM 1745
 
 typedef struct iga_options {
   int nquad;        /* Gauss points per element and direction; 0 => max_a(p_a) + 1 */
@@ -77,6 +82,7 @@ typedef struct iga_stats {
   int max_iters;        /* largest iteration count of one solve */
   double max_relres;    /* largest final ||r||/||b|| */
   long long launches;   /* CUDA kernel launches issued by the call */
+  double init_relres_sum; /* sum over the solves of ||b - M x0||_2 / ||b||_2 (x0 the initial guess) */
 } iga_stats;
 
 /* Kernel classes that iga_profile can time (see iga_profile). */
@@ -262,6 +268,88 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
  */
 int iga_profile(iga_handle* h, int kernel_class);
 int iga_profile_read(iga_handle* h, double* total_ms, long long* launches, double* flops, double* bytes);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper). A two-layer 3-D convolutional
+ * network on the interior control-point grid supplies the initial guess of the
+ * k mass solves of each step (Sec. 4, eq. ho1); PCG still stops at the same
+ * residual (Sec. 5.5), so the guess changes the iteration count, not the result.
+ *
+ * Network: y = conv2(R(relu(conv1(x)))), conv1 3 -> 16 and conv2 16 -> 1 channels,
+ * 3x3x3 taps (tap t = e1 + 3 e2 + 9 e3 reads the neighbour at offset
+ * (e1-1, e2-1, e3-1) along (i1, i2, i3)), zero padding, biases. Inputs,
+ * activations and parameters are BF16 values (R rounds to nearest even), sums
+ * FP32. Parameter vector: IGA_NET_NPARAM floats, W1 [o][c][t], b1, W2 [c][t], b2.
+ *
+ * Features of the solve M Z^n = b^n of one stage, from the same stage's right-hand
+ * sides b^{n-1}, b^{n-2} and solutions Z^{n-1}, Z^{n-2}, with D = diag(M):
+ *   E = 2 Z^{n-1} - Z^{n-2},  c0 = D^{-1}(b^n - 2 b^{n-1} + b^{n-2}),
+ *   s0 = rms(c0), s1 = rms(Z^{n-1}) (1 where zero),
+ *   x = BF16(FP32(c0/s0, Z^{n-1}/s1, Z^{n-2}/s1)),  guess = E + s0 y.
+ * Training target t = (Z^n - E)/s0; loss sum (y - t)^2 / (2N) per sample; Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8), one sample per update.
+ * ---------------------------------------------------------------------------
+ */
+
+/*
+ * iga_ws_collect -- record training samples from later iga_step calls on h:
+ * every solve of a step taken with IGA_GUESS_LEARNED and two steps of history
+ * stores its features and target (10 bytes per dof on the device). capacity is the
+ * number of samples (solves) to keep; recording stops when full. capacity = 0
+ * stops recording and frees the samples. Steps taken while recording use the
+ * host-driven loop (no step graph). Untrained, the learned guess is E.
+ */
+int iga_ws_collect(iga_handle* h, int capacity);
+/* Number of samples recorded so far (host int). */
+int iga_ws_samples(iga_handle* h, int* count);
+/*
+ * iga_ws_train -- `epochs` passes of Adam over the recorded samples (one sample
+ * per update, order a seeded permutation per epoch, learning rate lr), on the
+ * device with the library's forward and backward kernels. loss_first /
+ * loss_last (host, may be NULL) receive the mean loss of the first and last
+ * epoch. Parameters not yet set are first drawn by iga_ws_init_params(seed).
+ * Afterwards IGA_GUESS_LEARNED uses the trained network. IGA_EINVAL without samples.
+ */
+int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* loss_first,
+                 double* loss_last);
+/* Draw the parameters: weights uniform in +-1/sqrt(fan_in) (81 for W1, 432 for W2)
+ * from a splitmix64 stream seeded by seed, biases zero; resets Adam's moments. */
+int iga_ws_init_params(iga_handle* h, unsigned long long seed);
+/* Copy the FP32 parameters out (host, IGA_NET_NPARAM floats) / in (the network
+ * counts as trained after a set). */
+int iga_ws_get_params(iga_handle* h, float* theta_host);
+int iga_ws_set_params(iga_handle* h, const float* theta_host);
+/*
+ * iga_ws_features -- the features of k solves (test hook for the kernels of the
+ * learned guess). Device pointers, [k][N] each: b, b1, b2, z1, z2 (b1, b2, z1, z2
+ * are overwritten by the moved histories b2 <- b1 <- b, z2 <- z1 <- E); x
+ * [k][3][N] BF16 bits; E [k][N]; scales [k][2] = (s0, s1). Synchronises.
+ */
+int iga_ws_features(iga_handle* h, int k, const double* b, double* b1, double* b2, double* z1, double* z2,
+                    unsigned short* x, double* E, double* scales);
+
+/*
+ * Handle-free network kernels (building blocks and test hooks). Device pointers;
+ * grid n1 x n2 x n3 (N points), nb samples; stream is a cudaStream_t (NULL =
+ * legacy default stream). They return IGA_EINVAL for non-positive sizes or a grid
+ * beyond the launch limits, IGA_ECUDA if a launch fails; they do not synchronise.
+ *   iga_net_forward:  x [nb][3][N] BF16 bits, theta IGA_NET_NPARAM floats ->
+ *                     act [nb][16][N] BF16 bits, y [nb][N] floats.
+ *   iga_net_backward: gradient of sum_s sum_p dy[s][p] y[s][p] with respect to
+ *                     theta (grad, IGA_NET_NPARAM floats) from x, theta, the act of
+ *                     iga_net_forward and dy [nb][N]; work: at least
+ *                     iga_net_workspace_bytes(n1, n2, n3, nb) bytes.
+ *   iga_net_adam:     one Adam update (step counts from 1) of n parameters with
+ *                     moments m, v (floats, updated).
+ */
+int iga_net_forward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
+                    unsigned short* act, float* y, void* stream);
+unsigned long long iga_net_workspace_bytes(int n1, int n2, int n3, int nb);
+int iga_net_backward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
+                     const unsigned short* act, const float* dy, float* grad, void* work,
+                     unsigned long long work_bytes, void* stream);
+int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int step, double lr, void* stream);
 
 /*
  * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in

@@ -113,11 +113,18 @@ def forward(x, theta, round_act=True):
     return h, a, y
 
 
-def backward(x, theta, dy, round_act=True):
+def backward(x, theta, dy, round_act=True, act=None):
     """Gradient of sum_p dy_p y_p with respect to theta (the BF16 rounding of the
-    activations passes gradients through unchanged)."""
+    activations passes gradients through unchanged). With `act` given, that hidden
+    layer is used instead of recomputing it and the ReLU derivative is [act > 0]
+    (equal to [h > 0] for a layer computed from h): a check of another
+    implementation's backward can then take the ReLU decision on its own values."""
     W1, b1, W2, b2 = split_params(theta)
-    h, a, _ = forward(x, theta, round_act)
+    if act is None:
+        h, a, _ = forward(x, theta, round_act)
+    else:
+        a = np.asarray(act, dtype=np.float64)
+        h = a
     gW2 = np.empty_like(W2)
     da = np.zeros_like(a)
     for t in range(NTAP):

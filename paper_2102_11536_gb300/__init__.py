@@ -22,7 +22,8 @@ _LIB = None
 OK, EINVAL, ENOMEM, ECUDA, ENOT_CONVERGED, ENUMERIC, EUNSTABLE, EGEOMETRY = range(8)
 OP_FORMS = {"matrix_free": 0, "assembled": 1}
 PRECONDS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
-GUESSES = {"zero": 0, "prev": 1, "extrap": 2, "taylor": 3}
+GUESSES = {"zero": 0, "prev": 1, "extrap": 2, "taylor": 3, "learned": 4}
+NET_NPARAM = 1745
 
 
 class IgaError(RuntimeError):
@@ -39,7 +40,8 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("solves", ctypes.c_int), ("iters", ctypes.c_longlong),
-                ("max_iters", ctypes.c_int), ("max_relres", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("max_iters", ctypes.c_int), ("max_relres", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("init_relres_sum", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,6 +87,17 @@ def lib():
         "iga_profile": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_probe_fp64_fma": (ctypes.c_int, [ctypes.c_int, dp, dp]),
         "iga_profile_read": (ctypes.c_int, [H, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
+        "iga_ws_collect": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_ws_samples": (ctypes.c_int, [H, ip]),
+        "iga_ws_train": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong, dp, dp]),
+        "iga_ws_init_params": (ctypes.c_int, [H, ctypes.c_ulonglong]),
+        "iga_ws_get_params": (ctypes.c_int, [H, vp]),
+        "iga_ws_set_params": (ctypes.c_int, [H, vp]),
+        "iga_ws_features": (ctypes.c_int, [H, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "iga_net_forward": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp, vp, vp]),
+        "iga_net_workspace_bytes": (ctypes.c_ulonglong, [ctypes.c_int] * 4),
+        "iga_net_backward": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp, vp, vp, vp, ctypes.c_ulonglong, vp]),
+        "iga_net_adam": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -100,7 +113,9 @@ def exported_symbols():
             "iga_ndof", "iga_assemble", "iga_set_op_form", "iga_set_precond", "iga_set_guess", "iga_set_tol",
             "iga_apply_M", "iga_apply_K", "iga_apply_Pinv", "iga_solve_M", "iga_galpha_params", "iga_cfl",
             "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read",
-            "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma", "iga_set_graphs"]
+            "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma", "iga_set_graphs", "iga_ws_collect",
+            "iga_ws_samples", "iga_ws_train", "iga_ws_init_params", "iga_ws_get_params", "iga_ws_set_params",
+            "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam"]
 
 
 def fp64_fma_probe(device=0):
@@ -148,6 +163,65 @@ def _default_stream():
     return None
 
 
+def _check_dev_typed(t, n, name, dtype):
+    if isinstance(t, int):
+        return
+    import torch
+    if getattr(t, "is_cuda", False) is not True or t.dtype != dtype or not t.is_contiguous() or t.numel() < n:
+        raise ValueError("%s must be a contiguous CUDA %s tensor with at least %d elements" % (name, dtype, n))
+
+
+def net_forward(shape, x, theta, act, y, nb=1, stream=None):
+    """Warm-start network forward on an (n1, n2, n3) grid: x [nb][3][N] bfloat16,
+    theta float32 [NET_NPARAM] -> act [nb][16][N] bfloat16, y [nb][N] float32."""
+    import torch
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    _check_dev_typed(x, nb * 3 * N, "x", torch.bfloat16)
+    _check_dev_typed(theta, NET_NPARAM, "theta", torch.float32)
+    _check_dev_typed(act, nb * 16 * N, "act", torch.bfloat16)
+    _check_dev_typed(y, nb * N, "y", torch.float32)
+    rc = lib().iga_net_forward(n1, n2, n3, nb, _ptr(x), _ptr(theta), _ptr(act), _ptr(y),
+                               stream if stream is not None else _default_stream())
+    if rc != OK:
+        raise IgaError(rc, "iga_net_forward")
+
+
+def net_workspace_bytes(shape, nb=1):
+    n1, n2, n3 = shape
+    return int(lib().iga_net_workspace_bytes(n1, n2, n3, nb))
+
+
+def net_backward(shape, x, theta, act, dy, grad, work, nb=1, stream=None):
+    """Gradient of sum(dy * y) with respect to theta (grad float32 [NET_NPARAM]);
+    work: a uint8 CUDA tensor of at least net_workspace_bytes(shape, nb) bytes."""
+    import torch
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    _check_dev_typed(x, nb * 3 * N, "x", torch.bfloat16)
+    _check_dev_typed(theta, NET_NPARAM, "theta", torch.float32)
+    _check_dev_typed(act, nb * 16 * N, "act", torch.bfloat16)
+    _check_dev_typed(dy, nb * N, "dy", torch.float32)
+    _check_dev_typed(grad, NET_NPARAM, "grad", torch.float32)
+    rc = lib().iga_net_backward(n1, n2, n3, nb, _ptr(x), _ptr(theta), _ptr(act), _ptr(dy), _ptr(grad), _ptr(work),
+                                work.numel() * work.element_size(),
+                                stream if stream is not None else _default_stream())
+    if rc != OK:
+        raise IgaError(rc, "iga_net_backward")
+
+
+def net_adam(theta, grad, m, v, step, lr, stream=None):
+    """One Adam update of float32 CUDA tensors theta, m, v from grad (step counts from 1)."""
+    import torch
+    n = theta.numel()
+    for t, name in ((theta, "theta"), (grad, "grad"), (m, "m"), (v, "v")):
+        _check_dev_typed(t, n, name, torch.float32)
+    rc = lib().iga_net_adam(n, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), step, lr,
+                            stream if stream is not None else _default_stream())
+    if rc != OK:
+        raise IgaError(rc, "iga_net_adam")
+
+
 def galpha_params(k: int, rho: float):
     """(alpha, beta, gamma) lists of the method for order 2k (Sec. 4.1)."""
     a = (ctypes.c_double * k)()
@@ -188,6 +262,8 @@ class Patch:
         n = ctypes.c_longlong()
         L.iga_ndof(h, ctypes.byref(n))
         self.N = int(n.value)
+        # interior control points per direction (n1, n2, n3), i1 fastest
+        self.shape = tuple([len(k) - int(p) - 3 for k, p in zip(self._knots, degrees)] + [1] * (3 - self.d))
 
     def _chk(self, rc, what):
         if rc != OK:
@@ -278,6 +354,50 @@ class Patch:
         self._chk(lib().iga_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
                                          ctypes.byref(by)), "iga_profile_read")
         return ms.value, n.value, fl.value, by.value
+
+    # -- learned warm start -------------------------------------------------------
+    def ws_collect(self, capacity):
+        """Record up to `capacity` (features, target) samples from later learned-guess steps."""
+        self._chk(lib().iga_ws_collect(self.h, capacity), "iga_ws_collect")
+
+    def ws_samples(self):
+        n = ctypes.c_int()
+        self._chk(lib().iga_ws_samples(self.h, ctypes.byref(n)), "iga_ws_samples")
+        return n.value
+
+    def ws_train(self, epochs, lr=1e-3, seed=0):
+        """Adam over the recorded samples; returns (mean loss of the first epoch, of the last)."""
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        self._chk(lib().iga_ws_train(self.h, epochs, lr, seed, ctypes.byref(a), ctypes.byref(b)), "iga_ws_train")
+        return a.value, b.value
+
+    def ws_init_params(self, seed=0):
+        self._chk(lib().iga_ws_init_params(self.h, seed), "iga_ws_init_params")
+
+    def ws_get_params(self):
+        import numpy as np
+        out = np.empty(NET_NPARAM, dtype=np.float32)
+        self._chk(lib().iga_ws_get_params(self.h, out.ctypes.data), "iga_ws_get_params")
+        return out
+
+    def ws_set_params(self, theta):
+        import numpy as np
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != NET_NPARAM:
+            raise ValueError("expected %d parameters" % NET_NPARAM)
+        self._chk(lib().iga_ws_set_params(self.h, th.ctypes.data), "iga_ws_set_params")
+
+    def ws_features(self, k, b, b1, b2, z1, z2, x, E, scales):
+        """Features of k solves (device tensors; b1, b2, z1, z2 are overwritten by the moved histories)."""
+        import torch
+        n = k * self.N
+        for t, name in ((b, "b"), (b1, "b1"), (b2, "b2"), (z1, "z1"), (z2, "z2"), (E, "E")):
+            _check_dev(t, n, name)
+        _check_dev_typed(x, 3 * n, "x", torch.bfloat16)
+        _check_dev(scales, 2 * k, "scales")
+        self._chk(lib().iga_ws_features(self.h, k, _ptr(b), _ptr(b1), _ptr(b2), _ptr(z1), _ptr(z2), _ptr(x),
+                                        _ptr(E), _ptr(scales)), "iga_ws_features")
 
     def step_host(self, state_host, k, rho, dt, nsteps=1, stats=None):
         """state_host: host buffer (numpy array or pinned CPU tensor) of 3k*N float64."""

@@ -72,7 +72,24 @@ struct iga_handle {
   int* d_loop = nullptr;       // [2] iterations of the current solve, body executions since reset
   long long* d_tot = nullptr;  // [kMaxVec] iterations per system slot, summed over solves
   int* d_max = nullptr;        // [kMaxVec] largest count of one solve
+  double* d_init = nullptr;    // [kMaxVec] initial relative residuals, summed over solves
+  double last_init[kMaxVec] = {};  // initial relative residuals of the last host-driven solve
   int* d_stat = nullptr;       // [2] first error status, any unconverged solve
+  // learned initial guess (kernels_net.cu)
+  float *ws_theta = nullptr, *ws_m = nullptr, *ws_v = nullptr, *ws_grad = nullptr;
+  bool ws_params = false, ws_trained = false;
+  long long ws_adam_t = 0;
+  int ws_k = 0;                                         // stages the step buffers hold
+  double *ws_E = nullptr, *ws_B1 = nullptr, *ws_B2 = nullptr;  // [k][N]
+  double *ws_sc = nullptr, *ws_part = nullptr;          // scales [k][2], norm partials
+  __nv_bfloat16 *ws_x = nullptr, *ws_act = nullptr;     // [k][3][N], [k][16][N]
+  int ws_cap = 0, ws_count = 0;                         // recorded samples
+  __nv_bfloat16* ws_sx = nullptr;                       // [cap][3][N]
+  float* ws_st = nullptr;                               // [cap][N]
+  float *ws_y = nullptr, *ws_dy = nullptr;              // training: [N]
+  void* ws_work = nullptr;
+  double *ws_loss = nullptr, *ws_lpart = nullptr;
+  long long ws_loss_cap = 0;
   std::string err;
 };
 
@@ -190,8 +207,13 @@ void galpha_params(int k, double rho, double* alpha, double* beta, double* gamma
 
 double theta_crit(double rho) { return 12.0 * (1.0 + rho) * (2.0 - rho) / (rho * rho - 5.0 * rho + 10.0); }
 
+// A captured step graph holds workspace addresses: every workspace reallocation
+// below drops it, and the next step captures again.
+void drop_step_graph(iga_handle* h);
+
 int ensure_op_ws(iga_handle* h, int nvec) {
   if (h->ws_vec >= nvec) return IGA_OK;
+  drop_step_graph(h);
   if (h->dim == 3) {
     h->su = (long long)h->Q[0] * h->n[1] * h->n[2];
     h->st = (long long)h->Q[0] * h->Q[1] * h->n[2];
@@ -212,6 +234,7 @@ int ensure_op_ws(iga_handle* h, int nvec) {
 
 int ensure_cg_ws(iga_handle* h, int nvec) {
   if (h->cg_vec >= nvec) return IGA_OK;
+  drop_step_graph(h);
   const size_t sz = (size_t)nvec * h->N;
   CKS(dalloc(h, &h->r, sz));
   CKS(dalloc(h, &h->z, sz));
@@ -423,15 +446,27 @@ int assemble_band(iga_handle* h) {
   CKS(dalloc(h, &h->Kband, (size_t)H * h->N));
   CK(cudaMemsetAsync(h->Mband, 0, sizeof(double) * H * h->N, s));
   CK(cudaMemsetAsync(h->Kband, 0, sizeof(double) * H * h->N, s));
+  // Probe vectors in buffers of their own: the assembly may run lazily inside an
+  // operator call whose caller holds pointers into the PCG workspace, so it must
+  // not resize that workspace.
   constexpr int kBatch = 8;
-  CKS(ensure_cg_ws(h, kBatch));
+  struct ProbeBufs {
+    double* x = nullptr;
+    double* y = nullptr;
+    ~ProbeBufs() {
+      if (x) cudaFree(x);
+      if (y) cudaFree(y);
+    }
+  } pb;
+  CKS(dalloc(h, &pb.x, (size_t)kBatch * h->N));
+  CKS(dalloc(h, &pb.y, (size_t)kBatch * h->N));
   for (int first = 0; first < S; first += kBatch) {
     const int nv = std::min(kBatch, S - first);
-    LK(launch_probe_gen(s, h->N, h->n, p3, first, S, nv, h->r, h->N));
-    CKS(apply_M_mf(h, nv, nullptr, h->r, h->z));
-    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, h->z, h->N, h->Mband));
-    CKS(apply_K_mf(h, nv, nullptr, h->r, h->z));
-    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, h->z, h->N, h->Kband));
+    LK(launch_probe_gen(s, h->N, h->n, p3, first, S, nv, pb.x, h->N));
+    CKS(apply_M_mf(h, nv, nullptr, pb.x, pb.y));
+    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, pb.y, h->N, h->Mband));
+    CKS(apply_K_mf(h, nv, nullptr, pb.x, pb.y));
+    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, pb.y, h->N, h->Kband));
   }
   CK(cudaStreamSynchronize(s));
   h->band_H = H;
@@ -571,7 +606,8 @@ int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int*
     CKS(solve_iter_b(h, nvec));
   }
   int hit[kMaxVec], hst[kMaxVec];
-  double hrr[kMaxVec], hbb[kMaxVec];
+  double hrr[kMaxVec], hbb[kMaxVec], hr0[kMaxVec];
+  CK(cudaMemcpyAsync(hr0, c.rr0, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hit, c.iters, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hst, c.status, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hrr, c.rr, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
@@ -580,6 +616,7 @@ int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int*
   int status = IGA_OK;
   for (int v = 0; v < nvec; ++v) {
     const double rel = hbb[v] > 0 ? std::sqrt(hrr[v] / hbb[v]) : 0.0;
+    h->last_init[v] = hbb[v] > 0 ? std::sqrt(hr0[v] / hbb[v]) : 0.0;
     if (iters) iters[v] = hit[v];
     if (relres) relres[v] = rel;
     if (hst[v] != 0) status = IGA_ENUMERIC;
@@ -604,12 +641,48 @@ int check_handle(iga_handle* h) {
 
 int ensure_step_ws(iga_handle* h, int k) {
   if (h->step_k >= k) return IGA_OK;
+  drop_step_graph(h);
   const size_t sz = (size_t)k * h->N;
   CKS(dalloc(h, &h->Yneg, sz));
   CKS(dalloc(h, &h->rhs, sz));
   CKS(dalloc(h, &h->Z, sz));
   CKS(dalloc(h, &h->Z2, sz));
   h->step_k = k;
+  return IGA_OK;
+}
+
+// Buffers of the learned guess for k stages: histories, features, hidden layer.
+int ensure_ws_step(iga_handle* h, int k) {
+  if (!h->ws_theta) {
+    CKS(dalloc(h, &h->ws_theta, IGA_NET_NPARAM));
+    CKS(dalloc(h, &h->ws_m, IGA_NET_NPARAM));
+    CKS(dalloc(h, &h->ws_v, IGA_NET_NPARAM));
+    CKS(dalloc(h, &h->ws_grad, IGA_NET_NPARAM));
+    CKS(dalloc(h, &h->ws_sc, 2 * kMaxVec));
+    CKS(dalloc(h, &h->ws_part, (size_t)2 * kMaxVec * kRedBlocks));
+  }
+  if (h->ws_k >= k) return IGA_OK;
+  drop_step_graph(h);
+  const size_t sz = (size_t)k * h->N;
+  CKS(dalloc(h, &h->ws_E, sz));
+  CKS(dalloc(h, &h->ws_B1, sz));
+  CKS(dalloc(h, &h->ws_B2, sz));
+  CKS(dalloc(h, &h->ws_x, 3 * sz));
+  CKS(dalloc(h, &h->ws_act, 16 * sz));
+  h->ws_k = k;
+  return IGA_OK;
+}
+
+NetGrid net_grid_of(const iga_handle* h) { return NetGrid{h->n[0], h->n[1], h->n[2]}; }
+
+// The learned guess of the k solves of a step, two steps of history present:
+// features (into x), histories moved, Z = E (+ s0 y once the network is trained).
+int learned_guess(iga_handle* h, cudaStream_t s, int k, __nv_bfloat16* x) {
+  CK(launch_ws_features(s, h->N, k, h->rhs, h->ws_B1, h->ws_B2, h->Dm, h->Z, h->Z2, x, h->ws_E, h->ws_part,
+                        h->ws_sc, &h->nlaunch));
+  if (h->ws_trained)
+    CK(launch_net_forward(s, net_grid_of(h), k, x, h->ws_theta, h->ws_act, nullptr, h->Z, h->ws_E, h->ws_sc,
+                          &h->nlaunch));
   return IGA_OK;
 }
 
@@ -641,11 +714,13 @@ int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
     CKS(dalloc(h, &h->d_loop, 2));
     CKS(dalloc(h, &h->d_tot, kMaxVec));
     CKS(dalloc(h, &h->d_max, kMaxVec));
+    CKS(dalloc(h, &h->d_init, kMaxVec));
     CKS(dalloc(h, &h->d_stat, 2));
   }
   CKS(ensure_step_ws(h, k));
   CKS(ensure_cg_ws(h, k));
   CKS(ensure_op_ws(h, k));
+  if (h->opt.guess == IGA_GUESS_LEARNED) CKS(ensure_ws_step(h, k));
   if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
   const long long N = h->N;
   const int guess = h->opt.guess;
@@ -661,6 +736,7 @@ int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
     LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr));
     CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
     if (guess == IGA_GUESS_EXTRAP) LK(launch_extrap(h->gs, (long long)k * N, h->Z, h->Z2));
+    if (guess == IGA_GUESS_LEARNED) CKS(learned_guess(h, h->gs, k, h->ws_x));
     CKS(solve_begin(h, k, h->rhs, h->Z, guess != IGA_GUESS_ZERO));
     CKS(solve_prime(h, k));  // masked: no work for systems that start converged
     cudaStreamCaptureStatus cst;
@@ -699,7 +775,7 @@ int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
     h->g_body = h->nlaunch - l1;
     CK(cudaStreamUpdateCaptureDependencies(h->gs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     const long long l2 = h->nlaunch;
-    LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_stat));
+    LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_init, h->d_stat));
     LK(launch_update(h->gs, N, sc, state, h->Z));
     h->g_epi = h->nlaunch - l2;
     return IGA_OK;
@@ -753,6 +829,7 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->d_tot, 0, sizeof(long long) * kMaxVec, s));
   CK(cudaMemsetAsync(h->d_max, 0, sizeof(int) * kMaxVec, s));
+  CK(cudaMemsetAsync(h->d_init, 0, sizeof(double) * kMaxVec, s));
   CK(cudaMemsetAsync(h->d_stat, 0, sizeof(int) * 2, s));
   CK(cudaMemsetAsync(h->d_loop, 0, sizeof(int) * 2, s));
   CK(cudaEventRecord(h->ev_in, s));
@@ -762,7 +839,8 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
   CK(cudaStreamWaitEvent(s, h->ev_out, 0));
   long long tot[kMaxVec];
   int mx[kMaxVec], st[2], loop[2];
-  double rr[kMaxVec], bb[kMaxVec];
+  double rr[kMaxVec], bb[kMaxVec], ini[kMaxVec];
+  CK(cudaMemcpyAsync(ini, h->d_init, sizeof(ini), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(tot, h->d_tot, sizeof(tot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(mx, h->d_max, sizeof(mx), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(st, h->d_stat, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -777,6 +855,7 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
     stats->solves += k * nsteps;
     for (int j = 0; j < k; ++j) {
       stats->iters += tot[j];
+      stats->init_relres_sum += ini[j];
       stats->max_iters = std::max(stats->max_iters, mx[j]);
       const double rel = bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0;  // last step's solves
       stats->max_relres = std::max(stats->max_relres, rel);
@@ -859,7 +938,7 @@ void iga_destroy(iga_handle* h) {
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial);
-  dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.alpha); dfree(h->cs.beta);
+  dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
   dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
   if (h->h_nactive) cudaFreeHost(h->h_nactive);
   for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -870,7 +949,12 @@ void iga_destroy(iga_handle* h) {
   if (h->gbody) cudaStreamDestroy(h->gbody);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
-  dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_stat);
+  dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_init); dfree(h->d_stat);
+  dfree(h->ws_theta); dfree(h->ws_m); dfree(h->ws_v); dfree(h->ws_grad);
+  dfree(h->ws_E); dfree(h->ws_B1); dfree(h->ws_B2); dfree(h->ws_sc); dfree(h->ws_part);
+  dfree(h->ws_x); dfree(h->ws_act); dfree(h->ws_sx); dfree(h->ws_st);
+  dfree(h->ws_y); dfree(h->ws_dy); dfree(h->ws_loss); dfree(h->ws_lpart);
+  if (h->ws_work) cudaFree(h->ws_work);
   delete h;
 }
 
@@ -886,7 +970,7 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
   if (opt) h->opt = *opt;
   else iga_options_default(&h->opt);
   if (!(h->opt.tol >= 0.0) || h->opt.max_iter < 1 || h->opt.precond < 0 || h->opt.precond > 3 ||
-      h->opt.op_form < 0 || h->opt.op_form > 1 || h->opt.guess < 0 || h->opt.guess > 3) {
+      h->opt.op_form < 0 || h->opt.op_form > 1 || h->opt.guess < 0 || h->opt.guess > IGA_GUESS_LEARNED) {
     delete h;
     return fail(nullptr, IGA_EINVAL, "invalid options");
   }
@@ -978,7 +1062,7 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
     if (bad) return fail(h, IGA_EGEOMETRY, "det DF <= 0 at a quadrature point");
     // PCG scalars and reduction scratch
     CKS(dalloc(h, &h->partial, (size_t)3 * kMaxVec * kRedBlocks));
-    CKS(dalloc(h, &h->cs.bb, kMaxVec)); CKS(dalloc(h, &h->cs.rz, kMaxVec)); CKS(dalloc(h, &h->cs.rr, kMaxVec));
+    CKS(dalloc(h, &h->cs.bb, kMaxVec)); CKS(dalloc(h, &h->cs.rz, kMaxVec)); CKS(dalloc(h, &h->cs.rr, kMaxVec)); CKS(dalloc(h, &h->cs.rr0, kMaxVec));
     CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
     CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
     CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
@@ -1036,7 +1120,7 @@ int iga_set_precond(iga_handle* h, int precond) {
   return IGA_OK;
 }
 int iga_set_guess(iga_handle* h, int guess) {
-  if (!h || guess < 0 || guess > 3) return IGA_EINVAL;
+  if (!h || guess < 0 || guess > IGA_GUESS_LEARNED) return IGA_EINVAL;
   h->opt.guess = guess;
   return IGA_OK;
 }
@@ -1130,7 +1214,8 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
   for (int step = 0; step < nsteps; ++step) {
     const int guess = h->opt.guess;
     // steady state: replay the captured step (device-side PCG loop) for the remaining steps
-    const bool graph_ok = h->use_graphs && h->prof_class == IGA_PROF_OFF &&
+    const bool recording = guess == IGA_GUESS_LEARNED && h->ws_cap > 0;
+    const bool graph_ok = h->use_graphs && h->prof_class == IGA_PROF_OFF && !recording &&
                           (guess == IGA_GUESS_ZERO || guess == IGA_GUESS_TAYLOR || h->hist >= 2);
     if (graph_ok) {
       iga_handle::GraphKey key{};
@@ -1163,11 +1248,34 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
       else CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
       use_x0 = true;
     }
+    // learned guess: histories b^{n-1}, b^{n-2} (ws_B1, ws_B2) and Z^{n-1}, Z^{n-2} (Z, Z2)
+    const size_t kvec = sizeof(double) * k * N;
+    bool record = false;
+    if (guess == IGA_GUESS_LEARNED) {
+      CKS(ensure_ws_step(h, k));
+      if (h->hist >= 2) {
+        record = recording && h->ws_count + k <= h->ws_cap;
+        __nv_bfloat16* x = record ? h->ws_sx + (size_t)h->ws_count * 3 * N : h->ws_x;
+        CKS(learned_guess(h, s, k, x));
+        use_x0 = true;
+      } else if (h->hist == 1) {  // previous solution as the guess; histories move
+        CK(cudaMemcpyAsync(h->Z2, h->Z, kvec, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->ws_B2, h->ws_B1, kvec, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->ws_B1, h->rhs, kvec, cudaMemcpyDeviceToDevice, s));
+        use_x0 = true;
+      } else {
+        CK(cudaMemcpyAsync(h->ws_B1, h->rhs, kvec, cudaMemcpyDeviceToDevice, s));
+      }
+    }
     int its[kMaxVec];
     double rel[kMaxVec];
     CKS(solve(h, k, h->rhs, h->Z, use_x0, its, rel));
-    if (guess == IGA_GUESS_EXTRAP && h->hist == 0)
-      CK(cudaMemcpyAsync(h->Z2, h->Z, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, s));
+    if ((guess == IGA_GUESS_EXTRAP || guess == IGA_GUESS_LEARNED) && h->hist == 0)
+      CK(cudaMemcpyAsync(h->Z2, h->Z, kvec, cudaMemcpyDeviceToDevice, s));
+    if (record) {
+      CK(launch_ws_target(s, N, k, h->Z, h->ws_E, h->ws_sc, h->ws_st + (size_t)h->ws_count * N, &h->nlaunch));
+      h->ws_count += k;
+    }
     LK(launch_update(s, N, sc, state, h->Z));
     h->hist = std::min(h->hist + 1, 2);
     if (stats) {
@@ -1175,6 +1283,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
       stats->solves += k;
       for (int j = 0; j < k; ++j) {
         stats->iters += its[j];
+        stats->init_relres_sum += h->last_init[j];
         stats->max_iters = std::max(stats->max_iters, its[j]);
         stats->max_relres = std::max(stats->max_relres, rel[j]);
       }
@@ -1234,8 +1343,12 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
     return fail(h, IGA_EINVAL, "bad arguments");
   const long long N = h->N;
   cudaStream_t s = h->stream;
+  // Every allocation first: the band assembly grows the PCG workspace, whose
+  // buffers are held by pointer below.
+  if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
   CKS(ensure_step_ws(h, 2));
   CKS(ensure_cg_ws(h, 2));
+  CKS(ensure_op_ws(h, 1));
   // start from a checkerboard (close to the highest mode) times a smooth bump
   std::vector<double> x0((size_t)N);
   for (long long i = 0; i < N; ++i) {
@@ -1285,6 +1398,194 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
   *lambda_max = lam;
   *tau_crit = std::sqrt(theta_crit(rho_inf) / lam);
   return IGA_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// learned warm start
+// ---------------------------------------------------------------------------
+namespace {
+
+uint64_t splitmix64(uint64_t& state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+double uniform01(uint64_t& state) { return (double)(splitmix64(state) >> 11) * (1.0 / 9007199254740992.0); }
+
+int ws_upload_params(iga_handle* h, const float* theta) {
+  CKS(ensure_ws_step(h, 1));
+  CK(cudaMemcpy(h->ws_theta, theta, sizeof(float) * IGA_NET_NPARAM, cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->ws_m, 0, sizeof(float) * IGA_NET_NPARAM));
+  CK(cudaMemset(h->ws_v, 0, sizeof(float) * IGA_NET_NPARAM));
+  h->ws_adam_t = 0;
+  h->ws_params = true;
+  return IGA_OK;
+}
+
+int net_args_ok(int n1, int n2, int n3, int nb) { return net_grid_ok(NetGrid{n1, n2, n3}, nb); }
+
+}  // namespace
+
+int iga_ws_init_params(iga_handle* h, unsigned long long seed) {
+  CKS(check_handle(h));
+  std::vector<float> th(IGA_NET_NPARAM, 0.0f);
+  uint64_t st = seed;
+  const double b1 = 1.0 / std::sqrt(81.0), b2 = 1.0 / std::sqrt(432.0);
+  for (int i = 0; i < 1296; ++i) th[i] = (float)((2.0 * uniform01(st) - 1.0) * b1);
+  for (int i = 1312; i < 1744; ++i) th[i] = (float)((2.0 * uniform01(st) - 1.0) * b2);
+  CKS(ws_upload_params(h, th.data()));
+  h->ws_trained = false;
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_ws_set_params(iga_handle* h, const float* theta_host) {
+  CKS(check_handle(h));
+  if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
+  CKS(ws_upload_params(h, theta_host));
+  h->ws_trained = true;
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_ws_get_params(iga_handle* h, float* theta_host) {
+  CKS(check_handle(h));
+  if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
+  if (!h->ws_params) return fail(h, IGA_EINVAL, "no parameters yet (iga_ws_init_params, iga_ws_train or iga_ws_set_params)");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(theta_host, h->ws_theta, sizeof(float) * IGA_NET_NPARAM, cudaMemcpyDeviceToHost));
+  return IGA_OK;
+}
+
+int iga_ws_collect(iga_handle* h, int capacity) {
+  CKS(check_handle(h));
+  if (capacity < 0) return fail(h, IGA_EINVAL, "capacity < 0");
+  CK(cudaStreamSynchronize(h->stream));
+  dfree(h->ws_sx);
+  dfree(h->ws_st);
+  h->ws_cap = h->ws_count = 0;
+  if (capacity == 0) return IGA_OK;
+  CKS(dalloc(h, &h->ws_sx, (size_t)capacity * 3 * h->N));
+  CKS(dalloc(h, &h->ws_st, (size_t)capacity * h->N));
+  h->ws_cap = capacity;
+  return IGA_OK;
+}
+
+int iga_ws_samples(iga_handle* h, int* count) {
+  CKS(check_handle(h));
+  if (!count) return fail(h, IGA_EINVAL, "count is NULL");
+  *count = h->ws_count;
+  return IGA_OK;
+}
+
+int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* loss_first,
+                 double* loss_last) {
+  CKS(check_handle(h));
+  if (epochs < 1 || !(lr > 0.0)) return fail(h, IGA_EINVAL, "epochs < 1 or lr <= 0");
+  if (h->ws_count < 1) return fail(h, IGA_EINVAL, "no recorded samples (iga_ws_collect, then iga_step)");
+  const NetGrid g = net_grid_of(h);
+  if (!net_grid_ok(g, 1)) return fail(h, IGA_EINVAL, "grid beyond the network kernels' launch limits");
+  if (!h->ws_params) CKS(iga_ws_init_params(h, seed));
+  const long long N = h->N;
+  const int ns = h->ws_count;
+  const long long nupd = (long long)epochs * ns;
+  if (!h->ws_y) {
+    CKS(dalloc(h, &h->ws_y, (size_t)N));
+    CKS(dalloc(h, &h->ws_dy, (size_t)N));
+    CKS(dalloc(h, &h->ws_lpart, (size_t)kRedBlocks));
+    void* w = nullptr;
+    const cudaError_t e = cudaMalloc(&w, net_workspace_bytes(g, 1));
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, IGA_ENOMEM, "network workspace"); }
+    h->ws_work = w;
+  }
+  if (h->ws_loss_cap < nupd) {
+    CKS(dalloc(h, &h->ws_loss, (size_t)nupd));
+    h->ws_loss_cap = nupd;
+  }
+  cudaStream_t s = h->stream;
+  std::vector<int> order(ns);
+  uint64_t st = seed ^ 0xA0761D6478BD642FULL;
+  long long u = 0;
+  for (int e = 0; e < epochs; ++e) {
+    for (int i = 0; i < ns; ++i) order[i] = i;
+    for (int i = ns - 1; i > 0; --i) {  // Fisher-Yates
+      const int j = (int)(splitmix64(st) % (uint64_t)(i + 1));
+      std::swap(order[i], order[j]);
+    }
+    for (int i = 0; i < ns; ++i, ++u) {
+      const __nv_bfloat16* x = h->ws_sx + (size_t)order[i] * 3 * N;
+      const float* t = h->ws_st + (size_t)order[i] * N;
+      CK(launch_net_forward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_y, nullptr, nullptr, nullptr, &h->nlaunch));
+      CK(launch_net_loss(s, N, h->ws_y, t, h->ws_dy, h->ws_lpart, h->ws_loss + u, &h->nlaunch));
+      CK(launch_net_backward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_dy, h->ws_grad, h->ws_work, &h->nlaunch));
+      CK(launch_net_adam(s, IGA_NET_NPARAM, h->ws_theta, h->ws_grad, h->ws_m, h->ws_v, ++h->ws_adam_t, lr,
+                         &h->nlaunch));
+    }
+  }
+  std::vector<double> L((size_t)nupd);
+  CK(cudaMemcpyAsync(L.data(), h->ws_loss, sizeof(double) * nupd, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double f = 0.0, l = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    f += L[i];
+    l += L[(size_t)(epochs - 1) * ns + i];
+  }
+  if (loss_first) *loss_first = f / ns;
+  if (loss_last) *loss_last = l / ns;
+  h->ws_trained = true;
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_ws_features(iga_handle* h, int k, const double* b, double* b1, double* b2, double* z1, double* z2,
+                    unsigned short* x, double* E, double* scales) {
+  CKS(check_handle(h));
+  if (k < 1 || k > kMaxVec || !b || !b1 || !b2 || !z1 || !z2 || !x || !E || !scales)
+    return fail(h, IGA_EINVAL, "bad arguments");
+  CKS(ensure_ws_step(h, 1));
+  cudaStream_t s = h->stream;
+  CK(launch_ws_features(s, h->N, k, b, b1, b2, h->Dm, z1, z2, reinterpret_cast<__nv_bfloat16*>(x), E, h->ws_part,
+                        h->ws_sc, &h->nlaunch));
+  CK(cudaMemcpyAsync(scales, h->ws_sc, sizeof(double) * 2 * k, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return IGA_OK;
+}
+
+int iga_net_forward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
+                    unsigned short* act, float* y, void* stream) {
+  if (!net_args_ok(n1, n2, n3, nb) || !x || !theta || !act || !y) return IGA_EINVAL;
+  long long nl = 0;
+  const cudaError_t e = launch_net_forward((cudaStream_t)stream, NetGrid{n1, n2, n3}, nb,
+                                           reinterpret_cast<const __nv_bfloat16*>(x), theta,
+                                           reinterpret_cast<__nv_bfloat16*>(act), y, nullptr, nullptr, nullptr, &nl);
+  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
+}
+
+unsigned long long iga_net_workspace_bytes(int n1, int n2, int n3, int nb) {
+  if (!net_args_ok(n1, n2, n3, nb)) return 0;
+  return net_workspace_bytes(NetGrid{n1, n2, n3}, nb);
+}
+
+int iga_net_backward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
+                     const unsigned short* act, const float* dy, float* grad, void* work,
+                     unsigned long long work_bytes, void* stream) {
+  if (!net_args_ok(n1, n2, n3, nb) || !x || !theta || !act || !dy || !grad || !work) return IGA_EINVAL;
+  const NetGrid g{n1, n2, n3};
+  if (work_bytes < net_workspace_bytes(g, nb)) return IGA_EINVAL;
+  long long nl = 0;
+  const cudaError_t e = launch_net_backward((cudaStream_t)stream, g, nb, reinterpret_cast<const __nv_bfloat16*>(x),
+                                            theta, reinterpret_cast<const __nv_bfloat16*>(act), dy, grad, work, &nl);
+  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
+}
+
+int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int step, double lr, void* stream) {
+  if (n < 1 || step < 1 || !(lr > 0.0) || !theta || !grad || !m || !v) return IGA_EINVAL;
+  long long nl = 0;
+  const cudaError_t e = launch_net_adam((cudaStream_t)stream, n, theta, grad, m, v, step, lr, &nl);
+  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
 }
 
 }  // extern "C"

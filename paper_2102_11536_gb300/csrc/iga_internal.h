@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -127,6 +128,7 @@ struct CgScalars {  // device arrays, one entry per system
   double* bb;      // ||b||^2
   double* rz;      // r.z (current)
   double* rr;      // ||r||^2
+  double* rr0;     // ||r||^2 of the initial guess
   double* alpha;
   double* beta;
   int* active;     // 1 while iterating
@@ -169,7 +171,8 @@ cudaError_t launch_extrap(cudaStream_t s, long long n, double* Z, double* Z2);
 // device-side loop control of the captured PCG (kernels_vec.cu)
 cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const int* nactive, int* loop, int max_iter,
                             int reset);
-cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, int* stat);
+// tot += iterations, mx = max iterations, init += ||b - M x0|| / ||b||, stat = first error / unconverged
+cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, double* init, int* stat);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
 
 // BF16 tensor-core mode product (kernels_tc.cu): B is the BF16 matrix arranged by
@@ -190,6 +193,37 @@ cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const in
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,
                                  int nvec, const double* y, long long vs, double* A);
+
+// Learned initial guess (kernels_net.cu). Fields on the n1 x n2 x n3 interior grid;
+// x [nb][3][N] BF16 features, act [nb][16][N] BF16 hidden layer, theta the FP32
+// parameter vector (IGA_NET_NPARAM). nl counts the kernels launched.
+struct NetGrid {
+  int n1, n2, n3;
+};
+long long net_blocks(const NetGrid& g, int nb);
+size_t net_workspace_bytes(const NetGrid& g, int nb);  // backward: dh and per-block partials
+bool net_grid_ok(const NetGrid& g, int nb);
+// act = R(relu(W1 * x + b1)); y = W2 * act + b2 (y nullable); if Z != nullptr also
+// Z = E + s0[2 s] y for sample s (the guess).
+cudaError_t launch_net_forward(cudaStream_t s, const NetGrid& g, int nb, const __nv_bfloat16* x, const float* theta,
+                               __nv_bfloat16* act, float* y, double* Z, const double* E, const double* s0,
+                               long long* nl);
+// dy = (y - t) / N; *loss = sum (y - t)^2 / (2 N); part: kRedBlocks doubles.
+cudaError_t launch_net_loss(cudaStream_t s, long long N, const float* y, const float* t, float* dy, double* part,
+                            double* loss, long long* nl);
+// grad = d(sum_s sum_p dy y)/d theta over nb samples; work: net_workspace_bytes.
+cudaError_t launch_net_backward(cudaStream_t s, const NetGrid& g, int nb, const __nv_bfloat16* x, const float* theta,
+                                const __nv_bfloat16* act, const float* dy, float* grad, void* work, long long* nl);
+cudaError_t launch_net_adam(cudaStream_t s, int n, float* theta, const float* grad, float* m, float* v, long long step,
+                            double lr, long long* nl);
+// Features of k solves (x [k][3][N], E, scales sc [k][2] = (s0, s1)); moves the
+// histories b2 <- b1 <- b, z2 <- z1 <- E. part: 2 k kRedBlocks doubles.
+cudaError_t launch_ws_features(cudaStream_t s, long long N, int k, const double* b, double* b1, double* b2,
+                               const double* D, double* z1, double* z2, __nv_bfloat16* x, double* E, double* part,
+                               double* sc, long long* nl);
+// t [k][N] = (Z - E) / s0, FP32.
+cudaError_t launch_ws_target(cudaStream_t s, long long N, int k, const double* Z, const double* E, const double* sc,
+                             float* t, long long* nl);
 
 // Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
 constexpr long long kNoAllocMaxElems = 1LL << 20;

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_cg_init(int nvec, const double*
     const double bb = sb[v], rr = sr[v];
     c.bb[v] = bb;
     c.rr[v] = rr;
+    c.rr0[v] = rr;
     c.iters[v] = 0;
     c.status[v] = 0;
     int act = (bb > 0.0) && (rr > tol2 * bb);
@@ -400,18 +401,19 @@ cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const
 
 // After a solve: total and largest iteration counts per system slot, the first
 // error status, and whether any system stopped unconverged.
-__global__ void k_accum(int nvec, CgScalars c, long long* tot, int* mx, int* stat) {
+__global__ void k_accum(int nvec, CgScalars c, long long* tot, int* mx, double* init, int* stat) {
   const int v = threadIdx.x;
   if (v < nvec) {
     tot[v] += c.iters[v];
+    if (c.bb[v] > 0.0) init[v] += sqrt(c.rr0[v] / c.bb[v]);
     if (c.iters[v] > mx[v]) mx[v] = c.iters[v];
     if (c.status[v] != 0) atomicCAS(stat, 0, c.status[v]);
   }
   if (v == 0 && *c.nactive > 0) stat[1] = 1;
 }
 
-cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, int* stat) {
-  k_accum<<<1, 32, 0, s>>>(nvec, c, tot, mx, stat);
+cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, double* init, int* stat) {
+  k_accum<<<1, 32, 0, s>>>(nvec, c, tot, mx, init, stat);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ def _declared():
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(hdr).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(iga_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:(?:const|unsigned|signed|long|short)\s+)*\w+\s*\*?\s*(iga_\w+)\s*\(", text, flags=re.M):
             names.add(m.group(1))
     return names
 
@@ -73,3 +73,19 @@ def test_create_rejects_bad_knots_before_device_use(lib):
     with pytest.raises(iga.IgaError) as e:
         iga.Patch([9, 2], [np.zeros(20), np.zeros(6)], np.zeros((9, 2)))
     assert e.value.status == iga.EINVAL
+
+
+def test_network_entry_points_validate_before_any_device_work(lib):
+    assert lib.iga_net_forward(0, 4, 4, 1, None, None, None, None, None) == iga.EINVAL
+    assert lib.iga_net_forward(4, 4, 4, 0, 1, 1, 1, 1, None) == iga.EINVAL
+    assert lib.iga_net_forward(4, 4, 4, 1, None, 1, 1, 1, None) == iga.EINVAL
+    assert lib.iga_net_workspace_bytes(0, 1, 1, 1) == 0
+    # dh [nb][16][N] floats plus per-block partials (1312 + 433 floats per 16x16x4 tile)
+    n1, n2, n3 = 19, 21, 9
+    blocks = 2 * 2 * 3
+    assert lib.iga_net_workspace_bytes(n1, n2, n3, 1) == 4 * (16 * n1 * n2 * n3 + blocks * (1312 + 433))
+    assert lib.iga_net_backward(4, 4, 4, 1, 1, 1, 1, 1, 1, 1, 10, None) == iga.EINVAL  # work too small
+    assert lib.iga_net_adam(0, 1, 1, 1, 1, 1, 1e-3, None) == iga.EINVAL
+    assert lib.iga_net_adam(8, 1, 1, 1, 1, 0, 1e-3, None) == iga.EINVAL
+    assert lib.iga_net_adam(8, 1, 1, 1, 1, 1, 0.0, None) == iga.EINVAL
+    assert iga.GUESSES["learned"] == 4 and iga.NET_NPARAM == 1745

@@ -179,3 +179,12 @@ def test_features_guard_zero_scales():
     zero = np.zeros(8)
     x, s0, s1, E = net.features(zero, zero, zero, np.ones(8), zero, zero, shape)
     assert s0 == 1.0 and s1 == 1.0 and not x.any() and not E.any()
+
+
+def test_backward_with_given_hidden_layer_equals_recomputed():
+    rng = np.random.default_rng(6)
+    x = net.bf16_round(rng.standard_normal((3, 3, 4, 5)))
+    theta = net.bf16_round(_rand_theta(rng))
+    dy = rng.standard_normal((3, 4, 5))
+    _, a, _ = net.forward(x, theta)
+    assert np.array_equal(net.backward(x, theta, dy), net.backward(x, theta, dy, act=a))
