@@ -18,6 +18,11 @@ Forms measured (all FP64 state, FP64 PCG residuals and dot products, same tol):
   mixed_taylor    as mixed_fp32 with the Taylor predictor as initial guess
   mixed_bf16      assembled band K, M; BF16 preconditioner on the tensor cores (tcgen05,
                   FP32 accumulation; flexible PCG); zero guess
+  mixed_extrap    as mixed_fp32 with 2 Z^{n-1} - Z^{n-2} as initial guess
+  mixed_learned   as mixed_fp32 with the learned warm start: the BF16 convolutional
+                  network, trained by the library's own kernels on the solves of the
+                  first --train-steps steps (set-up, not timed), corrects the
+                  extrapolated guess
   mixed_fp32_hostloop  mixed_fp32 with the PCG loop driven from the host (one
                   synchronisation per iteration) instead of the captured graph
 Every other form replays one captured CUDA graph per step whose PCG loop runs on
@@ -65,6 +70,10 @@ FORMS = [
      "k_band_spmv (assembled symmetric band product, mass)"),
     ("mixed_fp32_hostloop", dict(op_form="assembled", precond="fp32", guess="zero", graphs=False), "band_mass",
      "k_band_spmv (assembled symmetric band product, mass)"),
+    ("mixed_extrap", dict(op_form="assembled", precond="fp32", guess="extrap"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+    ("mixed_learned", dict(op_form="assembled", precond="fp32", guess="learned"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
 ]
 
 # DRAM traffic per launch of a profiled kernel from an ncu capture, keyed by
@@ -88,6 +97,9 @@ def parse_args():
     ap.add_argument("--forms", default=",".join(f[0] for f in FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--train-steps", type=int, default=200, help="steps whose solves train the warm start")
+    ap.add_argument("--train-epochs", type=int, default=10)
+    ap.add_argument("--train-lr", type=float, default=2e-3)
     return ap.parse_args()
 
 
@@ -238,6 +250,30 @@ def time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class):
     return total_ms, stats, prof
 
 
+def train_warm_start(patch, torch, w, dt, state, u0, v0, args):
+    """Record the solves of the first args.train_steps steps (after two steps of
+    history) and train the warm-start network on them; returns a summary."""
+    patch.set_op_form("assembled")
+    patch.set_precond("fp32")
+    patch.set_guess("learned")
+    patch.set_graphs(True)
+    patch.state_init(w.k, u0, v0, state)
+    nrec = w.k * args.train_steps
+    patch.ws_collect(nrec)
+    t0 = time.perf_counter()
+    patch.step(state, w.k, w.rho, dt, args.train_steps + 2)
+    torch.cuda.synchronize()
+    rec_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = patch.ws_train(args.train_epochs, args.train_lr, seed=0)
+    train_s = time.perf_counter() - t0
+    patch.ws_collect(0)
+    return {"recorded_steps": args.train_steps, "samples": nrec, "epochs": args.train_epochs, "lr": args.train_lr,
+            "loss_per_epoch": losses, "lr_schedule": "cosine decay to 0 over the updates",
+            "record_s": rec_s, "train_s": train_s,
+            "note": "set-up outside the timed region; the timed run starts from the initial state"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -279,6 +315,9 @@ def run_ours(args):
     wanted = args.forms.split(",")
     results = {}
     finals = {}
+    warm = None
+    if "mixed_learned" in wanted:
+        warm = train_warm_start(patch, torch, w, dt, state, u0, v0, args)
     sampler = ClockSampler(gpu_index_for(local_rank))
     if pg:
         pg.barrier()
@@ -314,6 +353,7 @@ def run_ours(args):
             "ms_per_step": total_ms / args.steps,
             "pcg_iters_per_step": stats.iters / args.steps,
             "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
+            "mean_initial_relres": stats.init_relres_sum / max(stats.solves, 1),
             "gpu_launches": int(stats.launches),
             "precond_ms_per_application": pc_ms / max(pc_n, 1),
             "precond_applications_per_step": pc_n / 5.0,
@@ -416,7 +456,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": 3 * k * N * 8,
                 "api": "iga_step_host (state in pinned host memory, copied in and out every step), form " + head},
         "clocks": clocks,
-        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s},
+        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s,
+                  "warm_start_training": warm},
     }
     if not args.no_cpu_baseline and world == 1:
         base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)

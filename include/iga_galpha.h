@@ -305,14 +305,14 @@ int iga_ws_collect(iga_handle* h, int capacity);
 int iga_ws_samples(iga_handle* h, int* count);
 /*
  * iga_ws_train -- `epochs` passes of Adam over the recorded samples (one sample
- * per update, order a seeded permutation per epoch, learning rate lr), on the
- * device with the library's forward and backward kernels. loss_first /
- * loss_last (host, may be NULL) receive the mean loss of the first and last
- * epoch. Parameters not yet set are first drawn by iga_ws_init_params(seed).
- * Afterwards IGA_GUESS_LEARNED uses the trained network. IGA_EINVAL without samples.
+ * per update, order a seeded permutation per epoch), on the device with the
+ * library's forward and backward kernels. The learning rate of update u of U
+ * follows a cosine decay, lr (1 + cos(pi u / U)) / 2. epoch_loss (host, `epochs`
+ * doubles, may be NULL) receives the mean loss of each epoch. Parameters not yet
+ * set are first drawn by iga_ws_init_params(seed). Afterwards IGA_GUESS_LEARNED
+ * uses the trained network. IGA_EINVAL without samples.
  */
-int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* loss_first,
-                 double* loss_last);
+int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* epoch_loss);
 /* Draw the parameters: weights uniform in +-1/sqrt(fan_in) (81 for W1, 432 for W2)
  * from a splitmix64 stream seeded by seed, biases zero; resets Adam's moments. */
 int iga_ws_init_params(iga_handle* h, unsigned long long seed);

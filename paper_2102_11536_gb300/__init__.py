@@ -89,7 +89,7 @@ def lib():
         "iga_profile_read": (ctypes.c_int, [H, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]),
         "iga_ws_collect": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_ws_samples": (ctypes.c_int, [H, ip]),
-        "iga_ws_train": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong, dp, dp]),
+        "iga_ws_train": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong, dp]),
         "iga_ws_init_params": (ctypes.c_int, [H, ctypes.c_ulonglong]),
         "iga_ws_get_params": (ctypes.c_int, [H, vp]),
         "iga_ws_set_params": (ctypes.c_int, [H, vp]),
@@ -366,11 +366,11 @@ class Patch:
         return n.value
 
     def ws_train(self, epochs, lr=1e-3, seed=0):
-        """Adam over the recorded samples; returns (mean loss of the first epoch, of the last)."""
-        a = ctypes.c_double()
-        b = ctypes.c_double()
-        self._chk(lib().iga_ws_train(self.h, epochs, lr, seed, ctypes.byref(a), ctypes.byref(b)), "iga_ws_train")
-        return a.value, b.value
+        """Adam over the recorded samples (cosine-decayed learning rate); returns the
+        mean loss of every epoch."""
+        out = (ctypes.c_double * epochs)()
+        self._chk(lib().iga_ws_train(self.h, epochs, lr, seed, out), "iga_ws_train")
+        return list(out)
 
     def ws_init_params(self, seed=0):
         self._chk(lib().iga_ws_init_params(self.h, seed), "iga_ws_init_params")

@@ -1481,8 +1481,7 @@ int iga_ws_samples(iga_handle* h, int* count) {
   return IGA_OK;
 }
 
-int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* loss_first,
-                 double* loss_last) {
+int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* epoch_loss) {
   CKS(check_handle(h));
   if (epochs < 1 || !(lr > 0.0)) return fail(h, IGA_EINVAL, "epochs < 1 or lr <= 0");
   if (h->ws_count < 1) return fail(h, IGA_EINVAL, "no recorded samples (iga_ws_collect, then iga_step)");
@@ -1521,20 +1520,20 @@ int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, 
       CK(launch_net_forward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_y, nullptr, nullptr, nullptr, &h->nlaunch));
       CK(launch_net_loss(s, N, h->ws_y, t, h->ws_dy, h->ws_lpart, h->ws_loss + u, &h->nlaunch));
       CK(launch_net_backward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_dy, h->ws_grad, h->ws_work, &h->nlaunch));
-      CK(launch_net_adam(s, IGA_NET_NPARAM, h->ws_theta, h->ws_grad, h->ws_m, h->ws_v, ++h->ws_adam_t, lr,
+      const double lr_u = lr * 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)u / (double)nupd));
+      CK(launch_net_adam(s, IGA_NET_NPARAM, h->ws_theta, h->ws_grad, h->ws_m, h->ws_v, ++h->ws_adam_t, lr_u,
                          &h->nlaunch));
     }
   }
   std::vector<double> L((size_t)nupd);
   CK(cudaMemcpyAsync(L.data(), h->ws_loss, sizeof(double) * nupd, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  double f = 0.0, l = 0.0;
-  for (int i = 0; i < ns; ++i) {
-    f += L[i];
-    l += L[(size_t)(epochs - 1) * ns + i];
-  }
-  if (loss_first) *loss_first = f / ns;
-  if (loss_last) *loss_last = l / ns;
+  if (epoch_loss)
+    for (int e = 0; e < epochs; ++e) {
+      double m = 0.0;
+      for (int i = 0; i < ns; ++i) m += L[(size_t)e * ns + i];
+      epoch_loss[e] = m / ns;
+    }
   h->ws_trained = true;
   drop_step_graph(h);
   return IGA_OK;

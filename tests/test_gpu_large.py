@@ -99,3 +99,47 @@ def test_cube128_forms_agree(c3):
     g.set_tol(w.tol, 500)
     e1 = _energy(g, ref)
     assert e1 <= e0 * (1 + 1e-4)
+
+
+def test_cube96_learned_warm_start():
+    """96^3 deformed cube, p = 3, k = 2, 16 random modes, 1000 steps: the network is
+    trained on the solves of the first 200 steps and then supplies the guesses of the
+    remaining 800, compared with the zero and the extrapolated guess on those steps."""
+    w = W.config("cube96_p3")
+    g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, op_form="assembled", precond="fp32")
+    lam, tc = g.cfl(w.rho, iters=30)
+    dt = 0.5 * tc
+    k = w.k
+    U0, V0 = w.initial()
+    u0 = torch.from_numpy(U0).to(DEV)
+    v0 = torch.from_numpy(V0).to(DEV)
+    state = torch.empty(3 * k * g.N, dtype=torch.float64, device=DEV)
+    n_train, n_total = 200, 1000
+    res = {}
+    for guess in ("learned", "extrap", "zero"):
+        g.set_guess(guess)
+        g.state_init(k, u0, v0, state)
+        if guess == "learned":
+            g.ws_collect(k * n_train)
+        g.step(state, k, w.rho, dt, n_train + 2)
+        if guess == "learned":
+            assert g.ws_samples() == k * n_train
+            losses = g.ws_train(10, 2e-3, seed=0)
+            print("cube96 training: mean loss per epoch", ["%.4g" % v for v in losses])
+            g.ws_collect(0)
+            assert losses[-1] < 0.5 * losses[0], losses
+        st = g.step(state, k, w.rho, dt, n_total - n_train - 2)
+        assert st.max_relres <= w.tol
+        res[guess] = (st, state.view(3 * k, g.N)[:2].cpu().numpy())
+    init = {n: r[0].init_relres_sum / r[0].solves for n, r in res.items()}
+    its = {n: r[0].iters / r[0].solves for n, r in res.items()}
+    print("cube96 held-out steps: mean initial residual", init, "iterations per solve", its)
+    assert init["learned"] < 0.7 * init["extrap"]
+    assert its["learned"] <= its["extrap"] <= its["zero"]
+    ref = res["zero"][1]
+    for n in ("learned", "extrap"):
+        for row in (0, 1):
+            err = np.linalg.norm(res[n][1][row] - ref[row]) / np.linalg.norm(ref[row])
+            print("cube96 %s vs zero guess after %d steps, row %d: %.3e" % (n, n_total, row, err))
+            assert err < 1e-7, (n, row, err)
+    g.close()
