@@ -352,6 +352,59 @@ int iga_net_backward(int n1, int n2, int n3, int nb, const unsigned short* x, co
 int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int step, double lr, void* stream);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Launch tuning and batches of independent patches (no counterpart in the paper:
+ * its multi-patch spaces are conforming and glued, Sec. 5.4; these patches share
+ * nothing).
+ * ---------------------------------------------------------------------------
+ */
+
+/* Band-product launch configuration of h (assembled operators): threads per block
+ * 128, 256 or 512 (0 = 256) and vectors per thread 1..4 sharing each coefficient
+ * load (0 = all of a call's vectors, at most 4). Every configuration computes
+ * each row with the same operations in the same order, so results are bitwise
+ * equal. IGA_EINVAL for other values. */
+int iga_set_band_config(iga_handle* h, int threads, int nv);
+
+/*
+ * iga_autotune -- time every band-product configuration (threads 128/256/512 x
+ * vectors per thread 1, 2, 4 up to nvec) on nvec vectors with h's assembled mass
+ * matrix (assembled first if needed): one warm-up launch, then reps launches
+ * between two CUDA events on h's stream. Keeps the fastest for h and returns it
+ * in threads / nv (host, may be NULL). 1 <= nvec <= 8, reps >= 1. Synchronises.
+ */
+int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv);
+
+typedef struct iga_batch iga_batch;
+
+/* iga_batch_create -- a batch of npatch >= 1 independent patches. The handles stay
+ * owned by the caller, must be on one device and must outlive the batch. */
+int iga_batch_create(int npatch, iga_handle* const* patches, iga_batch** out);
+void iga_batch_destroy(iga_batch* b);
+/* Message of the last failed batch call (empty if none). */
+const char* iga_batch_last_error(const iga_batch* b);
+
+/*
+ * iga_batch_step -- advance patch i (state states[i], device, layout of
+ * iga_state_init) by nsteps steps of size dt[i] (host array of npatch), with k
+ * and rho_inf common to the batch. One CUDA graph holds the step of every patch
+ * (Taylor predictor, batched K, the PCG loop as a device-side conditional node,
+ * stage update) as independent branches forked from and joined on one stream, so
+ * a single graph launch advances the whole batch by one step; the graph is
+ * captured once and replayed until a state pointer, a dt, an option or a
+ * workspace of a patch changes. Each patch keeps its own options (operator
+ * form, preconditioner, guess, tolerance, band configuration). Steps that need a
+ * patch's host-driven loop (a guess still without history, recording samples,
+ * profiling, graphs switched off) run through iga_step, one step for all patches
+ * at a time. Work is ordered after earlier work on every patch's stream and before
+ * later work on it. stats: host array of npatch entries (may be NULL), accumulated
+ * per patch. Synchronises. The first failing patch's status is returned and its
+ * message is in iga_batch_last_error.
+ */
+int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, const double* dt, int nsteps,
+                   iga_stats* stats);
+
+/*
  * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in
  * the paper; measurement aid): 8 independent FMA chains per thread, 4 blocks of 256
  * threads per SM, 2^14 iterations, averaged over 5 timed launches after 2

@@ -98,6 +98,13 @@ def lib():
         "iga_net_workspace_bytes": (ctypes.c_ulonglong, [ctypes.c_int] * 4),
         "iga_net_backward": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp, vp, vp, vp, ctypes.c_ulonglong, vp]),
         "iga_net_adam": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]),
+        "iga_set_band_config": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
+        "iga_autotune": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ip, ip]),
+        "iga_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(H), ctypes.POINTER(H)]),
+        "iga_batch_destroy": (None, [H]),
+        "iga_batch_last_error": (ctypes.c_char_p, [H]),
+        "iga_batch_step": (ctypes.c_int, [H, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
+                                          ctypes.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -115,7 +122,9 @@ def exported_symbols():
             "iga_state_init", "iga_step", "iga_step_host", "iga_profile", "iga_profile_read",
             "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma", "iga_set_graphs", "iga_ws_collect",
             "iga_ws_samples", "iga_ws_train", "iga_ws_init_params", "iga_ws_get_params", "iga_ws_set_params",
-            "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam"]
+            "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
+            "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
+            "iga_batch_step"]
 
 
 def fp64_fma_probe(device=0):
@@ -355,6 +364,18 @@ class Patch:
                                          ctypes.byref(by)), "iga_profile_read")
         return ms.value, n.value, fl.value, by.value
 
+    # -- launch tuning ------------------------------------------------------------
+    def set_band_config(self, threads=0, nv=0):
+        """Band-product launch configuration (threads per block, vectors per thread; 0 = default)."""
+        self._chk(lib().iga_set_band_config(self.h, threads, nv), "iga_set_band_config")
+
+    def autotune(self, nvec=2, reps=5):
+        """Time the band-product configurations on nvec vectors, keep the fastest; returns (threads, nv)."""
+        t = ctypes.c_int()
+        v = ctypes.c_int()
+        self._chk(lib().iga_autotune(self.h, nvec, reps, ctypes.byref(t), ctypes.byref(v)), "iga_autotune")
+        return t.value, v.value
+
     # -- learned warm start -------------------------------------------------------
     def ws_collect(self, capacity):
         """Record up to `capacity` (features, target) samples from later learned-guess steps."""
@@ -405,3 +426,48 @@ class Patch:
         self._chk(lib().iga_step_host(self.h, _ptr(state_host), k, rho, dt, nsteps, ctypes.byref(st)),
                   "iga_step_host")
         return st
+
+
+class Batch:
+    """Independent patches advanced together, one CUDA graph launch per batch step
+    (iga_batch_create / iga_batch_step). The Patch objects must outlive the batch."""
+
+    def __init__(self, patches):
+        self.patches = list(patches)
+        arr = (ctypes.c_void_p * len(self.patches))(*[p.h.value for p in self.patches])
+        b = ctypes.c_void_p()
+        rc = lib().iga_batch_create(len(self.patches), arr, ctypes.byref(b))
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_create")
+        self.b = b
+
+    def step(self, states, k, rho, dts, nsteps=1, stats=None):
+        """states: device float64 tensors (3k*N_i each); dts: per-patch step sizes.
+        Returns the per-patch Stats list (accumulated into `stats` if given)."""
+        n = len(self.patches)
+        if len(states) != n or len(dts) != n:
+            raise ValueError("one state and one dt per patch")
+        for st, p in zip(states, self.patches):
+            _check_dev(st, 3 * k * p.N, "state")
+        sp = (ctypes.c_void_p * n)(*[_ptr(t) for t in states])
+        dt = (ctypes.c_double * n)(*[float(v) for v in dts])
+        out = stats if stats is not None else [Stats() for _ in range(n)]
+        arr = (Stats * n)(*out)
+        rc = lib().iga_batch_step(self.b, sp, k, rho, dt, nsteps, arr)
+        for i in range(n):
+            ctypes.memmove(ctypes.addressof(out[i]), ctypes.addressof(arr[i]), ctypes.sizeof(Stats))
+        res = out
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_step: " + lib().iga_batch_last_error(self.b).decode())
+        return res
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().iga_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

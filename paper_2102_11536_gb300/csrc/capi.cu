@@ -32,6 +32,8 @@ struct iga_handle {
   long long* band_off = nullptr;  // [H] linear offsets of the stored slots
   int band_H = 0;
   bool band_ready = false;
+  int band_threads = 0, band_nv = 0;  // launch configuration of the band product (0 = default)
+  long long ws_gen = 0;               // bumped whenever an address a captured graph may hold changes
   double band_nnz = 0.0;          // nonzero couplings (for algorithmic flop counts)
   // operator workspace
   int ws_vec = 0;
@@ -203,6 +205,20 @@ void galpha_params(int k, double rho, double* alpha, double* beta, double* gamma
     beta[j - 1] = b;
     gamma[j - 1] = 0.5 - af + a;
   }
+}
+
+// Taylor coefficients tau^m / m! and the block parameters of one step.
+StepCoefs step_coefs(int k, double rho, double dt) {
+  StepCoefs sc{};
+  sc.k = k;
+  sc.tau = dt;
+  double fact = 1.0;
+  for (int m = 0; m < 3 * k; ++m) {
+    if (m > 0) fact *= m;
+    sc.c[m] = std::pow(dt, m) / fact;
+  }
+  galpha_params(k, rho, sc.alpha, sc.beta, sc.gamma);
+  return sc;
 }
 
 double theta_crit(double rho) { return 12.0 * (1.0 + rho) * (2.0 - rho) / (rho * rho - 5.0 * rho + 10.0); }
@@ -479,7 +495,8 @@ int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* act
   const int nact = active ? h->cur_active : nvec;
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, cls, &e));
-  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, A, active, nvec, x, y, h->N));
+  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, A, active, nvec, x, y, h->N, h->band_threads,
+                        h->band_nv));
   CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
@@ -690,6 +707,7 @@ int learned_guess(iga_handle* h, cudaStream_t s, int k, __nv_bfloat16* x) {
 // one time step as a CUDA graph, the PCG loop running on the device
 // ---------------------------------------------------------------------------
 void drop_step_graph(iga_handle* h) {
+  ++h->ws_gen;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   h->gexec = nullptr;
@@ -697,12 +715,9 @@ void drop_step_graph(iga_handle* h) {
   h->gvalid = false;
 }
 
-// Capture one step on h->gs: Taylor predictor, batched K, the solve's set-up, a
-// conditional while node whose body is one PCG iteration followed by the loop test
-// (k_set_cond: some system active and fewer than max_iter iterations), the
-// iteration statistics, and the stage update. Every buffer is sized beforehand:
-// nothing is allocated while capturing.
-int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
+// Everything a step capture uses, allocated beforehand (nothing is allocated while
+// capturing); drops the handle's own step graph.
+int prepare_capture(iga_handle* h, int k) {
   drop_step_graph(h);
   if (!h->gs) {
     CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
@@ -722,74 +737,80 @@ int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
   CKS(ensure_op_ws(h, k));
   if (h->opt.guess == IGA_GUESS_LEARNED) CKS(ensure_ws_step(h, k));
   if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
+  return IGA_OK;
+}
+
+// Capture one step into the capture that h->gs takes part in: Taylor predictor,
+// batched K, the solve's set-up, a conditional while node whose body is one PCG
+// iteration followed by the loop test (k_set_cond: some system active and fewer
+// than max_iter iterations), the iteration statistics, and the stage update.
+int capture_step(iga_handle* h, double* state, int k, const StepCoefs& sc) {
+  struct StreamSwap {
+    iga_handle* h;
+    cudaStream_t user;
+    ~StreamSwap() { h->stream = user; }
+  } swap{h, h->stream};
+  h->stream = h->gs;
   const long long N = h->N;
   const int guess = h->opt.guess;
-  cudaStream_t user = h->stream;
-  h->stream = h->gs;
-  cudaError_t e0 = cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal);
-  if (e0 != cudaSuccess) {
-    h->stream = user;
-    return fail(h, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e0));
+  const long long l0 = h->nlaunch;
+  LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr));
+  CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+  if (guess == IGA_GUESS_EXTRAP) LK(launch_extrap(h->gs, (long long)k * N, h->Z, h->Z2));
+  if (guess == IGA_GUESS_LEARNED) CKS(learned_guess(h, h->gs, k, h->ws_x));
+  CKS(solve_begin(h, k, h->rhs, h->Z, guess != IGA_GUESS_ZERO));
+  CKS(solve_prime(h, k));  // masked: no work for systems that start converged
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
+  LK(launch_set_cond(h->gs, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 1));
+  CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  h->g_pro = h->nlaunch - l0;
+  const long long l1 = h->nlaunch;
+  h->stream = h->gbody;
+  CK(cudaStreamBeginCaptureToGraph(h->gbody, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int brc = solve_iter_a(h, k, h->Z);
+  if (brc == IGA_OK) brc = solve_iter_b(h, k);
+  if (brc == IGA_OK) {
+    const cudaError_t be = launch_set_cond(h->gbody, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 0);
+    if (be != cudaSuccess) brc = fail(h, IGA_ECUDA, std::string("loop test: ") + cudaGetErrorString(be));
+    else ++h->nlaunch;
   }
-  auto capture = [&]() -> int {
-    const long long l0 = h->nlaunch;
-    LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr));
-    CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
-    if (guess == IGA_GUESS_EXTRAP) LK(launch_extrap(h->gs, (long long)k * N, h->Z, h->Z2));
-    if (guess == IGA_GUESS_LEARNED) CKS(learned_guess(h, h->gs, k, h->ws_x));
-    CKS(solve_begin(h, k, h->rhs, h->Z, guess != IGA_GUESS_ZERO));
-    CKS(solve_prime(h, k));  // masked: no work for systems that start converged
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
-    cudaGraphConditionalHandle hc;
-    CK(cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
-    LK(launch_set_cond(h->gs, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 1));
-    CK(cudaStreamGetCaptureInfo(h->gs, &cst, nullptr, &cg, &deps, nullptr, &nd));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hc;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
-    cudaGraph_t bg = cp.conditional.phGraph_out[0];
-    h->g_pro = h->nlaunch - l0;
-    const long long l1 = h->nlaunch;
-    h->stream = h->gbody;
-    CK(cudaStreamBeginCaptureToGraph(h->gbody, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int brc = solve_iter_a(h, k, h->Z);
-    if (brc == IGA_OK) brc = solve_iter_b(h, k);
-    if (brc == IGA_OK) {
-      const cudaError_t be = launch_set_cond(h->gbody, hc, h->cs.nactive, h->d_loop, h->opt.max_iter, 0);
-      if (be != cudaSuccess) brc = fail(h, IGA_ECUDA, std::string("loop test: ") + cudaGetErrorString(be));
-      else ++h->nlaunch;
-    }
-    cudaGraph_t bout = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(h->gbody, &bout);
-    h->stream = h->gs;
-    if (brc != IGA_OK) return brc;
-    if (ee != cudaSuccess) return fail(h, IGA_ECUDA, std::string("loop body capture: ") + cudaGetErrorString(ee));
-    h->g_body = h->nlaunch - l1;
-    CK(cudaStreamUpdateCaptureDependencies(h->gs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    const long long l2 = h->nlaunch;
-    LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_init, h->d_stat));
-    LK(launch_update(h->gs, N, sc, state, h->Z));
-    h->g_epi = h->nlaunch - l2;
-    return IGA_OK;
-  };
-  const int rc = capture();
-  cudaGraph_t g = nullptr;
-  const cudaError_t ee = cudaStreamEndCapture(h->gs, &g);
-  h->stream = user;
+  cudaGraph_t bout = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->gbody, &bout);
+  h->stream = h->gs;
+  if (brc != IGA_OK) return brc;
+  if (ee != cudaSuccess) return fail(h, IGA_ECUDA, std::string("loop body capture: ") + cudaGetErrorString(ee));
+  h->g_body = h->nlaunch - l1;
+  CK(cudaStreamUpdateCaptureDependencies(h->gs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  const long long l2 = h->nlaunch;
+  LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_init, h->d_stat));
+  LK(launch_update(h->gs, N, sc, state, h->Z));
+  h->g_epi = h->nlaunch - l2;
+  return IGA_OK;
+}
+
+// Instantiate the graph a capture produced (destroyed on failure).
+int instantiate(iga_handle* h, int rc, cudaError_t end_err, cudaGraph_t g, cudaGraph_t* graph,
+                cudaGraphExec_t* exec) {
   if (rc != IGA_OK) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
     return rc;
   }
-  if (ee != cudaSuccess) return fail(h, IGA_ECUDA, std::string("step capture: ") + cudaGetErrorString(ee));
+  if (end_err != cudaSuccess) return fail(h, IGA_ECUDA, std::string("step capture: ") + cudaGetErrorString(end_err));
   cudaGraphExec_t ge = nullptr;
   const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
   if (ie != cudaSuccess) {
@@ -797,8 +818,19 @@ int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
     cudaGetLastError();
     return fail(h, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
   }
-  h->graph = g;
-  h->gexec = ge;
+  *graph = g;
+  *exec = ge;
+  return IGA_OK;
+}
+
+int build_step_graph(iga_handle* h, double* state, int k, const StepCoefs& sc) {
+  CKS(prepare_capture(h, k));
+  const cudaError_t e0 = cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal);
+  if (e0 != cudaSuccess) return fail(h, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e0));
+  const int rc = capture_step(h, state, k, sc);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->gs, &g);
+  CKS(instantiate(h, rc, ee, g, &h->graph, &h->gexec));
   h->gvalid = true;
   return IGA_OK;
 }
@@ -808,35 +840,19 @@ bool same_key(const iga_handle::GraphKey& a, const iga_handle::GraphKey& b) {
          a.max_iter == b.max_iter && a.dt == b.dt && a.rho == b.rho && a.tol == b.tol;
 }
 
-// nsteps replays of the captured step on h->gs, ordered after earlier work on the
-// caller's stream and before later work on it; one host synchronisation at the end.
-int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCoefs& sc, int nsteps,
-                   iga_stats* stats) {
-  iga_handle::GraphKey key{};
-  key.state = state;
-  key.k = k;
-  key.op = h->opt.op_form;
-  key.prec = h->opt.precond;
-  key.guess = h->opt.guess;
-  key.max_iter = h->opt.max_iter;
-  key.dt = sc.tau;
-  key.rho = rho;
-  key.tol = h->opt.tol;
-  if (!h->gvalid || !same_key(key, h->gkey)) {
-    CKS(build_step_graph(h, state, k, sc));
-    h->gkey = key;
-  }
-  cudaStream_t s = h->stream;
+// Zero the device counters that the captured step accumulates into.
+int reset_graph_counters(iga_handle* h, cudaStream_t s) {
   CK(cudaMemsetAsync(h->d_tot, 0, sizeof(long long) * kMaxVec, s));
   CK(cudaMemsetAsync(h->d_max, 0, sizeof(int) * kMaxVec, s));
   CK(cudaMemsetAsync(h->d_init, 0, sizeof(double) * kMaxVec, s));
   CK(cudaMemsetAsync(h->d_stat, 0, sizeof(int) * 2, s));
   CK(cudaMemsetAsync(h->d_loop, 0, sizeof(int) * 2, s));
-  CK(cudaEventRecord(h->ev_in, s));
-  CK(cudaStreamWaitEvent(h->gs, h->ev_in, 0));
-  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(h->gexec, h->gs));
-  CK(cudaEventRecord(h->ev_out, h->gs));
-  CK(cudaStreamWaitEvent(s, h->ev_out, 0));
+  return IGA_OK;
+}
+
+// After nsteps replays (ordered before later work on s): launch count, history,
+// statistics and the error status of the solves. Synchronises s.
+int collect_graph_run(iga_handle* h, cudaStream_t s, int k, int nsteps, iga_stats* stats) {
   long long tot[kMaxVec];
   int mx[kMaxVec], st[2], loop[2];
   double rr[kMaxVec], bb[kMaxVec], ini[kMaxVec];
@@ -869,6 +885,39 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
     return fail(h, IGA_ENOT_CONVERGED, buf);
   }
   return IGA_OK;
+}
+
+iga_handle::GraphKey graph_key(const iga_handle* h, double* state, int k, double rho, double dt) {
+  iga_handle::GraphKey key{};
+  key.state = state;
+  key.k = k;
+  key.op = h->opt.op_form;
+  key.prec = h->opt.precond;
+  key.guess = h->opt.guess;
+  key.max_iter = h->opt.max_iter;
+  key.dt = dt;
+  key.rho = rho;
+  key.tol = h->opt.tol;
+  return key;
+}
+
+// nsteps replays of the captured step on h->gs, ordered after earlier work on the
+// caller's stream and before later work on it; one host synchronisation at the end.
+int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCoefs& sc, int nsteps,
+                   iga_stats* stats) {
+  const iga_handle::GraphKey key = graph_key(h, state, k, rho, sc.tau);
+  if (!h->gvalid || !same_key(key, h->gkey)) {
+    CKS(build_step_graph(h, state, k, sc));
+    h->gkey = key;
+  }
+  cudaStream_t s = h->stream;
+  CKS(reset_graph_counters(h, s));
+  CK(cudaEventRecord(h->ev_in, s));
+  CK(cudaStreamWaitEvent(h->gs, h->ev_in, 0));
+  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(h->gexec, h->gs));
+  CK(cudaEventRecord(h->ev_out, h->gs));
+  CK(cudaStreamWaitEvent(s, h->ev_out, 0));
+  return collect_graph_run(h, s, k, nsteps, stats);
 }
 
 }  // namespace
@@ -1201,15 +1250,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
   const long long N = h->N;
   cudaStream_t s = h->stream;
   CKS(ensure_step_ws(h, k));
-  StepCoefs sc{};
-  sc.k = k;
-  sc.tau = dt;
-  double fact = 1.0;
-  for (int m = 0; m < 3 * k; ++m) {
-    if (m > 0) fact *= m;
-    sc.c[m] = std::pow(dt, m) / fact;
-  }
-  galpha_params(k, rho_inf, sc.alpha, sc.beta, sc.gamma);
+  const StepCoefs sc = step_coefs(k, rho_inf, dt);
   const long long launches0 = h->nlaunch;
   for (int step = 0; step < nsteps; ++step) {
     const int guess = h->opt.guess;
@@ -1218,9 +1259,7 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
     const bool graph_ok = h->use_graphs && h->prof_class == IGA_PROF_OFF && !recording &&
                           (guess == IGA_GUESS_ZERO || guess == IGA_GUESS_TAYLOR || h->hist >= 2);
     if (graph_ok) {
-      iga_handle::GraphKey key{};
-      key.state = state; key.k = k; key.op = h->opt.op_form; key.prec = h->opt.precond; key.guess = guess;
-      key.max_iter = h->opt.max_iter; key.dt = dt; key.rho = rho_inf; key.tol = h->opt.tol;
+      const iga_handle::GraphKey key = graph_key(h, state, k, rho_inf, dt);
       if (!h->gvalid || !same_key(key, h->gkey)) {
         if (build_step_graph(h, state, k, sc) != IGA_OK) {
           h->use_graphs = false;  // capture refused: keep the host-driven loop for this handle
@@ -1585,6 +1624,271 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
   long long nl = 0;
   const cudaError_t e = launch_net_adam((cudaStream_t)stream, n, theta, grad, m, v, step, lr, &nl);
   return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
+}
+
+
+// ---------------------------------------------------------------------------
+// launch tuning and batches of independent patches
+// ---------------------------------------------------------------------------
+int iga_set_band_config(iga_handle* h, int threads, int nv) {
+  CKS(check_handle(h));
+  if (!(threads == 0 || threads == 128 || threads == 256 || threads == 512) || nv < 0 || nv > 4)
+    return fail(h, IGA_EINVAL, "threads must be 0, 128, 256 or 512 and nv 0..4");
+  h->band_threads = threads;
+  h->band_nv = nv;
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
+  CKS(check_handle(h));
+  if (nvec < 1 || nvec > kMaxVec || reps < 1) return fail(h, IGA_EINVAL, "need 1 <= nvec <= 8 and reps >= 1");
+  CKS(assemble_band(h));
+  CKS(ensure_cg_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->p, 0, sizeof(double) * nvec * h->N, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  const cudaError_t ec = cudaEventCreate(&e1);
+  if (ec != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, IGA_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ec));
+  }
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } ev{e0, e1};
+  const int cand_t[3] = {128, 256, 512};
+  const int cand_v[3] = {1, 2, 4};
+  int best_t = 256, best_v = 0;
+  float best = 1e30f;
+  for (int ti = 0; ti < 3; ++ti)
+    for (int vi = 0; vi < 3; ++vi) {
+      const int v = std::min(cand_v[vi], nvec);
+      if (vi > 0 && v == std::min(cand_v[vi - 1], nvec)) continue;  // same as the previous candidate
+      LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->Mband, nullptr, nvec, h->p, h->q, h->N, cand_t[ti], v));
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r)
+        LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->Mband, nullptr, nvec, h->p, h->q, h->N, cand_t[ti],
+                            v));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_t = cand_t[ti];
+        best_v = v;
+      }
+    }
+  h->band_threads = best_t;
+  h->band_nv = best_v;
+  drop_step_graph(h);
+  if (threads) *threads = best_t;
+  if (nv) *nv = best_v;
+  return IGA_OK;
+}
+
+}  // extern "C"
+
+struct iga_batch {
+  std::vector<iga_handle*> p;
+  int device = 0;
+  cudaStream_t s0 = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool gvalid = false;
+  std::vector<iga_handle::GraphKey> keys;
+  std::vector<long long> gens;
+  std::string err;
+};
+
+namespace {
+
+int bfail(iga_batch* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+void drop_batch_graph(iga_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->gvalid = false;
+}
+
+bool needs_host_loop(const iga_handle* h) {
+  const int g = h->opt.guess;
+  return !h->use_graphs || h->prof_class != IGA_PROF_OFF || (g == IGA_GUESS_LEARNED && h->ws_cap > 0) ||
+         !(g == IGA_GUESS_ZERO || g == IGA_GUESS_TAYLOR || h->hist >= 2);
+}
+
+// One graph: fork from b->s0 to every patch's capture stream, each patch's step,
+// join back on b->s0.
+int build_batch_graph(iga_batch* b, double* const* states, int k, double rho, const double* dt) {
+  drop_batch_graph(b);
+  const int np = (int)b->p.size();
+  for (int i = 0; i < np; ++i) {
+    const int rc = prepare_capture(b->p[i], k);
+    if (rc != IGA_OK) return bfail(b, rc, "patch " + std::to_string(i) + ": " + b->p[i]->err);
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  int rc = IGA_OK;
+  std::string msg;
+  e = cudaEventRecord(b->fork, b->s0);
+  for (int i = 0; i < np && rc == IGA_OK && e == cudaSuccess; ++i) {
+    iga_handle* h = b->p[i];
+    e = cudaStreamWaitEvent(h->gs, b->fork, 0);
+    if (e != cudaSuccess) break;
+    rc = capture_step(h, states[i], k, step_coefs(k, rho, dt[i]));
+    if (rc != IGA_OK) {
+      msg = "patch " + std::to_string(i) + ": " + h->err;
+      break;
+    }
+    e = cudaEventRecord(b->join[i], h->gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s0, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->s0, &g);
+  if (rc != IGA_OK || e != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (rc != IGA_OK) return bfail(b, rc, msg);
+    return bfail(b, IGA_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
+  }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return bfail(b, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  b->graph = g;
+  b->gexec = ge;
+  b->gvalid = true;
+  b->keys.resize(np);
+  b->gens.resize(np);
+  for (int i = 0; i < np; ++i) {
+    b->keys[i] = graph_key(b->p[i], states[i], k, rho, dt[i]);
+    b->gens[i] = b->p[i]->ws_gen;
+  }
+  return IGA_OK;
+}
+
+bool batch_graph_current(const iga_batch* b, double* const* states, int k, double rho, const double* dt) {
+  if (!b->gvalid) return false;
+  for (size_t i = 0; i < b->p.size(); ++i)
+    if (!same_key(b->keys[i], graph_key(b->p[i], states[i], k, rho, dt[i])) || b->gens[i] != b->p[i]->ws_gen)
+      return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iga_batch_create(int npatch, iga_handle* const* patches, iga_batch** out) {
+  if (!out) return IGA_EINVAL;
+  *out = nullptr;
+  if (npatch < 1 || !patches) return IGA_EINVAL;
+  for (int i = 0; i < npatch; ++i)
+    if (!patches[i] || patches[i]->opt.device != patches[0]->opt.device) return IGA_EINVAL;
+  iga_batch* b = new (std::nothrow) iga_batch;
+  if (!b) return IGA_ENOMEM;
+  b->p.assign(patches, patches + npatch);
+  b->device = patches[0]->opt.device;
+  b->join.assign(npatch, nullptr);
+  bool ok = cudaSetDevice(b->device) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < npatch; ++i)
+    ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    iga_batch_destroy(b);
+    return IGA_ECUDA;
+  }
+  *out = b;
+  return IGA_OK;
+}
+
+void iga_batch_destroy(iga_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  drop_batch_graph(b);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->s0) cudaStreamDestroy(b->s0);
+  delete b;
+}
+
+const char* iga_batch_last_error(const iga_batch* b) { return b ? b->err.c_str() : ""; }
+
+int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, const double* dt, int nsteps,
+                   iga_stats* stats) {
+  if (!b) return IGA_EINVAL;
+  b->err.clear();
+  const int np = (int)b->p.size();
+  if (!states || !dt || k < 1 || k > kMaxK || nsteps < 0 || !(rho_inf >= 0.0 && rho_inf <= 1.0))
+    return bfail(b, IGA_EINVAL, "bad arguments");
+  for (int i = 0; i < np; ++i)
+    if (!states[i] || !(dt[i] > 0.0)) return bfail(b, IGA_EINVAL, "patch " + std::to_string(i) + ": bad state or dt");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, IGA_ECUDA, "cudaSetDevice");
+  int done = 0;
+  auto host_steps = [&](int n) -> int {  // every patch through iga_step, one step at a time
+    for (int t = 0; t < n; ++t)
+      for (int i = 0; i < np; ++i) {
+        const int rc = iga_step(b->p[i], states[i], k, rho_inf, dt[i], 1, stats ? &stats[i] : nullptr);
+        if (rc != IGA_OK) return bfail(b, rc, "patch " + std::to_string(i) + ": " + b->p[i]->err);
+      }
+    return IGA_OK;
+  };
+  while (done < nsteps) {
+    bool any = false;
+    for (auto* h : b->p) any = any || needs_host_loop(h);
+    if (!any) break;
+    const int rc = host_steps(1);
+    if (rc != IGA_OK) return rc;
+    ++done;
+  }
+  const int n = nsteps - done;
+  if (n == 0) return IGA_OK;
+  if (!batch_graph_current(b, states, k, rho_inf, dt)) {
+    const int rc = build_batch_graph(b, states, k, rho_inf, dt);
+    if (rc != IGA_OK) return rc;
+  }
+  std::vector<long long> l0(np);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    iga_handle* h = b->p[i];
+    l0[i] = h->nlaunch;
+    if (reset_graph_counters(h, b->s0) != IGA_OK) return bfail(b, IGA_ECUDA, h->err);
+    e = cudaEventRecord(h->ev_in, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s0, h->ev_in, 0);
+  }
+  for (int t = 0; t < n && e == cudaSuccess; ++t) e = cudaGraphLaunch(b->gexec, b->s0);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, b->s0);
+  for (int i = 0; i < np && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->p[i]->stream, b->done, 0);
+  if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("batch replay: ") + cudaGetErrorString(e));
+  int first = IGA_OK;
+  for (int i = 0; i < np; ++i) {
+    iga_handle* h = b->p[i];
+    const int rc = collect_graph_run(h, b->s0, k, n, stats ? &stats[i] : nullptr);
+    if (stats) stats[i].launches += h->nlaunch - l0[i];
+    if (rc != IGA_OK && first == IGA_OK) {
+      first = rc;
+      b->err = "patch " + std::to_string(i) + ": " + h->err;
+    }
+  }
+  return first;
 }
 
 }  // extern "C"

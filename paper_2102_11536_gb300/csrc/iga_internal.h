@@ -187,8 +187,10 @@ void tc_arrange_bf16(int n, const double* Mat_ij, std::vector<uint16_t>& outbits
 
 // Assembled band form (kernels_band.cu): H stored slots (centre + upper half),
 // off[h] the linear offset of slot h, A [H][N].
+// threads: block size 128 / 256 / 512 (other = 256); nv: vectors per thread (0 = min(nvec, 4)).
 cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
-                             const int* active, int nvec, const double* x, double* y, long long vs);
+                             const int* active, int nvec, const double* x, double* y, long long vs, int threads,
+                             int nv);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,

@@ -21,8 +21,8 @@
 
 namespace iga {
 
-template <int NV>
-__global__ void __launch_bounds__(256) k_band_spmv(long long N, int H, const long long* __restrict__ off,
+template <int NV, int BS>
+__global__ void __launch_bounds__(BS) k_band_spmv(long long N, int H, const long long* __restrict__ off,
                                                    const double* __restrict__ A, const int* __restrict__ active,
                                                    int nvec, const double* __restrict__ x, double* __restrict__ y,
                                                    long long vs) {
@@ -122,18 +122,32 @@ static BandGeom make_geom(const int* n, const int* p) {
   return g;
 }
 
-cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
-                             const int* active, int nvec, const double* x, double* y, long long vs) {
-  const unsigned bx = (unsigned)((N + 255) / 256);
-  if (nvec <= 1) {
-    k_band_spmv<1><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
-  } else if (nvec == 2) {
-    k_band_spmv<2><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
-  } else if (nvec == 3) {
-    k_band_spmv<3><<<dim3(bx, 1), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
-  } else {
-    k_band_spmv<4><<<dim3(bx, (unsigned)((nvec + 3) / 4)), 256, 0, s>>>(N, H, off, A, active, nvec, x, y, vs);
+namespace {
+template <int BS>
+void band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, const double* A, const int* active,
+             int nvec, const double* x, double* y, long long vs) {
+  const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
+  switch (nv) {
+    case 1: k_band_spmv<1, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
+    case 2: k_band_spmv<2, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
+    case 3: k_band_spmv<3, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
+    default: k_band_spmv<4, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
   }
+}
+}  // namespace
+
+// threads: block size (128, 256 or 512; anything else = 256); nv: vectors per thread
+// sharing each coefficient load (1..4; 0 = min(nvec, 4)). Every configuration
+// computes each row with the same operations in the same order.
+cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
+                             const int* active, int nvec, const double* x, double* y, long long vs, int threads,
+                             int nv) {
+  if (nv <= 0) nv = nvec < 4 ? nvec : 4;
+  if (nv < 1) nv = 1;
+  if (nv > 4) nv = 4;
+  if (threads == 128) band_go<128>(s, nv, N, H, off, A, active, nvec, x, y, vs);
+  else if (threads == 512) band_go<512>(s, nv, N, H, off, A, active, nvec, x, y, vs);
+  else band_go<256>(s, nv, N, H, off, A, active, nvec, x, y, vs);
   return cudaGetLastError();
 }
 

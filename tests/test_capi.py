@@ -89,3 +89,15 @@ def test_network_entry_points_validate_before_any_device_work(lib):
     assert lib.iga_net_adam(8, 1, 1, 1, 1, 0, 1e-3, None) == iga.EINVAL
     assert lib.iga_net_adam(8, 1, 1, 1, 1, 1, 0.0, None) == iga.EINVAL
     assert iga.GUESSES["learned"] == 4 and iga.NET_NPARAM == 1745
+
+
+def test_tuning_and_batch_entry_points_validate(lib):
+    out = ctypes.c_void_p()
+    assert lib.iga_batch_create(0, None, ctypes.byref(out)) == iga.EINVAL
+    assert lib.iga_batch_create(1, None, ctypes.byref(out)) == iga.EINVAL
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.iga_batch_create(1, arr, ctypes.byref(out)) == iga.EINVAL
+    assert lib.iga_batch_step(None, None, 2, 0.5, None, 1, None) == iga.EINVAL
+    assert lib.iga_batch_last_error(None) == b""
+    assert lib.iga_set_band_config(None, 256, 2) == iga.EINVAL
+    assert lib.iga_autotune(None, 2, 3, None, None) == iga.EINVAL
