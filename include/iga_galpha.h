@@ -360,14 +360,14 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
  */
 
 /* Band-product launch configuration of h (assembled operators): threads per block
- * 128, 256 or 512 (0 = 256) and vectors per thread 1..4 sharing each coefficient
+ * 64, 128, 256 or 512 (0 = 256) and vectors per thread 1..4 sharing each coefficient
  * load (0 = all of a call's vectors, at most 4). Every configuration computes
  * each row with the same operations in the same order, so results are bitwise
  * equal. IGA_EINVAL for other values. */
 int iga_set_band_config(iga_handle* h, int threads, int nv);
 
 /*
- * iga_autotune -- time every band-product configuration (threads 128/256/512 x
+ * iga_autotune -- time every band-product configuration (threads 64/128/256/512 x
  * vectors per thread 1, 2, 4 up to nvec) on nvec vectors with h's assembled mass
  * matrix (assembled first if needed): one warm-up launch, then reps launches
  * between two CUDA events on h's stream. Keeps the fastest for h and returns it

@@ -30,6 +30,7 @@ struct iga_handle {
   double* Mband = nullptr;
   double* Kband = nullptr;
   long long* band_off = nullptr;  // [H] linear offsets of the stored slots
+  int* band_o12 = nullptr;        // [H] packed offsets along directions 1, 2
   int band_H = 0;
   bool band_ready = false;
   int band_threads = 0, band_nv = 0;  // launch configuration of the band product (0 = default)
@@ -397,28 +398,31 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     }
     return IGA_OK;
   }
-  if (h->opt.precond == IGA_PREC_BF16) {
-    // the same sequence on the tensor cores: BF16 operands, FP32 accumulation and intermediates
+  if (h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16) {
+    // the same sequence on the tensor cores: 16-bit operands, FP32 accumulation and intermediates
+    const int f16 = h->opt.precond == IGA_PREC_FP16;
     for (int a = 0; a < h->dim; ++a)
       if (!d[a].Btc[0])
-        return fail(h, IGA_EINVAL, "BF16 preconditioner needs at most 256 interior functions per direction");
+        return fail(h, IGA_EINVAL, "tensor-core preconditioner needs at most 256 interior functions per direction");
+    void* const* B[3] = {f16 ? d[0].Btc16 : d[0].Btc, f16 ? d[1].Btc16 : d[1].Btc,
+                         f16 ? d[2].Btc16 : d[2].Btc};
     float* f1 = reinterpret_cast<float*>(t1);
     float* f2 = reinterpret_cast<float*>(t2);
     const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
     const double* sc = h->scale;
     int* err = h->dflag + 1;
     if (d3) {
-      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].Btc[1], r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].Btc[1], f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].Btc[1], f2, 0, f1, 0, N, nullptr, nullptr, lam, n, err));
-      LK(launch_fd_mode_tc(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].Btc[0], f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].Btc[0], f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].Btc[0], f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n12}, nvec, active, B[0][1], f16, r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], n[2]}, nvec, active, B[1][1], f16, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[2], 2, {n01, n[2], n[2], 1}, nvec, active, B[2][1], f16, f2, 0, f1, 0, N, nullptr, nullptr, lam, n, err));
+      LK(launch_fd_mode_tc(s, n[2], 2, {n01, n[2], n[2], 1}, nvec, active, B[2][0], f16, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], n[2]}, nvec, active, B[1][0], f16, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n12}, nvec, active, B[0][0], f16, f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
     } else {
-      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].Btc[1], r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].Btc[1], f1, 0, f2, 0, N, nullptr, nullptr, lam, n, err));
-      LK(launch_fd_mode_tc(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].Btc[0], f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].Btc[0], f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n[1]}, nvec, active, B[0][1], f16, r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], 1}, nvec, active, B[1][1], f16, f1, 0, f2, 0, N, nullptr, nullptr, lam, n, err));
+      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], 1}, nvec, active, B[1][0], f16, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
+      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n[1]}, nvec, active, B[0][0], f16, f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
     }
     return IGA_OK;
   }
@@ -449,12 +453,15 @@ int assemble_band(iga_handle* h) {
   for (int a = 0; a < 3; ++a) S *= 2 * p3[a] + 1;
   const int centre = S / 2, H = S - centre;
   std::vector<long long> off(H);
+  std::vector<int> o12(H);
   for (int hh = 0; hh < H; ++hh) {
     const int sl = centre + hh;
     const int m0 = 2 * p3[0] + 1, m1 = 2 * p3[1] + 1;
     const int o0 = sl % m0 - p3[0], o1 = (sl / m0) % m1 - p3[1], o2 = sl / (m0 * m1) - p3[2];
     off[hh] = o0 + (long long)h->n[0] * (o1 + (long long)h->n[1] * o2);
+    o12[hh] = (o1 + 64) | ((o2 + 64) << 8);
   }
+  CKS(upload(h, &h->band_o12, o12));
   double nnz = 1.0;
   for (int a = 0; a < 3; ++a) nnz *= (double)h->n[a] * (2 * p3[a] + 1) - (double)p3[a] * (p3[a] + 1);
   CKS(upload(h, &h->band_off, off));
@@ -495,8 +502,8 @@ int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* act
   const int nact = active ? h->cur_active : nvec;
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, cls, &e));
-  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, A, active, nvec, x, y, h->N, h->band_threads,
-                        h->band_nv));
+  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, h->band_o12, h->n, A, active, nvec, x, y, h->N,
+                        h->band_threads, h->band_nv));
   CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
@@ -981,9 +988,11 @@ void iga_destroy(iga_handle* h) {
     dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32);
     for (int t = 0; t < 2; ++t)
       if (d.Btc[t]) { cudaFree(d.Btc[t]); d.Btc[t] = nullptr; }
+    for (int t = 0; t < 2; ++t)
+      if (d.Btc16[t]) { cudaFree(d.Btc16[t]); d.Btc16[t] = nullptr; }
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
-  dfree(h->Mband); dfree(h->Kband); dfree(h->band_off);
+  dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial);
@@ -1080,14 +1089,13 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
             Mt[(size_t)i * t.n + j] = t.evec[(size_t)j * t.n + i];
           }
         std::vector<uint16_t> bits;
-        tc_arrange_bf16(t.n, Mu.data(), bits);
-        uint16_t* p0 = nullptr;
-        CKS(upload(h, &p0, bits));
-        d.Btc[0] = p0;
-        tc_arrange_bf16(t.n, Mt.data(), bits);
-        uint16_t* p1 = nullptr;
-        CKS(upload(h, &p1, bits));
-        d.Btc[1] = p1;
+        for (int f16 = 0; f16 < 2; ++f16)
+          for (int tr = 0; tr < 2; ++tr) {
+            tc_arrange(t.n, tr ? Mt.data() : Mu.data(), f16 != 0, bits);
+            uint16_t* pb = nullptr;
+            CKS(upload(h, &pb, bits));
+            (f16 ? d.Btc16 : d.Btc)[tr] = pb;
+          }
       }
       CKS(upload(h, &d.U32, U32)); CKS(upload(h, &d.lam32, l32));
     }
@@ -1632,8 +1640,8 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
 // ---------------------------------------------------------------------------
 int iga_set_band_config(iga_handle* h, int threads, int nv) {
   CKS(check_handle(h));
-  if (!(threads == 0 || threads == 128 || threads == 256 || threads == 512) || nv < 0 || nv > 4)
-    return fail(h, IGA_EINVAL, "threads must be 0, 128, 256 or 512 and nv 0..4");
+  if (!(threads == 0 || threads == 64 || threads == 128 || threads == 256 || threads == 512) || nv < 0 || nv > 4)
+    return fail(h, IGA_EINVAL, "threads must be 0, 64, 128, 256 or 512 and nv 0..4");
   h->band_threads = threads;
   h->band_nv = nv;
   drop_step_graph(h);
@@ -1658,19 +1666,20 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
     cudaEvent_t a, b;
     ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } ev{e0, e1};
-  const int cand_t[3] = {128, 256, 512};
+  const int cand_t[4] = {64, 128, 256, 512};
   const int cand_v[3] = {1, 2, 4};
   int best_t = 256, best_v = 0;
   float best = 1e30f;
-  for (int ti = 0; ti < 3; ++ti)
+  for (int ti = 0; ti < 4; ++ti)
     for (int vi = 0; vi < 3; ++vi) {
       const int v = std::min(cand_v[vi], nvec);
       if (vi > 0 && v == std::min(cand_v[vi - 1], nvec)) continue;  // same as the previous candidate
-      LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->Mband, nullptr, nvec, h->p, h->q, h->N, cand_t[ti], v));
+      LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, h->Mband, nullptr, nvec, h->p, h->q,
+                          h->N, cand_t[ti], v));
       CK(cudaEventRecord(e0, s));
       for (int r = 0; r < reps; ++r)
-        LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->Mband, nullptr, nvec, h->p, h->q, h->N, cand_t[ti],
-                            v));
+        LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, h->Mband, nullptr, nvec, h->p, h->q,
+                            h->N, cand_t[ti], v));
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;

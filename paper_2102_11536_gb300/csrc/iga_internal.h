@@ -61,6 +61,7 @@ struct DirDev {
   float* U32;
   float* lam32;
   void* Btc[2];   // BF16 U and U^T in the tensor-core operand layout (kernels_tc.cu)
+  void* Btc16[2]; // the same in FP16
 };
 
 // ---------------------------------------------------------------------------
@@ -175,22 +176,26 @@ cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const
 cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, double* init, int* stat);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
 
-// BF16 tensor-core mode product (kernels_tc.cu): B is the BF16 matrix arranged by
-// tc_arrange_bf16; err (device int) is set to 1 if an mbarrier wait times out.
-cudaError_t launch_fd_mode_tc(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const void* B,
-                              const void* in, int in_is_double, void* out, int out_is_double, long long vs,
-                              const double* pre, const double* post, const float* const* lam, const int* nn,
-                              int* err);
+// BF16 / FP16 tensor-core mode product along `axis` (kernels_tc.cu): B is the
+// 16-bit matrix arranged by tc_arrange (f16 selects FP16 with per-line power-of-two
+// scaling); err (device int) is set to 1 if an mbarrier wait times out.
+cudaError_t launch_fd_mode_tc(cudaStream_t s, int n, int axis, AxisShape sh, int nvec, const int* active,
+                              const void* B, int f16, const void* in, int in_is_double, void* out, int out_is_double,
+                              long long vs, const double* pre, const double* post, const float* const* lam,
+                              const int* nn, int* err);
 int tc_pad(int n);
-// Mat(i, j) row-major n x n (i output, j summed) -> BF16 bits in the K-major core-matrix layout
-void tc_arrange_bf16(int n, const double* Mat_ij, std::vector<uint16_t>& outbits);
+// Mat(i, j) row-major n x n (i output, j summed) -> BF16 or FP16 bits in the K-major
+// core-matrix layout
+void tc_arrange(int n, const double* Mat_ij, bool f16, std::vector<uint16_t>& outbits);
 
 // Assembled band form (kernels_band.cu): H stored slots (centre + upper half),
 // off[h] the linear offset of slot h, A [H][N].
-// threads: block size 128 / 256 / 512 (other = 256); nv: vectors per thread (0 = min(nvec, 4)).
-cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
-                             const int* active, int nvec, const double* x, double* y, long long vs, int threads,
-                             int nv);
+// o12 (nullable): packed slot offsets along directions 1, 2 ((o1+64) | (o2+64) << 8) for
+// skipping slots outside the grid for a whole warp; n: grid sizes (3 entries).
+// threads: block size 64 / 128 / 256 / 512 (other = 256); nv: vectors per thread (0 = min(nvec, 4)).
+cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const int* o12, const int* n,
+                             const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
+                             int threads, int nv);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,

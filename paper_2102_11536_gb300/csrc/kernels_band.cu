@@ -21,35 +21,57 @@
 
 namespace iga {
 
+// o12 (nullable) packs each stored slot's offsets along directions 1 and 2,
+// (o1 + 64) | (o2 + 64) << 8. With it, a slot whose neighbour (i + o for the upper
+// term, i - o for the lower) lies outside the grid along direction 1 or 2 for every
+// lane of the warp is skipped: its coefficients are zero. Lanes of a warp share
+// (i1, i2) except where the warp wraps a grid line, so the vote is almost always
+// unanimous; skipped lanes would only have added zeros.
 template <int NV, int BS>
 __global__ void __launch_bounds__(BS) k_band_spmv(long long N, int H, const long long* __restrict__ off,
-                                                   const double* __restrict__ A, const int* __restrict__ active,
-                                                   int nvec, const double* __restrict__ x, double* __restrict__ y,
-                                                   long long vs) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+                                                  const int* __restrict__ o12, int n0, int n1, int n2,
+                                                  const double* __restrict__ A, const int* __restrict__ active,
+                                                  int nvec, const double* __restrict__ x, double* __restrict__ y,
+                                                  long long vs) {
+  const long long i = (long long)blockIdx.x * BS + threadIdx.x;
+  const bool row = i < N;  // no early return: the slot votes need every lane
   // up to NV vectors per thread share every coefficient load
   const int v0 = blockIdx.y * NV;
   bool on[NV];
   double acc[NV];
-  const double a0 = A[i];
+  const double a0 = row ? A[i] : 0.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int vv = v0 + v;
-    on[v] = vv < nvec && (!active || active[vv]);
+    on[v] = row && vv < nvec && (!active || active[vv]);
     acc[v] = on[v] ? a0 * x[vv * vs + i] : 0.0;
+  }
+  int i1 = 0, i2 = 0;
+  if (row && o12) {
+    const long long t = i / n0;
+    i1 = (int)(t % n1);
+    i2 = (int)(t / n1);
   }
   for (int h = 1; h < H; ++h) {
     const long long L = off[h];
     const long long jp = i + L, jm = i - L;
     const double* Ah = A + (long long)h * N;
-    if (jp >= 0 && jp < N) {
+    bool up = row && jp >= 0 && jp < N;
+    bool dn = row && jm >= 0 && jm < N;
+    if (o12) {
+      const int pk = o12[h];
+      const int o1 = (pk & 255) - 64, o2 = ((pk >> 8) & 255) - 64;
+      up = up && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
+      dn = dn && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
+      if (!__any_sync(0xffffffffu, up || dn)) continue;
+    }
+    if (up) {
       const double a = Ah[i];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
         if (on[v]) acc[v] = fma(a, x[(v0 + v) * vs + jp], acc[v]);
     }
-    if (jm >= 0 && jm < N) {
+    if (dn) {
       const double a = Ah[jm];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
@@ -124,30 +146,32 @@ static BandGeom make_geom(const int* n, const int* p) {
 
 namespace {
 template <int BS>
-void band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, const double* A, const int* active,
-             int nvec, const double* x, double* y, long long vs) {
+void band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, const int* o12, const int* n,
+             const double* A, const int* active, int nvec, const double* x, double* y, long long vs) {
   const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
+  const int n0 = n[0], n1 = n[1], n2 = n[2];
   switch (nv) {
-    case 1: k_band_spmv<1, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
-    case 2: k_band_spmv<2, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
-    case 3: k_band_spmv<3, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
-    default: k_band_spmv<4, BS><<<grid, BS, 0, s>>>(N, H, off, A, active, nvec, x, y, vs); break;
+    case 1: k_band_spmv<1, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
+    case 2: k_band_spmv<2, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
+    case 3: k_band_spmv<3, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
+    default: k_band_spmv<4, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
   }
 }
 }  // namespace
 
-// threads: block size (128, 256 or 512; anything else = 256); nv: vectors per thread
-// sharing each coefficient load (1..4; 0 = min(nvec, 4)). Every configuration
-// computes each row with the same operations in the same order.
-cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const double* A,
-                             const int* active, int nvec, const double* x, double* y, long long vs, int threads,
-                             int nv) {
+// threads: block size (64, 128, 256 or 512; anything else = 256); nv: vectors per
+// thread sharing each coefficient load (1..4; 0 = min(nvec, 4)). Every
+// configuration computes each row with the same operations in the same order.
+cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const int* o12, const int* n,
+                             const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
+                             int threads, int nv) {
   if (nv <= 0) nv = nvec < 4 ? nvec : 4;
   if (nv < 1) nv = 1;
   if (nv > 4) nv = 4;
-  if (threads == 128) band_go<128>(s, nv, N, H, off, A, active, nvec, x, y, vs);
-  else if (threads == 512) band_go<512>(s, nv, N, H, off, A, active, nvec, x, y, vs);
-  else band_go<256>(s, nv, N, H, off, A, active, nvec, x, y, vs);
+  if (threads == 64) band_go<64>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
+  else if (threads == 128) band_go<128>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
+  else if (threads == 512) band_go<512>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
+  else band_go<256>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
   return cudaGetLastError();
 }
 

@@ -231,7 +231,8 @@ def test_nonuniform_repeated_knots():
 
 
 @pytest.mark.parametrize("form", [("matrix_free", "fp64", "zero"), ("assembled", "fp32", "zero"),
-                                  ("assembled", "fp64", "extrap"), ("assembled", "bf16", "taylor")])
+                                  ("assembled", "fp64", "extrap"), ("assembled", "bf16", "taylor"),
+                                  ("assembled", "fp16", "zero")])
 def test_graph_replay_equals_host_loop(form):
     """The captured step (PCG loop on the device) and the host-driven loop run the same
     kernels in the same order: bitwise equal states and equal iteration counts."""
@@ -281,12 +282,14 @@ def test_max_iter_reports_not_converged():
     g.close()
 
 
-# FP32 mode products: FP32 rounding; BF16 (tensor cores): 8-bit mantissa operands,
-# FP32 accumulation over six mode products -> about 1e-2 norm-wise.
-PRECOND_TOL = {"fp32": 1e-5, "bf16": 5e-2}
+# FP32 mode products: FP32 rounding; BF16 (tensor cores): 8-bit significand operands
+# (unit roundoff 2^-9), FP32 accumulation over six mode products -> about 1e-2
+# norm-wise; FP16: 11-bit significand (unit roundoff 2^-11, 4x smaller) after an
+# exact per-line power-of-two scaling.
+PRECOND_TOL = {"fp32": 1e-5, "bf16": 5e-2, "fp16": 5e-2 / 4}
 
 
-@pytest.mark.parametrize("precond", ["fp32", "bf16"])
+@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("name", ["3d_mixed_p", "3d_ragged_p3", "2d_square32_p2", "3d_p4"])
 def test_low_precision_preconditioner_close_to_oracle(name, precond):
     """Norm-wise relative error of P^{-1} r against the FP64 oracle at the arithmetic's level."""
@@ -304,21 +307,39 @@ def test_low_precision_preconditioner_close_to_oracle(name, precond):
     g.close()
 
 
-def test_bf16_preconditioner_cube64():
-    """The tensor-core form at full size (n = 65 per direction, 34 row tiles per mode)."""
+@pytest.mark.parametrize("precond", ["bf16", "fp16"])
+def test_tensor_core_preconditioner_cube64(precond):
+    """The tensor-core forms at full size (n = 65 per direction, 2146 line tiles per mode)."""
     w = W.config("cube64_p3")
     P = oracle.Patch(w.p, w.knots, w.ctrl())
     pre = oracle.Preconditioner(P)
-    g = _gpu(w, precond="bf16")
+    g = _gpu(w, precond=precond)
     X = np.random.default_rng(6).standard_normal(P.N)
     y = torch.empty(P.N, dtype=torch.float64, device=DEV)
     g.apply_Pinv(_t(X), y)
     ref = pre.apply_Pinv(X)
-    assert np.linalg.norm(_np(y) - ref) / np.linalg.norm(ref) < PRECOND_TOL["bf16"]
+    assert np.linalg.norm(_np(y) - ref) / np.linalg.norm(ref) < PRECOND_TOL[precond]
     g.close()
 
 
-@pytest.mark.parametrize("precond", ["fp32", "bf16"])
+@pytest.mark.parametrize("precond", ["bf16", "fp16"])
+@pytest.mark.parametrize("e", [60, -60])
+def test_tensor_core_preconditioner_is_exactly_homogeneous(precond, e):
+    """Scaling the input by 2^e scales the output by 2^e bitwise: FP16's per-line
+    power-of-two scaling is exact, and neither form under- or overflows."""
+    w = OPERATOR_CASES["3d_ragged_p3"]
+    g = _gpu(w, precond=precond)
+    X = np.random.default_rng(12).standard_normal(2 * g.N)
+    X[: g.N // 3] *= 1e-9  # lines of very different magnitudes
+    y0 = torch.empty(2 * g.N, dtype=torch.float64, device=DEV)
+    y1 = torch.empty_like(y0)
+    g.apply_Pinv(_t(X), y0, 2)
+    g.apply_Pinv(_t(np.ldexp(X, e)), y1, 2)
+    assert np.array_equal(np.ldexp(_np(y0), e), _np(y1))
+    g.close()
+
+
+@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_step_with_low_precision_preconditioner_matches_fp64_oracle(k, precond):
     """Flexible PCG with an FP32 or BF16 preconditioner reaches the same FP64 tolerance, so
