@@ -112,6 +112,18 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def combine_over_ranks(torch, pg, dev, maxed, summed):
+    """Maximum over ranks of the values in `maxed` and sum of those in `summed`
+    (lists of floats); the values themselves without a process group."""
+    if not pg:
+        return [float(v) for v in maxed], [float(v) for v in summed]
+    t = torch.tensor([float(v) for v in maxed], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    u = torch.tensor([float(v) for v in summed] or [0.0], dtype=torch.float64, device=dev)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()], [float(v) for v in u.tolist()][:len(summed)]
+
+
 def workload_desc(w):
     return ("%s: %dD unit %s, %s, p=%d C^%d, %s elements, N=%d, k=%d (order %d), rho_inf=%g, "
             "dt=%.2f tau_crit, PCG tol %g" % (
@@ -278,13 +290,18 @@ def train_warm_start(patch, torch, w, dt, state, u0, v0, args):
             "note": "set-up outside the timed region; the timed run starts from the initial state"}
 
 
-def run_batch(args, iga, torch, workloads, dev, flush):
+def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     """The 48-patch batch: FP64 assembled operators, BF16 preconditioner, per-patch
     dt = 0.5 tau_crit, autotuned band launches; one graph launch per batch step,
-    against the same patches stepped one after the other (each with its own graph)."""
+    against the same patches stepped one after the other (each with its own graph).
+    Under torchrun the patches are sharded over the ranks (longest-processing-time
+    partition by estimated work, no collective on the data path); times are the
+    maximum over ranks."""
     t0 = time.perf_counter()
-    ws = workloads.multipatch_batch()
+    allw = workloads.multipatch_batch()
     k, rho = 2, 0.5
+    shards = iga.shard_patches([iga.patch_work(w.ndof, w.p[0]) for w in allw], world)
+    ws = [allw[i] for i in shards[rank]]
     pats, states, dts, inits, tuned = [], [], [], [], {}
     for w in ws:
         g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, op_form="assembled", precond="bf16",
@@ -307,6 +324,8 @@ def run_batch(args, iga, torch, workloads, dev, flush):
 
     def timed(step_fn, nsteps):
         ms = 0.0
+        if pg:
+            pg.barrier()
         for _ in range(nsteps):
             flush.add_(1.0)
             e0.record(stream)
@@ -329,27 +348,30 @@ def run_batch(args, iga, torch, workloads, dev, flush):
 
     alone()  # each patch captures its own graph
     ms_alone = timed(alone, nb)
-    ndof = sum(g.N for g in pats)
-    iters = sum(s.iters for s in stats)
-    solves = sum(s.solves for s in stats)
+    (ms_batch, ms_alone), (ndof, iters, solves, launches) = combine_over_ranks(
+        torch, pg, dev, [ms_batch, ms_alone],
+        [sum(g.N for g in pats), sum(s.iters for s in stats), sum(s.solves for s in stats),
+         sum(s.launches for s in stats)])
     out = {
         "workload": "48 independent 3-D patches, nel ~ U{16..96} per axis, p in {2,3,4}, per-coordinate "
                     "deformation amplitudes ~ U(0, 0.15), k=2, rho_inf=0.5, per-patch dt = 0.5 tau_crit, "
                     "FP64 assembled operators, BF16 tensor-core preconditioner, PCG tol 1e-10, zero guess",
-        "patches": len(pats),
-        "total_dofs": ndof,
+        "patches": len(allw),
+        "total_dofs": int(ndof),
+        "ranks": world,
+        "patches_per_rank": [len(sh) for sh in shards],
         "batch_steps": nb,
         "value": nb / (ms_batch / 1e3),
         "unit": "batch steps/s (every patch advanced one step)",
         "dof_updates_per_s": ndof * nb / (ms_batch / 1e3),
         "ms_per_batch_step": ms_batch / nb,
-        "pcg_iters_per_solve": iters / max(solves, 1),
-        "gpu_launches_per_batch_step": sum(s.launches for s in stats) / nb,
-        "graph_launches_per_batch_step": 1,
+        "pcg_iters_per_solve": iters / max(solves, 1.0),
+        "gpu_launches_per_batch_step": launches / nb,
+        "graph_launches_per_batch_step_per_rank": 1,
         "sequential": {"ms_per_batch_step": ms_alone / nb, "value": nb / (ms_alone / 1e3),
                        "note": "the same patches stepped one after another, each replaying its own step graph"},
         "speedup_vs_sequential": ms_alone / ms_batch,
-        "autotuned_band_configs": tuned,
+        "autotuned_band_configs_rank0": tuned,
         "setup_s": setup_s,
         "l2": "L2 flushed before every timed batch step; the batch holds ~33 GB of band coefficients",
     }
@@ -417,13 +439,7 @@ def run_ours(args):
         patch.set_graphs(opts.get("graphs", True))
         patch.state_init(k, u0, v0, state)
         total_ms, stats, prof = time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class)
-        t_local = total_ms / 1000.0
-        if pg:
-            tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            t_max = float(tt.item())
-        else:
-            t_max = t_local
+        (t_max,), _ = combine_over_ranks(torch, pg, dev, [total_ms / 1000.0], [])
         finals[name] = state.view(3 * k, N)[:2].cpu().numpy()
         # whole preconditioner applications of this form, timed live on a few more steps
         patch.profile("precond")
@@ -488,12 +504,11 @@ def run_ours(args):
     for _ in range(args.steps):
         patch.step_host(host, k, w.rho, dt, 1, st_e2e)
     e2e_s = time.perf_counter() - t0
+    (e2e_s,), _ = combine_over_ranks(torch, pg, dev, [e2e_s], [])
     if pg:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_s = float(tt.item())
         pg.barrier()
     e2e_rate = world * args.steps / e2e_s
+    batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
 
     if rank != 0:
         if pg:
@@ -546,8 +561,8 @@ def run_ours(args):
                   "band_launch": {"threads": band_cfg[0], "vectors_per_thread": band_cfg[1], "chosen_by": "iga_autotune"},
                   "warm_start_training": warm},
     }
-    if args.batch_steps > 0:
-        result["multipatch_batch"] = run_batch(args, iga, torch, workloads, dev, flush)
+    if batch_res is not None:
+        result["multipatch_batch"] = batch_res
     if not args.no_cpu_baseline and world == 1:
         base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
         result["cpu_baseline"] = base

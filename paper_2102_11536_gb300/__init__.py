@@ -471,3 +471,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def shard_patches(works, world):
+    """Longest-processing-time partition of independent patches over `world` ranks:
+    patches in decreasing order of estimated work go to the rank with the least work
+    so far (ties to the lower rank). Returns one sorted index list per rank."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(works)), key=lambda i: (-works[i], i))
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += works[i]
+    return [sorted(o) for o in out]
+
+
+def patch_work(ndof, p):
+    """Work estimate of one patch step: couplings of the assembled band, N (2p+1)^3."""
+    return float(ndof) * (2 * p + 1) ** 3
