@@ -15,6 +15,9 @@ Forms measured (all FP64 state, FP64 PCG residuals and dot products, same tol):
                   (the paper's PCG setting)
   fp64_assembled  assembled band K, M; FP64 preconditioner; zero guess
   mixed_fp32      assembled band K, M; FP32 preconditioner (flexible PCG); zero guess
+  fp64_banded     assembled band K, M; FP64 preconditioner with the Kronecker solve by band
+                  Cholesky along each direction (O(N)) instead of fast diagonalisation; plain PCG
+  mixed_banded32  the same Kronecker solve in FP32 (flexible PCG)
   mixed_taylor    as mixed_fp32 with the Taylor predictor as initial guess
   mixed_bf16      assembled band K, M; BF16 preconditioner on the tensor cores (tcgen05,
                   FP32 accumulation; flexible PCG); zero guess
@@ -64,6 +67,10 @@ FORMS = [
     ("fp64_assembled", dict(op_form="assembled", precond="fp64", guess="zero"), "band_mass",
      "k_band_spmv (assembled symmetric band product, mass)"),
     ("mixed_fp32", dict(op_form="assembled", precond="fp32", guess="zero"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+    ("fp64_banded", dict(op_form="assembled", precond="banded", guess="zero"), "band_mass",
+     "k_band_spmv (assembled symmetric band product, mass)"),
+    ("mixed_banded32", dict(op_form="assembled", precond="banded32", guess="zero"), "band_mass",
      "k_band_spmv (assembled symmetric band product, mass)"),
     ("mixed_taylor", dict(op_form="assembled", precond="fp32", guess="taylor"), "band_mass",
      "k_band_spmv (assembled symmetric band product, mass)"),

@@ -52,6 +52,9 @@ extern "C" {
 #define IGA_PREC_FP32 1       /* FP32 CUDA cores; flexible CG */
 #define IGA_PREC_BF16 2       /* BF16 tensor cores, FP32 accumulation; flexible CG */
 #define IGA_PREC_FP16 3       /* FP16 tensor cores, FP32 accumulation; flexible CG */
+#define IGA_PREC_BANDED 4     /* FP64 Kronecker solve by band Cholesky along each direction (the O(N)
+                                 Kronecker solver of Sec. 5.5) instead of fast diagonalisation; plain CG */
+#define IGA_PREC_BANDED32 5   /* the same band Cholesky Kronecker solve in FP32; flexible CG */
 
 /* Initial guess of each mass solve inside a time step. */
 #define IGA_GUESS_ZERO 0      /* null vector, as in the paper's experiments (Sec. 6) */

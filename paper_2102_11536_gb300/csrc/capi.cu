@@ -378,6 +378,26 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     }
     return IGA_OK;
   }
+  if (h->opt.precond == IGA_PREC_BANDED || h->opt.precond == IGA_PREC_BANDED32) {
+    // (Mhat_1 x Mhat_2 x Mhat_3)^{-1} by band Cholesky along each axis, FP64 or FP32
+    // (FP32 intermediates between the axes)
+    const int f32 = h->opt.precond == IGA_PREC_BANDED32;
+    const void* L[3] = {f32 ? (const void*)d[0].chol32 : d[0].chol, f32 ? (const void*)d[1].chol32 : d[1].chol,
+                        f32 ? (const void*)d[2].chol32 : d[2].chol};
+    const void* Di[3] = {f32 ? (const void*)d[0].cdinv32 : d[0].cdinv, f32 ? (const void*)d[1].cdinv32 : d[1].cdinv,
+                         f32 ? (const void*)d[2].cdinv32 : d[2].cdinv};
+    const int mid = f32 ? 0 : 1;  // intermediates are FP64 only in the FP64 form
+    const double* sc = h->scale;
+    if (d3) {
+      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n12}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
+      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], n[2]}, nvec, active, f32, L[1], Di[1], t1, mid, t2, mid, N, nullptr, nullptr));
+      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc));
+    } else {
+      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n[1]}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
+      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc));
+    }
+    return IGA_OK;
+  }
   if (h->opt.precond == IGA_PREC_FP32) {
     float* f1 = reinterpret_cast<float*>(t1);
     float* f2 = reinterpret_cast<float*>(t2);
@@ -431,7 +451,7 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
 
 // The tensor-core kernels set dflag[1] when an mbarrier wait runs out.
 int check_tc_error(iga_handle* h) {
-  if (h->opt.precond != IGA_PREC_BF16) return IGA_OK;
+  if (h->opt.precond != IGA_PREC_BF16 && h->opt.precond != IGA_PREC_FP16) return IGA_OK;
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -594,7 +614,8 @@ int solve_iter_b(iga_handle* h, int nvec) {
   CgScalars& c = h->cs;
   double* pA = h->partial;
   double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
-  const bool flexible = h->opt.precond != IGA_PREC_FP64;
+  // the FP64 preconditioners are symmetric and linear to rounding: plain CG
+  const bool flexible = h->opt.precond != IGA_PREC_FP64 && h->opt.precond != IGA_PREC_BANDED;
   if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
   CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
   LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
@@ -985,7 +1006,7 @@ void iga_destroy(iga_handle* h) {
     DirDev& d = h->dd[a];
     dfree(d.val); dfree(d.der); dfree(d.sq); dfree(d.val32); dfree(d.der32);
     dfree(d.qfirst); dfree(d.flo); dfree(d.fhi); dfree(d.qw);
-    dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32);
+    dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32); dfree(d.chol); dfree(d.cdinv); dfree(d.chol32); dfree(d.cdinv32);
     for (int t = 0; t < 2; ++t)
       if (d.Btc[t]) { cudaFree(d.Btc[t]); d.Btc[t] = nullptr; }
     for (int t = 0; t < 2; ++t)
@@ -1027,7 +1048,7 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
   if (!h) return fail(nullptr, IGA_ENOMEM, "host allocation failed");
   if (opt) h->opt = *opt;
   else iga_options_default(&h->opt);
-  if (!(h->opt.tol >= 0.0) || h->opt.max_iter < 1 || h->opt.precond < 0 || h->opt.precond > 3 ||
+  if (!(h->opt.tol >= 0.0) || h->opt.max_iter < 1 || h->opt.precond < 0 || h->opt.precond > IGA_PREC_BANDED32 ||
       h->opt.op_form < 0 || h->opt.op_form > 1 || h->opt.guess < 0 || h->opt.guess > IGA_GUESS_LEARNED) {
     delete h;
     return fail(nullptr, IGA_EINVAL, "invalid options");
@@ -1081,6 +1102,9 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
       CKS(upload(h, &d.qfirst, t.qfirst)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
       CKS(upload(h, &d.qw, t.qw));
       CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, linv));
+      CKS(upload(h, &d.chol, t.chol)); CKS(upload(h, &d.cdinv, t.cdinv));
+      CKS(upload(h, &d.chol32, std::vector<float>(t.chol.begin(), t.chol.end())));
+      CKS(upload(h, &d.cdinv32, std::vector<float>(t.cdinv.begin(), t.cdinv.end())));
       if (tc_pad(t.n) <= 256) {  // BF16 tensor-core operands: Mat = U and Mat = U^T, (i, j) row-major
         std::vector<double> Mu((size_t)t.n * t.n), Mt((size_t)t.n * t.n);
         for (int i = 0; i < t.n; ++i)
@@ -1172,7 +1196,7 @@ int iga_set_op_form(iga_handle* h, int op_form) {
   return IGA_OK;
 }
 int iga_set_precond(iga_handle* h, int precond) {
-  if (!h || precond < 0 || precond > 3) return IGA_EINVAL;
+  if (!h || precond < 0 || precond > IGA_PREC_BANDED32) return IGA_EINVAL;
   h->opt.precond = precond;
   return IGA_OK;
 }

@@ -203,6 +203,36 @@ bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::
   jacobi_eigen(t.n, t.mhat, t.evec, t.eval);
   for (double l : t.eval)
     if (!(l > 0)) { err = "parametric mass matrix not positive definite"; return false; }
+  if (!band_cholesky(t.n, t.p, t.mhat, t.chol, t.cdinv)) {
+    err = "band Cholesky of the parametric mass matrix failed";
+    return false;
+  }
+  return true;
+}
+
+// Cholesky factor M = L L^T of a symmetric positive definite matrix with half
+// bandwidth p (row-major n x n): L[i*(p+1) + d] = L_{i, i-d} (zero where i-d < 0),
+// dinv[i] = 1 / L_ii. Column by column: L_jj = sqrt(M_jj - sum_k L_jk^2) and
+// L_ij = (M_ij - sum_k L_ik L_jk) / L_jj for j < i <= j + p, the sums over the
+// columns k < j inside both bands.
+bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<double>& L, std::vector<double>& dinv) {
+  const int w = p + 1;
+  L.assign((size_t)n * w, 0.0);
+  dinv.assign((size_t)n, 0.0);
+  auto at = [&](int i, int j) -> double& { return L[(size_t)i * w + (i - j)]; };  // needs 0 <= i - j <= p
+  for (int j = 0; j < n; ++j) {
+    double s = M[(size_t)j * n + j];
+    for (int k = std::max(0, j - p); k < j; ++k) s -= at(j, k) * at(j, k);
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    at(j, j) = ljj;
+    dinv[j] = 1.0 / ljj;
+    for (int i = j + 1; i <= std::min(n - 1, j + p); ++i) {
+      double t = M[(size_t)i * n + j];
+      for (int k = std::max(0, i - p); k < j; ++k) t -= at(i, k) * at(j, k);
+      at(i, j) = t / ljj;
+    }
+  }
   return true;
 }
 

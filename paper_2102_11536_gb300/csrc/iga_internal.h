@@ -31,6 +31,8 @@ struct Tables1D {
   std::vector<double> mhat;         // [n][n] interior parametric mass matrix
   std::vector<double> evec;         // [n][n] row-major, column c = eigenvector c
   std::vector<double> eval;         // [n]
+  std::vector<double> chol;         // [n][p+1] band Cholesky factor of mhat, chol[i][d] = L_{i,i-d}
+  std::vector<double> cdinv;        // [n] 1 / L_ii
 };
 
 // Gauss-Legendre rule on [-1, 1].
@@ -39,6 +41,9 @@ void gauss_legendre(int n, double* x, double* w);
 void bspline_span(int p, const double* U, int s, double x, double* val, double* der);
 // Build all tables of one direction; returns false on invalid knots.
 bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err);
+// Band Cholesky factor of an SPD matrix with half bandwidth p (row-major n x n):
+// L [n][p+1] with L[i][d] = L_{i,i-d}, dinv [n] = 1 / L_ii. False if not positive definite.
+bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<double>& L, std::vector<double>& dinv);
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).
 void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evec, std::vector<double>& eval);
 
@@ -62,6 +67,10 @@ struct DirDev {
   float* lam32;
   void* Btc[2];   // BF16 U and U^T in the tensor-core operand layout (kernels_tc.cu)
   void* Btc16[2]; // the same in FP16
+  double* chol;   // [n][p+1] band Cholesky factor of the interior parametric mass matrix
+  double* cdinv;  // [n] inverse diagonal of the factor
+  float* chol32;  // the same in FP32
+  float* cdinv32;
 };
 
 // ---------------------------------------------------------------------------
@@ -231,6 +240,15 @@ cudaError_t launch_ws_features(cudaStream_t s, long long N, int k, const double*
 // t [k][N] = (Z - E) / s0, FP32.
 cudaError_t launch_ws_target(cudaStream_t s, long long N, int k, const double* Z, const double* E, const double* sc,
                              float* t, long long* nl);
+
+// Kronecker solve along one axis (kernels_kron.cu): every line of the tensor (line
+// rr = xx + A y holds elements xx + A (k + n y), k < n) is replaced by Mhat_a^{-1} times
+// it, by forward and backward substitution with the band Cholesky factor (half
+// bandwidth p); pre / post (nullable, per element) multiply the input / output in
+// FP64. f32 selects FP32 arithmetic with the FP32 factor (FP32 or FP64 input / output).
+cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nvec, const int* active, int f32,
+                             const void* L, const void* dinv, const void* in, int in_is_double, void* out,
+                             int out_is_double, long long vs, const double* pre, const double* post);
 
 // Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
 constexpr long long kNoAllocMaxElems = 1LL << 20;

@@ -1,0 +1,170 @@
+// Kronecker solve of the preconditioner (Sec. 5.3, def:single_patch_prec) by band
+// Cholesky: (Mhat_1 x Mhat_2 x Mhat_3)^{-1} is the product of the univariate
+// inverses applied along each direction, and Mhat_a = L_a L_a^T is banded with half
+// bandwidth p, so each line along axis a is solved by a forward and a backward
+// substitution of p terms per entry (about 4 (p+1) flops per entry and axis, the
+// O(N) cost of the paper's Kronecker solvers).
+//
+// One block of kThreads threads takes kLines lines: all threads stage them in shared
+// memory (element (k, line) at k * kLines + line; reads coalesced along the lines
+// for axis 0, where a block's lines are one contiguous range, and across the lines
+// for the other axes; several loads in flight per thread), the first kLines threads
+// run the two substitutions, one line each, in shared memory, and all threads write
+// the lines back the same way. pre multiplies the
+// input entries (the first axis: D^{-1/2} Dhat^{1/2}), post the output entries
+// (the last axis).
+#include "iga_internal.h"
+
+
+namespace iga {
+
+namespace {
+
+constexpr int kLines = 32;    // lines per block (one warp solves them)
+constexpr int kThreads = 256; // threads staging and writing back
+
+// P = p: entries below the diagonal in a row of the factor; T: arithmetic (double, or
+// float for the FP32 form); TI / TO: input / output element types. pre / post are
+// applied in FP64 before rounding to T / after widening from T.
+template <int P, typename T, typename TI, typename TO>
+__global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long long R, const T* __restrict__ L,
+                                                      const T* __restrict__ dinv, const int* __restrict__ active,
+                                                      const TI* __restrict__ in, TO* __restrict__ out,
+                                                      long long vs, const double* __restrict__ pre,
+                                                      const double* __restrict__ post) {
+  extern __shared__ __align__(16) unsigned char kron_smem[];
+  T* sb = reinterpret_cast<T*>(kron_smem);  // [n][kLines] lines, then the factor [n][P+1] and 1/L_kk [n]
+  T* sL = sb + (size_t)n * kLines;
+  T* sD = sL + (size_t)n * (P + 1);
+  const int v = blockIdx.y;
+  if (active && !active[v]) return;
+  const long long l0 = (long long)blockIdx.x * kLines;
+  const int nl = (int)min((long long)kLines, R - l0);
+  const int t = threadIdx.x;
+  const TI* x = in + v * vs;
+  TO* o = out + v * vs;
+  const int cnt = nl * n;
+  for (int e = t; e < n * (P + 1); e += kThreads) sL[e] = L[e];
+  for (int e = t; e < n; e += kThreads) sD[e] = dinv[e];
+  // stage
+  if (A == 1) {
+    const long long g0 = l0 * n;  // the block's lines are one contiguous range
+#pragma unroll 4
+    for (int e = t; e < cnt; e += kThreads) {
+      const int line = e / n, k = e - line * n;
+      double u = (double)x[g0 + e];
+      if (pre) u *= pre[g0 + e];
+      sb[k * kLines + line] = (T)u;
+    }
+  } else {
+#pragma unroll 4
+    for (int e = t; e < cnt; e += kThreads) {
+      const int k = e / nl, line = e - k * nl;
+      const long long rr = l0 + line;
+      const long long y = rr / A, xx = rr - y * A;
+      const long long g = xx + A * (k + (long long)n * y);
+      double u = (double)x[g];
+      if (pre) u *= pre[g];
+      sb[k * kLines + line] = (T)u;
+    }
+  }
+  __syncthreads();
+  if (t < nl) {
+    // forward: w_k = (s_k - sum_{d=1..p} L_{k,k-d} w_{k-d}) / L_kk
+    for (int k = 0; k < n; ++k) {
+      T s = sb[k * kLines + t];
+      const T* Lk = sL + (size_t)k * (P + 1);
+#pragma unroll
+      for (int d = 1; d <= P; ++d)
+        if (k - d >= 0) s -= Lk[d] * sb[(k - d) * kLines + t];
+      sb[k * kLines + t] = s * sD[k];
+    }
+    // backward: z_k = (w_k - sum_{d=1..p} L_{k+d,k} z_{k+d}) / L_kk
+    for (int k = n - 1; k >= 0; --k) {
+      T s = sb[k * kLines + t];
+#pragma unroll
+      for (int d = 1; d <= P; ++d)
+        if (k + d < n) s -= sL[(size_t)(k + d) * (P + 1) + d] * sb[(k + d) * kLines + t];
+      sb[k * kLines + t] = s * sD[k];
+    }
+  }
+  __syncthreads();
+  // write back
+  if (A == 1) {
+    const long long g0 = l0 * n;
+#pragma unroll 4
+    for (int e = t; e < cnt; e += kThreads) {
+      const int line = e / n, k = e - line * n;
+      double u = (double)sb[k * kLines + line];
+      if (post) u *= post[g0 + e];
+      o[g0 + e] = (TO)u;
+    }
+  } else {
+#pragma unroll 4
+    for (int e = t; e < cnt; e += kThreads) {
+      const int k = e / nl, line = e - k * nl;
+      const long long rr = l0 + line;
+      const long long y = rr / A, xx = rr - y * A;
+      const long long g = xx + A * (k + (long long)n * y);
+      double u = (double)sb[k * kLines + line];
+      if (post) u *= post[g];
+      o[g] = (TO)u;
+    }
+  }
+}
+
+template <int P, typename T, typename TI, typename TO>
+cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const void* L,
+                    const void* dinv, const void* in, void* out, long long vs, const double* pre,
+                    const double* post) {
+  const long long R = sh.A * sh.B;
+  const size_t smem = (size_t)n * (kLines + P + 2) * sizeof(T);
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_kron_axis<P, T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((unsigned)((R + kLines - 1) / kLines), (unsigned)nvec);
+  k_kron_axis<P, T, TI, TO><<<grid, kThreads, smem, s>>>(
+      n, sh.A, R, static_cast<const T*>(L), static_cast<const T*>(dinv), active, static_cast<const TI*>(in),
+      static_cast<TO*>(out), vs, pre, post);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t kron_types(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, int f32, const void* L,
+                       const void* dinv, const void* in, int in_is_double, void* out, int out_is_double, long long vs,
+                       const double* pre, const double* post) {
+  if (!f32) return kron_go<P, double, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+  if (in_is_double && !out_is_double)
+    return kron_go<P, float, double, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+  if (!in_is_double && out_is_double)
+    return kron_go<P, float, float, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+  if (!in_is_double && !out_is_double)
+    return kron_go<P, float, float, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+  return kron_go<P, float, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+}
+
+}  // namespace
+
+cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nvec, const int* active, int f32,
+                             const void* L, const void* dinv, const void* in, int in_is_double, void* out,
+                             int out_is_double, long long vs, const double* pre, const double* post) {
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  if (n < 1 || nvec < 1 || (size_t)n * (kLines + p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
+  if (!f32 && !(in_is_double && out_is_double)) return cudaErrorInvalidValue;
+#define IGA_KRON(PP) \
+  return kron_types<PP>(s, n, sh, nvec, active, f32, L, dinv, in, in_is_double, out, out_is_double, vs, pre, post)
+  switch (p) {
+    case 1: IGA_KRON(1);
+    case 2: IGA_KRON(2);
+    case 3: IGA_KRON(3);
+    case 4: IGA_KRON(4);
+    case 5: IGA_KRON(5);
+    case 6: IGA_KRON(6);
+    default: return cudaErrorInvalidValue;
+  }
+#undef IGA_KRON
+}
+
+}  // namespace iga

@@ -171,7 +171,7 @@ def test_step_matches_oracle(k, rho):
         assert err < 1e-10, (row, err)
 
 
-@pytest.mark.parametrize("precond", ["fp64", "fp32"])
+@pytest.mark.parametrize("precond", ["fp64", "fp32", "banded"])
 @pytest.mark.parametrize("k", [2, 3])
 def test_assembled_step_matches_oracle(k, precond):
     w = W.small(d=3, nel=(5, 4, 6), p=3, amp=0.1, k=k, rho=0.5, init="random")
@@ -232,7 +232,8 @@ def test_nonuniform_repeated_knots():
 
 @pytest.mark.parametrize("form", [("matrix_free", "fp64", "zero"), ("assembled", "fp32", "zero"),
                                   ("assembled", "fp64", "extrap"), ("assembled", "bf16", "taylor"),
-                                  ("assembled", "fp16", "zero")])
+                                  ("assembled", "fp16", "zero"), ("assembled", "banded", "zero"),
+                                  ("assembled", "banded32", "zero")])
 def test_graph_replay_equals_host_loop(form):
     """The captured step (PCG loop on the device) and the host-driven loop run the same
     kernels in the same order: bitwise equal states and equal iteration counts."""
@@ -282,14 +283,40 @@ def test_max_iter_reports_not_converged():
     g.close()
 
 
+@pytest.mark.parametrize("name", list(OPERATOR_CASES))
+def test_banded_preconditioner_matches_oracle(name):
+    """FP64 Kronecker solve by band Cholesky along each direction: the same operator
+    as the oracle's (LAPACK band Cholesky) to FP64 rounding."""
+    w = OPERATOR_CASES[name]
+    pre = oracle.Preconditioner(oracle.Patch(w.p, w.knots, w.ctrl()))
+    g = _gpu(w, precond="banded")
+    X = np.random.default_rng(3).standard_normal((3, pre.N))
+    y = torch.empty(3 * pre.N, dtype=torch.float64, device=DEV)
+    g.apply_Pinv(_t(X), y, 3)
+    Y = _np(y).reshape(3, pre.N)
+    for v in range(3):
+        assert _maxrel(Y[v], pre.apply_Pinv(X[v])) < 1e-12
+    g.close()
+
+
+def test_banded_preconditioner_iterations_equal_fp64_fd():
+    """Both FP64 preconditioners apply the same operator: the same PCG iteration counts."""
+    w = W.small(d=3, nel=(7, 6, 5), p=3, amp=0.1, k=2, rho=0.5, init="random")
+    ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+    dt = _dt(ops, w.rho)
+    _, sa = _gpu_run(w, 6, dt, 1e-11, precond="fp64", op_form="assembled")
+    _, sb = _gpu_run(w, 6, dt, 1e-11, precond="banded", op_form="assembled")
+    assert sa.iters == sb.iters and sa.max_iters == sb.max_iters
+
+
 # FP32 mode products: FP32 rounding; BF16 (tensor cores): 8-bit significand operands
 # (unit roundoff 2^-9), FP32 accumulation over six mode products -> about 1e-2
 # norm-wise; FP16: 11-bit significand (unit roundoff 2^-11, 4x smaller) after an
 # exact per-line power-of-two scaling.
-PRECOND_TOL = {"fp32": 1e-5, "bf16": 5e-2, "fp16": 5e-2 / 4}
+PRECOND_TOL = {"fp32": 1e-5, "bf16": 5e-2, "fp16": 5e-2 / 4, "banded32": 1e-5}
 
 
-@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16", "banded32"])
 @pytest.mark.parametrize("name", ["3d_mixed_p", "3d_ragged_p3", "2d_square32_p2", "3d_p4"])
 def test_low_precision_preconditioner_close_to_oracle(name, precond):
     """Norm-wise relative error of P^{-1} r against the FP64 oracle at the arithmetic's level."""
@@ -339,7 +366,7 @@ def test_tensor_core_preconditioner_is_exactly_homogeneous(precond, e):
     g.close()
 
 
-@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("precond", ["fp32", "bf16", "fp16", "banded32"])
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_step_with_low_precision_preconditioner_matches_fp64_oracle(k, precond):
     """Flexible PCG with an FP32 or BF16 preconditioner reaches the same FP64 tolerance, so
@@ -352,7 +379,7 @@ def test_step_with_low_precision_preconditioner_matches_fp64_oracle(k, precond):
     for row in (0, 1):
         err = np.linalg.norm(Xg[row] - Xo[row]) / np.linalg.norm(Xo[row])
         assert err < 1e-9, (row, err)
-    extra = 2 if precond == "fp32" else 6
+    extra = 2 if precond in ("fp32", "banded32") else 6
     assert st.iters <= sum(sum(i) for i in it_o) + extra * st.solves
 
 
