@@ -90,7 +90,7 @@ FORMS = [
 # (kernel, sha256 of the kernel's source file, first 16 hex): a capture only
 # counts while the source it was taken on is unchanged (profiles/*.md).
 NCU_TRAFFIC = {
-    ("band_mass", "2e47d6a0de65e57d"): 393.06e6,  # k_band_spmv<2>, 2-vector launch
+    ("band_mass", "1c1221dd916a1cdf"): 375.13e6,  # k_band_spmv<2, 64>, 2-vector launch (profiles/k_band_spmv_cube64_p3.md)
     ("mass", "618d068dc16a5b19"): 186.69e6,       # k_mid_mass<4>, 1-vector launch
 }
 
@@ -111,6 +111,9 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-driven PCG loop for every form (the same kernels; for profilers that cannot "
+                         "see inside graphs with conditional nodes)")
     return ap.parse_args()
 
 
@@ -443,7 +446,7 @@ def run_ours(args):
         patch.set_op_form(opts["op_form"])
         patch.set_precond(opts["precond"])
         patch.set_guess(opts["guess"])
-        patch.set_graphs(opts.get("graphs", True))
+        patch.set_graphs(opts.get("graphs", True) and not args.no_graphs)
         patch.state_init(k, u0, v0, state)
         total_ms, stats, prof = time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class)
         (t_max,), _ = combine_over_ranks(torch, pg, dev, [total_ms / 1000.0], [])

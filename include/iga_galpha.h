@@ -373,8 +373,10 @@ int iga_set_band_config(iga_handle* h, int threads, int nv);
  * iga_autotune -- time every band-product configuration (threads 64/128/256/512 x
  * vectors per thread 1, 2, 4 up to nvec) on nvec vectors with h's assembled mass
  * matrix (assembled first if needed): one warm-up launch, then reps launches
- * between two CUDA events on h's stream. Keeps the fastest for h and returns it
- * in threads / nv (host, may be NULL). 1 <= nvec <= 8, reps >= 1. Synchronises.
+ * between two CUDA events on h's stream. Keeps for h, among the shapes within 3 % of
+ * the fastest, the one with the most vectors per thread (each band coefficient read
+ * once for more vectors), and returns it in threads / nv (host, may be NULL).
+ * 1 <= nvec <= 8, reps >= 1. Synchronises.
  */
 int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv);
 

@@ -1692,8 +1692,11 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
   } ev{e0, e1};
   const int cand_t[4] = {64, 128, 256, 512};
   const int cand_v[3] = {1, 2, 4};
-  int best_t = 256, best_v = 0;
-  float best = 1e30f;
+  struct Cand {
+    int t, v;
+    float ms;
+  };
+  std::vector<Cand> res;
   for (int ti = 0; ti < 4; ++ti)
     for (int vi = 0; vi < 3; ++vi) {
       const int v = std::min(cand_v[vi], nvec);
@@ -1708,11 +1711,19 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        best_t = cand_t[ti];
-        best_v = v;
-      }
+      res.push_back({cand_t[ti], v, ms});
+    }
+  // the fastest; among shapes within 3 % of it, the most vectors per thread (each
+  // coefficient read once for more vectors: fewer DRAM bytes for the same time)
+  float best = 1e30f;
+  for (const Cand& c : res) best = std::min(best, c.ms);
+  int best_t = 256, best_v = 0;
+  float best_ms = 1e30f;
+  for (const Cand& c : res)
+    if (c.ms <= 1.03f * best && (c.v > best_v || (c.v == best_v && c.ms < best_ms))) {
+      best_t = c.t;
+      best_v = c.v;
+      best_ms = c.ms;
     }
   h->band_threads = best_t;
   h->band_nv = best_v;
