@@ -101,3 +101,11 @@ def test_tuning_and_batch_entry_points_validate(lib):
     assert lib.iga_batch_last_error(None) == b""
     assert lib.iga_set_band_config(None, 256, 2) == iga.EINVAL
     assert lib.iga_autotune(None, 2, 3, None, None) == iga.EINVAL
+
+
+def test_create_rejects_patches_without_interior_dofs(lib):
+    # one linear element per direction: 2 basis functions, both carry the Dirichlet condition
+    k1 = np.array([0, 0, 1, 1.0])
+    with pytest.raises(iga.IgaError) as e:
+        iga.Patch([1, 1, 1], [k1, k1, k1], np.zeros((8, 3)))
+    assert e.value.status == iga.EINVAL

@@ -406,3 +406,36 @@ def test_cube64_sampled_rows_and_preconditioner():
     g.apply_Pinv(_t(X), y)
     assert _maxrel(_np(y), pre.apply_Pinv(X)) < 1e-11
     g.close()
+
+
+SMALLEST = [W.Workload("s1", 3, (1, 3, 2), (2, 2, 2), 0.1, 2, 0.5, 3, init="random"),
+            W.Workload("s2", 3, (1, 1, 1), (2, 2, 2), 0.1, 2, 0.5, 3, init="random"),
+            W.Workload("s3", 3, (2, 1, 3), (3, 2, 2), 0.1, 1, 0.5, 3, init="random"),
+            W.Workload("s4", 2, (3, 2), (1, 1), 0.1, 2, 0.5, 3, init="random")]
+
+
+@pytest.mark.parametrize("precond", ["fp64", "fp32", "bf16", "fp16", "banded", "banded32"])
+@pytest.mark.parametrize("wi", range(len(SMALLEST)))
+def test_smallest_patches(wi, precond):
+    """Degenerate sizes: one interior function in some directions (N = 1 for one element
+    of degree 2 per direction); operators, preconditioner and steps against the oracle."""
+    w = SMALLEST[wi]
+    ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+    g = _gpu(w, tol=1e-12, precond=precond, op_form="assembled")
+    X = np.random.default_rng(13).standard_normal(ops.N)
+    y = torch.empty(ops.N, dtype=torch.float64, device=DEV)
+    g.apply_M(_t(X), y)
+    assert _maxrel(_np(y), ops.apply_M(X)) < 1e-12
+    g.apply_K(_t(X), y)
+    assert _maxrel(_np(y), ops.apply_K(X)) < 1e-11
+    g.apply_Pinv(_t(X), y)
+    assert _maxrel(_np(y), ops.apply_Pinv(X)) < (1e-12 if precond in ("fp64", "banded") else 5e-2)
+    g.close()
+    dt = _dt(ops, w.rho)
+    Xo, _ = _oracle_run(w, ops, w.steps, dt, 1e-12)
+    Xg, st = _gpu_run(w, w.steps, dt, 1e-12, precond=precond, op_form="assembled")
+    for row in (0, 1):
+        den = max(np.linalg.norm(Xo[row]), 1e-300)
+        assert np.linalg.norm(Xg[row] - Xo[row]) / den < 1e-9, (row,)
+    if ops.N == 1:
+        assert st.max_iters <= 1  # the preconditioner is the exact inverse of a 1 x 1 mass matrix
