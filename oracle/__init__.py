@@ -427,19 +427,34 @@ class Stepper:
 
     State X: array (3k, N), rows (U, V, A, L^1, ..., L^{3k-3}), i.e. X_q at row q + 2.
     Block j = 1..k solves for s_j = 3j - 3:
-        M Z_j = F_j - K Y_j,   Y_j = T_{s_j - 2} (j < k, alpha_f = 1),  Y_k = X_{s_k - 2}
+        M Z_j = F^{(s_j)}(t_{n + alpha_fj}) - K Y_j - C Y'_j,
+        Y_j = T_{s_j - 2}, Y'_j = T_{s_j - 1} (j < k, alpha_f = 1),  Y_k = X_{s_k - 2}, Y'_k = X_{s_k - 1}
         P_j = (Z_j - T_{s_j}) / alpha_j
         X_{s_j} <- T_{s_j} + P_j,  X_{s_j-1} <- T_{s_j-1} + gamma_j tau P_j,
         X_{s_j-2} <- T_{s_j-2} + beta_j tau^2 P_j.
     (Z_j is the paper's L^{s_j}(A_n)^{alpha_j} = T_{s_j} + alpha_j P_{n,j}.) The stiffness
     argument Y_j is the reading that gives order 2k; see the design doc."""
 
-    def __init__(self, ops, k: int, rho: float, tol=1e-10, max_iter=500, guess="zero", params=None):
+    def __init__(self, ops, k: int, rho: float, tol=1e-10, max_iter=500, guess="zero", params=None,
+                 damping=None, forcing=None, t0=0.0):
         self.ops, self.k, self.rho = ops, k, rho
         self.tol, self.max_iter, self.guess = tol, max_iter, guess
         self.params = params if params is not None else galpha_params(k, rho)
         self.hist = [[None, None] for _ in range(k)]  # Z_j at the previous two steps
         self.iters = []
+        # M U'' + C U' + K U = F (eq. mp): C = a_M M + a_K K (Rayleigh damping) when
+        # damping = (a_M, a_K); forcing(s, t) returns F^{(s)}(t), the s-th time derivative
+        # of the load vector. None: C = 0, F = 0.
+        self.damping = damping
+        self.forcing = forcing
+        self.t = t0
+
+    def apply_C(self, x):
+        aM, aK = self.damping
+        return aM * self.ops.apply_M(x) + aK * self.ops.apply_K(x)
+
+    def _load(self, s, t, n):
+        return np.zeros(n) if self.forcing is None else np.asarray(self.forcing(s, t), dtype=np.float64)
 
     def solve(self, b, x0=None):
         x, it, rr = pcg(self.ops.apply_M, self.ops.apply_Pinv, b, x0, self.tol, self.max_iter)
@@ -448,13 +463,17 @@ class Stepper:
         return x, it
 
     def init(self, U0, V0):
-        """Initial data (Sec. 3, after eq. 4aup; C = 0, F = 0):
-        X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3, with X_{-2} = U0, X_{-1} = V0."""
+        """Initial data (Sec. 3, after eq. 4aup):
+        X_a = M^{-1}(F^{(a)}(0) - K X_{a-2} - C X_{a-1}), a = 0..3k-3, with X_{-2} = U0, X_{-1} = V0."""
         nq = 3 * self.k
-        X = np.zeros((nq, self.ops.N))
+        n = self.ops.N
+        X = np.zeros((nq, n))
         X[0], X[1] = U0, V0
         for a in range(0, 3 * self.k - 2):
-            X[a + 2], _ = self.solve(-self.ops.apply_K(X[a]))
+            b = self._load(a, self.t, n) - self.ops.apply_K(X[a])
+            if self.damping is not None:
+                b = b - self.apply_C(X[a + 1])
+            X[a + 2], _ = self.solve(b)
         return X
 
     def _guess(self, j, T, row):
@@ -477,8 +496,13 @@ class Stepper:
         for j in range(1, k + 1):
             a, b, g, _ = self.params[j - 1]
             row = 3 * j - 3 + 2
+            # blocks j < k (alpha_f = 1): the predictors at t_{n+1}; block k (alpha_f = 0): X^n at t_n
             Y = T[row - 2] if j < k else X[row - 2]
-            rhs = -self.ops.apply_K(Y)
+            Yv = T[row - 1] if j < k else X[row - 1]
+            tj = self.t + tau if j < k else self.t
+            rhs = self._load(3 * j - 3, tj, X.shape[1]) - self.ops.apply_K(Y)
+            if self.damping is not None:
+                rhs = rhs - self.apply_C(Yv)
             Z, it = self.solve(rhs, self._guess(j - 1, T, row))
             its.append(it)
             self.hist[j - 1] = [Z, self.hist[j - 1][0]]
@@ -487,6 +511,7 @@ class Stepper:
             Xn[row - 1] = T[row - 1] + g * tau * P
             Xn[row - 2] = T[row - 2] + b * tau * tau * P
         self.iters.append(its)
+        self.t += tau
         return Xn
 
 

@@ -4,6 +4,7 @@ scipy adaptive quadrature, dense LAPACK solves and eigendecompositions), closed 
 the paper's printed amplification blocks and characteristic polynomials
 (tests/golden/), a textbook special case (Hulbert-Chung explicit generalized-alpha)
 and brute force on tiny meshes."""
+import cmath
 import math
 
 import numpy as np
@@ -482,3 +483,117 @@ def test_cfl_limit_independent_of_k_on_mesh(k):
     late = lambda h: max(h[600:800])
     assert late(stable) <= mid(stable) * 1.001
     assert late(unstable) > 1e2 * mid(unstable)
+
+
+# -- general model M U'' + C U' + K U = F: Rayleigh damping and harmonic forcing ----------
+def _osc_exact(lam, c, terms, u0, v0):
+    """Closed form of u'' + c u' + lam u = sum_m g_m sin(w_m t + p_m), u(0) = u0, u'(0) = v0
+    (characteristic roots plus one particular solution per term); returns a function
+    (t, m) -> m-th derivative of u at t."""
+    parts = []
+    for g, w, p in terms:  # particular: P sin(w t + p) + Q cos(w t + p)
+        a, b = lam - w * w, c * w
+        det = a * a + b * b
+        parts.append((g * a / det, -g * b / det, w, p))
+
+    def part(t, m):
+        s = 0.0
+        for P, Q, w, p in parts:
+            ph = w * t + p + m * math.pi / 2
+            s += w ** m * (P * math.sin(ph) + Q * math.cos(ph))
+        return s
+
+    r1 = (-c + cmath.sqrt(c * c - 4 * lam)) / 2
+    r2 = (-c - cmath.sqrt(c * c - 4 * lam)) / 2
+    h0, h1 = u0 - part(0.0, 0), v0 - part(0.0, 1)
+    B = (h1 - r1 * h0) / (r2 - r1)
+    A = h0 - B
+
+    def u(t, m=0):
+        return (A * r1 ** m * cmath.exp(r1 * t) + B * r2 ** m * cmath.exp(r2 * t)).real + part(t, m)
+
+    return u
+
+
+def _forcing_fn(G, terms):
+    def F(s, t):
+        return sum(g * G[i] * w ** s * math.sin(w * t + p + s * math.pi / 2) for i, (g, w, p) in enumerate(terms))
+    return F
+
+
+def _osc_error(k, rho, n, lam, aM, aK, terms, T=1.0):
+    c = aM + aK * lam
+    u = _osc_exact(lam, c, terms, 1.0, 0.0)
+    forcing = _forcing_fn([np.ones(1)] * len(terms), terms) if terms else None
+    st = oracle.Stepper(oracle.ScalarOps(lam), k, rho, tol=0.0,
+                        damping=(aM, aK) if (aM or aK) else None, forcing=forcing)
+    X = st.init(np.array([1.0]), np.array([0.0]))
+    eu = ev = 0.0
+    for s in range(1, n + 1):
+        X = st.step(X, T / n)
+        t = s * T / n
+        eu = max(eu, abs(X[0, 0] - u(t)))
+        ev = max(ev, abs(X[1, 0] - u(t, 1)))
+    return eu, ev
+
+
+OSC_CASES = {"damped": (0.8, 0.0, []), "stiffness_damped": (0.3, 0.1, []), "forced": (0.0, 0.0, [(1.0, 3.0, 0.0)]),
+             "damped_forced": (0.5, 0.075, [(1.0, 3.0, 0.4), (0.5, 1.3, -0.7)])}
+
+
+@pytest.mark.parametrize("k,ns,minorder", [(1, (40, 80), 1.9), (2, (80, 160), 3.7), (3, (32, 64), 5.4)])
+@pytest.mark.parametrize("rho", [0.5, 1.0])
+@pytest.mark.parametrize("case", list(OSC_CASES))
+def test_damped_forced_modal_order_is_2k(k, ns, minorder, rho, case):
+    """With C acting on the block's velocity-like predictor and F^{(s_j)} at t_{n+alpha_fj},
+    the scheme keeps order 2k on the damped, forced oscillator (exact closed form)."""
+    aM, aK, terms = OSC_CASES[case]
+    e1 = _osc_error(k, rho, ns[0], 4.0, aM, aK, terms)
+    e2 = _osc_error(k, rho, ns[1], 4.0, aM, aK, terms)
+    for a, b in zip(e1, e2):
+        assert math.log2(a / b) > minorder, (e1, e2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_init_gives_the_exact_initial_derivatives(k):
+    """X_a = M^{-1}(F^{(a)}(0) - K X_{a-2} - C X_{a-1}) are the derivatives u^{(a+2)}(0)."""
+    lam, aM, aK = 4.0, 0.5, 0.075
+    terms = [(1.0, 3.0, 0.4), (0.5, 1.3, -0.7)]
+    u = _osc_exact(lam, aM + aK * lam, terms, 1.0, -0.3)
+    st = oracle.Stepper(oracle.ScalarOps(lam), k, 0.5, tol=0.0, damping=(aM, aK),
+                        forcing=_forcing_fn([np.ones(1)] * 2, terms))
+    X = st.init(np.array([1.0]), np.array([-0.3]))
+    for r in range(3 * k):
+        assert abs(X[r, 0] - u(0.0, r)) < 1e-11 * max(1.0, abs(u(0.0, r))), r
+
+
+def test_damped_forced_semidiscrete_order():
+    """A small isogeometric system with Rayleigh damping and two harmonic loads against its
+    exact modal solution (generalized eigenvectors of (K, M) decouple C = aM M + aK K)."""
+    w = W.small(d=2, nel=4, p=2, amp=0.1, k=2)
+    ops = oracle.Operators(_patch(w))
+    Md, Kd = ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K)
+    lam, Phi = scipy.linalg.eigh(Kd, Md)
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((2, ops.N))
+    terms = [(1.0, 7.0, 0.2), (1.0, 2.5, -1.0)]
+    aM, aK = 0.6, 2e-4
+    U0, V0 = rng.standard_normal(ops.N), np.zeros(ops.N)
+    a0, b0 = Phi.T @ (Md @ U0), Phi.T @ (Md @ V0)
+    g = Phi.T @ G.T  # modal loads [mode][term]
+    T = 0.2
+    exact = []
+    for i in range(ops.N):
+        u = _osc_exact(lam[i], aM + aK * lam[i], [(g[i, m], terms[m][1], terms[m][2]) for m in range(2)],
+                       a0[i], b0[i])
+        exact.append(u(T))
+    Ue = Phi @ np.array(exact)
+    tau0 = 0.4 * math.sqrt(oracle.theta_crit(0.5) / lam[-1])
+    errs = []
+    for n in (int(np.ceil(T / tau0)) * 2, int(np.ceil(T / tau0)) * 4):
+        st = oracle.Stepper(ops, 2, 0.5, tol=1e-15, damping=(aM, aK), forcing=_forcing_fn(G, terms))
+        X = st.init(U0, V0)
+        for _ in range(n):
+            X = st.step(X, T / n)
+        errs.append(np.linalg.norm(X[0] - Ue) / np.linalg.norm(Ue))
+    assert math.log2(errs[0] / errs[1]) > 3.6, errs
