@@ -233,8 +233,32 @@ int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double
 int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double* tau_crit);
 
 /*
- * iga_state_init -- initial high-order data (Sec. 3, after eq. 4aup; C = 0, F = 0):
- * X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3, with X_{-2} = U0, X_{-1} = V0.
+ * General model M U'' + C U' + K U = F (Sec. 2.1, eq. mp). Defaults: C = 0, F = 0,
+ * t = 0.
+ *
+ * iga_set_damping -- Rayleigh damping C = aM M + aK K (aM, aK >= 0; both 0 = none).
+ *   In block j of a step (eq. ho1) C acts on the predictor of the block's
+ *   velocity-like variable, T_{s_j - 1} for j < k and X^n_{s_k - 1} for j = k, as K
+ *   acts on T_{s_j - 2} / X^n_{s_k - 2}; aM != 0 costs one more mass product per step.
+ * iga_set_forcing -- F(t) = sum_{m < nterm} G_m sin(omega_m t + phase_m), nterm <= 8,
+ *   G device [nterm][N] (copied), omega / phase host. Block j uses the derivative
+ *   F^{(s_j)} at t_{n+1} for j < k (alpha_f = 1) and at t_n for j = k (alpha_f = 0),
+ *   by the closed form d^s/dt^s sin(w t + p) = w^s sin(w t + p + s pi/2).
+ * iga_set_time / iga_get_time -- t_n of the handle's state (host double). Each
+ *   step advances it by dt on the device and on the host; iga_state_init
+ *   evaluates F^{(a)} at the current t and leaves it unchanged.
+ * All return IGA_EINVAL for negative or non-finite values; the setters synchronise.
+ */
+int iga_set_damping(iga_handle* h, double aM, double aK);
+int iga_set_forcing(iga_handle* h, int nterm, const double* G, const double* omega, const double* phase);
+int iga_set_time(iga_handle* h, double t);
+int iga_get_time(iga_handle* h, double* t);
+
+/*
+ * iga_state_init -- initial high-order data (Sec. 3, after eq. 4aup):
+ * X_a = M^{-1}(F^{(a)}(t) - K X_{a-2} - C X_{a-1}), a = 0..3k-3, with X_{-2} = U0,
+ * X_{-1} = V0 (C, F and t as set above; without them the even and odd chains are
+ * solved in pairs).
  *   k      order parameter, 1 <= k <= 4 (order 2k).
  *   U0, V0 device, N doubles each.
  *   state  device, 3k*N doubles, caller-owned: rows U, V, A, L^1, ..., L^{3k-3}.

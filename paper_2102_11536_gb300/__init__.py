@@ -99,6 +99,10 @@ def lib():
         "iga_net_backward": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp, vp, vp, vp, ctypes.c_ulonglong, vp]),
         "iga_net_adam": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]),
         "iga_set_band_config": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
+        "iga_set_damping": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_double]),
+        "iga_set_forcing": (ctypes.c_int, [H, ctypes.c_int, vp, dp, dp]),
+        "iga_set_time": (ctypes.c_int, [H, ctypes.c_double]),
+        "iga_get_time": (ctypes.c_int, [H, dp]),
         "iga_autotune": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ip, ip]),
         "iga_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(H), ctypes.POINTER(H)]),
         "iga_batch_destroy": (None, [H]),
@@ -124,7 +128,7 @@ def exported_symbols():
             "iga_ws_samples", "iga_ws_train", "iga_ws_init_params", "iga_ws_get_params", "iga_ws_set_params",
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
-            "iga_batch_step"]
+            "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time"]
 
 
 def fp64_fma_probe(device=0):
@@ -363,6 +367,30 @@ class Patch:
         self._chk(lib().iga_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
                                          ctypes.byref(by)), "iga_profile_read")
         return ms.value, n.value, fl.value, by.value
+
+    # -- general model M U'' + C U' + K U = F ---------------------------------------
+    def set_damping(self, aM, aK):
+        """Rayleigh damping C = aM M + aK K."""
+        self._chk(lib().iga_set_damping(self.h, aM, aK), "iga_set_damping")
+
+    def set_forcing(self, G, omegas, phases):
+        """F(t) = sum_m G[m] sin(omegas[m] t + phases[m]); G: device float64 tensor [nterm][N] (copied)."""
+        n = len(omegas)
+        if len(phases) != n:
+            raise ValueError("one phase per frequency")
+        if n:
+            _check_dev(G, n * self.N, "G")
+        om = (ctypes.c_double * max(n, 1))(*[float(v) for v in omegas])
+        ph = (ctypes.c_double * max(n, 1))(*[float(v) for v in phases])
+        self._chk(lib().iga_set_forcing(self.h, n, _ptr(G) if n else None, om, ph), "iga_set_forcing")
+
+    def set_time(self, t):
+        self._chk(lib().iga_set_time(self.h, t), "iga_set_time")
+
+    def get_time(self):
+        t = ctypes.c_double()
+        self._chk(lib().iga_get_time(self.h, ctypes.byref(t)), "iga_get_time")
+        return t.value
 
     # -- launch tuning ------------------------------------------------------------
     def set_band_config(self, threads=0, nv=0):

@@ -78,6 +78,16 @@ struct iga_handle {
   double* d_init = nullptr;    // [kMaxVec] initial relative residuals, summed over solves
   double last_init[kMaxVec] = {};  // initial relative residuals of the last host-driven solve
   int* d_stat = nullptr;       // [2] first error status, any unconverged solve
+  // damping C = aM M + aK K and forcing F(t) = sum_m G_m sin(om_m t + ph_m) (eq. mp)
+  bool damped = false;
+  double aM = 0.0, aK = 0.0;
+  int nforce = 0;
+  double* fG = nullptr;  // [nforce][N] load vectors
+  double fom[kMaxForce] = {}, fph[kMaxForce] = {};
+  double *Yv = nullptr, *MYv = nullptr;  // [k][N] when aM != 0
+  int yv_k = 0;
+  double* d_time = nullptr;  // t_n on the device (advanced inside each step)
+  double time = 0.0;         // the same on the host
   // learned initial guess (kernels_net.cu)
   float *ws_theta = nullptr, *ws_m = nullptr, *ws_v = nullptr, *ws_grad = nullptr;
   bool ws_params = false, ws_trained = false;
@@ -211,6 +221,7 @@ void galpha_params(int k, double rho, double* alpha, double* beta, double* gamma
 // Taylor coefficients tau^m / m! and the block parameters of one step.
 StepCoefs step_coefs(int k, double rho, double dt) {
   StepCoefs sc{};
+  sc.damped = 0;
   sc.k = k;
   sc.tau = dt;
   double fact = 1.0;
@@ -219,6 +230,15 @@ StepCoefs step_coefs(int k, double rho, double dt) {
     sc.c[m] = std::pow(dt, m) / fact;
   }
   galpha_params(k, rho, sc.alpha, sc.beta, sc.gamma);
+  return sc;
+}
+
+// The same with the handle's damping (predictor forms Y + aK Y').
+StepCoefs handle_coefs(const iga_handle* h, int k, double rho, double dt) {
+  StepCoefs sc = step_coefs(k, rho, dt);
+  sc.damped = h->damped ? 1 : 0;
+  sc.aM = h->aM;
+  sc.aK = h->aK;
   return sc;
 }
 
@@ -718,6 +738,46 @@ int ensure_ws_step(iga_handle* h, int k) {
   return IGA_OK;
 }
 
+// Buffers of the damping term aM M Y'_j for k stages, and the device time.
+int ensure_damp_ws(iga_handle* h, int k) {
+  if (!h->d_time) {
+    CKS(dalloc(h, &h->d_time, 1));
+    CK(cudaMemcpy(h->d_time, &h->time, sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!(h->damped && h->aM != 0.0) || h->yv_k >= k) return IGA_OK;
+  drop_step_graph(h);
+  CKS(dalloc(h, &h->Yv, (size_t)k * h->N));
+  CKS(dalloc(h, &h->MYv, (size_t)k * h->N));
+  h->yv_k = k;
+  return IGA_OK;
+}
+
+bool m_term(const iga_handle* h) { return h->damped && h->aM != 0.0; }
+
+// Loads of the stages after the predictor: rhs_j = F^{(s_j)}(t_{n+alpha_fj}) - K (Y_j + aK Y'_j)
+// - aM M Y'_j (eq. ho1 with C = aM M + aK K; Yneg = -(Y_j + aK Y'_j), Yv = -Y'_j).
+int stage_rhs(iga_handle* h, cudaStream_t s, int k, const StepCoefs& sc) {
+  CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+  const bool mt = m_term(h);
+  if (mt) CKS(apply_M(h, k, nullptr, h->Yv, h->MYv));
+  if (mt || h->nforce > 0) {
+    StageLoad a{};
+    a.nstage = k;
+    for (int j = 0; j < k; ++j) {
+      a.sder[j] = 3 * j;
+      a.toff[j] = j < k - 1 ? sc.tau : 0.0;  // alpha_f = 1 for the blocks j < k, 0 for the last
+    }
+    a.nterm = h->nforce;
+    for (int m = 0; m < h->nforce; ++m) {
+      a.om[m] = h->fom[m];
+      a.ph[m] = h->fph[m];
+    }
+    a.aM = h->aM;
+    LK(launch_stage_load(s, h->N, a, h->fG, h->d_time, mt ? h->MYv : nullptr, h->rhs));
+  }
+  return IGA_OK;
+}
+
 NetGrid net_grid_of(const iga_handle* h) { return NetGrid{h->n[0], h->n[1], h->n[2]}; }
 
 // The learned guess of the k solves of a step, two steps of history present:
@@ -764,6 +824,7 @@ int prepare_capture(iga_handle* h, int k) {
   CKS(ensure_cg_ws(h, k));
   CKS(ensure_op_ws(h, k));
   if (h->opt.guess == IGA_GUESS_LEARNED) CKS(ensure_ws_step(h, k));
+  CKS(ensure_damp_ws(h, k));
   if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
   return IGA_OK;
 }
@@ -782,8 +843,9 @@ int capture_step(iga_handle* h, double* state, int k, const StepCoefs& sc) {
   const long long N = h->N;
   const int guess = h->opt.guess;
   const long long l0 = h->nlaunch;
-  LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr));
-  CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+  LK(launch_predict(h->gs, N, sc, state, h->Yneg, guess == IGA_GUESS_TAYLOR ? h->Z : nullptr,
+                    m_term(h) ? h->Yv : nullptr));
+  CKS(stage_rhs(h, h->gs, k, sc));
   if (guess == IGA_GUESS_EXTRAP) LK(launch_extrap(h->gs, (long long)k * N, h->Z, h->Z2));
   if (guess == IGA_GUESS_LEARNED) CKS(learned_guess(h, h->gs, k, h->ws_x));
   CKS(solve_begin(h, k, h->rhs, h->Z, guess != IGA_GUESS_ZERO));
@@ -826,6 +888,7 @@ int capture_step(iga_handle* h, double* state, int k, const StepCoefs& sc) {
   const long long l2 = h->nlaunch;
   LK(launch_accum(h->gs, k, h->cs, h->d_tot, h->d_max, h->d_init, h->d_stat));
   LK(launch_update(h->gs, N, sc, state, h->Z));
+  LK(launch_advance_time(h->gs, h->d_time, sc.tau));
   h->g_epi = h->nlaunch - l2;
   return IGA_OK;
 }
@@ -880,7 +943,7 @@ int reset_graph_counters(iga_handle* h, cudaStream_t s) {
 
 // After nsteps replays (ordered before later work on s): launch count, history,
 // statistics and the error status of the solves. Synchronises s.
-int collect_graph_run(iga_handle* h, cudaStream_t s, int k, int nsteps, iga_stats* stats) {
+int collect_graph_run(iga_handle* h, cudaStream_t s, int k, int nsteps, double dt, iga_stats* stats) {
   long long tot[kMaxVec];
   int mx[kMaxVec], st[2], loop[2];
   double rr[kMaxVec], bb[kMaxVec], ini[kMaxVec];
@@ -894,6 +957,7 @@ int collect_graph_run(iga_handle* h, cudaStream_t s, int k, int nsteps, iga_stat
   CK(cudaStreamSynchronize(s));
   h->nlaunch += (long long)nsteps * (h->g_pro + h->g_epi) + (long long)loop[1] * h->g_body;
   h->hist = std::min(h->hist + nsteps, 2);
+  for (int i = 0; i < nsteps; ++i) h->time += dt;  // the device adds dt once per step too
   if (stats) {
     stats->steps += nsteps;
     stats->solves += k * nsteps;
@@ -945,7 +1009,7 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
   for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(h->gexec, h->gs));
   CK(cudaEventRecord(h->ev_out, h->gs));
   CK(cudaStreamWaitEvent(s, h->ev_out, 0));
-  return collect_graph_run(h, s, k, nsteps, stats);
+  return collect_graph_run(h, s, k, nsteps, sc.tau, stats);
 }
 
 }  // namespace
@@ -1029,6 +1093,7 @@ void iga_destroy(iga_handle* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_init); dfree(h->d_stat);
+  dfree(h->fG); dfree(h->Yv); dfree(h->MYv); dfree(h->d_time);
   dfree(h->ws_theta); dfree(h->ws_m); dfree(h->ws_v); dfree(h->ws_grad);
   dfree(h->ws_E); dfree(h->ws_B1); dfree(h->ws_B2); dfree(h->ws_sc); dfree(h->ws_part);
   dfree(h->ws_x); dfree(h->ws_act); dfree(h->ws_sx); dfree(h->ws_st);
@@ -1205,6 +1270,56 @@ int iga_set_guess(iga_handle* h, int guess) {
   h->opt.guess = guess;
   return IGA_OK;
 }
+int iga_set_damping(iga_handle* h, double aM, double aK) {
+  CKS(check_handle(h));
+  if (!(aM >= 0.0 && aK >= 0.0 && std::isfinite(aM) && std::isfinite(aK)))
+    return fail(h, IGA_EINVAL, "damping coefficients must be finite and non-negative");
+  h->damped = aM != 0.0 || aK != 0.0;
+  h->aM = aM;
+  h->aK = aK;
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_set_forcing(iga_handle* h, int nterm, const double* G, const double* omega, const double* phase) {
+  CKS(check_handle(h));
+  if (nterm < 0 || nterm > kMaxForce || (nterm > 0 && (!G || !omega || !phase)))
+    return fail(h, IGA_EINVAL, "need 0 <= nterm <= 8 and non-NULL arrays");
+  for (int m = 0; m < nterm; ++m)
+    if (!std::isfinite(omega[m]) || !std::isfinite(phase[m])) return fail(h, IGA_EINVAL, "non-finite frequency");
+  CK(cudaStreamSynchronize(h->stream));
+  dfree(h->fG);
+  h->nforce = 0;
+  if (nterm > 0) {
+    CKS(dalloc(h, &h->fG, (size_t)nterm * h->N));
+    CK(cudaMemcpy(h->fG, G, sizeof(double) * nterm * h->N, cudaMemcpyDeviceToDevice));
+    for (int m = 0; m < nterm; ++m) {
+      h->fom[m] = omega[m];
+      h->fph[m] = phase[m];
+    }
+    h->nforce = nterm;
+  }
+  drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_set_time(iga_handle* h, double t) {
+  CKS(check_handle(h));
+  if (!std::isfinite(t)) return fail(h, IGA_EINVAL, "non-finite time");
+  CKS(ensure_damp_ws(h, 0));
+  CK(cudaStreamSynchronize(h->stream));
+  h->time = t;
+  CK(cudaMemcpy(h->d_time, &h->time, sizeof(double), cudaMemcpyHostToDevice));
+  return IGA_OK;
+}
+
+int iga_get_time(iga_handle* h, double* t) {
+  CKS(check_handle(h));
+  if (!t) return fail(h, IGA_EINVAL, "t is NULL");
+  *t = h->time;
+  return IGA_OK;
+}
+
 int iga_set_graphs(iga_handle* h, int on) {
   if (!h) return IGA_EINVAL;
   h->use_graphs = on != 0;
@@ -1262,14 +1377,42 @@ int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, dou
   CKS(ensure_step_ws(h, 2));
   CK(cudaMemcpyAsync(state, U0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(state + N, V0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-  // X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3: the chains of even and odd a are
-  // independent, so consecutive pairs are solved together.
+  CKS(ensure_damp_ws(h, 1));
   const int last = 3 * k - 3;
-  for (int a = 0; a <= last; a += 2) {
-    const int nv = (a + 1 <= last) ? 2 : 1;
-    CKS(apply_K(h, nv, nullptr, state + (long long)a * N, h->rhs));
-    LK(launch_scale_neg(s, nv * N, h->rhs));
-    CKS(solve(h, nv, h->rhs, state + (long long)(a + 2) * N, false, nullptr, nullptr));
+  if (!h->damped && h->nforce == 0) {
+    // X_a = M^{-1}(-K X_{a-2}), a = 0..3k-3: the chains of even and odd a are
+    // independent, so consecutive pairs are solved together.
+    for (int a = 0; a <= last; a += 2) {
+      const int nv = (a + 1 <= last) ? 2 : 1;
+      CKS(apply_K(h, nv, nullptr, state + (long long)a * N, h->rhs));
+      LK(launch_scale_neg(s, nv * N, h->rhs));
+      CKS(solve(h, nv, h->rhs, state + (long long)(a + 2) * N, false, nullptr, nullptr));
+    }
+  } else {
+    // X_a = M^{-1}(F^{(a)}(t) - K X_{a-2} - C X_{a-1}) in order (the damping couples the chains)
+    for (int a = 0; a <= last; ++a) {
+      const double* xd = state + (long long)a * N;        // X_{a-2}
+      const double* xv = state + (long long)(a + 1) * N;  // X_{a-1}
+      LK(launch_lincomb(s, N, -1.0, xd, -h->aK, xv, h->Yneg));
+      CKS(apply_K(h, 1, nullptr, h->Yneg, h->rhs));
+      const bool mt = m_term(h);
+      if (mt) {
+        LK(launch_lincomb(s, N, -1.0, xv, 0.0, xv, h->Yv));
+        CKS(apply_M(h, 1, nullptr, h->Yv, h->MYv));
+      }
+      StageLoad ld{};
+      ld.nstage = 1;
+      ld.sder[0] = a;
+      ld.toff[0] = 0.0;
+      ld.nterm = h->nforce;
+      for (int m = 0; m < h->nforce; ++m) {
+        ld.om[m] = h->fom[m];
+        ld.ph[m] = h->fph[m];
+      }
+      ld.aM = h->aM;
+      LK(launch_stage_load(s, N, ld, h->fG, h->d_time, mt ? h->MYv : nullptr, h->rhs));
+      CKS(solve(h, 1, h->rhs, state + (long long)(a + 2) * N, false, nullptr, nullptr));
+    }
   }
   h->hist = 0;
   return IGA_OK;
@@ -1282,7 +1425,8 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
   const long long N = h->N;
   cudaStream_t s = h->stream;
   CKS(ensure_step_ws(h, k));
-  const StepCoefs sc = step_coefs(k, rho_inf, dt);
+  CKS(ensure_damp_ws(h, k));
+  const StepCoefs sc = handle_coefs(h, k, rho_inf, dt);
   const long long launches0 = h->nlaunch;
   for (int step = 0; step < nsteps; ++step) {
     const int guess = h->opt.guess;
@@ -1307,8 +1451,8 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
       }
     }
     const bool taylor = guess == IGA_GUESS_TAYLOR;
-    LK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr));
-    CKS(apply_K(h, k, nullptr, h->Yneg, h->rhs));
+    LK(launch_predict(s, N, sc, state, h->Yneg, taylor ? h->Z : nullptr, m_term(h) ? h->Yv : nullptr));
+    CKS(stage_rhs(h, s, k, sc));
     bool use_x0 = false;
     if (taylor) {
       use_x0 = true;
@@ -1348,6 +1492,8 @@ int iga_step(iga_handle* h, double* state, int k, double rho_inf, double dt, int
       h->ws_count += k;
     }
     LK(launch_update(s, N, sc, state, h->Z));
+    LK(launch_advance_time(s, h->d_time, dt));
+    h->time += dt;
     h->hist = std::min(h->hist + 1, 2);
     if (stats) {
       stats->steps += 1;
@@ -1788,7 +1934,7 @@ int build_batch_graph(iga_batch* b, double* const* states, int k, double rho, co
     iga_handle* h = b->p[i];
     e = cudaStreamWaitEvent(h->gs, b->fork, 0);
     if (e != cudaSuccess) break;
-    rc = capture_step(h, states[i], k, step_coefs(k, rho, dt[i]));
+    rc = capture_step(h, states[i], k, handle_coefs(h, k, rho, dt[i]));
     if (rc != IGA_OK) {
       msg = "patch " + std::to_string(i) + ": " + h->err;
       break;
@@ -1925,7 +2071,7 @@ int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, c
   int first = IGA_OK;
   for (int i = 0; i < np; ++i) {
     iga_handle* h = b->p[i];
-    const int rc = collect_graph_run(h, b->s0, k, n, stats ? &stats[i] : nullptr);
+    const int rc = collect_graph_run(h, b->s0, k, n, dt[i], stats ? &stats[i] : nullptr);
     if (stats) stats[i].launches += h->nlaunch - l0[i];
     if (rc != IGA_OK && first == IGA_OK) {
       first = rc;

@@ -171,9 +171,29 @@ struct StepCoefs {
   double c[kMaxRows];          // tau^m / m!
   double alpha[kMaxK], beta[kMaxK], gamma[kMaxK];
   double tau;
+  int damped;                  // Rayleigh damping C = aM M + aK K present
+  double aM, aK;
 };
-// Writes -Y_j (k vectors) and, if T != nullptr, the Taylor predictor T_{s_j} of each solved row.
-cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T);
+// Writes -Y_j (k vectors) and, if T != nullptr, the Taylor predictor T_{s_j} of each
+// solved row. With damping: -(Y_j + aK Y'_j) (K acts on it), and -Y'_j into Yv if
+// Yv != nullptr (the aM M Y'_j term), Y'_j the predictor of the block's velocity-like row.
+cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T,
+                           double* Yv);
+// Loads of the stage equations (eq. ho1): rhs[j] += aM * MYv[j] (MYv nullable) +
+// sum_m G_m om_m^{s_j} sin(om_m t_j + ph_m + s_j pi/2), t_j = *time + toff[j].
+constexpr int kMaxForce = 8;
+struct StageLoad {
+  int nstage;
+  int sder[kMaxK];
+  double toff[kMaxK];
+  int nterm;
+  double om[kMaxForce], ph[kMaxForce];
+  double aM;
+};
+cudaError_t launch_stage_load(cudaStream_t s, long long N, StageLoad a, const double* G, const double* time,
+                              const double* MYv, double* rhs);
+// *time += dt (one thread)
+cudaError_t launch_advance_time(cudaStream_t s, double* time, double dt);
 // Fused stage update in place.
 cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, const double* Z);
 // Z <- 2 Z - Z2, Z2 <- old Z
@@ -184,6 +204,9 @@ cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle hc, const
 // tot += iterations, mx = max iterations, init += ||b - M x0|| / ||b||, stat = first error / unconverged
 cudaError_t launch_accum(cudaStream_t s, int nvec, CgScalars c, long long* tot, int* mx, double* init, int* stat);
 cudaError_t launch_scale_neg(cudaStream_t s, long long n, double* x);
+// out = ca * a + cb * b (n entries)
+cudaError_t launch_lincomb(cudaStream_t s, long long n, double ca, const double* a, double cb, const double* b,
+                           double* out);
 
 // BF16 / FP16 tensor-core mode product along `axis` (kernels_tc.cu): B is the
 // 16-bit matrix arranged by tc_arrange (f16 selects FP16 with per-line power-of-two

@@ -274,7 +274,8 @@ cudaError_t launch_copy_active(cudaStream_t s, long long N, int nvec, const int*
 // ----------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(256) k_predict(long long N, StepCoefs sc, const double* __restrict__ X,
-                                                 double* __restrict__ Yneg, double* __restrict__ T) {
+                                                 double* __restrict__ Yneg, double* __restrict__ T,
+                                                 double* __restrict__ Yv) {
   constexpr int R = 3 * K;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -292,6 +293,18 @@ __global__ void __launch_bounds__(256) k_predict(long long N, StepCoefs sc, cons
       for (int r = R - 1; r >= ry; --r) y = fma(sc.c[r - ry], x[r], y);
     } else {                     // alpha_f = 0: the current value
       y = x[ry];
+    }
+    if (sc.damped) {             // the same for the velocity-like row ry + 1
+      double yv;
+      if (j < K - 1) {
+        yv = 0.0;
+#pragma unroll
+        for (int r = R - 1; r >= ry + 1; --r) yv = fma(sc.c[r - ry - 1], x[r], yv);
+      } else {
+        yv = x[ry + 1];
+      }
+      y = fma(sc.aK, yv, y);
+      if (Yv) Yv[j * N + i] = -yv;
     }
     Yneg[j * N + i] = -y;
     if (T) {
@@ -330,13 +343,14 @@ __global__ void __launch_bounds__(256) k_update(long long N, StepCoefs sc, doubl
   }
 }
 
-cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T) {
+cudaError_t launch_predict(cudaStream_t s, long long N, StepCoefs sc, const double* X, double* Yneg, double* T,
+                           double* Yv) {
   const unsigned blocks = (unsigned)((N + 255) / 256);
   switch (sc.k) {
-    case 1: k_predict<1><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
-    case 2: k_predict<2><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
-    case 3: k_predict<3><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
-    case 4: k_predict<4><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T); break;
+    case 1: k_predict<1><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T, Yv); break;
+    case 2: k_predict<2><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T, Yv); break;
+    case 3: k_predict<3><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T, Yv); break;
+    case 4: k_predict<4><<<blocks, 256, 0, s>>>(N, sc, X, Yneg, T, Yv); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -351,6 +365,59 @@ cudaError_t launch_update(cudaStream_t s, long long N, StepCoefs sc, double* X, 
     case 4: k_update<4><<<blocks, 256, 0, s>>>(N, sc, X, Z); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Loads of the stage equations: the time derivatives of F(t) = sum_m G_m sin(om_m t + ph_m)
+// are closed forms, d^s/dt^s sin(w t + p) = w^s sin(w t + p + s pi/2).
+__global__ void __launch_bounds__(256) k_stage_load(long long N, StageLoad a, const double* __restrict__ G,
+                                                    const double* __restrict__ time,
+                                                    const double* __restrict__ MYv, double* __restrict__ rhs) {
+  __shared__ double coef[kMaxK * kMaxForce];
+  const int tid = threadIdx.x;
+  if (tid < a.nstage * a.nterm) {
+    const int j = tid / a.nterm, m = tid - j * a.nterm;
+    const int sd = a.sder[j];
+    const double t = *time + a.toff[j];
+    double w = 1.0;
+    for (int q = 0; q < sd; ++q) w *= a.om[m];
+    coef[tid] = w * sin(a.om[m] * t + a.ph[m] + sd * 1.5707963267948966);
+  }
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < N; i += (long long)gridDim.x * blockDim.x)
+    for (int j = 0; j < a.nstage; ++j) {
+      double r = rhs[j * N + i];
+      if (MYv) r = fma(a.aM, MYv[j * N + i], r);
+      for (int m = 0; m < a.nterm; ++m) r = fma(coef[j * a.nterm + m], G[m * N + i], r);
+      rhs[j * N + i] = r;
+    }
+}
+
+cudaError_t launch_stage_load(cudaStream_t s, long long N, StageLoad a, const double* G, const double* time,
+                              const double* MYv, double* rhs) {
+  if (a.nstage < 1 || a.nstage > kMaxK || a.nterm < 0 || a.nterm > kMaxForce) return cudaErrorInvalidValue;
+  k_stage_load<<<kRedBlocks, 256, 0, s>>>(N, a, G, time, MYv, rhs);
+  return cudaGetLastError();
+}
+
+__global__ void k_advance_time(double* time, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *time += dt;
+}
+
+cudaError_t launch_advance_time(cudaStream_t s, double* time, double dt) {
+  k_advance_time<<<1, 32, 0, s>>>(time, dt);
+  return cudaGetLastError();
+}
+
+__global__ void k_lincomb(long long n, double ca, const double* __restrict__ a, double cb,
+                          const double* __restrict__ b, double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = fma(ca, a[i], cb * b[i]);
+}
+
+cudaError_t launch_lincomb(cudaStream_t s, long long n, double ca, const double* a, double cb, const double* b,
+                           double* out) {
+  k_lincomb<<<kRedBlocks, 256, 0, s>>>(n, ca, a, cb, b, out);
   return cudaGetLastError();
 }
 
