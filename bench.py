@@ -111,6 +111,8 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
+    ap.add_argument("--no-general", dest="general", action="store_false",
+                    help="skip the damped, forced variant of the headline step")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven PCG loop for every form (the same kernels; for profilers that cannot "
                          "see inside graphs with conditional nodes)")
@@ -391,6 +393,43 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     return out
 
 
+def run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush):
+    """The general model M U'' + C U' + K U = F on the headline workload and form:
+    Rayleigh damping C = 0.4 M + 1e-4 K and two harmonic loads; timed like the forms."""
+    import numpy as np
+    k = w.k
+    N = patch.N
+    G = torch.from_numpy(np.random.default_rng(7).standard_normal((2, N))).to(state.device)
+    patch.set_op_form("assembled")
+    patch.set_precond("banded32")
+    patch.set_guess("zero")
+    patch.set_graphs(not args.no_graphs)
+    patch.set_damping(0.4, 1e-4)
+    patch.set_forcing(G, [2.0, 5.0], [0.3, -1.0])
+    patch.set_time(0.0)
+    patch.state_init(k, u0, v0, state)
+    for _ in range(args.warmup):
+        patch.step(state, k, w.rho, dt, 1)
+    stats = iga.Stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        patch.step(state, k, w.rho, dt, 1, stats)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    patch.set_damping(0.0, 0.0)
+    patch.set_forcing(None, [], [])
+    patch.set_time(0.0)
+    return {"form": "mixed_banded32 with C = 0.4 M + 1e-4 K and F(t) = G1 sin(2t + 0.3) + G2 sin(5t - 1)",
+            "value": args.steps / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms / args.steps,
+            "pcg_iters_per_solve": stats.iters / max(stats.solves, 1), "gpu_launches": int(stats.launches),
+            "note": "one more mass product per step for the aM M term; parity in tests/test_gpu_general.py"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -518,6 +557,7 @@ def run_ours(args):
     if pg:
         pg.barrier()
     e2e_rate = world * args.steps / e2e_s
+    general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush) if args.general else None
     batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
 
     if rank != 0:
@@ -573,6 +613,8 @@ def run_ours(args):
     }
     if batch_res is not None:
         result["multipatch_batch"] = batch_res
+    if general is not None:
+        result["general_model"] = general
     if not args.no_cpu_baseline and world == 1:
         base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
         result["cpu_baseline"] = base
