@@ -44,6 +44,8 @@ struct iga_handle {
   int cg_vec = 0;
   double *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *f1 = nullptr, *f2 = nullptr;
   double* partial = nullptr;  // 3 * kMaxVec * kRedBlocks
+  double* pq_part = nullptr;  // per-block partials of p.q from the band product, cg_vec * (N / 64 + 2)
+  double* rz_part = nullptr;  // per-block partials of r.z, r.z_old from the preconditioner, 2 cg_vec (N / 32 + 2)
   CgScalars cs{};
   int* h_nactive = nullptr;   // pinned
   // stepping
@@ -280,6 +282,8 @@ int ensure_cg_ws(iga_handle* h, int nvec) {
   CKS(dalloc(h, &h->q, sz));
   CKS(dalloc(h, &h->f1, sz));
   CKS(dalloc(h, &h->f2, sz));
+  CKS(dalloc(h, &h->pq_part, (size_t)nvec * (size_t)(h->N / 64 + 2)));
+  CKS(dalloc(h, &h->rz_part, (size_t)2 * nvec * (size_t)(h->N / 32 + 2)));
   h->cg_vec = nvec;
   return IGA_OK;
 }
@@ -367,7 +371,11 @@ int apply_K_mf(iga_handle* h, int nvec, const int* active, const double* x, doub
 // axis, division by Lambda_0(i0) Lambda_1(i1) Lambda_2(i2), U along each axis, S.
 // FP64 form: all in FP64. FP32 form: the scaled residual is rounded to FP32,
 // mode products and Lambda in FP32, final rescale in FP64.
-int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* t1, double* t2) {
+// rzp (nullable): with the band-Cholesky forms, per-block partials of r.z and r.z_old
+// (z's previous content) come out of the last axis, [2][nvec][*nrz]; *nrz = 0 otherwise.
+int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* t1, double* t2,
+             double* rzp = nullptr, int* nrz = nullptr) {
+  if (nrz) *nrz = 0;
   cudaStream_t s = h->stream;
   const int* n = h->n;
   const DirDev* d = h->dd;
@@ -411,10 +419,10 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
     if (d3) {
       LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n12}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
       LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], n[2]}, nvec, active, f32, L[1], Di[1], t1, mid, t2, mid, N, nullptr, nullptr));
-      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc));
+      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz));
     } else {
       LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n[1]}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
-      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc));
+      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz));
     }
     return IGA_OK;
   }
@@ -538,20 +546,25 @@ int assemble_band(iga_handle* h) {
   return IGA_OK;
 }
 
-int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* active, const double* x, double* y) {
+int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* active, const double* x, double* y,
+               double* pq = nullptr, int* npq = nullptr) {
   const int nact = active ? h->cur_active : nvec;
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, cls, &e));
   LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, h->band_o12, h->n, A, active, nvec, x, y, h->N,
-                        h->band_threads, h->band_nv));
+                        h->band_threads, h->band_nv, pq, npq));
   CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
 
-int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+// y = M x; with pq, the assembled form also leaves per-block partials of x . y in pq
+// ([nvec][*npq]); *npq = 0 when they were not computed (matrix-free form).
+int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
+            int* npq = nullptr) {
+  if (npq) *npq = 0;
   if (h->opt.op_form == IGA_OP_ASSEMBLED) {
     CKS(assemble_band(h));
-    return apply_band(h, h->Mband, IGA_PROF_BAND_MASS, nvec, active, x, y);
+    return apply_band(h, h->Mband, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq);
   }
   return apply_M_mf(h, nvec, active, x, y);
 }
@@ -562,14 +575,15 @@ int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double*
   }
   return apply_K_mf(h, nvec, active, x, y);
 }
-int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z) {
+int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* rzp = nullptr,
+               int* nrz = nullptr) {
   const int nact = active ? h->cur_active : nvec;
   double modes = 0.0;  // sum_a n_a: one mode product costs 2 n_a flops per entry, done twice
   for (int a = 0; a < h->dim; ++a) modes += h->n[a];
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, IGA_PROF_PRECOND, &e));
   CKS(ensure_cg_ws(h, nvec));
-  CKS(fd_apply(h, nvec, active, r, z, h->f1, h->f2));
+  CKS(fd_apply(h, nvec, active, r, z, h->f1, h->f2, rzp, nrz));
   CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
   return IGA_OK;
 }
@@ -605,9 +619,14 @@ int solve_prime(iga_handle* h, int nvec) {
   cudaStream_t s = h->stream;
   const long long N = h->N;
   CgScalars& c = h->cs;
-  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-  LK(launch_dot(s, N, nvec, h->r, h->z, N, h->partial));
-  LK(launch_cg_start(s, nvec, h->partial, c));
+  int nrz = 0;
+  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z, h->rz_part, &nrz));
+  if (nrz > 0) {  // r.z came with the preconditioner's last pass
+    LK(launch_cg_start(s, nvec, h->rz_part, nrz, c));
+  } else {
+    LK(launch_dot(s, N, nvec, h->r, h->z, N, h->partial));
+    LK(launch_cg_start(s, nvec, h->partial, kRedBlocks, c));
+  }
   LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
   return IGA_OK;
 }
@@ -619,9 +638,14 @@ int solve_iter_a(iga_handle* h, int nvec, double* x) {
   CgScalars& c = h->cs;
   double* pA = h->partial;
   double* pB = h->partial + kMaxVec * kRedBlocks;
-  CKS(apply_M(h, nvec, c.active, h->p, h->q));
-  LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
-  LK(launch_cg_alpha(s, nvec, pA, c));
+  int npq = 0;
+  CKS(apply_M(h, nvec, c.active, h->p, h->q, h->pq_part, &npq));
+  if (npq > 0) {  // p.q came with the band product
+    LK(launch_cg_alpha(s, nvec, h->pq_part, npq, c));
+  } else {
+    LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
+    LK(launch_cg_alpha(s, nvec, pA, kRedBlocks, c));
+  }
   LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
   LK(launch_cg_check(s, nvec, pB, c, h->opt.tol * h->opt.tol));
   return IGA_OK;
@@ -636,10 +660,18 @@ int solve_iter_b(iga_handle* h, int nvec) {
   double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
   // the FP64 preconditioners are symmetric and linear to rounding: plain CG
   const bool flexible = h->opt.precond != IGA_PREC_FP64 && h->opt.precond != IGA_PREC_BANDED;
-  if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
-  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-  LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-  LK(launch_cg_beta(s, nvec, pA, pC, c, flexible ? 1 : 0));
+  const bool fused = h->opt.precond == IGA_PREC_BANDED || h->opt.precond == IGA_PREC_BANDED32;
+  int nrz = 0;
+  if (fused) {  // r.z and r.z_old come with the preconditioner's last pass
+    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z, h->rz_part, &nrz));
+    if (nrz <= 0) return fail(h, IGA_ECUDA, "fused inner products missing");
+    LK(launch_cg_beta(s, nvec, h->rz_part, h->rz_part + (size_t)nvec * nrz, nrz, c, flexible ? 1 : 0));
+  } else {
+    if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
+    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
+    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
+    LK(launch_cg_beta(s, nvec, pA, pC, kRedBlocks, c, flexible ? 1 : 0));
+  }
   LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
   return IGA_OK;
 }
@@ -1080,7 +1112,7 @@ void iga_destroy(iga_handle* h) {
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
-  dfree(h->partial);
+  dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
   dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
   dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
   if (h->h_nactive) cudaFreeHost(h->h_nactive);

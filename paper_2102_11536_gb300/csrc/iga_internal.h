@@ -147,13 +147,14 @@ struct CgScalars {  // device arrays, one entry per system
   int* nactive;    // single counter
 };
 // Reduction epilogues of PCG (one thread per system, tiny kernels).
-cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, CgScalars c);
+// partials [nvec][np]
+cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int np, CgScalars c);
 cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgScalars c, double tol2);
-cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, CgScalars c,
-                           int flexible);
+cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, int np,
+                           CgScalars c, int flexible);
 cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, const double* partial_rr,
                            CgScalars c, double tol2);
-cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, CgScalars c);
+cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, int np, CgScalars c);
 // x += alpha p; r -= alpha q; partial ||r||^2
 cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
                                 const double* p, const double* q, long long vs, double* partial);
@@ -225,9 +226,10 @@ void tc_arrange(int n, const double* Mat_ij, bool f16, std::vector<uint16_t>& ou
 // o12 (nullable): packed slot offsets along directions 1, 2 ((o1+64) | (o2+64) << 8) for
 // skipping slots outside the grid for a whole warp; n: grid sizes (3 entries).
 // threads: block size 64 / 128 / 256 / 512 (other = 256); nv: vectors per thread (0 = min(nvec, 4)).
+// pq (nullable): per-block partials of x . y, [nvec][*npq] (the p.q of PCG, fused).
 cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const int* o12, const int* n,
                              const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
-                             int threads, int nv);
+                             int threads, int nv, double* pq = nullptr, int* npq = nullptr);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,
@@ -269,9 +271,12 @@ cudaError_t launch_ws_target(cudaStream_t s, long long N, int k, const double* Z
 // it, by forward and backward substitution with the band Cholesky factor (half
 // bandwidth p); pre / post (nullable, per element) multiply the input / output in
 // FP64. f32 selects FP32 arithmetic with the FP32 factor (FP32 or FP64 input / output).
+// rdot (nullable; FP64 output only): also per-block partials of rdot . out and of rdot .
+// (out before the write), [2][nvec][*npart] in part (*npart = 0 if not computed).
 cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nvec, const int* active, int f32,
                              const void* L, const void* dinv, const void* in, int in_is_double, void* out,
-                             int out_is_double, long long vs, const double* pre, const double* post);
+                             int out_is_double, long long vs, const double* pre, const double* post,
+                             const double* rdot = nullptr, double* part = nullptr, int* npart = nullptr);
 
 // Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
 constexpr long long kNoAllocMaxElems = 1LL << 20;

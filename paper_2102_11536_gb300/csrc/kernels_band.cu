@@ -27,24 +27,27 @@ namespace iga {
 // lane of the warp is skipped: its coefficients are zero. Lanes of a warp share
 // (i1, i2) except where the warp wraps a grid line, so the vote is almost always
 // unanimous; skipped lanes would only have added zeros.
+// pq (nullable): per block and vector the partial sum of x_i y_i over the block's rows,
+// at pq[v * gridDim.x + blockIdx.x] (0 for inactive vectors) -- the p.q of PCG.
 template <int NV, int BS>
 __global__ void __launch_bounds__(BS) k_band_spmv(long long N, int H, const long long* __restrict__ off,
                                                   const int* __restrict__ o12, int n0, int n1, int n2,
                                                   const double* __restrict__ A, const int* __restrict__ active,
                                                   int nvec, const double* __restrict__ x, double* __restrict__ y,
-                                                  long long vs) {
+                                                  long long vs, double* __restrict__ pq) {
   const long long i = (long long)blockIdx.x * BS + threadIdx.x;
   const bool row = i < N;  // no early return: the slot votes need every lane
   // up to NV vectors per thread share every coefficient load
   const int v0 = blockIdx.y * NV;
   bool on[NV];
-  double acc[NV];
+  double acc[NV], xi[NV];
   const double a0 = row ? A[i] : 0.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int vv = v0 + v;
     on[v] = row && vv < nvec && (!active || active[vv]);
-    acc[v] = on[v] ? a0 * x[vv * vs + i] : 0.0;
+    xi[v] = on[v] ? x[vv * vs + i] : 0.0;
+    acc[v] = a0 * xi[v];
   }
   int i1 = 0, i2 = 0;
   if (row && o12) {
@@ -81,6 +84,26 @@ __global__ void __launch_bounds__(BS) k_band_spmv(long long N, int H, const long
 #pragma unroll
   for (int v = 0; v < NV; ++v)
     if (on[v]) y[(v0 + v) * vs + i] = acc[v];
+  if (pq) {  // fixed-order block sums: warps by shuffles, then the warps in order
+    __shared__ double sred[BS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int vv = v0 + v;
+      if (vv >= nvec) break;
+      double t = on[v] ? xi[v] * acc[v] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) sred[w] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < BS / 32; ++q) sum += sred[q];
+        pq[(long long)vv * gridDim.x + blockIdx.x] = sum;
+      }
+      __syncthreads();
+    }
+  }
 }
 
 struct BandGeom {
@@ -146,16 +169,17 @@ static BandGeom make_geom(const int* n, const int* p) {
 
 namespace {
 template <int BS>
-void band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, const int* o12, const int* n,
-             const double* A, const int* active, int nvec, const double* x, double* y, long long vs) {
+int band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, const int* o12, const int* n,
+            const double* A, const int* active, int nvec, const double* x, double* y, long long vs, double* pq) {
   const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
   const int n0 = n[0], n1 = n[1], n2 = n[2];
   switch (nv) {
-    case 1: k_band_spmv<1, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
-    case 2: k_band_spmv<2, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
-    case 3: k_band_spmv<3, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
-    default: k_band_spmv<4, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs); break;
+    case 1: k_band_spmv<1, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs, pq); break;
+    case 2: k_band_spmv<2, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs, pq); break;
+    case 3: k_band_spmv<3, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs, pq); break;
+    default: k_band_spmv<4, BS><<<grid, BS, 0, s>>>(N, H, off, o12, n0, n1, n2, A, active, nvec, x, y, vs, pq); break;
   }
+  return (int)grid.x;
 }
 }  // namespace
 
@@ -164,14 +188,16 @@ void band_go(cudaStream_t s, int nv, long long N, int H, const long long* off, c
 // configuration computes each row with the same operations in the same order.
 cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const int* o12, const int* n,
                              const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
-                             int threads, int nv) {
+                             int threads, int nv, double* pq, int* npq) {
   if (nv <= 0) nv = nvec < 4 ? nvec : 4;
   if (nv < 1) nv = 1;
   if (nv > 4) nv = 4;
-  if (threads == 64) band_go<64>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
-  else if (threads == 128) band_go<128>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
-  else if (threads == 512) band_go<512>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
-  else band_go<256>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs);
+  int nb;
+  if (threads == 64) nb = band_go<64>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs, pq);
+  else if (threads == 128) nb = band_go<128>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs, pq);
+  else if (threads == 512) nb = band_go<512>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs, pq);
+  else nb = band_go<256>(s, nv, N, H, off, o12, n, A, active, nvec, x, y, vs, pq);
+  if (npq) *npq = nb;
   return cudaGetLastError();
 }
 

@@ -26,12 +26,16 @@ constexpr int kThreads = 256; // threads staging and writing back
 // P = p: entries below the diagonal in a row of the factor; T: arithmetic (double, or
 // float for the FP32 form); TI / TO: input / output element types. pre / post are
 // applied in FP64 before rounding to T / after widening from T.
+// rdot (nullable, FP64 output only): also the per-block partials of rdot . out (new) and
+// rdot . out (the values out held before: the previous z of flexible PCG) into
+// part[v * gridDim.x + b] and part[(gridDim.y + v) * gridDim.x + b].
 template <int P, typename T, typename TI, typename TO>
 __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long long R, const T* __restrict__ L,
                                                       const T* __restrict__ dinv, const int* __restrict__ active,
                                                       const TI* __restrict__ in, TO* __restrict__ out,
                                                       long long vs, const double* __restrict__ pre,
-                                                      const double* __restrict__ post) {
+                                                      const double* __restrict__ post,
+                                                      const double* __restrict__ rdot, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char kron_smem[];
   T* sb = reinterpret_cast<T*>(kron_smem);  // [n][kLines] lines, then the factor [n][P+1] and 1/L_kk [n]
   T* sL = sb + (size_t)n * kLines;
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
   }
   __syncthreads();
   // write back
+  const double* rv = rdot ? rdot + v * vs : nullptr;
+  double snew = 0.0, sold = 0.0;
   if (A == 1) {
     const long long g0 = l0 * n;
 #pragma unroll 4
@@ -97,6 +103,11 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
       const int line = e / n, k = e - line * n;
       double u = (double)sb[k * kLines + line];
       if (post) u *= post[g0 + e];
+      if (rv) {
+        const double rr = rv[g0 + e];
+        sold = fma(rr, (double)o[g0 + e], sold);
+        snew = fma(rr, u, snew);
+      }
       o[g0 + e] = (TO)u;
     }
   } else {
@@ -108,7 +119,35 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
       const long long g = xx + A * (k + (long long)n * y);
       double u = (double)sb[k * kLines + line];
       if (post) u *= post[g];
+      if (rv) {
+        const double rr = rv[g];
+        sold = fma(rr, (double)o[g], sold);
+        snew = fma(rr, u, snew);
+      }
       o[g] = (TO)u;
+    }
+  }
+  if (rv) {  // fixed-order block sums
+    __shared__ double red[2][kThreads / 32];
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      snew += __shfl_down_sync(0xffffffffu, snew, o2);
+      sold += __shfl_down_sync(0xffffffffu, sold, o2);
+    }
+    if (lane == 0) {
+      red[0][w] = snew;
+      red[1][w] = sold;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) {
+        a += red[0][q];
+        b += red[1][q];
+      }
+      part[(long long)v * gridDim.x + blockIdx.x] = a;
+      part[(long long)(gridDim.y + v) * gridDim.x + blockIdx.x] = b;
     }
   }
 }
@@ -116,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
 template <int P, typename T, typename TI, typename TO>
 cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, const void* L,
                     const void* dinv, const void* in, void* out, long long vs, const double* pre,
-                    const double* post) {
+                    const double* post, const double* rdot, double* part, int* npart) {
   const long long R = sh.A * sh.B;
   const size_t smem = (size_t)n * (kLines + P + 2) * sizeof(T);
   if (smem > 48 * 1024) {
@@ -125,36 +164,46 @@ cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* ac
     if (e != cudaSuccess) return e;
   }
   const dim3 grid((unsigned)((R + kLines - 1) / kLines), (unsigned)nvec);
+  const bool fused = rdot && sizeof(TO) == sizeof(double);
   k_kron_axis<P, T, TI, TO><<<grid, kThreads, smem, s>>>(
       n, sh.A, R, static_cast<const T*>(L), static_cast<const T*>(dinv), active, static_cast<const TI*>(in),
-      static_cast<TO*>(out), vs, pre, post);
+      static_cast<TO*>(out), vs, pre, post, fused ? rdot : nullptr, part);
+  if (npart) *npart = fused ? (int)grid.x : 0;
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t kron_types(cudaStream_t s, int n, AxisShape sh, int nvec, const int* active, int f32, const void* L,
                        const void* dinv, const void* in, int in_is_double, void* out, int out_is_double, long long vs,
-                       const double* pre, const double* post) {
-  if (!f32) return kron_go<P, double, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+                       const double* pre, const double* post, const double* rdot, double* part, int* npart) {
+  if (!f32)
+    return kron_go<P, double, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part,
+                                              npart);
   if (in_is_double && !out_is_double)
-    return kron_go<P, float, double, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+    return kron_go<P, float, double, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part,
+                                            npart);
   if (!in_is_double && out_is_double)
-    return kron_go<P, float, float, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+    return kron_go<P, float, float, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part,
+                                            npart);
   if (!in_is_double && !out_is_double)
-    return kron_go<P, float, float, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
-  return kron_go<P, float, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post);
+    return kron_go<P, float, float, float>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part,
+                                           npart);
+  return kron_go<P, float, double, double>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part, npart);
 }
 
 }  // namespace
 
 cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nvec, const int* active, int f32,
                              const void* L, const void* dinv, const void* in, int in_is_double, void* out,
-                             int out_is_double, long long vs, const double* pre, const double* post) {
+                             int out_is_double, long long vs, const double* pre, const double* post,
+                             const double* rdot, double* part, int* npart) {
+  if (npart) *npart = 0;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
   if (n < 1 || nvec < 1 || (size_t)n * (kLines + p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
   if (!f32 && !(in_is_double && out_is_double)) return cudaErrorInvalidValue;
 #define IGA_KRON(PP) \
-  return kron_types<PP>(s, n, sh, nvec, active, f32, L, dinv, in, in_is_double, out, out_is_double, vs, pre, post)
+  return kron_types<PP>(s, n, sh, nvec, active, f32, L, dinv, in, in_is_double, out, out_is_double, vs, pre, post, \
+                        rdot, part, npart)
   switch (p) {
     case 1: IGA_KRON(1);
     case 2: IGA_KRON(2);

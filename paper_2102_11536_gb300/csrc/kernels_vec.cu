@@ -45,14 +45,14 @@ cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, c
   return cudaGetLastError();
 }
 
-// Warp w of a 256-thread block sums vector w's kRedBlocks partials (lane stride 32,
-// then a shuffle tree): a fixed order, so the result is reproducible, and 32
-// lanes instead of one serial FP64 chain.
-__device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out) {
+// Warp w of a 256-thread block sums vector w's np partials (layout [v][np]; lane
+// stride 32, then a shuffle tree): a fixed order, so the result is reproducible, and
+// 32 lanes instead of one serial FP64 chain.
+__device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out, int np = kRedBlocks) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (w < nvec) {
     double s = 0.0;
-    for (int b = lane; b < kRedBlocks; b += 32) s += partial[w * kRedBlocks + b];
+    for (int b = lane; b < np; b += 32) s += partial[(long long)w * np + b];
     s = warp_sum(s);
     if (lane == 0) out[w] = s;
   }
@@ -108,22 +108,22 @@ cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, c
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kEpiThreads) k_cg_start(int nvec, const double* prz, CgScalars c) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_start(int nvec, const double* prz, int np, CgScalars c) {
   __shared__ double sz[kMaxVec];
-  reduce_partials(nvec, prz, sz);
+  reduce_partials(nvec, prz, sz, np);
   const int v = threadIdx.x;
   if (v < nvec) c.rz[v] = sz[v];
 }
 
-cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, CgScalars c) {
-  k_cg_start<<<1, kEpiThreads, 0, s>>>(nvec, partial_rz, c);
+cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, int np, CgScalars c) {
+  k_cg_start<<<1, kEpiThreads, 0, s>>>(nvec, partial_rz, np, c);
   return cudaGetLastError();
 }
 
 // alpha = r.z / p.q; breakdown (p.q <= 0 or not finite) stops the system with IGA_ENUMERIC.
-__global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double* ppq, CgScalars c) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double* ppq, int np, CgScalars c) {
   __shared__ double sq[kMaxVec];
-  reduce_partials(nvec, ppq, sq);
+  reduce_partials(nvec, ppq, sq, np);
   const int v = threadIdx.x;
   if (v >= nvec) return;
   if (!c.active[v]) {
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double
   c.alpha[v] = c.rz[v] / pq;
 }
 
-cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, CgScalars c) {
-  k_cg_alpha<<<1, kEpiThreads, 0, s>>>(nvec, partial, c);
+cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int np, CgScalars c) {
+  k_cg_alpha<<<1, kEpiThreads, 0, s>>>(nvec, partial, np, c);
   return cudaGetLastError();
 }
 
@@ -176,11 +176,11 @@ cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgS
 
 // beta = r.z_new / r.z_old (plain CG) or (r.z_new - r.z_prev) / r.z_old (flexible,
 // Polak-Ribiere form for a preconditioner that is not exactly linear).
-__global__ void __launch_bounds__(kEpiThreads) k_cg_beta(int nvec, const double* prz, const double* prz2, CgScalars c,
-                                                         int flexible) {
+__global__ void __launch_bounds__(kEpiThreads) k_cg_beta(int nvec, const double* prz, const double* prz2, int np,
+                                                         CgScalars c, int flexible) {
   __shared__ double sz[kMaxVec], sz2[kMaxVec];
-  reduce_partials(nvec, prz, sz);
-  if (flexible) reduce_partials(nvec, prz2, sz2);
+  reduce_partials(nvec, prz, sz, np);
+  if (flexible) reduce_partials(nvec, prz2, sz2, np);
   const int v = threadIdx.x;
   if (v >= nvec || !c.active[v]) return;
   const double rz_new = sz[v];
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kEpiThreads) k_cg_beta(int nvec, const double*
   c.rz[v] = rz_new;
 }
 
-cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, CgScalars c,
-                           int flexible) {
-  k_cg_beta<<<1, kEpiThreads, 0, s>>>(nvec, partial, partial2, c, flexible);
+cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, const double* partial2, int np,
+                           CgScalars c, int flexible) {
+  k_cg_beta<<<1, kEpiThreads, 0, s>>>(nvec, partial, partial2, np, c, flexible);
   return cudaGetLastError();
 }
 
