@@ -103,7 +103,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cube64_p3")
     ap.add_argument("--rho", type=float, default=0.5)
-    ap.add_argument("--cfl-iters", type=int, default=60)
+    ap.add_argument("--cfl-iters", type=int, default=100)
     ap.add_argument("--forms", default=",".join(f[0] for f in FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -318,7 +318,7 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     for w in ws:
         g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, op_form="assembled", precond="bf16",
                       device=dev.index or 0)
-        lam, tc = g.cfl(rho, iters=20)
+        lam, tc = g.cfl(rho, iters=100)
         cfg = g.autotune(nvec=k, reps=3)
         tuned["%dx%d" % cfg] = tuned.get("%dx%d" % cfg, 0) + 1
         U0, V0 = w.initial()
@@ -618,7 +618,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 3 * k * N * 8,
                 "api": "iga_step_host (state in pinned host memory, copied in and out every step), form " + head},
         "clocks": clocks,
-        "setup": {"cfl_power_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s,
+        "setup": {"cfl_lanczos_max_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s,
                   "band_launch": {"threads": band_cfg[0], "vectors_per_thread": band_cfg[1], "chosen_by": "iga_autotune"},
                   "warm_start_training": warm},
     }
@@ -658,10 +658,10 @@ def run_reference(args):
 
     w = workloads.config(args.config)
     w.rho = args.rho
-    # lambda_max by the oracle's own power iteration (each iteration one PCG solve;
-    # capped at 20 on the CPU), dt = 0.5 tau_crit as on the GPU arm
+    # lambda_max by the oracle's own Lanczos process (each step one PCG solve), the
+    # same estimate the GPU arm computes; dt = 0.5 tau_crit as there
     st, X, setup_s, cores = oracle_setup(w)
-    lam = oracle.lambda_max_power(st.ops, iters=min(args.cfl_iters, 20), tol=1e-8)
+    lam = oracle.lambda_max_lanczos(st.ops, iters=args.cfl_iters)
     dt = w.cfl_fraction * math.sqrt(oracle.theta_crit(w.rho) / lam)
     for _ in range(args.warmup):
         X = st.step(X, dt)

@@ -224,8 +224,10 @@ int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0,
 int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double* gamma);
 
 /*
- * iga_cfl -- largest eigenvalue of M^{-1} K by power iteration (iters steps, each
- * one K product and one PCG solve), and the critical step
+ * iga_cfl -- largest eigenvalue of M^{-1} K by the Lanczos process in the M inner
+ * product from a seeded start (at most iters steps, each one K product, one PCG
+ * solve and one M product; it stops once the largest eigenvalue of the Lanczos
+ * tridiagonal matrix changes by less than 1e-11 relative), and the critical step
  * tau_crit = sqrt(Theta_crit(rho_inf) / lambda_max), Theta_crit = 12(1+rho)(2-rho)/(rho^2-5rho+10),
  * the k-independent stability limit of the method (Sec. 3.2 and 4.1).
  * lambda_max and tau_crit are host pointers.

@@ -560,6 +560,38 @@ def lambda_max_dense(Md, Kd):
     return float(scipy.linalg.eigh(Kd, Md, eigvals_only=True)[-1])
 
 
+def lambda_max_lanczos(ops: Operators, iters=60, seed=0, tol=1e-12, rtol=1e-12):
+    """Largest eigenvalue of M^{-1}K by the Lanczos process in the M inner product (M^{-1}K is
+    self-adjoint there): v_1 M-normalised, w = M^{-1} K v_j - alpha_j v_j - beta_{j-1} v_{j-1},
+    alpha_j = v_j^T K v_j, beta_j = ||w||_M, v_{j+1} = w / beta_j; the estimate is the largest
+    eigenvalue of the tridiagonal matrix of the alphas and betas. Stops after `iters` steps,
+    or when that estimate changes by less than rtol (relative) from one step to the next."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(ops.N)
+    v = v / math.sqrt(v @ ops.apply_M(v))
+    vp = np.zeros(ops.N)
+    alphas, betas = [], []
+    beta = 0.0
+    est = None
+    for _ in range(iters):
+        y = ops.apply_K(v)
+        w, _, _ = pcg(ops.apply_M, ops.apply_Pinv, y, None, tol)
+        alpha = float(v @ y)
+        w = w - alpha * v - beta * vp
+        alphas.append(alpha)
+        T = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
+        new = float(np.linalg.eigvalsh(T)[-1])
+        if est is not None and abs(new - est) <= rtol * abs(new):
+            return new
+        est = new
+        beta = math.sqrt(max(float(w @ ops.apply_M(w)), 0.0))
+        if beta == 0.0:
+            return est
+        betas.append(beta)
+        vp, v = v, w / beta
+    return est
+
+
 def lambda_max_power(ops: Operators, iters=200, seed=0, tol=1e-12):
     """Largest eigenvalue of M^{-1}K by power iteration (each step one K product and one
     PCG solve with M), returned as the Rayleigh quotient x^T K x / x^T M x."""

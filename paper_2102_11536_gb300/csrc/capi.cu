@@ -1592,60 +1592,77 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
     return fail(h, IGA_EINVAL, "bad arguments");
   const long long N = h->N;
   cudaStream_t s = h->stream;
-  // Every allocation first: the band assembly grows the PCG workspace, whose
-  // buffers are held by pointer below.
+  // Every allocation first: the band assembly grows the operator workspace, and the
+  // buffers below are held by pointer.
   if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
   CKS(ensure_step_ws(h, 2));
   CKS(ensure_cg_ws(h, 2));
   CKS(ensure_op_ws(h, 1));
-  // start from a checkerboard (close to the highest mode) times a smooth bump
-  std::vector<double> x0((size_t)N);
-  for (long long i = 0; i < N; ++i) {
-    const int i0 = (int)(i % h->n[0]), i1 = (int)((i / h->n[0]) % h->n[1]), i2 = (int)(i / ((long long)h->n[0] * h->n[1]));
-    const double sgn = ((i0 + i1 + i2) & 1) ? -1.0 : 1.0;
-    const double bump = std::sin(3.14159265358979 * (i0 + 1) / (h->n[0] + 1)) *
-                        std::sin(3.14159265358979 * (i1 + 1) / (h->n[1] + 1)) *
-                        (h->dim == 3 ? std::sin(3.14159265358979 * (i2 + 1) / (h->n[2] + 1)) : 1.0);
-    x0[i] = sgn * (0.5 + bump);
-  }
-  double* x = h->Z2;
-  double* y = h->rhs;
-  double* zz = h->Z;
-  CK(cudaMemcpyAsync(x, x0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
-  const double tol_save = h->opt.tol;
-  h->opt.tol = 1e-10;
+  double* v = h->Z;        // Lanczos vector v_j
+  double* vp = h->Z + N;   // v_{j-1}
+  double* w = h->Z2;       // M^{-1} K v_j, then the next residual
+  double* y = h->rhs;      // K v_j, then M w
   double* pA = h->partial;
-  double* res = h->f1;  // scratch for reduced scalars
-  double lam = 0.0;
-  for (int it = 0; it < iters; ++it) {
-    CKS(apply_K(h, 1, nullptr, x, y));
-    int st = solve(h, 1, y, zz, false, nullptr, nullptr);
-    if (st != IGA_OK) { h->opt.tol = tol_save; return st; }
-    LK(launch_dot(s, N, 1, zz, zz, N, pA));
+  double* res = h->f1;     // reduced scalars
+  auto dot = [&](const double* a, const double* b, double* out) -> int {
+    LK(launch_dot(s, N, 1, a, b, N, pA));
     LK(launch_reduce(s, 1, pA, res));
-    double nz = 0.0;
-    CK(cudaMemcpyAsync(&nz, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<double> tmp((size_t)N);
-    CK(cudaMemcpy(tmp.data(), zz, sizeof(double) * N, cudaMemcpyDeviceToHost));
-    const double inv = 1.0 / std::sqrt(nz);
-    for (auto& v : tmp) v *= inv;
-    CK(cudaMemcpy(x, tmp.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    return IGA_OK;
+  };
+  // seeded start (splitmix64, uniform in [-1, 1]), M-normalised
+  {
+    std::vector<double> x0((size_t)N);
+    uint64_t st = 0x6A09E667F3BCC909ULL;
+    for (auto& xv : x0) {
+      st += 0x9E3779B97F4A7C15ULL;
+      uint64_t z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+      z ^= z >> 31;
+      xv = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    }
+    CK(cudaMemcpyAsync(v, x0.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CKS(apply_M(h, 1, nullptr, v, y));
+  double nv = 0.0;
+  CKS(dot(v, y, &nv));
+  LK(launch_lincomb(s, N, 1.0 / std::sqrt(nv), v, 0.0, v, v));
+  CK(cudaMemsetAsync(vp, 0, sizeof(double) * N, s));
+  const double tol_save = h->opt.tol;
+  h->opt.tol = std::min(tol_save, 1e-10);
+  std::vector<double> al, be;
+  double beta = 0.0, est = 0.0;
+  int rc = IGA_OK;
+  for (int j = 0; j < iters; ++j) {
+    // w = M^{-1} K v_j - alpha_j v_j - beta_{j-1} v_{j-1}, alpha_j = v_j^T K v_j
+    if ((rc = apply_K(h, 1, nullptr, v, y)) != IGA_OK) break;
+    if ((rc = solve(h, 1, y, w, false, nullptr, nullptr)) != IGA_OK) break;
+    double alpha = 0.0;
+    if ((rc = dot(v, y, &alpha)) != IGA_OK) break;
+    LK(launch_lincomb(s, N, 1.0, w, -alpha, v, w));
+    LK(launch_lincomb(s, N, 1.0, w, -beta, vp, w));
+    al.push_back(alpha);
+    const double prev = est;
+    est = tridiag_max_eig(al, be);
+    if (j > 0 && std::fabs(est - prev) <= 1e-11 * std::fabs(est)) break;
+    // beta_j = ||w||_M, v_{j+1} = w / beta_j
+    if ((rc = apply_M(h, 1, nullptr, w, y)) != IGA_OK) break;
+    double b2 = 0.0;
+    if ((rc = dot(w, y, &b2)) != IGA_OK) break;
+    beta = std::sqrt(std::max(b2, 0.0));
+    if (!(beta > 0.0)) break;
+    be.push_back(beta);
+    CK(cudaMemcpyAsync(vp, v, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    LK(launch_lincomb(s, N, 1.0 / beta, w, 0.0, w, v));
   }
   h->opt.tol = tol_save;
-  // Rayleigh quotient x^T K x / x^T M x
-  CKS(apply_K(h, 1, nullptr, x, y));
-  CKS(apply_M(h, 1, nullptr, x, zz));
-  LK(launch_dot(s, N, 1, x, y, N, pA));
-  LK(launch_reduce(s, 1, pA, res));
-  LK(launch_dot(s, N, 1, x, zz, N, pA));
-  LK(launch_reduce(s, 1, pA, res + 1));
-  double kx[2];
-  CK(cudaMemcpyAsync(kx, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  lam = kx[0] / kx[1];
-  *lambda_max = lam;
-  *tau_crit = std::sqrt(theta_crit(rho_inf) / lam);
+  CKS(rc);
+  if (!(est > 0.0)) return fail(h, IGA_ENUMERIC, "non-positive eigenvalue estimate");
+  *lambda_max = est;
+  *tau_crit = std::sqrt(theta_crit(rho_inf) / est);
   return IGA_OK;
 }
 

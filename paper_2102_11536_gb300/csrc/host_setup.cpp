@@ -236,4 +236,36 @@ bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<doubl
   return true;
 }
 
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..m) and
+// off-diagonal b[0..m-1), by bisection on the Sturm count (the number of negative
+// pivots of T - x I = L D L^T is the number of eigenvalues below x), starting from
+// the Gershgorin interval.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  if (m == 0) return 0.0;
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto below = [&](double x) {
+    int cnt = 0;
+    double q = a[0] - x;
+    for (int i = 0;; ++i) {
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++cnt;
+      if (i + 1 >= m) break;
+      q = (a[i + 1] - x) - b[i] * b[i] / q;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 4e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid;  // every eigenvalue lies below mid
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 }  // namespace iga

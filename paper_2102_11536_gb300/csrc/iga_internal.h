@@ -44,6 +44,8 @@ bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::
 // Band Cholesky factor of an SPD matrix with half bandwidth p (row-major n x n):
 // L [n][p+1] with L[i][d] = L_{i,i-d}, dinv [n] = 1 / L_ii. False if not positive definite.
 bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<double>& L, std::vector<double>& dinv);
+// Largest eigenvalue of the symmetric tridiagonal matrix (diagonal a, off-diagonal b).
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b);
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).
 void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evec, std::vector<double>& eval);
 

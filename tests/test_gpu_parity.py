@@ -439,3 +439,19 @@ def test_smallest_patches(wi, precond):
         assert np.linalg.norm(Xg[row] - Xo[row]) / den < 1e-9, (row,)
     if ops.N == 1:
         assert st.max_iters <= 1  # the preconditioner is the exact inverse of a 1 x 1 mass matrix
+
+
+@pytest.mark.parametrize("case", ["3d_mixed_p", "2d_p23"])
+@pytest.mark.parametrize("form", [("matrix_free", "fp64"), ("assembled", "banded32"), ("assembled", "bf16")])
+def test_cfl_lambda_max_matches_dense_eigenvalue(case, form):
+    """iga_cfl's Lanczos estimate of lambda_max(M^{-1} K) against the dense generalised
+    eigenvalue, and tau_crit = sqrt(Theta_crit / lambda_max) with Theta_crit the stability
+    limit of the characteristic equation."""
+    w = OPERATOR_CASES[case]
+    ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+    lmax = oracle.lambda_max_dense(ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K))
+    g = _gpu(w, tol=1e-10, op_form=form[0], precond=form[1])
+    lam, tc = g.cfl(0.5, iters=min(ops.N, 200))
+    g.close()
+    assert abs(lam - lmax) <= 1e-8 * lmax
+    assert abs(tc - math.sqrt(oracle.theta_crit(0.5) / lmax)) <= 1e-8 * tc

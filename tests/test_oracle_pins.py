@@ -597,3 +597,16 @@ def test_damped_forced_semidiscrete_order():
             X = st.step(X, T / n)
         errs.append(np.linalg.norm(X[0] - Ue) / np.linalg.norm(Ue))
     assert math.log2(errs[0] / errs[1]) > 3.6, errs
+
+
+@pytest.mark.parametrize("d,nel,p,amp", [(2, 8, 2, 0.1), (3, 4, 3, 0.12), (3, (5, 3, 4), 2, 0.0)])
+def test_lanczos_lambda_max_equals_dense_eigenvalue(d, nel, p, amp):
+    w = W.small(d=d, nel=nel, p=p, amp=amp)
+    ops = oracle.Operators(_patch(w))
+    Md, Kd = ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K)
+    ref = oracle.lambda_max_dense(Md, Kd)
+    lam = oracle.lambda_max_lanczos(ops, iters=min(ops.N, 80))
+    assert abs(lam - ref) <= 1e-9 * ref, (lam, ref)
+    # a few steps already bound it from below
+    lam5 = oracle.lambda_max_lanczos(ops, iters=5)
+    assert lam5 <= ref * (1 + 1e-12)
