@@ -29,6 +29,11 @@ Forms measured (all FP64 state, FP64 PCG residuals and dot products, same tol):
                   extrapolated guess
   mixed_fp32_hostloop  mixed_fp32 with the PCG loop driven from the host (one
                   synchronisation per iteration) instead of the captured graph
+  df_banded       band K, M held as pairs of FP32 numbers (48 significant bits, one
+                  power-of-two scale per matrix and per vector), products in double-FP32
+                  arithmetic (error-free FP32 products, TwoSum accumulation: a few 2^-48 of
+                  sum |a||x| per row); FP64 band-Cholesky Kronecker preconditioner, plain PCG
+  df_banded32     the same with the FP32 Kronecker solve (flexible PCG)
 Every other form replays one captured CUDA graph per step whose PCG loop runs on
 the device (a conditional while node).
 The headline value is the fastest form whose U and V stay within 1e-8 (relative
@@ -84,6 +89,10 @@ FORMS = [
      "k_band_spmv (assembled symmetric band product, mass)"),
     ("mixed_learned", dict(op_form="assembled", precond="banded32", guess="learned"), "band_mass",
      "k_band_spmv (assembled symmetric band product, mass)"),
+    ("df_banded", dict(op_form="assembled_df", precond="banded", guess="zero"), "band_mass",
+     "k_band_df (double-FP32 band product, mass; with the scaling and split of x)"),
+    ("df_banded32", dict(op_form="assembled_df", precond="banded32", guess="zero"), "band_mass",
+     "k_band_df (double-FP32 band product, mass; with the scaling and split of x)"),
 ]
 
 # DRAM traffic per launch of a profiled kernel from an ncu capture, keyed by
@@ -214,7 +223,7 @@ def source_sha(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-KERNEL_SOURCE = {"mass": "kernels_ops.cu", "band_mass": "kernels_band.cu"}
+KERNEL_SOURCE = {"mass": "kernels_ops.cu", "band_mass": "kernels_band.cu", "band_mass_df": "kernels_banddf.cu"}
 
 
 # ---------------------------------------------------------------------------- oracle (CPU)
@@ -249,6 +258,45 @@ def run_cpu_baseline(w, dt, target_s):
 
 
 # ---------------------------------------------------------------------------- GPU arm
+def select_form(patch, opts, band_cfgs, k):
+    """Switch the patch to a form; each band form gets its own tuned launch shape."""
+    patch.set_op_form(opts["op_form"])
+    patch.set_precond(opts["precond"])
+    patch.set_guess(opts["guess"])
+    form = opts["op_form"]
+    if form != "matrix_free":
+        if form not in band_cfgs:
+            band_cfgs[form] = patch.autotune(nvec=k, reps=5)
+        patch.set_band_config(*band_cfgs[form])
+
+
+def roofline(prof_class, op_form, kdesc, prof, hbm, hbm_kind):
+    """Roofline of the profiled kernel class: the FP64 kernels against the FP64 FMA
+    peak (ALU-bound), the double-FP32 band product against the measured HBM copy
+    bandwidth (its algorithmic bytes: the split coefficients and the vectors)."""
+    prof_ms, prof_n, prof_flops, prof_bytes = prof
+    df = op_form == "assembled_df"
+    key = prof_class + ("_df" if df else "")
+    sha = source_sha(KERNEL_SOURCE[key])
+    gbs = prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0
+    tfl = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
+    common = {
+        "kernel": kdesc,
+        "traffic": NCU_TRAFFIC.get((key, sha)),
+        "launches": prof_n,
+        "avg_launch_ms": prof_ms / max(prof_n, 1),
+        "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
+        "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
+    }
+    if df:
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_kind": hbm_kind, **common,
+                "fp64_equivalent_view": {"achieved_tflops": tfl, "fp64_peak_tflops": FP64_PEAK_TFLOPS}}
+    return {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": tfl / FP64_PEAK_TFLOPS, "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
+            **common, "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind}}
+
+
 def time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class):
     k = w.k
     for _ in range(args.warmup):
@@ -404,17 +452,15 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     return out
 
 
-def run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush):
+def run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, hopts, band_cfgs):
     """The general model M U'' + C U' + K U = F on the headline workload and form:
     Rayleigh damping C = 0.4 M + 1e-4 K and two harmonic loads; timed like the forms."""
     import numpy as np
     k = w.k
     N = patch.N
     G = torch.from_numpy(np.random.default_rng(7).standard_normal((2, N))).to(state.device)
-    patch.set_op_form("assembled")
-    patch.set_precond("banded32")
-    patch.set_guess("zero")
-    patch.set_graphs(not args.no_graphs)
+    select_form(patch, hopts, band_cfgs, k)
+    patch.set_graphs(hopts.get("graphs", True) and not args.no_graphs)
     patch.set_damping(0.4, 1e-4)
     patch.set_forcing(G, [2.0, 5.0], [0.3, -1.0])
     patch.set_time(0.0)
@@ -435,7 +481,8 @@ def run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush):
     patch.set_damping(0.0, 0.0)
     patch.set_forcing(None, [], [])
     patch.set_time(0.0)
-    return {"form": "mixed_banded32 with C = 0.4 M + 1e-4 K and F(t) = G1 sin(2t + 0.3) + G2 sin(5t - 1)",
+    return {"form": "headline form (%s, %s, %s guess) with C = 0.4 M + 1e-4 K and F(t) = G1 sin(2t + 0.3) "
+                    "+ G2 sin(5t - 1)" % (hopts["op_form"], hopts["precond"], hopts["guess"]),
             "value": args.steps / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms / args.steps,
             "pcg_iters_per_solve": stats.iters / max(stats.solves, 1), "gpu_launches": int(stats.launches),
             "note": "one more mass product per step for the aM M term; parity in tests/test_gpu_general.py"}
@@ -472,7 +519,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     patch.assemble()
     assemble_s = time.perf_counter() - t0
-    band_cfg = patch.autotune(nvec=k, reps=5)  # band-product launch shape for this patch
+    band_cfgs = {"assembled": patch.autotune(nvec=k, reps=5)}  # band-product launch shape per band form
     state = torch.empty(3 * k * N, dtype=torch.float64, device=dev)
     u0 = torch.from_numpy(U0).to(dev)
     v0 = torch.from_numpy(V0).to(dev)
@@ -493,9 +540,7 @@ def run_ours(args):
     for name, opts, prof_class, kdesc in FORMS:
         if name not in wanted:
             continue
-        patch.set_op_form(opts["op_form"])
-        patch.set_precond(opts["precond"])
-        patch.set_guess(opts["guess"])
+        select_form(patch, opts, band_cfgs, k)
         patch.set_graphs(opts.get("graphs", True) and not args.no_graphs)
         patch.state_init(k, u0, v0, state)
         total_ms, stats, prof = time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class)
@@ -506,9 +551,6 @@ def run_ours(args):
         patch.step(state, k, w.rho, dt, 5)
         pc_ms, pc_n, pc_fl, _ = patch.profile_read()
         patch.profile("off")
-        prof_ms, prof_n, prof_flops, prof_bytes = prof
-        achieved = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
-        sha = source_sha(KERNEL_SOURCE[prof_class])
         results[name] = {
             "options": opts,
             "value": world * args.steps / t_max,
@@ -519,22 +561,7 @@ def run_ours(args):
             "gpu_launches": int(stats.launches),
             "precond_ms_per_application": pc_ms / max(pc_n, 1),
             "precond_applications_per_step": pc_n / 5.0,
-            "roofline": {
-                "kernel": kdesc,
-                "bound": "alu",
-                "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": NCU_TRAFFIC.get((prof_class, sha)),
-                "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
-                "launches": prof_n,
-                "avg_launch_ms": prof_ms / max(prof_n, 1),
-                "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
-                "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
-                "hbm_view": {"achieved_gbs": prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0,
-                             "peak_gbs": hbm, "peak_kind": hbm_kind},
-            },
+            "roofline": roofline(prof_class, opts["op_form"], kdesc, prof, hbm, hbm_kind),
         }
     clocks = sampler.stop()
     ref = finals.get("fp64_paper")
@@ -550,9 +577,7 @@ def run_ours(args):
 
     # end to end through the public C API on host memory, headline form: every step
     # copies the state in from pinned host memory and the new state back out.
-    patch.set_op_form(hopts["op_form"])
-    patch.set_precond(hopts["precond"])
-    patch.set_guess(hopts["guess"])
+    select_form(patch, hopts, band_cfgs, k)
     patch.set_graphs(hopts.get("graphs", True))
     patch.state_init(k, u0, v0, state)
     host = torch.empty(3 * k * N, dtype=torch.float64, pin_memory=True)
@@ -568,7 +593,8 @@ def run_ours(args):
     if pg:
         pg.barrier()
     e2e_rate = world * args.steps / e2e_s
-    general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush) if args.general else None
+    general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, hopts,
+                          band_cfgs) if args.general else None
     batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
 
     if rank != 0:
@@ -619,7 +645,8 @@ def run_ours(args):
                 "api": "iga_step_host (state in pinned host memory, copied in and out every step), form " + head},
         "clocks": clocks,
         "setup": {"cfl_lanczos_max_iters": args.cfl_iters, "cfl_s": cfl_s, "assemble_s": assemble_s,
-                  "band_launch": {"threads": band_cfg[0], "vectors_per_thread": band_cfg[1], "chosen_by": "iga_autotune"},
+                  "band_launch": {f: {"threads": c[0], "vectors_per_thread": c[1], "chosen_by": "iga_autotune"}
+                                  for f, c in band_cfgs.items()},
                   "warm_start_training": warm},
     }
     if batch_res is not None:

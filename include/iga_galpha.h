@@ -46,6 +46,10 @@ extern "C" {
 /* Form of the K and M operators. */
 #define IGA_OP_MATRIX_FREE 0  /* sum-factorised at the Gauss points (default) */
 #define IGA_OP_ASSEMBLED 1    /* assembled band rows, (2p+1)^d coefficients per row */
+#define IGA_OP_ASSEMBLED_DF 2 /* the same band rows held as pairs of FP32 numbers (hi + lo, 48
+                                 significant bits, one power-of-two scale per matrix and per
+                                 vector); products in double-FP32 arithmetic: error-free FP32
+                                 products and TwoSum accumulation, a few 2^-48 of sum |a||x| */
 
 /* Arithmetic of the preconditioner's fast-diagonalisation mode products. */
 #define IGA_PREC_FP64 0       /* FP64 (default); plain CG */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libiga_galpha.so")
 _LIB = None
 
 OK, EINVAL, ENOMEM, ECUDA, ENOT_CONVERGED, ENUMERIC, EUNSTABLE, EGEOMETRY = range(8)
-OP_FORMS = {"matrix_free": 0, "assembled": 1}
+OP_FORMS = {"matrix_free": 0, "assembled": 1, "assembled_df": 2}
 PRECONDS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "banded": 4, "banded32": 5}
 GUESSES = {"zero": 0, "prev": 1, "extrap": 2, "taylor": 3, "learned": 4}
 NET_NPARAM = 1745

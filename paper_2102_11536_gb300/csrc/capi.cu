@@ -36,6 +36,17 @@ struct iga_handle {
   int band_threads = 0, band_nv = 0;  // launch configuration of the band product (0 = default)
   long long ws_gen = 0;               // bumped whenever an address a captured graph may hold changes
   double band_nnz = 0.0;          // nonzero couplings (for algorithmic flop counts)
+  // double-FP32 form of the band (IGA_OP_ASSEMBLED_DF)
+  float2* Mdf = nullptr;
+  float2* Kdf = nullptr;
+  int EAm = 0, EAk = 0;           // power-of-two exponents of the split bands
+  int* band_runs = nullptr;       // [nruns][4] runs of the upper half
+  int band_nruns = 0;
+  long long band_Np = 0;          // row stride of the split bands and vectors
+  float2* df_xs = nullptr;        // [kMaxVec][Np] split input vectors (zero pads)
+  int* df_E = nullptr;            // [kMaxVec] their exponents, [kMaxVec] scratch
+  unsigned long long* df_part = nullptr;  // [kMaxVec][kDfBlocks] partial maxima
+  bool df_ready = false;
   // operator workspace
   int ws_vec = 0;
   double *u0 = nullptr, *u1 = nullptr, *ta = nullptr, *tb = nullptr, *tc = nullptr;
@@ -249,6 +260,9 @@ double theta_crit(double rho) { return 12.0 * (1.0 + rho) * (2.0 - rho) / (rho *
 // A captured step graph holds workspace addresses: every workspace reallocation
 // below drops it, and the next step captures again.
 void drop_step_graph(iga_handle* h);
+inline bool is_assembled(const iga_handle* h) {
+  return h->opt.op_form == IGA_OP_ASSEMBLED || h->opt.op_form == IGA_OP_ASSEMBLED_DF;
+}
 
 int ensure_op_ws(iga_handle* h, int nvec) {
   if (h->ws_vec >= nvec) return IGA_OK;
@@ -492,8 +506,9 @@ int check_tc_error(iga_handle* h) {
 
 // Assembled band rows of M and K by probing the matrix-free operators with the
 // (2p+1)^d colour vectors, 8 colours per application (kernels_band.cu).
-int assemble_band(iga_handle* h) {
+int assemble_band64(iga_handle* h) {
   if (h->band_ready) return IGA_OK;
+  drop_step_graph(h);  // new addresses
   cudaStream_t s = h->stream;
   int p3[3] = {0, 0, 0};
   for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
@@ -546,13 +561,73 @@ int assemble_band(iga_handle* h) {
   return IGA_OK;
 }
 
-int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* active, const double* x, double* y,
+// The double-FP32 copies of the assembled band (kernels_banddf.cu): split once from
+// the FP64 band, which is then released.
+int assemble_band_df(iga_handle* h) {
+  if (h->df_ready) return IGA_OK;
+  CKS(assemble_band64(h));
+  drop_step_graph(h);
+  cudaStream_t s = h->stream;
+  const int H = h->band_H;
+  const long long N = h->N, Np = N + 2 * kDfPad;
+  int p3[3] = {0, 0, 0};
+  for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
+  const std::vector<int> runs = band_df_runs(h->n, p3);
+  CKS(upload(h, &h->band_runs, runs));
+  h->band_nruns = (int)runs.size() / 4;
+  CKS(dalloc(h, &h->Mdf, (size_t)H * Np));
+  CKS(dalloc(h, &h->Kdf, (size_t)H * Np));
+  CKS(dalloc(h, &h->df_xs, (size_t)kMaxVec * Np));
+  CKS(dalloc(h, &h->df_E, (size_t)2 * kMaxVec));
+  CKS(dalloc(h, &h->df_part, (size_t)kMaxVec * kDfBlocks));
+  CK(cudaMemsetAsync(h->Mdf, 0, sizeof(float2) * H * Np, s));
+  CK(cudaMemsetAsync(h->Kdf, 0, sizeof(float2) * H * Np, s));
+  CK(cudaMemsetAsync(h->df_xs, 0, sizeof(float2) * kMaxVec * Np, s));
+  int* dE = h->df_E + kMaxVec;
+  int EA[2] = {0, 0};
+  LK(launch_df_split_matrix(s, N, H, h->Mband, h->Mdf, Np, h->df_part, dE));
+  CK(cudaMemcpyAsync(&EA[0], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  LK(launch_df_split_matrix(s, N, H, h->Kband, h->Kdf, Np, h->df_part, dE));
+  CK(cudaMemcpyAsync(&EA[1], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->EAm = EA[0];
+  h->EAk = EA[1];
+  h->band_Np = Np;
+  dfree(h->Mband);
+  dfree(h->Kband);
+  h->band_ready = false;
+  h->df_ready = true;
+  return IGA_OK;
+}
+
+// the band rows of the handle's assembled form
+int assemble_band(iga_handle* h) {
+  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? assemble_band_df(h) : assemble_band64(h);
+}
+
+// one band product y = A x in the handle's assembled form (FP64, or double-FP32 with
+// the split of x first); cls selects the matrix (IGA_PROF_BAND_MASS / _STIFF)
+cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const int* active, const double* x,
+                        double* y, int threads, int nv, double* pq, int* npq) {
+  const bool mass = cls == IGA_PROF_BAND_MASS;
+  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
+    cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, h->df_xs, h->band_Np, h->df_E, h->df_part);
+    if (e != cudaSuccess) return e;
+    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n,
+                          mass ? h->Mdf : h->Kdf, h->band_Np, mass ? h->EAm : h->EAk, active, nvec, h->df_xs,
+                          h->df_E, x, y, h->N, threads, nv, pq, npq);
+  }
+  return launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, mass ? h->Mband : h->Kband, active,
+                          nvec, x, y, h->N, threads, nv, pq, npq);
+}
+
+int apply_band(iga_handle* h, int cls, int nvec, const int* active, const double* x, double* y,
                double* pq = nullptr, int* npq = nullptr) {
   const int nact = active ? h->cur_active : nvec;
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, cls, &e));
-  LK(launch_band_spmv(h->stream, h->N, h->band_H, h->band_off, h->band_o12, h->n, A, active, nvec, x, y, h->N,
-                        h->band_threads, h->band_nv, pq, npq));
+  LK(launch_band(h, h->stream, cls, nvec, active, x, y, h->band_threads, h->band_nv, pq, npq));
   CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
@@ -562,16 +637,16 @@ int apply_band(iga_handle* h, const double* A, int cls, int nvec, const int* act
 int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
             int* npq = nullptr) {
   if (npq) *npq = 0;
-  if (h->opt.op_form == IGA_OP_ASSEMBLED) {
+  if (is_assembled(h)) {
     CKS(assemble_band(h));
-    return apply_band(h, h->Mband, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq);
+    return apply_band(h, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq);
   }
   return apply_M_mf(h, nvec, active, x, y);
 }
 int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
-  if (h->opt.op_form == IGA_OP_ASSEMBLED) {
+  if (is_assembled(h)) {
     CKS(assemble_band(h));
-    return apply_band(h, h->Kband, IGA_PROF_BAND_STIFF, nvec, active, x, y);
+    return apply_band(h, IGA_PROF_BAND_STIFF, nvec, active, x, y);
   }
   return apply_K_mf(h, nvec, active, x, y);
 }
@@ -857,7 +932,7 @@ int prepare_capture(iga_handle* h, int k) {
   CKS(ensure_op_ws(h, k));
   if (h->opt.guess == IGA_GUESS_LEARNED) CKS(ensure_ws_step(h, k));
   CKS(ensure_damp_ws(h, k));
-  if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
+  if (is_assembled(h)) CKS(assemble_band(h));
   return IGA_OK;
 }
 
@@ -1110,6 +1185,7 @@ void iga_destroy(iga_handle* h) {
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
+  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
@@ -1146,7 +1222,7 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
   if (opt) h->opt = *opt;
   else iga_options_default(&h->opt);
   if (!(h->opt.tol >= 0.0) || h->opt.max_iter < 1 || h->opt.precond < 0 || h->opt.precond > IGA_PREC_BANDED32 ||
-      h->opt.op_form < 0 || h->opt.op_form > 1 || h->opt.guess < 0 || h->opt.guess > IGA_GUESS_LEARNED) {
+      h->opt.op_form < 0 || h->opt.op_form > IGA_OP_ASSEMBLED_DF || h->opt.guess < 0 || h->opt.guess > IGA_GUESS_LEARNED) {
     delete h;
     return fail(nullptr, IGA_EINVAL, "invalid options");
   }
@@ -1288,7 +1364,7 @@ int iga_ndof(const iga_handle* h, long long* ndof) {
 }
 
 int iga_set_op_form(iga_handle* h, int op_form) {
-  if (!h || op_form < 0 || op_form > 1) return IGA_EINVAL;
+  if (!h || op_form < 0 || op_form > IGA_OP_ASSEMBLED_DF) return IGA_EINVAL;
   h->opt.op_form = op_form;
   return IGA_OK;
 }
@@ -1594,7 +1670,7 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
   cudaStream_t s = h->stream;
   // Every allocation first: the band assembly grows the operator workspace, and the
   // buffers below are held by pointer.
-  if (h->opt.op_form == IGA_OP_ASSEMBLED) CKS(assemble_band(h));
+  if (is_assembled(h)) CKS(assemble_band(h));
   CKS(ensure_step_ws(h, 2));
   CKS(ensure_cg_ws(h, 2));
   CKS(ensure_op_ws(h, 1));
@@ -1896,12 +1972,10 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
     for (int vi = 0; vi < 3; ++vi) {
       const int v = std::min(cand_v[vi], nvec);
       if (vi > 0 && v == std::min(cand_v[vi - 1], nvec)) continue;  // same as the previous candidate
-      LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, h->Mband, nullptr, nvec, h->p, h->q,
-                          h->N, cand_t[ti], v));
+      LK(launch_band(h, s, IGA_PROF_BAND_MASS, nvec, nullptr, h->p, h->q, cand_t[ti], v, nullptr, nullptr));
       CK(cudaEventRecord(e0, s));
       for (int r = 0; r < reps; ++r)
-        LK(launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, h->Mband, nullptr, nvec, h->p, h->q,
-                            h->N, cand_t[ti], v));
+        LK(launch_band(h, s, IGA_PROF_BAND_MASS, nvec, nullptr, h->p, h->q, cand_t[ti], v, nullptr, nullptr));
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;

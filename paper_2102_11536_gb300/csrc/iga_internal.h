@@ -232,6 +232,23 @@ void tc_arrange(int n, const double* Mat_ij, bool f16, std::vector<uint16_t>& ou
 cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long* off, const int* o12, const int* n,
                              const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
                              int threads, int nv, double* pq = nullptr, int* npq = nullptr);
+// Double-FP32 band product (kernels_banddf.cu). Split storage: float2 (hi, lo) rows
+// of stride Np = N + 2 kDfPad with zero pads; kDfBlocks partial maxima per vector.
+constexpr int kDfPad = 16;
+constexpr int kDfBlocks = 256;
+// the runs of the upper half: per run {first slot, length, (o1 + 64) | (o2 + 64) << 8, linear offset}
+std::vector<int> band_df_runs(const int* n, const int* p);
+// Adf = split(A 2^-E) with one exponent E (left in dE[0]) for the whole [H][N] band
+cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const double* A, float2* Adf, long long Np,
+                                   unsigned long long* part, int* dE);
+// xs[v] = split(x[v] 2^-E_v), E_v (into Ex[v]) from the vector's largest magnitude
+cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
+                            float2* xs, long long Np, int* Ex, unsigned long long* part);
+// y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
+// pq / npq as in launch_band_spmv (x is the FP64 input, read only for pq)
+cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
+                           long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
+                           const double* x, double* y, long long vs, int threads, int nv, double* pq, int* npq);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,
