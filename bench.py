@@ -122,6 +122,8 @@ def parse_args():
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
     ap.add_argument("--no-general", dest="general", action="store_false",
                     help="skip the damped, forced variant of the headline step")
+    ap.add_argument("--band-config", default="",
+                    help="threads,vectors for the double-FP32 band product instead of autotuning (profiling)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven PCG loop for every form (the same kernels; for profilers that cannot "
                          "see inside graphs with conditional nodes)")
@@ -259,7 +261,8 @@ def run_cpu_baseline(w, dt, target_s):
 
 # ---------------------------------------------------------------------------- GPU arm
 def select_form(patch, opts, band_cfgs, k):
-    """Switch the patch to a form; each band form gets its own tuned launch shape."""
+    """Switch the patch to a form; each band form gets its own tuned launch shape
+    (band_cfgs may hold a fixed shape for a form, then nothing is tuned)."""
     patch.set_op_form(opts["op_form"])
     patch.set_precond(opts["precond"])
     patch.set_guess(opts["guess"])
@@ -520,6 +523,8 @@ def run_ours(args):
     patch.assemble()
     assemble_s = time.perf_counter() - t0
     band_cfgs = {"assembled": patch.autotune(nvec=k, reps=5)}  # band-product launch shape per band form
+    if args.band_config:
+        band_cfgs["assembled_df"] = tuple(int(v) for v in args.band_config.split(","))
     state = torch.empty(3 * k * N, dtype=torch.float64, device=dev)
     u0 = torch.from_numpy(U0).to(dev)
     v0 = torch.from_numpy(V0).to(dev)

@@ -394,9 +394,14 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
 
 /* Band-product launch configuration of h (assembled operators): threads per block
  * 64, 128, 256 or 512 (0 = 256) and vectors per thread 1..4 sharing each coefficient
- * load (0 = all of a call's vectors, at most 4). Every configuration computes
- * each row with the same operations in the same order, so results are bitwise
- * equal. IGA_EINVAL for other values. */
+ * load (0 = all of a call's vectors, at most 4). In the IGA_OP_ASSEMBLED_DF form,
+ * 64, 128 or 256 threads with at most 2 vectors per thread and a degree 2..4 along
+ * the first direction select the TMA-staged kernel with that many rows per block
+ * and one more warp that issues the copies (each block's rows, run by run, copied
+ * into a ring of shared-memory buffers ahead of use; its bounded mbarrier waits
+ * report IGA_ECUDA on the next checked call if one runs out). Every configuration
+ * computes each row with the same operations in the same order, so results are
+ * bitwise equal. IGA_EINVAL for other values. */
 int iga_set_band_config(iga_handle* h, int threads, int nv);
 
 /*

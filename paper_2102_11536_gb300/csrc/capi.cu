@@ -43,10 +43,12 @@ struct iga_handle {
   int* band_runs = nullptr;       // [nruns][4] runs of the upper half
   int band_nruns = 0;
   long long band_Np = 0;          // row stride of the split bands and vectors
+  long long df_slack = 0;         // zeroed elements before and after each split array
   float2* df_xs = nullptr;        // [kMaxVec][Np] split input vectors (zero pads)
   int* df_E = nullptr;            // [kMaxVec] their exponents, [kMaxVec] scratch
   unsigned long long* df_part = nullptr;  // [kMaxVec][kDfBlocks] partial maxima
   bool df_ready = false;
+  DfTmaps tmM, tmK;               // tensor maps of the split bands (and vectors)
   // operator workspace
   int ws_vec = 0;
   double *u0 = nullptr, *u1 = nullptr, *ta = nullptr, *tb = nullptr, *tc = nullptr;
@@ -491,15 +493,19 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
   return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
 }
 
-// The tensor-core kernels set dflag[1] when an mbarrier wait runs out.
+// The tensor-core kernels set dflag[1], the TMA-staged band product dflag[2], when an
+// mbarrier wait runs out.
 int check_tc_error(iga_handle* h) {
-  if (h->opt.precond != IGA_PREC_BF16 && h->opt.precond != IGA_PREC_FP16) return IGA_OK;
-  int e = 0;
-  CK(cudaMemcpyAsync(&e, h->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  const bool tc = h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16;
+  const bool df = h->opt.op_form == IGA_OP_ASSEMBLED_DF;
+  if (!tc && !df) return IGA_OK;
+  int e[2] = {0, 0};
+  CK(cudaMemcpyAsync(e, h->dflag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (e) {
-    CK(cudaMemsetAsync(h->dflag + 1, 0, sizeof(int), h->stream));
-    return fail(h, IGA_ECUDA, "tensor-core mode product: mbarrier wait timed out");
+  if (e[0] || e[1]) {
+    CK(cudaMemsetAsync(h->dflag + 1, 0, 2 * sizeof(int), h->stream));
+    return fail(h, IGA_ECUDA, e[0] ? "tensor-core mode product: mbarrier wait timed out"
+                                   : "staged band product: mbarrier wait timed out");
   }
   return IGA_OK;
 }
@@ -569,31 +575,38 @@ int assemble_band_df(iga_handle* h) {
   drop_step_graph(h);
   cudaStream_t s = h->stream;
   const int H = h->band_H;
-  const long long N = h->N, Np = N + 2 * kDfPad;
+  const long long N = h->N, Np = df_row_stride(N);
   int p3[3] = {0, 0, 0};
   for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
   const std::vector<int> runs = band_df_runs(h->n, p3);
   CKS(upload(h, &h->band_runs, runs));
   h->band_nruns = (int)runs.size() / 4;
-  CKS(dalloc(h, &h->Mdf, (size_t)H * Np));
-  CKS(dalloc(h, &h->Kdf, (size_t)H * Np));
-  CKS(dalloc(h, &h->df_xs, (size_t)kMaxVec * Np));
+  long long maxL = 0;  // reach of a run's staged copies beyond its rows
+  for (size_t q = 0; q < runs.size(); q += 4) maxL = std::max(maxL, (long long)std::abs(runs[q + 3]) + runs[q + 1]);
+  const long long sl = df_slack(maxL);
+  h->df_slack = sl;
+  const size_t nA = (size_t)H * Np + 2 * sl, nX = (size_t)kMaxVec * Np + 2 * sl;
+  CKS(dalloc(h, &h->Mdf, nA));
+  CKS(dalloc(h, &h->Kdf, nA));
+  CKS(dalloc(h, &h->df_xs, nX));
   CKS(dalloc(h, &h->df_E, (size_t)2 * kMaxVec));
   CKS(dalloc(h, &h->df_part, (size_t)kMaxVec * kDfBlocks));
-  CK(cudaMemsetAsync(h->Mdf, 0, sizeof(float2) * H * Np, s));
-  CK(cudaMemsetAsync(h->Kdf, 0, sizeof(float2) * H * Np, s));
-  CK(cudaMemsetAsync(h->df_xs, 0, sizeof(float2) * kMaxVec * Np, s));
+  CK(cudaMemsetAsync(h->Mdf, 0, sizeof(float2) * nA, s));
+  CK(cudaMemsetAsync(h->Kdf, 0, sizeof(float2) * nA, s));
+  CK(cudaMemsetAsync(h->df_xs, 0, sizeof(float2) * nX, s));
   int* dE = h->df_E + kMaxVec;
   int EA[2] = {0, 0};
-  LK(launch_df_split_matrix(s, N, H, h->Mband, h->Mdf, Np, h->df_part, dE));
+  LK(launch_df_split_matrix(s, N, H, h->Mband, h->Mdf + sl, Np, h->df_part, dE));
   CK(cudaMemcpyAsync(&EA[0], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  LK(launch_df_split_matrix(s, N, H, h->Kband, h->Kdf, Np, h->df_part, dE));
+  LK(launch_df_split_matrix(s, N, H, h->Kband, h->Kdf + sl, Np, h->df_part, dE));
   CK(cudaMemcpyAsync(&EA[1], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   h->EAm = EA[0];
   h->EAk = EA[1];
   h->band_Np = Np;
+  df_encode_maps(h->Mdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmM);
+  df_encode_maps(h->Kdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmK);
   dfree(h->Mband);
   dfree(h->Kband);
   h->band_ready = false;
@@ -612,11 +625,12 @@ cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const 
                         double* y, int threads, int nv, double* pq, int* npq) {
   const bool mass = cls == IGA_PROF_BAND_MASS;
   if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
-    cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, h->df_xs, h->band_Np, h->df_E, h->df_part);
+    float2* xs = h->df_xs + h->df_slack;
+    cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part);
     if (e != cudaSuccess) return e;
-    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n,
-                          mass ? h->Mdf : h->Kdf, h->band_Np, mass ? h->EAm : h->EAk, active, nvec, h->df_xs,
-                          h->df_E, x, y, h->N, threads, nv, pq, npq);
+    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
+                          (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
+                          xs, h->df_E, x, y, h->N, threads, nv, pq, npq, h->dflag + 2, mass ? &h->tmM : &h->tmK);
   }
   return launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, mass ? h->Mband : h->Kband, active,
                           nvec, x, y, h->N, threads, nv, pq, npq);
@@ -1449,13 +1463,15 @@ int iga_assemble(iga_handle* h) {
 int iga_apply_M(iga_handle* h, int nvec, const double* x, double* y) {
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
-  return apply_M(h, nvec, nullptr, x, y);
+  CKS(apply_M(h, nvec, nullptr, x, y));
+  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? check_tc_error(h) : IGA_OK;
 }
 
 int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y) {
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
-  return apply_K(h, nvec, nullptr, x, y);
+  CKS(apply_K(h, nvec, nullptr, x, y));
+  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? check_tc_error(h) : IGA_OK;
 }
 
 int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y) {
@@ -1999,7 +2015,7 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
   drop_step_graph(h);
   if (threads) *threads = best_t;
   if (nv) *nv = best_v;
-  return IGA_OK;
+  return check_tc_error(h);
 }
 
 }  // extern "C"

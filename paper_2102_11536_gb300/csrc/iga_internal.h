@@ -1,5 +1,7 @@
 // Internal declarations of the GB300 generalized-alpha IGA library.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -233,9 +235,13 @@ cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long
                              const double* A, const int* active, int nvec, const double* x, double* y, long long vs,
                              int threads, int nv, double* pq = nullptr, int* npq = nullptr);
 // Double-FP32 band product (kernels_banddf.cu). Split storage: float2 (hi, lo) rows
-// of stride Np = N + 2 kDfPad with zero pads; kDfBlocks partial maxima per vector.
+// of stride Np (N + 2 kDfPad rounded up to a multiple of 16) with zero pads, and
+// df_slack(maxL) zeroed elements before and after every split array (the reach of
+// the staged copies); kDfBlocks partial maxima per vector.
 constexpr int kDfPad = 16;
 constexpr int kDfBlocks = 256;
+inline long long df_row_stride(long long N) { return (N + 2 * kDfPad + 15) / 16 * 16; }
+inline long long df_slack(long long maxL) { return (maxL + 1024 + 15) / 16 * 16; }
 // the runs of the upper half: per run {first slot, length, (o1 + 64) | (o2 + 64) << 8, linear offset}
 std::vector<int> band_df_runs(const int* n, const int* p);
 // Adf = split(A 2^-E) with one exponent E (left in dE[0]) for the whole [H][N] band
@@ -246,9 +252,23 @@ cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int 
                             float2* xs, long long Np, int* Ex, unsigned long long* part);
 // y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
 // pq / npq as in launch_band_spmv (x is the FP64 input, read only for pq)
-cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
-                           long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
-                           const double* x, double* y, long long vs, int threads, int nv, double* pq, int* npq);
+// 2-D tensor maps over a split band ([H][Np], boxes for the upper rows and the lower
+// parallelogram of a run) and over the split vectors ([kMaxVec][Np], 1 or 2 rows).
+struct DfTmaps {
+  CUtensorMap up, dn, x1, x2;
+  bool ok = false;
+};
+bool df_encode_maps(const float2* A, int H, const float2* xs, int nvmax, long long Np, int p0, DfTmaps* tm);
+// (p0: the degree along direction 0, for the kernels compiled for it). threads 128
+// with nv <= 2, p0 in 2..4 and tm->ok selects the tensor-map kernel; threads 64,
+// 128 or 256 with nv <= 2 and p0 in 2..4 selects the TMA-staged kernel with that many
+// rows per block (err: device int
+// set to 1 if one of its mbarrier waits runs out; null: never that kernel); other
+// shapes the register kernel. Every shape gives bitwise the same result.
+cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0,
+                           const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs,
+                           const int* Ex, const double* x, double* y, long long vs, int threads, int nv, double* pq,
+                           int* npq, int* err, const DfTmaps* tm);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,

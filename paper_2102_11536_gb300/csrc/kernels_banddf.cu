@@ -113,7 +113,69 @@ __device__ __forceinline__ void df_term(float& s, float& c, const float2 a, cons
   s = S;
 }
 
-template <int NV, int BS>
+// Fast2Sum renormalisation of (s, c): |c| is at most a few ulps of s
+template <int NV>
+__device__ __forceinline__ void df_renorm(float (&s)[NV], float (&c)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float S = __fadd_rn(s[v], c[v]);
+    c[v] = __fsub_rn(c[v], __fsub_rn(S, s[v]));
+    s[v] = S;
+  }
+}
+
+// The terms of one run: slot h0 + t contributes A[h0 + t][i] x[i + L0 + t] (upper, when
+// the neighbour lines exist: up) and A[h0 + t][i - L0 - t] x[i - L0 - t] (lower: dn).
+// au = &A[h0][i], ad = &A[h0][i - L0], xu[v] = &x_v[i + L0], xd[v] = &x_v[i - L0].
+// LEN > 0: a compile-time length (the loads of the run can all be issued at once);
+// LEN == 0: the runtime length len.
+template <int LEN, int NV>
+__device__ __forceinline__ void df_run(int len, bool up, bool dn, const float2* __restrict__ au,
+                                       const float2* __restrict__ ad, long long Np, const float2* const (&xu)[NV],
+                                       const float2* const (&xd)[NV], float (&s)[NV], float (&c)[NV]) {
+  // the upper terms of the run, then the lower ones
+  if constexpr (LEN > 0) {
+    if (up) {
+#pragma unroll
+      for (int t = 0; t < LEN; ++t) {
+        const float2 a = au[t * Np];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v][t]);
+      }
+    }
+    if (dn) {
+#pragma unroll
+      for (int t = 0; t < LEN; ++t) {
+        const float2 a = ad[t * (Np - 1)];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v][-t]);
+      }
+    }
+  } else {
+    if (up) {
+#pragma unroll 1
+      for (int t = 0; t < len; ++t) {
+        const float2 a = au[t * Np];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v][t]);
+      }
+    }
+    if (dn) {
+#pragma unroll 1
+      for (int t = 0; t < len; ++t) {
+        const float2 a = ad[t * (Np - 1)];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v][-t]);
+      }
+    }
+  }
+}
+
+// P0: the degree along direction 0 when compiled for it (run lengths P0 and 2 P0 + 1),
+// 0 for any degree. A vector slot past nvec repeats the last vector's arithmetic and
+// an inactive vector is computed from its stale split copy; neither is stored, so the
+// inner loop carries no per-vector conditions.
+template <int P0, int NV, int BS>
 __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const int4* __restrict__ runs, int n0, int n1,
                                                 int n2, const float2* __restrict__ A, long long Np, int EA,
                                                 const int* __restrict__ active, int nvec,
@@ -123,18 +185,18 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
   const long long i = (long long)blockIdx.x * BS + threadIdx.x;
   const bool row = i < N;  // no early return: the run votes need every lane
   const int v0 = blockIdx.y * NV;
-  bool on[NV];
   float s[NV], c[NV];
   const float2* xv[NV];  // row pad + i of each vector's split copy
-  const float2 a0 = row ? A[kDfPad + i] : make_float2(0.f, 0.f);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const int vv = min(v0 + v, nvec - 1);
-    on[v] = row && v0 + v < nvec && (!active || active[vv]);
-    xv[v] = xs + (long long)vv * Np + kDfPad + i;
+    xv[v] = xs + (long long)min(v0 + v, nvec - 1) * Np + kDfPad + i;
     s[v] = 0.f;
     c[v] = 0.f;
-    if (on[v]) df_term(s[v], c[v], a0, xv[v][0]);
+  }
+  if (row) {
+    const float2 a0 = A[kDfPad + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a0, xv[v][0]);
   }
   int i1 = 0, i2 = 0;
   if (row) {
@@ -144,41 +206,38 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
   }
   for (int r = 0; r < nruns; ++r) {
     const int4 R = runs[r];  // first slot, length, packed (o1, o2), linear offset of the first slot
-    const int o1 = (R.z & 255) - 64, o2 = ((R.z >> 8) & 255) - 64;
-    const bool up = row && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
-    const bool dn = row && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
-    if (!__any_sync(0xffffffffu, up || dn)) continue;
-    // upper term of slot h0 + t: A[h0 + t][i], x[i + L0 + t]; lower term: A[h0 + t][i - L0 - t], x[i - L0 - t]
+    bool up = row, dn = row;
+    if (r > 0) {  // run 0 is (o1, o2) = (0, 0): both neighbour lines are the row's own
+      const int o1 = (R.z & 255) - 64, o2 = ((R.z >> 8) & 255) - 64;
+      up = up && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
+      dn = dn && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
+      if (!__any_sync(0xffffffffu, up || dn)) continue;
+    }
     const float2* au = A + (long long)R.x * Np + kDfPad + i;
     const float2* ad = au - R.w;
-    const int L0 = R.w;
-    for (int t = 0; t < R.y; ++t) {
-      if (up) {
-        const float2 a = au[(long long)t * Np];
+    const float2* xu[NV];
+    const float2* xd[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          if (on[v]) df_term(s[v], c[v], a, xv[v][L0 + t]);
-      }
-      if (dn) {
-        const float2 a = ad[(long long)t * (Np - 1)];
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-          if (on[v]) df_term(s[v], c[v], a, xv[v][-L0 - t]);
-      }
+    for (int v = 0; v < NV; ++v) {
+      xu[v] = xv[v] + R.w;
+      xd[v] = xv[v] - R.w;
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {  // Fast2Sum renormalisation, |c| <= |s| ulp-wise
-      const float S = __fadd_rn(s[v], c[v]);
-      c[v] = __fsub_rn(c[v], __fsub_rn(S, s[v]));
-      s[v] = S;
+    if (P0 > 0) {
+      if (r == 0) df_run<P0, NV>(0, up, dn, au, ad, Np, xu, xd, s, c);
+      else df_run<2 * P0 + 1, NV>(0, up, dn, au, ad, Np, xu, xd, s, c);
+    } else {
+      df_run<0, NV>(R.y, up, dn, au, ad, Np, xu, xd, s, c);
     }
+    df_renorm<NV>(s, c);
   }
+  bool on[NV];
   double out[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
+    const int vv = v0 + v;
+    on[v] = row && vv < nvec && (!active || active[vv]);
     out[v] = 0.0;
     if (on[v]) {
-      const int vv = v0 + v;
       out[v] = ((double)s[v] + (double)c[v]) * ldexp(1.0, Ex[vv] + EA);
       y[vv * vs + i] = out[v];
     }
@@ -205,14 +264,508 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
   }
 }
 
-template <int BS>
-int band_df_go(cudaStream_t s, int nv, long long N, int nruns, const int4* runs, const int* n, const float2* A,
-               long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex, const double* x,
-               double* y, long long vs, double* pq) {
-  const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
-  const int n0 = n[0], n1 = n[1], n2 = n[2];
-#define IGA_DF_GO(NVV) \
-  k_band_df<NVV, BS><<<grid, BS, 0, s>>>(N, nruns, runs, n0, n1, n2, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq)
+// ---------------------------------------------------------------------------
+// TMA-staged form: a block owns R consecutive rows and walks the runs; a producer
+// warp stages each run's operands into a ring of kStages shared-memory buffers with
+// bulk copies (cp.async.bulk, completion on an mbarrier) as soon as the consumer
+// warps release a buffer, and the consumers (one row per thread) compute from
+// shared memory. Per run and buffer:
+//   cu[t][j]  = A[h0 + t][i0 + j]                  (upper terms, t < len, j < R)
+//   cd[t][.]  = A[h0 + t][i0 - L0 - t + j]         (lower terms; the copy starts at the
+//               even index at or below, so the row sits at offset (L0 + t) & 1)
+//   xu[v][.]  = x_v[i0 + L0 + j'],  xd[v][.] = x_v[i0 - L0 - (len - 1) + j']  (j' < W,
+//               same rounding: offset L0 & 1, resp. (L0 + len - 1) & 1)
+// Every index is relative to the padded row layout; the split arrays carry slack
+// before and after (kDfSlack) so that every copy lies inside its allocation; rows
+// whose neighbour line is outside the grid read slack or other rows but are
+// predicated off, exactly as in the register form. The arithmetic, its order and the
+// per-warp run votes (which decide the renormalisations) are those of k_band_df.
+// buffers in the ring: more for smaller blocks (more blocks per SM share the same
+// shared memory, each needs enough runs in flight)
+__host__ __device__ constexpr int df_stages(int R) { return R <= 64 ? 4 : (R <= 128 ? 3 : 2); }
+constexpr long long kTmaWaitLimit = 1LL << 22;  // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < kTmaWaitLimit; ++it)
+    if (mbar_try(mbar, phase)) return true;
+  return false;
+}
+
+template <int P0, int NV, int R>
+struct DfStage {
+  static constexpr int M0 = 2 * P0 + 1;
+  static constexpr int W = R + M0 + 1;  // x span length (even)
+  static constexpr int CU = 0;
+  static constexpr int CD = CU + M0 * R;
+  static constexpr int XU = CD + M0 * (R + 2);
+  static constexpr int XD = XU + NV * W;
+  static constexpr int ELEMS = XD + NV * W;  // float2 per buffer
+  static constexpr size_t BYTES = (size_t)ELEMS * 8;
+};
+
+// issue the copies of run r (length LEN) into buffer b
+template <int P0, int NV, int R, int LEN>
+__device__ __forceinline__ void df_issue(const int4 R4, float2* buf, uint32_t mbar, const float2* A, long long Np,
+                                         long long i0, const float2* xs, int v0, int nvec) {
+  using St = DfStage<P0, NV, R>;
+  const long long h0 = R4.x, L0 = R4.w;
+  constexpr uint32_t bytes = (uint32_t)((LEN * R + LEN * (R + 2) + 2 * NV * St::W) * 8);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+#pragma unroll
+  for (int t = 0; t < LEN; ++t) {
+    const long long eu = (h0 + t) * Np + kDfPad + i0;
+    bulk_g2s(s_u32(buf + St::CU + t * R), A + eu, R * 8, mbar);
+    const long long ed = eu - L0 - t;
+    bulk_g2s(s_u32(buf + St::CD + t * (R + 2)), A + (ed & ~1LL), (R + 2) * 8, mbar);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long base = (long long)min(v0 + v, nvec - 1) * Np + kDfPad + i0;
+    bulk_g2s(s_u32(buf + St::XU + v * St::W), xs + ((base + L0) & ~1LL), St::W * 8, mbar);
+    bulk_g2s(s_u32(buf + St::XD + v * St::W), xs + ((base - L0 - (LEN - 1)) & ~1LL), St::W * 8, mbar);
+  }
+}
+
+// the terms of run (LEN slots) from buffer buf for row j of the block: the upper
+// terms, then the lower ones, as in df_run
+template <int P0, int NV, int R, int LEN>
+__device__ __forceinline__ void df_run_smem(const float2* buf, int j, int L0, bool up, bool dn, float (&s)[NV],
+                                            float (&c)[NV]) {
+  using St = DfStage<P0, NV, R>;
+  if (up) {
+    const float2* xu = buf + St::XU + (L0 & 1) + j;
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const float2 a = buf[St::CU + t * R + j];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v * St::W + t]);
+    }
+  }
+  if (dn) {
+    const float2* xd = buf + St::XD + ((L0 + LEN - 1) & 1) + j + (LEN - 1);
+    const float2* cd0 = buf + St::CD + (L0 & 1) + j;        // even t
+    const float2* cd1 = buf + St::CD + ((L0 + 1) & 1) + j;  // odd t
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const float2 a = ((t & 1) ? cd1 : cd0)[t * (R + 2)];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v * St::W - t]);
+    }
+  }
+}
+
+// Warp-specialised: R / 32 consumer warps (one row per thread) and one producer warp
+// whose lane 0 issues the copies. full[b] completes when run r's copies into buffer
+// b = r mod kStages have landed; empty[b] when every consumer warp is done with it.
+template <int P0, int NV, int R>
+__global__ void __launch_bounds__(R + 32) k_band_df_tma(long long N, int nruns, const int4* __restrict__ runs, int n0,
+                                                        int n1, int n2, const float2* __restrict__ A, long long Np,
+                                                        int EA, const int* __restrict__ active, int nvec,
+                                                        const float2* __restrict__ xs, const int* __restrict__ Ex,
+                                                        const double* __restrict__ x, double* __restrict__ y,
+                                                        long long vs, double* __restrict__ pq, int* __restrict__ err) {
+  using St = DfStage<P0, NV, R>;
+  constexpr int M0 = St::M0;
+  constexpr int NW = R / 32;  // consumer warps
+  constexpr int kStages = df_stages(R);
+  extern __shared__ __align__(128) float2 dsm[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  const int j = threadIdx.x;
+  const int lane = j & 31;
+  const long long i0 = (long long)blockIdx.x * R;
+  const int v0 = blockIdx.y * NV;
+  if (j == 0) {
+    for (int b = 0; b < kStages; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(&empty[b])), "r"(NW));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long i = i0 + j;
+  const bool row = j < R && i < N;
+  float s[NV], c[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    s[v] = 0.f;
+    c[v] = 0.f;
+  }
+  if (j >= R) {  // producer warp
+    if (lane == 0) {
+      bool ok = true;
+      int last = -1;
+      for (int r = 0; r < nruns; ++r) {
+        const int b = r % kStages, k = r / kStages;
+        if (k > 0 && !mbar_wait_bounded(s_u32(&empty[b]), (uint32_t)((k - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        float2* buf = dsm + (size_t)b * St::ELEMS;
+        if (r == 0) df_issue<P0, NV, R, P0>(runs[0], buf, s_u32(&full[b]), A, Np, i0, xs, v0, nvec);
+        else df_issue<P0, NV, R, M0>(runs[r], buf, s_u32(&full[b]), A, Np, i0, xs, v0, nvec);
+        last = r;
+      }
+      if (!ok) atomicExch(err, 1);
+      // let every copy in flight land before the block can leave
+      for (int q = last - kStages + 1; q <= last; ++q)
+        if (q >= 0) mbar_wait_bounded(s_u32(&full[q % kStages]), (uint32_t)((q / kStages) & 1));
+    }
+  } else {  // consumer warps
+    if (row) {
+      const float2 a0 = A[kDfPad + i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a0, xs[(long long)min(v0 + v, nvec - 1) * Np + kDfPad + i]);
+    }
+    int i1 = 0, i2 = 0;
+    if (row) {
+      const long long t = i / n0;
+      i1 = (int)(t % n1);
+      i2 = (int)(t / n1);
+    }
+    bool ok = true;
+    for (int r = 0; r < nruns; ++r) {
+      const int b = r % kStages;
+      const int4 R4 = runs[r];
+      bool up = row, dn = row;
+      if (r > 0) {
+        const int o1 = (R4.z & 255) - 64, o2 = ((R4.z >> 8) & 255) - 64;
+        up = up && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
+        dn = dn && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
+      }
+      const bool warp_on = r == 0 || __any_sync(0xffffffffu, up || dn);
+      if (ok && !mbar_wait_bounded(s_u32(&full[b]), (uint32_t)((r / kStages) & 1))) {
+        ok = false;
+        atomicExch(err, 1);
+      }
+      if (ok && warp_on) {
+        const float2* buf = dsm + (size_t)b * St::ELEMS;
+        if (r == 0) df_run_smem<P0, NV, R, P0>(buf, j, R4.w, up, dn, s, c);
+        else df_run_smem<P0, NV, R, M0>(buf, j, R4.w, up, dn, s, c);
+        df_renorm<NV>(s, c);
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&empty[b])) : "memory");
+    }
+  }
+  bool on[NV];
+  double out[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int vv = v0 + v;
+    on[v] = row && vv < nvec && (!active || active[vv]);
+    out[v] = 0.0;
+    if (on[v]) {
+      out[v] = ((double)s[v] + (double)c[v]) * ldexp(1.0, Ex[vv] + EA);
+      y[vv * vs + i] = out[v];
+    }
+  }
+  if (pq) {  // fixed-order block sums of x_i y_i over the consumer warps
+    __shared__ double sred[NW];
+    const int w = j >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int vv = v0 + v;
+      if (vv >= nvec) break;
+      double t = on[v] ? x[vv * vs + i] * out[v] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0 && w < NW) sred[w] = t;
+      __syncthreads();
+      if (j == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < NW; ++q) sum += sred[q];
+        pq[(long long)vv * gridDim.x + blockIdx.x] = sum;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int P0, int NV, int R>
+cudaError_t band_df_tma_go(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
+                           long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
+                           const double* x, double* y, long long vs, double* pq, int* err, int* nblocks) {
+  using St = DfStage<P0, NV, R>;
+  const size_t smem = St::BYTES * df_stages(R);
+  static unsigned long long attr = 0;  // devices on which the attribute is set (one bit each)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(attr >> dev & 1ULL)) {
+    e = cudaFuncSetAttribute(k_band_df_tma<P0, NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr |= 1ULL << dev;
+  }
+  const dim3 grid((unsigned)((N + R - 1) / R), (unsigned)((nvec + NV - 1) / NV));
+  k_band_df_tma<P0, NV, R><<<grid, R + 32, smem, s>>>(N, nruns, runs, n[0], n[1], n[2], A, Np, EA, active, nvec, xs,
+                                                      Ex, x, y, vs, pq, err);
+  *nblocks = (int)grid.x;
+  return cudaGetLastError();
+}
+
+template <int P0>
+cudaError_t band_df_tma_p(cudaStream_t s, int R, int nv, long long N, int nruns, const int4* runs, const int* n,
+                          const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs,
+                          const int* Ex, const double* x, double* y, long long vs, double* pq, int* err, int* nb) {
+  if (R == 64) {
+    if (nv == 1) return band_df_tma_go<P0, 1, 64>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+    return band_df_tma_go<P0, 2, 64>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+  }
+  if (R == 128) {
+    if (nv == 1) return band_df_tma_go<P0, 1, 128>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+    return band_df_tma_go<P0, 2, 128>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+  }
+  if (nv == 1) return band_df_tma_go<P0, 1, 256>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+  return band_df_tma_go<P0, 2, 256>(s, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, nb);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-map form of the staged kernel (128 rows per block): per run four 2-D TMA
+// copies instead of 2 len + 2 NV bulk copies --
+//   cu[t][j]  = A[h0 + t][i0 + j]                       box {R, M0} at (i0, h0)
+//   cd[t][.]  = A[h0 + t][c0 + .], c0 = i0 - L0 - (M0 - 1) rounded down to even,
+//               the bounding box {W, M0} of the lower terms' parallelogram
+//   xu[v][.]  = x_{v0 + v}[i0 + L0 rounded down to even + .]   box {W, NV}
+//   xd[v][.]  = x_{v0 + v}[c0 + .]                             box {W, NV}
+// (indices in the padded row layout). Coordinates outside the tensor read zeros;
+// such entries only meet rows whose neighbour line is outside the grid, which are
+// predicated off. Row j's lower term of slot h0 + t sits at column
+// (L0 & 1) + j + (M0 - 1 - t) of cd and xd, its upper x at (L0 & 1) + j + t of xu.
+constexpr int kTmRows = 128;
+
+template <int P0, int NV>
+struct DfTmStage {
+  static constexpr int R = kTmRows;
+  static constexpr int M0 = 2 * P0 + 1;
+  static constexpr int W = R + M0 + 1;  // even
+  static constexpr int al(int v) { return (v + 15) / 16 * 16; }  // 128-byte sub-buffer starts
+  static constexpr int CU = 0;
+  static constexpr int CD = al(CU + M0 * R);
+  static constexpr int XU = al(CD + M0 * W);
+  static constexpr int XD = al(XU + NV * W);
+  static constexpr int ELEMS = al(XD + NV * W);
+  static constexpr uint32_t TX = (uint32_t)((M0 * R + M0 * W + 2 * NV * W) * 8);
+};
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+
+template <int P0, int NV, int LEN>
+__device__ __forceinline__ void df_run_tm(const float2* buf, int j, int L0, bool up, bool dn, float (&s)[NV],
+                                          float (&c)[NV]) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0, W = St::W;
+  const int o = L0 & 1;
+  if (up) {
+    const float2* xu = buf + St::XU + o + j;
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const float2 a = buf[St::CU + t * R + j];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v * W + t]);
+    }
+  }
+  if (dn) {
+    const float2* cd = buf + St::CD + o + j + (M0 - 1);
+    const float2* xd = buf + St::XD + o + j + (M0 - 1);
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const float2 a = cd[t * W - t];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v * W - t]);
+    }
+  }
+}
+
+template <int P0, int NV>
+__global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nruns, const int4* __restrict__ runs,
+                                                             int n0, int n1, int n2, const float2* __restrict__ A,
+                                                             const __grid_constant__ CUtensorMap tmUp,
+                                                             const __grid_constant__ CUtensorMap tmDn,
+                                                             const __grid_constant__ CUtensorMap tmX, long long Np,
+                                                             int EA, const int* __restrict__ active, int nvec,
+                                                             const float2* __restrict__ xs, const int* __restrict__ Ex,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             long long vs, double* __restrict__ pq,
+                                                             int* __restrict__ err) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0;
+  constexpr int NW = R / 32;
+  constexpr int S = 2;  // buffers in the ring (more resident blocks beat a deeper ring)
+  extern __shared__ __align__(128) float2 dsm[];
+  __shared__ __align__(8) unsigned long long full[S], empty[S];
+  const int j = threadIdx.x;
+  const int lane = j & 31;
+  const long long i0 = (long long)blockIdx.x * R;
+  const int v0 = blockIdx.y * NV;
+  if (j == 0) {
+    for (int b = 0; b < S; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(&empty[b])), "r"(NW));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long i = i0 + j;
+  const bool row = j < R && i < N;
+  float s[NV], c[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    s[v] = 0.f;
+    c[v] = 0.f;
+  }
+  if (j >= R) {  // producer warp
+    if (lane == 0) {
+      bool ok = true;
+      int last = -1;
+      const int xi = (int)(kDfPad + i0);
+      for (int r = 0; r < nruns; ++r) {
+        const int b = r % S, k = r / S;
+        if (k > 0 && !mbar_wait_bounded(s_u32(&empty[b]), (uint32_t)((k - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const int4 R4 = runs[r];
+        const int c0 = (xi - R4.w - (M0 - 1)) & ~1;
+        const uint32_t mb = s_u32(&full[b]);
+        const uint32_t base = s_u32(dsm + (size_t)b * St::ELEMS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(St::TX) : "memory");
+        tma_2d(base + St::CU * 8, &tmUp, xi, R4.x, mb);
+        tma_2d(base + St::CD * 8, &tmDn, c0, R4.x, mb);
+        tma_2d(base + St::XU * 8, &tmX, (xi + R4.w) & ~1, v0, mb);
+        tma_2d(base + St::XD * 8, &tmX, c0, v0, mb);
+        last = r;
+      }
+      if (!ok) atomicExch(err, 1);
+      for (int q = last - S + 1; q <= last; ++q)  // let every copy in flight land
+        if (q >= 0) mbar_wait_bounded(s_u32(&full[q % S]), (uint32_t)((q / S) & 1));
+    }
+  } else {  // consumer warps
+    if (row) {
+      const float2 a0 = A[kDfPad + i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a0, xs[(long long)min(v0 + v, nvec - 1) * Np + kDfPad + i]);
+    }
+    int i1 = 0, i2 = 0;
+    if (row) {
+      const long long t = i / n0;
+      i1 = (int)(t % n1);
+      i2 = (int)(t / n1);
+    }
+    bool ok = true;
+    for (int r = 0; r < nruns; ++r) {
+      const int b = r % S;
+      const int4 R4 = runs[r];
+      bool up = row, dn = row;
+      if (r > 0) {
+        const int o1 = (R4.z & 255) - 64, o2 = ((R4.z >> 8) & 255) - 64;
+        up = up && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
+        dn = dn && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
+      }
+      const bool warp_on = r == 0 || __any_sync(0xffffffffu, up || dn);
+      if (ok && !mbar_wait_bounded(s_u32(&full[b]), (uint32_t)((r / S) & 1))) {
+        ok = false;
+        atomicExch(err, 1);
+      }
+      if (ok && warp_on) {
+        const float2* buf = dsm + (size_t)b * St::ELEMS;
+        if (r == 0) df_run_tm<P0, NV, P0>(buf, j, R4.w, up, dn, s, c);
+        else df_run_tm<P0, NV, M0>(buf, j, R4.w, up, dn, s, c);
+        df_renorm<NV>(s, c);
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&empty[b])) : "memory");
+    }
+  }
+  bool on[NV];
+  double out[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int vv = v0 + v;
+    on[v] = row && vv < nvec && (!active || active[vv]);
+    out[v] = 0.0;
+    if (on[v]) {
+      out[v] = ((double)s[v] + (double)c[v]) * ldexp(1.0, Ex[vv] + EA);
+      y[vv * vs + i] = out[v];
+    }
+  }
+  if (pq) {
+    __shared__ double sred[NW];
+    const int w = j >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int vv = v0 + v;
+      if (vv >= nvec) break;
+      double t = on[v] ? x[vv * vs + i] * out[v] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0 && w < NW) sred[w] = t;
+      __syncthreads();
+      if (j == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < NW; ++q) sum += sred[q];
+        pq[(long long)vv * gridDim.x + blockIdx.x] = sum;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int P0, int NV>
+cudaError_t band_df_tm_go(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
+                          const DfTmaps& tm, long long Np, int EA, const int* active, int nvec, const float2* xs,
+                          const int* Ex, const double* x, double* y, long long vs, double* pq, int* err,
+                          int* nblocks) {
+  using St = DfTmStage<P0, NV>;
+  const size_t smem = (size_t)St::ELEMS * 8 * 2;
+  static unsigned long long attr = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(attr >> dev & 1ULL)) {
+    e = cudaFuncSetAttribute(k_band_df_tm<P0, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr |= 1ULL << dev;
+  }
+  const dim3 grid((unsigned)((N + kTmRows - 1) / kTmRows), (unsigned)((nvec + NV - 1) / NV));
+  k_band_df_tm<P0, NV><<<grid, kTmRows + 32, smem, s>>>(N, nruns, runs, n[0], n[1], n[2], A, tm.up, tm.dn,
+                                                        NV == 1 ? tm.x1 : tm.x2, Np, EA, active, nvec, xs, Ex, x, y,
+                                                        vs, pq, err);
+  *nblocks = (int)grid.x;
+  return cudaGetLastError();
+}
+
+template <int P0, int BS>
+void band_df_nv(cudaStream_t s, int nv, dim3 grid, long long N, int nruns, const int4* runs, const int* n,
+                const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
+                const double* x, double* y, long long vs, double* pq) {
+#define IGA_DF_GO(NVV)                                                                                          \
+  k_band_df<P0, NVV, BS><<<grid, BS, 0, s>>>(N, nruns, runs, n[0], n[1], n[2], A, Np, EA, active, nvec, xs, Ex, \
+                                              x, y, vs, pq)
   switch (nv) {
     case 1: IGA_DF_GO(1); break;
     case 2: IGA_DF_GO(2); break;
@@ -220,6 +773,19 @@ int band_df_go(cudaStream_t s, int nv, long long N, int nruns, const int4* runs,
     default: IGA_DF_GO(4); break;
   }
 #undef IGA_DF_GO
+}
+
+template <int BS>
+int band_df_go(cudaStream_t s, int nv, int p0, long long N, int nruns, const int4* runs, const int* n,
+               const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
+               const double* x, double* y, long long vs, double* pq) {
+  const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
+  switch (p0) {
+    case 2: band_df_nv<2, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
+    case 3: band_df_nv<3, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
+    case 4: band_df_nv<4, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
+    default: band_df_nv<0, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
+  }
   return (int)grid.x;
 }
 
@@ -262,19 +828,71 @@ cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
-                           long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
-                           const double* x, double* y, long long vs, int threads, int nv, double* pq, int* npq) {
+cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0,
+                           const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs,
+                           const int* Ex, const double* x, double* y, long long vs, int threads, int nv, double* pq,
+                           int* npq, int* err, const DfTmaps* tm) {
   if (nv <= 0) nv = nvec < 4 ? nvec : 4;
   if (nv < 1) nv = 1;
   if (nv > 4) nv = 4;
   int nb;
-  if (threads == 64) nb = band_df_go<64>(s, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else if (threads == 128) nb = band_df_go<128>(s, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else if (threads == 512) nb = band_df_go<512>(s, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else nb = band_df_go<256>(s, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  if (threads == 128 && nv <= 2 && p0 >= 2 && p0 <= 4 && err && tm && tm->ok) {
+    cudaError_t e;
+#define IGA_TM_GO(P, V) band_df_tm_go<P, V>(s, N, nruns, runs, n, A, *tm, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb)
+    if (p0 == 2) e = nv == 1 ? IGA_TM_GO(2, 1) : IGA_TM_GO(2, 2);
+    else if (p0 == 3) e = nv == 1 ? IGA_TM_GO(3, 1) : IGA_TM_GO(3, 2);
+    else e = nv == 1 ? IGA_TM_GO(4, 1) : IGA_TM_GO(4, 2);
+#undef IGA_TM_GO
+    if (npq) *npq = nb;
+    return e;
+  }
+  if ((threads == 64 || threads == 128 || threads == 256) && nv <= 2 && p0 >= 2 && p0 <= 4 && err) {
+    cudaError_t e;
+    if (p0 == 2) e = band_df_tma_p<2>(s, threads, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb);
+    else if (p0 == 3) e = band_df_tma_p<3>(s, threads, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb);
+    else e = band_df_tma_p<4>(s, threads, nv, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb);
+    if (npq) *npq = nb;
+    return e;
+  }
+  if (threads == 64) nb = band_df_go<64>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else if (threads == 128) nb = band_df_go<128>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else if (threads == 512) nb = band_df_go<512>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else nb = band_df_go<256>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
   if (npq) *npq = nb;
   return cudaGetLastError();
+}
+
+// The tensor maps of one split band (M or K) and of the split vectors, for the
+// 128-row tensor-map kernel: 8-byte elements, rows of stride Np, no swizzle, zero
+// fill outside. ok = false (and the bulk-copy kernels serve) if the driver does not
+// provide the encoder or refuses a map.
+bool df_encode_maps(const float2* A, int H, const float2* xs, int nvmax, long long Np, int p0, DfTmaps* tm) {
+  tm->ok = false;
+  if (p0 < 2 || p0 > 4) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int M0 = 2 * p0 + 1, W = kTmRows + M0 + 1;
+  auto make = [&](CUtensorMap* m, const float2* base, int rows, int bx, int by) {
+    const cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Np * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!make(&tm->up, A, H, kTmRows, M0) || !make(&tm->dn, A, H, W, M0) || !make(&tm->x1, xs, nvmax, W, 1) ||
+      !make(&tm->x2, xs, nvmax, W, 2))
+    return false;
+  tm->ok = true;
+  return true;
 }
 
 }  // namespace iga

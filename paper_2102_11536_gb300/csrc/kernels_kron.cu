@@ -9,8 +9,9 @@
 // memory (element (k, line) at k * kLines + line; reads coalesced along the lines
 // for axis 0, where a block's lines are one contiguous range, and across the lines
 // for the other axes; several loads in flight per thread), the first kLines threads
-// run the two substitutions, one line each, in shared memory, and all threads write
-// the lines back the same way. pre multiplies the
+// run the two substitutions, one line each (with the factor rows pre-scaled by
+// 1 / L_kk and the recurrence window in registers), and all threads write the lines
+// back the same way. pre multiplies the
 // input entries (the first axis: D^{-1/2} Dhat^{1/2}), post the output entries
 // (the last axis).
 #include "iga_internal.h"
@@ -37,9 +38,11 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
                                                       const double* __restrict__ post,
                                                       const double* __restrict__ rdot, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char kron_smem[];
-  T* sb = reinterpret_cast<T*>(kron_smem);  // [n][kLines] lines, then the factor [n][P+1] and 1/L_kk [n]
-  T* sL = sb + (size_t)n * kLines;
-  T* sD = sL + (size_t)n * (P + 1);
+  // [n][kLines] lines, then the scaled factor rows for the forward [n][P+1] and the
+  // backward [n][P+1] substitution
+  T* sb = reinterpret_cast<T*>(kron_smem);
+  T* sF = sb + (size_t)n * kLines;
+  T* sG = sF + (size_t)n * (P + 1);
   const int v = blockIdx.y;
   if (active && !active[v]) return;
   const long long l0 = (long long)blockIdx.x * kLines;
@@ -48,8 +51,14 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
   const TI* x = in + v * vs;
   TO* o = out + v * vs;
   const int cnt = nl * n;
-  for (int e = t; e < n * (P + 1); e += kThreads) sL[e] = L[e];
-  for (int e = t; e < n; e += kThreads) sD[e] = dinv[e];
+  // forward  w_k = d_k s_k - sum_d (d_k L_{k,k-d}) w_{k-d},
+  // backward z_k = d_k w_k - sum_d (d_k L_{k+d,k}) z_{k+d},   d_k = 1 / L_kk
+  for (int e = t; e < n * (P + 1); e += kThreads) {
+    const int k = e / (P + 1), d = e - k * (P + 1);
+    const T dk = dinv[k];
+    sF[e] = d == 0 ? dk : dk * L[e];
+    sG[e] = d == 0 ? dk : (k + d < n ? dk * L[(size_t)(k + d) * (P + 1) + d] : T(0));
+  }
   // stage
   if (A == 1) {
     const long long g0 = l0 * n;  // the block's lines are one contiguous range
@@ -74,22 +83,36 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
   }
   __syncthreads();
   if (t < nl) {
-    // forward: w_k = (s_k - sum_{d=1..p} L_{k,k-d} w_{k-d}) / L_kk
+    // The last P values of the recurrence stay in registers (win[d] = value d steps
+    // back; zero before the line's start, where the factor entries are zero too), and
+    // the terms not involving the previous value are summed first, so one multiply-add
+    // per step lies on the dependency chain.
+    T win[P + 1];
+#pragma unroll
+    for (int d = 0; d <= P; ++d) win[d] = T(0);
     for (int k = 0; k < n; ++k) {
-      T s = sb[k * kLines + t];
-      const T* Lk = sL + (size_t)k * (P + 1);
+      const T* F = sF + (size_t)k * (P + 1);
+      T acc = F[0] * sb[k * kLines + t];
 #pragma unroll
-      for (int d = 1; d <= P; ++d)
-        if (k - d >= 0) s -= Lk[d] * sb[(k - d) * kLines + t];
-      sb[k * kLines + t] = s * sD[k];
+      for (int d = P; d >= 2; --d) acc -= F[d] * win[d];
+      const T w = acc - F[1] * win[1];
+      sb[k * kLines + t] = w;
+#pragma unroll
+      for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+      win[1] = w;
     }
-    // backward: z_k = (w_k - sum_{d=1..p} L_{k+d,k} z_{k+d}) / L_kk
-    for (int k = n - 1; k >= 0; --k) {
-      T s = sb[k * kLines + t];
 #pragma unroll
-      for (int d = 1; d <= P; ++d)
-        if (k + d < n) s -= sL[(size_t)(k + d) * (P + 1) + d] * sb[(k + d) * kLines + t];
-      sb[k * kLines + t] = s * sD[k];
+    for (int d = 0; d <= P; ++d) win[d] = T(0);
+    for (int k = n - 1; k >= 0; --k) {
+      const T* G = sG + (size_t)k * (P + 1);
+      T acc = G[0] * sb[k * kLines + t];
+#pragma unroll
+      for (int d = P; d >= 2; --d) acc -= G[d] * win[d];
+      const T z = acc - G[1] * win[1];
+      sb[k * kLines + t] = z;
+#pragma unroll
+      for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+      win[1] = z;
     }
   }
   __syncthreads();
@@ -157,7 +180,7 @@ cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* ac
                     const void* dinv, const void* in, void* out, long long vs, const double* pre,
                     const double* post, const double* rdot, double* part, int* npart) {
   const long long R = sh.A * sh.B;
-  const size_t smem = (size_t)n * (kLines + P + 2) * sizeof(T);
+  const size_t smem = (size_t)n * (kLines + 2 * P + 2) * sizeof(T);
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(k_kron_axis<P, T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -199,7 +222,7 @@ cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nve
                              const double* rdot, double* part, int* npart) {
   if (npart) *npart = 0;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
-  if (n < 1 || nvec < 1 || (size_t)n * (kLines + p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
+  if (n < 1 || nvec < 1 || (size_t)n * (kLines + 2 * p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
   if (!f32 && !(in_is_double && out_is_double)) return cudaErrorInvalidValue;
 #define IGA_KRON(PP) \
   return kron_types<PP>(s, n, sh, nvec, active, f32, L, dinv, in, in_is_double, out, out_is_double, vs, pre, post, \
