@@ -99,7 +99,8 @@ FORMS = [
 # (kernel, sha256 of the kernel's source file, first 16 hex): a capture only
 # counts while the source it was taken on is unchanged (profiles/*.md).
 NCU_TRAFFIC = {
-    ("band_mass", "1c1221dd916a1cdf"): 375.13e6,  # k_band_spmv<2, 64>, 2-vector launch (profiles/k_band_spmv_cube64_p3.md)
+    ("band_mass", "6428c7f922f0f6eb"): 373.9e6,   # k_band_spmv<2, 64>, 2-vector launch (profiles/k_band_spmv_cube64_p3.md)
+    ("band_mass_df", "07fe6d7e4301a12e"): 390.5e6,  # k_band_df_tm<3, 2>, 2-vector launch (profiles/k_band_df_tm_cube64_p3.md)
     ("mass", "618d068dc16a5b19"): 186.69e6,       # k_mid_mass<4>, 1-vector launch
 }
 

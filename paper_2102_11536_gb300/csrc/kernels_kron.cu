@@ -6,7 +6,7 @@
 // O(N) cost of the paper's Kronecker solvers).
 //
 // One block of kThreads threads takes kLines lines: all threads stage them in shared
-// memory (element (k, line) at k * kLines + line; reads coalesced along the lines
+// memory (element (k, line) at k * kLS + line; reads coalesced along the lines
 // for axis 0, where a block's lines are one contiguous range, and across the lines
 // for the other axes; several loads in flight per thread), the first kLines threads
 // run the two substitutions, one line each (with the factor rows pre-scaled by
@@ -22,6 +22,9 @@ namespace iga {
 namespace {
 
 constexpr int kLines = 32;    // lines per block (one warp solves them)
+constexpr int kLS = kLines + 1;  // shared row stride: odd, so that both the staging walks
+                                 // (consecutive entries of a line) and the solve
+                                 // (consecutive lines) are free of bank conflicts
 constexpr int kThreads = 256; // threads staging and writing back
 
 // P = p: entries below the diagonal in a row of the factor; T: arithmetic (double, or
@@ -38,10 +41,10 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
                                                       const double* __restrict__ post,
                                                       const double* __restrict__ rdot, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char kron_smem[];
-  // [n][kLines] lines, then the scaled factor rows for the forward [n][P+1] and the
+  // [n][kLS] lines, then the scaled factor rows for the forward [n][P+1] and the
   // backward [n][P+1] substitution
   T* sb = reinterpret_cast<T*>(kron_smem);
-  T* sF = sb + (size_t)n * kLines;
+  T* sF = sb + (size_t)n * kLS;
   T* sG = sF + (size_t)n * (P + 1);
   const int v = blockIdx.y;
   if (active && !active[v]) return;
@@ -59,18 +62,39 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
     sF[e] = d == 0 ? dk : dk * L[e];
     sG[e] = d == 0 ? dk : (k + d < n ? dk * L[(size_t)(k + d) * (P + 1) + d] : T(0));
   }
-  // stage
+  // stage (the (entry, line) walks are incremental: no division per element)
+  const int dl = kThreads / n, dk = kThreads - dl * n;  // axis 0: e -> e + kThreads
+  long long gline = 0;                                  // other axes, full blocks: line t % kLines
+  if (A != 1 && nl == kLines) {
+    const long long rr = l0 + (t & (kLines - 1));
+    const long long y = rr / A;
+    gline = (rr - y * A) + A * (long long)n * y;
+  }
   if (A == 1) {
     const long long g0 = l0 * n;  // the block's lines are one contiguous range
+    int line = t / n, k = t - (t / n) * n;
 #pragma unroll 4
     for (int e = t; e < cnt; e += kThreads) {
-      const int line = e / n, k = e - line * n;
       double u = (double)x[g0 + e];
       if (pre) u *= pre[g0 + e];
-      sb[k * kLines + line] = (T)u;
+      sb[k * kLS + line] = (T)u;
+      k += dk;
+      line += dl;
+      if (k >= n) {
+        k -= n;
+        ++line;
+      }
+    }
+  } else if (nl == kLines) {
+    const int line = t & (kLines - 1);
+#pragma unroll 4
+    for (int k = t / kLines; k < n; k += kThreads / kLines) {
+      const long long g = gline + A * k;
+      double u = (double)x[g];
+      if (pre) u *= pre[g];
+      sb[k * kLS + line] = (T)u;
     }
   } else {
-#pragma unroll 4
     for (int e = t; e < cnt; e += kThreads) {
       const int k = e / nl, line = e - k * nl;
       const long long rr = l0 + line;
@@ -78,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
       const long long g = xx + A * (k + (long long)n * y);
       double u = (double)x[g];
       if (pre) u *= pre[g];
-      sb[k * kLines + line] = (T)u;
+      sb[k * kLS + line] = (T)u;
     }
   }
   __syncthreads();
@@ -90,26 +114,28 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
     T win[P + 1];
 #pragma unroll
     for (int d = 0; d <= P; ++d) win[d] = T(0);
+#pragma unroll 4
     for (int k = 0; k < n; ++k) {
       const T* F = sF + (size_t)k * (P + 1);
-      T acc = F[0] * sb[k * kLines + t];
+      T acc = F[0] * sb[k * kLS + t];
 #pragma unroll
       for (int d = P; d >= 2; --d) acc -= F[d] * win[d];
       const T w = acc - F[1] * win[1];
-      sb[k * kLines + t] = w;
+      sb[k * kLS + t] = w;
 #pragma unroll
       for (int d = P; d >= 2; --d) win[d] = win[d - 1];
       win[1] = w;
     }
 #pragma unroll
     for (int d = 0; d <= P; ++d) win[d] = T(0);
+#pragma unroll 4
     for (int k = n - 1; k >= 0; --k) {
       const T* G = sG + (size_t)k * (P + 1);
-      T acc = G[0] * sb[k * kLines + t];
+      T acc = G[0] * sb[k * kLS + t];
 #pragma unroll
       for (int d = P; d >= 2; --d) acc -= G[d] * win[d];
       const T z = acc - G[1] * win[1];
-      sb[k * kLines + t] = z;
+      sb[k * kLS + t] = z;
 #pragma unroll
       for (int d = P; d >= 2; --d) win[d] = win[d - 1];
       win[1] = z;
@@ -121,10 +147,10 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
   double snew = 0.0, sold = 0.0;
   if (A == 1) {
     const long long g0 = l0 * n;
+    int line = t / n, k = t - (t / n) * n;
 #pragma unroll 4
     for (int e = t; e < cnt; e += kThreads) {
-      const int line = e / n, k = e - line * n;
-      double u = (double)sb[k * kLines + line];
+      double u = (double)sb[k * kLS + line];
       if (post) u *= post[g0 + e];
       if (rv) {
         const double rr = rv[g0 + e];
@@ -132,15 +158,34 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
         snew = fma(rr, u, snew);
       }
       o[g0 + e] = (TO)u;
+      k += dk;
+      line += dl;
+      if (k >= n) {
+        k -= n;
+        ++line;
+      }
+    }
+  } else if (nl == kLines) {
+    const int line = t & (kLines - 1);
+#pragma unroll 4
+    for (int k = t / kLines; k < n; k += kThreads / kLines) {
+      const long long g = gline + A * k;
+      double u = (double)sb[k * kLS + line];
+      if (post) u *= post[g];
+      if (rv) {
+        const double rr = rv[g];
+        sold = fma(rr, (double)o[g], sold);
+        snew = fma(rr, u, snew);
+      }
+      o[g] = (TO)u;
     }
   } else {
-#pragma unroll 4
     for (int e = t; e < cnt; e += kThreads) {
       const int k = e / nl, line = e - k * nl;
       const long long rr = l0 + line;
       const long long y = rr / A, xx = rr - y * A;
       const long long g = xx + A * (k + (long long)n * y);
-      double u = (double)sb[k * kLines + line];
+      double u = (double)sb[k * kLS + line];
       if (post) u *= post[g];
       if (rv) {
         const double rr = rv[g];
@@ -180,7 +225,7 @@ cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* ac
                     const void* dinv, const void* in, void* out, long long vs, const double* pre,
                     const double* post, const double* rdot, double* part, int* npart) {
   const long long R = sh.A * sh.B;
-  const size_t smem = (size_t)n * (kLines + 2 * P + 2) * sizeof(T);
+  const size_t smem = (size_t)n * (kLS + 2 * P + 2) * sizeof(T);
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(k_kron_axis<P, T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -222,7 +267,7 @@ cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nve
                              const double* rdot, double* part, int* npart) {
   if (npart) *npart = 0;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
-  if (n < 1 || nvec < 1 || (size_t)n * (kLines + 2 * p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
+  if (n < 1 || nvec < 1 || (size_t)n * (kLS + 2 * p + 2) * esz > 227 * 1024) return cudaErrorInvalidValue;
   if (!f32 && !(in_is_double && out_is_double)) return cudaErrorInvalidValue;
 #define IGA_KRON(PP) \
   return kron_types<PP>(s, n, sh, nvec, active, f32, L, dinv, in, in_is_double, out, out_is_double, vs, pre, post, \

@@ -48,13 +48,26 @@ cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, c
 // Warp w of a 256-thread block sums vector w's np partials (layout [v][np]; lane
 // stride 32, then a shuffle tree): a fixed order, so the result is reproducible, and
 // 32 lanes instead of one serial FP64 chain.
+// out[v] = sum of partial[v][0..np) for v < nvec, by the whole block (blockDim.x a
+// multiple of 32 with at least nvec warps): each vector gets blockDim.x / 32 / nvec
+// warps, which sum fixed strided shares, then their warp sums are added in order.
 __device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out, int np = kRedBlocks) {
+  __shared__ double wsum[32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w < nvec) {
+  const int nw = (int)(blockDim.x >> 5), per = nw / nvec;  // warps per vector
+  const int v = w / per, q = w - v * per;
+  if (v < nvec) {
     double s = 0.0;
-    for (int b = lane; b < np; b += 32) s += partial[(long long)w * np + b];
+#pragma unroll 4
+    for (int b = q * 32 + lane; b < np; b += per * 32) s += partial[(long long)v * np + b];
     s = warp_sum(s);
-    if (lane == 0) out[w] = s;
+    if (lane == 0) wsum[w] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int i = 0; i < per; ++i) s += wsum[threadIdx.x * per + i];
+    out[threadIdx.x] = s;
   }
   __syncthreads();
 }
