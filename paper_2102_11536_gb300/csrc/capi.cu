@@ -47,6 +47,7 @@ struct iga_handle {
   float2* df_xs = nullptr;        // [kMaxVec][Np] split input vectors (zero pads)
   int* df_E = nullptr;            // [kMaxVec] their exponents, [kMaxVec] scratch
   unsigned long long* df_part = nullptr;  // [kMaxVec][kDfBlocks] partial maxima
+  unsigned int* df_bar = nullptr;         // grid barrier of the cooperative split (count, generation)
   bool df_ready = false;
   DfTmaps tmM, tmK;               // tensor maps of the split bands (and vectors)
   // operator workspace
@@ -591,6 +592,8 @@ int assemble_band_df(iga_handle* h) {
   CKS(dalloc(h, &h->df_xs, nX));
   CKS(dalloc(h, &h->df_E, (size_t)2 * kMaxVec));
   CKS(dalloc(h, &h->df_part, (size_t)kMaxVec * kDfBlocks));
+  CKS(dalloc(h, &h->df_bar, 2));
+  CK(cudaMemsetAsync(h->df_bar, 0, 2 * sizeof(unsigned int), s));
   CK(cudaMemsetAsync(h->Mdf, 0, sizeof(float2) * nA, s));
   CK(cudaMemsetAsync(h->Kdf, 0, sizeof(float2) * nA, s));
   CK(cudaMemsetAsync(h->df_xs, 0, sizeof(float2) * nX, s));
@@ -626,7 +629,8 @@ cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const 
   const bool mass = cls == IGA_PROF_BAND_MASS;
   if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
     float2* xs = h->df_xs + h->df_slack;
-    cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part);
+    cudaError_t e =
+        launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar, h->dflag + 2);
     if (e != cudaSuccess) return e;
     return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
                           (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
@@ -1199,7 +1203,7 @@ void iga_destroy(iga_handle* h) {
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
-  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part);
+  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
@@ -1463,15 +1467,13 @@ int iga_assemble(iga_handle* h) {
 int iga_apply_M(iga_handle* h, int nvec, const double* x, double* y) {
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
-  CKS(apply_M(h, nvec, nullptr, x, y));
-  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? check_tc_error(h) : IGA_OK;
+  return apply_M(h, nvec, nullptr, x, y);
 }
 
 int iga_apply_K(iga_handle* h, int nvec, const double* x, double* y) {
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !x || !y) return fail(h, IGA_EINVAL, "bad arguments");
-  CKS(apply_K(h, nvec, nullptr, x, y));
-  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? check_tc_error(h) : IGA_OK;
+  return apply_K(h, nvec, nullptr, x, y);
 }
 
 int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y) {

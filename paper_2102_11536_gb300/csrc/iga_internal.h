@@ -239,7 +239,7 @@ cudaError_t launch_band_spmv(cudaStream_t s, long long N, int H, const long long
 // df_slack(maxL) zeroed elements before and after every split array (the reach of
 // the staged copies); kDfBlocks partial maxima per vector.
 constexpr int kDfPad = 16;
-constexpr int kDfBlocks = 256;
+constexpr int kDfBlocks = 512;
 inline long long df_row_stride(long long N) { return (N + 2 * kDfPad + 15) / 16 * 16; }
 inline long long df_slack(long long maxL) { return (maxL + 1024 + 15) / 16 * 16; }
 // the runs of the upper half: per run {first slot, length, (o1 + 64) | (o2 + 64) << 8, linear offset}
@@ -247,9 +247,11 @@ std::vector<int> band_df_runs(const int* n, const int* p);
 // Adf = split(A 2^-E) with one exponent E (left in dE[0]) for the whole [H][N] band
 cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const double* A, float2* Adf, long long Np,
                                    unsigned long long* part, int* dE);
-// xs[v] = split(x[v] 2^-E_v), E_v (into Ex[v]) from the vector's largest magnitude
+// xs[v] = split(x[v] 2^-E_v), E_v (into Ex[v]) from the vector's largest magnitude; with
+// bar (2 zeroed device words kept for it) and err, one cooperative launch whose grid
+// barrier's bounded wait sets *err = 1 if it runs out, else two launches
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
-                            float2* xs, long long Np, int* Ex, unsigned long long* part);
+                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err);
 // y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
 // pq / npq as in launch_band_spmv (x is the FP64 input, read only for pq)
 // 2-D tensor maps over a split band ([H][Np], boxes for the upper rows and the lower

@@ -63,6 +63,47 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long m) {
   return m;
 }
 
+// (hi, lo) of w = x 2^-E by integer operations on x's bits: hi = w rounded to 24
+// significant bits (to nearest, ties to even: the 53-bit significand cut after 24 bits),
+// lo = the exact remainder w - hi (an integer of at most 29 bits times 2^(e - 52))
+// rounded to FP32. The same values as __double2float_rn(w) and __double2float_rn(w - hi),
+// without the FP64 conversions, which GB300 runs on its narrow FP64 units. Zero, subnormal,
+// infinite and NaN entries, and w outside [2^-74, 4) (hi or the scaled remainder would
+// leave FP32's normal range), take that FP64 path (sc = 2^-E).
+__device__ __forceinline__ float2 df_split_entry(double x, int E, double sc) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+  if (e == 0 && m == 0) return make_float2(__uint_as_float(sign << 31), 0.0f);
+  const int ep = e - E;  // biased exponent of w
+  if (e == 0 || e == 0x7FF || ep < 949 || ep > 1024) {
+    const double w = x * sc;
+    const float hi = __double2float_rn(w);
+    return make_float2(hi, __double2float_rn(w - (double)hi));
+  }
+  const unsigned long long M = m | (1ULL << 52);
+  unsigned q = (unsigned)(M >> 29);
+  const int rem = (int)(M & 0x1FFFFFFFULL);
+  int fe = ep - 896;  // FP32 biased exponent
+  int r = rem;
+  if (rem > (1 << 28) || (rem == (1 << 28) && (q & 1u))) {
+    ++q;
+    r = rem - (1 << 29);
+  }
+  if (q == (1u << 24)) {
+    q = 1u << 23;
+    ++fe;
+  }
+  const float hi = __uint_as_float((sign << 31) | ((unsigned)fe << 23) | (q & 0x7FFFFFu));
+  float lo = 0.0f;
+  if (r != 0) {
+    lo = __fmul_rn(__int2float_rn(r), __uint_as_float((unsigned)(ep - 948) << 23));  // r 2^(ep - 1075)
+    if (sign) lo = -lo;
+  }
+  return make_float2(hi, lo);
+}
+
 // part[v][blockIdx.x] = max_i |x[v][i]| over the block's grid-stride share (as bits)
 __global__ void k_df_absmax(long long n, const int* __restrict__ active, const double* __restrict__ x, long long vs,
                             unsigned long long* __restrict__ part) {
@@ -93,10 +134,63 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
   if (blockIdx.x == 0 && threadIdx.x == 0 && Eout) Eout[v] = E;
   const double sc = ldexp(1.0, -E);
   float2* out = xs + (long long)v * xvs + kDfPad;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double w = x[v * vs + i] * sc;
-    const float hi = __double2float_rn(w);
-    out[i] = make_float2(hi, __double2float_rn(w - (double)hi));
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_split_entry(x[v * vs + i], E, sc);
+}
+
+// The two passes of a vector split in one cooperative launch (every block resident):
+// block maxima, a grid barrier, then every block reduces the maxima and splits its
+// grid-stride share. bar[0] counts arrivals, bar[1] is the barrier's generation; the
+// wait is bounded (err = 1 if it runs out; the results are then not to be used).
+constexpr long long kBarLimit = 1LL << 22;
+
+__global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, const int* __restrict__ active,
+                                                       const double* __restrict__ x, long long vs,
+                                                       unsigned long long* __restrict__ part,
+                                                       float2* __restrict__ xs, long long xvs, int* __restrict__ Eout,
+                                                       unsigned int* bar, int* err) {
+  const int G = gridDim.x;
+  const long long stride = (long long)G * blockDim.x;
+  for (int v = 0; v < nvec; ++v) {
+    unsigned long long m = 0;
+    if (!active || active[v])
+      for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = max(m, abs_bits(x[v * vs + i]));
+    m = block_max(m);
+    if (threadIdx.x == 0) part[(long long)v * G + blockIdx.x] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g0 = *gen;
+    if (atomicAdd(bar, 1u) == (unsigned int)G - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g0) {
+        if (++it > kBarLimit) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  for (int v = 0; v < nvec; ++v) {
+    if (active && !active[v]) continue;  // uniform over the block
+    unsigned long long m = 0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) m = max(m, *(volatile unsigned long long*)&part[(long long)v * G + b]);
+    const int E = df_exponent(block_max(m));
+    if (blockIdx.x == 0 && threadIdx.x == 0) Eout[v] = E;
+    const double sc = ldexp(1.0, -E);
+    float2* out = xs + (long long)v * xvs + kDfPad;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      out[i] = df_split_entry(x[v * vs + i], E, sc);
   }
 }
 
@@ -821,7 +915,34 @@ cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const dou
 }
 
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
-                            float2* xs, long long Np, int* Ex, unsigned long long* part) {
+                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err) {
+  if (bar && err) {  // one cooperative launch, two blocks per SM
+    static int nsm[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && nsm[dev] == 0) {
+      int v = 0, coop = 0;
+      if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+      nsm[dev] = coop ? v : -1;
+    }
+    const int sm = dev < 64 ? nsm[dev] : -1;
+    if (sm > 0) {
+      const long long G = std::min<long long>(std::min<long long>(2LL * sm, kDfBlocks), std::max<long long>(1, (N + 255) / 256));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)G);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, vs, part, xs, Np, Ex, bar, err);
+    }
+  }
   k_df_absmax<<<dim3(kDfBlocks, nvec), 256, 0, s>>>(N, active, x, vs, part);
   const unsigned gx = (unsigned)std::min<long long>((N + 255) / 256, 2 * kDfBlocks);
   k_df_split<<<dim3(gx, nvec), 256, 0, s>>>(N, kDfBlocks, active, x, vs, part, nullptr, xs, Np, Ex);
