@@ -49,7 +49,9 @@ extern "C" {
 #define IGA_OP_ASSEMBLED_DF 2 /* the same band rows held as pairs of FP32 numbers (hi + lo, 48
                                  significant bits, one power-of-two scale per matrix and per
                                  vector); products in double-FP32 arithmetic: error-free FP32
-                                 products and TwoSum accumulation, a few 2^-48 of sum |a||x| */
+                                 products and TwoSum accumulation, a few 2^-48 of sum |a||x|,
+                                 plus, for entries below about 2^-130 of the vector's largest,
+                                 an absolute error of that order */
 
 /* Arithmetic of the preconditioner's fast-diagonalisation mode products. */
 #define IGA_PREC_FP64 0       /* FP64 (default); plain CG */

@@ -237,3 +237,39 @@ def test_df_cube64_sampled_rows():
             bound = C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X[v]))
             assert np.all(np.abs(Y[v][rows] - ref) <= bound)
     g.close()
+
+
+@pytest.mark.parametrize("decades", [15, 200])
+def test_df_split_paths_wide_dynamic_range(decades):
+    """Inputs spanning 10^-decades .. 10^decades with zeros and negative zeros: the
+    split's integer path, its FP64 fallback (entries whose scaled value leaves FP32's
+    normal range) and zero handling. Bound: the relative term of the arithmetic plus
+    the absolute floor of a per-vector power-of-two scale, 2^-130 max|x| sum_j |a_ij|
+    per term (entries that far below the largest are carried to that absolute
+    precision only). The reference is the FP64 product of the same assembled band:
+    with inputs spread over 10^400 a small coefficient's assembly roundoff (probing
+    against the oracle's direct quadrature, ~1e-16 of the row's larger terms) times a
+    10^200 entry is not the arithmetic under test; at 10^+-15 the oracle's rows serve
+    as well."""
+    w = CASES["3d_ragged_p3"]
+    P = oracle.Patch(w.p, w.knots, w.ctrl())
+    Mr, Kr = P.assemble()
+    rows = np.arange(P.N)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal(P.N) * 10.0 ** rng.uniform(-decades, decades, P.N)
+    X[rng.integers(0, P.N, 40)] = 0.0
+    X[rng.integers(0, P.N, 40)] = -0.0
+    gdf = _gpu(w, op_form="assembled_df")
+    g64 = _gpu(w, op_form="assembled")
+    y = torch.empty(P.N, dtype=torch.float64, device=DEV)
+    y64 = torch.empty_like(y)
+    for A, adf, a64 in ((Mr, gdf.apply_M, g64.apply_M), (Kr, gdf.apply_K, g64.apply_K)):
+        adf(_t(X), y)
+        a64(_t(X), y64)
+        absA = P.band_rows_times(rows, np.abs(A), np.ones(P.N))
+        bound = C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X)) + 343 * 2.0 ** -130 * np.abs(X).max() * absA
+        assert np.all(np.abs(_np(y) - _np(y64)) <= bound)
+        if decades <= 15:
+            assert np.all(np.abs(_np(y) - P.band_rows_times(rows, A, X)) <= bound)
+    gdf.close()
+    g64.close()
