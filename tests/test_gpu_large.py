@@ -1,10 +1,11 @@
 """Full-size check of the largest configuration: 3-D deformed cube, p = 4 (C^3),
 128^3 elements, N = 2 197 000 interior dofs, 262 M Gauss points, k = 3 (6th order).
 
-The oracle computes single rows of M and K one by one at this size; the time
-stepping is checked by properties that hold at any size: the mixed forms stay
-within 1e-8 of the FP64 form, the graph replay equals the host loop, and the
-discrete energy does not grow at rho_inf = 0.5.
+The oracle computes single rows of M and K one by one at this size (the
+double-FP32 band products against the bound of their arithmetic); the time
+stepping is checked by properties that hold at any size: the mixed and double-FP32
+forms stay within 1e-8 of the FP64 form, the graph replay equals the host loop,
+and the discrete energy does not grow at rho_inf = 0.5.
 """
 import numpy as np
 import pytest
@@ -46,6 +47,15 @@ def test_cube128_sampled_rows(c3):
         yk = y.cpu().numpy()[rows]
         ref = P.band_rows_times(rows, Kr, X)
         assert np.abs(yk - ref).max() < 1e-11 * np.abs(ref).max(), form
+    # double-FP32 band products: each sampled row within 64 2^-48 sum_j |a_ij||x_j|
+    g.set_op_form("assembled_df")
+    bound = 64 * 2.0 ** -48
+    g.apply_M(x, y)
+    assert np.all(np.abs(y.cpu().numpy()[rows] - P.band_rows_times(rows, Mr, X))
+                  <= bound * P.band_rows_times(rows, np.abs(Mr), np.abs(X)))
+    g.apply_K(x, y)
+    assert np.all(np.abs(y.cpu().numpy()[rows] - P.band_rows_times(rows, Kr, X))
+                  <= bound * P.band_rows_times(rows, np.abs(Kr), np.abs(X)))
     g.set_op_form("matrix_free")
 
 
@@ -77,7 +87,9 @@ def test_cube128_forms_agree(c3):
                                         ("fp32", "assembled", "fp32", True, w.tol),
                                         ("fp32_host", "assembled", "fp32", False, w.tol),
                                         ("bf16", "assembled", "bf16", True, 1e-11),
-                                        ("mf", "matrix_free", "fp64", True, w.tol)]:
+                                        ("mf", "matrix_free", "fp64", True, w.tol),
+                                        ("df", "assembled_df", "banded32", True, w.tol),
+                                        ("df_host", "assembled_df", "banded32", False, w.tol)]:
         g.set_op_form(op)
         g.set_precond(prec)
         g.set_graphs(graphs)
@@ -89,11 +101,12 @@ def test_cube128_forms_agree(c3):
         assert st.max_relres <= tol
         finals[name] = state.view(3 * k, g.N)[:2].cpu().numpy()
     ref = finals["fp64"]
-    for name in ("fp32", "bf16", "mf"):
+    for name in ("fp32", "bf16", "mf", "df"):
         for row in (0, 1):
             err = np.linalg.norm(finals[name][row] - ref[row]) / np.linalg.norm(ref[row])
             assert err < 1e-8, (name, row, err)
     assert np.array_equal(finals["fp32"], finals["fp32_host"])
+    assert np.array_equal(finals["df"], finals["df_host"])
     g.set_op_form("assembled")
     g.set_precond("fp64")
     g.set_tol(w.tol, 500)
