@@ -18,6 +18,7 @@ Contents and the passage each follows:
   * Stepper.step()                   -- eq. ho1-ho3 (Sec. 4), eq. 4a/4aup for k = 2
   * Stepper.init()                   -- initial high-order data (Sec. 3, after eq. 4aup)
   * theta_crit()                     -- stability limit from eq. charact at lambda = -1
+  * modal_response()                 -- the scheme on one mode (dispersion study, Sec. 6.2)
 Readings of passages the paper leaves silent or garbled are listed in the design doc.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py.
@@ -543,6 +544,20 @@ def scalar_amplification(k, rho, Theta, params=None):
         X[c, 0] = 1.0
         G[:, c] = st.step(X, 1.0)[:, 0]
     return G
+
+
+def modal_response(k, rho, lam, tau, n, U0=1.0, V0=0.0):
+    """The scheme on one mode u'' = -lam u (Sec. 3.1's modal problem): U_s for s = 0..n
+    after s steps of length tau from the initial data (U0, V0) (higher derivatives as
+    in Stepper.init). The dispersion and dissipation of the discrete scheme on that mode
+    (Sec. 6.2) are read off this series against cos(sqrt(lam) t)."""
+    st = Stepper(ScalarOps(lam), k, rho, tol=0.0)
+    X = st.init(np.array([float(U0)]), np.array([float(V0)]))
+    out = [float(X[0, 0])]
+    for _ in range(n):
+        X = st.step(X, tau)
+        out.append(float(X[0, 0]))
+    return np.array(out)
 
 
 def exact_semidiscrete(Md, Kd, U0, V0, t):

@@ -610,3 +610,25 @@ def test_lanczos_lambda_max_equals_dense_eigenvalue(d, nel, p, amp):
     # a few steps already bound it from below
     lam5 = oracle.lambda_max_lanczos(ops, iters=5)
     assert lam5 <= ref * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("Omega", [0.1, 0.7, 1.4, 1.99])
+def test_modal_response_k1_rho1_is_central_difference(Omega):
+    """k = 1 at rho_inf = 1 is the central-difference scheme: with U0 = 1, V0 = 0 the first
+    step gives 1 - Omega^2/2 = cos(theta), and U_{s+1} = (2 - Omega^2) U_s - U_{s-1}
+    makes U_s = cos(s theta), theta = arccos(1 - Omega^2/2) (stable for Omega < 2)."""
+    lam = 3.7
+    tau = Omega / math.sqrt(lam)
+    U = oracle.modal_response(1, 1.0, lam, tau, 60)
+    theta = math.acos(1 - Omega ** 2 / 2)
+    assert np.allclose(U, np.cos(np.arange(61) * theta), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_modal_response_dissipation_follows_rho(k):
+    """At rho_inf = 1 nothing is damped; below it the response decays, the more the
+    smaller rho_inf, with the same frequency for every k to leading order."""
+    lam, tau, n = 1.0, 1.2, 400
+    amp = {rho: np.abs(oracle.modal_response(k, rho, lam, tau, n)[-40:]).max() for rho in (1.0, 0.5, 0.0)}
+    assert amp[1.0] > 0.99
+    assert amp[1.0] > amp[0.5] > amp[0.0]
