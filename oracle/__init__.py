@@ -18,7 +18,7 @@ Contents and the passage each follows:
   * Stepper.step()                   -- eq. ho1-ho3 (Sec. 4), eq. 4a/4aup for k = 2
   * Stepper.init()                   -- initial high-order data (Sec. 3, after eq. 4aup)
   * theta_crit()                     -- stability limit from eq. charact at lambda = -1
-  * modal_response()                 -- the scheme on one mode (dispersion study, Sec. 6.2)
+  * modal_response(), spectral_radius() -- the scheme on one mode (Sec. 6.2), stability diagram
 Readings of passages the paper leaves silent or garbled are listed in the design doc.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py.
@@ -544,6 +544,13 @@ def scalar_amplification(k, rho, Theta, params=None):
         X[c, 0] = 1.0
         G[:, c] = st.step(X, 1.0)[:, 0]
     return G
+
+
+def spectral_radius(k, rho, Omega):
+    """Spectral radius of one step's amplification matrix at Omega = tau sqrt(lam) (the
+    stability diagram of Sec. 3.2: below 1 up to the limit sqrt(Theta_crit), rho_inf at
+    the bifurcation point)."""
+    return float(max(abs(np.linalg.eigvals(scalar_amplification(k, rho, Omega * Omega)))))
 
 
 def modal_response(k, rho, lam, tau, n, U0=1.0, V0=0.0):
