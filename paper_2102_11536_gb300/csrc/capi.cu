@@ -494,8 +494,8 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
   return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
 }
 
-// The tensor-core kernels set dflag[1], the TMA-staged band product dflag[2], when an
-// mbarrier wait runs out.
+// The tensor-core kernels set dflag[1], the TMA-staged band product and the cooperative
+// split dflag[2], when an mbarrier or grid-barrier wait runs out.
 int check_tc_error(iga_handle* h) {
   const bool tc = h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16;
   const bool df = h->opt.op_form == IGA_OP_ASSEMBLED_DF;
@@ -505,6 +505,8 @@ int check_tc_error(iga_handle* h) {
   CK(cudaStreamSynchronize(h->stream));
   if (e[0] || e[1]) {
     CK(cudaMemsetAsync(h->dflag + 1, 0, 2 * sizeof(int), h->stream));
+    // a grid barrier that ran out may have left its arrival count behind: start afresh
+    if (e[1] && h->df_bar) CK(cudaMemsetAsync(h->df_bar, 0, 2 * sizeof(unsigned int), h->stream));
     return fail(h, IGA_ECUDA, e[0] ? "tensor-core mode product: mbarrier wait timed out"
                                    : "staged band product: mbarrier wait timed out");
   }
