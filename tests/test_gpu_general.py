@@ -46,7 +46,8 @@ def _gpu(w, G, damping=DAMP, forcing=True, t0=0.0, **kw):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-@pytest.mark.parametrize("form", [("matrix_free", "fp64"), ("assembled", "banded"), ("assembled", "banded32")])
+@pytest.mark.parametrize("form", [("matrix_free", "fp64"), ("assembled", "banded"), ("assembled", "banded32"),
+                                  ("assembled_df", "banded32")])
 @pytest.mark.parametrize("case", ["damped", "forced", "both"])
 def test_general_model_steps_match_oracle(k, form, case):
     w = W.small(d=3, nel=(5, 4, 4), p=3, amp=0.1, k=k, rho=0.5, init="random")
