@@ -647,3 +647,24 @@ def test_stability_diagram_is_independent_of_the_order(rho):
         assert r[0] <= 1 + 1e-9
         if rho == 1.0:
             assert abs(r[0] - 1) < 1e-9
+
+
+def test_thin_patch_is_the_1d_problem():
+    """The dispersion study's stand-in for (0, 1) (paper_2102_11536_gb300.dispersion): the
+    thin 2-D patch's generalised eigenvalues equal those of the 1-D B-spline
+    discretisation on (0, 1) (the oracle's univariate mass and stiffness, identity map)
+    up to the O(stretch^-2) shift, and the lowest ones are (j pi)^2 to the spline error."""
+    import scipy.linalg
+    from paper_2102_11536_gb300 import dispersion
+
+    nel, p = 24, 4
+    deg, knots, ctrl = dispersion.thin_patch_geometry(nel, p)
+    P = oracle.Patch(list(deg), knots, ctrl)
+    ops = oracle.Operators(P)
+    lam2 = scipy.linalg.eigh(P.band_to_dense(ops.K), P.band_to_dense(ops.M), eigvals_only=True)
+    q = oracle.Quad1D(p, knots[0], p + 1)
+    lam1 = scipy.linalg.eigh(q.stiffness_interior(), q.mass_interior(), eigvals_only=True)
+    assert len(lam1) == len(lam2)
+    assert np.max(np.abs(lam2 / lam1 - 1)) < 1e-9
+    for j in (1, 2, 3):
+        assert abs(lam1[j - 1] / (j * math.pi) ** 2 - 1) < 1e-8
