@@ -625,15 +625,18 @@ int assemble_band(iga_handle* h) {
 }
 
 // one band product y = A x in the handle's assembled form (FP64, or double-FP32 with
-// the split of x first); cls selects the matrix (IGA_PROF_BAND_MASS / _STIFF)
+// the split of x first -- unless presplit: the split copy already holds x, as the PCG
+// direction's producers leave it); cls selects the matrix (IGA_PROF_BAND_MASS / _STIFF)
 cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const int* active, const double* x,
-                        double* y, int threads, int nv, double* pq, int* npq) {
+                        double* y, int threads, int nv, double* pq, int* npq, bool presplit = false) {
   const bool mass = cls == IGA_PROF_BAND_MASS;
   if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
     float2* xs = h->df_xs + h->df_slack;
-    cudaError_t e =
-        launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar, h->dflag + 2);
-    if (e != cudaSuccess) return e;
+    if (!presplit) {
+      const cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part,
+                                            h->df_bar, h->dflag + 2);
+      if (e != cudaSuccess) return e;
+    }
     return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
                           (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
                           xs, h->df_E, x, y, h->N, threads, nv, pq, npq, h->dflag + 2, mass ? &h->tmM : &h->tmK);
@@ -643,23 +646,25 @@ cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const 
 }
 
 int apply_band(iga_handle* h, int cls, int nvec, const int* active, const double* x, double* y,
-               double* pq = nullptr, int* npq = nullptr) {
+               double* pq = nullptr, int* npq = nullptr, bool presplit = false) {
   const int nact = active ? h->cur_active : nvec;
   cudaEvent_t e = nullptr;
   CKS(prof_begin(h, cls, &e));
-  LK(launch_band(h, h->stream, cls, nvec, active, x, y, h->band_threads, h->band_nv, pq, npq));
+  LK(launch_band(h, h->stream, cls, nvec, active, x, y, h->band_threads, h->band_nv, pq, npq, presplit));
   CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
   return IGA_OK;
 }
 
 // y = M x; with pq, the assembled form also leaves per-block partials of x . y in pq
 // ([nvec][*npq]); *npq = 0 when they were not computed (matrix-free form).
+// presplit (double-FP32 form): the split copy of x is already in place
 int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
-            int* npq = nullptr) {
+            int* npq = nullptr, bool presplit = false) {
   if (npq) *npq = 0;
   if (is_assembled(h)) {
     CKS(assemble_band(h));
-    return apply_band(h, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq);
+    return apply_band(h, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq,
+                      presplit && h->opt.op_form == IGA_OP_ASSEMBLED_DF);
   }
   return apply_M_mf(h, nvec, active, x, y);
 }
@@ -723,6 +728,11 @@ int solve_prime(iga_handle* h, int nvec) {
     LK(launch_cg_start(s, nvec, h->partial, kRedBlocks, c));
   }
   LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
+  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // the first product's split, made here (see solve_iter_a)
+    CKS(assemble_band(h));
+    LK(launch_df_split(s, N, c.active, nvec, h->p, N, h->df_xs + h->df_slack, h->band_Np, h->df_E, h->df_part,
+                       h->df_bar, h->dflag + 2));
+  }
   return IGA_OK;
 }
 
@@ -734,7 +744,8 @@ int solve_iter_a(iga_handle* h, int nvec, double* x) {
   double* pA = h->partial;
   double* pB = h->partial + kMaxVec * kRedBlocks;
   int npq = 0;
-  CKS(apply_M(h, nvec, c.active, h->p, h->q, h->pq_part, &npq));
+  // double-FP32 form: p's split copy was made where p was (solve_prime, solve_iter_b)
+  CKS(apply_M(h, nvec, c.active, h->p, h->q, h->pq_part, &npq, true));
   if (npq > 0) {  // p.q came with the band product
     LK(launch_cg_alpha(s, nvec, h->pq_part, npq, c));
   } else {
@@ -766,6 +777,19 @@ int solve_iter_b(iga_handle* h, int nvec) {
     CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
     LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
     LK(launch_cg_beta(s, nvec, pA, pC, kRedBlocks, c, flexible ? 1 : 0));
+  }
+  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // p = z + beta p and its split for the next product, one launch
+    float2* xs = h->df_xs + h->df_slack;
+    cudaError_t e = launch_df_update_split(s, N, c.active, nvec, h->p, h->z, c.beta, N, xs, h->band_Np, h->df_E,
+                                           h->df_part, h->df_bar, h->dflag + 2);
+    if (e == cudaErrorNotSupported) {
+      cudaGetLastError();
+      LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
+      e = launch_df_split(s, N, c.active, nvec, h->p, N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar,
+                          h->dflag + 2);
+    }
+    LK(e);
+    return IGA_OK;
   }
   LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
   return IGA_OK;

@@ -252,6 +252,11 @@ cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const dou
 // barrier's bounded wait sets *err = 1 if it runs out, else two launches
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
                             float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err);
+// p = z + beta p (active systems, the PCG direction update) and the split of the new p in
+// one cooperative launch; cudaErrorNotSupported without cooperative launch (nothing done)
+cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
+                                   const double* z, const double* beta, long long vs, float2* xs, long long Np,
+                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err);
 // y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
 // pq / npq as in launch_band_spmv (x is the FP64 input, read only for pq)
 // 2-D tensor maps over a split band ([H][Np], boxes for the upper rows and the lower

@@ -140,12 +140,16 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
 
 // The two passes of a vector split in one cooperative launch (every block resident):
 // block maxima, a grid barrier, then every block reduces the maxima and splits its
-// grid-stride share. bar[0] counts arrivals, bar[1] is the barrier's generation; the
-// wait is bounded (err = 1 if it runs out; the results are then not to be used).
+// grid-stride share. With z (and beta), the first pass also forms the PCG direction
+// x = z + beta x (active systems; the same operation as k_cg_update_p) before taking
+// the maxima, and the second pass splits what the same thread wrote. bar[0] counts
+// arrivals, bar[1] is the barrier's generation; the wait is bounded (err = 1 if it runs
+// out; the results are then not to be used).
 constexpr long long kBarLimit = 1LL << 22;
 
 __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, const int* __restrict__ active,
-                                                       const double* __restrict__ x, long long vs,
+                                                       double* __restrict__ x, const double* __restrict__ z,
+                                                       const double* __restrict__ beta, long long vs,
                                                        unsigned long long* __restrict__ part,
                                                        float2* __restrict__ xs, long long xvs, int* __restrict__ Eout,
                                                        unsigned int* bar, int* err) {
@@ -153,9 +157,19 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
   const long long stride = (long long)G * blockDim.x;
   for (int v = 0; v < nvec; ++v) {
     unsigned long long m = 0;
-    if (!active || active[v])
-      for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        m = max(m, abs_bits(x[v * vs + i]));
+    if (!active || active[v]) {
+      if (z) {
+        const double b = beta[v];
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+          const double pn = fma(b, x[v * vs + i], z[v * vs + i]);
+          x[v * vs + i] = pn;
+          m = max(m, abs_bits(pn));
+        }
+      } else {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+          m = max(m, abs_bits(x[v * vs + i]));
+      }
+    }
     m = block_max(m);
     if (threadIdx.x == 0) part[(long long)v * G + blockIdx.x] = m;
   }
@@ -914,39 +928,56 @@ cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const dou
   return cudaGetLastError();
 }
 
+namespace {
+// the cooperative split (z: with the direction update x = z + beta x first); returns
+// cudaErrorNotSupported when the device has no cooperative launch
+cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nvec, double* x, const double* z,
+                          const double* beta, long long vs, float2* xs, long long Np, int* Ex,
+                          unsigned long long* part, unsigned int* bar, int* err) {
+  static int nsm[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && nsm[dev] == 0) {
+    int v = 0, coop = 0;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    nsm[dev] = coop ? v : -1;
+  }
+  const int sm = dev < 64 ? nsm[dev] : -1;
+  if (sm <= 0) return cudaErrorNotSupported;
+  const long long G = std::min<long long>(std::min<long long>(2LL * sm, kDfBlocks), std::max<long long>(1, (N + 255) / 256));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, z, beta, vs, part, xs, Np, Ex, bar, err);
+}
+}  // namespace
+
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
                             float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err) {
   if (bar && err) {  // one cooperative launch, two blocks per SM
-    static int nsm[64] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 64 && nsm[dev] == 0) {
-      int v = 0, coop = 0;
-      if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-      if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
-      nsm[dev] = coop ? v : -1;
-    }
-    const int sm = dev < 64 ? nsm[dev] : -1;
-    if (sm > 0) {
-      const long long G = std::min<long long>(std::min<long long>(2LL * sm, kDfBlocks), std::max<long long>(1, (N + 255) / 256));
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)G);
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = 0;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeCooperative;
-      at[0].val.cooperative = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, vs, part, xs, Np, Ex, bar, err);
-    }
+    const cudaError_t e = df_split_coop(s, N, active, nvec, const_cast<double*>(x), nullptr, nullptr, vs, xs, Np,
+                                        Ex, part, bar, err);
+    if (e != cudaErrorNotSupported) return e;
   }
   k_df_absmax<<<dim3(kDfBlocks, nvec), 256, 0, s>>>(N, active, x, vs, part);
   const unsigned gx = (unsigned)std::min<long long>((N + 255) / 256, 2 * kDfBlocks);
   k_df_split<<<dim3(gx, nvec), 256, 0, s>>>(N, kDfBlocks, active, x, vs, part, nullptr, xs, Np, Ex);
   return cudaGetLastError();
+}
+
+cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
+                                   const double* z, const double* beta, long long vs, float2* xs, long long Np,
+                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err) {
+  return df_split_coop(s, N, active, nvec, p, z, beta, vs, xs, Np, Ex, part, bar, err);
 }
 
 cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0,
