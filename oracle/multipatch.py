@@ -3,16 +3,20 @@
 
 Test infrastructure, like the rest of `oracle/`: only the tests use it.
 
-Scope: 2-D patches of one degree p in a row along direction 0, patch r glued to patch
-r+1 along its face i0 = m0 - 1 (the face i0 = 0 of patch r+1), both faces with the same
-knot vector in direction 1 and the same control points (Assumption ass:conformity);
-homogeneous Dirichlet conditions on the outer boundary.
+Scope: 2-D or 3-D patches glued face to face in any layout (rows, grids, L-shapes; any
+relative orientation of the parameter directions), each interface face shared by exactly
+two patches with the same knots and the same control points (Assumption ass:conformity);
+homogeneous Dirichlet conditions on every face that is not an interface.
 
-- Local functions of patch r: its tensor-product B-splines that do not lie on an outer
-  face (per direction a range of indices: 1..m-2, extended to 0 or m-1 where that face is
-  an interface).
-- Global functions: the local ones with the interface functions of both sides identified
-  (G^(r) of Sec. 5.1); global M and K are sums over the patches of their local matrices
+- Interfaces: a face of a patch is an interface when its control points are, as a set,
+  those of a face of another patch. Conformity makes the functions on the two faces equal
+  one by one, and each pair has coincident control points, so the gluing G^(r) of Sec. 5.1
+  is read off the control points: whatever the orientation of the two patches.
+- Local functions of patch r: its tensor-product B-splines that lie on no outer face (per
+  direction a range of indices: 1..m-2, extended to 0 or m-1 where that face is an
+  interface), so the local index set stays a tensor product.
+- Global functions: the local ones, the functions on interfaces identified through their
+  control points; global M and K are sums over the patches of their local matrices
   (integrals over the patch) scattered through G^(r).
 - Additive Schwarz (def:asp): P_ad^{-1} = sum_r R^(r)T P^(r)^{-1} R^(r), R^(r) the selection
   of patch r's global functions, P^(r) = D^(r)^{1/2} Dhat^(r)^{-1/2} Mhat^(r) Dhat^(r)^{-1/2}
@@ -23,81 +27,120 @@ homogeneous Dirichlet conditions on the outer boundary.
 """
 from __future__ import annotations
 
+import itertools
+
 import numpy as np
 import scipy.linalg
 
 from . import Quad1D
 
 
+def _tensor(tables):
+    """Kronecker product of per-direction tables with direction 0 fastest: tables[a] is
+    (Q_a, m_a); the result has row q_0 + Q_0 (q_1 + Q_1 q_2) and column i_0 + m_0 (i_1 + ...)."""
+    T = np.ones((1, 1))
+    for t in tables:
+        T = np.kron(t, T)
+    return T
+
+
 def patch_full_matrices(degrees, knots, ctrl, nq=None):
-    """Mass and stiffness matrices of one 2-D patch over ALL its tensor-product functions
-    (index j * m0 + i for function (i, j), direction 0 fastest), by Gauss quadrature
-    (nq points per element and direction, default p + 1) with the geometry of the control
-    net ctrl (shape (m0 m1, 2), direction 0 fastest): M = int N_a N_b |det J|,
-    K = int grad N_a . grad N_b |det J| (Sec. 2)."""
-    p0, p1 = degrees
-    nq = nq or max(p0, p1) + 1
-    q0, q1 = Quad1D(p0, knots[0], nq), Quad1D(p1, knots[1], nq)
-    B0, dB0 = q0.dense(), q0.dense(True)  # (Q0, m0)
-    B1, dB1 = q1.dense(), q1.dense(True)  # (Q1, m1)
-    m0, m1 = q0.m, q1.m
-    C = np.asarray(ctrl, dtype=np.float64).reshape(m1, m0, 2)
-    Cx, Cy = C[:, :, 0], C[:, :, 1]
-    # geometry at the points (q1, q0)
-    x_xi = B1 @ Cx @ dB0.T
-    x_eta = dB1 @ Cx @ B0.T
-    y_xi = B1 @ Cy @ dB0.T
-    y_eta = dB1 @ Cy @ B0.T
-    det = x_xi * y_eta - x_eta * y_xi
-    if np.min(det) <= 0:
-        raise ValueError("det DF <= 0 at a quadrature point")
-    w = np.outer(q1.qw, q0.qw) * det  # |det J| times the weights
-    # J^{-1} J^{-T} |det J|: with J = [[x_xi, x_eta], [y_xi, y_eta]],
-    # J^{-1} = [[y_eta, -x_eta], [-y_xi, x_xi]] / det
-    g00 = np.outer(q1.qw, q0.qw) * (y_eta ** 2 + x_eta ** 2) / det
-    g01 = np.outer(q1.qw, q0.qw) * (-(y_eta * y_xi) - (x_eta * x_xi)) / det
-    g11 = np.outer(q1.qw, q0.qw) * (y_xi ** 2 + x_xi ** 2) / det
-    M = np.einsum("ab,aj,bi,al,bk->jilk", w, B1, B0, B1, B0, optimize=True).reshape(m0 * m1, m0 * m1)
-    # d/dxi of N_(i,j) = B1_j dB0_i, d/deta = dB1_j B0_i
-    K = (np.einsum("ab,aj,bi,al,bk->jilk", g00, B1, dB0, B1, dB0, optimize=True)
-         + np.einsum("ab,aj,bi,al,bk->jilk", g01, B1, dB0, dB1, B0, optimize=True)
-         + np.einsum("ab,aj,bi,al,bk->jilk", g01, dB1, B0, B1, dB0, optimize=True)
-         + np.einsum("ab,aj,bi,al,bk->jilk", g11, dB1, B0, dB1, B0, optimize=True)).reshape(m0 * m1, m0 * m1)
-    Mhat = (q0.dense().T @ (q0.qw[:, None] * q0.dense()), q1.dense().T @ (q1.qw[:, None] * q1.dense()))
-    return M, K, Mhat, (m0, m1)
+    """Mass and stiffness matrices of one patch over ALL its tensor-product functions (index
+    i_0 + m_0 (i_1 + m_1 i_2), direction 0 fastest), by Gauss quadrature (nq points per
+    element and direction, default max p + 1) with the geometry of the control net ctrl
+    (shape (prod m, d), same order): M = int N_a N_b |det J|, K = int grad N_a . grad N_b
+    |det J| (Sec. 2), with grad = J^{-T} grad_xi. Also the univariate parametric mass
+    matrices over all functions and the counts m."""
+    d = len(degrees)
+    nq = nq or max(degrees) + 1
+    quads = [Quad1D(p, kn, nq) for p, kn in zip(degrees, knots)]
+    m = [q.m for q in quads]
+    B = _tensor([q.dense() for q in quads])  # (Q, N) values at the tensor points
+    dB = [_tensor([q.dense(c == a) for c, q in enumerate(quads)]) for a in range(d)]
+    w = _tensor([q.qw[:, None] for q in quads])[:, 0]
+    P = np.asarray(ctrl, dtype=np.float64).reshape(-1, d)
+    J = np.stack([dB[a] @ P for a in range(d)], axis=2)  # J[q, c, a] = d x_c / d xi_a
+    det = np.linalg.det(J)
+    if not (np.all(det > 0) or np.all(det < 0)):
+        raise ValueError("det DF vanishes or changes sign in the patch")
+    Jinv = np.linalg.inv(J)  # Jinv[q, a, c] = d xi_a / d x_c
+    G = Jinv @ np.transpose(Jinv, (0, 2, 1))  # G[q, a, b] = grad xi_a . grad xi_b
+    wd = w * np.abs(det)
+    M = B.T @ (wd[:, None] * B)
+    K = sum(dB[a].T @ ((wd * G[:, a, b])[:, None] * dB[b]) for a in range(d) for b in range(d))
+    Mhat = [q.dense().T @ (q.qw[:, None] * q.dense()) for q in quads]
+    return M, K, Mhat, m
+
+
+def _key(pt):
+    return tuple(np.round(np.asarray(pt, dtype=np.float64), 10) + 0.0)
+
+
+def _face_flat(m, a, side):
+    """Flat indices (direction 0 fastest) of the functions on the face i_a = 0 (side 0) or
+    i_a = m_a - 1 (side 1)."""
+    rng = [range(n) for n in m]
+    rng[a] = [0] if side == 0 else [m[a] - 1]
+    return [_flat(ix, m) for ix in itertools.product(*reversed(rng))]
+
+
+def _flat(ix_rev, m):
+    """Flat index of the multi-index given last direction first."""
+    f = 0
+    for i, n in zip(ix_rev, reversed(m)):
+        f = f * n + i
+    return f
 
 
 class GluedPatches:
-    """Patches in a row along direction 0, glued conformingly (see the module docstring)."""
+    """Conforming patches glued face to face (see the module docstring)."""
 
     def __init__(self, patches, nq=None):
-        """patches: list of (degrees, knots, ctrl), patch r's face i0 = m0 - 1 glued to the
-        face i0 = 0 of patch r + 1."""
+        """patches: list of (degrees, knots, ctrl)."""
         self.P = len(patches)
-        self.local = []  # per patch: kept ranges, global ids of the kept functions, matrices
+        self.d = len(patches[0][0])
+        d = self.d
+        full = []
+        for deg, knots, ctrl in patches:
+            M, K, Mhat, m = patch_full_matrices(deg, knots, ctrl, nq)
+            full.append((M, K, Mhat, m, np.asarray(ctrl, dtype=np.float64).reshape(-1, d)))
+        # interface faces: equal control-point sets on two different patches
+        owners = {}
+        for r, (_, _, _, m, pts) in enumerate(full):
+            for a in range(d):
+                for side in (0, 1):
+                    fk = frozenset(_key(pts[f]) for f in _face_flat(m, a, side))
+                    owners.setdefault(fk, []).append((r, a, side))
+        self.interfaces = []
+        iface = set()
+        for fk, own in owners.items():
+            if len(own) > 2 or (len(own) == 2 and own[0][0] == own[1][0]):
+                raise ValueError("a face is shared by more than two patch faces: not conforming")
+            if len(own) == 2:
+                self.interfaces.append(tuple(own))
+                iface.update(own)
+        self.local = []
         gid = {}
         nglob = 0
-        for r, (deg, knots, ctrl) in enumerate(patches):
-            M, K, Mhat, (m0, m1) = patch_full_matrices(deg, knots, ctrl, nq)
-            lo0 = 0 if r > 0 else 1
-            hi0 = m0 - 1 if r < self.P - 1 else m0 - 2
-            lo1, hi1 = 1, m1 - 2
-            ids = []
-            for j in range(lo1, hi1 + 1):
-                for i in range(lo0, hi0 + 1):
-                    key = (r, i, j)
-                    if r > 0 and i == 0:  # the left patch's face i0 = m0 - 1, same j
-                        key = (r - 1, self.local[r - 1]["m"][0] - 1, j)
-                    if key not in gid:
-                        gid[key] = nglob
-                        nglob += 1
-                    ids.append(gid[key])
-            keep = [j * m0 + i for j in range(lo1, hi1 + 1) for i in range(lo0, hi0 + 1)]
-            Ml, Kl = M[np.ix_(keep, keep)], K[np.ix_(keep, keep)]
-            Mh0 = Mhat[0][lo0:hi0 + 1, lo0:hi0 + 1]
-            Mh1 = Mhat[1][lo1:hi1 + 1, lo1:hi1 + 1]
-            self.local.append({"m": (m0, m1), "ids": np.array(ids), "M": Ml, "K": Kl, "Mhat": (Mh0, Mh1),
-                               "n": (hi0 - lo0 + 1, hi1 - lo1 + 1)})
+        for r, (M, K, Mhat, m, pts) in enumerate(full):
+            lo = [0 if (r, a, 0) in iface else 1 for a in range(d)]
+            hi = [m[a] - 1 if (r, a, 1) in iface else m[a] - 2 for a in range(d)]
+            keep, ids = [], []
+            for ix_rev in itertools.product(*[range(lo[a], hi[a] + 1) for a in reversed(range(d))]):
+                f = _flat(ix_rev, m)
+                ix = ix_rev[::-1]
+                on_iface = any((ix[a] == 0 and (r, a, 0) in iface) or (ix[a] == m[a] - 1 and (r, a, 1) in iface)
+                               for a in range(d))
+                key = ("iface", _key(pts[f])) if on_iface else ("own", r, f)
+                if key not in gid:
+                    gid[key] = nglob
+                    nglob += 1
+                keep.append(f)
+                ids.append(gid[key])
+            n = [hi[a] - lo[a] + 1 for a in range(d)]
+            self.local.append({"m": m, "lo": lo, "n": n, "ids": np.array(ids),
+                               "M": M[np.ix_(keep, keep)], "K": K[np.ix_(keep, keep)],
+                               "Mhat": [Mhat[a][lo[a]:hi[a] + 1, lo[a]:hi[a] + 1] for a in range(d)]})
         self.N = nglob
         self.M = np.zeros((nglob, nglob))
         self.K = np.zeros((nglob, nglob))
@@ -112,18 +155,21 @@ class GluedPatches:
         self.n_adj = int(self.mult.max())
         # local preconditioners P^(r): Cholesky factors of the univariate Mhat, the scalings
         for loc in self.local:
-            Mh0, Mh1 = loc["Mhat"]
-            loc["cho"] = (scipy.linalg.cho_factor(Mh0), scipy.linalg.cho_factor(Mh1))
-            dhat = np.kron(np.diag(Mh1), np.diag(Mh0))  # direction 0 fastest
+            loc["cho"] = [scipy.linalg.cho_factor(Mh) for Mh in loc["Mhat"]]
+            dhat = _tensor([np.diag(Mh)[:, None] for Mh in loc["Mhat"]])[:, 0]
             loc["scale"] = np.sqrt(dhat / np.diag(loc["M"]))  # D^(r)^{-1/2} Dhat^(r)^{1/2}
 
     def local_Pinv(self, r, v):
-        """P^(r)^{-1} v = D^{-1/2} Dhat^{1/2} (Mhat_1 (x) Mhat_0)^{-1} Dhat^{1/2} D^{-1/2} v."""
+        """P^(r)^{-1} v = D^{-1/2} Dhat^{1/2} (Mhat_{d-1} (x) ... (x) Mhat_0)^{-1} Dhat^{1/2} D^{-1/2} v."""
         loc = self.local[r]
-        n0, n1 = loc["n"]
-        t = (loc["scale"] * v).reshape(n1, n0)
-        t = scipy.linalg.cho_solve(loc["cho"][0], t.T).T  # direction 0
-        t = scipy.linalg.cho_solve(loc["cho"][1], t)  # direction 1
+        d = self.d
+        t = (loc["scale"] * v).reshape(list(reversed(loc["n"])))  # array axis d-1-a is direction a
+        for a in range(d):
+            ax = d - 1 - a
+            u = np.moveaxis(t, ax, 0)
+            sh = u.shape
+            u = scipy.linalg.cho_solve(loc["cho"][a], u.reshape(sh[0], -1)).reshape(sh)
+            t = np.moveaxis(u, 0, ax)
         return loc["scale"] * t.reshape(-1)
 
     # Operators-like interface (oracle.pcg, oracle.Stepper)
@@ -144,27 +190,61 @@ class GluedPatches:
         return np.column_stack([self.apply_Pinv(e) for e in np.eye(self.N)])
 
 
-def row_of_patches(npatch, nel, p, amp=0.0):
-    """npatch unit-square patches side by side along x ([r, r+1] x [0, 1]), nel x nel
-    elements of degree p each, control points at the Greville abscissae moved by the
-    smooth map (x, y) -> (x + amp sin(pi x / npatch) sin(pi y), y + amp sin(pi x / npatch)
-    sin(pi y)); interface control points coincide, so the patches are conforming."""
-    def knots_(n):
-        return np.array([0.0] * (p + 1) + [i / n for i in range(1, n)] + [1.0] * (p + 1))
+def open_knots(nel, p):
+    """Open uniform knot vector on [0, 1] with nel elements (maximal regularity C^{p-1})."""
+    return np.array([0.0] * (p + 1) + [i / nel for i in range(1, nel)] + [1.0] * (p + 1))
 
-    def greville(kn):
-        m = len(kn) - p - 1
-        return np.array([kn[i + 1:i + p + 1].mean() for i in range(m)])
 
-    kx = ky = knots_(nel)
-    gx, gy = greville(kx), greville(ky)
+def greville(knots, p):
+    m = len(knots) - p - 1
+    return np.array([knots[i + 1:i + p + 1].mean() for i in range(m)])
+
+
+def grid_of_patches(shape, nel, p, amp=0.0):
+    """Unit patches [r_0, r_0 + 1] x ... on a grid of shape[a] patches per direction (d =
+    len(shape)), patch index r_0 + shape_0 (r_1 + shape_1 r_2); nel elements of degree p per
+    direction each, control points at the Greville abscissae, every coordinate moved by the
+    smooth b(X) = amp prod_a sin(pi X_a / shape_a). Neighbouring patches have the same
+    control points on their common face, so the patches are conforming."""
+    d = len(shape)
+    kn = open_knots(nel, p)
+    g = greville(kn, p)
     out = []
-    for r in range(npatch):
+    for r_rev in itertools.product(*[range(s) for s in reversed(shape)]):
+        r = r_rev[::-1]
         pts = []
-        for y in gy:
-            for x in gx:
-                X = r + x
-                b = amp * np.sin(np.pi * X / npatch) * np.sin(np.pi * y)
-                pts.append((X + b, y + b))
-        out.append(((p, p), [kx, ky], np.array(pts)))
+        for ix_rev in itertools.product(*[range(len(g))] * d):
+            X = np.array([r[a] + g[ix_rev[d - 1 - a]] for a in range(d)])
+            b = amp
+            for a in range(d):
+                b = b * np.sin(np.pi * X[a] / shape[a])
+            pts.append(X + b)
+        out.append(((p,) * d, [kn] * d, np.array(pts)))
     return out
+
+
+def row_of_patches(npatch, nel, p, amp=0.0):
+    """npatch unit-square patches side by side along x ([r, r+1] x [0, 1])."""
+    return grid_of_patches((npatch, 1), nel, p, amp)
+
+
+def l_shape(nel, p, amp=0.0):
+    """Three unit squares forming an L: the 2 x 2 grid without its patch at [1, 2] x [1, 2]."""
+    return [pt for r, pt in enumerate(grid_of_patches((2, 2), nel, p, amp)) if r != 3]
+
+
+def reorient(patch, perm=None, flip=()):
+    """The same patch with its parameter directions renamed and reversed: new direction a is
+    the old direction perm[a], reversed if a is in flip. The geometry, the space and the
+    matrices (up to the order of the functions) are unchanged."""
+    degrees, knots, ctrl = patch
+    d = len(degrees)
+    perm = list(perm) if perm is not None else list(range(d))
+    m = [len(kn) - p - 1 for p, kn in zip(degrees, knots)]
+    net = np.asarray(ctrl, dtype=np.float64).reshape(list(reversed(m)) + [d])
+    net = np.transpose(net, [d - 1 - perm[a] for a in reversed(range(d))] + [d])
+    kn2 = [np.asarray(knots[perm[a]], dtype=np.float64) for a in range(d)]
+    for a in flip:
+        net = np.flip(net, axis=d - 1 - a)
+        kn2[a] = (kn2[a][0] + kn2[a][-1]) - kn2[a][::-1]
+    return tuple(degrees[perm[a]] for a in range(d)), kn2, np.ascontiguousarray(net).reshape(-1, d)

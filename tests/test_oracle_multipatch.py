@@ -13,20 +13,23 @@ import oracle
 from oracle import multipatch as mp
 
 
-@pytest.mark.parametrize("p", [2, 3])
-def test_patch_assembly_equals_the_c_oracle_on_interior_functions(p):
-    deg, knots, ctrl = mp.row_of_patches(1, 5, p, amp=0.12)[0]
-    M, K, _, (m0, m1) = mp.patch_full_matrices(deg, knots, ctrl)
+@pytest.mark.parametrize("shape,nel,p", [((1, 1), 5, 2), ((1, 1), 5, 3), ((1, 1, 1), 3, 2)])
+def test_patch_assembly_equals_the_c_oracle_on_interior_functions(shape, nel, p):
+    deg, knots, ctrl = mp.grid_of_patches(shape, nel, p, amp=0.12)[0]
+    M, K, _, m = mp.patch_full_matrices(deg, knots, ctrl)
     P = oracle.Patch(list(deg), knots, ctrl)
     ops = oracle.Operators(P)
-    inner = [j * m0 + i for j in range(1, m1 - 1) for i in range(1, m0 - 1)]
+    rng = [range(1, n - 1) for n in m] + [range(1)] * (3 - len(m))
+    m3 = list(m) + [1] * (3 - len(m))
+    inner = [i0 + m3[0] * (i1 + m3[1] * i2) for i2 in rng[2] for i1 in rng[1] for i0 in rng[0]]
     Md, Kd = P.band_to_dense(ops.M), P.band_to_dense(ops.K)
     assert np.abs(M[np.ix_(inner, inner)] - Md).max() <= 1e-13 * np.abs(Md).max()
     assert np.abs(K[np.ix_(inner, inner)] - Kd).max() <= 1e-13 * np.abs(Kd).max()
 
 
-def test_one_patch_schwarz_is_the_single_patch_preconditioner():
-    pat = mp.row_of_patches(1, 6, 3, amp=0.1)[0]
+@pytest.mark.parametrize("shape,nel,p", [((1, 1), 6, 3), ((1, 1, 1), 4, 2)])
+def test_one_patch_schwarz_is_the_single_patch_preconditioner(shape, nel, p):
+    pat = mp.grid_of_patches(shape, nel, p, amp=0.1)[0]
     g = mp.GluedPatches([pat])
     pre = oracle.Preconditioner(oracle.Patch(list(pat[0]), pat[1], pat[2]))
     r = np.random.default_rng(0).standard_normal(g.N)
@@ -34,24 +37,27 @@ def test_one_patch_schwarz_is_the_single_patch_preconditioner():
     assert np.abs(z1 - z2).max() <= 1e-12 * np.abs(z2).max()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
-def test_glued_patches_equal_one_patch_with_a_p_fold_knot(p):
-    """Two unit patches glued along x = 1 span the C^0 space of one patch on [0, 2] x [0, 1]
-    whose knot vector repeats the middle knot p times; with the affine geometries the
-    global M and K are that patch's up to the order of the functions, so the spectra of
-    M and of the pencil (K, M) coincide."""
-    nel = 4
-    g = mp.GluedPatches(mp.row_of_patches(2, nel, p, amp=0.0))
-    kx = np.array([0.0] * (p + 1) + [i / (2 * nel) for i in range(1, nel)] + [0.5] * p
-                  + [0.5 + i / (2 * nel) for i in range(1, nel)] + [1.0] * (p + 1))
-    ky = np.array([0.0] * (p + 1) + [i / nel for i in range(1, nel)] + [1.0] * (p + 1))
+def _pfold_patch(shape, nel, p):
+    """One patch on [0, shape_0] x ... whose knot vector in direction a joins shape_a blocks
+    of nel uniform elements with the knots between blocks repeated p times (C^0 there); the
+    affine geometry x_a = shape_a xi_a (control points at the Greville abscissae)."""
+    kns = []
+    for s in shape:
+        inner = []
+        for b in range(s):
+            inner += [(b + i / nel) / s for i in range(1, nel)]
+            if b < s - 1:
+                inner += [(b + 1) / s] * p
+        kns.append(np.array([0.0] * (p + 1) + inner + [1.0] * (p + 1)))
+    g = [mp.greville(kn, p) * s for kn, s in zip(kns, shape)]
+    d = len(shape)
+    import itertools
+    ctrl = np.array([[g[a][ix[d - 1 - a]] for a in range(d)]
+                     for ix in itertools.product(*[range(len(gg)) for gg in reversed(g)])])
+    return oracle.Patch([p] * d, kns, ctrl)
 
-    def greville(kn):
-        m = len(kn) - p - 1
-        return np.array([kn[i + 1:i + p + 1].mean() for i in range(m)])
 
-    ctrl = np.array([(2 * x, y) for y in greville(ky) for x in greville(kx)])
-    P = oracle.Patch([p, p], [kx, ky], ctrl)
+def _same_spectra(g, P):
     ops = oracle.Operators(P)
     Md, Kd = P.band_to_dense(ops.M), P.band_to_dense(ops.K)
     assert P.N == g.N
@@ -61,33 +67,79 @@ def test_glued_patches_equal_one_patch_with_a_p_fold_knot(p):
     assert np.allclose(scipy.linalg.eigh(g.K, g.M, eigvals_only=True), ev, rtol=1e-9, atol=0)
 
 
-def test_schwarz_conditioning_is_bounded_independently_of_h():
+@pytest.mark.parametrize("shape,nel,p", [((2, 1), 4, 1), ((2, 1), 4, 2), ((2, 1), 4, 3), ((2, 2), 3, 2),
+                                         ((3, 2), 2, 3), ((2, 1, 1), 2, 2), ((2, 2, 2), 2, 2)])
+def test_glued_patches_equal_one_patch_with_p_fold_knots(shape, nel, p):
+    """A grid of unit patches glued face to face spans the C^0 space of one patch on the
+    union whose knot vectors repeat the knots between patches p times; with the affine
+    geometries the global M and K are that patch's up to the order of the functions, so the
+    spectra of M and of the pencil (K, M) coincide. The grids of 2 x 2 and 2 x 2 x 2 patches
+    share functions among 4 and 8 patches."""
+    g = mp.GluedPatches(mp.grid_of_patches(shape, nel, p, amp=0.0))
+    _same_spectra(g, _pfold_patch(shape, nel, p))
+    assert g.n_adj == 2 ** sum(1 for s in shape if s > 1)
+
+
+@pytest.mark.parametrize("perm,flip", [((0, 1), (0,)), ((0, 1), (0, 1)), ((1, 0), ()), ((1, 0), (1,))])
+def test_numbering_is_independent_of_the_patches_orientation(perm, flip):
+    """Renaming or reversing the parameter directions of some patches leaves the glued space,
+    hence the spectra of M and of (K, M), unchanged (reversal makes det DF < 0)."""
+    base = mp.grid_of_patches((2, 2), 3, 2, amp=0.1)
+    g0 = mp.GluedPatches(base)
+    g1 = mp.GluedPatches([mp.reorient(pt, perm, flip) if r in (1, 2) else pt for r, pt in enumerate(base)])
+    assert g1.N == g0.N and g1.n_adj == g0.n_adj == 4
+    assert np.allclose(np.sort(np.linalg.eigvalsh(g1.M)), np.sort(np.linalg.eigvalsh(g0.M)), rtol=1e-11, atol=0)
+    assert np.allclose(scipy.linalg.eigh(g1.K, g1.M, eigvals_only=True),
+                       scipy.linalg.eigh(g0.K, g0.M, eigvals_only=True), rtol=1e-9, atol=0)
+
+
+def test_reoriented_preconditioner_is_the_same_operator():
+    """P_ad^{-1} M has the same spectrum whatever the orientation of each patch: the local
+    Kronecker factors follow the renamed directions."""
+    base = mp.l_shape(4, 3, amp=0.1)
+    g0 = mp.GluedPatches(base)
+    g1 = mp.GluedPatches([mp.reorient(base[0], (1, 0), (0,)), base[1], mp.reorient(base[2], (0, 1), (0, 1))])
+    e0 = np.sort(np.real(np.linalg.eigvals(g0.dense_Pinv() @ g0.M)))
+    e1 = np.sort(np.real(np.linalg.eigvals(g1.dense_Pinv() @ g1.M)))
+    assert np.allclose(e1, e0, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("layout,sizes", [
+    (lambda n: mp.row_of_patches(2, n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: mp.row_of_patches(3, n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: mp.l_shape(n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: mp.grid_of_patches((2, 2), n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: mp.grid_of_patches((2, 2, 2), n, 2, amp=0.1), (2, 4)),
+])
+def test_schwarz_conditioning_is_bounded_independently_of_h(layout, sizes):
     """kappa(P_ad^{-1} M) <= C N_adj^2 with C independent of h and of the number of
-    patches (Sec. 5.4): a row of 2 or 3 deformed patches at 3, 6, 12 elements per side."""
-    kap = {}
-    for npch in (2, 3):
-        for nel in (3, 6, 12):
-            g = mp.GluedPatches(mp.row_of_patches(npch, nel, 3, amp=0.1))
-            assert g.n_adj == 2
-            ev = np.sort(np.real(np.linalg.eigvals(g.dense_Pinv() @ g.M)))
-            assert ev[0] > 0
-            kap[(npch, nel)] = ev[-1] / ev[0]
-    assert max(kap.values()) < 2.0 * 2 ** 2
-    assert max(kap.values()) / min(kap.values()) < 1.2
+    patches (Sec. 5.4): rows, an L, 2 x 2 and 2 x 2 x 2 grids of deformed patches (N_adj =
+    2, 2, 4, 8) at several mesh sizes; here C = 2 holds and kappa varies by < 10 % with h."""
+    kap = []
+    for nel in sizes:
+        g = mp.GluedPatches(layout(nel))
+        ev = np.sort(np.real(np.linalg.eigvals(g.dense_Pinv() @ g.M)))
+        assert ev[0] > 0
+        kap.append(ev[-1] / ev[0])
+        assert kap[-1] < 2.0 * g.n_adj ** 2, (nel, g.n_adj, kap)
+    assert max(kap) / min(kap) < 1.1, kap
 
 
-def test_pcg_with_schwarz_reaches_the_dense_solution():
-    g = mp.GluedPatches(mp.row_of_patches(3, 6, 3, amp=0.1))
+@pytest.mark.parametrize("layout", [lambda: mp.row_of_patches(3, 6, 3, amp=0.1), lambda: mp.l_shape(6, 3, amp=0.1),
+                                    lambda: mp.grid_of_patches((2, 2), 6, 3, amp=0.1)])
+def test_pcg_with_schwarz_reaches_the_dense_solution(layout):
+    g = mp.GluedPatches(layout())
     b = np.random.default_rng(3).standard_normal(g.N)
     x, it, rel = oracle.pcg(g.apply_M, g.apply_Pinv, b, tol=1e-12)
     xd = np.linalg.solve(g.M, b)
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
-    assert it <= 25
+    assert it <= 40
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_scheme_on_glued_patches_has_order_2k(k):
-    g = mp.GluedPatches(mp.row_of_patches(2, 4, 2, amp=0.1))
+@pytest.mark.parametrize("layout", [lambda: mp.row_of_patches(2, 4, 2, amp=0.1), lambda: mp.l_shape(3, 2, amp=0.1)])
+def test_scheme_on_glued_patches_has_order_2k(k, layout):
+    g = mp.GluedPatches(layout())
     rng = np.random.default_rng(5)
     lam = scipy.linalg.eigh(g.K, g.M, eigvals_only=True)
     U0 = rng.standard_normal(g.N)
