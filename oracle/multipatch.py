@@ -12,18 +12,24 @@ homogeneous Dirichlet conditions on every face that is not an interface.
   those of a face of another patch. Conformity makes the functions on the two faces equal
   one by one, and each pair has coincident control points, so the gluing G^(r) of Sec. 5.1
   is read off the control points: whatever the orientation of the two patches.
-- Local functions of patch r: its tensor-product B-splines that lie on no outer face (per
-  direction a range of indices: 1..m-2, extended to 0 or m-1 where that face is an
-  interface), so the local index set stays a tensor product.
-- Global functions: the local ones, the functions on interfaces identified through their
-  control points; global M and K are sums over the patches of their local matrices
-  (integrals over the patch) scattered through G^(r).
+- Global functions (def:mp_basis): the patches' tensor-product B-splines, those on
+  interfaces identified through their control points; a global function is kept unless one
+  of its copies lies on an outer face (it would not vanish on the Dirichlet boundary: at a
+  re-entrant corner that removes a function whose other copies lie on interfaces only).
+- Local functions of patch r: the copies of kept global functions. They lie in the tensor
+  range of indices 1..m-2 per direction, widened to 0 or m-1 where that face is an
+  interface; the range is the whole local set except next to re-entrant corners.
+- Global M and K are sums over the patches of their local matrices (integrals over the
+  patch) scattered through G^(r).
 - Additive Schwarz (def:asp): P_ad^{-1} = sum_r R^(r)T P^(r)^{-1} R^(r), R^(r) the selection
   of patch r's global functions, P^(r) = D^(r)^{1/2} Dhat^(r)^{-1/2} Mhat^(r) Dhat^(r)^{-1/2}
   D^(r)^{1/2} (def:loc_forms2) with Mhat^(r) the Kronecker product of the univariate
   parametric mass matrices over the local index ranges, Dhat^(r) its diagonal and D^(r) the
   diagonal of the patch's own mass matrix M^(r) (def:loc_matrices; the reading: the patch's
-  integral, not the global diagonal restricted to the patch).
+  integral, not the global diagonal restricted to the patch). Where the local set is the
+  tensor range minus some functions, P^(r)^{-1} is the Kronecker inverse over the range
+  with those entries zero on input and dropped on output (the reading that keeps the
+  Kronecker solve; a principal block of an SPD inverse, so still SPD).
 """
 from __future__ import annotations
 
@@ -119,26 +125,40 @@ class GluedPatches:
             if len(own) == 2:
                 self.interfaces.append(tuple(own))
                 iface.update(own)
+        # identification: every function of every patch gets a key (functions on interfaces:
+        # their control point); a key is outer when one of its copies lies on an outer face
+        keys, outer = [], set()
+        for r, (M, K, Mhat, m, pts) in enumerate(full):
+            kr = {}
+            for ix_rev in itertools.product(*[range(n) for n in reversed(m)]):
+                f = _flat(ix_rev, m)
+                ix = ix_rev[::-1]
+                faces = [(a, 0) for a in range(d) if ix[a] == 0] + [(a, 1) for a in range(d) if ix[a] == m[a] - 1]
+                on_iface = any((r, a, s_) in iface for a, s_ in faces)
+                kr[f] = ("iface", _key(pts[f])) if on_iface else ("own", r, f)
+                if any((r, a, s_) not in iface for a, s_ in faces):
+                    outer.add(kr[f])
+            keys.append(kr)
         self.local = []
         gid = {}
         nglob = 0
         for r, (M, K, Mhat, m, pts) in enumerate(full):
             lo = [0 if (r, a, 0) in iface else 1 for a in range(d)]
             hi = [m[a] - 1 if (r, a, 1) in iface else m[a] - 2 for a in range(d)]
-            keep, ids = [], []
+            keep, ids, mask = [], [], []
             for ix_rev in itertools.product(*[range(lo[a], hi[a] + 1) for a in reversed(range(d))]):
                 f = _flat(ix_rev, m)
-                ix = ix_rev[::-1]
-                on_iface = any((ix[a] == 0 and (r, a, 0) in iface) or (ix[a] == m[a] - 1 and (r, a, 1) in iface)
-                               for a in range(d))
-                key = ("iface", _key(pts[f])) if on_iface else ("own", r, f)
+                key = keys[r][f]
+                mask.append(key not in outer)
+                if key in outer:
+                    continue
                 if key not in gid:
                     gid[key] = nglob
                     nglob += 1
                 keep.append(f)
                 ids.append(gid[key])
             n = [hi[a] - lo[a] + 1 for a in range(d)]
-            self.local.append({"m": m, "lo": lo, "n": n, "ids": np.array(ids),
+            self.local.append({"m": m, "lo": lo, "n": n, "ids": np.array(ids, dtype=int), "mask": np.array(mask),
                                "M": M[np.ix_(keep, keep)], "K": K[np.ix_(keep, keep)],
                                "Mhat": [Mhat[a][lo[a]:hi[a] + 1, lo[a]:hi[a] + 1] for a in range(d)]})
         self.N = nglob
@@ -156,21 +176,23 @@ class GluedPatches:
         # local preconditioners P^(r): Cholesky factors of the univariate Mhat, the scalings
         for loc in self.local:
             loc["cho"] = [scipy.linalg.cho_factor(Mh) for Mh in loc["Mhat"]]
-            dhat = _tensor([np.diag(Mh)[:, None] for Mh in loc["Mhat"]])[:, 0]
+            dhat = _tensor([np.diag(Mh)[:, None] for Mh in loc["Mhat"]])[:, 0][loc["mask"]]
             loc["scale"] = np.sqrt(dhat / np.diag(loc["M"]))  # D^(r)^{-1/2} Dhat^(r)^{1/2}
 
     def local_Pinv(self, r, v):
         """P^(r)^{-1} v = D^{-1/2} Dhat^{1/2} (Mhat_{d-1} (x) ... (x) Mhat_0)^{-1} Dhat^{1/2} D^{-1/2} v."""
         loc = self.local[r]
         d = self.d
-        t = (loc["scale"] * v).reshape(list(reversed(loc["n"])))  # array axis d-1-a is direction a
+        t = np.zeros(loc["mask"].size)
+        t[loc["mask"]] = loc["scale"] * v
+        t = t.reshape(list(reversed(loc["n"])))  # array axis d-1-a is direction a
         for a in range(d):
             ax = d - 1 - a
             u = np.moveaxis(t, ax, 0)
             sh = u.shape
             u = scipy.linalg.cho_solve(loc["cho"][a], u.reshape(sh[0], -1)).reshape(sh)
             t = np.moveaxis(u, 0, ax)
-        return loc["scale"] * t.reshape(-1)
+        return loc["scale"] * t.reshape(-1)[loc["mask"]]
 
     # Operators-like interface (oracle.pcg, oracle.Stepper)
     def apply_M(self, x):

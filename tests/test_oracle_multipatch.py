@@ -80,6 +80,25 @@ def test_glued_patches_equal_one_patch_with_p_fold_knots(shape, nel, p):
     assert g.n_adj == 2 ** sum(1 for s in shape if s > 1)
 
 
+@pytest.mark.parametrize("p,amp", [(1, 0.0), (2, 0.1), (3, 0.1)])
+def test_l_shape_is_the_grid_without_the_functions_of_the_removed_patch(p, amp):
+    """The space of the L (the 2 x 2 grid without patch 3) with homogeneous Dirichlet data is
+    the subspace of the grid's space of the functions that vanish on patch 3: the grid's
+    global functions with no copy in patch 3 (def:mp_basis; local B-splines are linearly
+    independent). Their integrals over the grid and over the L agree, so the L's M and K
+    are principal blocks of the grid's. The function at the re-entrant corner touches the
+    removed patch and must not be in the L's space."""
+    grid = mp.grid_of_patches((2, 2), 3, p, amp=amp)
+    g4 = mp.GluedPatches(grid)
+    gl = mp.GluedPatches(grid[:3])
+    S = np.setdiff1d(np.arange(g4.N), g4.local[3]["ids"])
+    assert gl.N == S.size
+    ev = np.sort(np.linalg.eigvalsh(g4.M[np.ix_(S, S)]))
+    assert np.allclose(np.sort(np.linalg.eigvalsh(gl.M)), ev, rtol=1e-11, atol=1e-15 * ev[-1])
+    evk = scipy.linalg.eigh(g4.K[np.ix_(S, S)], g4.M[np.ix_(S, S)], eigvals_only=True)
+    assert np.allclose(scipy.linalg.eigh(gl.K, gl.M, eigvals_only=True), evk, rtol=1e-9, atol=0)
+
+
 @pytest.mark.parametrize("perm,flip", [((0, 1), (0,)), ((0, 1), (0, 1)), ((1, 0), ()), ((1, 0), (1,))])
 def test_numbering_is_independent_of_the_patches_orientation(perm, flip):
     """Renaming or reversing the parameter directions of some patches leaves the glued space,
@@ -114,14 +133,16 @@ def test_reoriented_preconditioner_is_the_same_operator():
 def test_schwarz_conditioning_is_bounded_independently_of_h(layout, sizes):
     """kappa(P_ad^{-1} M) <= C N_adj^2 with C independent of h and of the number of
     patches (Sec. 5.4): rows, an L, 2 x 2 and 2 x 2 x 2 grids of deformed patches (N_adj =
-    2, 2, 4, 8) at several mesh sizes; here C = 2 holds and kappa varies by < 10 % with h."""
+    2, 2, 4, 8) at several mesh sizes. The paper gives no value of C; measured, kappa / N_adj^2
+    lies between 1.3 and 2.4 here (the L's re-entrant corner gives the largest), and kappa
+    varies by < 10 % with h."""
     kap = []
     for nel in sizes:
         g = mp.GluedPatches(layout(nel))
         ev = np.sort(np.real(np.linalg.eigvals(g.dense_Pinv() @ g.M)))
         assert ev[0] > 0
         kap.append(ev[-1] / ev[0])
-        assert kap[-1] < 2.0 * g.n_adj ** 2, (nel, g.n_adj, kap)
+        assert kap[-1] < 2.5 * g.n_adj ** 2, (nel, g.n_adj, kap)
     assert max(kap) / min(kap) < 1.1, kap
 
 
@@ -147,7 +168,7 @@ def test_scheme_on_glued_patches_has_order_2k(k, layout):
     tau0 = 0.4 * math.sqrt(oracle.theta_crit(0.5) / lam[-1])
     T = 16 * tau0
     errs = []
-    for n in (16, 32):
+    for n in (32, 64):
         st = oracle.Stepper(g, k, 0.5, tol=1e-15)
         X = st.init(U0, V0)
         for _ in range(n):
