@@ -1,0 +1,61 @@
+/*
+ * iga_multipatch.h -- gluing of conforming B-spline patches (arXiv 2102.11536,
+ * Sec. 5.1: the global space V_h, Assumption ass:conformity, the numbering G^(r),
+ * def:mp_basis, def:n_l, def:N_patch) for the additive Schwarz mass preconditioner
+ * of Sec. 5.4 (def:asp). Host-only: no device memory is touched and no CUDA call is
+ * made, so it runs without a GPU. Status codes and iga_last_error as in iga_galpha.h.
+ */
+#ifndef IGA_MULTIPATCH_H
+#define IGA_MULTIPATCH_H
+
+#include "iga_galpha.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * iga_mp_layout -- interfaces, global numbering and local index boxes of patches that
+ * are glued face to face.
+ *   npatch   number of patches, >= 1.
+ *   dim      2 or 3, the same for every patch.
+ *   degree   host [npatch][dim], degrees 1..6.
+ *   nknots   host [npatch][dim], knot-vector lengths; m = nknots - degree - 1 >= 2.
+ *   knots    host [npatch * dim] pointers: patch r, direction a at knots[r * dim + a];
+ *            open, non-decreasing knot vectors.
+ *   ctrl     host [npatch] pointers to full control nets laid out as in iga_create
+ *            (prod_a m_a points, direction 0 fastest, dim coordinates per point).
+ *   tol      two control points coincide when every coordinate differs by at most
+ *            tol * max(1, largest absolute coordinate of all nets); 0 => 1e-10.
+ *   lo, hi   out, host [npatch][dim]: the box of each patch's local functions, full
+ *            indices, inclusive: 1 .. m-2, widened to 0 (to m-1) where the face
+ *            i_a = 0 (i_a = m-1) is an interface.
+ *   nglob    out: number of global functions (degrees of freedom).
+ *   n_adj    out: the largest number of patches sharing one global function (def:N_patch).
+ *   gid      out, host, or NULL: for patch 0, 1, ... in turn and every index of its box
+ *            (direction 0 fastest), the global id of that function, or -1 where the box
+ *            holds a copy of a function that lies on the Dirichlet boundary (only next to
+ *            a re-entrant corner). Ids run from 0 in order of first appearance in that
+ *            walk.
+ *   gid_len  length of gid, which must equal sum_r prod_a (hi - lo + 1); call once with
+ *            gid = NULL to obtain lo and hi.
+ * Rules. A face of one patch and a face of another form an interface when, under one
+ * orientation (a permutation of the face's directions and a reversal of each), their
+ * control points coincide one by one; the two faces must then have the same degrees and
+ * knots along the matched directions (Assumption ass:conformity). Every other face
+ * carries homogeneous Dirichlet conditions: a global function -- one set of identified
+ * copies, def:mp_basis -- is dropped when any copy lies on such a face.
+ * Errors: IGA_EINVAL (message by iga_last_error(NULL)) for bad sizes, knots or
+ * pointers, non-finite control points, a face that coincides with two other faces, an
+ * interface whose faces differ in degree or knots, or a wrong gid_len. The caller owns
+ * every buffer; nothing is retained.
+ */
+int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
+                  const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj,
+                  long long* gid, long long gid_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGA_MULTIPATCH_H */

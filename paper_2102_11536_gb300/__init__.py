@@ -109,6 +109,9 @@ def lib():
         "iga_batch_last_error": (ctypes.c_char_p, [H]),
         "iga_batch_step": (ctypes.c_int, [H, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
                                           ctypes.POINTER(Stats)]),
+        "iga_mp_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
+                                         ctypes.c_double, ip, ip, ctypes.POINTER(ctypes.c_longlong), ip,
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -128,7 +131,47 @@ def exported_symbols():
             "iga_ws_samples", "iga_ws_train", "iga_ws_init_params", "iga_ws_get_params", "iga_ws_set_params",
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
-            "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time"]
+            "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
+            "iga_mp_layout"]
+
+
+def multipatch_layout(patches, tol=0.0):
+    """Gluing of conforming patches (iga_mp_layout, host only; Sec. 5.1, def:mp_basis).
+    patches: list of (degrees, knots, ctrl) as for Patch. Returns a dict with "lo", "hi"
+    ((npatch, dim) index boxes, inclusive), "nglob", "n_adj" and "gid": per patch an integer
+    array shaped like its box (last direction first), the global id of each function or -1."""
+    import numpy as np
+    L = lib()
+    npatch = len(patches)
+    dim = len(patches[0][0])
+    deg = (ctypes.c_int * (npatch * dim))(*[int(p) for pt in patches for p in pt[0]])
+    nk = (ctypes.c_int * (npatch * dim))(*[len(kn) for pt in patches for kn in pt[1]])
+    kn_arrays = [np.ascontiguousarray(kn, dtype=np.float64) for pt in patches for kn in pt[1]]
+    ct_arrays = [np.ascontiguousarray(pt[2], dtype=np.float64).reshape(-1) for pt in patches]
+    dp = ctypes.POINTER(ctypes.c_double)
+    kn_ptr = (dp * len(kn_arrays))(*[a.ctypes.data_as(dp) for a in kn_arrays])
+    ct_ptr = (dp * npatch)(*[a.ctypes.data_as(dp) for a in ct_arrays])
+    lo = (ctypes.c_int * (npatch * dim))()
+    hi = (ctypes.c_int * (npatch * dim))()
+    nglob = ctypes.c_longlong()
+    nadj = ctypes.c_int()
+    rc = L.iga_mp_layout(npatch, dim, deg, nk, kn_ptr, ct_ptr, tol, lo, hi, ctypes.byref(nglob), ctypes.byref(nadj),
+                         None, 0)
+    if rc != OK:
+        raise IgaError(rc, "iga_mp_layout: " + L.iga_last_error(None).decode())
+    lo_a = np.array(lo[:], dtype=int).reshape(npatch, dim)
+    hi_a = np.array(hi[:], dtype=int).reshape(npatch, dim)
+    sizes = [int(np.prod(hi_a[r] - lo_a[r] + 1)) for r in range(npatch)]
+    gid = np.zeros(sum(sizes), dtype=np.int64)
+    rc = L.iga_mp_layout(npatch, dim, deg, nk, kn_ptr, ct_ptr, tol, lo, hi, ctypes.byref(nglob), ctypes.byref(nadj),
+                         gid.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), gid.size)
+    if rc != OK:
+        raise IgaError(rc, "iga_mp_layout: " + L.iga_last_error(None).decode())
+    out, w = [], 0
+    for r in range(npatch):
+        out.append(gid[w:w + sizes[r]].reshape(list(reversed((hi_a[r] - lo_a[r] + 1).tolist()))))
+        w += sizes[r]
+    return {"lo": lo_a, "hi": hi_a, "nglob": int(nglob.value), "n_adj": int(nadj.value), "gid": out}
 
 
 def fp64_fma_probe(device=0):

@@ -1521,6 +1521,14 @@ int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double
   return IGA_OK;
 }
 
+int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
+                  const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj,
+                  long long* gid, long long gid_len) {
+  std::string msg;
+  const int rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo, hi, nglob, n_adj, gid, gid_len, msg);
+  return rc == IGA_OK ? IGA_OK : fail(nullptr, rc, msg);
+}
+
 int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, double* state) {
   CKS(check_handle(h));
   if (k < 1 || k > kMaxK || !U0 || !V0 || !state) return fail(h, IGA_EINVAL, "bad arguments");

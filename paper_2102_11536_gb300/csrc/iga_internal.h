@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/iga_galpha.h"
+#include "../../include/iga_multipatch.h"
 
 namespace iga {
 
@@ -48,6 +49,10 @@ bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::
 bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<double>& L, std::vector<double>& dinv);
 // Largest eigenvalue of the symmetric tridiagonal matrix (diagonal a, off-diagonal b).
 double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b);
+// Gluing of conforming patches (host_multipatch.cpp); arguments as iga_mp_layout.
+int mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
+              const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj, long long* gid,
+              long long gid_len, std::string& err);
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).
 void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evec, std::vector<double>& eval);
 
