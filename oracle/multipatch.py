@@ -210,63 +210,3 @@ class GluedPatches:
 
     def dense_Pinv(self):
         return np.column_stack([self.apply_Pinv(e) for e in np.eye(self.N)])
-
-
-def open_knots(nel, p):
-    """Open uniform knot vector on [0, 1] with nel elements (maximal regularity C^{p-1})."""
-    return np.array([0.0] * (p + 1) + [i / nel for i in range(1, nel)] + [1.0] * (p + 1))
-
-
-def greville(knots, p):
-    m = len(knots) - p - 1
-    return np.array([knots[i + 1:i + p + 1].mean() for i in range(m)])
-
-
-def grid_of_patches(shape, nel, p, amp=0.0):
-    """Unit patches [r_0, r_0 + 1] x ... on a grid of shape[a] patches per direction (d =
-    len(shape)), patch index r_0 + shape_0 (r_1 + shape_1 r_2); nel elements of degree p per
-    direction each, control points at the Greville abscissae, every coordinate moved by the
-    smooth b(X) = amp prod_a sin(pi X_a / shape_a). Neighbouring patches have the same
-    control points on their common face, so the patches are conforming."""
-    d = len(shape)
-    kn = open_knots(nel, p)
-    g = greville(kn, p)
-    out = []
-    for r_rev in itertools.product(*[range(s) for s in reversed(shape)]):
-        r = r_rev[::-1]
-        pts = []
-        for ix_rev in itertools.product(*[range(len(g))] * d):
-            X = np.array([r[a] + g[ix_rev[d - 1 - a]] for a in range(d)])
-            b = amp
-            for a in range(d):
-                b = b * np.sin(np.pi * X[a] / shape[a])
-            pts.append(X + b)
-        out.append(((p,) * d, [kn] * d, np.array(pts)))
-    return out
-
-
-def row_of_patches(npatch, nel, p, amp=0.0):
-    """npatch unit-square patches side by side along x ([r, r+1] x [0, 1])."""
-    return grid_of_patches((npatch, 1), nel, p, amp)
-
-
-def l_shape(nel, p, amp=0.0):
-    """Three unit squares forming an L: the 2 x 2 grid without its patch at [1, 2] x [1, 2]."""
-    return [pt for r, pt in enumerate(grid_of_patches((2, 2), nel, p, amp)) if r != 3]
-
-
-def reorient(patch, perm=None, flip=()):
-    """The same patch with its parameter directions renamed and reversed: new direction a is
-    the old direction perm[a], reversed if a is in flip. The geometry, the space and the
-    matrices (up to the order of the functions) are unchanged."""
-    degrees, knots, ctrl = patch
-    d = len(degrees)
-    perm = list(perm) if perm is not None else list(range(d))
-    m = [len(kn) - p - 1 for p, kn in zip(degrees, knots)]
-    net = np.asarray(ctrl, dtype=np.float64).reshape(list(reversed(m)) + [d])
-    net = np.transpose(net, [d - 1 - perm[a] for a in reversed(range(d))] + [d])
-    kn2 = [np.asarray(knots[perm[a]], dtype=np.float64) for a in range(d)]
-    for a in flip:
-        net = np.flip(net, axis=d - 1 - a)
-        kn2[a] = (kn2[a][0] + kn2[a][-1]) - kn2[a][::-1]
-    return tuple(degrees[perm[a]] for a in range(d)), kn2, np.ascontiguousarray(net).reshape(-1, d)

@@ -7,6 +7,7 @@ import pytest
 
 import paper_2102_11536_gb300 as iga
 from oracle import multipatch as mp
+from workloads import multipatch as WM
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,20 +26,20 @@ def _oracle_boxes(g):
 
 
 LAYOUTS = {
-    "single": lambda: mp.grid_of_patches((1, 1), 4, 2, amp=0.1),
-    "row3": lambda: mp.row_of_patches(3, 3, 3, amp=0.1),
-    "grid2x2": lambda: mp.grid_of_patches((2, 2), 3, 2, amp=0.1),
-    "grid3x2": lambda: mp.grid_of_patches((3, 2), 2, 3, amp=0.05),
-    "L": lambda: mp.l_shape(3, 2, amp=0.1),
-    "L_p1": lambda: mp.l_shape(2, 1),
-    "grid2x2x2": lambda: mp.grid_of_patches((2, 2, 2), 2, 2, amp=0.1),
-    "row3d": lambda: mp.grid_of_patches((1, 1, 3), 2, 3, amp=0.1),
-    "reoriented2d": lambda: [mp.reorient(pt, *o) for pt, o in zip(mp.grid_of_patches((2, 2), 3, 2, amp=0.1),
+    "single": lambda: WM.grid_of_patches((1, 1), 4, 2, amp=0.1),
+    "row3": lambda: WM.row_of_patches(3, 3, 3, amp=0.1),
+    "grid2x2": lambda: WM.grid_of_patches((2, 2), 3, 2, amp=0.1),
+    "grid3x2": lambda: WM.grid_of_patches((3, 2), 2, 3, amp=0.05),
+    "L": lambda: WM.l_shape(3, 2, amp=0.1),
+    "L_p1": lambda: WM.l_shape(2, 1),
+    "grid2x2x2": lambda: WM.grid_of_patches((2, 2, 2), 2, 2, amp=0.1),
+    "row3d": lambda: WM.grid_of_patches((1, 1, 3), 2, 3, amp=0.1),
+    "reoriented2d": lambda: [WM.reorient(pt, *o) for pt, o in zip(WM.grid_of_patches((2, 2), 3, 2, amp=0.1),
                                                                     [((0, 1), ()), ((1, 0), (0,)), ((0, 1), (0, 1)),
                                                                      ((1, 0), ())])],
-    "reorientedL": lambda: [mp.reorient(pt, *o) for pt, o in zip(mp.l_shape(3, 3, amp=0.1),
+    "reorientedL": lambda: [WM.reorient(pt, *o) for pt, o in zip(WM.l_shape(3, 3, amp=0.1),
                                                                    [((1, 0), (1,)), ((0, 1), (0,)), ((1, 0), (0, 1))])],
-    "reoriented3d": lambda: [mp.reorient(pt, *o) for pt, o in zip(mp.grid_of_patches((2, 2, 1), 2, 2, amp=0.1),
+    "reoriented3d": lambda: [WM.reorient(pt, *o) for pt, o in zip(WM.grid_of_patches((2, 2, 1), 2, 2, amp=0.1),
                                                                     [((0, 1, 2), ()), ((2, 0, 1), (1,)),
                                                                      ((1, 2, 0), (0, 2)), ((0, 2, 1), (0, 1, 2))])],
 }
@@ -60,7 +61,7 @@ def test_layout_matches_the_oracle(name):
 
 
 def test_re_entrant_corner_function_is_not_a_degree_of_freedom():
-    lay = iga.multipatch_layout(mp.l_shape(3, 2))
+    lay = iga.multipatch_layout(WM.l_shape(3, 2))
     # patch 0 ([0, 1]^2) has interfaces on both of its upper faces: its box reaches the
     # corner (1, 1), which lies on the boundary of the L
     assert lay["gid"][0][-1, -1] == -1
@@ -69,13 +70,13 @@ def test_re_entrant_corner_function_is_not_a_degree_of_freedom():
 
 
 def test_n_adj_counts_the_patches_at_a_vertex():
-    assert iga.multipatch_layout(mp.grid_of_patches((2, 2), 2, 2))["n_adj"] == 4
-    assert iga.multipatch_layout(mp.grid_of_patches((2, 2, 2), 2, 2))["n_adj"] == 8
-    assert iga.multipatch_layout(mp.grid_of_patches((3, 1), 2, 2))["n_adj"] == 2
+    assert iga.multipatch_layout(WM.grid_of_patches((2, 2), 2, 2))["n_adj"] == 4
+    assert iga.multipatch_layout(WM.grid_of_patches((2, 2, 2), 2, 2))["n_adj"] == 8
+    assert iga.multipatch_layout(WM.grid_of_patches((3, 1), 2, 2))["n_adj"] == 2
 
 
 def test_tolerance_identifies_nearly_equal_control_points():
-    patches = mp.row_of_patches(2, 3, 2, amp=0.1)
+    patches = WM.row_of_patches(2, 3, 2, amp=0.1)
     deg, kn, ctrl = patches[1]
     patches[1] = (deg, kn, ctrl + 1e-13)
     assert iga.multipatch_layout(patches)["n_adj"] == 2
@@ -86,7 +87,7 @@ def test_tolerance_identifies_nearly_equal_control_points():
 
 
 def test_non_conforming_knots_are_rejected():
-    patches = mp.row_of_patches(2, 3, 2, amp=0.0)
+    patches = WM.row_of_patches(2, 3, 2, amp=0.0)
     deg, kn, ctrl = patches[1]
     kn2 = [kn[0], np.array([0, 0, 0, 0.25, 2 / 3, 1, 1, 1.0])]  # same count, other interior knots
     patches[1] = (deg, kn2, ctrl)
@@ -96,7 +97,7 @@ def test_non_conforming_knots_are_rejected():
 
 
 def test_a_face_shared_by_three_patches_is_rejected():
-    patches = mp.row_of_patches(2, 2, 2, amp=0.0)
+    patches = WM.row_of_patches(2, 2, 2, amp=0.0)
     with pytest.raises(iga.IgaError) as e:
         iga.multipatch_layout(patches + [patches[1]])
     assert "more than one other face" in str(e.value)
@@ -104,7 +105,7 @@ def test_a_face_shared_by_three_patches_is_rejected():
 
 @pytest.mark.parametrize("bad", ["degree", "knots", "open", "nan"])
 def test_bad_arguments_are_rejected(bad):
-    patches = mp.row_of_patches(2, 2, 2, amp=0.0)
+    patches = WM.row_of_patches(2, 2, 2, amp=0.0)
     deg, kn, ctrl = patches[0]
     if bad == "degree":
         patches[0] = ((7, 2), kn, ctrl)

@@ -10,12 +10,14 @@ import pytest
 import scipy.linalg
 
 import oracle
+import workloads as W
 from oracle import multipatch as mp
+from workloads import multipatch as WM
 
 
 @pytest.mark.parametrize("shape,nel,p", [((1, 1), 5, 2), ((1, 1), 5, 3), ((1, 1, 1), 3, 2)])
 def test_patch_assembly_equals_the_c_oracle_on_interior_functions(shape, nel, p):
-    deg, knots, ctrl = mp.grid_of_patches(shape, nel, p, amp=0.12)[0]
+    deg, knots, ctrl = WM.grid_of_patches(shape, nel, p, amp=0.12)[0]
     M, K, _, m = mp.patch_full_matrices(deg, knots, ctrl)
     P = oracle.Patch(list(deg), knots, ctrl)
     ops = oracle.Operators(P)
@@ -29,7 +31,7 @@ def test_patch_assembly_equals_the_c_oracle_on_interior_functions(shape, nel, p)
 
 @pytest.mark.parametrize("shape,nel,p", [((1, 1), 6, 3), ((1, 1, 1), 4, 2)])
 def test_one_patch_schwarz_is_the_single_patch_preconditioner(shape, nel, p):
-    pat = mp.grid_of_patches(shape, nel, p, amp=0.1)[0]
+    pat = WM.grid_of_patches(shape, nel, p, amp=0.1)[0]
     g = mp.GluedPatches([pat])
     pre = oracle.Preconditioner(oracle.Patch(list(pat[0]), pat[1], pat[2]))
     r = np.random.default_rng(0).standard_normal(g.N)
@@ -49,7 +51,7 @@ def _pfold_patch(shape, nel, p):
             if b < s - 1:
                 inner += [(b + 1) / s] * p
         kns.append(np.array([0.0] * (p + 1) + inner + [1.0] * (p + 1)))
-    g = [mp.greville(kn, p) * s for kn, s in zip(kns, shape)]
+    g = [W.greville(kn, p) * s for kn, s in zip(kns, shape)]
     d = len(shape)
     import itertools
     ctrl = np.array([[g[a][ix[d - 1 - a]] for a in range(d)]
@@ -75,7 +77,7 @@ def test_glued_patches_equal_one_patch_with_p_fold_knots(shape, nel, p):
     geometries the global M and K are that patch's up to the order of the functions, so the
     spectra of M and of the pencil (K, M) coincide. The grids of 2 x 2 and 2 x 2 x 2 patches
     share functions among 4 and 8 patches."""
-    g = mp.GluedPatches(mp.grid_of_patches(shape, nel, p, amp=0.0))
+    g = mp.GluedPatches(WM.grid_of_patches(shape, nel, p, amp=0.0))
     _same_spectra(g, _pfold_patch(shape, nel, p))
     assert g.n_adj == 2 ** sum(1 for s in shape if s > 1)
 
@@ -88,7 +90,7 @@ def test_l_shape_is_the_grid_without_the_functions_of_the_removed_patch(p, amp):
     independent). Their integrals over the grid and over the L agree, so the L's M and K
     are principal blocks of the grid's. The function at the re-entrant corner touches the
     removed patch and must not be in the L's space."""
-    grid = mp.grid_of_patches((2, 2), 3, p, amp=amp)
+    grid = WM.grid_of_patches((2, 2), 3, p, amp=amp)
     g4 = mp.GluedPatches(grid)
     gl = mp.GluedPatches(grid[:3])
     S = np.setdiff1d(np.arange(g4.N), g4.local[3]["ids"])
@@ -103,9 +105,9 @@ def test_l_shape_is_the_grid_without_the_functions_of_the_removed_patch(p, amp):
 def test_numbering_is_independent_of_the_patches_orientation(perm, flip):
     """Renaming or reversing the parameter directions of some patches leaves the glued space,
     hence the spectra of M and of (K, M), unchanged (reversal makes det DF < 0)."""
-    base = mp.grid_of_patches((2, 2), 3, 2, amp=0.1)
+    base = WM.grid_of_patches((2, 2), 3, 2, amp=0.1)
     g0 = mp.GluedPatches(base)
-    g1 = mp.GluedPatches([mp.reorient(pt, perm, flip) if r in (1, 2) else pt for r, pt in enumerate(base)])
+    g1 = mp.GluedPatches([WM.reorient(pt, perm, flip) if r in (1, 2) else pt for r, pt in enumerate(base)])
     assert g1.N == g0.N and g1.n_adj == g0.n_adj == 4
     assert np.allclose(np.sort(np.linalg.eigvalsh(g1.M)), np.sort(np.linalg.eigvalsh(g0.M)), rtol=1e-11, atol=0)
     assert np.allclose(scipy.linalg.eigh(g1.K, g1.M, eigvals_only=True),
@@ -115,20 +117,20 @@ def test_numbering_is_independent_of_the_patches_orientation(perm, flip):
 def test_reoriented_preconditioner_is_the_same_operator():
     """P_ad^{-1} M has the same spectrum whatever the orientation of each patch: the local
     Kronecker factors follow the renamed directions."""
-    base = mp.l_shape(4, 3, amp=0.1)
+    base = WM.l_shape(4, 3, amp=0.1)
     g0 = mp.GluedPatches(base)
-    g1 = mp.GluedPatches([mp.reorient(base[0], (1, 0), (0,)), base[1], mp.reorient(base[2], (0, 1), (0, 1))])
+    g1 = mp.GluedPatches([WM.reorient(base[0], (1, 0), (0,)), base[1], WM.reorient(base[2], (0, 1), (0, 1))])
     e0 = np.sort(np.real(np.linalg.eigvals(g0.dense_Pinv() @ g0.M)))
     e1 = np.sort(np.real(np.linalg.eigvals(g1.dense_Pinv() @ g1.M)))
     assert np.allclose(e1, e0, rtol=1e-9, atol=0)
 
 
 @pytest.mark.parametrize("layout,sizes", [
-    (lambda n: mp.row_of_patches(2, n, 3, amp=0.1), (3, 6, 12)),
-    (lambda n: mp.row_of_patches(3, n, 3, amp=0.1), (3, 6, 12)),
-    (lambda n: mp.l_shape(n, 3, amp=0.1), (3, 6, 12)),
-    (lambda n: mp.grid_of_patches((2, 2), n, 3, amp=0.1), (3, 6, 12)),
-    (lambda n: mp.grid_of_patches((2, 2, 2), n, 2, amp=0.1), (2, 4)),
+    (lambda n: WM.row_of_patches(2, n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: WM.row_of_patches(3, n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: WM.l_shape(n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: WM.grid_of_patches((2, 2), n, 3, amp=0.1), (3, 6, 12)),
+    (lambda n: WM.grid_of_patches((2, 2, 2), n, 2, amp=0.1), (2, 4)),
 ])
 def test_schwarz_conditioning_is_bounded_independently_of_h(layout, sizes):
     """kappa(P_ad^{-1} M) <= C N_adj^2 with C independent of h and of the number of
@@ -146,8 +148,8 @@ def test_schwarz_conditioning_is_bounded_independently_of_h(layout, sizes):
     assert max(kap) / min(kap) < 1.1, kap
 
 
-@pytest.mark.parametrize("layout", [lambda: mp.row_of_patches(3, 6, 3, amp=0.1), lambda: mp.l_shape(6, 3, amp=0.1),
-                                    lambda: mp.grid_of_patches((2, 2), 6, 3, amp=0.1)])
+@pytest.mark.parametrize("layout", [lambda: WM.row_of_patches(3, 6, 3, amp=0.1), lambda: WM.l_shape(6, 3, amp=0.1),
+                                    lambda: WM.grid_of_patches((2, 2), 6, 3, amp=0.1)])
 def test_pcg_with_schwarz_reaches_the_dense_solution(layout):
     g = mp.GluedPatches(layout())
     b = np.random.default_rng(3).standard_normal(g.N)
@@ -158,7 +160,7 @@ def test_pcg_with_schwarz_reaches_the_dense_solution(layout):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-@pytest.mark.parametrize("layout", [lambda: mp.row_of_patches(2, 4, 2, amp=0.1), lambda: mp.l_shape(3, 2, amp=0.1)])
+@pytest.mark.parametrize("layout", [lambda: WM.row_of_patches(2, 4, 2, amp=0.1), lambda: WM.l_shape(3, 2, amp=0.1)])
 def test_scheme_on_glued_patches_has_order_2k(k, layout):
     g = mp.GluedPatches(layout())
     rng = np.random.default_rng(5)
