@@ -54,6 +54,38 @@ int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, con
                   const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj,
                   long long* gid, long long gid_len);
 
+/*
+ * iga_mp_create -- a system of conforming patches glued as iga_mp_layout describes (same
+ * arguments npatch .. tol), for the explicit generalized-alpha steps on V_h with the
+ * additive Schwarz mass preconditioner of Sec. 5.4.
+ *   opt   options as for iga_create (NULL => defaults), shared by every patch: op_form and
+ *         precond are the patches' forms (each local preconditioner P^(r) of def:loc_forms2
+ *         in that arithmetic); the learned guess is refused (IGA_EINVAL).
+ *   out   receives a handle that the iga_galpha.h entry points accept: vectors have length
+ *         nglob (iga_ndof) in the global numbering of iga_mp_layout, and
+ *           M = sum_r R^(r)T M^(r) R^(r),  K likewise,
+ *           P_ad^{-1} = sum_r R^(r)T P^(r)^{-1} R^(r)  (def:asp),
+ *         where M^(r), K^(r) are patch r's integrals over its box and R^(r) gathers the
+ *         box's global functions (zero at box entries that are not degrees of freedom;
+ *         their results are dropped). iga_apply_M / _K / _Pinv, iga_solve_M (PCG with
+ *         P_ad: plain for the FP64 local forms, flexible otherwise), iga_state_init,
+ *         iga_step, iga_step_host, iga_cfl, iga_set_damping / _forcing / _time /
+ *         _tol / _guess / _op_form / _precond / _band_config, iga_assemble, iga_ndof,
+ *         iga_last_error and iga_destroy work on it; the steps run the host-driven loop
+ *         (iga_set_graphs has no effect). iga_profile, iga_autotune, the iga_ws_*
+ *         calls, iga_apply_Pinv_noalloc and iga_batch_create refuse it (IGA_EINVAL).
+ * Each patch gets a handle over its index box (the interior functions widened to the
+ * interface faces), with its own geometry factors, diag(M^(r)) and Kronecker factors.
+ * Errors: those of iga_mp_layout and iga_create (the message of iga_last_error(NULL)
+ * names the patch); IGA_EINVAL if no function is a degree of freedom.
+ */
+int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
+                  const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out);
+
+/* iga_mp_info -- number of patches, N_adj and the summed box sizes of a multi-patch
+ * handle (any pointer may be NULL). IGA_EINVAL for a single-patch handle. Host only. */
+int iga_mp_info(const iga_handle* h, int* npatch, int* n_adj, long long* nloc);
+
 #ifdef __cplusplus
 }
 #endif

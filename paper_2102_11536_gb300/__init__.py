@@ -112,6 +112,9 @@ def lib():
         "iga_mp_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ip, ip, ctypes.POINTER(ctypes.c_longlong), ip,
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]),
+        "iga_mp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
+                                         ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(H)]),
+        "iga_mp_info": (ctypes.c_int, [H, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -132,7 +135,7 @@ def exported_symbols():
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
-            "iga_mp_layout"]
+            "iga_mp_layout", "iga_mp_create", "iga_mp_info"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -498,6 +501,46 @@ class Patch:
                   "iga_step_host")
         return st
 
+
+
+class MultiPatch(Patch):
+    """Conforming patches glued face to face as one system on the GPU (iga_mp_create; Sec. 5.1,
+    5.4): vectors have length N in the global numbering of multipatch_layout, M and K are
+    the sums of the patches' matrices, apply_Pinv is the additive Schwarz preconditioner
+    (def:asp), and the step, solve and CFL calls of Patch work on it (host-driven loop).
+    patches: list of (degrees, knots, ctrl) as for Patch; the options are shared."""
+
+    def __init__(self, patches, tol_glue=0.0, nquad=0, tol=1e-10, max_iter=500, precond="fp64",
+                 op_form="matrix_free", guess="zero", device=0, stream="current"):
+        import numpy as np
+        L = lib()
+        npatch = len(patches)
+        self.d = len(patches[0][0])
+        opt = Options()
+        L.iga_options_default(ctypes.byref(opt))
+        opt.nquad, opt.tol, opt.max_iter = nquad, tol, max_iter
+        opt.precond, opt.op_form, opt.guess = PRECONDS[precond], OP_FORMS[op_form], GUESSES[guess]
+        opt.device = device
+        opt.stream = _default_stream() if stream == "current" else stream
+        dp = ctypes.POINTER(ctypes.c_double)
+        deg = (ctypes.c_int * (npatch * self.d))(*[int(p) for pt in patches for p in pt[0]])
+        self._knots = [np.ascontiguousarray(kn, dtype=np.float64) for pt in patches for kn in pt[1]]
+        nk = (ctypes.c_int * (npatch * self.d))(*[len(kn) for kn in self._knots])
+        kp = (dp * len(self._knots))(*[kn.ctypes.data_as(dp) for kn in self._knots])
+        self._ctrl = [np.ascontiguousarray(pt[2], dtype=np.float64).reshape(-1) for pt in patches]
+        cp = (dp * npatch)(*[c.ctypes.data_as(dp) for c in self._ctrl])
+        h = ctypes.c_void_p()
+        rc = L.iga_mp_create(npatch, self.d, deg, nk, kp, cp, tol_glue, ctypes.byref(opt), ctypes.byref(h))
+        if rc != OK:
+            raise IgaError(rc, "iga_mp_create: " + L.iga_last_error(None).decode())
+        self.h = h
+        n = ctypes.c_longlong()
+        L.iga_ndof(h, ctypes.byref(n))
+        self.N = int(n.value)
+        self.shape = None  # no single grid
+        npc, nadj, nloc = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        L.iga_mp_info(h, ctypes.byref(npc), ctypes.byref(nadj), ctypes.byref(nloc))
+        self.npatch, self.n_adj, self.nloc = int(npc.value), int(nadj.value), int(nloc.value)
 
 class Batch:
     """Independent patches advanced together, one CUDA graph launch per batch step

@@ -11,6 +11,8 @@
 
 using namespace iga;
 
+struct MpState;
+
 struct iga_handle {
   int dim = 0;
   iga_options opt{};
@@ -119,7 +121,25 @@ struct iga_handle {
   void* ws_work = nullptr;
   double *ws_loss = nullptr, *ws_lpart = nullptr;
   long long ws_loss_cap = 0;
+  // multi-patch system (iga_mp_create): M, K and the additive Schwarz preconditioner act
+  // through the patches' own handles; null for a single patch
+  MpState* mp = nullptr;
   std::string err;
+};
+
+// A multi-patch system of conforming patches (Sec. 5.1, 5.4): one handle per patch over
+// its index box, and the maps between global and local vectors.
+struct MpState {
+  std::vector<iga_handle*> patch;
+  std::vector<long long> off, nr;  // first entry and size of each patch's box
+  long long nloc = 0;              // sum of the box sizes
+  int n_adj = 0;
+  int op_form = IGA_OP_MATRIX_FREE, precond = IGA_PREC_FP64;  // the patches' forms
+  long long *d_gid = nullptr, *d_off = nullptr, *d_nr = nullptr, *d_crow = nullptr, *d_cent = nullptr;
+  int* d_epatch = nullptr;
+  MpMaps maps;
+  double *xl = nullptr, *yl = nullptr;  // [vec_cap][nloc] local inputs and results
+  int vec_cap = 0;
 };
 
 namespace {
@@ -497,6 +517,15 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
 // The tensor-core kernels set dflag[1], the TMA-staged band product and the cooperative
 // split dflag[2], when an mbarrier or grid-barrier wait runs out.
 int check_tc_error(iga_handle* h) {
+  if (h->mp) {
+    for (size_t r = 0; r < h->mp->patch.size(); ++r) {
+      iga_handle* p = h->mp->patch[r];
+      p->stream = h->stream;
+      const int rc = check_tc_error(p);
+      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+    }
+    return IGA_OK;
+  }
   const bool tc = h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16;
   const bool df = h->opt.op_form == IGA_OP_ASSEMBLED_DF;
   if (!tc && !df) return IGA_OK;
@@ -658,9 +687,12 @@ int apply_band(iga_handle* h, int cls, int nvec, const int* active, const double
 // y = M x; with pq, the assembled form also leaves per-block partials of x . y in pq
 // ([nvec][*npq]); *npq = 0 when they were not computed (matrix-free form).
 // presplit (double-FP32 form): the split copy of x is already in place
+int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double* x, double* y);
+
 int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
             int* npq = nullptr, bool presplit = false) {
   if (npq) *npq = 0;
+  if (h->mp) return mp_apply(h, 0, nvec, active, x, y);
   if (is_assembled(h)) {
     CKS(assemble_band(h));
     return apply_band(h, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq,
@@ -669,6 +701,7 @@ int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double*
   return apply_M_mf(h, nvec, active, x, y);
 }
 int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
+  if (h->mp) return mp_apply(h, 1, nvec, active, x, y);
   if (is_assembled(h)) {
     CKS(assemble_band(h));
     return apply_band(h, IGA_PROF_BAND_STIFF, nvec, active, x, y);
@@ -677,6 +710,10 @@ int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double*
 }
 int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* rzp = nullptr,
                int* nrz = nullptr) {
+  if (h->mp) {
+    if (nrz) *nrz = 0;
+    return mp_apply(h, 2, nvec, active, r, z);
+  }
   const int nact = active ? h->cur_active : nvec;
   double modes = 0.0;  // sum_a n_a: one mode product costs 2 n_a flops per entry, done twice
   for (int a = 0; a < h->dim; ++a) modes += h->n[a];
@@ -685,6 +722,38 @@ int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, doub
   CKS(ensure_cg_ws(h, nvec));
   CKS(fd_apply(h, nvec, active, r, z, h->f1, h->f2, rzp, nrz));
   CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
+  return IGA_OK;
+}
+
+// Multi-patch operators (Sec. 5.1, 5.4): the global vectors are gathered into every
+// patch's box (zero where a box entry is no degree of freedom), the patch's own operator
+// acts on its box -- M^(r), K^(r), or the local preconditioner P^(r)^{-1}
+// (def:loc_forms2) -- and the local results are summed into the global vector:
+// which = 0: M = sum_r R^(r)T M^(r) R^(r); 1: K likewise; 2: P_ad^{-1} (def:asp).
+int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double* x, double* y) {
+  MpState& mp = *h->mp;
+  if (nvec > mp.vec_cap) {
+    drop_step_graph(h);
+    CKS(dalloc(h, &mp.xl, (size_t)nvec * mp.nloc));
+    CKS(dalloc(h, &mp.yl, (size_t)nvec * mp.nloc));
+    mp.vec_cap = nvec;
+  }
+  cudaStream_t s = h->stream;
+  LK(launch_mp_gather(s, mp.maps, nvec, active, x, mp.xl));
+  for (size_t r = 0; r < mp.patch.size(); ++r) {
+    iga_handle* p = mp.patch[r];
+    p->stream = s;
+    p->cur_active = h->cur_active;
+    const long long l0 = p->nlaunch;
+    double* xr = mp.xl + nvec * mp.off[r];
+    double* yr = mp.yl + nvec * mp.off[r];
+    const int rc = which == 0   ? apply_M(p, nvec, active, xr, yr)
+                   : which == 1 ? apply_K(p, nvec, active, xr, yr)
+                                : apply_Pinv(p, nvec, active, xr, yr);
+    h->nlaunch += p->nlaunch - l0;
+    if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+  }
+  LK(launch_mp_scatter(s, mp.maps, nvec, active, mp.yl, y));
   return IGA_OK;
 }
 
@@ -852,6 +921,13 @@ int check_handle(iga_handle* h) {
   h->err.clear();
   cudaError_t e = cudaSetDevice(h->opt.device);
   if (e != cudaSuccess) return fail(h, IGA_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return IGA_OK;
+}
+
+// Entry points that need one patch's grid (the learned guess, profiling, tuning, the
+// allocation-free preconditioner, batches) refuse a multi-patch handle.
+int single_patch(iga_handle* h, const char* what) {
+  if (h && h->mp) return fail(h, IGA_EINVAL, std::string(what) + " is not available on a multi-patch handle");
   return IGA_OK;
 }
 
@@ -1163,99 +1239,11 @@ int run_step_graph(iga_handle* h, double* state, int k, double rho, const StepCo
   return collect_graph_run(h, s, k, nsteps, sc.tau, stats);
 }
 
-}  // namespace
-
-namespace iga {
-
-int handle_device(iga_handle* h, int* device) {
-  CKS(check_handle(h));
-  *device = h->opt.device;
-  return IGA_OK;
-}
-
-int handle_fail(iga_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
-
-int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2) {
-  return fd_apply(h, nvec, nullptr, x, y, t1, t2);
-}
-
-}  // namespace iga
-
-// ===========================================================================
-// public API
-// ===========================================================================
-extern "C" {
-
-void iga_options_default(iga_options* opt) {
-  if (!opt) return;
-  opt->nquad = 0;
-  opt->tol = 1e-10;
-  opt->max_iter = 500;
-  opt->precond = IGA_PREC_FP64;
-  opt->op_form = IGA_OP_MATRIX_FREE;
-  opt->guess = IGA_GUESS_ZERO;
-  opt->device = 0;
-  opt->stream = nullptr;
-}
-
-const char* iga_status_string(int status) {
-  switch (status) {
-    case IGA_OK: return "ok";
-    case IGA_EINVAL: return "invalid argument";
-    case IGA_ENOMEM: return "out of memory";
-    case IGA_ECUDA: return "CUDA error";
-    case IGA_ENOT_CONVERGED: return "PCG not converged";
-    case IGA_ENUMERIC: return "numerical breakdown";
-    case IGA_EUNSTABLE: return "unstable time step";
-    case IGA_EGEOMETRY: return "invalid geometry (det DF <= 0)";
-    default: return "unknown status";
-  }
-}
-
-const char* iga_last_error(const iga_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
-
-void iga_destroy(iga_handle* h) {
-  if (!h) return;
-  cudaSetDevice(h->opt.device);
-  for (int a = 0; a < 3; ++a) {
-    DirDev& d = h->dd[a];
-    dfree(d.val); dfree(d.der); dfree(d.sq); dfree(d.val32); dfree(d.der32);
-    dfree(d.qfirst); dfree(d.flo); dfree(d.fhi); dfree(d.qw);
-    dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32); dfree(d.chol); dfree(d.cdinv); dfree(d.chol32); dfree(d.cdinv32);
-    for (int t = 0; t < 2; ++t)
-      if (d.Btc[t]) { cudaFree(d.Btc[t]); d.Btc[t] = nullptr; }
-    for (int t = 0; t < 2; ++t)
-      if (d.Btc16[t]) { cudaFree(d.Btc16[t]); d.Btc16[t] = nullptr; }
-  }
-  dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
-  dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
-  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
-  dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
-  dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
-  dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
-  dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
-  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
-  if (h->h_nactive) cudaFreeHost(h->h_nactive);
-  for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
-  for (auto e : h->prof_pool) cudaEventDestroy(e);
-  dfree(h->Yneg); dfree(h->rhs); dfree(h->Z); dfree(h->Z2); dfree(h->dstate);
-  drop_step_graph(h);
-  if (h->gs) cudaStreamDestroy(h->gs);
-  if (h->gbody) cudaStreamDestroy(h->gbody);
-  if (h->ev_in) cudaEventDestroy(h->ev_in);
-  if (h->ev_out) cudaEventDestroy(h->ev_out);
-  dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_init); dfree(h->d_stat);
-  dfree(h->fG); dfree(h->Yv); dfree(h->MYv); dfree(h->d_time);
-  dfree(h->ws_theta); dfree(h->ws_m); dfree(h->ws_v); dfree(h->ws_grad);
-  dfree(h->ws_E); dfree(h->ws_B1); dfree(h->ws_B2); dfree(h->ws_sc); dfree(h->ws_part);
-  dfree(h->ws_x); dfree(h->ws_act); dfree(h->ws_sx); dfree(h->ws_st);
-  dfree(h->ws_y); dfree(h->ws_dy); dfree(h->ws_loss); dfree(h->ws_lpart);
-  if (h->ws_work) cudaFree(h->ws_work);
-  delete h;
-}
-
-int iga_create(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
-               const iga_options* opt, iga_handle** out) {
+// One patch over the index box lo .. hi per direction (full indices; NULL: the interior
+// functions 1 .. m-2, iga_create). The operators see only the box's functions; the
+// geometry uses the whole control net.
+int create_handle(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
+                  const int* lo, const int* hi, const iga_options* opt, iga_handle** out) {
   g_create_err.clear();
   if (!out) return fail(nullptr, IGA_EINVAL, "out is NULL");
   *out = nullptr;
@@ -1277,7 +1265,8 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
   const int nq = h->opt.nquad > 0 ? h->opt.nquad : pmax + 1;
   std::string err;
   for (int a = 0; a < dim; ++a) {
-    if (!knots[a] || !build_tables(degree[a], nknots[a], knots[a], nq, h->tab[a], err)) {
+    if (!knots[a] || !build_tables(degree[a], nknots[a], knots[a], nq, h->tab[a], err, lo ? lo[a] : 1,
+                                   hi ? hi[a] : -1)) {
       delete h;
       return fail(nullptr, IGA_EINVAL, "direction " + std::to_string(a) + ": " + (knots[a] ? err : "NULL knots"));
     }
@@ -1316,7 +1305,8 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
       std::vector<float> U32(U.begin(), U.end()), l32(linv.begin(), linv.end());
       CKS(upload(h, &d.val, t.val)); CKS(upload(h, &d.der, t.der)); CKS(upload(h, &d.sq, sq));
       CKS(upload(h, &d.val32, v32)); CKS(upload(h, &d.der32, d32));
-      CKS(upload(h, &d.qfirst, t.qfirst)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
+      CKS(upload(h, &d.qfirst, t.qfirst_op)); CKS(upload(h, &d.flo, t.flo)); CKS(upload(h, &d.fhi, t.fhi));
+      if (t.lo != 1) CKS(upload(h, &d.qfirst_geo, t.qfirst));
       CKS(upload(h, &d.qw, t.qw));
       CKS(upload(h, &d.U64, U)); CKS(upload(h, &d.lam64, linv));
       CKS(upload(h, &d.chol, t.chol)); CKS(upload(h, &d.cdinv, t.cdinv));
@@ -1401,6 +1391,111 @@ int iga_create(int dim, const int* degree, const int* nknots, const double* cons
   return IGA_OK;
 }
 
+}  // namespace
+
+namespace iga {
+
+int handle_device(iga_handle* h, int* device) {
+  CKS(check_handle(h));
+  *device = h->opt.device;
+  return IGA_OK;
+}
+
+int handle_fail(iga_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
+
+int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2) {
+  CKS(single_patch(h, "iga_apply_Pinv_noalloc"));
+  return fd_apply(h, nvec, nullptr, x, y, t1, t2);
+}
+
+}  // namespace iga
+
+// ===========================================================================
+// public API
+// ===========================================================================
+extern "C" {
+
+void iga_options_default(iga_options* opt) {
+  if (!opt) return;
+  opt->nquad = 0;
+  opt->tol = 1e-10;
+  opt->max_iter = 500;
+  opt->precond = IGA_PREC_FP64;
+  opt->op_form = IGA_OP_MATRIX_FREE;
+  opt->guess = IGA_GUESS_ZERO;
+  opt->device = 0;
+  opt->stream = nullptr;
+}
+
+const char* iga_status_string(int status) {
+  switch (status) {
+    case IGA_OK: return "ok";
+    case IGA_EINVAL: return "invalid argument";
+    case IGA_ENOMEM: return "out of memory";
+    case IGA_ECUDA: return "CUDA error";
+    case IGA_ENOT_CONVERGED: return "PCG not converged";
+    case IGA_ENUMERIC: return "numerical breakdown";
+    case IGA_EUNSTABLE: return "unstable time step";
+    case IGA_EGEOMETRY: return "invalid geometry (det DF <= 0)";
+    default: return "unknown status";
+  }
+}
+
+const char* iga_last_error(const iga_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+void iga_destroy(iga_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->opt.device);
+  if (h->mp) {
+    MpState* mp = h->mp;
+    for (iga_handle* p : mp->patch) iga_destroy(p);
+    dfree(mp->d_gid); dfree(mp->d_off); dfree(mp->d_nr); dfree(mp->d_crow); dfree(mp->d_cent); dfree(mp->d_epatch);
+    dfree(mp->xl); dfree(mp->yl);
+    delete mp;
+    h->mp = nullptr;
+  }
+  for (int a = 0; a < 3; ++a) {
+    DirDev& d = h->dd[a];
+    dfree(d.val); dfree(d.der); dfree(d.sq); dfree(d.val32); dfree(d.der32);
+    dfree(d.qfirst); dfree(d.qfirst_geo); dfree(d.flo); dfree(d.fhi); dfree(d.qw);
+    dfree(d.U64); dfree(d.lam64); dfree(d.U32); dfree(d.lam32); dfree(d.chol); dfree(d.cdinv); dfree(d.chol32); dfree(d.cdinv32);
+    for (int t = 0; t < 2; ++t)
+      if (d.Btc[t]) { cudaFree(d.Btc[t]); d.Btc[t] = nullptr; }
+    for (int t = 0; t < 2; ++t)
+      if (d.Btc16[t]) { cudaFree(d.Btc16[t]); d.Btc16[t] = nullptr; }
+  }
+  dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
+  dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
+  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
+  dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
+  dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
+  dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
+  dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
+  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
+  if (h->h_nactive) cudaFreeHost(h->h_nactive);
+  for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
+  dfree(h->Yneg); dfree(h->rhs); dfree(h->Z); dfree(h->Z2); dfree(h->dstate);
+  drop_step_graph(h);
+  if (h->gs) cudaStreamDestroy(h->gs);
+  if (h->gbody) cudaStreamDestroy(h->gbody);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_init); dfree(h->d_stat);
+  dfree(h->fG); dfree(h->Yv); dfree(h->MYv); dfree(h->d_time);
+  dfree(h->ws_theta); dfree(h->ws_m); dfree(h->ws_v); dfree(h->ws_grad);
+  dfree(h->ws_E); dfree(h->ws_B1); dfree(h->ws_B2); dfree(h->ws_sc); dfree(h->ws_part);
+  dfree(h->ws_x); dfree(h->ws_act); dfree(h->ws_sx); dfree(h->ws_st);
+  dfree(h->ws_y); dfree(h->ws_dy); dfree(h->ws_loss); dfree(h->ws_lpart);
+  if (h->ws_work) cudaFree(h->ws_work);
+  delete h;
+}
+
+int iga_create(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
+               const iga_options* opt, iga_handle** out) {
+  return create_handle(dim, degree, nknots, knots, ctrl, nullptr, nullptr, opt, out);
+}
+
 int iga_ndof(const iga_handle* h, long long* ndof) {
   if (!h || !ndof) return IGA_EINVAL;
   *ndof = h->N;
@@ -1409,16 +1504,28 @@ int iga_ndof(const iga_handle* h, long long* ndof) {
 
 int iga_set_op_form(iga_handle* h, int op_form) {
   if (!h || op_form < 0 || op_form > IGA_OP_ASSEMBLED_DF) return IGA_EINVAL;
+  if (h->mp) {  // the patches' form; the composite dispatches through them
+    h->mp->op_form = op_form;
+    for (iga_handle* p : h->mp->patch) p->opt.op_form = op_form;
+    return IGA_OK;
+  }
   h->opt.op_form = op_form;
   return IGA_OK;
 }
 int iga_set_precond(iga_handle* h, int precond) {
   if (!h || precond < 0 || precond > IGA_PREC_BANDED32) return IGA_EINVAL;
+  if (h->mp) {  // the patches' local preconditioners; the composite's PCG follows their class
+    h->mp->precond = precond;
+    for (iga_handle* p : h->mp->patch) p->opt.precond = precond;
+    h->opt.precond = (precond == IGA_PREC_FP64 || precond == IGA_PREC_BANDED) ? IGA_PREC_FP64 : IGA_PREC_FP32;
+    return IGA_OK;
+  }
   h->opt.precond = precond;
   return IGA_OK;
 }
 int iga_set_guess(iga_handle* h, int guess) {
   if (!h || guess < 0 || guess > IGA_GUESS_LEARNED) return IGA_EINVAL;
+  if (h->mp && guess == IGA_GUESS_LEARNED) return fail(h, IGA_EINVAL, "the learned guess needs a single patch");
   h->opt.guess = guess;
   return IGA_OK;
 }
@@ -1474,7 +1581,7 @@ int iga_get_time(iga_handle* h, double* t) {
 
 int iga_set_graphs(iga_handle* h, int on) {
   if (!h) return IGA_EINVAL;
-  h->use_graphs = on != 0;
+  h->use_graphs = on != 0 && !h->mp;  // a multi-patch handle runs the host-driven loop
   return IGA_OK;
 }
 
@@ -1487,6 +1594,15 @@ int iga_set_tol(iga_handle* h, double tol, int max_iter) {
 
 int iga_assemble(iga_handle* h) {
   CKS(check_handle(h));
+  if (h->mp) {
+    for (size_t r = 0; r < h->mp->patch.size(); ++r) {
+      iga_handle* p = h->mp->patch[r];
+      p->stream = h->stream;
+      const int rc = assemble_band(p);
+      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+    }
+    return IGA_OK;
+  }
   return assemble_band(h);
 }
 
@@ -1527,6 +1643,141 @@ int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, con
   std::string msg;
   const int rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo, hi, nglob, n_adj, gid, gid_len, msg);
   return rc == IGA_OK ? IGA_OK : fail(nullptr, rc, msg);
+}
+
+int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
+                  const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, IGA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (npatch < 1 || (dim != 2 && dim != 3) || !degree || !nknots || !knots || !ctrl)
+    return fail(nullptr, IGA_EINVAL, "iga_mp_create: npatch >= 1, dim 2 or 3 and non-null arrays required");
+  iga_options o;
+  if (opt) o = *opt;
+  else iga_options_default(&o);
+  if (!(o.tol >= 0.0) || o.max_iter < 1 || o.precond < 0 || o.precond > IGA_PREC_BANDED32 || o.op_form < 0 ||
+      o.op_form > IGA_OP_ASSEMBLED_DF || o.guess < 0 || o.guess > IGA_GUESS_TAYLOR)
+    return fail(nullptr, IGA_EINVAL, "invalid options (the learned guess is not available on a multi-patch handle)");
+  // gluing: boxes first, then the global id of every box entry
+  std::vector<int> lo((size_t)npatch * dim), hi((size_t)npatch * dim);
+  long long nglob = 0;
+  int n_adj = 0;
+  std::string err;
+  int rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo.data(), hi.data(), &nglob, &n_adj, nullptr, 0,
+                     err);
+  if (rc != IGA_OK) return fail(nullptr, rc, err);
+  std::vector<long long> off(npatch), nr(npatch);
+  long long nloc = 0;
+  for (int r = 0; r < npatch; ++r) {
+    long long c = 1;
+    for (int a = 0; a < dim; ++a) c *= hi[(size_t)r * dim + a] - lo[(size_t)r * dim + a] + 1;
+    off[r] = nloc;
+    nr[r] = c;
+    nloc += c;
+  }
+  std::vector<long long> gid((size_t)nloc);
+  rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo.data(), hi.data(), &nglob, &n_adj, gid.data(),
+                 nloc, err);
+  if (rc != IGA_OK) return fail(nullptr, rc, err);
+  if (nglob < 1) return fail(nullptr, IGA_EINVAL, "iga_mp_create: no degrees of freedom");
+  // global -> entries (CSR, entries ascending) and entry -> patch
+  std::vector<long long> crow((size_t)nglob + 1, 0), cent;
+  std::vector<int> epatch((size_t)nloc);
+  for (int r = 0; r < npatch; ++r)
+    for (long long i = 0; i < nr[r]; ++i) epatch[(size_t)(off[r] + i)] = r;
+  for (long long e = 0; e < nloc; ++e)
+    if (gid[(size_t)e] >= 0) ++crow[(size_t)gid[(size_t)e] + 1];
+  for (long long g = 0; g < nglob; ++g) crow[(size_t)g + 1] += crow[(size_t)g];
+  cent.assign((size_t)crow[(size_t)nglob], 0);
+  {
+    std::vector<long long> fill(crow.begin(), crow.end() - 1);
+    for (long long e = 0; e < nloc; ++e)
+      if (gid[(size_t)e] >= 0) cent[(size_t)fill[(size_t)gid[(size_t)e]]++] = e;
+  }
+  iga_handle* h = new (std::nothrow) iga_handle();
+  if (!h) return fail(nullptr, IGA_ENOMEM, "host allocation failed");
+  h->mp = new (std::nothrow) MpState();
+  if (!h->mp) {
+    delete h;
+    return fail(nullptr, IGA_ENOMEM, "host allocation failed");
+  }
+  MpState& mp = *h->mp;
+  h->opt = o;
+  h->dim = dim;
+  h->stream = (cudaStream_t)o.stream;
+  h->N = nglob;
+  h->Qt = 1;
+  h->use_graphs = false;  // the host-driven loop: the patches' launches go to the stream of the call
+  // the composite runs the PCG of its preconditioner's class: plain CG for the FP64 forms,
+  // flexible CG otherwise; its own operator form is the dispatch through the patches
+  mp.op_form = o.op_form;
+  mp.precond = o.precond;
+  h->opt.op_form = IGA_OP_MATRIX_FREE;
+  h->opt.precond = (o.precond == IGA_PREC_FP64 || o.precond == IGA_PREC_BANDED) ? IGA_PREC_FP64 : IGA_PREC_FP32;
+  mp.off = off;
+  mp.nr = nr;
+  mp.nloc = nloc;
+  mp.n_adj = n_adj;
+  if (cudaSetDevice(o.device) != cudaSuccess) {
+    cudaGetLastError();
+    iga_destroy(h);
+    return fail(nullptr, IGA_ECUDA, "cudaSetDevice failed");
+  }
+  iga_options po = o;
+  po.guess = IGA_GUESS_ZERO;
+  for (int r = 0; r < npatch; ++r) {
+    iga_handle* p = nullptr;
+    rc = create_handle(dim, degree + (size_t)r * dim, nknots + (size_t)r * dim, knots + (size_t)r * dim, ctrl[r],
+                       lo.data() + (size_t)r * dim, hi.data() + (size_t)r * dim, &po, &p);
+    if (rc != IGA_OK) {
+      const std::string msg = "patch " + std::to_string(r) + ": " + g_create_err;
+      iga_destroy(h);
+      return fail(nullptr, rc, msg);
+    }
+    mp.patch.push_back(p);
+  }
+  auto setup = [&]() -> int {
+    CKS(upload(h, &mp.d_gid, gid));
+    CKS(upload(h, &mp.d_off, off));
+    CKS(upload(h, &mp.d_nr, nr));
+    CKS(upload(h, &mp.d_crow, crow));
+    CKS(upload(h, &mp.d_cent, cent));
+    CKS(upload(h, &mp.d_epatch, epatch));
+    mp.maps.nloc = nloc;
+    mp.maps.nglob = nglob;
+    mp.maps.gid = mp.d_gid;
+    mp.maps.epatch = mp.d_epatch;
+    mp.maps.off = mp.d_off;
+    mp.maps.nr = mp.d_nr;
+    mp.maps.crow = mp.d_crow;
+    mp.maps.cent = mp.d_cent;
+    CKS(dalloc(h, &h->dflag, 4));
+    CK(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 4, h->stream));
+    CKS(dalloc(h, &h->partial, (size_t)3 * kMaxVec * kRedBlocks));
+    CKS(dalloc(h, &h->cs.bb, kMaxVec)); CKS(dalloc(h, &h->cs.rz, kMaxVec)); CKS(dalloc(h, &h->cs.rr, kMaxVec)); CKS(dalloc(h, &h->cs.rr0, kMaxVec));
+    CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
+    CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
+    CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
+    CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
+    CK(cudaStreamSynchronize(h->stream));
+    return IGA_OK;
+  };
+  rc = setup();
+  if (rc != IGA_OK) {
+    const std::string msg = h->err;
+    iga_destroy(h);
+    return fail(nullptr, rc, msg);
+  }
+  *out = h;
+  return IGA_OK;
+}
+
+int iga_mp_info(const iga_handle* h, int* npatch, int* n_adj, long long* nloc) {
+  if (!h || !h->mp) return IGA_EINVAL;
+  if (npatch) *npatch = (int)h->mp->patch.size();
+  if (n_adj) *n_adj = h->mp->n_adj;
+  if (nloc) *nloc = h->mp->nloc;
+  return IGA_OK;
 }
 
 int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, double* state) {
@@ -1689,6 +1940,7 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
 
 int iga_profile(iga_handle* h, int kernel_class) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_profile"));
   if (kernel_class < IGA_PROF_OFF || kernel_class > IGA_PROF_BAND_STIFF) return fail(h, IGA_EINVAL, "bad kernel class");
   h->prof_class = kernel_class;
   return IGA_OK;
@@ -1825,6 +2077,7 @@ int net_args_ok(int n1, int n2, int n3, int nb) { return net_grid_ok(NetGrid{n1,
 
 int iga_ws_init_params(iga_handle* h, unsigned long long seed) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_init_params"));
   std::vector<float> th(IGA_NET_NPARAM, 0.0f);
   uint64_t st = seed;
   const double b1 = 1.0 / std::sqrt(81.0), b2 = 1.0 / std::sqrt(432.0);
@@ -1838,6 +2091,7 @@ int iga_ws_init_params(iga_handle* h, unsigned long long seed) {
 
 int iga_ws_set_params(iga_handle* h, const float* theta_host) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_set_params"));
   if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
   CKS(ws_upload_params(h, theta_host));
   h->ws_trained = true;
@@ -1847,6 +2101,7 @@ int iga_ws_set_params(iga_handle* h, const float* theta_host) {
 
 int iga_ws_get_params(iga_handle* h, float* theta_host) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_get_params"));
   if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
   if (!h->ws_params) return fail(h, IGA_EINVAL, "no parameters yet (iga_ws_init_params, iga_ws_train or iga_ws_set_params)");
   CK(cudaStreamSynchronize(h->stream));
@@ -1856,6 +2111,7 @@ int iga_ws_get_params(iga_handle* h, float* theta_host) {
 
 int iga_ws_collect(iga_handle* h, int capacity) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_collect"));
   if (capacity < 0) return fail(h, IGA_EINVAL, "capacity < 0");
   CK(cudaStreamSynchronize(h->stream));
   dfree(h->ws_sx);
@@ -1870,6 +2126,7 @@ int iga_ws_collect(iga_handle* h, int capacity) {
 
 int iga_ws_samples(iga_handle* h, int* count) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_samples"));
   if (!count) return fail(h, IGA_EINVAL, "count is NULL");
   *count = h->ws_count;
   return IGA_OK;
@@ -1877,6 +2134,7 @@ int iga_ws_samples(iga_handle* h, int* count) {
 
 int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* epoch_loss) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_train"));
   if (epochs < 1 || !(lr > 0.0)) return fail(h, IGA_EINVAL, "epochs < 1 or lr <= 0");
   if (h->ws_count < 1) return fail(h, IGA_EINVAL, "no recorded samples (iga_ws_collect, then iga_step)");
   const NetGrid g = net_grid_of(h);
@@ -1936,6 +2194,7 @@ int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, 
 int iga_ws_features(iga_handle* h, int k, const double* b, double* b1, double* b2, double* z1, double* z2,
                     unsigned short* x, double* E, double* scales) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_ws_features"));
   if (k < 1 || k > kMaxVec || !b || !b1 || !b2 || !z1 || !z2 || !x || !E || !scales)
     return fail(h, IGA_EINVAL, "bad arguments");
   CKS(ensure_ws_step(h, 1));
@@ -1989,6 +2248,11 @@ int iga_set_band_config(iga_handle* h, int threads, int nv) {
   CKS(check_handle(h));
   if (!(threads == 0 || threads == 64 || threads == 128 || threads == 256 || threads == 512) || nv < 0 || nv > 4)
     return fail(h, IGA_EINVAL, "threads must be 0, 64, 128, 256 or 512 and nv 0..4");
+  if (h->mp)
+    for (iga_handle* p : h->mp->patch) {
+      p->band_threads = threads;
+      p->band_nv = nv;
+    }
   h->band_threads = threads;
   h->band_nv = nv;
   drop_step_graph(h);
@@ -1997,6 +2261,7 @@ int iga_set_band_config(iga_handle* h, int threads, int nv) {
 
 int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
   CKS(check_handle(h));
+  CKS(single_patch(h, "iga_autotune"));
   if (nvec < 1 || nvec > kMaxVec || reps < 1) return fail(h, IGA_EINVAL, "need 1 <= nvec <= 8 and reps >= 1");
   CKS(assemble_band(h));
   CKS(ensure_cg_ws(h, nvec));
@@ -2161,7 +2426,7 @@ int iga_batch_create(int npatch, iga_handle* const* patches, iga_batch** out) {
   *out = nullptr;
   if (npatch < 1 || !patches) return IGA_EINVAL;
   for (int i = 0; i < npatch; ++i)
-    if (!patches[i] || patches[i]->opt.device != patches[0]->opt.device) return IGA_EINVAL;
+    if (!patches[i] || patches[i]->mp || patches[i]->opt.device != patches[0]->opt.device) return IGA_EINVAL;
   iga_batch* b = new (std::nothrow) iga_batch;
   if (!b) return IGA_ENOMEM;
   b->p.assign(patches, patches + npatch);

@@ -137,11 +137,13 @@ void bspline_span(int p, const double* U, int s, double x, double* val, double* 
   }
 }
 
-bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err) {
+bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err, int lo, int hi) {
   char buf[256];
   int m = nknots - p - 1;
   if (p < 1 || p > kMaxDeg) { snprintf(buf, sizeof buf, "degree %d outside [1, %d]", p, kMaxDeg); err = buf; return false; }
-  if (m < 3) { err = "fewer than 3 basis functions in a direction"; return false; }
+  if (hi < 0) hi = m - 2;
+  if (lo == 1 && hi == m - 2 && m < 3) { err = "fewer than 3 basis functions in a direction"; return false; }
+  if (lo < 0 || hi > m - 1 || hi < lo) { err = "function box outside 0 .. m-1 or empty"; return false; }
   if (nq < 1 || nq > 16) { err = "nquad outside [1, 16]"; return false; }
   for (int i = 0; i + 1 < nknots; ++i)
     if (!(U[i + 1] >= U[i])) { err = "knot vector not non-decreasing"; return false; }
@@ -153,7 +155,7 @@ bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::
     while (i + mult < m && U[i + mult] == U[i]) ++mult;
     if (mult > p) { err = "interior knot multiplicity above p"; return false; }
   }
-  t.p = p; t.m = m; t.n = m - 2; t.nq = nq;
+  t.p = p; t.m = m; t.n = hi - lo + 1; t.lo = lo; t.nq = nq;
   std::vector<double> gx(nq), gw(nq);
   gauss_legendre(nq, gx.data(), gw.data());
   std::vector<int> spans;
@@ -176,26 +178,29 @@ bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::
       bspline_span(p, U, s, x, &t.val[(size_t)q * P], &t.der[(size_t)q * P]);
     }
   }
-  // quadrature ranges of the interior functions (qfirst is non-decreasing in q)
+  // the operators' window start: the box index of the point's first function, plus one
+  t.qfirst_op.resize(t.Q);
+  for (int q = 0; q < t.Q; ++q) t.qfirst_op[q] = t.qfirst[q] - lo + 1;
+  // quadrature ranges of the box's functions (qfirst is non-decreasing in q)
   t.flo.assign(t.n, 0); t.fhi.assign(t.n, 0);
   for (int i = 0; i < t.n; ++i) {
-    int f = i + 1, lo = -1, hi = -1;
+    int f = i + lo, qlo = -1, qhi = -1;
     for (int q = 0; q < t.Q; ++q)
       if (t.qfirst[q] <= f && f <= t.qfirst[q] + p) {
-        if (lo < 0) lo = q;
-        hi = q + 1;
+        if (qlo < 0) qlo = q;
+        qhi = q + 1;
       }
-    if (lo < 0) { err = "interior function without quadrature support"; return false; }
-    t.flo[i] = lo; t.fhi[i] = hi;
+    if (qlo < 0) { err = "interior function without quadrature support"; return false; }
+    t.flo[i] = qlo; t.fhi[i] = qhi;
   }
-  // interior parametric mass matrix (one direction of def:matrices_1)
+  // parametric mass matrix over the box (one direction of def:matrices_1)
   t.mhat.assign((size_t)t.n * t.n, 0.0);
   for (int q = 0; q < t.Q; ++q)
     for (int a = 0; a < P; ++a) {
-      int i = t.qfirst[q] + a - 1;
+      int i = t.qfirst[q] + a - lo;
       if (i < 0 || i >= t.n) continue;
       for (int b = 0; b < P; ++b) {
-        int j = t.qfirst[q] + b - 1;
+        int j = t.qfirst[q] + b - lo;
         if (j < 0 || j >= t.n) continue;
         t.mhat[(size_t)i * t.n + j] += t.qw[q] * t.val[(size_t)q * P + a] * t.val[(size_t)q * P + b];
       }

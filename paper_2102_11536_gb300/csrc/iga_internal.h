@@ -27,11 +27,13 @@ constexpr int kMaxRows = 3 * kMaxK;
 // ---------------------------------------------------------------------------
 struct Tables1D {
   int p = 0, m = 0, n = 0, nel = 0, nq = 0, Q = 0;
+  int lo = 1;                       // the box of functions: full indices lo .. lo + n - 1 (1 .. m-2 by default)
   std::vector<double> qx, qw;       // [Q] point, weight (Gauss weight * span/2)
   std::vector<int> qfirst;          // [Q] first full function index nonzero on the span
+  std::vector<int> qfirst_op;       // [Q] qfirst - lo + 1: the operators' window starts at box index qfirst_op - 1
   std::vector<double> val, der;     // [Q][p+1]
-  std::vector<int> flo, fhi;        // [n] quadrature range [lo, hi) of interior function i (full i+1)
-  std::vector<double> mhat;         // [n][n] interior parametric mass matrix
+  std::vector<int> flo, fhi;        // [n] quadrature range [lo, hi) of box function i (full i + lo)
+  std::vector<double> mhat;         // [n][n] parametric mass matrix over the box
   std::vector<double> evec;         // [n][n] row-major, column c = eigenvector c
   std::vector<double> eval;         // [n]
   std::vector<double> chol;         // [n][p+1] band Cholesky factor of mhat, chol[i][d] = L_{i,i-d}
@@ -42,13 +44,32 @@ struct Tables1D {
 void gauss_legendre(int n, double* x, double* w);
 // Values and derivatives of the degree-p B-splines nonzero at x in span s (s-p..s).
 void bspline_span(int p, const double* U, int s, double x, double* val, double* der);
-// Build all tables of one direction; returns false on invalid knots.
-bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err);
+// Build all tables of one direction over the box of functions lo .. hi (full indices;
+// hi < 0 means m - 2: the interior functions); returns false on invalid knots or box.
+bool build_tables(int p, int nknots, const double* U, int nq, Tables1D& t, std::string& err, int lo = 1,
+                  int hi = -1);
 // Band Cholesky factor of an SPD matrix with half bandwidth p (row-major n x n):
 // L [n][p+1] with L[i][d] = L_{i,i-d}, dinv [n] = 1 / L_ii. False if not positive definite.
 bool band_cholesky(int n, int p, const std::vector<double>& M, std::vector<double>& L, std::vector<double>& dinv);
 // Largest eigenvalue of the symmetric tridiagonal matrix (diagonal a, off-diagonal b).
 double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b);
+// Multi-patch gather / scatter (kernels_mp.cu). Patch r's local vectors lie at
+// xl + nvec * off[r], vector v at + v * nr[r]; entry e of the concatenated boxes belongs to
+// patch epatch[e] at box index e - off[r] and to global function gid[e] (-1: none); the
+// entries of global function g are cent[crow[g] .. crow[g+1]), ascending. Device arrays.
+struct MpMaps {
+  long long nloc = 0, nglob = 0;
+  const long long* gid = nullptr;   // [nloc]
+  const int* epatch = nullptr;      // [nloc]
+  const long long* off = nullptr;   // [npatch]
+  const long long* nr = nullptr;    // [npatch]
+  const long long* crow = nullptr;  // [nglob + 1]
+  const long long* cent = nullptr;  // [crow[nglob]]
+};
+cudaError_t launch_mp_gather(cudaStream_t s, const MpMaps& m, int nvec, const int* active, const double* x,
+                             double* xl);
+cudaError_t launch_mp_scatter(cudaStream_t s, const MpMaps& m, int nvec, const int* active, const double* yl,
+                              double* y);
 // Gluing of conforming patches (host_multipatch.cpp); arguments as iga_mp_layout.
 int mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
               const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj, long long* gid,
@@ -66,7 +87,8 @@ struct DirDev {
   double* sq;     // [Q][P] squared values (for diag(M))
   float* val32;
   float* der32;
-  int* qfirst;    // [Q]
+  int* qfirst;    // [Q] the operators' window start + 1 (Tables1D::qfirst_op)
+  int* qfirst_geo;  // [Q] full first function index, when it differs from qfirst (a box not starting at 1)
   int* flo;       // [n]
   int* fhi;       // [n]
   double* qw;     // [Q]

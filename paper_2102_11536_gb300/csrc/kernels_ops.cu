@@ -474,7 +474,9 @@ cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const i
   long long Qt = 1;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
-      g[a] = GeoDir{dirs[a].val, dirs[a].der, dirs[a].qfirst, dirs[a].qw, dirs[a].P, dirs[a].Q, m[a]};
+      // the geometry reads the full control net: full function indices
+      const int* qf = dirs[a].qfirst_geo ? dirs[a].qfirst_geo : dirs[a].qfirst;
+      g[a] = GeoDir{dirs[a].val, dirs[a].der, qf, dirs[a].qw, dirs[a].P, dirs[a].Q, m[a]};
       Qt *= dirs[a].Q;
     } else {
       g[a] = GeoDir{nullptr, nullptr, nullptr, nullptr, 1, 1, 1};

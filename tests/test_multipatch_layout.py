@@ -120,3 +120,25 @@ def test_bad_arguments_are_rejected(bad):
     with pytest.raises(iga.IgaError) as e:
         iga.multipatch_layout(patches)
     assert e.value.status == iga.EINVAL
+
+
+# iga_mp_create checks its arguments and the gluing before it touches a device, so its
+# refusals are host logic.
+
+def test_multipatch_handle_refuses_the_learned_guess():
+    with pytest.raises(iga.IgaError) as e:
+        iga.MultiPatch(WM.row_of_patches(2, 2, 2), guess="learned", stream=None)
+    assert e.value.status == iga.EINVAL and "learned" in str(e.value)
+
+
+def test_multipatch_handle_refuses_non_conforming_patches():
+    patches = WM.row_of_patches(2, 3, 2)
+    deg, kn, ctrl = patches[1]
+    patches[1] = (deg, [kn[0], np.array([0, 0, 0, 0.25, 2 / 3, 1, 1, 1.0])], ctrl)
+    with pytest.raises(iga.IgaError) as e:
+        iga.MultiPatch(patches, stream=None)
+    assert e.value.status == iga.EINVAL and "not conforming" in str(e.value)
+
+
+def test_multipatch_info_refuses_a_null_handle():
+    assert iga.lib().iga_mp_info(None, None, None, None) == iga.EINVAL
