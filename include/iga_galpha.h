@@ -15,7 +15,9 @@
  *   - All vectors are FP64, length N = prod_a (m_a - 2), the interior control
  *     points (the first and last univariate function of each direction carry
  *     the Dirichlet condition and are dropped). Order is co-lexicographic,
- *     direction 0 fastest (Sec. 5.2, def:parametric_spline).
+ *     direction 0 fastest (Sec. 5.2, def:parametric_spline). On a handle made by
+ *     iga_mp_create (iga_multipatch.h) N is the number of global functions of
+ *     the glued patches, in that header's global numbering.
  *   - "device" pointers are CUDA global memory on the handle's device; "host"
  *     pointers are ordinary (preferably pinned) CPU memory.
  *   - Every call returns an IGA_* status; on failure iga_last_error() gives a
