@@ -142,3 +142,14 @@ def test_multipatch_handle_refuses_non_conforming_patches():
 
 def test_multipatch_info_refuses_a_null_handle():
     assert iga.lib().iga_mp_info(None, None, None, None) == iga.EINVAL
+
+
+def test_multipatch_handle_without_a_device_fails_cleanly():
+    """On a machine without a GPU the gluing succeeds and the device set-up fails with
+    IGA_ECUDA; the partly built system is released without touching a device."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the handle would be created")
+    with pytest.raises(iga.IgaError) as e:
+        iga.MultiPatch(WM.l_shape(3, 2, amp=0.1), stream=None)
+    assert e.value.status == iga.ECUDA
