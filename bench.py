@@ -121,6 +121,10 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
+    ap.add_argument("--multipatch-steps", type=int, default=0,
+                    help="timed steps of the conforming multi-patch system (2 x 2 x 2 glued patches, additive "
+                         "Schwarz preconditioner; 0 = skip)")
+    ap.add_argument("--multipatch-nel", type=int, default=24, help="elements per direction of each glued patch")
     ap.add_argument("--no-general", dest="general", action="store_false",
                     help="skip the damped, forced variant of the headline step")
     ap.add_argument("--band-config", default="",
@@ -521,6 +525,60 @@ def run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, ho
             "note": "one more mass product per step for the aM M term; parity in tests/test_gpu_general.py"}
 
 
+def run_multipatch(args, iga, torch, dev, flush, stream):
+    """The conforming multi-patch system (Sec. 5.1, 5.4): a 2 x 2 x 2 grid of deformed patches of
+    nel^3 elements of degree 3 glued face to face (N_adj = 8), double-FP32 band products and FP32
+    band-Cholesky local preconditioners on every patch, the additive Schwarz preconditioner,
+    k = 2, rho_inf = 0.5, dt = 0.5 tau_crit, PCG tol 1e-10; host-driven loop."""
+    import numpy as np
+    from workloads import multipatch as WM
+    k, rho = 2, 0.5
+    patches = WM.grid_of_patches((2, 2, 2), args.multipatch_nel, 3, amp=0.1)
+    lay = iga.multipatch_layout(patches)
+    # initial displacement: prod_a sin(pi x_a / 2) at each global function's control point
+    coords = np.zeros((lay["nglob"], 3))
+    for r, (deg, kn, ctrl) in enumerate(patches):
+        m = [len(kv) - p - 1 for p, kv in zip(deg, kn)]
+        net = np.asarray(ctrl).reshape(m[2], m[1], m[0], 3)
+        lo, hi = lay["lo"][r], lay["hi"][r]
+        box = net[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1].reshape(-1, 3)
+        ids = lay["gid"][r].reshape(-1)
+        coords[ids[ids >= 0]] = box[ids >= 0]
+    u0 = torch.from_numpy(np.prod(np.sin(np.pi * coords / 2.0), axis=1)).to(dev)
+    v0 = torch.zeros_like(u0)
+    t0 = time.perf_counter()
+    sysm = iga.MultiPatch(patches, tol=1e-10, precond="banded32", op_form="assembled_df")
+    N = sysm.N
+    sysm.assemble()
+    lam, tau = sysm.cfl(rho, iters=args.cfl_iters)
+    setup_s = time.perf_counter() - t0
+    dt = 0.5 * tau
+    state = torch.zeros(3 * k * N, dtype=torch.float64, device=dev)
+    sysm.state_init(k, u0, v0, state)
+    for _ in range(args.warmup):
+        sysm.step(state, k, rho, dt, 1)
+    stats = iga.Stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(args.multipatch_steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        sysm.step(state, k, rho, dt, 1, stats)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    sysm.close()
+    rate = args.multipatch_steps / (ms / 1e3)
+    return {"workload": "2 x 2 x 2 glued patches, %d^3 elements each, p = 3, deformed 0.1; N = %d global functions "
+                        "(N_adj = %d, %d local box entries)" % (args.multipatch_nel, N, sysm.n_adj, sysm.nloc),
+            "form": "assembled_df products and banded32 local preconditioners on every patch, additive Schwarz",
+            "value": rate, "unit": "steps/s", "ms_per_step": ms / args.multipatch_steps,
+            "dof_updates_per_s": rate * N, "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
+            "gpu_launches": int(stats.launches), "lambda_max": lam, "dt": dt, "setup_s": setup_s,
+            "note": "host-driven loop (no graphs yet); parity in the multi-patch GPU tests"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -631,6 +689,8 @@ def run_ours(args):
     general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, hopts,
                           band_cfgs) if args.general else None
     batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
+    mp_res = (run_multipatch(args, iga, torch, dev, flush, stream)
+              if args.multipatch_steps > 0 and world == 1 else None)
 
     if rank != 0:
         if pg:
@@ -688,6 +748,8 @@ def run_ours(args):
         result["multipatch_batch"] = batch_res
     if general is not None:
         result["general_model"] = general
+    if mp_res is not None:
+        result["multipatch_system"] = mp_res
     if not args.no_cpu_baseline and world == 1:
         base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
         result["cpu_baseline"] = base
