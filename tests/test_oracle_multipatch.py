@@ -178,3 +178,13 @@ def test_scheme_on_glued_patches_has_order_2k(k, layout):
         Ue, _ = oracle.exact_semidiscrete(g.M, g.K, U0, V0, T)
         errs.append(np.linalg.norm(X[0] - Ue) / np.linalg.norm(Ue))
     assert math.log2(errs[0] / errs[1]) > 2 * k - 0.35, errs
+
+
+@pytest.mark.parametrize("layout", [lambda: WM.l_shape(4, 3, amp=0.1), lambda: WM.grid_of_patches((2, 1, 2), 3, 2, amp=0.1)])
+def test_lanczos_critical_step_on_glued_patches(layout):
+    """The oracle's Lanczos estimate of lambda_max(M^{-1} K), the critical step's input,
+    on glued patches (with P_ad in its solves) equals the dense generalised eigenvalue."""
+    g = mp.GluedPatches(layout())
+    ref = scipy.linalg.eigh(g.K, g.M, eigvals_only=True)[-1]
+    est = oracle.lambda_max_lanczos(g, iters=g.N)
+    assert abs(est - ref) <= 1e-9 * ref
