@@ -1053,6 +1053,22 @@ int prepare_capture(iga_handle* h, int k) {
   if (h->opt.guess == IGA_GUESS_LEARNED) CKS(ensure_ws_step(h, k));
   CKS(ensure_damp_ws(h, k));
   if (is_assembled(h)) CKS(assemble_band(h));
+  if (h->mp) {  // a multi-patch step reaches every patch: their workspaces too, at full size
+    MpState& mp = *h->mp;
+    if (mp.vec_cap < kMaxVec) {
+      CKS(dalloc(h, &mp.xl, (size_t)kMaxVec * mp.nloc));
+      CKS(dalloc(h, &mp.yl, (size_t)kMaxVec * mp.nloc));
+      mp.vec_cap = kMaxVec;
+    }
+    for (size_t r = 0; r < mp.patch.size(); ++r) {
+      iga_handle* p = mp.patch[r];
+      p->stream = h->stream;
+      int rc = ensure_op_ws(p, kMaxVec);
+      if (rc == IGA_OK) rc = ensure_cg_ws(p, kMaxVec);
+      if (rc == IGA_OK && is_assembled(p)) rc = assemble_band(p);
+      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+    }
+  }
   return IGA_OK;
 }
 
@@ -1507,6 +1523,7 @@ int iga_set_op_form(iga_handle* h, int op_form) {
   if (h->mp) {  // the patches' form; the composite dispatches through them
     h->mp->op_form = op_form;
     for (iga_handle* p : h->mp->patch) p->opt.op_form = op_form;
+    drop_step_graph(h);
     return IGA_OK;
   }
   h->opt.op_form = op_form;
@@ -1518,6 +1535,7 @@ int iga_set_precond(iga_handle* h, int precond) {
     h->mp->precond = precond;
     for (iga_handle* p : h->mp->patch) p->opt.precond = precond;
     h->opt.precond = (precond == IGA_PREC_FP64 || precond == IGA_PREC_BANDED) ? IGA_PREC_FP64 : IGA_PREC_FP32;
+    drop_step_graph(h);
     return IGA_OK;
   }
   h->opt.precond = precond;
@@ -1581,7 +1599,7 @@ int iga_get_time(iga_handle* h, double* t) {
 
 int iga_set_graphs(iga_handle* h, int on) {
   if (!h) return IGA_EINVAL;
-  h->use_graphs = on != 0 && !h->mp;  // a multi-patch handle runs the host-driven loop
+  h->use_graphs = on != 0;
   return IGA_OK;
 }
 
@@ -1707,7 +1725,9 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
   h->stream = (cudaStream_t)o.stream;
   h->N = nglob;
   h->Qt = 1;
-  h->use_graphs = false;  // the host-driven loop: the patches' launches go to the stream of the call
+  // host-driven loop unless iga_set_graphs(h, 1): a captured step reaches the patches through
+  // the stream they are handed on every call, and prepare_capture sizes their workspaces
+  h->use_graphs = false;
   // the composite runs the PCG of its preconditioner's class: plain CG for the FP64 forms,
   // flexible CG otherwise; its own operator form is the dispatch through the patches
   mp.op_form = o.op_form;
