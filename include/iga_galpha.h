@@ -225,6 +225,38 @@ int iga_apply_Pinv_noalloc(iga_handle* h, int nvec, const double* x, double* y);
 int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0, int* iters, double* relres);
 
 /*
+ * Fields at the Gauss points (Sec. 2 and 5.1: the quadrature that defines M, K and the
+ * load vectors). The points are the tensor Gauss rule of the handle (nquad per element
+ * and direction), point q = q0 + Q0 (q1 + Q1 q2) with q_a running over the Gauss points
+ * of direction a element by element; Qt = prod_a Q_a. Single-patch handles only
+ * (IGA_EINVAL on a multi-patch handle).
+ *
+ * iga_npoints -- Qt and, if Q is not NULL, Q_a per direction ([dim], host). Host only.
+ */
+int iga_npoints(const iga_handle* h, long long* Qt, int* Q);
+
+/*
+ * iga_gauss_points -- physical coordinates x = F(xi_q) (device [dim][Qt], coordinate-major)
+ * and weights w_q |det DF(xi_q)| (device [Qt]) at the Gauss points; either may be NULL.
+ * Asynchronous on the handle's stream.
+ */
+int iga_gauss_points(iga_handle* h, double* x, double* w);
+
+/*
+ * iga_evaluate -- g[v][q] = sum_i U[v][i] B_i(xi_q), the spline fields of nvec coefficient
+ * vectors (device [nvec][N]) at the Gauss points (device [nvec][Qt]). 1 <= nvec <= 8.
+ */
+int iga_evaluate(iga_handle* h, int nvec, const double* U, double* g);
+
+/*
+ * iga_integrate -- b[v][i] = sum_q w_q |det DF_q| g[v][q] B_i(xi_q): the load vectors
+ * int g B_i of nvec point fields (device [nvec][Qt] -> device [nvec][N]), with the same
+ * quadrature as M (so iga_integrate of iga_evaluate(U) is M U). 1 <= nvec <= 8; the first
+ * call at a given nvec allocates a [nvec][Qt] scratch that the handle keeps.
+ */
+int iga_integrate(iga_handle* h, int nvec, const double* g, double* b);
+
+/*
  * iga_galpha_params -- the method's parameters for order 2k and user parameter
  * rho_inf in [0, 1] (Sec. 4.1, boxed formulas with rho_b = rho_s; eq. HOgamma):
  * alpha[k], beta[k], gamma[k] (host arrays, block j at index j-1).

@@ -115,6 +115,10 @@ def lib():
         "iga_mp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(H)]),
         "iga_mp_info": (ctypes.c_int, [H, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "iga_npoints": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_longlong), ip]),
+        "iga_gauss_points": (ctypes.c_int, [H, vp, vp]),
+        "iga_evaluate": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
+        "iga_integrate": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -135,7 +139,8 @@ def exported_symbols():
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
-            "iga_mp_layout", "iga_mp_create", "iga_mp_info"]
+            "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_npoints", "iga_gauss_points", "iga_evaluate",
+            "iga_integrate"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -382,6 +387,35 @@ class Patch:
         rel = (ctypes.c_double * nvec)()
         self._chk(lib().iga_solve_M(self.h, nvec, _ptr(b), _ptr(x), int(use_x0), its, rel), "iga_solve_M")
         return list(its), list(rel)
+
+    def npoints(self):
+        """(Qt, [Q_a]): the Gauss points of the handle's quadrature."""
+        qt = ctypes.c_longlong()
+        q = (ctypes.c_int * 3)()
+        self._chk(lib().iga_npoints(self.h, ctypes.byref(qt), q), "iga_npoints")
+        return int(qt.value), list(q)[:self.d]
+
+    def gauss_points(self, x=None, w=None):
+        """Physical Gauss points x ([d][Qt]) and weights w |det DF| ([Qt]) into device tensors."""
+        qt, _ = self.npoints()
+        if x is not None:
+            _check_dev(x, self.d * qt, "x")
+        if w is not None:
+            _check_dev(w, qt, "w")
+        self._chk(lib().iga_gauss_points(self.h, _ptr(x) if x is not None else None,
+                                         _ptr(w) if w is not None else None), "iga_gauss_points")
+
+    def evaluate(self, U, g, nvec=1):
+        """g = sum_i U_i B_i at the Gauss points ([nvec][N] -> [nvec][Qt], device)."""
+        qt, _ = self.npoints()
+        _check_dev(U, nvec * self.N, "U"); _check_dev(g, nvec * qt, "g")
+        self._chk(lib().iga_evaluate(self.h, nvec, _ptr(U), _ptr(g)), "iga_evaluate")
+
+    def integrate(self, g, b, nvec=1):
+        """b_i = int g B_i by the handle's quadrature ([nvec][Qt] -> [nvec][N], device)."""
+        qt, _ = self.npoints()
+        _check_dev(g, nvec * qt, "g"); _check_dev(b, nvec * self.N, "b")
+        self._chk(lib().iga_integrate(self.h, nvec, _ptr(g), _ptr(b)), "iga_integrate")
 
     def cfl(self, rho, iters=100):
         lam = ctypes.c_double()

@@ -121,6 +121,8 @@ struct iga_handle {
   void* ws_work = nullptr;
   double *ws_loss = nullptr, *ws_lpart = nullptr;
   long long ws_loss_cap = 0;
+  double* pts = nullptr;  // [pts_cap] weighted point values (iga_integrate)
+  long long pts_cap = 0;
   // multi-patch system (iga_mp_create): M, K and the additive Schwarz preconditioner act
   // through the patches' own handles; null for a single patch
   MpState* mp = nullptr;
@@ -1498,7 +1500,7 @@ void iga_destroy(iga_handle* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   dfree(h->d_loop); dfree(h->d_tot); dfree(h->d_max); dfree(h->d_init); dfree(h->d_stat);
-  dfree(h->fG); dfree(h->Yv); dfree(h->MYv); dfree(h->d_time);
+  dfree(h->fG); dfree(h->Yv); dfree(h->MYv); dfree(h->d_time); dfree(h->pts);
   dfree(h->ws_theta); dfree(h->ws_m); dfree(h->ws_v); dfree(h->ws_grad);
   dfree(h->ws_E); dfree(h->ws_B1); dfree(h->ws_B2); dfree(h->ws_sc); dfree(h->ws_part);
   dfree(h->ws_x); dfree(h->ws_act); dfree(h->ws_sx); dfree(h->ws_st);
@@ -1647,6 +1649,71 @@ int iga_solve_M(iga_handle* h, int nvec, const double* b, double* x, int use_x0,
   CKS(check_handle(h));
   if (nvec < 1 || nvec > kMaxVec || !b || !x) return fail(h, IGA_EINVAL, "bad arguments");
   return solve(h, nvec, b, x, use_x0 != 0, iters, relres);
+}
+
+int iga_npoints(const iga_handle* h, long long* Qt, int* Q) {
+  if (!h || !Qt || h->mp) return IGA_EINVAL;
+  *Qt = h->Qt;
+  if (Q)
+    for (int a = 0; a < h->dim; ++a) Q[a] = h->Q[a];
+  return IGA_OK;
+}
+
+int iga_gauss_points(iga_handle* h, double* x, double* w) {
+  CKS(check_handle(h));
+  CKS(single_patch(h, "iga_gauss_points"));
+  if (x) {
+    int mm[3] = {h->m[0], h->m[1], h->m[2]};
+    LK(launch_points(h->stream, h->dim, h->dd, mm, h->ctrl, x));
+  }
+  if (w) CK(cudaMemcpyAsync(w, h->W, sizeof(double) * h->Qt, cudaMemcpyDeviceToDevice, h->stream));
+  return IGA_OK;
+}
+
+// g = B U: the forward banded passes of the mass operator, without the weighting
+int iga_evaluate(iga_handle* h, int nvec, const double* U, double* g) {
+  CKS(check_handle(h));
+  CKS(single_patch(h, "iga_evaluate"));
+  if (nvec < 1 || nvec > kMaxVec || !U || !g) return fail(h, IGA_EINVAL, "bad arguments");
+  CKS(ensure_op_ws(h, nvec));
+  cudaStream_t s = h->stream;
+  const int *n = h->n, *Q = h->Q;
+  const DirDev* d = h->dd;
+  if (h->dim == 3) {
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, nullptr, U, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, nullptr, h->u0, h->su, d[1].val, h->ta, nullptr, nullptr, h->st));
+    LK(launch_fwd(s, d[2], {(long long)Q[0] * Q[1], n[2], Q[2], 1}, nvec, nullptr, h->ta, h->st, d[2].val, g, nullptr, nullptr, h->Qt));
+  } else {
+    LK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, nullptr, U, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
+    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], 1}, nvec, nullptr, h->u0, h->su, d[1].val, g, nullptr, nullptr, h->Qt));
+  }
+  return IGA_OK;
+}
+
+// b = B^T (W .* g): the quadrature of int g B_i, by the transposed passes
+int iga_integrate(iga_handle* h, int nvec, const double* g, double* b) {
+  CKS(check_handle(h));
+  CKS(single_patch(h, "iga_integrate"));
+  if (nvec < 1 || nvec > kMaxVec || !g || !b) return fail(h, IGA_EINVAL, "bad arguments");
+  CKS(ensure_op_ws(h, nvec));
+  if (h->pts_cap < nvec * h->Qt) {
+    CK(cudaStreamSynchronize(h->stream));
+    CKS(dalloc(h, &h->pts, (size_t)(nvec * h->Qt)));
+    h->pts_cap = nvec * h->Qt;
+  }
+  cudaStream_t s = h->stream;
+  const int *n = h->n, *Q = h->Q;
+  const DirDev* d = h->dd;
+  LK(launch_weight_points(s, h->Qt, nvec, h->W, g, h->pts));
+  if (h->dim == 3) {
+    LK(launch_tr(s, d[2], {(long long)Q[0] * Q[1], Q[2], n[2], 1}, nvec, nullptr, h->pts, d[2].val, nullptr, nullptr, h->Qt, h->ta, h->st));
+    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, nullptr, h->ta, d[1].val, nullptr, nullptr, h->st, h->u0, h->su));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, nullptr, h->u0, d[0].val, nullptr, nullptr, h->su, b, h->N));
+  } else {
+    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], 1}, nvec, nullptr, h->pts, d[1].val, nullptr, nullptr, h->Qt, h->u0, h->su));
+    LK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, nullptr, h->u0, d[0].val, nullptr, nullptr, h->su, b, h->N));
+  }
+  return IGA_OK;
 }
 
 int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double* gamma) {

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -138,6 +139,12 @@ cudaError_t launch_mid_stiff2(cudaStream_t s, const DirDev& d, long long A, int 
 // Geometric factors at the quadrature points; sets *bad = 1 if det DF <= 0 somewhere.
 cudaError_t launch_geometry(cudaStream_t s, int dim, const DirDev* dirs, const int* m, const double* ctrl_soa,
                             double* W, double* G, long long gstride, int* bad);
+// Fields at the Gauss points (kernels_field.cu): physical points X [dim][Qt] (point
+// q = q0 + Q0 (q1 + Q1 q2)) from the SoA control net, and out = W .* g for nvec vectors.
+cudaError_t launch_points(cudaStream_t s, int dim, const DirDev* dirs, const int* m, const double* ctrl_soa,
+                          double* X);
+cudaError_t launch_weight_points(cudaStream_t s, long long Qt, int nvec, const double* W, const double* g,
+                                 double* out);
 
 // Fast-diagonalisation mode product along one axis: out[x,i,y] = sum_j Mat(i,j) in[x,j,y]
 // with Mat = U (transpose=0) or U^T (transpose=1), U holding [U | U^T] column-major,
