@@ -46,8 +46,9 @@ extern "C" {
  * carries homogeneous Dirichlet conditions: a global function -- one set of identified
  * copies, def:mp_basis -- is dropped when any copy lies on such a face.
  * Errors: IGA_EINVAL (message by iga_last_error(NULL)) for bad sizes, knots or
- * pointers, non-finite control points, a face that coincides with two other faces, an
- * interface whose faces differ in degree or knots, or a wrong gid_len. The caller owns
+ * pointers, non-finite control points, a face that coincides with two other faces, two
+ * faces that cover the same region (equal bounding boxes) without matching control points,
+ * an interface whose faces differ in degree or knots, or a wrong gid_len. The caller owns
  * every buffer; nothing is retained.
  */
 int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,

@@ -204,7 +204,11 @@ int mp_layout(int npatch, int dim, const int* degree, const int* nknots, const d
             best_flip = flip;
           }
         }
-      if (!matched) continue;
+      if (!matched) {  // the same extent without matching functions: a non-conforming interface
+        err = "iga_mp_layout: a face of patch " + std::to_string(F.r) + " and one of patch " + std::to_string(G.r) +
+              " cover the same region with different control points (not conforming)";
+        return IGA_EINVAL;
+      }
       if (partner[f] >= 0 || partner[g] >= 0) {
         err = "iga_mp_layout: a face of patch " + std::to_string(F.r) +
               " or " + std::to_string(G.r) + " coincides with more than one other face (not conforming)";

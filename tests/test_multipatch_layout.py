@@ -96,6 +96,16 @@ def test_non_conforming_knots_are_rejected():
     assert e.value.status == iga.EINVAL and "not conforming" in str(e.value)
 
 
+def test_a_non_matching_interface_is_rejected():
+    """Two patches that share a face region but not its control points (the right one
+    refined): a non-conforming interface, not two Dirichlet faces."""
+    left = WM.row_of_patches(2, 3, 2, amp=0.0)[0]
+    right = WM.row_of_patches(2, 4, 2, amp=0.0)[1]
+    with pytest.raises(iga.IgaError) as e:
+        iga.multipatch_layout([left, right])
+    assert e.value.status == iga.EINVAL and "not conforming" in str(e.value)
+
+
 def test_a_face_shared_by_three_patches_is_rejected():
     patches = WM.row_of_patches(2, 2, 2, amp=0.0)
     with pytest.raises(iga.IgaError) as e:
