@@ -98,69 +98,176 @@ def _flat(ix_rev, m):
     return f
 
 
+def _einsum_rows(S, facs):
+    """sum over the tensor points of S (array axes: direction d-1 first) times, per direction
+    a, the table facs[a] (|S_a|, c_a): the array of shape (c_{d-1}, ..., c_0)."""
+    d = len(facs)
+    pts = "".join(chr(ord("a") + k) for k in range(d))          # point axes, direction d-1 first
+    outs = "".join(chr(ord("n") + k) for k in range(d))         # candidate axes, same order
+    terms = [pts] + [pts[d - 1 - a] + outs[d - 1 - a] for a in range(d)]
+    return np.einsum(",".join(terms) + "->" + outs, S, *facs, optimize=True)
+
+
+def patch_rows(degrees, knots, ctrl, rows, nq=None):
+    """Rows of one patch's M and K over ALL its functions (flat index i_0 + m_0 (i_1 + ...)),
+    for the functions `rows` (flat indices), integrated by the Gauss rule (nq points, default
+    max p + 1) over the elements in each row function's support only: for each row a dict
+    {column: (M_ij, K_ij)} over the columns with |j_a - i_a| <= p_a. The geometry comes from
+    the whole control net at the support points (Sec. 2: M_ij = int B_i B_j |det J|,
+    K_ij = int grad B_i . grad B_j |det J|)."""
+    d = len(degrees)
+    nq = nq or max(degrees) + 1
+    quads = [Quad1D(p, kn, nq) for p, kn in zip(degrees, knots)]
+    m = [q.m for q in quads]
+    B = [q.dense() for q in quads]
+    dB = [q.dense(True) for q in quads]
+    net = np.asarray(ctrl, dtype=np.float64).reshape(list(reversed(m)) + [d])
+    wq = [q.qw for q in quads]
+    out = []
+    for i in rows:
+        ia, f = [], int(i)
+        for a in range(d):
+            ia.append(f % m[a])
+            f //= m[a]
+        S = [np.nonzero(B[a][:, ia[a]])[0] for a in range(d)]          # support points per direction
+        cand = [np.arange(max(0, ia[a] - degrees[a]), min(m[a], ia[a] + degrees[a] + 1)) for a in range(d)]
+        # geometry at the support points
+        J = np.empty([len(S[a]) for a in reversed(range(d))] + [d, d])
+        for b in range(d):
+            tabs = [(dB[a] if a == b else B[a])[S[a], :] for a in range(d)]
+            for c in range(d):
+                A = net[..., c]
+                for a in range(d):
+                    ax = d - 1 - a
+                    A = np.moveaxis(np.tensordot(tabs[a], A, axes=(1, ax)), 0, ax)
+                J[..., c, b] = A
+        det = np.linalg.det(J)
+        w = wq[0][S[0]]
+        for a in range(1, d):
+            w = np.multiply.outer(wq[a][S[a]], w)
+        W = w * np.abs(det)
+        Jinv = np.linalg.inv(J)
+        G = np.einsum("...ac,...bc->...ab", Jinv, Jinv)
+        # the row function and its parametric gradient at the support points
+        def tensor(vecs):
+            T = vecs[0]
+            for a in range(1, d):
+                T = np.multiply.outer(vecs[a], T)
+            return T
+        Ni = tensor([B[a][S[a], ia[a]] for a in range(d)])
+        dNi = [tensor([(dB[a] if a == b else B[a])[S[a], ia[a]] for a in range(d)]) for b in range(d)]
+        Mrow = _einsum_rows(W * Ni, [B[a][np.ix_(S[a], cand[a])] for a in range(d)])
+        Krow = np.zeros_like(Mrow)
+        for b in range(d):
+            for c in range(d):
+                Krow += _einsum_rows(W * G[..., b, c] * dNi[b],
+                                     [(dB[a] if a == c else B[a])[np.ix_(S[a], cand[a])] for a in range(d)])
+        row = {}
+        for jr in itertools.product(*[range(len(cand[a])) for a in reversed(range(d))]):
+            ja = [cand[a][jr[d - 1 - a]] for a in range(d)]
+            j = 0
+            for a in reversed(range(d)):
+                j = j * m[a] + int(ja[a])
+            row[j] = (float(Mrow[jr]), float(Krow[jr]))
+        out.append(row)
+    return out
+
+
+def glued_rows(patches, local, rows, x, nq=None):
+    """(M x)_g and (K x)_g of the glued system for the global functions `rows`, x a global
+    vector: the sums over the copies (r, i) of global function g of patch r's rows over its
+    local functions, sum_j M^(r)_ij x_gid(r, j) (Sec. 5.1: M = sum_r R^(r)T M^(r) R^(r)).
+    local: the first result of glue(patches)."""
+    copies = {}
+    for r, loc in enumerate(local):
+        for f, g in loc["to_gid"].items():
+            copies.setdefault(g, []).append((r, f))
+    Mx, Kx = np.zeros(len(rows)), np.zeros(len(rows))
+    for k, g in enumerate(rows):
+        for r, f in copies[g]:
+            deg, knots, ctrl = patches[r]
+            (row,) = patch_rows(deg, knots, ctrl, [f], nq)
+            to_gid = local[r]["to_gid"]
+            for j, (mij, kij) in row.items():
+                if j in to_gid:
+                    Mx[k] += mij * x[to_gid[j]]
+                    Kx[k] += kij * x[to_gid[j]]
+    return Mx, Kx
+
+
+def glue(patches):
+    """The numbering of Sec. 5.1 for conforming patches (see the module docstring), without
+    matrices: per patch its function counts m, index box (lo, n), the flat full indices of
+    its local functions (keep, box order), their global ids (ids), the box mask, and a dict
+    full index -> global id; plus the number of global functions."""
+    d = len(patches[0][0])
+    nets = []
+    for deg, knots, ctrl in patches:
+        m = [len(kn) - p - 1 for p, kn in zip(deg, knots)]
+        nets.append((m, np.asarray(ctrl, dtype=np.float64).reshape(-1, d)))
+    # interface faces: equal control-point sets on two different patches
+    owners = {}
+    for r, (m, pts) in enumerate(nets):
+        for a in range(d):
+            for side in (0, 1):
+                fk = frozenset(_key(pts[f]) for f in _face_flat(m, a, side))
+                owners.setdefault(fk, []).append((r, a, side))
+    interfaces, iface = [], set()
+    for fk, own in owners.items():
+        if len(own) > 2 or (len(own) == 2 and own[0][0] == own[1][0]):
+            raise ValueError("a face is shared by more than two patch faces: not conforming")
+        if len(own) == 2:
+            interfaces.append(tuple(own))
+            iface.update(own)
+    # identification: every function of every patch gets a key (functions on interfaces:
+    # their control point); a key is outer when one of its copies lies on an outer face
+    keys, outer = [], set()
+    for r, (m, pts) in enumerate(nets):
+        kr = {}
+        for ix_rev in itertools.product(*[range(n) for n in reversed(m)]):
+            f = _flat(ix_rev, m)
+            ix = ix_rev[::-1]
+            faces = [(a, 0) for a in range(d) if ix[a] == 0] + [(a, 1) for a in range(d) if ix[a] == m[a] - 1]
+            on_iface = any((r, a, s_) in iface for a, s_ in faces)
+            kr[f] = ("iface", _key(pts[f])) if on_iface else ("own", r, f)
+            if any((r, a, s_) not in iface for a, s_ in faces):
+                outer.add(kr[f])
+        keys.append(kr)
+    local, gid, nglob = [], {}, 0
+    for r, (m, pts) in enumerate(nets):
+        lo = [0 if (r, a, 0) in iface else 1 for a in range(d)]
+        hi = [m[a] - 1 if (r, a, 1) in iface else m[a] - 2 for a in range(d)]
+        keep, ids, mask, to_gid = [], [], [], {}
+        for ix_rev in itertools.product(*[range(lo[a], hi[a] + 1) for a in reversed(range(d))]):
+            f = _flat(ix_rev, m)
+            key = keys[r][f]
+            mask.append(key not in outer)
+            if key in outer:
+                continue
+            if key not in gid:
+                gid[key] = nglob
+                nglob += 1
+            keep.append(f)
+            ids.append(gid[key])
+            to_gid[f] = gid[key]
+        local.append({"m": m, "lo": lo, "n": [hi[a] - lo[a] + 1 for a in range(d)], "keep": keep,
+                      "ids": np.array(ids, dtype=int), "mask": np.array(mask), "to_gid": to_gid})
+    return local, nglob, interfaces
+
+
 class GluedPatches:
     """Conforming patches glued face to face (see the module docstring)."""
 
     def __init__(self, patches, nq=None):
         """patches: list of (degrees, knots, ctrl)."""
         self.P = len(patches)
-        self.d = len(patches[0][0])
-        d = self.d
-        full = []
-        for deg, knots, ctrl in patches:
+        self.d = d = len(patches[0][0])
+        self.local, nglob, self.interfaces = glue(patches)
+        for loc, (deg, knots, ctrl) in zip(self.local, patches):
             M, K, Mhat, m = patch_full_matrices(deg, knots, ctrl, nq)
-            full.append((M, K, Mhat, m, np.asarray(ctrl, dtype=np.float64).reshape(-1, d)))
-        # interface faces: equal control-point sets on two different patches
-        owners = {}
-        for r, (_, _, _, m, pts) in enumerate(full):
-            for a in range(d):
-                for side in (0, 1):
-                    fk = frozenset(_key(pts[f]) for f in _face_flat(m, a, side))
-                    owners.setdefault(fk, []).append((r, a, side))
-        self.interfaces = []
-        iface = set()
-        for fk, own in owners.items():
-            if len(own) > 2 or (len(own) == 2 and own[0][0] == own[1][0]):
-                raise ValueError("a face is shared by more than two patch faces: not conforming")
-            if len(own) == 2:
-                self.interfaces.append(tuple(own))
-                iface.update(own)
-        # identification: every function of every patch gets a key (functions on interfaces:
-        # their control point); a key is outer when one of its copies lies on an outer face
-        keys, outer = [], set()
-        for r, (M, K, Mhat, m, pts) in enumerate(full):
-            kr = {}
-            for ix_rev in itertools.product(*[range(n) for n in reversed(m)]):
-                f = _flat(ix_rev, m)
-                ix = ix_rev[::-1]
-                faces = [(a, 0) for a in range(d) if ix[a] == 0] + [(a, 1) for a in range(d) if ix[a] == m[a] - 1]
-                on_iface = any((r, a, s_) in iface for a, s_ in faces)
-                kr[f] = ("iface", _key(pts[f])) if on_iface else ("own", r, f)
-                if any((r, a, s_) not in iface for a, s_ in faces):
-                    outer.add(kr[f])
-            keys.append(kr)
-        self.local = []
-        gid = {}
-        nglob = 0
-        for r, (M, K, Mhat, m, pts) in enumerate(full):
-            lo = [0 if (r, a, 0) in iface else 1 for a in range(d)]
-            hi = [m[a] - 1 if (r, a, 1) in iface else m[a] - 2 for a in range(d)]
-            keep, ids, mask = [], [], []
-            for ix_rev in itertools.product(*[range(lo[a], hi[a] + 1) for a in reversed(range(d))]):
-                f = _flat(ix_rev, m)
-                key = keys[r][f]
-                mask.append(key not in outer)
-                if key in outer:
-                    continue
-                if key not in gid:
-                    gid[key] = nglob
-                    nglob += 1
-                keep.append(f)
-                ids.append(gid[key])
-            n = [hi[a] - lo[a] + 1 for a in range(d)]
-            self.local.append({"m": m, "lo": lo, "n": n, "ids": np.array(ids, dtype=int), "mask": np.array(mask),
-                               "M": M[np.ix_(keep, keep)], "K": K[np.ix_(keep, keep)],
-                               "Mhat": [Mhat[a][lo[a]:hi[a] + 1, lo[a]:hi[a] + 1] for a in range(d)]})
+            keep, lo, n = loc["keep"], loc["lo"], loc["n"]
+            loc["M"], loc["K"] = M[np.ix_(keep, keep)], K[np.ix_(keep, keep)]
+            loc["Mhat"] = [Mhat[a][lo[a]:lo[a] + n[a], lo[a]:lo[a] + n[a]] for a in range(d)]
         self.N = nglob
         self.M = np.zeros((nglob, nglob))
         self.K = np.zeros((nglob, nglob))

@@ -188,3 +188,33 @@ def test_lanczos_critical_step_on_glued_patches(layout):
     ref = scipy.linalg.eigh(g.K, g.M, eigvals_only=True)[-1]
     est = oracle.lambda_max_lanczos(g, iters=g.N)
     assert abs(est - ref) <= 1e-9 * ref
+
+
+@pytest.mark.parametrize("patch", [lambda: WM.grid_of_patches((1, 1), 4, 2, amp=0.12)[0],
+                                   lambda: WM.reorient(WM.grid_of_patches((1, 1), 3, 3, amp=0.1)[0], (1, 0), (0,)),
+                                   lambda: WM.grid_of_patches((1, 1, 1), 3, 2, amp=0.12)[0]])
+def test_row_assembly_equals_the_dense_patch_matrices(patch):
+    """patch_rows integrates over the row function's support only; every row of M and K
+    (boundary functions included) equals the dense assembly's."""
+    deg, kn, ctrl = patch()
+    M, K, _, m = mp.patch_full_matrices(deg, kn, ctrl)
+    rows = mp.patch_rows(deg, kn, ctrl, range(M.shape[0]))
+    Mr, Kr = np.zeros_like(M), np.zeros_like(K)
+    for i, row in enumerate(rows):
+        for j, (mij, kij) in row.items():
+            Mr[i, j], Kr[i, j] = mij, kij
+    assert np.abs(Mr - M).max() <= 1e-13 * np.abs(M).max()
+    assert np.abs(Kr - K).max() <= 1e-13 * np.abs(K).max()
+
+
+@pytest.mark.parametrize("layout", [lambda: WM.l_shape(3, 3, amp=0.1), lambda: WM.grid_of_patches((2, 2), 3, 2, amp=0.1),
+                                    lambda: WM.grid_of_patches((2, 1, 2), 2, 2, amp=0.1)])
+def test_sampled_glued_products_equal_the_global_matrices(layout):
+    """glued_rows (per-row assembly through the copies of each global function, for
+    full-size sampled checks) equals the dense global M x and K x on every row."""
+    patches = layout()
+    g = mp.GluedPatches(patches)
+    x = np.random.default_rng(4).standard_normal(g.N)
+    Mx, Kx = mp.glued_rows(patches, g.local, list(range(g.N)), x)
+    assert np.abs(Mx - g.M @ x).max() <= 1e-13 * np.abs(g.M @ x).max()
+    assert np.abs(Kx - g.K @ x).max() <= 1e-12 * np.abs(g.K @ x).max()
