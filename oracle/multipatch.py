@@ -219,6 +219,16 @@ def glue(patches):
         if len(own) == 2:
             interfaces.append(tuple(own))
             iface.update(own)
+    # faces that cover the same region (equal bounding boxes) without equal control-point sets:
+    # a non-conforming interface (Assumption ass:conformity), not two Dirichlet faces
+    boxes = {}
+    for fk, own in owners.items():
+        if len(own) == 1:
+            pts_f = np.array(sorted(fk))
+            bb = (_key(pts_f.min(axis=0)), _key(pts_f.max(axis=0)))
+            if bb in boxes and boxes[bb][0] != own[0][0]:
+                raise ValueError("two faces cover the same region with different control points: not conforming")
+            boxes[bb] = own[0]
     # identification: every function of every patch gets a key (functions on interfaces:
     # their control point); a key is outer when one of its copies lies on an outer face
     keys, outer = [], set()

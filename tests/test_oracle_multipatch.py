@@ -218,3 +218,12 @@ def test_sampled_glued_products_equal_the_global_matrices(layout):
     Mx, Kx = mp.glued_rows(patches, g.local, list(range(g.N)), x)
     assert np.abs(Mx - g.M @ x).max() <= 1e-13 * np.abs(g.M @ x).max()
     assert np.abs(Kx - g.K @ x).max() <= 1e-12 * np.abs(g.K @ x).max()
+
+
+def test_oracle_refuses_a_non_matching_interface():
+    """Assumption ass:conformity: a refined neighbour shares the face region but not its
+    functions; the oracle refuses it like the library does."""
+    left = WM.row_of_patches(2, 3, 2, amp=0.0)[0]
+    right = WM.row_of_patches(2, 4, 2, amp=0.0)[1]
+    with pytest.raises(ValueError, match="not conforming"):
+        mp.glue([left, right])
