@@ -227,3 +227,16 @@ def test_oracle_refuses_a_non_matching_interface():
     right = WM.row_of_patches(2, 4, 2, amp=0.0)[1]
     with pytest.raises(ValueError, match="not conforming"):
         mp.glue([left, right])
+
+
+def test_schwarz_iterations_grow_with_p_and_fall_with_refinement():
+    """Table Fan_its (Sec. 6): the mean PCG iterations with the additive Schwarz
+    preconditioner grow with the degree and fall as the patches are refined; here on a
+    2 x 2 grid of deformed patches at the table's tau = 5e-5, T = 64 tau, tol 1e-12."""
+    from oracle.multipatch_table import mean_iterations
+    its = {(n, p): mean_iterations(WM.grid_of_patches((2, 2), n, p, amp=0.1))[0] for n in (4, 8) for p in (1, 2, 3)}
+    for n in (4, 8):
+        assert its[(n, 1)] < its[(n, 2)] < its[(n, 3)], its
+    for p in (1, 2, 3):
+        assert its[(8, p)] < its[(4, p)], its
+    assert max(its.values()) < 30
