@@ -37,13 +37,17 @@ def _contract(tables, A):
 class PatchQuadrature:
     """Physical Gauss points, weights w |det DF| and interior basis tables of one patch."""
 
-    def __init__(self, degrees, knots, ctrl, nq):
+    def __init__(self, degrees, knots, ctrl, nq, lo=None, n=None):
+        """The functions are the box lo_a .. lo_a + n_a - 1 per direction (default: the
+        interior functions 1 .. m_a - 2)."""
         self.d = d = len(degrees)
         quads = [Quad1D(p, kn, nq) for p, kn in zip(degrees, knots)]
         self.m = [q.m for q in quads]
         full = [q.dense() for q in quads]
         dfull = [q.dense(True) for q in quads]
-        self.B = [t[:, 1:-1] for t in full]  # interior functions
+        lo = lo if lo is not None else [1] * d
+        n = n if n is not None else [self.m[a] - 2 for a in range(d)]
+        self.B = [full[a][:, lo[a]:lo[a] + n[a]] for a in range(d)]
         self.n = [t.shape[1] for t in self.B]
         net = np.asarray(ctrl, dtype=np.float64).reshape(list(reversed(self.m)) + [d])
         # x_c and its derivatives along each direction at the points
@@ -74,9 +78,10 @@ class PatchQuadrature:
         return math.sqrt(float(np.sum(self.W * (self.evaluate(U) - exact) ** 2)))
 
 
-def standing_profile(x):
-    """S(x) = prod_a sin(pi x_a) at points x of shape (d, ...)."""
-    return np.prod(np.sin(np.pi * x), axis=0)
+def standing_profile(x, lengths=None):
+    """S(x) = prod_a sin(pi x_a / L_a) at points x of shape (d, ...) (L_a = 1 by default)."""
+    L = np.ones(x.shape[0]) if lengths is None else np.asarray(lengths, dtype=np.float64)
+    return np.prod(np.sin(np.pi * x / L.reshape((-1,) + (1,) * (x.ndim - 1))), axis=0)
 
 
 class ForcedWave:
@@ -105,3 +110,44 @@ class ForcedWave:
         """L2 projections of u(0) = S and u_t(0) = w S: M U0 = G, V0 = w U0."""
         U0 = solve_M(self.G)
         return U0, self.omega * U0
+
+
+class GluedForcedWave:
+    """The forced wave u = S(x) (cos wt + sin wt), S = prod_a sin(pi x_a / L_a), on glued
+    patches covering the box prod_a [0, L_a] (Sec. 5.1: V_h on the union): the global load
+    G = sum_r R^(r)T int S B^(r), the L2 projections, and the L2 error summed over the
+    patches. f = (sum_a (pi / L_a)^2 - w^2) S (cos wt + sin wt)."""
+
+    def __init__(self, patches, glued, lengths, omega, nq):
+        self.omega = omega
+        self.quads, self.S = [], []
+        d = len(lengths)
+        G = np.zeros(glued.N)
+        for (deg, kn, ctrl), loc in zip(patches, glued.local):
+            q = PatchQuadrature(deg, kn, ctrl, nq, lo=loc["lo"], n=loc["n"])
+            S = standing_profile(q.x, lengths)
+            G[loc["ids"]] += q.integrate(S)[loc["mask"]]
+            self.quads.append((q, loc))
+            self.S.append(S)
+        self.G = G
+        self.amp = sum((math.pi / L) ** 2 for L in lengths) - omega ** 2
+        self.d = d
+
+    def time_factor(self, s, t):
+        w = self.omega
+        return w ** s * (math.cos(w * t + s * math.pi / 2) + math.sin(w * t + s * math.pi / 2))
+
+    def forcing(self, s, t):
+        return self.amp * self.time_factor(s, t) * self.G
+
+    def initial(self, solve_M):
+        U0 = solve_M(self.G)
+        return U0, self.omega * U0
+
+    def l2_error(self, U, t):
+        tot = 0.0
+        for (q, loc), S in zip(self.quads, self.S):
+            box = np.zeros(loc["mask"].size)
+            box[loc["mask"]] = U[loc["ids"]]
+            tot += q.l2_error(box, S * self.time_factor(0, t)) ** 2
+        return math.sqrt(tot)

@@ -66,3 +66,27 @@ def test_forced_wave_converges_at_order_p_plus_1(d, p, nels, rate):
             X = st.step(X, T / n)
         errs.append(q.l2_error(X[0], fw.exact(T)))
     assert math.log2(errs[-2] / errs[-1]) > rate, errs
+
+
+@pytest.mark.parametrize("p,rate", [(2, 2.8), (3, 3.7)])
+def test_forced_wave_on_glued_patches_converges_at_order_p_plus_1(p, rate):
+    """Optimal L2 convergence also on a multi-patch domain (Sec. 6): a 2 x 2 grid of
+    deformed patches glued into [0, 2]^2 (N_adj = 4, the additive Schwarz preconditioner in
+    the solves), S = sin(pi x / 2) sin(pi y / 2)."""
+    from oracle import multipatch as mp
+    from workloads import multipatch as WM
+    errs = []
+    for nsub in (4, 8):
+        pts = WM.grid_of_patches((2, 2), nsub, p, amp=0.1)
+        g = mp.GluedPatches(pts)
+        fw = mf.GluedForcedWave(pts, g, (2.0, 2.0), 2 * math.pi, p + 3)
+        U0, V0 = fw.initial(lambda b: oracle.pcg(g.apply_M, g.apply_Pinv, b, tol=1e-14)[0])
+        lam = oracle.lambda_max_lanczos(g, iters=min(g.N, 200))
+        T = 0.1
+        n = max(20, int(math.ceil(T / (0.5 * math.sqrt(oracle.theta_crit(0.5) / lam)))))
+        st = oracle.Stepper(g, 2, 0.5, tol=1e-13, forcing=fw.forcing)
+        X = st.init(U0, V0)
+        for _ in range(n):
+            X = st.step(X, T / n)
+        errs.append(fw.l2_error(X[0], T))
+    assert math.log2(errs[0] / errs[1]) > rate, errs
