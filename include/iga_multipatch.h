@@ -84,6 +84,25 @@ int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, con
 int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
                   const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out);
 
+/*
+ * iga_mp_patch -- the handle of patch r of a multi-patch system (borrowed: it lives until
+ * iga_destroy of the system and must not be destroyed; it works on the system's stream).
+ * Its vectors are the patch's box (iga_ndof of it gives the box size, direction 0 fastest),
+ * so iga_gauss_points, iga_evaluate and iga_integrate give per-patch points, fields and
+ * integrals (a box entry that is not a degree of freedom is a function of the patch like
+ * the others). IGA_EINVAL for a bad r or a single-patch handle. Host only.
+ */
+int iga_mp_patch(iga_handle* h, int r, iga_handle** patch);
+
+/*
+ * iga_mp_patch_io -- between the global vectors (device [nvec][N]) and patch r's box
+ * (device [nvec][box size]): add = 0 gathers, out = R^(r) in (zero at box entries that are
+ * no degree of freedom); add = 1 adds, out += R^(r)T in (each global function of the patch
+ * receives its copy). Sum the add = 1 calls over the patches for sum_r R^(r)T b^(r), e.g.
+ * a global load vector from per-patch integrals. Asynchronous on the system's stream.
+ */
+int iga_mp_patch_io(iga_handle* h, int r, int nvec, int add, const double* in, double* out);
+
 /* iga_mp_info -- number of patches, N_adj and the summed box sizes of a multi-patch
  * handle (any pointer may be NULL). IGA_EINVAL for a single-patch handle. Host only. */
 int iga_mp_info(const iga_handle* h, int* npatch, int* n_adj, long long* nloc);

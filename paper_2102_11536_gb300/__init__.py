@@ -115,6 +115,8 @@ def lib():
         "iga_mp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(H)]),
         "iga_mp_info": (ctypes.c_int, [H, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "iga_mp_patch": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(H)]),
+        "iga_mp_patch_io": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]),
         "iga_npoints": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_longlong), ip]),
         "iga_gauss_points": (ctypes.c_int, [H, vp, vp]),
         "iga_evaluate": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
@@ -139,7 +141,7 @@ def exported_symbols():
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
-            "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_npoints", "iga_gauss_points", "iga_evaluate",
+            "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_npoints", "iga_gauss_points", "iga_evaluate",
             "iga_integrate"]
 
 
@@ -334,6 +336,9 @@ class Patch:
             raise IgaError(rc, "%s: %s" % (what, lib().iga_last_error(self.h).decode()))
 
     def close(self):
+        if getattr(self, "_borrowed", False):  # a multi-patch system's patch: the system owns it
+            self.h = None
+            return
         if getattr(self, "h", None):
             lib().iga_destroy(self.h)
             self.h = None
@@ -575,6 +580,26 @@ class MultiPatch(Patch):
         npc, nadj, nloc = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
         L.iga_mp_info(h, ctypes.byref(npc), ctypes.byref(nadj), ctypes.byref(nloc))
         self.npatch, self.n_adj, self.nloc = int(npc.value), int(nadj.value), int(nloc.value)
+
+    def patch(self, r):
+        """Patch r's own handle (borrowed, a Patch over its box; valid while this system lives)."""
+        ph = ctypes.c_void_p()
+        self._chk(lib().iga_mp_patch(self.h, r, ctypes.byref(ph)), "iga_mp_patch")
+        p = Patch.__new__(Patch)
+        p.h, p.d, p.shape = ph, self.d, None
+        n = ctypes.c_longlong()
+        lib().iga_ndof(ph, ctypes.byref(n))
+        p.N = int(n.value)
+        p._borrowed = True
+        return p
+
+    def patch_gather(self, r, x, box, nvec=1):
+        """box = R^(r) x (global [nvec][N] -> patch r's box [nvec][box size], device)."""
+        self._chk(lib().iga_mp_patch_io(self.h, r, nvec, 0, _ptr(x), _ptr(box)), "iga_mp_patch_io")
+
+    def patch_scatter_add(self, r, box, y, nvec=1):
+        """y += R^(r)T box (patch r's box -> global, device)."""
+        self._chk(lib().iga_mp_patch_io(self.h, r, nvec, 1, _ptr(box), _ptr(y)), "iga_mp_patch_io")
 
 class Batch:
     """Independent patches advanced together, one CUDA graph launch per batch step

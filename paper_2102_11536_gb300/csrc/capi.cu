@@ -1859,6 +1859,22 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
   return IGA_OK;
 }
 
+int iga_mp_patch(iga_handle* h, int r, iga_handle** patch) {
+  if (!h || !h->mp || !patch || r < 0 || r >= (int)h->mp->patch.size()) return IGA_EINVAL;
+  *patch = h->mp->patch[(size_t)r];
+  (*patch)->stream = h->stream;
+  return IGA_OK;
+}
+
+int iga_mp_patch_io(iga_handle* h, int r, int nvec, int add, const double* in, double* out) {
+  CKS(check_handle(h));
+  if (!h->mp || r < 0 || r >= (int)h->mp->patch.size() || nvec < 1 || nvec > kMaxVec || !in || !out)
+    return fail(h, IGA_EINVAL, "bad arguments");
+  const MpState& mp = *h->mp;
+  LK(launch_mp_patch_io(h->stream, mp.maps, mp.off[(size_t)r], mp.nr[(size_t)r], nvec, add != 0, in, out));
+  return IGA_OK;
+}
+
 int iga_mp_info(const iga_handle* h, int* npatch, int* n_adj, long long* nloc) {
   if (!h || !h->mp) return IGA_EINVAL;
   if (npatch) *npatch = (int)h->mp->patch.size();

@@ -71,6 +71,10 @@ cudaError_t launch_mp_gather(cudaStream_t s, const MpMaps& m, int nvec, const in
                              double* xl);
 cudaError_t launch_mp_scatter(cudaStream_t s, const MpMaps& m, int nvec, const int* active, const double* yl,
                               double* y);
+// One patch's box (entries off .. off + nr - 1): add = 0 gathers the global vector into the
+// box (zero where no degree of freedom), add = 1 adds the box into the global vector.
+cudaError_t launch_mp_patch_io(cudaStream_t s, const MpMaps& m, long long off, long long nr, int nvec, int add,
+                               const double* in, double* out);
 // Gluing of conforming patches (host_multipatch.cpp); arguments as iga_mp_layout.
 int mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
               const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj, long long* gid,

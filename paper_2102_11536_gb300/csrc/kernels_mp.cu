@@ -37,7 +37,30 @@ __global__ void k_mp_scatter(MpMaps m, int nvec, const int* __restrict__ active,
   y[v * m.nglob + g] = acc;
 }
 
+// One patch's box <-> the global vector: entries off .. off + nr - 1 of the maps. A patch
+// holds at most one copy of each global function, so the scatter-add has no conflicts.
+__global__ void k_mp_patch_io(MpMaps m, long long off, long long nr, int nvec, int add, const double* __restrict__ in,
+                              double* __restrict__ out) {
+  const int v = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  const long long g = m.gid[off + i];
+  if (add) {  // in: the box, out: the global vector
+    if (g >= 0) out[v * m.nglob + g] += in[v * nr + i];
+  } else {    // in: the global vector, out: the box
+    out[v * nr + i] = g >= 0 ? in[v * m.nglob + g] : 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mp_patch_io(cudaStream_t s, const MpMaps& m, long long off, long long nr, int nvec, int add,
+                               const double* in, double* out) {
+  if (nr <= 0 || nvec <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((nr + 255) / 256), (unsigned)nvec);
+  k_mp_patch_io<<<grid, 256, 0, s>>>(m, off, nr, nvec, add, in, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mp_gather(cudaStream_t s, const MpMaps& m, int nvec, const int* active, const double* x,
                              double* xl) {
