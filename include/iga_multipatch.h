@@ -85,6 +85,15 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
                   const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out);
 
 /*
+ * iga_mp_set_concurrent -- on != 0: every operator of the system runs its patches on
+ * streams of their own, forked from and joined back into the system's stream by events
+ * (a captured step then holds the patches as parallel branches); 0: one after another on
+ * the system's stream (default). Results are the same either way. IGA_EINVAL for a
+ * single-patch handle.
+ */
+int iga_mp_set_concurrent(iga_handle* h, int on);
+
+/*
  * iga_mp_patch -- the handle of patch r of a multi-patch system (borrowed: it lives until
  * iga_destroy of the system and must not be destroyed; it works on the system's stream).
  * Its vectors are the patch's box (iga_ndof of it gives the box size, direction 0 fastest),

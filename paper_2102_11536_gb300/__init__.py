@@ -116,6 +116,7 @@ def lib():
                                          ctypes.c_double, ctypes.POINTER(Options), ctypes.POINTER(H)]),
         "iga_mp_info": (ctypes.c_int, [H, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
         "iga_mp_patch": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(H)]),
+        "iga_mp_set_concurrent": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_mp_patch_io": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]),
         "iga_npoints": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_longlong), ip]),
         "iga_gauss_points": (ctypes.c_int, [H, vp, vp]),
@@ -141,7 +142,7 @@ def exported_symbols():
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
-            "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_npoints", "iga_gauss_points", "iga_evaluate",
+            "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
             "iga_integrate"]
 
 
@@ -580,6 +581,10 @@ class MultiPatch(Patch):
         npc, nadj, nloc = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
         L.iga_mp_info(h, ctypes.byref(npc), ctypes.byref(nadj), ctypes.byref(nloc))
         self.npatch, self.n_adj, self.nloc = int(npc.value), int(nadj.value), int(nloc.value)
+
+    def set_concurrent(self, on=True):
+        """Run the patches of every operator on streams of their own (iga_mp_set_concurrent)."""
+        self._chk(lib().iga_mp_set_concurrent(self.h, int(bool(on))), "iga_mp_set_concurrent")
 
     def patch(self, r):
         """Patch r's own handle (borrowed, a Patch over its box; valid while this system lives)."""

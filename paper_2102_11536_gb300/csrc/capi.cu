@@ -142,6 +142,12 @@ struct MpState {
   MpMaps maps;
   double *xl = nullptr, *yl = nullptr;  // [vec_cap][nloc] local inputs and results
   int vec_cap = 0;
+  // concurrent patches (iga_mp_set_concurrent): one stream per patch, forked from and
+  // joined back into the caller's stream by events around every operator
+  bool concurrent = false;
+  std::vector<cudaStream_t> ps;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -742,9 +748,14 @@ int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double
   }
   cudaStream_t s = h->stream;
   LK(launch_mp_gather(s, mp.maps, nvec, active, x, mp.xl));
+  if (mp.concurrent) CK(cudaEventRecord(mp.fork, s));
   for (size_t r = 0; r < mp.patch.size(); ++r) {
     iga_handle* p = mp.patch[r];
     p->stream = s;
+    if (mp.concurrent) {
+      CK(cudaStreamWaitEvent(mp.ps[r], mp.fork, 0));
+      p->stream = mp.ps[r];
+    }
     p->cur_active = h->cur_active;
     const long long l0 = p->nlaunch;
     double* xr = mp.xl + nvec * mp.off[r];
@@ -754,6 +765,11 @@ int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double
                                 : apply_Pinv(p, nvec, active, xr, yr);
     h->nlaunch += p->nlaunch - l0;
     if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+    if (mp.concurrent) {
+      CK(cudaEventRecord(mp.join[r], mp.ps[r]));
+      CK(cudaStreamWaitEvent(s, mp.join[r], 0));
+      p->stream = s;
+    }
   }
   LK(launch_mp_scatter(s, mp.maps, nvec, active, mp.yl, y));
   return IGA_OK;
@@ -1469,6 +1485,9 @@ void iga_destroy(iga_handle* h) {
     for (iga_handle* p : mp->patch) iga_destroy(p);
     dfree(mp->d_gid); dfree(mp->d_off); dfree(mp->d_nr); dfree(mp->d_crow); dfree(mp->d_cent); dfree(mp->d_epatch);
     dfree(mp->xl); dfree(mp->yl);
+    for (cudaStream_t ps : mp->ps) cudaStreamDestroy(ps);
+    for (cudaEvent_t e : mp->join) cudaEventDestroy(e);
+    if (mp->fork) cudaEventDestroy(mp->fork);
     delete mp;
     h->mp = nullptr;
   }
@@ -1856,6 +1875,26 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
     return fail(nullptr, rc, msg);
   }
   *out = h;
+  return IGA_OK;
+}
+
+int iga_mp_set_concurrent(iga_handle* h, int on) {
+  CKS(check_handle(h));
+  if (!h->mp) return fail(h, IGA_EINVAL, "not a multi-patch handle");
+  MpState& mp = *h->mp;
+  if (on && mp.ps.empty()) {
+    CK(cudaEventCreateWithFlags(&mp.fork, cudaEventDisableTiming));
+    for (size_t r = 0; r < mp.patch.size(); ++r) {
+      cudaStream_t ps = nullptr;
+      cudaEvent_t e = nullptr;
+      CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+      mp.ps.push_back(ps);
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      mp.join.push_back(e);
+    }
+  }
+  mp.concurrent = on != 0;
+  drop_step_graph(h);
   return IGA_OK;
 }
 
