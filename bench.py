@@ -570,6 +570,14 @@ def run_multipatch(args, iga, torch, dev, flush, stream):
         e1.record(stream)
         e1.synchronize()
         ms += e0.elapsed_time(e1)
+    # the dominant kernel (the patches' band products of M) over a profiling pass after the
+    # timed region, summed over the patches
+    sysm.profile("band_mass")
+    sysm.step(state, k, rho, dt, 3)
+    prof = sysm.profile_read()
+    sysm.profile("off")
+    hbm, hbm_kind = hbm_peak()
+    roof = roofline("band_mass", "assembled_df", "k_band_df (every patch's M product)", prof, hbm, hbm_kind)
     sysm.close()
     rate = args.multipatch_steps / (ms / 1e3)
     return {"workload": "2 x 2 x 2 glued patches, %d^3 elements each, p = 3, deformed 0.1; N = %d global functions "
@@ -577,7 +585,7 @@ def run_multipatch(args, iga, torch, dev, flush, stream):
             "form": "assembled_df products and banded32 local preconditioners on every patch, additive Schwarz",
             "value": rate, "unit": "steps/s", "ms_per_step": ms / args.multipatch_steps,
             "dof_updates_per_s": rate * N, "pcg_iters_per_solve": stats.iters / max(stats.solves, 1),
-            "gpu_launches": int(stats.launches), "lambda_max": lam, "dt": dt, "setup_s": setup_s,
+            "gpu_launches": int(stats.launches), "lambda_max": lam, "dt": dt, "setup_s": setup_s, "roofline": roof,
             "note": "host-driven loop (no graphs yet); parity in the multi-patch GPU tests"}
 
 

@@ -74,7 +74,9 @@ int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, con
  *         _tol / _guess / _op_form / _precond / _band_config, iga_assemble, iga_ndof,
  *         iga_last_error and iga_destroy work on it; the steps run the host-driven loop
  *         unless iga_set_graphs(h, 1) asks for the captured step (one graph launch per
- *         step, the PCG loop on the device). iga_profile, iga_autotune, the iga_ws_*
+ *         step, the PCG loop on the device). iga_profile selects the kernel class in every
+ *         patch and iga_profile_read returns the sums over the patches (launches, time,
+ *         algorithmic work). iga_autotune, the iga_ws_*
  *         calls, iga_apply_Pinv_noalloc and iga_batch_create refuse it (IGA_EINVAL).
  * Each patch gets a handle over its index box (the interior functions widened to the
  * interface faces), with its own geometry factors, diag(M^(r)) and Kronecker factors.

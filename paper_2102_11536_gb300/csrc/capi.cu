@@ -2082,14 +2082,36 @@ int iga_step_host(iga_handle* h, double* state_host, int k, double rho_inf, doub
 
 int iga_profile(iga_handle* h, int kernel_class) {
   CKS(check_handle(h));
-  CKS(single_patch(h, "iga_profile"));
   if (kernel_class < IGA_PROF_OFF || kernel_class > IGA_PROF_BAND_STIFF) return fail(h, IGA_EINVAL, "bad kernel class");
   h->prof_class = kernel_class;
+  if (h->mp)  // the kernels run in the patches: each brackets its own launches
+    for (iga_handle* p : h->mp->patch) p->prof_class = kernel_class;
   return IGA_OK;
 }
 
 int iga_profile_read(iga_handle* h, double* total_ms, long long* launches, double* flops, double* bytes) {
   CKS(check_handle(h));
+  if (h->mp) {  // the sums over the patches
+    double ms = 0.0, fl = 0.0, by = 0.0;
+    long long n = 0;
+    for (size_t r = 0; r < h->mp->patch.size(); ++r) {
+      iga_handle* p = h->mp->patch[r];
+      p->stream = h->stream;
+      double pm = 0.0, pf = 0.0, pb = 0.0;
+      long long pn = 0;
+      const int rc = iga_profile_read(p, &pm, &pn, &pf, &pb);
+      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+      ms += pm;
+      n += pn;
+      fl += pf;
+      by += pb;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = n;
+    if (flops) *flops = fl;
+    if (bytes) *bytes = by;
+    return IGA_OK;
+  }
   CK(cudaStreamSynchronize(h->stream));
   double ms = 0.0;
   for (auto& pr : h->prof_pending) {
