@@ -1882,16 +1882,29 @@ int iga_mp_set_concurrent(iga_handle* h, int on) {
   CKS(check_handle(h));
   if (!h->mp) return fail(h, IGA_EINVAL, "not a multi-patch handle");
   MpState& mp = *h->mp;
-  if (on && mp.ps.empty()) {
-    CK(cudaEventCreateWithFlags(&mp.fork, cudaEventDisableTiming));
-    for (size_t r = 0; r < mp.patch.size(); ++r) {
-      cudaStream_t ps = nullptr;
-      cudaEvent_t e = nullptr;
-      CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
-      mp.ps.push_back(ps);
-      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      mp.join.push_back(e);
+  if (on && mp.ps.empty()) {  // all or nothing: the vectors stay empty if a creation fails
+    std::vector<cudaStream_t> ps;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (size_t r = 0; e == cudaSuccess && r < mp.patch.size(); ++r) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) ps.push_back(st);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) join.push_back(ev);
     }
+    if (e != cudaSuccess) {
+      for (cudaStream_t st : ps) cudaStreamDestroy(st);
+      for (cudaEvent_t ev : join) cudaEventDestroy(ev);
+      if (fork) cudaEventDestroy(fork);
+      cudaGetLastError();
+      return fail(h, IGA_ECUDA, std::string("iga_mp_set_concurrent: ") + cudaGetErrorString(e));
+    }
+    mp.ps = ps;
+    mp.join = join;
+    mp.fork = fork;
   }
   mp.concurrent = on != 0;
   drop_step_graph(h);
