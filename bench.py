@@ -552,6 +552,7 @@ def run_multipatch(args, iga, torch, dev, flush, stream):
     sysm = iga.MultiPatch(patches, tol=1e-10, precond="banded32", op_form="assembled_df")
     N = sysm.N
     sysm.assemble()
+    sysm.autotune(nvec=k, reps=5)  # every patch picks its band-product launch shape
     lam, tau = sysm.cfl(rho, iters=args.cfl_iters)
     setup_s = time.perf_counter() - t0
     dt = 0.5 * tau

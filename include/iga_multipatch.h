@@ -76,7 +76,8 @@ int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, con
  *         unless iga_set_graphs(h, 1) asks for the captured step (one graph launch per
  *         step, the PCG loop on the device). iga_profile selects the kernel class in every
  *         patch and iga_profile_read returns the sums over the patches (launches, time,
- *         algorithmic work). iga_autotune, the iga_ws_*
+ *         algorithmic work); iga_autotune tunes every patch's band product for its own
+ *         size (the outputs are the last patch's choice). The iga_ws_*
  *         calls, iga_apply_Pinv_noalloc and iga_batch_create refuse it (IGA_EINVAL).
  * Each patch gets a handle over its index box (the interior functions widened to the
  * interface faces), with its own geometry factors, diag(M^(r)) and Kronecker factors.

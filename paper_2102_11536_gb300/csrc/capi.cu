@@ -2438,7 +2438,16 @@ int iga_set_band_config(iga_handle* h, int threads, int nv) {
 
 int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
   CKS(check_handle(h));
-  CKS(single_patch(h, "iga_autotune"));
+  if (h->mp) {  // every patch picks its own shape; the outputs are the last patch's
+    for (size_t r = 0; r < h->mp->patch.size(); ++r) {
+      iga_handle* p = h->mp->patch[r];
+      p->stream = h->stream;
+      const int rc = iga_autotune(p, nvec, reps, threads, nv);
+      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
+    }
+    drop_step_graph(h);
+    return IGA_OK;
+  }
   if (nvec < 1 || nvec > kMaxVec || reps < 1) return fail(h, IGA_EINVAL, "need 1 <= nvec <= 8 and reps >= 1");
   CKS(assemble_band(h));
   CKS(ensure_cg_ws(h, nvec));
