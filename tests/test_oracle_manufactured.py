@@ -90,3 +90,25 @@ def test_forced_wave_on_glued_patches_converges_at_order_p_plus_1(p, rate):
             X = st.step(X, T / n)
         errs.append(fw.l2_error(X[0], T))
     assert math.log2(errs[0] / errs[1]) > rate, errs
+
+
+def test_forced_wave_on_glued_3d_patches_converges_at_order_p_plus_1():
+    """The same on a 3-D domain of 2 x 1 x 2 glued deformed patches ([0, 2] x [0, 1] x [0, 2],
+    N_adj = 4), p = 2."""
+    from oracle import multipatch as mp
+    from workloads import multipatch as WM
+    errs = []
+    for nsub in (3, 6):
+        pts = WM.grid_of_patches((2, 1, 2), nsub, 2, amp=0.1)
+        g = mp.GluedPatches(pts)
+        fw = mf.GluedForcedWave(pts, g, (2.0, 1.0, 2.0), 2 * math.pi, 4)
+        U0, V0 = fw.initial(lambda b: oracle.pcg(g.apply_M, g.apply_Pinv, b, tol=1e-14)[0])
+        lam = oracle.lambda_max_lanczos(g, iters=min(g.N, 200))
+        T = 0.1
+        n = max(20, int(math.ceil(T / (0.5 * math.sqrt(oracle.theta_crit(0.5) / lam)))))
+        st = oracle.Stepper(g, 2, 0.5, tol=1e-13, forcing=fw.forcing)
+        X = st.init(U0, V0)
+        for _ in range(n):
+            X = st.step(X, T / n)
+        errs.append(fw.l2_error(X[0], T))
+    assert math.log2(errs[0] / errs[1]) > 2.7, errs
