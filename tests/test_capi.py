@@ -109,3 +109,18 @@ def test_create_rejects_patches_without_interior_dofs(lib):
     with pytest.raises(iga.IgaError) as e:
         iga.Patch([1, 1, 1], [k1, k1, k1], np.zeros((8, 3)))
     assert e.value.status == iga.EINVAL
+
+
+def test_every_declared_entry_point_is_documented():
+    """Each entry point in include/*.h comes right after a comment block (argument meaning,
+    layout, ownership, errors and the passage it follows); a group of related calls may
+    share one block."""
+    for hdr in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        lines = open(hdr).read().split("\n")
+        last_end = -100
+        for i, line in enumerate(lines):
+            if "*/" in line:
+                last_end = i
+            m = re.match(r"^\s*(?:(?:const|unsigned|signed|long|short)\s+)*\w+\s*\*?\s*(iga_\w+)\s*\(", line)
+            if m:
+                assert i - last_end <= 8, (os.path.basename(hdr), m.group(1))
