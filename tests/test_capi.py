@@ -124,3 +124,14 @@ def test_every_declared_entry_point_is_documented():
             m = re.match(r"^\s*(?:(?:const|unsigned|signed|long|short)\s+)*\w+\s*\*?\s*(iga_\w+)\s*\(", line)
             if m:
                 assert i - last_end <= 8, (os.path.basename(hdr), m.group(1))
+
+
+def test_binding_declares_argument_types_for_every_call():
+    """Every entry point the headers declare, and every one the binding calls, has ctypes
+    argument and result types in the binding (an undeclared call would pass 64-bit pointers
+    as C ints)."""
+    src = open(os.path.join(ROOT, "paper_2102_11536_gb300", "__init__.py")).read()
+    typed = set(re.findall(r'"(iga_\w+)": \(', src))
+    called = set(re.findall(r"\.(iga_\w+)\(", src))
+    assert _declared() <= typed, sorted(_declared() - typed)
+    assert called <= typed, sorted(called - typed)
