@@ -668,3 +668,21 @@ def test_thin_patch_is_the_1d_problem():
     assert np.max(np.abs(lam2 / lam1 - 1)) < 1e-9
     for j in (1, 2, 3):
         assert abs(lam1[j - 1] / (j * math.pi) ** 2 - 1) < 1e-8
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_preconditioner_is_asymptotically_exact(p):
+    """Sec. 5.3: kappa(P^{-1} M) -> 1 as h -> 0 for the diagonal-scaled Kronecker
+    preconditioner on a deformed patch; measured, kappa - 1 about halves with every
+    refinement (O(h))."""
+    excess = []
+    for nel in (8, 16, 32):
+        kn = [W.open_uniform_knots(nel, p)] * 2
+        P = oracle.Patch([p, p], kn, W.control_net(kn, [p, p], 0.1))
+        ops = oracle.Operators(P)
+        Md = P.band_to_dense(ops.M)
+        Pinv = np.column_stack([ops.apply_Pinv(e) for e in np.eye(ops.N)])
+        ev = np.sort(np.real(np.linalg.eigvals(Pinv @ Md)))
+        excess.append(ev[-1] / ev[0] - 1.0)
+    assert excess[1] < 0.65 * excess[0] and excess[2] < 0.65 * excess[1], excess
+    assert excess[2] < 0.03
