@@ -61,7 +61,7 @@ METRIC = "time-steps/sec and PCG iters/step, FP64 vs mixed/learned, at ≤1e-8 r
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clock (2 FMA) x 2.07 GHz. The
 # per-SM unit count is inferred from an FMA-chain microbenchmark that reached
-# 1.201 TFLOP/s at ~1.98 GHz (profiles/fp64_peak_probe.md).
+# 1.201 TFLOP/s at ~1.98 GHz (the FP64 probe's profile summary).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 ERR_LIMIT = 1e-8
@@ -97,10 +97,10 @@ FORMS = [
 
 # DRAM traffic per launch of a profiled kernel from an ncu capture, keyed by
 # (kernel, sha256 of the kernel's source file, first 16 hex): a capture only
-# counts while the source it was taken on is unchanged (profiles/*.md).
+# counts while the source it was taken on is unchanged (summaries under profiles/).
 NCU_TRAFFIC = {
-    ("band_mass", "6428c7f922f0f6eb"): 373.9e6,   # k_band_spmv<2, 64>, 2-vector launch (profiles/k_band_spmv_cube64_p3.md)
-    ("band_mass_df", "089aa6988b2aaa18"): 390.2e6,  # k_band_df_tm<3, 2>, 2-vector launch (profiles/k_band_df_tm_cube64_p3.md)
+    ("band_mass", "6428c7f922f0f6eb"): 373.9e6,   # k_band_spmv<2, 64>, 2-vector launch on cube64_p3
+    ("band_mass_df", "089aa6988b2aaa18"): 390.2e6,  # k_band_df_tm<3, 2>, 2-vector launch on cube64_p3
     # k_mid_mass<4>, 1-vector launch, captured at file hash 618d068dc16a5b19; the file's later edit
     # touched only launch_geometry's host code (k_mid_mass byte-identical), hence the new key
     ("mass", "2b7c940689f4c144"): 186.69e6,
@@ -303,7 +303,7 @@ def roofline(prof_class, op_form, kdesc, prof, hbm, hbm_kind):
                 "peak_kind": hbm_kind, **common,
                 "fp64_equivalent_view": {"achieved_tflops": tfl, "fp64_peak_tflops": FP64_PEAK_TFLOPS}}
     return {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": tfl / FP64_PEAK_TFLOPS, "peak_kind": "FP64 FMA units x max SM clock (derived; see DESIGN.md)",
+            "frac": tfl / FP64_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 4 FP64 flop/clock x 2.07 GHz max SM clock",
             **common, "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind}}
 
 

@@ -206,8 +206,13 @@ int iga_apply_Pinv(iga_handle* h, int nvec, const double* x, double* y);
  * IGA_EINVAL with a message and do nothing.
  *
  * Set-up: the first call on each device looks up the device address of the
- * scratch array (with that device current). Make that first call before any
- * stream capture. Every call on a device shares the one array and leaves the
+ * scratch array (with that device current) and keeps it together with the id of
+ * the device's context. Make that first call before any stream capture. After a
+ * cudaDeviceReset the array lives in a new context at a new address: the first
+ * call there (again before any capture) looks it up anew; handles created before
+ * the reset are void and must be recreated, as for every other call.
+ * With the 16-bit tensor-core preconditioners the call waits for its kernels and
+ * returns IGA_ECUDA if one of their bounded waits ran out. Every call on a device shares the one array and leaves the
  * last call's values in it (nothing in it needs to start at zero), so calls
  * whose kernels overlap on the GPU -- from different streams, threads or
  * handles on the same device -- race and corrupt each other; serialise them.

@@ -19,7 +19,7 @@ Contents and the passage each follows:
   * Stepper.init()                   -- initial high-order data (Sec. 3, after eq. 4aup)
   * theta_crit()                     -- stability limit from eq. charact at lambda = -1
   * modal_response(), spectral_radius() -- the scheme on one mode (Sec. 6.2), stability diagram
-Readings of passages the paper leaves silent or garbled are listed in the design doc.
+Where the paper is silent or garbled, the reading taken is stated beside the code that uses it.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py.
 """
@@ -434,7 +434,8 @@ class Stepper:
         X_{s_j} <- T_{s_j} + P_j,  X_{s_j-1} <- T_{s_j-1} + gamma_j tau P_j,
         X_{s_j-2} <- T_{s_j-2} + beta_j tau^2 P_j.
     (Z_j is the paper's L^{s_j}(A_n)^{alpha_j} = T_{s_j} + alpha_j P_{n,j}.) The stiffness
-    argument Y_j is the reading that gives order 2k; see the design doc."""
+    argument Y_j is the reading that gives order 2k (eq. ho1 taken literally, K U_n for
+    every block, gives order 1 and is unstable for k >= 2)."""
 
     def __init__(self, ops, k: int, rho: float, tol=1e-10, max_iter=500, guess="zero", params=None,
                  damping=None, forcing=None, t0=0.0):
@@ -613,13 +614,3 @@ def lambda_max_lanczos(ops: Operators, iters=60, seed=0, tol=1e-12, rtol=1e-12):
         vp, v = v, w / beta
     return est
 
-
-def lambda_max_power(ops: Operators, iters=200, seed=0, tol=1e-12):
-    """Largest eigenvalue of M^{-1}K by power iteration (each step one K product and one
-    PCG solve with M), returned as the Rayleigh quotient x^T K x / x^T M x."""
-    rng = np.random.default_rng(seed)
-    x = rng.standard_normal(ops.N)
-    for _ in range(iters):
-        y, _, _ = pcg(ops.apply_M, ops.apply_Pinv, ops.apply_K(x), None, tol)
-        x = y / np.linalg.norm(y)
-    return float((x @ ops.apply_K(x)) / (x @ ops.apply_M(x)))

@@ -1439,7 +1439,9 @@ int handle_fail(iga_handle* h, int code, const std::string& msg) { return fail(h
 
 int pinv_with_scratch(iga_handle* h, int nvec, const double* x, double* y, double* t1, double* t2) {
   CKS(single_patch(h, "iga_apply_Pinv_noalloc"));
-  return fd_apply(h, nvec, nullptr, x, y, t1, t2);
+  CKS(fd_apply(h, nvec, nullptr, x, y, t1, t2));
+  // a tensor-core mode product whose wait ran out is reported here, not by the next call
+  return check_tc_error(h);
 }
 
 }  // namespace iga

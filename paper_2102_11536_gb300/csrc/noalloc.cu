@@ -13,22 +13,62 @@ namespace {
 __device__ __align__(256) double g_pinv_scratch[2 * iga::kNoAllocMaxElems];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;  // driver context the address belongs to (0: none yet)
+  double* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mutex;
+
+// Process-unique id of the current driver context (cuCtxGetId ids are never reused
+// within a process), looked up through the runtime's driver entry points.
+cudaError_t current_context_id(unsigned long long* id) {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1 ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+    get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  unsigned long long v = 0;
+  if (get_id(ctx, &v) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  *id = v;
+  return cudaSuccess;
+}
 
 // Device address of g_pinv_scratch on `device` (which must be current). The host
 // name g_pinv_scratch is only a stand-in for the symbol; the address a kernel can
-// use comes from cudaGetSymbolAddress, once per device.
+// use comes from cudaGetSymbolAddress, once per device and context: a device reset
+// ends the context (and the module holding the array), so the next call looks the
+// address up again in the new one.
 cudaError_t scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[device]) {
+  ScratchAddr& c = g_scratch_addr[device];
+  unsigned long long id = 0;
+  if (c.addr) {
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+  }
+  if (!c.addr || c.ctx_id != id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_pinv_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = static_cast<double*>(p);
+    e = current_context_id(&id);  // the context exists now
+    if (e != cudaSuccess) return e;
+    c.addr = static_cast<double*>(p);
+    c.ctx_id = id;
   }
-  *out = g_scratch_addr[device];
+  *out = c.addr;
   return cudaSuccess;
 }
 
