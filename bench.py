@@ -3,41 +3,42 @@
 isogeometric step on GB300, with PCG iterations per step, for the FP64 form of
 the method and its faster forms, at <= 1e-8 relative error.
 
-Workload (default): 3-D unit cube mapped by x + 0.1 sin(pi x) sin(pi y) sin(pi z)
-in each coordinate, B-splines p = 3 (C^2) on 64^3 elements (N = 274625 interior
-dofs), k = 2 (4th order), rho_inf = 0.5, dt = 0.5 tau_crit, standing-wave initial
-data, PCG to relative residual 1e-10 with the fast-diagonalisation
-preconditioner. One "step" is one time step of the method: Taylor predictor,
-batched K product over the k vectors, k mass solves by PCG, fused stage update.
+Workload (default, the largest configuration): 3-D unit cube mapped by
+x + 0.1 sin(pi x) sin(pi y) sin(pi z) in each coordinate, B-splines p = 4 (C^3) on
+128^3 elements (N = 2 197 000 interior dofs, 262 M Gauss points), k = 3 (6th
+order), rho_inf = 0.5, dt = 0.5 tau_crit, initial displacement a sum of 16 seeded
+Fourier modes, PCG to relative residual 1e-10. One "step" is one time step of the
+method: Taylor predictor, batched K product over the k vectors, k mass solves by
+PCG, fused stage update.
 
-Forms measured (all FP64 state, FP64 PCG residuals and dot products, same tol):
-  fp64_paper      matrix-free sum-factorised K, M; FP64 preconditioner; zero guess
-                  (the paper's PCG setting)
-  fp64_assembled  assembled band K, M; FP64 preconditioner; zero guess
-  mixed_fp32      assembled band K, M; FP32 preconditioner (flexible PCG); zero guess
+Forms measured (FP64 state, FP64 PCG residuals and dot products, same tol):
+  fp64_paper      matrix-free sum-factorised K, M; FP64 fast-diagonalisation
+                  preconditioner; zero guess (the paper's PCG setting)
+  fp64_assembled  assembled band K, M; FP64 fast-diagonalisation preconditioner
   fp64_banded     assembled band K, M; FP64 preconditioner with the Kronecker solve by band
-                  Cholesky along each direction (O(N)) instead of fast diagonalisation; plain PCG
-  mixed_banded32  the same Kronecker solve in FP32 (flexible PCG)
+                  Cholesky along each direction (O(N)); plain PCG. FP64 throughout.
+  mixed_fp32      assembled band K, M; FP32 fast diagonalisation (flexible PCG)
+  mixed_banded32  the band-Cholesky Kronecker solve in FP32 (flexible PCG)
   mixed_taylor    as mixed_banded32 with the Taylor predictor as initial guess
-  mixed_bf16      assembled band K, M; BF16 preconditioner on the tensor cores (tcgen05,
+  mixed_bf16      assembled band K, M; BF16 mode products on the tensor cores (tcgen05,
                   FP32 accumulation; flexible PCG); zero guess
   mixed_fp16      as mixed_bf16 with FP16 operands (each line scaled by a power of two)
   mixed_extrap    as mixed_banded32 with 2 Z^{n-1} - Z^{n-2} as initial guess
-  mixed_learned   as mixed_banded32 with the learned warm start: the BF16 convolutional
-                  network, trained by the library's own kernels on the solves of the
-                  first --train-steps steps (set-up, not timed), corrects the
-                  extrapolated guess
-  mixed_fp32_hostloop  mixed_fp32 with the PCG loop driven from the host (one
-                  synchronisation per iteration) instead of the captured graph
+  mixed_fp32_hostloop  mixed_fp32 with the PCG loop driven from the host
   df_banded       band K, M held as pairs of FP32 numbers (48 significant bits, one
                   power-of-two scale per matrix and per vector), products in double-FP32
-                  arithmetic (error-free FP32 products, TwoSum accumulation: a few 2^-48 of
-                  sum |a||x| per row); FP64 band-Cholesky Kronecker preconditioner, plain PCG
+                  arithmetic (error-free FP32 products, TwoSum accumulation); FP64
+                  band-Cholesky Kronecker preconditioner, plain PCG
   df_banded32     the same with the FP32 Kronecker solve (flexible PCG)
-Every other form replays one captured CUDA graph per step whose PCG loop runs on
-the device (a conditional while node).
+Every form but the host-loop one replays one captured CUDA graph per step whose PCG
+loop runs on the device (a conditional while node).
 The headline value is the fastest form whose U and V stay within 1e-8 (relative
-L2) of the fp64_paper run after the same steps from the same initial state.
+L2) of the fp64_paper run after the same steps from the same initial state; the
+line names its arithmetic in "dtype" and carries the FP64 forms' rates in "fp64".
+Secondary legs: the 64^3 p = 3 k = 2 configuration (headline and FP64 forms), the
+learned warm start on the 96^3 p = 3 configuration (its own configuration), the
+48-patch batch, the damped and forced general model, and the conforming
+multi-patch system.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -95,15 +96,35 @@ FORMS = [
      "k_band_df (double-FP32 band product, mass; with the scaling and split of x)"),
 ]
 
+DEFAULT_FORMS = [f[0] for f in FORMS if f[0] != "mixed_learned"]  # the learned form has its own leg
+
+
+def arithmetic(opts):
+    """What a form computes in, for the line's "dtype" (the state, the PCG residuals and
+    inner products and the stage updates are FP64 in every form)."""
+    prec = {"fp64": "f64 fast-diagonalisation preconditioner",
+            "banded": "f64 band-Cholesky Kronecker preconditioner",
+            "fp32": "f32 fast-diagonalisation preconditioner",
+            "banded32": "f32 band-Cholesky Kronecker preconditioner",
+            "bf16": "bf16 x f32-accumulate tcgen05 preconditioner mode products",
+            "fp16": "fp16 x f32-accumulate tcgen05 preconditioner mode products"}[opts["precond"]]
+    ops = {"matrix_free": "f64 matrix-free K and M", "assembled": "f64 band K and M",
+           "assembled_df": "df32 band K and M (pairs of f32, ~48-bit products)"}[opts["op_form"]]
+    if opts["op_form"] != "assembled_df" and opts["precond"] in ("fp64", "banded"):
+        return "f64"
+    return "f64 state, residuals, dots and stage updates; %s; %s" % (ops, prec)
+
+
 # DRAM traffic per launch of a profiled kernel from an ncu capture, keyed by
-# (kernel, sha256 of the kernel's source file, first 16 hex): a capture only
-# counts while the source it was taken on is unchanged (summaries under profiles/).
+# (kernel class, sha256 of the kernel's source file (first 16 hex), workload, vectors
+# in the launch): a capture only counts while the source it was taken on is
+# unchanged (summaries under profiles/).
 NCU_TRAFFIC = {
-    ("band_mass", "6428c7f922f0f6eb"): 373.9e6,   # k_band_spmv<2, 64>, 2-vector launch on cube64_p3
-    ("band_mass_df", "089aa6988b2aaa18"): 390.2e6,  # k_band_df_tm<3, 2>, 2-vector launch on cube64_p3
-    # k_mid_mass<4>, 1-vector launch, captured at file hash 618d068dc16a5b19; the file's later edit
-    # touched only launch_geometry's host code (k_mid_mass byte-identical), hence the new key
-    ("mass", "2b7c940689f4c144"): 186.69e6,
+    ("band_mass", "6428c7f922f0f6eb", "cube64_p3", 2): 373.9e6,   # k_band_spmv<2, 64>
+    ("band_mass_df", "089aa6988b2aaa18", "cube64_p3", 2): 390.2e6,  # k_band_df_tm<3, 2>
+    # k_mid_mass<4>, captured at file hash 618d068dc16a5b19; the file's later edit touched
+    # only launch_geometry's host code (k_mid_mass byte-identical), hence the new key
+    ("mass", "2b7c940689f4c144", "cube64_p3", 1): 186.69e6,
 }
 
 
@@ -113,10 +134,16 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cube64_p3")
+    ap.add_argument("--config", default="cube128_p4")
     ap.add_argument("--rho", type=float, default=0.5)
     ap.add_argument("--cfl-iters", type=int, default=100)
-    ap.add_argument("--forms", default=",".join(f[0] for f in FORMS))
+    ap.add_argument("--forms", default=",".join(DEFAULT_FORMS))
+    ap.add_argument("--secondary", default="cube64_p3",
+                    help="second configuration timed with the headline and FP64 forms ('' = skip)")
+    ap.add_argument("--learned-config", default="cube96_p3",
+                    help="configuration of the learned warm-start leg ('' = skip)")
+    ap.add_argument("--sample-nel", type=int, default=24,
+                    help="elements per direction of the oracle's bounded sample of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--train-steps", type=int, default=200, help="steps whose solves train the warm start")
@@ -248,10 +275,23 @@ def oracle_setup(w):
     return st, X, setup_s, oracle.num_threads()
 
 
-def run_cpu_baseline(w, dt, target_s):
-    """The oracle as it stands on the host cores: M and K assembled once (not
-    timed), then whole time steps timed until about target_s seconds."""
-    st, X, setup_s, cores = oracle_setup(w)
+def sample_workload(w, nel):
+    """The bounded sample of a workload the oracle is timed on: the same discretisation
+    (degrees, geometry, k, rho_inf, initial data, tolerance) on nel elements per direction.
+    The oracle's step costs O(N) (band products, Kronecker solves, vector updates), so its
+    rate scales to the full workload by N_sample / N."""
+    import dataclasses
+    if all(v <= nel for v in w.nel):
+        return w
+    return dataclasses.replace(w, name="%s on %s elements" % (w.name, "x".join([str(nel)] * w.d)),
+                               nel=tuple([nel] * w.d))
+
+
+def run_cpu_baseline(w, ws, dt, target_s):
+    """The oracle as it stands on the host cores, on the bounded sample ws of the workload
+    w: M and K assembled once (not timed), then whole time steps timed until about
+    target_s seconds; steps/s scaled to w by N_sample / N."""
+    st, X, setup_s, cores = oracle_setup(ws)
     t0 = time.perf_counter()
     X = st.step(X, dt)
     first = time.perf_counter() - t0
@@ -260,9 +300,12 @@ def run_cpu_baseline(w, dt, target_s):
     for _ in range(nsteps):
         X = st.step(X, dt)
     el = time.perf_counter() - t0
-    return {"value": nsteps / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": "%d time steps of %s on %d host threads after one warm-up step; M and K assembled once "
-                      "(%.0f s, not timed)" % (nsteps, w.name, cores, setup_s),
+    scale = ws.ndof / w.ndof
+    return {"value": nsteps / el * scale, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d time steps of %s (N = %d) on %d host threads after one warm-up step, %.2f steps/s there, "
+                      "scaled to N = %d by %d/%d (the oracle's step is O(N)); M and K assembled once (%.0f s, not "
+                      "timed)" % (nsteps, ws.name, ws.ndof, cores, nsteps / el, w.ndof, ws.ndof, w.ndof, setup_s),
+            "dof_updates_per_s": nsteps / el * ws.ndof,
             "iters_per_step": sum(sum(i) for i in st.iters[1:]) / nsteps}, X, nsteps + 1
 
 
@@ -280,31 +323,92 @@ def select_form(patch, opts, band_cfgs, k):
         patch.set_band_config(*band_cfgs[form])
 
 
-def roofline(prof_class, op_form, kdesc, prof, hbm, hbm_kind):
-    """Roofline of the profiled kernel class: the FP64 kernels against the FP64 FMA
-    peak (ALU-bound), the double-FP32 band product against the measured HBM copy
-    bandwidth (its algorithmic bytes: the split coefficients and the vectors)."""
+def band_slots(w):
+    """Slots of the stored upper half of the symmetric (2p+1)^d band (the centre included)."""
+    S = 1
+    for p in w.p:
+        S *= 2 * p + 1
+    return (S + 1) // 2
+
+
+def method_bytes(w, mass=True):
+    """Algorithmic bytes of one operator product by the method's matrix-free sum
+    factorisation at the Gauss points: the geometric factors at every point (mass: W,
+    8 B; stiffness: the 6 entries of the symmetric W DF^-1 DF^-T, 48 B) and 16 B per dof
+    and vector (input read, output written). Returns (factor bytes, bytes per vector)."""
+    Qt = 1
+    for nel, p in zip(w.nel, w.p):
+        Qt *= nel * (p + 1)
+    return Qt * (8 if mass else 48), 16 * w.ndof
+
+
+def roofline(prof_class, opts, kdesc, prof, hbm, hbm_kind, w):
+    """Roofline of the profiled kernel class. Band products (FP64 or double-FP32): their
+    achieved rate in the method's algorithmic bytes (method_bytes: the factor W and the
+    vectors, whatever the form reads) against the measured HBM copy bandwidth, with the
+    band's own bytes beside it; the matrix-free FP64 kernels: algorithmic flops against
+    the FP64 FMA peak (ALU-bound)."""
     prof_ms, prof_n, prof_flops, prof_bytes = prof
-    df = op_form == "assembled_df"
+    df = opts["op_form"] == "assembled_df"
     key = prof_class + ("_df" if df else "")
     sha = source_sha(KERNEL_SOURCE[key])
-    gbs = prof_bytes / (prof_ms * 1e-3) / 1e9 if prof_ms > 0 else 0.0
-    tfl = prof_flops / (prof_ms * 1e-3) / 1e12 if prof_ms > 0 else 0.0
-    common = {
-        "kernel": kdesc,
-        "traffic": NCU_TRAFFIC.get((key, sha)),
-        "launches": prof_n,
-        "avg_launch_ms": prof_ms / max(prof_n, 1),
-        "algorithmic_flops_per_launch": prof_flops / max(prof_n, 1),
-        "algorithmic_bytes_per_launch": prof_bytes / max(prof_n, 1),
-    }
-    if df:
-        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "peak_kind": hbm_kind, **common,
-                "fp64_equivalent_view": {"achieved_tflops": tfl, "fp64_peak_tflops": FP64_PEAK_TFLOPS}}
-    return {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": tfl / FP64_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 4 FP64 flop/clock x 2.07 GHz max SM clock",
-            **common, "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind}}
+    n = max(prof_n, 1)
+    sec = prof_ms * 1e-3 if prof_ms > 0 else float("inf")
+    tfl = prof_flops / sec / 1e12
+    common = {"kernel": kdesc, "launches": prof_n, "avg_launch_ms": prof_ms / n,
+              "algorithmic_flops_per_launch": prof_flops / n}
+    if opts["op_form"] == "matrix_free":
+        gbs = prof_bytes / sec / 1e9
+        return {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS,
+                "peak_kind": "derived: 152 SMs x 4 FP64 flop/clock x 2.07 GHz max SM clock",
+                "traffic": NCU_TRAFFIC.get((key, sha, w.name, 1)),
+                "algorithmic_bytes_per_launch": prof_bytes / n, **common,
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind}}
+    N = w.ndof
+    H = band_slots(w)
+    vec_sum = (prof_bytes / 8.0 - H * N * prof_n) / (2.0 * N)  # vectors over all launches
+    fac, per_vec = method_bytes(w, mass=prof_class == "band_mass")
+    alg = prof_n * fac + per_vec * vec_sum
+    gbs = alg / sec / 1e9
+    band_gbs = prof_bytes / sec / 1e9
+    vpl = vec_sum / n
+    out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_kind": hbm_kind,
+           "algorithmic_bytes_per_launch": alg / n,
+           "algorithmic_bytes_basis": "the method's sum factorisation: W at %d Gauss points (8 B each) + 16 B per "
+                                      "dof and vector; %.2f vectors per launch on average" % (fac // 8, vpl),
+           "traffic": None, **common,
+           "band_view": {"bytes_per_launch": prof_bytes / n, "achieved_gbs": band_gbs, "frac": band_gbs / hbm,
+                         "note": "the bytes the assembled band form reads (%d slots of 8 B per row + vectors): "
+                                 "%.2fx the method's" % (H, prof_bytes / max(alg, 1.0))},
+           "fp64_equivalent_view": {"achieved_tflops": tfl, "fp64_peak_tflops": FP64_PEAK_TFLOPS}}
+    # an ncu capture of a launch with `nv` vectors, scaled to the average launch by the band
+    # bytes it reads (the traffic follows them: coefficients once, vectors once per vector)
+    for nv in range(1, 9):
+        t = NCU_TRAFFIC.get((key, sha, w.name, nv))
+        if t is not None:
+            cap = 8.0 * (H * N + 2 * nv * N)
+            out["traffic"] = t * (prof_bytes / n) / cap
+            out["traffic_basis"] = "ncu dram bytes of one %d-vector launch (%.4g B) scaled to the average launch" % (
+                nv, t)
+            break
+    return out
+
+
+def mp_roofline(prof, hbm, hbm_kind, nloc, qt_total, H):
+    """Roofline of every patch's double-FP32 M product in the multi-patch system, in the
+    method's algorithmic bytes (W at every patch's Gauss points, 16 B per box entry and
+    vector), with the band's own bytes beside it."""
+    ms, n, _, by = prof
+    n = max(n, 1)
+    sec = ms * 1e-3 if ms > 0 else float("inf")
+    vec_sum = (by / 8.0 - H * nloc * n) / (2.0 * nloc)
+    alg = n * qt_total * 8 + 16 * nloc * vec_sum
+    gbs = alg / sec / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_kind": hbm_kind,
+            "kernel": "k_band_df (every patch's M product, with the split)", "launches": n,
+            "avg_launch_ms": ms / n, "algorithmic_bytes_per_launch": alg / n, "traffic": None,
+            "band_view": {"bytes_per_launch": by / n, "achieved_gbs": by / sec / 1e9, "frac": by / sec / 1e9 / hbm}}
 
 
 def time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class):
@@ -336,11 +440,11 @@ def time_form(patch, iga, torch, state, w, dt, args, stream, flush, prof_class):
     return total_ms, stats, prof
 
 
-def train_warm_start(patch, torch, w, dt, state, u0, v0, args):
+def train_warm_start(patch, torch, w, dt, state, u0, v0, args, op_form="assembled_df", precond="banded32"):
     """Record the solves of the first args.train_steps steps (after two steps of
     history) and train the warm-start network on them; returns a summary."""
-    patch.set_op_form("assembled")
-    patch.set_precond("banded32")
+    patch.set_op_form(op_form)
+    patch.set_precond(precond)
     patch.set_guess("learned")
     patch.set_graphs(True)
     patch.state_init(w.k, u0, v0, state)
@@ -357,7 +461,126 @@ def train_warm_start(patch, torch, w, dt, state, u0, v0, args):
     return {"recorded_steps": args.train_steps, "samples": nrec, "epochs": args.train_epochs, "lr": args.train_lr,
             "loss_per_epoch": losses, "lr_schedule": "cosine decay to 0 over the updates",
             "record_s": rec_s, "train_s": train_s,
-            "note": "set-up outside the timed region; the timed run starts from the initial state"}
+            "note": "set-up outside the timed region; the timed runs start from the initial state"}
+
+
+def timed_steps(patch, iga, torch, state, w, dt, nsteps, warmup, stream, flush):
+    """nsteps steps timed with CUDA events on the library's stream, L2 flushed before each."""
+    for _ in range(warmup):
+        patch.step(state, w.k, w.rho, dt, 1)
+    torch.cuda.synchronize()
+    stats = iga.Stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(nsteps):
+        flush.add_(1.0)
+        e0.record(stream)
+        patch.step(state, w.k, w.rho, dt, 1, stats)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms, stats
+
+
+def run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts):
+    """The 64^3 p = 3 k = 2 configuration with the headline form and the two FP64 forms,
+    each from the same initial state; errors of U and V against the fp64_paper run."""
+    import numpy as np
+    w = workloads.config(args.secondary)
+    w.rho = args.rho
+    g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, device=dev.index or 0)
+    lam, tc = g.cfl(w.rho, iters=args.cfl_iters)
+    dt = w.cfl_fraction * tc
+    g.assemble()
+    U0, V0 = w.initial()
+    u0 = torch.from_numpy(U0).to(dev)
+    v0 = torch.from_numpy(V0).to(dev)
+    state = torch.empty(3 * w.k * g.N, dtype=torch.float64, device=dev)
+    cfgs, out, finals = {}, {}, {}
+    forms = [("fp64_paper", dict(op_form="matrix_free", precond="fp64", guess="zero")),
+             ("fp64_banded", dict(op_form="assembled", precond="banded", guess="zero"))]
+    if head not in ("fp64_paper", "fp64_banded"):
+        forms.append((head, hopts))
+    for name, opts in forms:
+        select_form(g, opts, cfgs, w.k)
+        g.set_graphs(opts.get("graphs", True) and not args.no_graphs)
+        g.state_init(w.k, u0, v0, state)
+        ms, st = timed_steps(g, iga, torch, state, w, dt, args.steps, args.warmup, stream, flush)
+        finals[name] = state.view(3 * w.k, g.N)[:2].cpu().numpy()
+        out[name] = {"value": args.steps / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms / args.steps,
+                     "pcg_iters_per_step": st.iters / args.steps, "pcg_iters_per_solve": st.iters / max(st.solves, 1),
+                     "dtype": arithmetic(opts)}
+    ref = finals["fp64_paper"]
+    for name in out:
+        out[name]["rel_err_vs_fp64_paper"] = {
+            v: float(np.linalg.norm(finals[name][r] - ref[r]) / np.linalg.norm(ref[r])) for r, v in ((0, "U"), (1, "V"))}
+    g.close()
+    return {"workload": workload_desc(w), "ndof": w.ndof, "dt": dt, "lambda_max": lam, "steps": args.steps,
+            "forms": out}
+
+
+def run_learned(args, iga, torch, workloads, dev, stream, flush):
+    """The learned warm start on its own configuration (96^3 elements, p = 3, k = 2,
+    16 random modes): the network is trained on the solves of the first
+    args.train_steps steps (set-up), then the zero, extrapolated and learned guesses are
+    timed from the initial state with the headline arithmetic."""
+    import numpy as np
+    w = workloads.config(args.learned_config)
+    w.rho = args.rho
+    g = iga.Patch(w.p, w.knots, w.ctrl(), tol=w.tol, device=dev.index or 0)
+    lam, tc = g.cfl(w.rho, iters=args.cfl_iters)
+    dt = w.cfl_fraction * tc
+    g.assemble()
+    U0, V0 = w.initial()
+    u0 = torch.from_numpy(U0).to(dev)
+    v0 = torch.from_numpy(V0).to(dev)
+    state = torch.empty(3 * w.k * g.N, dtype=torch.float64, device=dev)
+    opts = dict(op_form="assembled_df", precond="banded32")
+    cfgs = {}
+    select_form(g, dict(opts, guess="zero"), cfgs, w.k)
+    train = train_warm_start(g, torch, w, dt, state, u0, v0, args, **opts)
+    out, finals = {}, {}
+    for guess in ("zero", "extrap", "learned"):
+        g.set_guess(guess)
+        g.state_init(w.k, u0, v0, state)
+        ms, st = timed_steps(g, iga, torch, state, w, dt, args.steps, args.warmup, stream, flush)
+        finals[guess] = state.view(3 * w.k, g.N)[:2].cpu().numpy()
+        out[guess] = {"value": args.steps / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms / args.steps,
+                      "pcg_iters_per_solve": st.iters / max(st.solves, 1),
+                      "mean_initial_relres": st.init_relres_sum / max(st.solves, 1)}
+    ref = finals["zero"]
+    for guess in out:
+        out[guess]["rel_err_vs_zero_guess"] = {
+            v: float(np.linalg.norm(finals[guess][r] - ref[r]) / np.linalg.norm(ref[r])) for r, v in ((0, "U"), (1, "V"))}
+    g.close()
+    return {"workload": workload_desc(w), "ndof": w.ndof, "dt": dt, "steps": args.steps,
+            "arithmetic": arithmetic(opts | {"guess": "zero"}), "guesses": out, "training": train,
+            "note": "the learned guess feeds PCG, which still iterates to the same tolerance; parity against the "
+                    "oracle in the full-size GPU tests"}
+
+
+def sample_parity(args, iga, torch, dev, ws, dt, nst, Xo, forms):
+    """The GPU forms on the oracle's sample workload, the same steps from the same initial
+    state: relative L2 of U and V against the oracle."""
+    import numpy as np
+    g = iga.Patch(ws.p, ws.knots, ws.ctrl(), tol=ws.tol, device=dev.index or 0)
+    g.assemble()
+    U0, V0 = ws.initial()
+    u0 = torch.from_numpy(U0).to(dev)
+    v0 = torch.from_numpy(V0).to(dev)
+    state = torch.empty(3 * ws.k * g.N, dtype=torch.float64, device=dev)
+    out, cfgs = {}, {}
+    for name, opts in forms:
+        select_form(g, opts, cfgs, ws.k)
+        g.set_graphs(opts.get("graphs", True))
+        g.state_init(ws.k, u0, v0, state)
+        g.step(state, ws.k, ws.rho, dt, nst)
+        Xg = state.view(3 * ws.k, g.N).cpu().numpy()
+        out[name] = {v: float(np.linalg.norm(Xg[r] - Xo[r]) / np.linalg.norm(Xo[r])) for r, v in ((0, "U"), (1, "V"))}
+    g.close()
+    return {"workload": workload_desc(ws), "steps": nst, "tol": ws.tol, "rel_l2_vs_oracle": out,
+            "note": "same dt, tolerance and initial data on both sides; full-size parity in the GPU tests"}
 
 
 def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
@@ -578,8 +801,7 @@ def run_multipatch(args, iga, torch, dev, flush, stream):
     prof = sysm.profile_read()
     sysm.profile("off")
     hbm, hbm_kind = hbm_peak()
-    roof = roofline("band_mass", "assembled_df", "k_band_df (every patch's M product)", prof, hbm, hbm_kind)
-    roof["traffic"] = None  # the recorded ncu traffic is the 64^3 headline launch's, not these patches'
+    roof = mp_roofline(prof, hbm, hbm_kind, sysm.nloc, 8 * (4 * args.multipatch_nel) ** 3, 172)
     sysm.close()
     rate = args.multipatch_steps / (ms / 1e3)
     return {"workload": "2 x 2 x 2 glued patches, %d^3 elements each, p = 3, deformed 0.1; N = %d global functions "
@@ -666,11 +888,12 @@ def run_ours(args):
             "gpu_launches": int(stats.launches),
             "precond_ms_per_application": pc_ms / max(pc_n, 1),
             "precond_applications_per_step": pc_n / 5.0,
-            "roofline": roofline(prof_class, opts["op_form"], kdesc, prof, hbm, hbm_kind),
+            "roofline": roofline(prof_class, opts, kdesc, prof, hbm, hbm_kind, w),
         }
     clocks = sampler.stop()
     ref = finals.get("fp64_paper")
     for name, r in results.items():
+        r["dtype"] = arithmetic(r["options"])
         if ref is not None:
             r["rel_err_vs_fp64_paper"] = {
                 "U": float(np.linalg.norm(finals[name][0] - ref[0]) / np.linalg.norm(ref[0])),
@@ -679,6 +902,11 @@ def run_ours(args):
           if "rel_err_vs_fp64_paper" not in r or max(r["rel_err_vs_fp64_paper"].values()) <= ERR_LIMIT]
     head = max(ok, key=lambda n: results[n]["value"])
     hopts = results[head]["options"]
+    fp64 = {n: {"value": results[n]["value"], "unit": "steps/s", "ms_per_step": results[n]["ms_per_step"],
+                "pcg_iters_per_step": results[n]["pcg_iters_per_step"],
+                "pcg_iters_per_solve": results[n]["pcg_iters_per_solve"],
+                "headline_speedup": results[head]["value"] / results[n]["value"]}
+            for n in ("fp64_paper", "fp64_banded", "fp64_assembled") if n in results}
 
     # end to end through the public C API on host memory, headline form: every step
     # copies the state in from pinned host memory and the new state back out.
@@ -700,6 +928,12 @@ def run_ours(args):
     e2e_rate = world * args.steps / e2e_s
     general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, hopts,
                           band_cfgs) if args.general else None
+    patch.close()
+    del state, host
+    torch.cuda.empty_cache()
+    secondary = (run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts)
+                 if args.secondary and rank == 0 else None)
+    learned = run_learned(args, iga, torch, workloads, dev, stream, flush) if args.learned_config and rank == 0 else None
     batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
     mp_res = (run_multipatch(args, iga, torch, dev, flush, stream)
               if args.multipatch_steps > 0 and world == 1 else None)
@@ -726,7 +960,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": h["dtype"],
         "data": "synthetic",
         "config": {
             "workload": workload_desc(w),
@@ -737,13 +971,15 @@ def run_ours(args):
             "lambda_max": lam,
             "form": head,
             "form_options": hopts,
-            "l2": "L2 flushed (256 MB write) before every timed step; geometric factors (%.0f MB) exceed L2"
-                  % (7 * 8 * (w.nel[0] * (w.p[0] + 1)) ** 3 / 1e6),
+            "l2": "L2 flushed (256 MB write) before every timed step; the band coefficients (%.1f GB per matrix) "
+                  "exceed L2" % (8.0 * band_slots(w) * N / 1e9),
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
         "pcg_iters_per_step": h["pcg_iters_per_step"],
         "pcg_iters_per_solve": h["pcg_iters_per_solve"],
         "dof_updates_per_s": h["value"] * N,
+        "rel_err_vs_fp64_paper": h.get("rel_err_vs_fp64_paper"),
+        "fp64": fp64,
         "gpu_launches": h["gpu_launches"],
         "roofline": h["roofline"],
         "forms": results,
@@ -756,6 +992,10 @@ def run_ours(args):
                                   for f, c in band_cfgs.items()},
                   "warm_start_training": warm},
     }
+    if secondary is not None:
+        result["secondary_workload"] = secondary
+    if learned is not None:
+        result["learned_warm_start"] = learned
     if batch_res is not None:
         result["multipatch_batch"] = batch_res
     if general is not None:
@@ -763,21 +1003,11 @@ def run_ours(args):
     if mp_res is not None:
         result["multipatch_system"] = mp_res
     if not args.no_cpu_baseline and world == 1:
-        base, Xo, nst = run_cpu_baseline(w, dt, args.cpu_seconds)
+        ws = sample_workload(w, args.sample_nel)
+        base, Xo, nst = run_cpu_baseline(w, ws, dt, args.cpu_seconds)
         result["cpu_baseline"] = base
-        # full-size parity: the same number of steps on the GPU (FP64 form) from the same initial state
-        patch.set_op_form("matrix_free")
-        patch.set_precond("fp64")
-        patch.set_guess("zero")
-        patch.state_init(k, u0, v0, state)
-        patch.step(state, k, w.rho, dt, nst)
-        Xg = state.view(3 * k, N).cpu().numpy()
-        result["parity_vs_oracle"] = {
-            "steps": nst,
-            "form": "fp64_paper",
-            "rel_l2_U": float(np.linalg.norm(Xg[0] - Xo[0]) / np.linalg.norm(Xo[0])),
-            "rel_l2_V": float(np.linalg.norm(Xg[1] - Xo[1]) / np.linalg.norm(Xo[1])),
-        }
+        forms = [(head, hopts)] + [(n, o) for n, o, _, _ in FORMS if n in ("fp64_paper", "fp64_banded") and n != head]
+        result["parity_vs_oracle"] = sample_parity(args, iga, torch, dev, ws, dt, nst, Xo, forms)
     print(json.dumps(result), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -785,7 +1015,9 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args):
-    """The oracle, as it stands, on the host cores: same workload, metric and unit."""
+    """The oracle, as it stands, on the host cores: same workload, metric and unit. Each
+    step is one oracle step on the bounded sample of the workload (sample_workload), and
+    the rate is scaled to the full workload by N_sample / N (the oracle's step is O(N))."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -794,10 +1026,12 @@ def run_reference(args):
 
     w = workloads.config(args.config)
     w.rho = args.rho
-    # lambda_max by the oracle's own Lanczos process (each step one PCG solve), the
-    # same estimate the GPU arm computes; dt = 0.5 tau_crit as there
-    st, X, setup_s, cores = oracle_setup(w)
-    lam = oracle.lambda_max_lanczos(st.ops, iters=args.cfl_iters)
+    ws = sample_workload(w, args.sample_nel)
+    st, X, setup_s, cores = oracle_setup(ws)
+    # lambda_max by the oracle's own Lanczos process on the sample, scaled by the squared
+    # ratio of the element sizes (lambda_max grows like h^-2): dt = 0.5 tau_crit of w
+    lam_s = oracle.lambda_max_lanczos(st.ops, iters=args.cfl_iters)
+    lam = lam_s * (w.nel[0] / ws.nel[0]) ** 2
     dt = w.cfl_fraction * math.sqrt(oracle.theta_crit(w.rho) / lam)
     for _ in range(args.warmup):
         X = st.step(X, dt)
@@ -806,18 +1040,21 @@ def run_reference(args):
     for _ in range(args.steps):
         X = st.step(X, dt)
     el = time.perf_counter() - t0
-    val = args.steps / el
+    scale = ws.ndof / w.ndof
+    val = args.steps / el * scale
     iters = sum(sum(i) for i in st.iters[n0:]) / args.steps
+    sample = ("%d whole time steps of %s (N = %d) after %d warm-up steps, %.3f steps/s there, scaled to N = %d by "
+              "%d/%d (the oracle's step is O(N)); M and K assembled once (%.0f s, not timed)" % (
+                  args.steps, ws.name, ws.ndof, args.warmup, args.steps / el, w.ndof, ws.ndof, w.ndof, setup_s))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps / scale,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(w), "ndof": w.ndof, "k": w.k, "rho_inf": w.rho, "dt": dt,
-                   "lambda_max": lam},
+                   "lambda_max": lam, "lambda_max_basis": "oracle Lanczos on the sample (%.6g) x (h_sample/h)^2"
+                   % lam_s},
         "pcg_iters_per_step": iters,
-        "cpu_baseline": {"value": val, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d whole time steps of %s after %d warm-up steps; M and K assembled once "
-                                   "(%.0f s, not timed)" % (args.steps, w.name, args.warmup, setup_s)},
+        "cpu_baseline": {"value": val, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -171,6 +171,23 @@ int iga_set_tol(iga_handle* h, double tol, int max_iter);
 int iga_set_graphs(iga_handle* h, int on);
 
 /*
+ * iga_set_barrier_limit -- failure detection on the device (the paper has no
+ * counterpart). With IGA_OP_ASSEMBLED_DF every band product first scales and splits
+ * its input vectors in one cooperative launch whose blocks meet at a grid barrier;
+ * a block waits there by polling a generation word (each poll sleeps at least
+ * 64 ns) and gives up after `polls` polls: it then sets the handle's error word and
+ * goes on, so the kernel always ends and the context stays usable, but the product
+ * that followed is not to be used. The next checked call (iga_solve_M, iga_step,
+ * iga_apply_Pinv, iga_autotune) returns IGA_ECUDA with a message, clears the error
+ * word and resets the barrier's words; calls after it run normally.
+ * polls < 0 restores the default (4,194,304 polls, about 0.3 s or more): a wait
+ * that long only runs out if a block of the launch never arrives. Small values
+ * exist to exercise this path (a limit of 0 gives up at the first poll). On a
+ * multi-patch handle the limit applies to every patch. Drops captured step graphs.
+ */
+int iga_set_barrier_limit(iga_handle* h, long long polls);
+
+/*
  * Operators (device pointers). x and y hold nvec vectors of N doubles each,
  * vector v at offset v*N; x and y must not overlap.
  *   iga_apply_M:    y = M x, [M]_ij = int B_i B_j |det DF| (Sec. 5.3, eq. mass_matrix).
@@ -434,15 +451,18 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
  */
 
 /* Band-product launch configuration of h (assembled operators): threads per block
- * 64, 128, 256 or 512 (0 = 256) and vectors per thread 1..4 sharing each coefficient
- * load (0 = all of a call's vectors, at most 4). In the IGA_OP_ASSEMBLED_DF form,
- * 64, 128 or 256 threads with at most 2 vectors per thread and a degree 2..4 along
- * the first direction select the TMA-staged kernel with that many rows per block
- * and one more warp that issues the copies (each block's rows, run by run, copied
- * into a ring of shared-memory buffers ahead of use; its bounded mbarrier waits
- * report IGA_ECUDA on the next checked call if one runs out). Every configuration
- * computes each row with the same operations in the same order, so results are
- * bitwise equal. IGA_EINVAL for other values. */
+ * 64, 96, 128, 256 or 512 (0 = 256; 96 counts as 256 outside the double-FP32 form)
+ * and vectors per thread 1..4 sharing each coefficient load (0 = all of a call's
+ * vectors, at most 4). In the IGA_OP_ASSEMBLED_DF form with a degree 2..4 along the
+ * first direction: 96 threads select the tensor-map kernel with 128 rows per block
+ * and two rows per thread, 128 threads the tensor-map kernel with one row per
+ * thread (both up to 4 vectors per pass; blocks ordered in strips of direction-1
+ * lines so that the transposed terms are read from L2), and 64 or 256 threads with
+ * at most 2 vectors the bulk-copy staged kernel; one more warp issues the copies
+ * (each block's rows, run by run, into a ring of shared-memory buffers ahead of use;
+ * its bounded mbarrier waits report IGA_ECUDA on the next checked call if one runs
+ * out). Every configuration computes each row with the same operations in the same
+ * order, so results are bitwise equal. IGA_EINVAL for other values. */
 int iga_set_band_config(iga_handle* h, int threads, int nv);
 
 /*

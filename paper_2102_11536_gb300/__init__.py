@@ -72,6 +72,7 @@ def lib():
         "iga_set_guess": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_set_tol": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_int]),
         "iga_set_graphs": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_set_barrier_limit": (ctypes.c_int, [H, ctypes.c_longlong]),
         "iga_apply_M": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_K": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
         "iga_apply_Pinv": (ctypes.c_int, [H, ctypes.c_int, vp, vp]),
@@ -143,7 +144,7 @@ def exported_symbols():
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
             "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
-            "iga_integrate"]
+            "iga_integrate", "iga_set_barrier_limit"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -368,6 +369,10 @@ class Patch:
 
     def set_tol(self, tol, max_iter=500):
         self._chk(lib().iga_set_tol(self.h, tol, max_iter), "iga_set_tol")
+
+    def set_barrier_limit(self, polls):
+        """Polls of the double-FP32 split's grid barrier before its wait gives up (< 0: default)."""
+        self._chk(lib().iga_set_barrier_limit(self.h, int(polls)), "iga_set_barrier_limit")
 
     def apply_M(self, x, y, nvec=1):
         _check_dev(x, nvec * self.N, "x"); _check_dev(y, nvec * self.N, "y")

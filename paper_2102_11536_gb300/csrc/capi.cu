@@ -50,6 +50,7 @@ struct iga_handle {
   int* df_E = nullptr;            // [kMaxVec] their exponents, [kMaxVec] scratch
   unsigned long long* df_part = nullptr;  // [kMaxVec][kDfBlocks] partial maxima
   unsigned int* df_bar = nullptr;         // grid barrier of the cooperative split (count, generation)
+  long long bar_limit = -1;               // polls of that barrier before a time-out (< 0: the default)
   bool df_ready = false;
   DfTmaps tmM, tmK;               // tensor maps of the split bands (and vectors)
   // operator workspace
@@ -60,7 +61,7 @@ struct iga_handle {
   int cg_vec = 0;
   double *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *f1 = nullptr, *f2 = nullptr;
   double* partial = nullptr;  // 3 * kMaxVec * kRedBlocks
-  double* pq_part = nullptr;  // per-block partials of p.q from the band product, cg_vec * (N / 64 + 2)
+  double* pq_part = nullptr;  // per-block partials of p.q from the band product, cg_vec * df_max_blocks
   double* rz_part = nullptr;  // per-block partials of r.z, r.z_old from the preconditioner, 2 cg_vec (N / 32 + 2)
   CgScalars cs{};
   int* h_nactive = nullptr;   // pinned
@@ -327,7 +328,7 @@ int ensure_cg_ws(iga_handle* h, int nvec) {
   CKS(dalloc(h, &h->q, sz));
   CKS(dalloc(h, &h->f1, sz));
   CKS(dalloc(h, &h->f2, sz));
-  CKS(dalloc(h, &h->pq_part, (size_t)nvec * (size_t)(h->N / 64 + 2)));
+  CKS(dalloc(h, &h->pq_part, (size_t)nvec * (size_t)df_max_blocks(h->N, h->n)));
   CKS(dalloc(h, &h->rz_part, (size_t)2 * nvec * (size_t)(h->N / 32 + 2)));
   h->cg_vec = nvec;
   return IGA_OK;
@@ -545,7 +546,8 @@ int check_tc_error(iga_handle* h) {
     // a grid barrier that ran out may have left its arrival count behind: start afresh
     if (e[1] && h->df_bar) CK(cudaMemsetAsync(h->df_bar, 0, 2 * sizeof(unsigned int), h->stream));
     return fail(h, IGA_ECUDA, e[0] ? "tensor-core mode product: mbarrier wait timed out"
-                                   : "staged band product: mbarrier wait timed out");
+                                   : "double-FP32 band product or split: a bounded wait (mbarrier or grid "
+                                     "barrier) timed out");
   }
   return IGA_OK;
 }
@@ -671,11 +673,11 @@ cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const 
     float2* xs = h->df_xs + h->df_slack;
     if (!presplit) {
       const cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part,
-                                            h->df_bar, h->dflag + 2);
+                                            h->df_bar, h->dflag + 2, h->bar_limit);
       if (e != cudaSuccess) return e;
     }
     return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
-                          (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
+                          h->dim == 3 ? h->dd[2].p : 0, h->band_H, (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
                           xs, h->df_E, x, y, h->N, threads, nv, pq, npq, h->dflag + 2, mass ? &h->tmM : &h->tmK);
   }
   return launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, mass ? h->Mband : h->Kband, active,
@@ -818,7 +820,7 @@ int solve_prime(iga_handle* h, int nvec) {
   if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // the first product's split, made here (see solve_iter_a)
     CKS(assemble_band(h));
     LK(launch_df_split(s, N, c.active, nvec, h->p, N, h->df_xs + h->df_slack, h->band_Np, h->df_E, h->df_part,
-                       h->df_bar, h->dflag + 2));
+                       h->df_bar, h->dflag + 2, h->bar_limit));
   }
   return IGA_OK;
 }
@@ -868,12 +870,12 @@ int solve_iter_b(iga_handle* h, int nvec) {
   if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // p = z + beta p and its split for the next product, one launch
     float2* xs = h->df_xs + h->df_slack;
     cudaError_t e = launch_df_update_split(s, N, c.active, nvec, h->p, h->z, c.beta, N, xs, h->band_Np, h->df_E,
-                                           h->df_part, h->df_bar, h->dflag + 2);
+                                           h->df_part, h->df_bar, h->dflag + 2, h->bar_limit);
     if (e == cudaErrorNotSupported) {
       cudaGetLastError();
       LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
       e = launch_df_split(s, N, c.active, nvec, h->p, N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar,
-                          h->dflag + 2);
+                          h->dflag + 2, h->bar_limit);
     }
     LK(e);
     return IGA_OK;
@@ -1623,6 +1625,16 @@ int iga_get_time(iga_handle* h, double* t) {
 int iga_set_graphs(iga_handle* h, int on) {
   if (!h) return IGA_EINVAL;
   h->use_graphs = on != 0;
+  return IGA_OK;
+}
+
+int iga_set_barrier_limit(iga_handle* h, long long polls) {
+  CKS(check_handle(h));
+  if (h->mp) {
+    for (iga_handle* p : h->mp->patch) CKS(iga_set_barrier_limit(p, polls));
+  }
+  h->bar_limit = polls < 0 ? -1 : polls;
+  drop_step_graph(h);  // captured launches hold the old limit
   return IGA_OK;
 }
 
@@ -2425,8 +2437,9 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
 // ---------------------------------------------------------------------------
 int iga_set_band_config(iga_handle* h, int threads, int nv) {
   CKS(check_handle(h));
-  if (!(threads == 0 || threads == 64 || threads == 128 || threads == 256 || threads == 512) || nv < 0 || nv > 4)
-    return fail(h, IGA_EINVAL, "threads must be 0, 64, 128, 256 or 512 and nv 0..4");
+  if (!(threads == 0 || threads == 64 || threads == 96 || threads == 128 || threads == 256 || threads == 512) ||
+      nv < 0 || nv > 4)
+    return fail(h, IGA_EINVAL, "threads must be 0, 64, 96, 128, 256 or 512 and nv 0..4");
   if (h->mp)
     for (iga_handle* p : h->mp->patch) {
       p->band_threads = threads;
@@ -2466,15 +2479,16 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
     cudaEvent_t a, b;
     ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } ev{e0, e1};
-  const int cand_t[4] = {64, 128, 256, 512};
-  const int cand_v[3] = {1, 2, 4};
+  const int cand_t[5] = {64, 96, 128, 256, 512};
+  const int cand_v[4] = {1, 2, 3, 4};
   struct Cand {
     int t, v;
     float ms;
   };
   std::vector<Cand> res;
-  for (int ti = 0; ti < 4; ++ti)
-    for (int vi = 0; vi < 3; ++vi) {
+  for (int ti = 0; ti < 5; ++ti)
+    for (int vi = 0; vi < 4; ++vi) {
+      if (cand_t[ti] == 96 && h->opt.op_form != IGA_OP_ASSEMBLED_DF) continue;  // a double-FP32 shape only
       const int v = std::min(cand_v[vi], nvec);
       if (vi > 0 && v == std::min(cand_v[vi - 1], nvec)) continue;  // same as the previous candidate
       LK(launch_band(h, s, IGA_PROF_BAND_MASS, nvec, nullptr, h->p, h->q, cand_t[ti], v, nullptr, nullptr));

@@ -287,33 +287,49 @@ cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const dou
                                    unsigned long long* part, int* dE);
 // xs[v] = split(x[v] 2^-E_v), E_v (into Ex[v]) from the vector's largest magnitude; with
 // bar (2 zeroed device words kept for it) and err, one cooperative launch whose grid
-// barrier's bounded wait sets *err = 1 if it runs out, else two launches
+// barrier's wait, bounded by bar_limit polls (< 0: the default), sets *err = 1 if it
+// runs out, else two launches
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
-                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err);
+                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err,
+                            long long bar_limit = -1);
 // p = z + beta p (active systems, the PCG direction update) and the split of the new p in
 // one cooperative launch; cudaErrorNotSupported without cooperative launch (nothing done)
 cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
                                    const double* z, const double* beta, long long vs, float2* xs, long long Np,
-                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err);
+                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err,
+                                   long long bar_limit = -1);
 // y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
 // pq / npq as in launch_band_spmv (x is the FP64 input, read only for pq)
 // 2-D tensor maps over a split band ([H][Np], boxes for the upper rows and the lower
 // parallelogram of a run) and over the split vectors ([kMaxVec][Np], 1 or 2 rows).
 struct DfTmaps {
-  CUtensorMap up, dn, x1, x2;
+  CUtensorMap up, dn, x1, x2, x3, x4;
   bool ok = false;
 };
 bool df_encode_maps(const float2* A, int H, const float2* xs, int nvmax, long long Np, int p0, DfTmaps* tm);
-// (p0: the degree along direction 0, for the kernels compiled for it). threads 128
-// with nv <= 2, p0 in 2..4 and tm->ok selects the tensor-map kernel; threads 64,
-// 128 or 256 with nv <= 2 and p0 in 2..4 selects the TMA-staged kernel with that many
-// rows per block (err: device int
-// set to 1 if one of its mbarrier waits runs out; null: never that kernel); other
-// shapes the register kernel. Every shape gives bitwise the same result.
-cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0,
-                           const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs,
-                           const int* Ex, const double* x, double* y, long long vs, int threads, int nv, double* pq,
-                           int* npq, int* err, const DfTmaps* tm);
+// Block order of the band products: windows of R rows over strips of W1 lines of
+// direction 1, plane after plane within a strip (S strips, the last one narrower);
+// nb0 / nbl windows per strip-plane of a full / the last strip.
+struct DfStrips {
+  int n0, n1, n2, W1, S, nb0, nbl;
+};
+// the strips for blocks of R rows: the last p2 planes of a strip hold at most ~48 MB of
+// the band's H slots (8 B each), so that the lower terms are read from L2
+DfStrips df_strips(const int* n, int p2, int H, int R);
+long long df_strip_blocks(const DfStrips& g);
+// upper bound on the blocks of any band-product launch shape (per-block partials)
+inline long long df_max_blocks(long long N, const int* n) { return N / 64 + (long long)n[1] * n[2] + 2; }
+// (p0, p2: the degrees along directions 0 and 2; H the stored slots). threads 96 with
+// nv <= 4, p0 in 2..4 and tm->ok selects the tensor-map kernel with two rows per thread;
+// threads 128 with nv <= 4, p0 in 2..4 and tm->ok the tensor-map kernel with one row per
+// thread; threads 64, 128 or 256 with nv <= 2 and p0 in 2..4 the TMA-staged kernel with
+// that many rows per block (err: device int set to 1 if one of its mbarrier waits runs
+// out; null: never these kernels); other shapes the register kernel. Every shape gives
+// bitwise the same result.
+cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0, int p2,
+                           int H, const float2* A, long long Np, int EA, const int* active, int nvec,
+                           const float2* xs, const int* Ex, const double* x, double* y, long long vs, int threads,
+                           int nv, double* pq, int* npq, int* err, const DfTmaps* tm);
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,

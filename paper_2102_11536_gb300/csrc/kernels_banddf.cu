@@ -25,7 +25,19 @@
 // read, so the inner loop has no bounds checks. The upper half is walked as runs:
 // the slots sharing (o1, o2) have consecutive h and consecutive linear offsets.
 // Every launch configuration computes each row with the same operations in the
-// same order.
+// same order: the diagonal term, then per run the upper terms and the lower terms
+// of the sides whose neighbour line exists, then a renormalisation if the row
+// computed any term of the run. Nothing a row computes depends on other rows, so
+// all launch shapes (rows per block and per thread, vectors per pass, the order of
+// the blocks) give bitwise equal products.
+//
+// Block order: the lower terms of a row reach up to p2 planes back (the coefficients
+// were read as upper terms of those planes' rows). The blocks of the tensor-map
+// kernels walk the grid in strips of W1 lines of direction 1, plane after plane
+// within a strip, with W1 chosen so that the last p2 planes of a strip (their
+// coefficients) fit in a part of L2: the lower terms then come from L2 instead of
+// DRAM. A block owns the rows of one strip-plane that fall in its window of R rows
+// (window starts even, for the tensor copies' 16-byte alignment).
 #include <algorithm>
 
 #include "iga_internal.h"
@@ -143,16 +155,17 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
 // grid-stride share. With z (and beta), the first pass also forms the PCG direction
 // x = z + beta x (active systems; the same operation as k_cg_update_p) before taking
 // the maxima, and the second pass splits what the same thread wrote. bar[0] counts
-// arrivals, bar[1] is the barrier's generation; the wait is bounded (err = 1 if it runs
-// out; the results are then not to be used).
-constexpr long long kBarLimit = 1LL << 22;
+// arrivals, bar[1] is the barrier's generation; the wait is bounded by `limit` polls of
+// at least 64 ns (err = 1 if it runs out; the results are then not to be used). Every
+// block arrives whether or not it waited, so the last one always resets the count.
+constexpr long long kBarLimit = 1LL << 22;  // default poll limit (about 0.3 s or more)
 
 __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, const int* __restrict__ active,
                                                        double* __restrict__ x, const double* __restrict__ z,
                                                        const double* __restrict__ beta, long long vs,
                                                        unsigned long long* __restrict__ part,
                                                        float2* __restrict__ xs, long long xvs, int* __restrict__ Eout,
-                                                       unsigned int* bar, int* err) {
+                                                       unsigned int* bar, int* err, long long limit) {
   const int G = gridDim.x;
   const long long stride = (long long)G * blockDim.x;
   for (int v = 0; v < nvec; ++v) {
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
     } else {
       long long it = 0;
       while (*gen == g0) {
-        if (++it > kBarLimit) {
+        if (++it > limit) {
           atomicExch(err, 1);
           break;
         }
@@ -221,9 +234,11 @@ __device__ __forceinline__ void df_term(float& s, float& c, const float2 a, cons
   s = S;
 }
 
-// Fast2Sum renormalisation of (s, c): |c| is at most a few ulps of s
+// Fast2Sum renormalisation of (s, c): |c| is at most a few ulps of s; only for rows
+// that computed a term of the run (on)
 template <int NV>
-__device__ __forceinline__ void df_renorm(float (&s)[NV], float (&c)[NV]) {
+__device__ __forceinline__ void df_renorm(float (&s)[NV], float (&c)[NV], bool on) {
+  if (!on) return;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const float S = __fadd_rn(s[v], c[v]);
@@ -279,6 +294,32 @@ __device__ __forceinline__ void df_run(int len, bool up, bool dn, const float2* 
   }
 }
 
+// The rows of block b for blocks of R rows in strip order: the copy window starts at
+// *i0c (even), the block's rows are [*lo, *hi) (empty for a block past the strip-plane).
+__device__ __forceinline__ void df_block_rows(const DfStrips& g, int R, long long b, long long* i0c, long long* lo,
+                                              long long* hi) {
+  const long long per0 = (long long)g.n2 * g.nb0;
+  long long sg = b / per0, rem;
+  int nb;
+  if (sg >= g.S - 1) {
+    sg = g.S - 1;
+    rem = b - (long long)(g.S - 1) * per0;
+    nb = g.nbl;
+  } else {
+    rem = b - sg * per0;
+    nb = g.nb0;
+  }
+  const long long i2 = rem / nb, q = rem - i2 * nb;
+  const long long l1 = sg * g.W1;
+  const long long w = min((long long)g.W1, (long long)g.n1 - l1);
+  const long long a = (long long)g.n0 * (l1 + (long long)g.n1 * i2);
+  const long long e = a + w * g.n0;
+  const long long c = (a & ~1LL) + q * R;
+  *i0c = c;
+  *lo = max(a, c);
+  *hi = min(e, c + R);
+}
+
 // P0: the degree along direction 0 when compiled for it (run lengths P0 and 2 P0 + 1),
 // 0 for any degree. A vector slot past nvec repeats the last vector's arithmetic and
 // an inactive vector is computed from its stale split copy; neither is stored, so the
@@ -289,9 +330,11 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
                                                 const int* __restrict__ active, int nvec,
                                                 const float2* __restrict__ xs, const int* __restrict__ Ex,
                                                 const double* __restrict__ x, double* __restrict__ y, long long vs,
-                                                double* __restrict__ pq) {
-  const long long i = (long long)blockIdx.x * BS + threadIdx.x;
-  const bool row = i < N;  // no early return: the run votes need every lane
+                                                double* __restrict__ pq, DfStrips g) {
+  long long i0c, lo, hi;
+  df_block_rows(g, BS, blockIdx.x, &i0c, &lo, &hi);
+  const long long i = i0c + threadIdx.x;
+  const bool row = i >= lo && i < hi;  // no early return: the run votes need every lane
   const int v0 = blockIdx.y * NV;
   float s[NV], c[NV];
   const float2* xv[NV];  // row pad + i of each vector's split copy
@@ -336,7 +379,7 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
     } else {
       df_run<0, NV>(R.y, up, dn, au, ad, Np, xu, xd, s, c);
     }
-    df_renorm<NV>(s, c);
+    df_renorm<NV>(s, c, up || dn);
   }
   bool on[NV];
   double out[NV];
@@ -569,7 +612,7 @@ __global__ void __launch_bounds__(R + 32) k_band_df_tma(long long N, int nruns, 
         const float2* buf = dsm + (size_t)b * St::ELEMS;
         if (r == 0) df_run_smem<P0, NV, R, P0>(buf, j, R4.w, up, dn, s, c);
         else df_run_smem<P0, NV, R, M0>(buf, j, R4.w, up, dn, s, c);
-        df_renorm<NV>(s, c);
+        df_renorm<NV>(s, c, up || dn);
       }
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&empty[b])) : "memory");
@@ -681,29 +724,62 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int
       ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
 }
 
-template <int P0, int NV, int LEN>
-__device__ __forceinline__ void df_run_tm(const float2* buf, int j, int L0, bool up, bool dn, float (&s)[NV],
+constexpr int kMaxTmRuns = 128;  // runs staged in shared memory by the tensor-map kernels
+constexpr int kTmStages = 2;     // ring buffers of the one-row tensor-map kernel
+constexpr int kTm2Stages = 1;    // ring buffers of the two-row tensor-map kernel
+
+// The terms of run (LEN slots) for row j, both sides (the common case), every vector
+// (ALL) or the vectors with act[v] (uniform tests over the block)
+template <int P0, int NV, int LEN, bool ALL>
+__device__ __forceinline__ void df_run_tm(const float2* buf, int j, int o, const bool (&act)[NV], float (&s)[NV],
                                           float (&c)[NV]) {
   using St = DfTmStage<P0, NV>;
   constexpr int R = St::R, M0 = St::M0, W = St::W;
-  const int o = L0 & 1;
+  const float2* xu = buf + St::XU + o + j;
+#pragma unroll
+  for (int t = 0; t < LEN; ++t) {
+    const float2 a = buf[St::CU + t * R + j];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (ALL || act[v]) df_term(s[v], c[v], a, xu[v * W + t]);
+  }
+  const float2* cd = buf + St::CD + o + j + (M0 - 1);
+  const float2* xd = buf + St::XD + o + j + (M0 - 1);
+#pragma unroll
+  for (int t = 0; t < LEN; ++t) {
+    const float2 a = cd[t * W - t];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (ALL || act[v]) df_term(s[v], c[v], a, xd[v * W - t]);
+  }
+}
+
+// the same for any sides and vectors (rows next to the grid's faces, converged systems):
+// the same operations per row and vector in the same order, compact code
+template <int P0, int NV>
+__device__ __forceinline__ void df_run_tm_any(const float2* buf, int j, int o, int len, bool up, bool dn,
+                                              const bool (&act)[NV], float (&s)[NV], float (&c)[NV]) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0, W = St::W;
   if (up) {
     const float2* xu = buf + St::XU + o + j;
-#pragma unroll
-    for (int t = 0; t < LEN; ++t) {
+#pragma unroll 1
+    for (int t = 0; t < len; ++t) {
       const float2 a = buf[St::CU + t * R + j];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v * W + t]);
+      for (int v = 0; v < NV; ++v)
+        if (act[v]) df_term(s[v], c[v], a, xu[v * W + t]);
     }
   }
   if (dn) {
     const float2* cd = buf + St::CD + o + j + (M0 - 1);
     const float2* xd = buf + St::XD + o + j + (M0 - 1);
-#pragma unroll
-    for (int t = 0; t < LEN; ++t) {
+#pragma unroll 1
+    for (int t = 0; t < len; ++t) {
       const float2 a = cd[t * W - t];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v * W - t]);
+      for (int v = 0; v < NV; ++v)
+        if (act[v]) df_term(s[v], c[v], a, xd[v * W - t]);
     }
   }
 }
@@ -718,17 +794,24 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
                                                              const float2* __restrict__ xs, const int* __restrict__ Ex,
                                                              const double* __restrict__ x, double* __restrict__ y,
                                                              long long vs, double* __restrict__ pq,
-                                                             int* __restrict__ err) {
+                                                             int* __restrict__ err, DfStrips g) {
   using St = DfTmStage<P0, NV>;
   constexpr int R = St::R, M0 = St::M0;
   constexpr int NW = R / 32;
-  constexpr int S = 2;  // buffers in the ring (more resident blocks beat a deeper ring)
+  constexpr int S = kTmStages;  // buffers in the ring
   extern __shared__ __align__(128) float2 dsm[];
   __shared__ __align__(8) unsigned long long full[S], empty[S];
+  __shared__ int4 sruns[kMaxTmRuns];
   const int j = threadIdx.x;
   const int lane = j & 31;
-  const long long i0 = (long long)blockIdx.x * R;
   const int v0 = blockIdx.y * NV;
+  long long i0, lo, hi;
+  df_block_rows(g, R, blockIdx.x, &i0, &lo, &hi);
+  if (lo >= hi) {  // no rows: only the partials, uniformly over the block
+    if (pq && j < NV && v0 + j < nvec) pq[(long long)(v0 + j) * gridDim.x + blockIdx.x] = 0.0;
+    return;
+  }
+  for (int r = j; r < nruns; r += blockDim.x) sruns[r] = runs[r];
   if (j == 0) {
     for (int b = 0; b < S; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&full[b])));
@@ -738,12 +821,16 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
   }
   __syncthreads();
   const long long i = i0 + j;
-  const bool row = j < R && i < N;
+  const bool row = j < R && i >= lo && i < hi;
   float s[NV], c[NV];
+  bool act[NV];  // the vectors whose products are stored: the others are not computed
+  bool all = true;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     s[v] = 0.f;
     c[v] = 0.f;
+    act[v] = v0 + v < nvec && (!active || active[v0 + v]);
+    all = all && act[v];
   }
   if (j >= R) {  // producer warp
     if (lane == 0) {
@@ -756,7 +843,7 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
           ok = false;
           break;
         }
-        const int4 R4 = runs[r];
+        const int4 R4 = sruns[r];
         const int c0 = (xi - R4.w - (M0 - 1)) & ~1;
         const uint32_t mb = s_u32(&full[b]);
         const uint32_t base = s_u32(dsm + (size_t)b * St::ELEMS);
@@ -787,7 +874,7 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
     bool ok = true;
     for (int r = 0; r < nruns; ++r) {
       const int b = r % S;
-      const int4 R4 = runs[r];
+      const int4 R4 = sruns[r];
       bool up = row, dn = row;
       if (r > 0) {
         const int o1 = (R4.z & 255) - 64, o2 = ((R4.z >> 8) & 255) - 64;
@@ -801,9 +888,17 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
       }
       if (ok && warp_on) {
         const float2* buf = dsm + (size_t)b * St::ELEMS;
-        if (r == 0) df_run_tm<P0, NV, P0>(buf, j, R4.w, up, dn, s, c);
-        else df_run_tm<P0, NV, M0>(buf, j, R4.w, up, dn, s, c);
-        df_renorm<NV>(s, c);
+        const int o = R4.w & 1;
+        if (up && dn && all) {
+          if (r == 0) df_run_tm<P0, NV, P0, true>(buf, j, o, act, s, c);
+          else df_run_tm<P0, NV, M0, true>(buf, j, o, act, s, c);
+        } else if (up && dn) {
+          if (r == 0) df_run_tm<P0, NV, P0, false>(buf, j, o, act, s, c);
+          else df_run_tm<P0, NV, M0, false>(buf, j, o, act, s, c);
+        } else {
+          df_run_tm_any<P0, NV>(buf, j, o, r == 0 ? P0 : M0, up, dn, act, s, c);
+        }
+        df_renorm<NV>(s, c, up || dn);
       }
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&empty[b])) : "memory");
@@ -843,13 +938,19 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
   }
 }
 
+// the tensor map over NV rows of the split vectors
+template <int NV>
+const CUtensorMap& df_xmap(const DfTmaps& tm) {
+  return NV == 1 ? tm.x1 : NV == 2 ? tm.x2 : NV == 3 ? tm.x3 : tm.x4;
+}
+
 template <int P0, int NV>
 cudaError_t band_df_tm_go(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
                           const DfTmaps& tm, long long Np, int EA, const int* active, int nvec, const float2* xs,
                           const int* Ex, const double* x, double* y, long long vs, double* pq, int* err,
-                          int* nblocks) {
+                          int* nblocks, const DfStrips& g) {
   using St = DfTmStage<P0, NV>;
-  const size_t smem = (size_t)St::ELEMS * 8 * 2;
+  const size_t smem = (size_t)St::ELEMS * 8 * kTmStages;
   static unsigned long long attr = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -859,10 +960,310 @@ cudaError_t band_df_tm_go(cudaStream_t s, long long N, int nruns, const int4* ru
     if (e != cudaSuccess) return e;
     attr |= 1ULL << dev;
   }
-  const dim3 grid((unsigned)((N + kTmRows - 1) / kTmRows), (unsigned)((nvec + NV - 1) / NV));
+  const dim3 grid((unsigned)df_strip_blocks(g), (unsigned)((nvec + NV - 1) / NV));
   k_band_df_tm<P0, NV><<<grid, kTmRows + 32, smem, s>>>(N, nruns, runs, n[0], n[1], n[2], A, tm.up, tm.dn,
-                                                        NV == 1 ? tm.x1 : tm.x2, Np, EA, active, nvec, xs, Ex, x, y,
-                                                        vs, pq, err);
+                                                        df_xmap<NV>(tm), Np, EA, active, nvec, xs, Ex, x, y, vs, pq,
+                                                        err, g);
+  *nblocks = (int)grid.x;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-map form with two rows per consumer thread: the staging (four 2-D copies
+// per run, 128 rows per block) is that of k_band_df_tm; thread t computes rows
+// 2t and 2t + 1 of the window. The pair's coefficients sit side by side in shared
+// memory (one 16-byte load: always for the upper terms, for every other lower term),
+// and the two rows' x values overlap: row 2t + 1 needs at term t what row 2t needs at
+// term t + 1 (upper) or t - 1 (lower), so each vector costs one 8-byte load per term
+// pair. The arithmetic of every row, and its order, are those of the other forms.
+// The terms of run (LEN slots) for rows 2t and 2t + 1, every vector, both sides (the
+// common case): one coefficient load per term serves both rows (a 16-byte pair for the
+// upper terms; for the lower terms on every other term), and the x loads slide
+template <int P0, int NV, int LEN, bool ALL>
+__device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, const bool (&act)[NV],
+                                           float (&s)[2][NV], float (&c)[2][NV]) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0, W = St::W;
+  {
+    const float2* cu = buf + St::CU + jj;
+    const float2* xu = buf + St::XU + o + jj;
+    float2 xa[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xa[v] = xu[v * W];
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const float4 a2 = *reinterpret_cast<const float4*>(cu + t * R);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (!ALL && !act[v]) continue;
+        const float2 xb = xu[v * W + t + 1];
+        df_term(s[0][v], c[0][v], make_float2(a2.x, a2.y), xa[v]);
+        df_term(s[1][v], c[1][v], make_float2(a2.z, a2.w), xb);
+        xa[v] = xb;
+      }
+    }
+  }
+  {
+    // row jj's lower term of slot t at column o + jj + (M0 - 1) - t, row jj + 1's next to it
+    const int base = St::CD + o + jj + (M0 - 1);
+    const float2* xd = buf + St::XD + o + jj + (M0 - 1);
+    float2 xb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xb[v] = xd[v * W + 1];
+#pragma unroll
+    for (int t = 0; t < LEN; ++t) {
+      const int off = base + t * (W - 1);
+      float2 a0, a1;
+      if ((off & 1) == 0) {
+        const float4 q = *reinterpret_cast<const float4*>(buf + off);
+        a0 = make_float2(q.x, q.y);
+        a1 = make_float2(q.z, q.w);
+      } else {
+        a0 = buf[off];
+        a1 = buf[off + 1];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (!ALL && !act[v]) continue;
+        const float2 xa = xd[v * W - t];
+        df_term(s[0][v], c[0][v], a0, xa);
+        df_term(s[1][v], c[1][v], a1, xb[v]);
+        xb[v] = xa;
+      }
+    }
+  }
+}
+
+// the same for any rows, sides and vectors (rows next to the grid's faces, converged
+// systems): per row and vector the same operations in the same order, compact code
+template <int P0, int NV>
+__device__ __forceinline__ void df_run_tm2_any(const float2* buf, int jj, int o, int len, bool up0, bool up1,
+                                               bool dn0, bool dn1, const bool (&act)[NV], float (&s)[2][NV],
+                                               float (&c)[2][NV]) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0, W = St::W;
+  if (up0 || up1) {
+    const float2* cu = buf + St::CU + jj;
+    const float2* xu = buf + St::XU + o + jj;
+#pragma unroll 1
+    for (int t = 0; t < len; ++t) {
+      const float2 a0 = cu[t * R], a1 = cu[t * R + 1];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (!act[v]) continue;
+        if (up0) df_term(s[0][v], c[0][v], a0, xu[v * W + t]);
+        if (up1) df_term(s[1][v], c[1][v], a1, xu[v * W + t + 1]);
+      }
+    }
+  }
+  if (dn0 || dn1) {
+    const float2* cd = buf + St::CD + o + jj + (M0 - 1);
+    const float2* xd = buf + St::XD + o + jj + (M0 - 1);
+#pragma unroll 1
+    for (int t = 0; t < len; ++t) {
+      const float2 a0 = cd[t * (W - 1)], a1 = cd[t * (W - 1) + 1];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (!act[v]) continue;
+        if (dn0) df_term(s[0][v], c[0][v], a0, xd[v * W - t]);
+        if (dn1) df_term(s[1][v], c[1][v], a1, xd[v * W - t + 1]);
+      }
+    }
+  }
+}
+
+template <int P0, int NV>
+__global__ void __launch_bounds__(kTmRows / 2 + 32) k_band_df_tm2(
+    long long N, int nruns, const int4* __restrict__ runs, int n0, int n1, int n2, const float2* __restrict__ A,
+    const __grid_constant__ CUtensorMap tmUp, const __grid_constant__ CUtensorMap tmDn,
+    const __grid_constant__ CUtensorMap tmX, long long Np, int EA, const int* __restrict__ active, int nvec,
+    const float2* __restrict__ xs, const int* __restrict__ Ex, const double* __restrict__ x, double* __restrict__ y,
+    long long vs, double* __restrict__ pq, int* __restrict__ err, DfStrips g) {
+  using St = DfTmStage<P0, NV>;
+  constexpr int R = St::R, M0 = St::M0;
+  constexpr int NC = R / 2;    // consumer threads
+  constexpr int NW = NC / 32;  // consumer warps
+  constexpr int S = kTm2Stages;  // buffers in the ring
+  extern __shared__ __align__(128) float2 dsm[];
+  __shared__ __align__(8) unsigned long long full[S], empty[S];
+  __shared__ int4 sruns[kMaxTmRuns];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int v0 = blockIdx.y * NV;
+  long long i0, lo, hi;
+  df_block_rows(g, R, blockIdx.x, &i0, &lo, &hi);
+  if (lo >= hi) {  // no rows: only the partials, uniformly over the block
+    if (pq && tid < NV && v0 + tid < nvec) pq[(long long)(v0 + tid) * gridDim.x + blockIdx.x] = 0.0;
+    return;
+  }
+  for (int r = tid; r < nruns; r += blockDim.x) sruns[r] = runs[r];
+  if (tid == 0) {
+    for (int b = 0; b < S; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(&empty[b])), "r"(NW));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int jj = 2 * tid;
+  const long long i = i0 + jj;  // rows i and i + 1
+  const bool row0 = tid < NC && i >= lo && i < hi;
+  const bool row1 = tid < NC && i + 1 >= lo && i + 1 < hi;
+  float s[2][NV], c[2][NV];
+  bool act[NV];  // the vectors whose products are stored: the others are not computed
+  bool all = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    s[0][v] = s[1][v] = 0.f;
+    c[0][v] = c[1][v] = 0.f;
+    act[v] = v0 + v < nvec && (!active || active[v0 + v]);
+    all = all && act[v];
+  }
+  if (tid >= NC) {  // producer warp
+    if (lane == 0) {
+      bool ok = true;
+      int last = -1;
+      const int xi = (int)(kDfPad + i0);
+      for (int r = 0; r < nruns; ++r) {
+        const int b = r % S, k = r / S;
+        if (k > 0 && !mbar_wait_bounded(s_u32(&empty[b]), (uint32_t)((k - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const int4 R4 = sruns[r];
+        const int c0 = (xi - R4.w - (M0 - 1)) & ~1;
+        const uint32_t mb = s_u32(&full[b]);
+        const uint32_t base = s_u32(dsm + (size_t)b * St::ELEMS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(St::TX) : "memory");
+        tma_2d(base + St::CU * 8, &tmUp, xi, R4.x, mb);
+        tma_2d(base + St::CD * 8, &tmDn, c0, R4.x, mb);
+        tma_2d(base + St::XU * 8, &tmX, (xi + R4.w) & ~1, v0, mb);
+        tma_2d(base + St::XD * 8, &tmX, c0, v0, mb);
+        last = r;
+      }
+      if (!ok) atomicExch(err, 1);
+      for (int q = last - S + 1; q <= last; ++q)  // let every copy in flight land
+        if (q >= 0) mbar_wait_bounded(s_u32(&full[q % S]), (uint32_t)((q / S) & 1));
+    }
+  } else {  // consumer warps
+    if (row0 || row1) {  // the diagonal: the window start is even, so both rows' pairs are one 16-byte load
+      const float4 a2 = *reinterpret_cast<const float4*>(A + kDfPad + i);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (!act[v]) continue;
+        const float4 x2 = *reinterpret_cast<const float4*>(xs + (long long)(v0 + v) * Np + kDfPad + i);
+        if (row0) df_term(s[0][v], c[0][v], make_float2(a2.x, a2.y), make_float2(x2.x, x2.y));
+        if (row1) df_term(s[1][v], c[1][v], make_float2(a2.z, a2.w), make_float2(x2.z, x2.w));
+      }
+    }
+    int i1a = 0, i2a = 0, i1b = 0, i2b = 0;
+    if (row0) {
+      const long long t = i / n0;
+      i1a = (int)(t % n1);
+      i2a = (int)(t / n1);
+    }
+    if (row1) {
+      const long long t = (i + 1) / n0;
+      i1b = (int)(t % n1);
+      i2b = (int)(t / n1);
+    }
+    bool ok = true;
+    for (int r = 0; r < nruns; ++r) {
+      const int b = r % S;
+      const int4 R4 = sruns[r];
+      bool up0 = row0, dn0 = row0, up1 = row1, dn1 = row1;
+      if (r > 0) {
+        const int o1 = (R4.z & 255) - 64, o2 = ((R4.z >> 8) & 255) - 64;
+        up0 = up0 && (unsigned)(i1a + o1) < (unsigned)n1 && (unsigned)(i2a + o2) < (unsigned)n2;
+        dn0 = dn0 && (unsigned)(i1a - o1) < (unsigned)n1 && (unsigned)(i2a - o2) < (unsigned)n2;
+        up1 = up1 && (unsigned)(i1b + o1) < (unsigned)n1 && (unsigned)(i2b + o2) < (unsigned)n2;
+        dn1 = dn1 && (unsigned)(i1b - o1) < (unsigned)n1 && (unsigned)(i2b - o2) < (unsigned)n2;
+      }
+      const bool warp_on = __any_sync(0xffffffffu, up0 || dn0 || up1 || dn1);
+      if (ok && !mbar_wait_bounded(s_u32(&full[b]), (uint32_t)((r / S) & 1))) {
+        ok = false;
+        atomicExch(err, 1);
+      }
+      if (ok && warp_on) {
+        const float2* buf = dsm + (size_t)b * St::ELEMS;
+        const int o = R4.w & 1;
+        if (up0 && up1 && dn0 && dn1 && all) {
+          if (r == 0) df_run_tm2<P0, NV, P0, true>(buf, jj, o, act, s, c);
+          else df_run_tm2<P0, NV, M0, true>(buf, jj, o, act, s, c);
+        } else if (up0 && up1 && dn0 && dn1) {
+          if (r == 0) df_run_tm2<P0, NV, P0, false>(buf, jj, o, act, s, c);
+          else df_run_tm2<P0, NV, M0, false>(buf, jj, o, act, s, c);
+        } else {
+          df_run_tm2_any<P0, NV>(buf, jj, o, r == 0 ? P0 : M0, up0, up1, dn0, dn1, act, s, c);
+        }
+        df_renorm<NV>(s[0], c[0], up0 || dn0);
+        df_renorm<NV>(s[1], c[1], up1 || dn1);
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(&empty[b])) : "memory");
+    }
+  }
+  bool on[2][NV];
+  double out[2][NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int vv = v0 + v;
+    const bool act = vv < nvec && (!active || active[vv]);
+    const double sc = act ? ldexp(1.0, Ex[vv] + EA) : 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      on[k][v] = (k ? row1 : row0) && act;
+      out[k][v] = 0.0;
+      if (on[k][v]) {
+        out[k][v] = ((double)s[k][v] + (double)c[k][v]) * sc;
+        y[vv * vs + i + k] = out[k][v];
+      }
+    }
+  }
+  if (pq) {  // fixed-order block sums of x_i y_i: the thread's two rows, the warp by shuffles, the warps in order
+    __shared__ double sred[NW];
+    const int w = tid >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int vv = v0 + v;
+      if (vv >= nvec) break;
+      double t = on[0][v] ? x[vv * vs + i] * out[0][v] : 0.0;
+      if (on[1][v]) t += x[vv * vs + i + 1] * out[1][v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0 && w < NW) sred[w] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < NW; ++q) sum += sred[q];
+        pq[(long long)vv * gridDim.x + blockIdx.x] = sum;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int P0, int NV>
+cudaError_t band_df_tm2_go(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, const float2* A,
+                           const DfTmaps& tm, long long Np, int EA, const int* active, int nvec, const float2* xs,
+                           const int* Ex, const double* x, double* y, long long vs, double* pq, int* err,
+                           int* nblocks, const DfStrips& g) {
+  using St = DfTmStage<P0, NV>;
+  const size_t smem = (size_t)St::ELEMS * 8 * kTm2Stages;
+  static unsigned long long attr = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(attr >> dev & 1ULL)) {
+    e = cudaFuncSetAttribute(k_band_df_tm2<P0, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr |= 1ULL << dev;
+  }
+  const dim3 grid((unsigned)df_strip_blocks(g), (unsigned)((nvec + NV - 1) / NV));
+  k_band_df_tm2<P0, NV><<<grid, kTmRows / 2 + 32, smem, s>>>(N, nruns, runs, n[0], n[1], n[2], A, tm.up, tm.dn,
+                                                             df_xmap<NV>(tm), Np, EA, active, nvec, xs, Ex, x, y, vs,
+                                                             pq, err, g);
   *nblocks = (int)grid.x;
   return cudaGetLastError();
 }
@@ -870,10 +1271,10 @@ cudaError_t band_df_tm_go(cudaStream_t s, long long N, int nruns, const int4* ru
 template <int P0, int BS>
 void band_df_nv(cudaStream_t s, int nv, dim3 grid, long long N, int nruns, const int4* runs, const int* n,
                 const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
-                const double* x, double* y, long long vs, double* pq) {
+                const double* x, double* y, long long vs, double* pq, const DfStrips& g) {
 #define IGA_DF_GO(NVV)                                                                                          \
   k_band_df<P0, NVV, BS><<<grid, BS, 0, s>>>(N, nruns, runs, n[0], n[1], n[2], A, Np, EA, active, nvec, xs, Ex, \
-                                              x, y, vs, pq)
+                                              x, y, vs, pq, g)
   switch (nv) {
     case 1: IGA_DF_GO(1); break;
     case 2: IGA_DF_GO(2); break;
@@ -884,20 +1285,42 @@ void band_df_nv(cudaStream_t s, int nv, dim3 grid, long long N, int nruns, const
 }
 
 template <int BS>
-int band_df_go(cudaStream_t s, int nv, int p0, long long N, int nruns, const int4* runs, const int* n,
+int band_df_go(cudaStream_t s, int nv, int p0, int p2, int H, long long N, int nruns, const int4* runs, const int* n,
                const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs, const int* Ex,
                const double* x, double* y, long long vs, double* pq) {
-  const dim3 grid((unsigned)((N + BS - 1) / BS), (unsigned)((nvec + nv - 1) / nv));
+  const DfStrips g = df_strips(n, p2, H, BS);
+  const dim3 grid((unsigned)df_strip_blocks(g), (unsigned)((nvec + nv - 1) / nv));
   switch (p0) {
-    case 2: band_df_nv<2, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
-    case 3: band_df_nv<3, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
-    case 4: band_df_nv<4, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
-    default: band_df_nv<0, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq); break;
+    case 2: band_df_nv<2, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, g); break;
+    case 3: band_df_nv<3, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, g); break;
+    case 4: band_df_nv<4, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, g); break;
+    default: band_df_nv<0, BS>(s, nv, grid, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, g); break;
   }
   return (int)grid.x;
 }
 
 }  // namespace
+
+DfStrips df_strips(const int* n, int p2, int H, int R) {
+  DfStrips g{n[0], n[1], n[2], n[1], 1, 0, 0};
+  if (n[2] > 1 && p2 > 0) {
+    // lines of direction 1 whose last p2 planes of coefficients fit in ~48 MB
+    const double budget = 48e6;
+    long long wmax = (long long)(budget / (8.0 * H * p2 * n[0]));
+    wmax = std::max(8LL, std::min<long long>(wmax, n[1]));
+    const int S = (int)((n[1] + wmax - 1) / wmax);
+    g.W1 = (n[1] + S - 1) / S;
+    g.S = (n[1] + g.W1 - 1) / g.W1;
+  }
+  const long long wl = (long long)n[1] - (long long)(g.S - 1) * g.W1;
+  g.nb0 = (int)(((long long)g.W1 * n[0] + 1 + R - 1) / R);  // + 1: the window starts at an even row
+  g.nbl = (int)((wl * n[0] + 1 + R - 1) / R);
+  return g;
+}
+
+long long df_strip_blocks(const DfStrips& g) {
+  return (long long)(g.S - 1) * g.n2 * g.nb0 + (long long)g.n2 * g.nbl;
+}
 
 std::vector<int> band_df_runs(const int* n, const int* p) {
   const int m0 = 2 * p[0] + 1, m1 = 2 * p[1] + 1, m2 = 2 * p[2] + 1;
@@ -933,7 +1356,7 @@ namespace {
 // cudaErrorNotSupported when the device has no cooperative launch
 cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nvec, double* x, const double* z,
                           const double* beta, long long vs, float2* xs, long long Np, int* Ex,
-                          unsigned long long* part, unsigned int* bar, int* err) {
+                          unsigned long long* part, unsigned int* bar, int* err, long long limit) {
   static int nsm[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -957,15 +1380,18 @@ cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nv
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, z, beta, vs, part, xs, Np, Ex, bar, err);
+  if (limit < 0) limit = kBarLimit;
+  return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, z, beta, vs, part, xs, Np, Ex, bar, err,
+                            limit);
 }
 }  // namespace
 
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
-                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err) {
+                            float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err,
+                            long long bar_limit) {
   if (bar && err) {  // one cooperative launch, two blocks per SM
     const cudaError_t e = df_split_coop(s, N, active, nvec, const_cast<double*>(x), nullptr, nullptr, vs, xs, Np,
-                                        Ex, part, bar, err);
+                                        Ex, part, bar, err, bar_limit);
     if (e != cudaErrorNotSupported) return e;
   }
   k_df_absmax<<<dim3(kDfBlocks, nvec), 256, 0, s>>>(N, active, x, vs, part);
@@ -976,25 +1402,36 @@ cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int 
 
 cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
                                    const double* z, const double* beta, long long vs, float2* xs, long long Np,
-                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err) {
-  return df_split_coop(s, N, active, nvec, p, z, beta, vs, xs, Np, Ex, part, bar, err);
+                                   int* Ex, unsigned long long* part, unsigned int* bar, int* err,
+                                   long long bar_limit) {
+  return df_split_coop(s, N, active, nvec, p, z, beta, vs, xs, Np, Ex, part, bar, err, bar_limit);
 }
 
-cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0,
-                           const float2* A, long long Np, int EA, const int* active, int nvec, const float2* xs,
-                           const int* Ex, const double* x, double* y, long long vs, int threads, int nv, double* pq,
-                           int* npq, int* err, const DfTmaps* tm) {
+cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0, int p2,
+                           int H, const float2* A, long long Np, int EA, const int* active, int nvec,
+                           const float2* xs, const int* Ex, const double* x, double* y, long long vs, int threads,
+                           int nv, double* pq, int* npq, int* err, const DfTmaps* tm) {
   if (nv <= 0) nv = nvec < 4 ? nvec : 4;
   if (nv < 1) nv = 1;
   if (nv > 4) nv = 4;
   int nb;
-  if (threads == 128 && nv <= 2 && p0 >= 2 && p0 <= 4 && err && tm && tm->ok) {
+  if ((threads == 96 || threads == 128) && p0 >= 2 && p0 <= 4 && err && tm && tm->ok && nruns <= kMaxTmRuns) {
+    const DfStrips g = df_strips(n, p2, H, kTmRows);
     cudaError_t e;
-#define IGA_TM_GO(P, V) band_df_tm_go<P, V>(s, N, nruns, runs, n, A, *tm, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb)
-    if (p0 == 2) e = nv == 1 ? IGA_TM_GO(2, 1) : IGA_TM_GO(2, 2);
-    else if (p0 == 3) e = nv == 1 ? IGA_TM_GO(3, 1) : IGA_TM_GO(3, 2);
-    else e = nv == 1 ? IGA_TM_GO(4, 1) : IGA_TM_GO(4, 2);
-#undef IGA_TM_GO
+#define IGA_TM_ARGS s, N, nruns, runs, n, A, *tm, Np, EA, active, nvec, xs, Ex, x, y, vs, pq, err, &nb, g
+#define IGA_TM_NV(GO, P) \
+  (nv == 1 ? GO<P, 1>(IGA_TM_ARGS) : nv == 2 ? GO<P, 2>(IGA_TM_ARGS) : nv == 3 ? GO<P, 3>(IGA_TM_ARGS) : GO<P, 4>(IGA_TM_ARGS))
+    if (threads == 96) {
+      if (p0 == 2) e = IGA_TM_NV(band_df_tm2_go, 2);
+      else if (p0 == 3) e = IGA_TM_NV(band_df_tm2_go, 3);
+      else e = IGA_TM_NV(band_df_tm2_go, 4);
+    } else {
+      if (p0 == 2) e = IGA_TM_NV(band_df_tm_go, 2);
+      else if (p0 == 3) e = IGA_TM_NV(band_df_tm_go, 3);
+      else e = IGA_TM_NV(band_df_tm_go, 4);
+    }
+#undef IGA_TM_NV
+#undef IGA_TM_ARGS
     if (npq) *npq = nb;
     return e;
   }
@@ -1006,10 +1443,10 @@ cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* r
     if (npq) *npq = nb;
     return e;
   }
-  if (threads == 64) nb = band_df_go<64>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else if (threads == 128) nb = band_df_go<128>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else if (threads == 512) nb = band_df_go<512>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
-  else nb = band_df_go<256>(s, nv, p0, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  if (threads == 64) nb = band_df_go<64>(s, nv, p0, p2, H, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else if (threads == 128) nb = band_df_go<128>(s, nv, p0, p2, H, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else if (threads == 512) nb = band_df_go<512>(s, nv, p0, p2, H, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
+  else nb = band_df_go<256>(s, nv, p0, p2, H, N, nruns, runs, n, A, Np, EA, active, nvec, xs, Ex, x, y, vs, pq);
   if (npq) *npq = nb;
   return cudaGetLastError();
 }
@@ -1041,7 +1478,7 @@ bool df_encode_maps(const float2* A, int H, const float2* xs, int nvmax, long lo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   if (!make(&tm->up, A, H, kTmRows, M0) || !make(&tm->dn, A, H, W, M0) || !make(&tm->x1, xs, nvmax, W, 1) ||
-      !make(&tm->x2, xs, nvmax, W, 2))
+      !make(&tm->x2, xs, nvmax, W, 2) || !make(&tm->x3, xs, nvmax, W, 3) || !make(&tm->x4, xs, nvmax, W, 4))
     return false;
   tm->ok = true;
   return true;

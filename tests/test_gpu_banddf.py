@@ -85,7 +85,7 @@ def test_df_product_is_exactly_homogeneous(e):
     g.close()
 
 
-@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+@pytest.mark.parametrize("threads", [64, 96, 128, 256, 512])
 @pytest.mark.parametrize("nv", [1, 2, 3, 4])
 def test_df_configs_are_bitwise_equal(threads, nv):
     w = W.small(d=3, nel=(9, 7, 6), p=3, amp=0.1)
@@ -293,4 +293,37 @@ def test_df_steps_2d_match_oracle(k):
     Xg = _np(state).reshape(3 * k, g.N)
     for row in (0, 1):
         assert np.linalg.norm(Xg[row] - Xo[row]) / np.linalg.norm(Xo[row]) < 1e-9
+    g.close()
+
+
+def test_df_strips_cover_every_row():
+    """p = 4 on 66 x 66 x 8 elements: the blocks walk two strips of 34 lines of direction
+    1, plane after plane, in windows that start at even rows. Every row of M x and K x
+    (3 vectors) matches the FP64 band product, and every launch shape gives the same
+    bits as every other."""
+    w = W.Workload("t", 3, (66, 66, 8), (4, 4, 4), 0.1, 3, 0.5, 1)
+    g = _gpu(w, op_form="assembled")
+    nvec = 3
+    x = _t(np.random.default_rng(9).standard_normal(nvec * g.N))
+    ref = {}
+    for name, apply in (("M", g.apply_M), ("K", g.apply_K)):
+        y = torch.empty_like(x)
+        apply(x, y, nvec)
+        ref[name] = _np(y)
+    g.set_op_form("assembled_df")
+    first = {}
+    for threads in (96, 128, 64, 256):
+        for nv in (1, 2, 3, 4):
+            g.set_band_config(threads, nv)
+            for name, apply in (("M", g.apply_M), ("K", g.apply_K)):
+                y = torch.full_like(x, float("nan"))
+                apply(x, y, nvec)
+                Y = _np(y)
+                r = ref[name]
+                assert np.all(np.isfinite(Y)), (threads, nv, name)
+                # M rows have terms of one sign; K rows cancel (bound relative to the largest entry)
+                assert np.abs(Y - r).max() <= 1e-12 * np.abs(r).max(), (threads, nv, name, np.abs(Y - r).max())
+                if name not in first:
+                    first[name] = Y
+                assert np.array_equal(Y, first[name]), (threads, nv, name)
     g.close()

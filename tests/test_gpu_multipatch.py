@@ -1,11 +1,17 @@
 """Parity of the multi-patch system (iga_mp_create: conforming patches, Sec. 5.1, with the
 additive Schwarz preconditioner, Sec. 5.4) with the multi-patch oracle on the same seeded
-layout: three deformed quadratic patches in a row (N_adj = 2), every operator form.
+layouts: three deformed quadratic patches in a row (N_adj = 2), an L of three patches (a
+re-entrant corner), a 2 x 2 grid of cubic patches (N_adj = 4) and a 2 x 2 x 2 grid of
+quadratic patches (N_adj = 8); every operator form, PCG, the critical step, the time
+steps (initial data and k = 2 steps) from the host loop, the captured step and the
+patches on concurrent streams.
 
 Tolerances: FP64 forms as for one patch (operators 1e-12 of max|y| for M and P_ad^{-1},
 1e-11 for K; solves at tol 1e-13 within 1e-10 relative, iteration counts within 1 of the
-oracle's PCG); the double-FP32 band products within 64 * 2^-48 (|A| |x|) + 1e-15 max|y|
-per entry."""
+oracle's PCG; steps at tol 1e-13 within 1e-10 in U and V); the double-FP32 band products
+within 64 * 2^-48 (|A| |x|) + 1e-15 max|y| per entry, and its steps (FP32 Kronecker local
+preconditioners, tol 1e-10) within 1e-8; lambda_max within 1e-8 of the dense generalised
+eigenvalue; captured and concurrent steps bitwise equal to the host loop."""
 
 import numpy as np
 import pytest
@@ -23,6 +29,9 @@ DEV = "cuda:0"
 
 LAYOUTS = {
     "row3_p2": lambda: WM.row_of_patches(3, 4, 2, amp=0.1),
+    "l3_p2": lambda: WM.l_shape(4, 2, amp=0.1),
+    "grid2x2_p3": lambda: WM.grid_of_patches((2, 2), 4, 3, amp=0.1),
+    "grid2x2x2_p2": lambda: WM.grid_of_patches((2, 2, 2), 2, 2, amp=0.1),
 }
 
 
@@ -89,3 +98,73 @@ def test_pcg_matches_the_oracle(layout):
             assert rel[v] <= 1e-13
     finally:
         sys_.close()
+
+
+def _dt(g, rho):
+    return 0.5 * np.sqrt(oracle.theta_crit(rho) / oracle.lambda_max_dense(g.M, g.K))
+
+
+def test_cfl_matches_the_oracle(layout):
+    patches, g = layout
+    sys_ = iga.MultiPatch(patches, tol=1e-13)
+    try:
+        lam, tau = sys_.cfl(0.5, iters=200)
+        ref = oracle.lambda_max_dense(g.M, g.K)
+        print("multi-patch lambda_max: GPU %.12g, dense %.12g" % (lam, ref))
+        assert abs(lam - ref) <= 1e-8 * ref
+        assert abs(tau - np.sqrt(oracle.theta_crit(0.5) / lam)) <= 1e-12 * tau
+    finally:
+        sys_.close()
+
+
+@pytest.mark.parametrize("form", [("matrix_free", "fp64", 1e-13, 1e-10), ("assembled_df", "banded32", 1e-10, 1e-8)])
+def test_steps_match_the_oracle(layout, form):
+    op_form, precond, tol, bound = form
+    patches, g = layout
+    k, rho, nsteps = 2, 0.5, 8
+    dt = _dt(g, rho)
+    rng = np.random.default_rng(6)
+    U0 = rng.standard_normal(g.N)
+    V0 = 0.3 * rng.standard_normal(g.N)
+    st = oracle.Stepper(g, k, rho, tol=1e-13)
+    X = st.init(U0, V0)
+    for _ in range(nsteps):
+        X = st.step(X, dt)
+    sys_ = iga.MultiPatch(patches, tol=tol, op_form=op_form, precond=precond)
+    try:
+        state = torch.zeros(3 * k * g.N, dtype=torch.float64, device=DEV)
+        sys_.state_init(k, _t(U0), _t(V0), state)
+        sg = sys_.step(state, k, rho, dt, nsteps)
+        assert sg.steps == nsteps and sg.max_relres <= tol
+        Xg = _np(state).reshape(3 * k, g.N)
+        for row, var in ((0, "U"), (1, "V")):
+            err = np.linalg.norm(Xg[row] - X[row]) / np.linalg.norm(X[row])
+            print("multi-patch steps (%s, %s) vs oracle, %s: %.3e" % (op_form, precond, var, err))
+            assert err <= bound, (var, err)
+    finally:
+        sys_.close()
+
+
+def test_captured_and_concurrent_steps_equal_the_host_loop(layout):
+    patches, g = layout
+    k, rho, nsteps = 2, 0.5, 5
+    dt = _dt(g, rho)
+    U0 = np.random.default_rng(8).standard_normal(g.N)
+    V0 = np.zeros(g.N)
+    finals = {}
+    for name, graphs, conc in (("host", False, False), ("graph", True, False), ("concurrent", False, True),
+                               ("graph_concurrent", True, True)):
+        sys_ = iga.MultiPatch(patches, tol=1e-12, op_form="assembled_df", precond="banded32")
+        try:
+            sys_.set_graphs(graphs)
+            if conc:
+                sys_.set_concurrent(True)
+            state = torch.zeros(3 * k * g.N, dtype=torch.float64, device=DEV)
+            sys_.state_init(k, _t(U0), _t(V0), state)
+            st = sys_.step(state, k, rho, dt, nsteps)
+            assert st.steps == nsteps
+            finals[name] = _np(state)
+        finally:
+            sys_.close()
+    for name in ("graph", "concurrent", "graph_concurrent"):
+        assert np.array_equal(finals[name], finals["host"]), name
