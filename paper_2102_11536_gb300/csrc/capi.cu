@@ -7,151 +7,11 @@
 #include <string>
 #include <vector>
 
-#include "iga_internal.h"
+#include "handle.h"
 
 using namespace iga;
 
-struct MpState;
-
-struct iga_handle {
-  int dim = 0;
-  iga_options opt{};
-  cudaStream_t stream = nullptr;
-  Tables1D tab[3];
-  DirDev dd[3]{};
-  int n[3] = {1, 1, 1}, Q[3] = {1, 1, 1}, m[3] = {1, 1, 1};
-  long long N = 0, Qt = 0;
-  double* ctrl = nullptr;   // SoA control net
-  double* W = nullptr;      // [Qt]
-  double* G = nullptr;      // [ng][Qt]
-  long long gstride = 0;
-  double* Dm = nullptr;     // diag(M)
-  double* scale = nullptr;  // D^{-1/2} Dhat^{1/2}
-  int* dflag = nullptr;     // device scratch flag
-  // assembled form
-  double* Mband = nullptr;
-  double* Kband = nullptr;
-  long long* band_off = nullptr;  // [H] linear offsets of the stored slots
-  int* band_o12 = nullptr;        // [H] packed offsets along directions 1, 2
-  int band_H = 0;
-  bool band_ready = false;
-  int band_threads = 0, band_nv = 0;  // launch configuration of the band product (0 = default)
-  long long ws_gen = 0;               // bumped whenever an address a captured graph may hold changes
-  double band_nnz = 0.0;          // nonzero couplings (for algorithmic flop counts)
-  // double-FP32 form of the band (IGA_OP_ASSEMBLED_DF)
-  float2* Mdf = nullptr;
-  float2* Kdf = nullptr;
-  int EAm = 0, EAk = 0;           // power-of-two exponents of the split bands
-  int* band_runs = nullptr;       // [nruns][4] runs of the upper half
-  int band_nruns = 0;
-  long long band_Np = 0;          // row stride of the split bands and vectors
-  long long df_slack = 0;         // zeroed elements before and after each split array
-  float2* df_xs = nullptr;        // [kMaxVec][Np] split input vectors (zero pads)
-  int* df_E = nullptr;            // [kMaxVec] their exponents, [kMaxVec] scratch
-  unsigned long long* df_part = nullptr;  // [kMaxVec][kDfBlocks] partial maxima
-  unsigned int* df_bar = nullptr;         // grid barrier of the cooperative split (count, generation)
-  long long bar_limit = -1;               // polls of that barrier before a time-out (< 0: the default)
-  bool df_ready = false;
-  DfTmaps tmM, tmK;               // tensor maps of the split bands (and vectors)
-  // operator workspace
-  int ws_vec = 0;
-  double *u0 = nullptr, *u1 = nullptr, *ta = nullptr, *tb = nullptr, *tc = nullptr;
-  long long su = 0, st = 0;
-  // PCG workspace
-  int cg_vec = 0;
-  double *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *f1 = nullptr, *f2 = nullptr;
-  double* partial = nullptr;  // 3 * kMaxVec * kRedBlocks
-  double* pq_part = nullptr;  // per-block partials of p.q from the band product, cg_vec * df_max_blocks
-  double* rz_part = nullptr;  // per-block partials of r.z, r.z_old from the preconditioner, 2 cg_vec (N / 32 + 2)
-  CgScalars cs{};
-  int* h_nactive = nullptr;   // pinned
-  // stepping
-  int step_k = 0;
-  double *Yneg = nullptr, *rhs = nullptr, *Z = nullptr, *Z2 = nullptr;
-  int hist = 0;
-  double* dstate = nullptr;
-  long long dstate_cap = 0;
-  // launch counting and profiling of one kernel class
-  long long nlaunch = 0;
-  int cur_active = 0;  // host-known number of active systems of the running PCG
-  int prof_class = IGA_PROF_OFF;
-  std::vector<cudaEvent_t> prof_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
-  double prof_flops = 0.0, prof_bytes = 0.0;
-  // captured step graph with the PCG loop on the device (conditional while node)
-  bool use_graphs = true;
-  cudaStream_t gs = nullptr, gbody = nullptr;  // non-default streams for capture and replay
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  bool gvalid = false;
-  struct GraphKey {
-    const double* state;
-    int k, op, prec, guess, max_iter;
-    double dt, rho, tol;
-  } gkey{};
-  long long g_pro = 0, g_body = 0, g_epi = 0;  // kernel launches captured before / in / after the loop
-  int* d_loop = nullptr;       // [2] iterations of the current solve, body executions since reset
-  long long* d_tot = nullptr;  // [kMaxVec] iterations per system slot, summed over solves
-  int* d_max = nullptr;        // [kMaxVec] largest count of one solve
-  double* d_init = nullptr;    // [kMaxVec] initial relative residuals, summed over solves
-  double last_init[kMaxVec] = {};  // initial relative residuals of the last host-driven solve
-  int* d_stat = nullptr;       // [2] first error status, any unconverged solve
-  // damping C = aM M + aK K and forcing F(t) = sum_m G_m sin(om_m t + ph_m) (eq. mp)
-  bool damped = false;
-  double aM = 0.0, aK = 0.0;
-  int nforce = 0;
-  double* fG = nullptr;  // [nforce][N] load vectors
-  double fom[kMaxForce] = {}, fph[kMaxForce] = {};
-  double *Yv = nullptr, *MYv = nullptr;  // [k][N] when aM != 0
-  int yv_k = 0;
-  double* d_time = nullptr;  // t_n on the device (advanced inside each step)
-  double time = 0.0;         // the same on the host
-  // learned initial guess (kernels_net.cu)
-  float *ws_theta = nullptr, *ws_m = nullptr, *ws_v = nullptr, *ws_grad = nullptr;
-  bool ws_params = false, ws_trained = false;
-  long long ws_adam_t = 0;
-  int ws_k = 0;                                         // stages the step buffers hold
-  double *ws_E = nullptr, *ws_B1 = nullptr, *ws_B2 = nullptr;  // [k][N]
-  double *ws_sc = nullptr, *ws_part = nullptr;          // scales [k][2], norm partials
-  __nv_bfloat16 *ws_x = nullptr, *ws_act = nullptr;     // [k][3][N], [k][16][N]
-  int ws_cap = 0, ws_count = 0;                         // recorded samples
-  __nv_bfloat16* ws_sx = nullptr;                       // [cap][3][N]
-  float* ws_st = nullptr;                               // [cap][N]
-  float *ws_y = nullptr, *ws_dy = nullptr;              // training: [N]
-  void* ws_work = nullptr;
-  double *ws_loss = nullptr, *ws_lpart = nullptr;
-  long long ws_loss_cap = 0;
-  double* pts = nullptr;  // [pts_cap] weighted point values (iga_integrate)
-  long long pts_cap = 0;
-  // multi-patch system (iga_mp_create): M, K and the additive Schwarz preconditioner act
-  // through the patches' own handles; null for a single patch
-  MpState* mp = nullptr;
-  std::string err;
-};
-
-// A multi-patch system of conforming patches (Sec. 5.1, 5.4): one handle per patch over
-// its index box, and the maps between global and local vectors.
-struct MpState {
-  std::vector<iga_handle*> patch;
-  std::vector<long long> off, nr;  // first entry and size of each patch's box
-  long long nloc = 0;              // sum of the box sizes
-  int n_adj = 0;
-  int op_form = IGA_OP_MATRIX_FREE, precond = IGA_PREC_FP64;  // the patches' forms
-  long long *d_gid = nullptr, *d_off = nullptr, *d_nr = nullptr, *d_crow = nullptr, *d_cent = nullptr;
-  int* d_epatch = nullptr;
-  MpMaps maps;
-  double *xl = nullptr, *yl = nullptr;  // [vec_cap][nloc] local inputs and results
-  int vec_cap = 0;
-  // concurrent patches (iga_mp_set_concurrent): one stream per patch, forked from and
-  // joined back into the caller's stream by events around every operator
-  bool concurrent = false;
-  std::vector<cudaStream_t> ps;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
-};
-
-namespace {
+namespace iga {
 
 thread_local std::string g_create_err;
 
@@ -160,26 +20,6 @@ int fail(iga_handle* h, int code, const std::string& msg) {
   else g_create_err = msg;
   return code;
 }
-
-#define CK(call)                                                                                   \
-  do {                                                                                             \
-    cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess)                                                                         \
-      return fail(h, IGA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));              \
-  } while (0)
-
-#define CKS(expr)                   \
-  do {                              \
-    int s_ = (expr);                \
-    if (s_ != IGA_OK) return s_;    \
-  } while (0)
-
-// a kernel launch: checked and counted
-#define LK(call)     \
-  do {               \
-    CK(call);        \
-    ++h->nlaunch;    \
-  } while (0)
 
 // Event bracket around the launches of one profiled kernel class.
 int prof_begin(iga_handle* h, int cls, cudaEvent_t* e1) {
@@ -207,35 +47,6 @@ int prof_end(iga_handle* h, cudaEvent_t e1, double flops, double bytes) {
   return IGA_OK;
 }
 
-template <typename T>
-int dalloc(iga_handle* h, T** p, size_t count) {
-  if (*p) {
-    cudaFree(*p);
-    *p = nullptr;
-  }
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return fail(h, IGA_ENOMEM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + " bytes): " +
-                                   cudaGetErrorString(e));
-  }
-  return IGA_OK;
-}
-
-template <typename T>
-int upload(iga_handle* h, T** p, const std::vector<T>& v) {
-  CKS(dalloc(h, p, v.size()));
-  CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return IGA_OK;
-}
-
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
-  p = nullptr;
-}
 
 // -- the method's parameters (Sec. 4.1, boxed formulas; eq. HOgamma) ----------
 // Block j = k: rho_b = rho_s = rho, alpha_f = 0. Blocks j < k: the boxed j<k
@@ -1427,7 +1238,7 @@ int create_handle(int dim, const int* degree, const int* nknots, const double* c
   return IGA_OK;
 }
 
-}  // namespace
+}  // namespace iga
 
 namespace iga {
 
@@ -2519,208 +2330,6 @@ int iga_autotune(iga_handle* h, int nvec, int reps, int* threads, int* nv) {
   if (threads) *threads = best_t;
   if (nv) *nv = best_v;
   return check_tc_error(h);
-}
-
-}  // extern "C"
-
-struct iga_batch {
-  std::vector<iga_handle*> p;
-  int device = 0;
-  cudaStream_t s0 = nullptr;
-  cudaEvent_t fork = nullptr, done = nullptr;
-  std::vector<cudaEvent_t> join;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  bool gvalid = false;
-  std::vector<iga_handle::GraphKey> keys;
-  std::vector<long long> gens;
-  std::string err;
-};
-
-namespace {
-
-int bfail(iga_batch* b, int code, const std::string& msg) {
-  b->err = msg;
-  return code;
-}
-
-void drop_batch_graph(iga_batch* b) {
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  b->gexec = nullptr;
-  b->graph = nullptr;
-  b->gvalid = false;
-}
-
-bool needs_host_loop(const iga_handle* h) {
-  const int g = h->opt.guess;
-  return !h->use_graphs || h->prof_class != IGA_PROF_OFF || (g == IGA_GUESS_LEARNED && h->ws_cap > 0) ||
-         !(g == IGA_GUESS_ZERO || g == IGA_GUESS_TAYLOR || h->hist >= 2);
-}
-
-// One graph: fork from b->s0 to every patch's capture stream, each patch's step,
-// join back on b->s0.
-int build_batch_graph(iga_batch* b, double* const* states, int k, double rho, const double* dt) {
-  drop_batch_graph(b);
-  const int np = (int)b->p.size();
-  for (int i = 0; i < np; ++i) {
-    const int rc = prepare_capture(b->p[i], k);
-    if (rc != IGA_OK) return bfail(b, rc, "patch " + std::to_string(i) + ": " + b->p[i]->err);
-  }
-  cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-  int rc = IGA_OK;
-  std::string msg;
-  e = cudaEventRecord(b->fork, b->s0);
-  for (int i = 0; i < np && rc == IGA_OK && e == cudaSuccess; ++i) {
-    iga_handle* h = b->p[i];
-    e = cudaStreamWaitEvent(h->gs, b->fork, 0);
-    if (e != cudaSuccess) break;
-    rc = capture_step(h, states[i], k, handle_coefs(h, k, rho, dt[i]));
-    if (rc != IGA_OK) {
-      msg = "patch " + std::to_string(i) + ": " + h->err;
-      break;
-    }
-    e = cudaEventRecord(b->join[i], h->gs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s0, b->join[i], 0);
-  }
-  cudaGraph_t g = nullptr;
-  const cudaError_t ee = cudaStreamEndCapture(b->s0, &g);
-  if (rc != IGA_OK || e != cudaSuccess || ee != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();
-    if (rc != IGA_OK) return bfail(b, rc, msg);
-    return bfail(b, IGA_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
-  }
-  cudaGraphExec_t ge = nullptr;
-  e = cudaGraphInstantiate(&ge, g, 0);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    cudaGetLastError();
-    return bfail(b, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-  }
-  b->graph = g;
-  b->gexec = ge;
-  b->gvalid = true;
-  b->keys.resize(np);
-  b->gens.resize(np);
-  for (int i = 0; i < np; ++i) {
-    b->keys[i] = graph_key(b->p[i], states[i], k, rho, dt[i]);
-    b->gens[i] = b->p[i]->ws_gen;
-  }
-  return IGA_OK;
-}
-
-bool batch_graph_current(const iga_batch* b, double* const* states, int k, double rho, const double* dt) {
-  if (!b->gvalid) return false;
-  for (size_t i = 0; i < b->p.size(); ++i)
-    if (!same_key(b->keys[i], graph_key(b->p[i], states[i], k, rho, dt[i])) || b->gens[i] != b->p[i]->ws_gen)
-      return false;
-  return true;
-}
-
-}  // namespace
-
-extern "C" {
-
-int iga_batch_create(int npatch, iga_handle* const* patches, iga_batch** out) {
-  if (!out) return IGA_EINVAL;
-  *out = nullptr;
-  if (npatch < 1 || !patches) return IGA_EINVAL;
-  for (int i = 0; i < npatch; ++i)
-    if (!patches[i] || patches[i]->mp || patches[i]->opt.device != patches[0]->opt.device) return IGA_EINVAL;
-  iga_batch* b = new (std::nothrow) iga_batch;
-  if (!b) return IGA_ENOMEM;
-  b->p.assign(patches, patches + npatch);
-  b->device = patches[0]->opt.device;
-  b->join.assign(npatch, nullptr);
-  bool ok = cudaSetDevice(b->device) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
-  for (int i = 0; ok && i < npatch; ++i)
-    ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    iga_batch_destroy(b);
-    return IGA_ECUDA;
-  }
-  *out = b;
-  return IGA_OK;
-}
-
-void iga_batch_destroy(iga_batch* b) {
-  if (!b) return;
-  cudaSetDevice(b->device);
-  if (b->s0) cudaStreamSynchronize(b->s0);
-  drop_batch_graph(b);
-  for (auto e : b->join)
-    if (e) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
-  if (b->done) cudaEventDestroy(b->done);
-  if (b->s0) cudaStreamDestroy(b->s0);
-  delete b;
-}
-
-const char* iga_batch_last_error(const iga_batch* b) { return b ? b->err.c_str() : ""; }
-
-int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, const double* dt, int nsteps,
-                   iga_stats* stats) {
-  if (!b) return IGA_EINVAL;
-  b->err.clear();
-  const int np = (int)b->p.size();
-  if (!states || !dt || k < 1 || k > kMaxK || nsteps < 0 || !(rho_inf >= 0.0 && rho_inf <= 1.0))
-    return bfail(b, IGA_EINVAL, "bad arguments");
-  for (int i = 0; i < np; ++i)
-    if (!states[i] || !(dt[i] > 0.0)) return bfail(b, IGA_EINVAL, "patch " + std::to_string(i) + ": bad state or dt");
-  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, IGA_ECUDA, "cudaSetDevice");
-  int done = 0;
-  auto host_steps = [&](int n) -> int {  // every patch through iga_step, one step at a time
-    for (int t = 0; t < n; ++t)
-      for (int i = 0; i < np; ++i) {
-        const int rc = iga_step(b->p[i], states[i], k, rho_inf, dt[i], 1, stats ? &stats[i] : nullptr);
-        if (rc != IGA_OK) return bfail(b, rc, "patch " + std::to_string(i) + ": " + b->p[i]->err);
-      }
-    return IGA_OK;
-  };
-  while (done < nsteps) {
-    bool any = false;
-    for (auto* h : b->p) any = any || needs_host_loop(h);
-    if (!any) break;
-    const int rc = host_steps(1);
-    if (rc != IGA_OK) return rc;
-    ++done;
-  }
-  const int n = nsteps - done;
-  if (n == 0) return IGA_OK;
-  if (!batch_graph_current(b, states, k, rho_inf, dt)) {
-    const int rc = build_batch_graph(b, states, k, rho_inf, dt);
-    if (rc != IGA_OK) return rc;
-  }
-  std::vector<long long> l0(np);
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < np && e == cudaSuccess; ++i) {
-    iga_handle* h = b->p[i];
-    l0[i] = h->nlaunch;
-    if (reset_graph_counters(h, b->s0) != IGA_OK) return bfail(b, IGA_ECUDA, h->err);
-    e = cudaEventRecord(h->ev_in, h->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s0, h->ev_in, 0);
-  }
-  for (int t = 0; t < n && e == cudaSuccess; ++t) e = cudaGraphLaunch(b->gexec, b->s0);
-  if (e == cudaSuccess) e = cudaEventRecord(b->done, b->s0);
-  for (int i = 0; i < np && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->p[i]->stream, b->done, 0);
-  if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("batch replay: ") + cudaGetErrorString(e));
-  int first = IGA_OK;
-  for (int i = 0; i < np; ++i) {
-    iga_handle* h = b->p[i];
-    const int rc = collect_graph_run(h, b->s0, k, n, dt[i], stats ? &stats[i] : nullptr);
-    if (stats) stats[i].launches += h->nlaunch - l0[i];
-    if (rc != IGA_OK && first == IGA_OK) {
-      first = rc;
-      b->err = "patch " + std::to_string(i) + ": " + h->err;
-    }
-  }
-  return first;
 }
 
 }  // extern "C"
