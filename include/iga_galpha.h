@@ -506,6 +506,28 @@ int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, c
                    iga_stats* stats);
 
 /*
+ * iga_batch_set_persistent -- on != 0: iga_batch_step advances the whole batch with ONE
+ * persistent, cooperative kernel launch per step (held in a CUDA graph): the blocks take
+ * (patch, tile) work items phase after phase -- Taylor predictor, the batched K product
+ * of every patch, PCG (mass products, the three axis phases of the Kronecker solve, the
+ * vector updates) until every system of every patch has converged, stage update --
+ * with a grid barrier between phases (bounded wait: a time-out returns IGA_ECUDA and the
+ * step's results are not to be used; iga_set_barrier_limit of patch 0 sets the limit).
+ * The per-system PCG scalars are reduced in a fixed order, so runs are reproducible;
+ * they are not bitwise those of the graph path, whose reductions are grouped otherwise.
+ * Forms (else IGA_EINVAL with a message, and the batch keeps the graph path): 3-D
+ * patches of degree 1..4, FP64 band operators (IGA_OP_ASSEMBLED), the band-Cholesky
+ * Kronecker preconditioner (IGA_PREC_BANDED, plain PCG, or IGA_PREC_BANDED32, flexible
+ * PCG) on every patch, the zero initial guess, no damping or loads, the same tolerance
+ * and iteration limit on every patch. Work vectors (9 k N doubles per patch at most)
+ * are allocated on the first step for a (k, rho_inf, dt, states) and kept. stats:
+ * steps, solves, iterations, largest relative residual per patch; the launches are
+ * counted on patch 0 (one per step). Semantics of the step otherwise as iga_batch_step.
+ * The paper has no counterpart (its patches are glued, Sec. 5.4; these share nothing).
+ */
+int iga_batch_set_persistent(iga_batch* b, int on);
+
+/*
  * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in
  * the paper; measurement aid): 8 independent FMA chains per thread, 4 blocks of 256
  * threads per SM, 2^14 iterations, averaged over 5 timed launches after 2

@@ -88,11 +88,12 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
                   const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out);
 
 /*
- * iga_mp_set_concurrent -- on != 0: every operator of the system runs its patches on
- * streams of their own, forked from and joined back into the system's stream by events
- * (a captured step then holds the patches as parallel branches); 0: one after another on
- * the system's stream (default). Results are the same either way. IGA_EINVAL for a
- * single-patch handle.
+ * iga_mp_set_concurrent -- on != 0: in the host-driven loop every operator of the system
+ * runs its patches on streams of their own, forked from and joined back into the system's
+ * stream by events; 0: one after another on the system's stream (default). A captured
+ * step (iga_set_graphs) always runs them one after another on its capture stream: streams
+ * joined to the step's capture cannot also join the capture of its PCG loop body. Results
+ * are the same either way. IGA_EINVAL for a single-patch handle.
  */
 int iga_mp_set_concurrent(iga_handle* h, int on);
 

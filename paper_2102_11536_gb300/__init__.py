@@ -110,6 +110,7 @@ def lib():
         "iga_batch_last_error": (ctypes.c_char_p, [H]),
         "iga_batch_step": (ctypes.c_int, [H, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
                                           ctypes.POINTER(Stats)]),
+        "iga_batch_set_persistent": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_mp_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ip, ip, ctypes.POINTER(ctypes.c_longlong), ip,
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]),
@@ -144,7 +145,7 @@ def exported_symbols():
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
             "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
-            "iga_integrate", "iga_set_barrier_limit"]
+            "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -643,6 +644,12 @@ class Batch:
         if rc != OK:
             raise IgaError(rc, "iga_batch_step: " + lib().iga_batch_last_error(self.b).decode())
         return res
+
+    def set_persistent(self, on=True):
+        """One persistent cooperative launch per batch step (iga_batch_set_persistent)."""
+        rc = lib().iga_batch_set_persistent(self.b, int(bool(on)))
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_set_persistent: " + lib().iga_batch_last_error(self.b).decode())
 
     def close(self):
         if getattr(self, "b", None):

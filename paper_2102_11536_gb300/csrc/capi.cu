@@ -560,12 +560,16 @@ int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double
     mp.vec_cap = nvec;
   }
   cudaStream_t s = h->stream;
+  // Patches on streams of their own in the host-driven loop only: inside a step capture
+  // (s is the capture or loop-body stream) they run in order on s, because the patch
+  // streams, once joined to the step's capture, cannot also join the loop body's.
+  const bool conc = mp.concurrent && s != h->gs && s != h->gbody;
   LK(launch_mp_gather(s, mp.maps, nvec, active, x, mp.xl));
-  if (mp.concurrent) CK(cudaEventRecord(mp.fork, s));
+  if (conc) CK(cudaEventRecord(mp.fork, s));
   for (size_t r = 0; r < mp.patch.size(); ++r) {
     iga_handle* p = mp.patch[r];
     p->stream = s;
-    if (mp.concurrent) {
+    if (conc) {
       CK(cudaStreamWaitEvent(mp.ps[r], mp.fork, 0));
       p->stream = mp.ps[r];
     }
@@ -578,7 +582,7 @@ int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double
                                 : apply_Pinv(p, nvec, active, xr, yr);
     h->nlaunch += p->nlaunch - l0;
     if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
-    if (mp.concurrent) {
+    if (conc) {
       CK(cudaEventRecord(mp.join[r], mp.ps[r]));
       CK(cudaStreamWaitEvent(s, mp.join[r], 0));
       p->stream = s;

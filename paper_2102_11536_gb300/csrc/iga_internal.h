@@ -330,6 +330,49 @@ cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* r
                            int H, const float2* A, long long Np, int EA, const int* active, int nvec,
                            const float2* xs, const int* Ex, const double* x, double* y, long long vs, int threads,
                            int nv, double* pq, int* npq, int* err, const DfTmaps* tm);
+// Persistent batch step (kernels_persist.cu): one cooperative launch advances every
+// patch of a batch by one time step with FP64 band operators and the band-Cholesky
+// Kronecker preconditioner (FP32 or FP64). Device tables, built by the host.
+struct PPatch {
+  long long N;
+  int n[3], deg[3], H;
+  const double *M, *K;          // [H][N] FP64 bands
+  const long long* off;         // [H] linear offsets of the stored slots
+  const int* o12;               // [H] packed offsets along directions 1, 2
+  const double* scale;          // [N] D^-1/2 Dhat^1/2
+  const void *L[3], *dinv[3];   // band Cholesky factors per axis ([n][p+1], [n]), FP32 or FP64
+  double* X;                    // state [3k][N] (the caller's)
+  double *Y, *T, *r, *x, *z, *p, *q;  // [k][N] work vectors
+  void *t1, *t2;                // [k][N] intermediates of the Kronecker solve
+  StepCoefs sc;
+};
+struct PBatch {
+  int np, k, max_iter, flexible;
+  double tol2;
+  const PPatch* pt;                   // [np]
+  const int2* rtile;                  // [nrt] (patch, row tile within the patch)
+  const int2* ltile[3];               // [nlt[a]] (patch, line tile within the patch)
+  int nrt, nlt[3];
+  const int *rt0, *nrt_p, *lt2, *nlt2_p;  // [np] first tile and tile count per patch (rows; axis-2 lines)
+  double* const* Yp;                  // [np] the patches' Y, r, p, q (band-product operands)
+  double* const* rp;
+  double* const* pp;
+  double* const* qp;
+  double* part;                       // [nrt][k] row-tile partials
+  double* lpart;                      // [2][nlt[2]][k] axis-2 partials of r.z (new, previous z)
+  double *bb, *rr, *rz, *rznew, *rzold, *pq, *alpha, *beta, *last_rel;  // [np k]
+  int *active, *iters, *status, *max_iters;                              // [np k]
+  long long* tot_iters;                                                  // [np k]
+  int* flags;                         // [0] some system active, [1] first failure status
+  unsigned int* bar;                  // grid barrier (count, generation)
+  long long bar_limit;
+  int* err;                           // set when a barrier wait runs out
+};
+int batch_row_tiles(long long N);
+int batch_line_tiles(long long N, int n);
+size_t batch_smem_bytes(int nmax, int pmax, bool f32);
+cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid);
+
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);
 cudaError_t launch_probe_extract(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol,

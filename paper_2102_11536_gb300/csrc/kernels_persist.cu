@@ -1,0 +1,559 @@
+// One persistent, cooperative launch per time step of a batch of independent patches:
+// every patch's Taylor predictor, batched K product, k mass solves by PCG with the
+// diagonal-scaled Kronecker preconditioner (def:single_patch_prec; the Kronecker
+// inverse by band Cholesky along each direction, Sec. 5.5) and stage update (Sec. 4,
+// eq. ho1-ho3). The work of each phase is a list of (patch, tile) items -- row tiles of
+// kPRows rows for the band products and vector updates, tiles of kPLines lines for the
+// axis solves -- which the resident blocks take in turn; phases are separated by a grid
+// barrier whose wait is bounded (a time-out sets the error word and every block
+// returns). The per-system scalars of PCG (one system per patch and stage) are summed by
+// one block from per-tile partials in a fixed order, so a run is reproducible.
+//
+// Arithmetic per row and line as in the single-patch kernels: the FP64 band product
+// (diagonal, then per stored slot the upper and the lower term), the band-Cholesky
+// substitutions with the factor rows scaled by 1 / L_kk (FP32 or FP64), the predictor
+// and update of k_predict / k_update. PCG: Hestenes-Stiefel with the FP64 Kronecker
+// solve, the flexible (Polak-Ribiere) beta with the FP32 one; stop at
+// ||r|| <= tol ||b||; x0 = 0.
+#include "iga_internal.h"
+
+namespace iga {
+
+namespace {
+
+constexpr int kPThreads = 256;     // threads per block
+constexpr int kPRows = kPThreads;  // rows per row tile: one per thread
+constexpr int kPLines = 32;        // lines per line tile: one warp runs the substitutions
+constexpr int kPLS = kPLines + 1;  // shared row stride of a staged tile (odd: no bank conflicts)
+
+// Grid barrier (arrival count bar[0], generation bar[1]). The wait is bounded: after
+// `limit` polls, or once another block has reported a time-out, the block records one
+// and the caller returns. Every block arrives before it waits, so the count is reset by
+// the last one to arrive even when some gave up.
+__device__ bool pgrid_sync(unsigned int* bar, long long limit, int* err) {
+  __shared__ int gave_up;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gave_up = 0;
+    __threadfence();
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g0 = *gen;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g0) {
+        if (++it > limit || *(volatile int*)err) {
+          atomicExch(err, 1);
+          gave_up = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return gave_up == 0;
+}
+
+// out[s] = sum over the patch's tiles t of part[(t0 + t) k + j], s = patch k + j, by the
+// block's warps (lanes take fixed strided shares, then a shuffle tree): a fixed order
+__device__ void psum_systems(const PBatch& B, const double* part, const int* t0, const int* nt, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int S = B.np * B.k;
+  for (int s = w; s < S; s += kPThreads / 32) {
+    const int pi = s / B.k, j = s - pi * B.k;
+    double a = 0.0;
+    for (int t = lane; t < nt[pi]; t += 32) a += *(volatile const double*)&part[(long long)(t0[pi] + t) * B.k + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) out[s] = a;
+  }
+}
+
+// fixed-order block sum of one value per thread (valid in thread 0)
+__device__ double pblock_sum(double v) {
+  __shared__ double red[kPThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kPThreads / 32; ++q) s += red[q];
+  return s;
+}
+
+// ---------------------------------------------------------------- row-tile phases
+// Taylor predictor: Y[j] = -Y_j (the argument of K, negated), T[j] = T_{s_j}; x[j] = 0
+template <int K>
+__device__ void ph_predict(const PBatch& B) {
+  constexpr int R = 3 * K;
+  for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
+    const int2 tl = B.rtile[it];
+    const PPatch& P = B.pt[tl.x];
+    const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    if (i >= N) continue;
+    double xr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) xr[r] = P.X[r * N + i];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int row = 3 * j + 2, ry = row - 2;
+      double y;
+      if (j < K - 1) {
+        y = 0.0;
+#pragma unroll
+        for (int r = R - 1; r >= ry; --r) y = fma(P.sc.c[r - ry], xr[r], y);
+      } else {
+        y = xr[ry];
+      }
+      P.Y[j * N + i] = -y;
+      P.z[j * N + i] = 0.0;  // the previous z of the first flexible beta
+      double t = 0.0;
+#pragma unroll
+      for (int r = R - 1; r >= row; --r) t = fma(P.sc.c[r - row], xr[r], t);
+      P.T[j * N + i] = t;
+      P.x[j * N + i] = 0.0;
+    }
+  }
+}
+
+// y[j] = A x[j] for the patch's active systems (mask act), one row per thread; with
+// dot, the per-tile partials of x[j].y[j] (dot = 1) or y[j].y[j] (dot = 2) into part
+template <int K>
+__device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, double* const* ys, int dot,
+                        double* part) {
+  for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
+    const int2 tl = B.rtile[it];
+    const PPatch& P = B.pt[tl.x];
+    const double* x = xs[tl.x];
+    double* y = ys[tl.x];
+    const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    const bool row = i < N;
+    const int* act = B.active + tl.x * K;
+    const double* A = stiff ? P.K : P.M;
+    bool on[K];
+    double acc[K], xi[K];
+    const double a0 = row ? A[i] : 0.0;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+      on[v] = row && (stiff || act[v]);
+      xi[v] = on[v] ? x[v * N + i] : 0.0;
+      acc[v] = a0 * xi[v];
+    }
+    int i1 = 0, i2 = 0;
+    if (row) {
+      const long long t = i / P.n[0];
+      i1 = (int)(t % P.n[1]);
+      i2 = (int)(t / P.n[1]);
+    }
+    for (int h = 1; h < P.H; ++h) {
+      const long long L = P.off[h];
+      const long long jp = i + L, jm = i - L;
+      const int pk = P.o12[h];
+      const int o1 = (pk & 255) - 64, o2 = ((pk >> 8) & 255) - 64;
+      const bool up = row && jp >= 0 && jp < N && (unsigned)(i1 + o1) < (unsigned)P.n[1] &&
+                      (unsigned)(i2 + o2) < (unsigned)P.n[2];
+      const bool dn = row && jm >= 0 && jm < N && (unsigned)(i1 - o1) < (unsigned)P.n[1] &&
+                      (unsigned)(i2 - o2) < (unsigned)P.n[2];
+      if (!__any_sync(0xffffffffu, up || dn)) continue;
+      const double* Ah = A + (long long)h * N;
+      if (up) {
+        const double a = Ah[i];
+#pragma unroll
+        for (int v = 0; v < K; ++v)
+          if (on[v]) acc[v] = fma(a, x[v * N + jp], acc[v]);
+      }
+      if (dn) {
+        const double a = Ah[jm];
+#pragma unroll
+        for (int v = 0; v < K; ++v)
+          if (on[v]) acc[v] = fma(a, x[v * N + jm], acc[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < K; ++v)
+      if (on[v]) y[v * N + i] = acc[v];
+    if (dot) {
+#pragma unroll
+      for (int v = 0; v < K; ++v) {
+        const double t = on[v] ? (dot == 1 ? xi[v] : acc[v]) * acc[v] : 0.0;
+        const double s = pblock_sum(t);
+        if (threadIdx.x == 0) part[(long long)it * K + v] = s;
+      }
+    }
+  }
+}
+
+// p = z (first) or z + beta p; active systems
+template <int K>
+__device__ void ph_dir(const PBatch& B, bool first) {
+  for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
+    const int2 tl = B.rtile[it];
+    const PPatch& P = B.pt[tl.x];
+    const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    if (i >= N) continue;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+      const int s = tl.x * K + v;
+      if (!B.active[s]) continue;
+      const double zv = P.z[v * N + i];
+      P.p[v * N + i] = first ? zv : fma(B.beta[s], P.p[v * N + i], zv);
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q; partials of r.r
+template <int K>
+__device__ void ph_xr(const PBatch& B) {
+  for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
+    const int2 tl = B.rtile[it];
+    const PPatch& P = B.pt[tl.x];
+    const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    const bool row = i < N;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+      const int s = tl.x * K + v;
+      double t = 0.0;
+      if (row && B.active[s]) {
+        const double al = B.alpha[s];
+        P.x[v * N + i] = fma(al, P.p[v * N + i], P.x[v * N + i]);
+        const double rn = fma(-al, P.q[v * N + i], P.r[v * N + i]);
+        P.r[v * N + i] = rn;
+        t = rn * rn;
+      }
+      const double sum = pblock_sum(t);
+      if (threadIdx.x == 0) B.part[(long long)it * K + v] = sum;
+    }
+  }
+}
+
+// stage update from the solutions x[j] = Z_j and the predictor
+template <int K>
+__device__ void ph_update(const PBatch& B) {
+  constexpr int R = 3 * K;
+  for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
+    const int2 tl = B.rtile[it];
+    const PPatch& P = B.pt[tl.x];
+    const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    if (i >= N) continue;
+    double xr[R], t[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) xr[r] = P.X[r * N + i];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      double s = 0.0;
+#pragma unroll
+      for (int r = R - 1; r >= q; --r) s = fma(P.sc.c[r - q], xr[r], s);
+      t[q] = s;
+    }
+    const double tau = P.sc.tau;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int row = 3 * j + 2;
+      const double Pj = (P.x[j * N + i] - t[row]) / P.sc.alpha[j];
+      P.X[row * N + i] = t[row] + Pj;
+      P.X[(row - 1) * N + i] = fma(P.sc.gamma[j] * tau, Pj, t[row - 1]);
+      P.X[(row - 2) * N + i] = fma(P.sc.beta[j] * tau * tau, Pj, t[row - 2]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Kronecker solve
+// One line tile of axis a for every active system of the patch: lines are staged in
+// shared memory (entry k of line l at k kPLS + l), kPLines threads run the forward and
+// backward substitutions (factor rows scaled by 1 / L_kk, recurrence window in
+// registers), and the lines are written back. Axis 0 reads r scaled by D^-1/2 Dhat^1/2
+// into t1; axis 1 t1 -> t2; axis 2 t2 -> z scaled again, with the partials of r.z (new)
+// and r.z (the previous z) of each system.
+template <int P, typename T>
+__device__ void solve_lines(T* sb, const T* sF, const T* sG, int n, int nl) {
+  const int t = threadIdx.x;
+  if (t >= nl) return;
+  T win[P + 1];
+#pragma unroll
+  for (int d = 0; d <= P; ++d) win[d] = T(0);
+  for (int k = 0; k < n; ++k) {
+    const T* F = sF + (size_t)k * (P + 1);
+    T acc = F[0] * sb[k * kPLS + t];
+#pragma unroll
+    for (int d = P; d >= 2; --d) acc -= F[d] * win[d];
+    const T w = acc - F[1] * win[1];
+    sb[k * kPLS + t] = w;
+#pragma unroll
+    for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+    win[1] = w;
+  }
+#pragma unroll
+  for (int d = 0; d <= P; ++d) win[d] = T(0);
+  for (int k = n - 1; k >= 0; --k) {
+    const T* G = sG + (size_t)k * (P + 1);
+    T acc = G[0] * sb[k * kPLS + t];
+#pragma unroll
+    for (int d = P; d >= 2; --d) acc -= G[d] * win[d];
+    const T z = acc - G[1] * win[1];
+    sb[k * kPLS + t] = z;
+#pragma unroll
+    for (int d = P; d >= 2; --d) win[d] = win[d - 1];
+    win[1] = z;
+  }
+}
+
+template <int K, typename T>
+__device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
+  for (int it = blockIdx.x; it < B.nlt[a]; it += gridDim.x) {
+    const int2 tl = B.ltile[a][it];
+    const PPatch& Pp = B.pt[tl.x];
+    const int n = Pp.n[a], p = Pp.deg[a];
+    const long long N = Pp.N;
+    const long long A = a == 0 ? 1 : (a == 1 ? (long long)Pp.n[0] : (long long)Pp.n[0] * Pp.n[1]);
+    const long long Rl = N / n;  // lines along axis a
+    const long long l0 = (long long)tl.y * kPLines;
+    const int nl = (int)min((long long)kPLines, Rl - l0);
+    T* sb = reinterpret_cast<T*>(smem);
+    T* sF = sb + (size_t)n * kPLS;
+    T* sG = sF + (size_t)n * (p + 1);
+    const T* L = static_cast<const T*>(Pp.L[a]);
+    const T* dinv = static_cast<const T*>(Pp.dinv[a]);
+    __syncthreads();  // the previous item's shared data is consumed
+    for (int e = threadIdx.x; e < n * (p + 1); e += kPThreads) {
+      const int k = e / (p + 1), d = e - k * (p + 1);
+      const T dk = dinv[k];
+      sF[e] = d == 0 ? dk : dk * L[e];
+      sG[e] = d == 0 ? dk : (k + d < n ? dk * L[(size_t)(k + d) * (p + 1) + d] : T(0));
+    }
+    for (int v = 0; v < K; ++v) {
+      const int s = tl.x * K + v;
+      const bool on = B.active[s] != 0;  // uniform over the block
+      const T* tin = a == 1 ? static_cast<const T*>(Pp.t1) : static_cast<const T*>(Pp.t2);
+      T* tout = a == 0 ? static_cast<T*>(Pp.t1) : static_cast<T*>(Pp.t2);
+      double snew = 0.0, sold = 0.0;
+      if (on) {
+        __syncthreads();
+        // stage: (entry k, line l) of the tile <- element xx + A (k + n y) of the input,
+        // line l0 + l = xx + A y
+        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
+          int k, l;
+          if (a == 0) { l = e / n; k = e - l * n; }  // consecutive entries of one line are adjacent
+          else { k = e / nl; l = e - k * nl; }       // consecutive lines are adjacent
+          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
+          const long long g = xx + A * (k + (long long)n * y);
+          T u;
+          if (a == 0) u = (T)(Pp.r[v * N + g] * Pp.scale[g]);
+          else u = tin[v * N + g];
+          sb[k * kPLS + l] = u;
+        }
+        __syncthreads();
+        switch (p) {
+          case 2: solve_lines<2, T>(sb, sF, sG, n, nl); break;
+          case 3: solve_lines<3, T>(sb, sF, sG, n, nl); break;
+          case 4: solve_lines<4, T>(sb, sF, sG, n, nl); break;
+          default: solve_lines<1, T>(sb, sF, sG, n, nl); break;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
+          int k, l;
+          if (a == 0) { l = e / n; k = e - l * n; }
+          else { k = e / nl; l = e - k * nl; }
+          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
+          const long long g = xx + A * (k + (long long)n * y);
+          if (a == 2) {
+            const double zn = (double)sb[k * kPLS + l] * Pp.scale[g];
+            const double rg = Pp.r[v * N + g];
+            sold = fma(rg, Pp.z[v * N + g], sold);
+            snew = fma(rg, zn, snew);
+            Pp.z[v * N + g] = zn;
+          } else {
+            tout[v * N + g] = sb[k * kPLS + l];
+          }
+        }
+      }
+      if (a == 2) {
+        const double s1 = pblock_sum(snew), s2 = pblock_sum(sold);
+        if (threadIdx.x == 0) {
+          B.lpart[(long long)it * K + v] = s1;
+          B.lpart[(long long)(B.nlt[2] + it) * K + v] = s2;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scalar updates (block 0)
+// start: ||b||^2, ||r||^2 = ||b||^2, activity, counters
+__device__ void lead_start(const PBatch& B) {
+  psum_systems(B, B.part, B.rt0, B.nrt_p, B.bb);
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
+    B.rr[s] = B.bb[s];
+    B.active[s] = B.bb[s] > 0.0 ? 1 : 0;
+    B.iters[s] = 0;
+  }
+}
+
+// after the preconditioner: r.z, and beta for the next direction (plain or flexible)
+__device__ void lead_rz(const PBatch& B, bool first) {
+  psum_systems(B, B.lpart, B.lt2, B.nlt2_p, B.rznew);
+  psum_systems(B, B.lpart + (long long)B.nlt[2] * B.k, B.lt2, B.nlt2_p, B.rzold);
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
+    if (!B.active[s]) continue;
+    if (!first) {
+      const double num = B.flexible ? B.rznew[s] - B.rzold[s] : B.rznew[s];
+      B.beta[s] = num / B.rz[s];
+    }
+    B.rz[s] = B.rznew[s];
+  }
+}
+
+// after q = M p: alpha = r.z / p.q (breakdown stops the system)
+__device__ void lead_alpha(const PBatch& B) {
+  psum_systems(B, B.part, B.rt0, B.nrt_p, B.pq);
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
+    if (!B.active[s]) continue;
+    const double pq = B.pq[s];
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(B.rz[s])) {
+      B.active[s] = 0;
+      B.status[s] = 1;
+      B.alpha[s] = 0.0;
+    } else {
+      B.alpha[s] = B.rz[s] / pq;
+    }
+  }
+}
+
+// after the x, r update: ||r||^2, iteration count, convergence; flags[0] = any active
+__device__ void lead_check(const PBatch& B) {
+  psum_systems(B, B.part, B.rt0, B.nrt_p, B.rr);
+  __syncthreads();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
+    if (!B.active[s]) continue;
+    const int it = B.iters[s] + 1;
+    B.iters[s] = it;
+    if (B.rr[s] <= B.tol2 * B.bb[s]) {
+      B.active[s] = 0;
+    } else if (it >= B.max_iter) {
+      B.active[s] = 0;
+      B.status[s] = 2;
+    } else {
+      atomicOr(&any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) B.flags[0] = any;
+}
+
+// end of a step: iteration statistics
+__device__ void lead_stats(const PBatch& B) {
+  for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
+    B.tot_iters[s] += B.iters[s];
+    B.max_iters[s] = max(B.max_iters[s], B.iters[s]);
+    const double rel = B.bb[s] > 0.0 ? sqrt(B.rr[s] / B.bb[s]) : 0.0;
+    B.last_rel[s] = rel;
+    if (B.status[s]) B.flags[1] = B.status[s];
+  }
+}
+
+// the preconditioner z = P^-1 r (three axis phases) and the r.z scalars
+template <int K, typename T>
+__device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first) {
+  for (int a = 0; a < 3; ++a) {
+    ph_axis<K, T>(B, a, smem);
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+  }
+  if (blockIdx.x == 0) lead_rz(B, first);
+  return pgrid_sync(B.bar, B.bar_limit, B.err);
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_batch_step(const PBatch B) {
+  extern __shared__ __align__(16) unsigned char psmem[];
+  ph_predict<K>(B);
+  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+  // b = K (-Y) into r (x0 = 0: r = b), partials of b.b
+  ph_band<K>(B, true, B.Yp, B.rp, 2, B.part);
+  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+  if (blockIdx.x == 0) lead_start(B);
+  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+  if (!pprecond<K, T>(B, psmem, true)) return;
+  bool first = true;
+  for (int iter = 0;; ++iter) {
+    ph_dir<K>(B, first);
+    first = false;
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    ph_band<K>(B, false, B.pp, B.qp, 1, B.part);  // q = M p, partials of p.q
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    if (blockIdx.x == 0) lead_alpha(B);
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    ph_xr<K>(B);
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    if (blockIdx.x == 0) lead_check(B);
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    if (*(volatile int*)&B.flags[0] == 0) break;  // the same value in every block
+    if (!pprecond<K, T>(B, psmem, false)) return;
+  }
+  ph_update<K>(B);
+  if (blockIdx.x == 0) lead_stats(B);
+}
+
+template <int K, typename T>
+cudaError_t batch_go(cudaStream_t s, const PBatch& B, size_t smem, int sms, int* grid_out) {
+  auto kern = k_batch_step<K, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kPThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  const int grid = per * sms;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (grid_out) *grid_out = grid;
+  return cudaLaunchKernelEx(&cfg, kern, B);
+}
+
+}  // namespace
+
+int batch_row_tiles(long long N) { return (int)((N + kPRows - 1) / kPRows); }
+int batch_line_tiles(long long N, int n) { return (int)((N / n + kPLines - 1) / kPLines); }
+size_t batch_smem_bytes(int nmax, int pmax, bool f32) {
+  return (size_t)nmax * (kPLS + 2 * (pmax + 1)) * (f32 ? sizeof(float) : sizeof(double)) + 64;
+}
+
+cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid) {
+  int dev = 0, sms = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess) return e;
+  if (!coop) return cudaErrorNotSupported;
+#define IGA_BG(KK) return f32 ? batch_go<KK, float>(s, B, smem, sms, grid) : batch_go<KK, double>(s, B, smem, sms, grid)
+  switch (B.k) {
+    case 1: IGA_BG(1);
+    case 2: IGA_BG(2);
+    case 3: IGA_BG(3);
+    case 4: IGA_BG(4);
+    default: return cudaErrorInvalidValue;
+  }
+#undef IGA_BG
+}
+
+}  // namespace iga
