@@ -65,6 +65,8 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 1.201 TFLOP/s at ~1.98 GHz (the FP64 probe's profile summary).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
+# FP32 operations per second of one GB300 (one per lane and clock): 152 SMs x 128 lanes x 2.07 GHz
+FP32_ISSUE_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 ERR_LIMIT = 1e-8
 
 FORMS = [
@@ -122,6 +124,8 @@ def arithmetic(opts):
 NCU_TRAFFIC = {
     ("band_mass", "6428c7f922f0f6eb", "cube64_p3", 2): 373.9e6,   # k_band_spmv<2, 64>
     ("band_mass_df", "089aa6988b2aaa18", "cube64_p3", 2): 390.2e6,  # k_band_df_tm<3, 2>
+    # k_band_df_tm<4, 3>, 128 rows per block, strips of 26 lines, one buffer
+    ("band_mass_df", "66e15df8082f7af7", "cube128_p4", 3): 8.325e9,
     # k_mid_mass<4>, captured at file hash 618d068dc16a5b19; the file's later edit touched
     # only launch_geometry's host code (k_mid_mass byte-identical), hence the new key
     ("mass", "2b7c940689f4c144", "cube64_p3", 1): 186.69e6,
@@ -150,7 +154,7 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
-    ap.add_argument("--multipatch-steps", type=int, default=0,
+    ap.add_argument("--multipatch-steps", type=int, default=20,
                     help="timed steps of the conforming multi-patch system (2 x 2 x 2 glued patches, additive "
                          "Schwarz preconditioner; 0 = skip)")
     ap.add_argument("--multipatch-nel", type=int, default=24, help="elements per direction of each glued patch")
@@ -382,6 +386,13 @@ def roofline(prof_class, opts, kdesc, prof, hbm, hbm_kind, w):
                          "note": "the bytes the assembled band form reads (%d slots of 8 B per row + vectors): "
                                  "%.2fx the method's" % (H, prof_bytes / max(alg, 1.0))},
            "fp64_equivalent_view": {"achieved_tflops": tfl, "fp64_peak_tflops": FP64_PEAK_TFLOPS}}
+    if opts["op_form"] == "assembled_df":
+        # the double-FP32 term (exact product by FMA, TwoSum, the error sums) is 12 FP32 operations;
+        # the profiler's flops count 2 per term
+        ops = 6.0 * prof_flops / sec / 1e12
+        out["alu_view"] = {"fp32_ops_per_term": 12, "achieved_tops": ops, "peak_tops": FP32_ISSUE_PEAK_TOPS,
+                           "frac": ops / FP32_ISSUE_PEAK_TOPS,
+                           "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"}
     # an ncu capture of a launch with `nv` vectors, scaled to the average launch by the band
     # bytes it reads (the traffic follows them: coefficients once, vectors once per vector)
     for nv in range(1, 9):
@@ -584,11 +595,13 @@ def sample_parity(args, iga, torch, dev, ws, dt, nst, Xo, forms):
 
 
 def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
-    """The 48-patch batch, per-patch dt = 0.5 tau_crit, autotuned band launches, one
-    graph launch per batch step against the same patches stepped one after the other
-    (each with its own graph): first with FP64 assembled operators and the BF16
-    preconditioner, then the FP32 band-Cholesky one, then double-FP32 band products
-    with it (the reported value).
+    """The 48-patch batch, per-patch dt = 0.5 tau_crit. The reported value: FP64 band operators
+    with the BF16 preconditioner (the configuration's form), one persistent cooperative launch
+    per batch step. Variants: the same persistent launch with the FP32 band-Cholesky Kronecker
+    solve, and one graph launch per batch step holding every patch's own step (autotuned band
+    launches) with FP64 band operators and the BF16 tensor-core or the FP32 Kronecker
+    preconditioner, and with double-FP32 band products -- the graph paths against the same
+    patches stepped one after the other.
     Under torchrun the patches are sharded over the ranks (longest-processing-time
     partition by estimated work, no collective on the data path); times are the
     maximum over ranks."""
@@ -667,41 +680,73 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     sst = [iga.Stats() for _ in pats]
     alone()  # each patch captures its own graph for the new form
     ms_alone_df = timed(alone, nb)
-    (ms_batch, ms_alone, ms_b32, ms_df, ms_alone_df), (ndof, iters, solves, launches, it32, so32, itdf, sodf,
-                                                       launchdf) = combine_over_ranks(
-        torch, pg, dev, [ms_batch, ms_alone, ms_b32, ms_df, ms_alone_df],
+    # one persistent cooperative launch per batch step, FP64 band operators: the configuration's BF16
+    # preconditioner (the reported value), then the FP32 band-Cholesky Kronecker solve
+    def persistent(precond):
+        for g in pats:
+            g.set_op_form("assembled")
+            g.set_precond(precond)
+        for g, st, (u0, v0) in zip(pats, states, inits):
+            g.state_init(k, u0, v0, st)
+        b.set_persistent(True)
+        for _ in range(args.warmup):
+            b.step(states, k, rho, dts, 1)
+        sp = [iga.Stats() for _ in pats]
+        ms = timed(lambda: b.step(states, k, rho, dts, 1, sp), nb)
+        b.set_persistent(False)
+        return ms, sp
+
+    ms_p, statsp = persistent("bf16")
+    ms_p32, statsp32 = persistent("banded32")
+    (ms_batch, ms_alone, ms_b32, ms_df, ms_alone_df, ms_p, ms_p32), (
+        ndof, iters, solves, launches, it32, so32, itdf, sodf, launchdf, itp, sop, launchp, itp32, sop32,
+        launchp32) = combine_over_ranks(
+        torch, pg, dev, [ms_batch, ms_alone, ms_b32, ms_df, ms_alone_df, ms_p, ms_p32],
         [sum(g.N for g in pats), sum(s.iters for s in stats), sum(s.solves for s in stats),
          sum(s.launches for s in stats), sum(s.iters for s in stats32), sum(s.solves for s in stats32),
-         sum(s.iters for s in statsdf), sum(s.solves for s in statsdf), sum(s.launches for s in statsdf)])
+         sum(s.iters for s in statsdf), sum(s.solves for s in statsdf), sum(s.launches for s in statsdf),
+         sum(s.iters for s in statsp), sum(s.solves for s in statsp), sum(s.launches for s in statsp),
+         sum(s.iters for s in statsp32), sum(s.solves for s in statsp32), sum(s.launches for s in statsp32)])
     out = {
         "workload": "48 independent 3-D patches, nel ~ U{16..96} per axis, p in {2,3,4}, per-coordinate "
                     "deformation amplitudes ~ U(0, 0.15), k=2, rho_inf=0.5, per-patch dt = 0.5 tau_crit, "
-                    "PCG tol 1e-10, zero guess; double-FP32 band products (op form assembled_df) with the FP32 "
-                    "band-Cholesky Kronecker preconditioner",
+                    "PCG tol 1e-10, zero guess; FP64 band operators with the BF16 preconditioner (the "
+                    "configuration's form), one persistent cooperative launch per batch step",
         "patches": len(allw),
         "total_dofs": int(ndof),
         "ranks": world,
         "patches_per_rank": [len(sh) for sh in shards],
         "batch_steps": nb,
-        "value": nb / (ms_df / 1e3),
+        "value": nb / (ms_p / 1e3),
         "unit": "batch steps/s (every patch advanced one step)",
-        "dof_updates_per_s": ndof * nb / (ms_df / 1e3),
-        "ms_per_batch_step": ms_df / nb,
-        "pcg_iters_per_solve": itdf / max(sodf, 1.0),
-        "gpu_launches_per_batch_step": launchdf / nb,
+        "dof_updates_per_s": ndof * nb / (ms_p / 1e3),
+        "ms_per_batch_step": ms_p / nb,
+        "pcg_iters_per_solve": itp / max(sop, 1.0),
+        "gpu_launches_per_batch_step": launchp / nb,
         "graph_launches_per_batch_step_per_rank": 1,
-        "sequential": {"ms_per_batch_step": ms_alone_df / nb, "value": nb / (ms_alone_df / 1e3),
-                       "note": "the same patches stepped one after another, each replaying its own step graph"},
-        "speedup_vs_sequential": ms_alone_df / ms_df,
-        "autotuned_band_configs_rank0": tuned_df,
+        "arithmetic": "f64 state, residuals, dots and band K, M; bf16 x f32-accumulate fast-diagonalisation mode "
+                      "products on CUDA cores inside the persistent kernel",
         "variants": {
-            "fp64_band_bf16_preconditioner": {
+            "persistent_fp64_band_banded32_preconditioner": {
+                "value": nb / (ms_p32 / 1e3), "dof_updates_per_s": ndof * nb / (ms_p32 / 1e3),
+                "ms_per_batch_step": ms_p32 / nb, "pcg_iters_per_solve": itp32 / max(sop32, 1.0),
+                "gpu_launches_per_batch_step": launchp32 / nb,
+                "note": "one persistent cooperative launch per batch step; FP32 band-Cholesky Kronecker solve"},
+            "graph_df_band_banded32_preconditioner": {
+                "value": nb / (ms_df / 1e3), "dof_updates_per_s": ndof * nb / (ms_df / 1e3),
+                "ms_per_batch_step": ms_df / nb, "pcg_iters_per_solve": itdf / max(sodf, 1.0),
+                "gpu_launches_per_batch_step": launchdf / nb,
+                "sequential_value": nb / (ms_alone_df / 1e3), "speedup_vs_sequential": ms_alone_df / ms_df,
+                "autotuned_band_configs_rank0": tuned_df,
+                "note": "one graph launch per batch step holding every patch's step (about 57 kernels each); "
+                        "double-FP32 band products, FP32 band-Cholesky Kronecker solve"},
+            "graph_fp64_band_bf16_preconditioner": {
                 "value": nb / (ms_batch / 1e3), "dof_updates_per_s": ndof * nb / (ms_batch / 1e3),
                 "pcg_iters_per_solve": iters / max(solves, 1.0), "gpu_launches_per_batch_step": launches / nb,
                 "sequential_value": nb / (ms_alone / 1e3), "speedup_vs_sequential": ms_alone / ms_batch,
                 "autotuned_band_configs_rank0": tuned,
-                "note": "FP64 assembled operators, BF16 tensor-core preconditioner"},
-            "fp64_band_banded32_preconditioner": {
+                "note": "one graph launch per batch step; FP64 band operators, BF16 tensor-core preconditioner"},
+            "graph_fp64_band_banded32_preconditioner": {
                 "value": nb / (ms_b32 / 1e3), "dof_updates_per_s": ndof * nb / (ms_b32 / 1e3),
                 "pcg_iters_per_solve": it32 / max(so32, 1.0)},
         },

@@ -516,10 +516,13 @@ int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, c
  * The per-system PCG scalars are reduced in a fixed order, so runs are reproducible;
  * they are not bitwise those of the graph path, whose reductions are grouped otherwise.
  * Forms (else IGA_EINVAL with a message, and the batch keeps the graph path): 3-D
- * patches of degree 1..4, FP64 band operators (IGA_OP_ASSEMBLED), the band-Cholesky
- * Kronecker preconditioner (IGA_PREC_BANDED, plain PCG, or IGA_PREC_BANDED32, flexible
- * PCG) on every patch, the zero initial guess, no damping or loads, the same tolerance
- * and iteration limit on every patch. Work vectors (9 k N doubles per patch at most)
+ * patches of degree 1..4, FP64 band operators (IGA_OP_ASSEMBLED), on every patch the
+ * band-Cholesky Kronecker preconditioner (IGA_PREC_BANDED, plain PCG, or
+ * IGA_PREC_BANDED32, flexible PCG) or the BF16 fast diagonalisation (IGA_PREC_BF16,
+ * flexible PCG: six mode products with matrix entries and inputs rounded to BF16 and
+ * FP32 sums -- the tensor-core form's arithmetic, computed by the persistent blocks on
+ * CUDA cores), the zero initial guess, no damping or loads, the same tolerance and
+ * iteration limit on every patch. Work vectors (9 k N doubles per patch at most)
  * are allocated on the first step for a (k, rho_inf, dt, states) and kept. stats:
  * steps, solves, iterations, largest relative residual per patch; the launches are
  * counted on patch 0 (one per step). Semantics of the step otherwise as iga_batch_step.

@@ -1,6 +1,8 @@
 // Batches of independent patches (iga_batch_*, include/iga_galpha.h): one captured
 // graph holding every patch's step, or (iga_batch_set_persistent) one persistent
 // cooperative launch per batch step over all patches (kernels_persist.cu).
+#include <cuda_bf16.h>
+
 #include <new>
 #include <string>
 #include <vector>
@@ -71,8 +73,9 @@ void free_persist(PersistState* ps) {
 }
 
 // The forms the persistent step computes: 3-D patches, FP64 band operators, the
-// band-Cholesky Kronecker preconditioner (all patches FP64 or all FP32), zero initial
-// guess, no damping or loads, common tolerance and iteration limit, degrees 1..4.
+// band-Cholesky Kronecker preconditioner (all patches FP64 or all FP32) or the BF16 fast
+// diagonalisation, zero initial guess, no damping or loads, common tolerance and
+// iteration limit, degrees 1..4.
 int persist_supported(iga_batch* b) {
   const iga_handle* h0 = b->p[0];
   for (size_t i = 0; i < b->p.size(); ++i) {
@@ -81,8 +84,9 @@ int persist_supported(iga_batch* b) {
     if (h->dim != 3) return bfail(b, IGA_EINVAL, who + "the persistent batch step needs 3-D patches");
     if (h->opt.op_form != IGA_OP_ASSEMBLED)
       return bfail(b, IGA_EINVAL, who + "the persistent batch step needs the FP64 band operators (IGA_OP_ASSEMBLED)");
-    if (h->opt.precond != IGA_PREC_BANDED && h->opt.precond != IGA_PREC_BANDED32)
-      return bfail(b, IGA_EINVAL, who + "the persistent batch step needs a band-Cholesky Kronecker preconditioner");
+    if (h->opt.precond != IGA_PREC_BANDED && h->opt.precond != IGA_PREC_BANDED32 && h->opt.precond != IGA_PREC_BF16)
+      return bfail(b, IGA_EINVAL,
+                   who + "the persistent batch step needs a band-Cholesky Kronecker or the BF16 preconditioner");
     if (h->opt.precond != h0->opt.precond || h->opt.tol != h0->opt.tol || h->opt.max_iter != h0->opt.max_iter)
       return bfail(b, IGA_EINVAL, who + "preconditioner, tolerance and iteration limit must be those of patch 0");
     if (h->opt.guess != IGA_GUESS_ZERO || h->damped || h->nforce > 0)
@@ -133,7 +137,8 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
   ps->rho = rho;
   ps->dt.assign(dt, dt + np);
   ps->states.assign(states, states + np);
-  ps->f32 = b->p[0]->opt.precond == IGA_PREC_BANDED32;
+  const bool fd = b->p[0]->opt.precond == IGA_PREC_BF16;
+  ps->f32 = fd || b->p[0]->opt.precond == IGA_PREC_BANDED32;
   const size_t esz = ps->f32 ? sizeof(float) : sizeof(double);
   std::vector<PPatch> pt(np);
   std::vector<int2> rtile, ltile[3];
@@ -167,13 +172,33 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
     P.t1 = t;
     P.t2 = t + kn * esz;
     P.sc = handle_coefs(h, k, rho, dt[i]);
+    for (int a = 0; a < 3; ++a) {
+      P.lam[a] = h->dd[a].lam32;
+      P.Ub[a][0] = P.Ub[a][1] = nullptr;
+      if (!fd) continue;
+      // U_a (column c = eigenvector c of the parametric mass matrix) and U_a^T, rounded to BF16
+      const int n = h->tab[a].n;
+      const std::vector<double>& ev = h->tab[a].evec;
+      std::vector<float> mu((size_t)n * n), mt((size_t)n * n);
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+          mu[(size_t)r * n + c] = __bfloat162float(__float2bfloat16((float)ev[(size_t)r * n + c]));
+          mt[(size_t)r * n + c] = __bfloat162float(__float2bfloat16((float)ev[(size_t)c * n + r]));
+        }
+      float *du = nullptr, *dt_ = nullptr;
+      CKB(pupload(b, ps, &du, mu));
+      CKB(pupload(b, ps, &dt_, mt));
+      P.Ub[a][0] = du;
+      P.Ub[a][1] = dt_;
+    }
     rt0[i] = (int)rtile.size();
     nrt[i] = batch_row_tiles(h->N);
     for (int q = 0; q < nrt[i]; ++q) rtile.push_back(make_int2(i, q));
+    const int last = fd ? 0 : 2;  // the axis of the preconditioner's last phase (its r.z partials)
     for (int a = 0; a < 3; ++a) {
-      if (a == 2) lt2[i] = (int)ltile[2].size();
+      if (a == last) lt2[i] = (int)ltile[a].size();
       const int nl = batch_line_tiles(h->N, h->n[a]);
-      if (a == 2) nlt2[i] = nl;
+      if (a == last) nlt2[i] = nl;
       for (int q = 0; q < nl; ++q) ltile[a].push_back(make_int2(i, q));
     }
     Yp[i] = P.Y;
@@ -186,6 +211,7 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
   B.k = k;
   B.max_iter = b->p[0]->opt.max_iter;
   B.flexible = ps->f32 ? 1 : 0;
+  B.fd = fd ? 1 : 0;
   B.tol2 = b->p[0]->opt.tol * b->p[0]->opt.tol;
   B.nrt = (int)rtile.size();
   PPatch* dpt = nullptr;
@@ -218,7 +244,8 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
   B.qp = dptr[3];
   const size_t S = (size_t)np * k;
   CKB(palloc(b, ps, &B.part, (size_t)B.nrt * k));
-  CKB(palloc(b, ps, &B.lpart, (size_t)2 * B.nlt[2] * k));
+  B.nrzt = B.nlt[fd ? 0 : 2];
+  CKB(palloc(b, ps, &B.lpart, (size_t)2 * B.nrzt * k));
   double** sc[9] = {&B.bb, &B.rr, &B.rz, &B.rznew, &B.rzold, &B.pq, &B.alpha, &B.beta, &B.last_rel};
   for (double** v : sc) CKB(palloc(b, ps, v, S));
   int** si[4] = {&B.active, &B.iters, &B.status, &B.max_iters};
@@ -227,13 +254,15 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
   CKB(palloc(b, ps, &B.flags, 2));
   CKB(palloc(b, ps, &B.bar, 2));
   CKB(palloc(b, ps, &B.err, 1));
-  B.bar_limit = b->p[0]->bar_limit;
+  // polls of a barrier wait before it gives up (< 0 on the handle: the default, about 0.3 s or
+  // more, far beyond the longest phase)
+  B.bar_limit = b->p[0]->bar_limit < 0 ? (1LL << 22) : b->p[0]->bar_limit;
   if (cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), b->s0) != cudaSuccess ||
       cudaMemsetAsync(B.err, 0, sizeof(int), b->s0) != cudaSuccess ||
       cudaMemsetAsync(B.status, 0, sizeof(int) * S, b->s0) != cudaSuccess ||
       cudaMemsetAsync(B.beta, 0, sizeof(double) * S, b->s0) != cudaSuccess)
     return bfail(b, IGA_ECUDA, "persistent batch: cudaMemsetAsync");
-  ps->smem = batch_smem_bytes(nmax, pmax, ps->f32);
+  ps->smem = batch_smem_bytes(nmax, pmax, ps->f32, fd);
   // the graph holding the one cooperative launch of a batch step
   cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));

@@ -341,6 +341,9 @@ struct PPatch {
   const int* o12;               // [H] packed offsets along directions 1, 2
   const double* scale;          // [N] D^-1/2 Dhat^1/2
   const void *L[3], *dinv[3];   // band Cholesky factors per axis ([n][p+1], [n]), FP32 or FP64
+  const float* Ub[3][2];        // fast diagonalisation: U_a (0) and U_a^T (1) rounded to BF16, as FP32,
+                                // row-major [n][n] (Mat(i, j) at i n + j, i the output)
+  const float* lam[3];          // 1 / Lambda_a, FP32
   double* X;                    // state [3k][N] (the caller's)
   double *Y, *T, *r, *x, *z, *p, *q;  // [k][N] work vectors
   void *t1, *t2;                // [k][N] intermediates of the Kronecker solve
@@ -348,18 +351,21 @@ struct PPatch {
 };
 struct PBatch {
   int np, k, max_iter, flexible;
+  int fd;                             // 1: BF16 fast diagonalisation, 0: band Cholesky
   double tol2;
   const PPatch* pt;                   // [np]
   const int2* rtile;                  // [nrt] (patch, row tile within the patch)
   const int2* ltile[3];               // [nlt[a]] (patch, line tile within the patch)
   int nrt, nlt[3];
-  const int *rt0, *nrt_p, *lt2, *nlt2_p;  // [np] first tile and tile count per patch (rows; axis-2 lines)
+  const int *rt0, *nrt_p;             // [np] first row tile and row tiles per patch
+  const int *lt2, *nlt2_p;            // [np] the same for the line tiles of the preconditioner's last
+  int nrzt;                           // phase (axis 2: band Cholesky, axis 0: fast diagonalisation)
   double* const* Yp;                  // [np] the patches' Y, r, p, q (band-product operands)
   double* const* rp;
   double* const* pp;
   double* const* qp;
   double* part;                       // [nrt][k] row-tile partials
-  double* lpart;                      // [2][nlt[2]][k] axis-2 partials of r.z (new, previous z)
+  double* lpart;                      // [2][nrzt][k] last-phase partials of r.z (new, previous z)
   double *bb, *rr, *rz, *rznew, *rzold, *pq, *alpha, *beta, *last_rel;  // [np k]
   int *active, *iters, *status, *max_iters;                              // [np k]
   long long* tot_iters;                                                  // [np k]
@@ -370,7 +376,7 @@ struct PBatch {
 };
 int batch_row_tiles(long long N);
 int batch_line_tiles(long long N, int n);
-size_t batch_smem_bytes(int nmax, int pmax, bool f32);
+size_t batch_smem_bytes(int nmax, int pmax, bool f32, bool fd);
 cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid);
 
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,

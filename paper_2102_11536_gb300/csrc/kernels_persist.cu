@@ -12,9 +12,15 @@
 // Arithmetic per row and line as in the single-patch kernels: the FP64 band product
 // (diagonal, then per stored slot the upper and the lower term), the band-Cholesky
 // substitutions with the factor rows scaled by 1 / L_kk (FP32 or FP64), the predictor
-// and update of k_predict / k_update. PCG: Hestenes-Stiefel with the FP64 Kronecker
-// solve, the flexible (Polak-Ribiere) beta with the FP32 one; stop at
-// ||r|| <= tol ||b||; x0 = 0.
+// and update of k_predict / k_update. Or the preconditioner by fast diagonalisation
+// with 16-bit operands: six mode products whose matrix entries and inputs are rounded
+// to BF16 and whose products (exact in FP32) are summed in FP32 -- the arithmetic of
+// the tensor-core form, here on the CUDA cores of the persistent blocks (the products
+// of one line tile are 32 n^2 multiply-adds, n <= 98 for these patches). PCG:
+// Hestenes-Stiefel with the FP64 Kronecker solve, the flexible (Polak-Ribiere) beta
+// with the FP32 and BF16 ones; stop at ||r|| <= tol ||b||; x0 = 0.
+#include <cuda_bf16.h>
+
 #include "iga_internal.h"
 
 namespace iga {
@@ -67,7 +73,7 @@ __device__ void psum_systems(const PBatch& B, const double* part, const int* t0,
   for (int s = w; s < S; s += kPThreads / 32) {
     const int pi = s / B.k, j = s - pi * B.k;
     double a = 0.0;
-    for (int t = lane; t < nt[pi]; t += 32) a += *(volatile const double*)&part[(long long)(t0[pi] + t) * B.k + j];
+    for (int t = lane; t < nt[pi]; t += 32) a += __ldcg(&part[(long long)(t0[pi] + t) * B.k + j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if (lane == 0) out[s] = a;
@@ -137,6 +143,12 @@ __device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, do
     const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
     const bool row = i < N;
     const int* act = B.active + tl.x * K;
+    if (!stiff) {  // a patch whose systems have all converged: nothing to do (uniform over the block)
+      bool any = false;
+#pragma unroll
+      for (int v = 0; v < K; ++v) any = any || act[v];
+      if (!any) continue;
+    }
     const double* A = stiff ? P.K : P.M;
     bool on[K];
     double acc[K], xi[K];
@@ -196,6 +208,10 @@ template <int K>
 __device__ void ph_dir(const PBatch& B, bool first) {
   for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
     const int2 tl = B.rtile[it];
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < K; ++v) any = any || B.active[tl.x * K + v];
+    if (!any) continue;
     const PPatch& P = B.pt[tl.x];
     const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
     if (i >= N) continue;
@@ -214,6 +230,10 @@ template <int K>
 __device__ void ph_xr(const PBatch& B) {
   for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
     const int2 tl = B.rtile[it];
+    bool any = false;  // a converged patch: its partials are not read (uniform over the block)
+#pragma unroll
+    for (int v = 0; v < K; ++v) any = any || B.active[tl.x * K + v];
+    if (!any) continue;
     const PPatch& P = B.pt[tl.x];
     const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
     const bool row = i < N;
@@ -378,7 +398,87 @@ __device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
         const double s1 = pblock_sum(snew), s2 = pblock_sum(sold);
         if (threadIdx.x == 0) {
           B.lpart[(long long)it * K + v] = s1;
-          B.lpart[(long long)(B.nlt[2] + it) * K + v] = s2;
+          B.lpart[(long long)(B.nrzt + it) * K + v] = s2;
+        }
+      }
+    }
+  }
+}
+
+// One mode product of the fast-diagonalisation preconditioner for every active system
+// of a line tile of axis a: out_line = Mat bf16(in_line), Mat = U_a^T (tr = 1) or U_a.
+// stage 0: in = r D^-1/2 Dhat^1/2 (FP64 scaled, then FP32) -> t1 (axis 0, U^T)
+// stage 1: t1 -> t2 (axis 1, U^T); stage 2: t2 -> t1 (axis 2, U^T) times 1 / Lambda
+// stage 3: t1 -> t2 (axis 2, U); stage 4: t2 -> t1 (axis 1, U)
+// stage 5: t1 -> z (axis 0, U) times D^-1/2 Dhat^1/2, with the partials of r.z (new, old).
+// Thread (warp w, lane l): line l of the tile, outputs i = w, w + 8, ...; the warp reads
+// one matrix row (a broadcast) and 32 lines' staged entries (consecutive banks).
+template <int K>
+__device__ void ph_fd(const PBatch& B, int stage, unsigned char* smem) {
+  const int a = stage < 3 ? stage : 5 - stage;
+  const int tr = stage < 3 ? 1 : 0;
+  for (int it = blockIdx.x; it < B.nlt[a]; it += gridDim.x) {
+    const int2 tl = B.ltile[a][it];
+    const PPatch& Pp = B.pt[tl.x];
+    const int n = Pp.n[a];
+    const long long N = Pp.N;
+    const long long A = a == 0 ? 1 : (a == 1 ? (long long)Pp.n[0] : (long long)Pp.n[0] * Pp.n[1]);
+    const long long Rl = N / n;
+    const long long l0 = (long long)tl.y * kPLines;
+    const int nl = (int)min((long long)kPLines, Rl - l0);
+    float* sb = reinterpret_cast<float*>(smem);
+    const float* Mat = Pp.Ub[a][tr];
+    // stages 1, 3, 5 read t1 and 2, 4 read t2; stages 1, 3 write t2 and 0, 2, 4 write t1
+    const float* tin = (stage == 2 || stage == 4) ? static_cast<const float*>(Pp.t2) : static_cast<const float*>(Pp.t1);
+    float* tout = (stage == 1 || stage == 3) ? static_cast<float*>(Pp.t2) : static_cast<float*>(Pp.t1);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int v = 0; v < K; ++v) {
+      const int s = tl.x * K + v;
+      const bool on = B.active[s] != 0;  // uniform over the block
+      double snew = 0.0, sold = 0.0;
+      if (on) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
+          int k, l;
+          if (a == 0) { l = e / n; k = e - l * n; }
+          else { k = e / nl; l = e - k * nl; }
+          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
+          const long long g = xx + A * (k + (long long)n * y);
+          const float u = stage == 0 ? (float)(Pp.r[v * N + g] * Pp.scale[g]) : tin[v * N + g];
+          sb[k * kPLS + l] = __bfloat162float(__float2bfloat16(u));
+        }
+        __syncthreads();
+        if (lane < nl) {
+          const long long rr = l0 + lane, y = rr / A, xx = rr - y * A;
+          // the line's other two indices, for 1 / Lambda (stage 2: along axis 2, the line is (i0, i1))
+          float lam01 = 1.0f;
+          if (stage == 2) {
+            const int i0 = (int)(xx % Pp.n[0]), i1 = (int)(xx / Pp.n[0]);
+            lam01 = Pp.lam[0][i0] * Pp.lam[1][i1];
+          }
+          for (int i = w; i < n; i += kPThreads / 32) {
+            const float* Mi = Mat + (size_t)i * n;
+            float acc = 0.0f;
+            for (int j = 0; j < n; ++j) acc = fmaf(Mi[j], sb[j * kPLS + lane], acc);
+            const long long g = xx + A * (i + (long long)n * y);
+            if (stage == 2) acc *= lam01 * Pp.lam[2][i];
+            if (stage == 5) {
+              const double zn = (double)acc * Pp.scale[g];
+              const double rg = Pp.r[v * N + g];
+              sold = fma(rg, Pp.z[v * N + g], sold);
+              snew = fma(rg, zn, snew);
+              Pp.z[v * N + g] = zn;
+            } else {
+              tout[v * N + g] = acc;
+            }
+          }
+        }
+      }
+      if (stage == 5) {
+        const double s1 = pblock_sum(snew), s2 = pblock_sum(sold);
+        if (threadIdx.x == 0) {
+          B.lpart[(long long)it * K + v] = s1;
+          B.lpart[(long long)(B.nrzt + it) * K + v] = s2;
         }
       }
     }
@@ -400,7 +500,7 @@ __device__ void lead_start(const PBatch& B) {
 // after the preconditioner: r.z, and beta for the next direction (plain or flexible)
 __device__ void lead_rz(const PBatch& B, bool first) {
   psum_systems(B, B.lpart, B.lt2, B.nlt2_p, B.rznew);
-  psum_systems(B, B.lpart + (long long)B.nlt[2] * B.k, B.lt2, B.nlt2_p, B.rzold);
+  psum_systems(B, B.lpart + (long long)B.nrzt * B.k, B.lt2, B.nlt2_p, B.rzold);
   __syncthreads();
   for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
     if (!B.active[s]) continue;
@@ -467,16 +567,23 @@ __device__ void lead_stats(const PBatch& B) {
 // the preconditioner z = P^-1 r (three axis phases) and the r.z scalars
 template <int K, typename T>
 __device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first) {
-  for (int a = 0; a < 3; ++a) {
-    ph_axis<K, T>(B, a, smem);
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+  if (B.fd) {
+    for (int st = 0; st < 6; ++st) {
+      ph_fd<K>(B, st, smem);
+      if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+    }
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      ph_axis<K, T>(B, a, smem);
+      if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+    }
   }
   if (blockIdx.x == 0) lead_rz(B, first);
   return pgrid_sync(B.bar, B.bar_limit, B.err);
 }
 
 template <int K, typename T>
-__global__ void __launch_bounds__(kPThreads, 1) k_batch_step(const PBatch B) {
+__global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
   extern __shared__ __align__(16) unsigned char psmem[];
   ph_predict<K>(B);
   if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
@@ -534,7 +641,8 @@ cudaError_t batch_go(cudaStream_t s, const PBatch& B, size_t smem, int sms, int*
 
 int batch_row_tiles(long long N) { return (int)((N + kPRows - 1) / kPRows); }
 int batch_line_tiles(long long N, int n) { return (int)((N / n + kPLines - 1) / kPLines); }
-size_t batch_smem_bytes(int nmax, int pmax, bool f32) {
+size_t batch_smem_bytes(int nmax, int pmax, bool f32, bool fd) {
+  if (fd) return (size_t)nmax * kPLS * sizeof(float) + 64;
   return (size_t)nmax * (kPLS + 2 * (pmax + 1)) * (f32 ? sizeof(float) : sizeof(double)) + 64;
 }
 

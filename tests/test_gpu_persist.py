@@ -1,6 +1,6 @@
 """The persistent batch step (iga_batch_set_persistent): one cooperative launch per
 step advances every patch of a batch of independent, uneven patches (FP64 band
-operators, band-Cholesky Kronecker preconditioner).
+operators; band-Cholesky Kronecker or BF16 fast-diagonalisation preconditioner).
 
   * three small patches of degrees 2, 3, 4 at PCG tol 1e-13: every patch after 6 steps
     within 1e-10 (relative L2 of U and V) of the oracle's Stepper on the same inputs,
@@ -9,6 +9,8 @@ operators, band-Cholesky Kronecker preconditioner).
     stepped alone with it;
   * the 48-patch batch (16^3..96^3 elements, p in {2, 3, 4}) for 3 steps: every patch
     within 1e-8 of that patch stepped alone, one launch per batch step;
+  * the BF16 fast diagonalisation (flexible PCG) at tol 1e-10: within 1e-8 of the oracle
+    and of the patches stepped alone with the tensor-core BF16 preconditioner;
   * a second persistent run equals the first bit for bit (fixed-order reductions);
   * refusals: a form the persistent step does not compute gives IGA_EINVAL and the batch
     keeps its graph path.
@@ -163,13 +165,52 @@ def test_persistent_batch_of_48_patches():
         g.close()
 
 
+def test_persistent_batch_bf16_fast_diagonalisation():
+    ws = _small_patches()
+    k, rho, nsteps = 2, 0.5, 5
+    pats, states, inits = _setup(ws, "bf16", 1e-10)
+    dts, refs = [], []
+    for w in ws:
+        ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+        lam = oracle.lambda_max_dense(ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K))
+        dt = 0.5 * math.sqrt(oracle.theta_crit(rho) / lam)
+        st = oracle.Stepper(ops, k, rho, tol=1e-13)
+        U0, V0 = w.initial()
+        X = st.init(U0, V0)
+        for _ in range(nsteps):
+            X = st.step(X, dt)
+        dts.append(dt)
+        refs.append(X)
+    for g, st, (u0, v0) in zip(pats, states, inits):
+        g.state_init(k, u0, v0, st)
+    b = iga.Batch(pats)
+    b.set_persistent(True)
+    stats = b.step(states, k, rho, dts, nsteps)
+    assert all(s.max_relres <= 1e-10 for s in stats)
+    batched = [s.cpu().numpy().reshape(3 * k, -1) for s in states]
+    for i, (g, st, (u0, v0), dt) in enumerate(zip(pats, states, inits, dts)):
+        g.state_init(k, u0, v0, st)
+        sa = g.step(st, k, rho, dt, nsteps)
+        alone = st.cpu().numpy().reshape(3 * k, -1)
+        print("persistent BF16 batch, patch %d: %.2f iterations per solve (tensor-core form alone: %.2f)" % (
+            i, stats[i].iters / stats[i].solves, sa.iters / sa.solves))
+        for row, var in ((0, "U"), (1, "V")):
+            e_o = _rel(batched[i][row], refs[i][row])
+            e_a = _rel(batched[i][row], alone[row])
+            print("  %s: vs oracle %.3e, vs alone %.3e" % (var, e_o, e_a))
+            assert e_o <= 1e-8 and e_a <= 1e-8, (i, var, e_o, e_a)
+    b.close()
+    for g in pats:
+        g.close()
+
+
 def test_persistent_batch_refuses_other_forms():
     ws = _small_patches()
-    pats, states, inits = _setup(ws, "bf16", 1e-10)
+    pats, states, inits = _setup(ws, "fp32", 1e-10)
     b = iga.Batch(pats)
     with pytest.raises(iga.IgaError) as e:
         b.set_persistent(True)
-    assert e.value.status == iga.EINVAL and "band-Cholesky" in str(e.value)
+    assert e.value.status == iga.EINVAL and "preconditioner" in str(e.value)
     b.close()
     for g in pats:
         g.close()

@@ -131,7 +131,16 @@ class Workload:
 
 
 def config(name: str) -> Workload:
-    """The five synthetic configurations of the benchmark suite, by name."""
+    """The five synthetic configurations of the benchmark suite, by name; also
+    'cube:<nel>:<p>[:<k>]', the deformed unit cube (amplitude 0.1) with nel^3 elements of
+    degree p, k = 3 unless given, 16 seeded random modes (smaller cases of the same kind,
+    for profiling and sweeps)."""
+    if name.startswith("cube:"):
+        f = [int(v) for v in name.split(":")[1:]]
+        if len(f) not in (2, 3) or f[0] < 1 or f[1] < 1:
+            raise KeyError(name)
+        k = f[2] if len(f) == 3 else 3
+        return Workload(name, 3, (f[0],) * 3, (f[1],) * 3, 0.1, k, 0.5, 100, init="random")
     if name == "square32_p2":  # 2-D, identity, p=2, 32^2, k=1
         return Workload(name, 2, (32, 32), (2, 2), 0.0, 1, 0.5, 100)
     if name == "cube64_p3":  # 3-D deformed, p=3, 64^3, k=2
@@ -140,6 +149,8 @@ def config(name: str) -> Workload:
         return Workload(name, 3, (128, 128, 128), (4, 4, 4), 0.1, 3, 0.5, 200, init="random")
     if name == "cube96_p3":  # 3-D deformed, p=3, 96^3, k=2, random modes
         return Workload(name, 3, (96, 96, 96), (3, 3, 3), 0.1, 2, 0.5, 1000, init="random")
+    if name == "cube64_p4":  # the 128^3 p=4 discretisation on 64^3 elements (a few GB: profiling captures)
+        return Workload(name, 3, (64, 64, 64), (4, 4, 4), 0.1, 3, 0.5, 200, init="random")
     raise KeyError(name)
 
 
