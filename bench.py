@@ -630,7 +630,7 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
-    def timed(step_fn, nsteps):
+    def timed(step_fn, nsteps, after=None):
         ms = 0.0
         if pg:
             pg.barrier()
@@ -641,6 +641,8 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
+            if after:
+                after()
         return ms
 
     for _ in range(args.warmup):
@@ -692,12 +694,27 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
         for _ in range(args.warmup):
             b.step(states, k, rho, dts, 1)
         sp = [iga.Stats() for _ in pats]
-        ms = timed(lambda: b.step(states, k, rho, dts, 1, sp), nb)
-        b.set_persistent(False)
-        return ms, sp
+        ph = dict.fromkeys(iga.Batch.PHASES, 0.0)
 
-    ms_p, statsp = persistent("bf16")
-    ms_p32, statsp32 = persistent("banded32")
+        def add_phases():
+            for key, v in b.phase_times().items():
+                ph[key] += v / nb
+
+        ms = timed(lambda: b.step(states, k, rho, dts, 1, sp), nb, add_phases)
+        b.set_persistent(False)
+        return ms, sp, ph
+
+    def fp64_band_floor_ms(sp):
+        """Per batch step: the FP64 multiply-adds of the band products (every stored coupling of
+        a row in both halves, per vector: k for K, one per PCG iteration for M) at the measured
+        FP64 FMA rate."""
+        fmas = sum(g.N * (2 * w.p[0] + 1) ** 3 * (k * nb + s.iters) for g, w, s in zip(pats, ws, sp)) / nb
+        return fmas / (fp64_tf * 1e12 / 2) * 1e3
+
+    fp64_tf, _ = iga.fp64_fma_probe(dev.index or 0)
+    ms_p, statsp, php = persistent("bf16")
+    ms_p32, statsp32, php32 = persistent("banded32")
+    floor_p, floor_p32 = fp64_band_floor_ms(statsp), fp64_band_floor_ms(statsp32)
     (ms_batch, ms_alone, ms_b32, ms_df, ms_alone_df, ms_p, ms_p32), (
         ndof, iters, solves, launches, it32, so32, itdf, sodf, launchdf, itp, sop, launchp, itp32, sop32,
         launchp32) = combine_over_ranks(
@@ -726,11 +743,18 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
         "graph_launches_per_batch_step_per_rank": 1,
         "arithmetic": "f64 state, residuals, dots and band K, M; bf16 x f32-accumulate fast-diagonalisation mode "
                       "products on CUDA cores inside the persistent kernel",
+        "phase_ms_per_batch_step_rank0": php,
+        "fp64_band_floor_ms_per_batch_step_rank0": floor_p,
+        "fp64_band_floor_basis": "FP64 multiply-adds of the band products (N (2p+1)^3 per vector product; k K "
+                                 "products and one M product per PCG iteration) at the measured FP64 FMA rate "
+                                 "(%.3f TFLOP/s)" % fp64_tf,
         "variants": {
             "persistent_fp64_band_banded32_preconditioner": {
                 "value": nb / (ms_p32 / 1e3), "dof_updates_per_s": ndof * nb / (ms_p32 / 1e3),
                 "ms_per_batch_step": ms_p32 / nb, "pcg_iters_per_solve": itp32 / max(sop32, 1.0),
                 "gpu_launches_per_batch_step": launchp32 / nb,
+                "phase_ms_per_batch_step_rank0": php32,
+                "fp64_band_floor_ms_per_batch_step_rank0": floor_p32,
                 "note": "one persistent cooperative launch per batch step; FP32 band-Cholesky Kronecker solve"},
             "graph_df_band_banded32_preconditioner": {
                 "value": nb / (ms_df / 1e3), "dof_updates_per_s": ndof * nb / (ms_df / 1e3),

@@ -531,6 +531,21 @@ int iga_batch_step(iga_batch* b, double* const* states, int k, double rho_inf, c
 int iga_batch_set_persistent(iga_batch* b, int on);
 
 /*
+ * iga_batch_phase_times -- where the last persistent iga_batch_step spent its time: ms
+ * (host array of n) receives, summed over that call's steps, the milliseconds of each
+ * kind of phase, measured on the device by block 0 of the persistent kernel from one
+ * passed grid barrier to the next (a phase's time includes its barrier): [0] Taylor
+ * predictor, [1] K product with the partials of b.b, [2] PCG scalars (the per-system
+ * sums and alpha, beta, convergence, done by one block), [3] preconditioner (axis or
+ * mode-product phases), [4] direction update, [5] M product with the partials of p.q,
+ * [6] x and r update with the partials of r.r, [7] stage update (block 0's own end).
+ * Entries past [7] are set to 0. IGA_EINVAL if the batch is not persistent or no
+ * persistent step has completed since it was set up (or the last one timed out).
+ * Measurement aid; the paper has no counterpart.
+ */
+int iga_batch_phase_times(iga_batch* b, double* ms, int n);
+
+/*
  * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in
  * the paper; measurement aid): 8 independent FMA chains per thread, 4 blocks of 256
  * threads per SM, 2^14 iterations, averaged over 5 timed launches after 2

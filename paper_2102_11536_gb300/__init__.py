@@ -111,6 +111,7 @@ def lib():
         "iga_batch_step": (ctypes.c_int, [H, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
                                           ctypes.POINTER(Stats)]),
         "iga_batch_set_persistent": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_batch_phase_times": (ctypes.c_int, [H, dp, ctypes.c_int]),
         "iga_mp_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ip, ip, ctypes.POINTER(ctypes.c_longlong), ip,
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]),
@@ -145,7 +146,7 @@ def exported_symbols():
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
             "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
-            "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent"]
+            "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent", "iga_batch_phase_times"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -650,6 +651,18 @@ class Batch:
         rc = lib().iga_batch_set_persistent(self.b, int(bool(on)))
         if rc != OK:
             raise IgaError(rc, "iga_batch_set_persistent: " + lib().iga_batch_last_error(self.b).decode())
+
+    PHASES = ("predictor", "K product", "PCG scalars", "preconditioner", "direction update", "M product",
+              "x, r update", "stage update")
+
+    def phase_times(self):
+        """Milliseconds per phase kind of the last persistent step call (iga_batch_phase_times),
+        as a dict keyed by Batch.PHASES."""
+        ms = (ctypes.c_double * len(self.PHASES))()
+        rc = lib().iga_batch_phase_times(self.b, ms, len(self.PHASES))
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_phase_times: " + lib().iga_batch_last_error(self.b).decode())
+        return dict(zip(self.PHASES, list(ms)))
 
     def close(self):
         if getattr(self, "b", None):

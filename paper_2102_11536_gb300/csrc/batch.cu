@@ -25,6 +25,8 @@ struct PersistState {
   std::vector<void*> allocs;  // every device allocation, freed together
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  double phase_ms[kPersistPhases] = {};  // of the last iga_batch_step, summed over its steps
+  bool have_phases = false;
 };
 
 struct iga_batch {
@@ -254,6 +256,7 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
   CKB(palloc(b, ps, &B.flags, 2));
   CKB(palloc(b, ps, &B.bar, 2));
   CKB(palloc(b, ps, &B.err, 1));
+  CKB(palloc(b, ps, &B.ptime, kPersistPhases));
   // polls of a barrier wait before it gives up (< 0 on the handle: the default, about 0.3 s or
   // more, far beyond the longest phase)
   B.bar_limit = b->p[0]->bar_limit < 0 ? (1LL << 22) : b->p[0]->bar_limit;
@@ -262,7 +265,7 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
       cudaMemsetAsync(B.status, 0, sizeof(int) * S, b->s0) != cudaSuccess ||
       cudaMemsetAsync(B.beta, 0, sizeof(double) * S, b->s0) != cudaSuccess)
     return bfail(b, IGA_ECUDA, "persistent batch: cudaMemsetAsync");
-  ps->smem = batch_smem_bytes(nmax, pmax, ps->f32, fd);
+  ps->smem = batch_smem_bytes(nmax, pmax, k, ps->f32, fd);
   // the graph holding the one cooperative launch of a batch step
   cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
@@ -308,6 +311,7 @@ int persist_steps(iga_batch* b, double* const* states, int k, double rho, const 
   if (e == cudaSuccess) e = cudaMemsetAsync(B.tot_iters, 0, sizeof(long long) * S, b->s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.max_iters, 0, sizeof(int) * S, b->s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.flags, 0, sizeof(int) * 2, b->s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.ptime, 0, sizeof(unsigned long long) * kPersistPhases, b->s0);
   for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = cudaGraphLaunch(ps->gexec, b->s0);
   std::vector<long long> tot(S);
   std::vector<int> mx(S), st(S);
@@ -319,10 +323,15 @@ int persist_steps(iga_batch* b, double* const* states, int k, double rho, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), B.status, sizeof(int) * S, cudaMemcpyDeviceToHost, b->s0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, B.err, sizeof(int), cudaMemcpyDeviceToHost, b->s0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(flags, B.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, b->s0);
+  unsigned long long pns[kPersistPhases] = {};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pns, B.ptime, sizeof(unsigned long long) * kPersistPhases, cudaMemcpyDeviceToHost, b->s0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->s0);
   if (e == cudaSuccess) e = cudaEventRecord(b->done, b->s0);
   for (int i = 0; i < np && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->p[i]->stream, b->done, 0);
   if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("persistent batch step: ") + cudaGetErrorString(e));
+  for (int c = 0; c < kPersistPhases; ++c) ps->phase_ms[c] = 1e-6 * (double)pns[c];
+  ps->have_phases = !err;
   if (err) {  // a barrier wait ran out: the step's results are not to be used; start the words afresh
     cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), b->s0);
     cudaMemsetAsync(B.err, 0, sizeof(int), b->s0);
@@ -472,6 +481,16 @@ int iga_batch_set_persistent(iga_batch* b, int on) {
     free_persist(b->ps);
     b->ps = nullptr;
   }
+  return IGA_OK;
+}
+
+int iga_batch_phase_times(iga_batch* b, double* ms, int n) {
+  if (!b) return IGA_EINVAL;
+  b->err.clear();
+  if (!ms || n < 1) return bfail(b, IGA_EINVAL, "bad arguments");
+  if (!b->persistent || !b->ps || !b->ps->have_phases)
+    return bfail(b, IGA_EINVAL, "no persistent batch step has completed since the persistent step was set up");
+  for (int c = 0; c < n; ++c) ms[c] = c < kPersistPhases ? b->ps->phase_ms[c] : 0.0;
   return IGA_OK;
 }
 

@@ -373,10 +373,13 @@ struct PBatch {
   unsigned int* bar;                  // grid barrier (count, generation)
   long long bar_limit;
   int* err;                           // set when a barrier wait runs out
+  unsigned long long* ptime;          // [kPersistPhases] ns per phase kind, added by block 0 (nullable)
 };
+constexpr int kPersistPhases = 8;     // predictor, K product, PCG scalars, preconditioner, direction,
+                                      // M product, x and r update, stage update
 int batch_row_tiles(long long N);
 int batch_line_tiles(long long N, int n);
-size_t batch_smem_bytes(int nmax, int pmax, bool f32, bool fd);
+size_t batch_smem_bytes(int nmax, int pmax, int k, bool f32, bool fd);
 cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid);
 
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,

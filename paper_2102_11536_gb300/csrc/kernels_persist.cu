@@ -131,71 +131,92 @@ __device__ void ph_predict(const PBatch& B) {
 }
 
 // y[j] = A x[j] for the patch's active systems (mask act), one row per thread; with
-// dot, the per-tile partials of x[j].y[j] (dot = 1) or y[j].y[j] (dot = 2) into part
+// dot, the per-tile partials of x[j].y[j] (dot = 1) or y[j].y[j] (dot = 2) into part.
+// Two slots per pass: both slots' coefficients and x values are loaded before their
+// multiply-adds (twice the loads in flight; the phase is bound by the FP64 units once
+// enough loads are in flight); the terms are added in slot order, the upper term before
+// the lower one, as in the single-patch band product.
 template <int K>
 __device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, double* const* ys, int dot,
                         double* part) {
   for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
     const int2 tl = B.rtile[it];
+    int on = (1 << K) - 1;  // the systems computed (uniform over the block)
+    if (!stiff) {
+      on = 0;
+#pragma unroll
+      for (int v = 0; v < K; ++v)
+        if (B.active[tl.x * K + v]) on |= 1 << v;
+      if (!on) continue;  // a patch whose systems have all converged
+    }
     const PPatch& P = B.pt[tl.x];
-    const double* x = xs[tl.x];
+    const double* __restrict__ x = xs[tl.x];
     double* y = ys[tl.x];
     const long long N = P.N, i = (long long)tl.y * kPRows + threadIdx.x;
+    const int H = P.H, n1 = P.n[1], n2 = P.n[2];
     const bool row = i < N;
-    const int* act = B.active + tl.x * K;
-    if (!stiff) {  // a patch whose systems have all converged: nothing to do (uniform over the block)
-      bool any = false;
-#pragma unroll
-      for (int v = 0; v < K; ++v) any = any || act[v];
-      if (!any) continue;
-    }
-    const double* A = stiff ? P.K : P.M;
-    bool on[K];
-    double acc[K], xi[K];
+    const double* __restrict__ A = stiff ? P.K : P.M;
+    const long long* __restrict__ off = P.off;
+    const int* __restrict__ o12 = P.o12;
+    double acc[K];
     const double a0 = row ? A[i] : 0.0;
 #pragma unroll
-    for (int v = 0; v < K; ++v) {
-      on[v] = row && (stiff || act[v]);
-      xi[v] = on[v] ? x[v * N + i] : 0.0;
-      acc[v] = a0 * xi[v];
-    }
+    for (int v = 0; v < K; ++v) acc[v] = row && (on >> v & 1) ? a0 * x[v * N + i] : 0.0;
     int i1 = 0, i2 = 0;
     if (row) {
       const long long t = i / P.n[0];
-      i1 = (int)(t % P.n[1]);
-      i2 = (int)(t / P.n[1]);
+      i1 = (int)(t % n1);
+      i2 = (int)(t / n1);
     }
-    for (int h = 1; h < P.H; ++h) {
-      const long long L = P.off[h];
-      const long long jp = i + L, jm = i - L;
-      const int pk = P.o12[h];
-      const int o1 = (pk & 255) - 64, o2 = ((pk >> 8) & 255) - 64;
-      const bool up = row && jp >= 0 && jp < N && (unsigned)(i1 + o1) < (unsigned)P.n[1] &&
-                      (unsigned)(i2 + o2) < (unsigned)P.n[2];
-      const bool dn = row && jm >= 0 && jm < N && (unsigned)(i1 - o1) < (unsigned)P.n[1] &&
-                      (unsigned)(i2 - o2) < (unsigned)P.n[2];
-      if (!__any_sync(0xffffffffu, up || dn)) continue;
-      const double* Ah = A + (long long)h * N;
-      if (up) {
-        const double a = Ah[i];
+    for (int h = 1; h < H; h += 2) {
+      bool up[2], dn[2];
+      double au[2], ad[2], xu[2][K], xd[2][K];
 #pragma unroll
-        for (int v = 0; v < K; ++v)
-          if (on[v]) acc[v] = fma(a, x[v * N + jp], acc[v]);
+      for (int u = 0; u < 2; ++u) {
+        const int hh = h + u;
+        up[u] = dn[u] = false;
+        long long jp = 0, jm = 0;
+        if (hh < H) {
+          const long long L = off[hh];
+          jp = i + L;
+          jm = i - L;
+          const int pk = o12[hh];
+          const int o1 = (pk & 255) - 64, o2 = ((pk >> 8) & 255) - 64;
+          up[u] = row && jp < N && (unsigned)(i1 + o1) < (unsigned)n1 && (unsigned)(i2 + o2) < (unsigned)n2;
+          dn[u] = row && jm >= 0 && (unsigned)(i1 - o1) < (unsigned)n1 && (unsigned)(i2 - o2) < (unsigned)n2;
+        }
+        const double* Ah = A + (long long)hh * N;
+        au[u] = up[u] ? Ah[i] : 0.0;
+        ad[u] = dn[u] ? Ah[jm] : 0.0;
+#pragma unroll
+        for (int v = 0; v < K; ++v) {
+          xu[u][v] = up[u] && (on >> v & 1) ? x[v * N + jp] : 0.0;
+          xd[u][v] = dn[u] && (on >> v & 1) ? x[v * N + jm] : 0.0;
+        }
       }
-      if (dn) {
-        const double a = Ah[jm];
+      if (!__any_sync(0xffffffffu, up[0] || dn[0] || up[1] || dn[1])) continue;
 #pragma unroll
-        for (int v = 0; v < K; ++v)
-          if (on[v]) acc[v] = fma(a, x[v * N + jm], acc[v]);
+      for (int u = 0; u < 2; ++u) {
+        if (up[u]) {
+#pragma unroll
+          for (int v = 0; v < K; ++v)
+            if (on >> v & 1) acc[v] = fma(au[u], xu[u][v], acc[v]);
+        }
+        if (dn[u]) {
+#pragma unroll
+          for (int v = 0; v < K; ++v)
+            if (on >> v & 1) acc[v] = fma(ad[u], xd[u][v], acc[v]);
+        }
       }
     }
 #pragma unroll
     for (int v = 0; v < K; ++v)
-      if (on[v]) y[v * N + i] = acc[v];
+      if (row && (on >> v & 1)) y[v * N + i] = acc[v];
     if (dot) {
 #pragma unroll
       for (int v = 0; v < K; ++v) {
-        const double t = on[v] ? (dot == 1 ? xi[v] : acc[v]) * acc[v] : 0.0;
+        const bool o = row && (on >> v & 1);
+        const double t = o ? (dot == 1 ? x[v * N + i] : acc[v]) * acc[v] : 0.0;
         const double s = pblock_sum(t);
         if (threadIdx.x == 0) part[(long long)it * K + v] = s;
       }
@@ -286,26 +307,72 @@ __device__ void ph_update(const PBatch& B) {
 }
 
 // ---------------------------------------------------------------- Kronecker solve
-// One line tile of axis a for every active system of the patch: lines are staged in
-// shared memory (entry k of line l at k kPLS + l), kPLines threads run the forward and
-// backward substitutions (factor rows scaled by 1 / L_kk, recurrence window in
-// registers), and the lines are written back. Axis 0 reads r scaled by D^-1/2 Dhat^1/2
-// into t1; axis 1 t1 -> t2; axis 2 t2 -> z scaled again, with the partials of r.z (new)
-// and r.z (the previous z) of each system.
+// A line tile of axis a: lines l0 .. l0 + nl - 1 of the patch (line l0 + l = xx + A y, its
+// entry k the element xx + A (k + n y)), staged in shared memory for every active system
+// of the patch at once (entry k of line l of system v at (v n + k) kPLS + l).
+struct LineTile {
+  int n, nl, a;
+  long long A, N, l0;
+  long long base;  // a > 0: the element of entry 0 of this thread's line (lane = line)
+};
+
+__device__ __forceinline__ LineTile line_tile(const PPatch& Pp, int a, int tile) {
+  LineTile t;
+  t.a = a;
+  t.n = Pp.n[a];
+  t.N = Pp.N;
+  t.A = a == 0 ? 1 : (a == 1 ? (long long)Pp.n[0] : (long long)Pp.n[0] * Pp.n[1]);
+  t.l0 = (long long)tile * kPLines;
+  t.nl = (int)min((long long)kPLines, t.N / t.n - t.l0);
+  t.base = 0;
+  const int l = threadIdx.x & (kPLines - 1);
+  if (a > 0 && l < t.nl) {
+    const long long rr = t.l0 + l, y = rr / t.A;
+    t.base = (rr - y * t.A) + t.A * (long long)t.n * y;
+  }
+  return t;
+}
+
+// f(k, l, g) over the tile's entries: entry k of line l is element g. Axis 0: the tile
+// is one contiguous range, walked by consecutive threads (no division per entry); other
+// axes: lane = line (consecutive lines are adjacent elements), warps step over k.
+template <typename F>
+__device__ __forceinline__ void tile_walk(const LineTile& t, F&& f) {
+  if (t.a == 0) {
+    const long long g0 = t.l0 * t.n;
+    const int cnt = t.nl * t.n;
+    const int dl = kPThreads / t.n, dk = kPThreads - dl * t.n;
+    int l = threadIdx.x / t.n, k = threadIdx.x - l * t.n;
+    for (int e = threadIdx.x; e < cnt; e += kPThreads) {
+      f(k, l, g0 + e);
+      k += dk;
+      l += dl;
+      if (k >= t.n) {
+        k -= t.n;
+        ++l;
+      }
+    }
+  } else {
+    const int l = threadIdx.x & (kPLines - 1);
+    if (l >= t.nl) return;
+    for (int k = threadIdx.x >> 5; k < t.n; k += kPThreads / 32) f(k, l, t.base + t.A * k);
+  }
+}
+
+// The forward and backward substitutions of line `lane` of one staged system (factor
+// rows scaled by 1 / L_kk, recurrence window in registers).
 template <int P, typename T>
-__device__ void solve_lines(T* sb, const T* sF, const T* sG, int n, int nl) {
-  const int t = threadIdx.x;
-  if (t >= nl) return;
+__device__ void solve_lines(T* sb, const T* sF, const T* sG, int n, int lane) {
   T win[P + 1];
 #pragma unroll
   for (int d = 0; d <= P; ++d) win[d] = T(0);
   for (int k = 0; k < n; ++k) {
     const T* F = sF + (size_t)k * (P + 1);
-    T acc = F[0] * sb[k * kPLS + t];
+    T acc = F[0] * sb[k * kPLS + lane];
 #pragma unroll
     for (int d = P; d >= 2; --d) acc -= F[d] * win[d];
     const T w = acc - F[1] * win[1];
-    sb[k * kPLS + t] = w;
+    sb[k * kPLS + lane] = w;
 #pragma unroll
     for (int d = P; d >= 2; --d) win[d] = win[d - 1];
     win[1] = w;
@@ -314,33 +381,54 @@ __device__ void solve_lines(T* sb, const T* sF, const T* sG, int n, int nl) {
   for (int d = 0; d <= P; ++d) win[d] = T(0);
   for (int k = n - 1; k >= 0; --k) {
     const T* G = sG + (size_t)k * (P + 1);
-    T acc = G[0] * sb[k * kPLS + t];
+    T acc = G[0] * sb[k * kPLS + lane];
 #pragma unroll
     for (int d = P; d >= 2; --d) acc -= G[d] * win[d];
     const T z = acc - G[1] * win[1];
-    sb[k * kPLS + t] = z;
+    sb[k * kPLS + lane] = z;
 #pragma unroll
     for (int d = P; d >= 2; --d) win[d] = win[d - 1];
     win[1] = z;
   }
 }
 
+// the active systems of a patch as a bit mask (uniform over the block)
+template <int K>
+__device__ __forceinline__ int patch_active(const PBatch& B, int patch) {
+  int m = 0;
+#pragma unroll
+  for (int v = 0; v < K; ++v)
+    if (B.active[patch * K + v]) m |= 1 << v;
+  return m;
+}
+
+// Band-Cholesky axis phase: axis 0 reads r scaled by D^-1/2 Dhat^1/2 into t1; axis 1
+// t1 -> t2; axis 2 t2 -> z scaled again, with the partials of r.z (new) and r.z (the
+// previous z) of each system. Every active system of the tile is staged at once and
+// warp v runs the substitutions of system v.
 template <int K, typename T>
 __device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
   for (int it = blockIdx.x; it < B.nlt[a]; it += gridDim.x) {
     const int2 tl = B.ltile[a][it];
+    const int act = patch_active<K>(B, tl.x);
+    if (!act) {  // a converged patch: only the last phase's partials (zeros)
+      if (a == 2 && threadIdx.x < K) {
+        B.lpart[(long long)it * K + threadIdx.x] = 0.0;
+        B.lpart[(long long)(B.nrzt + it) * K + threadIdx.x] = 0.0;
+      }
+      continue;
+    }
     const PPatch& Pp = B.pt[tl.x];
-    const int n = Pp.n[a], p = Pp.deg[a];
-    const long long N = Pp.N;
-    const long long A = a == 0 ? 1 : (a == 1 ? (long long)Pp.n[0] : (long long)Pp.n[0] * Pp.n[1]);
-    const long long Rl = N / n;  // lines along axis a
-    const long long l0 = (long long)tl.y * kPLines;
-    const int nl = (int)min((long long)kPLines, Rl - l0);
-    T* sb = reinterpret_cast<T*>(smem);
-    T* sF = sb + (size_t)n * kPLS;
+    const LineTile t = line_tile(Pp, a, tl.y);
+    const int n = t.n, p = Pp.deg[a];
+    const long long N = t.N;
+    T* sF = reinterpret_cast<T*>(smem);
     T* sG = sF + (size_t)n * (p + 1);
+    T* sb = sG + (size_t)n * (p + 1);
     const T* L = static_cast<const T*>(Pp.L[a]);
     const T* dinv = static_cast<const T*>(Pp.dinv[a]);
+    const T* tin = a == 1 ? static_cast<const T*>(Pp.t1) : static_cast<const T*>(Pp.t2);
+    T* tout = a == 0 ? static_cast<T*>(Pp.t1) : static_cast<T*>(Pp.t2);
     __syncthreads();  // the previous item's shared data is consumed
     for (int e = threadIdx.x; e < n * (p + 1); e += kPThreads) {
       const int k = e / (p + 1), d = e - k * (p + 1);
@@ -348,54 +436,55 @@ __device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
       sF[e] = d == 0 ? dk : dk * L[e];
       sG[e] = d == 0 ? dk : (k + d < n ? dk * L[(size_t)(k + d) * (p + 1) + d] : T(0));
     }
+#pragma unroll
     for (int v = 0; v < K; ++v) {
-      const int s = tl.x * K + v;
-      const bool on = B.active[s] != 0;  // uniform over the block
-      const T* tin = a == 1 ? static_cast<const T*>(Pp.t1) : static_cast<const T*>(Pp.t2);
-      T* tout = a == 0 ? static_cast<T*>(Pp.t1) : static_cast<T*>(Pp.t2);
-      double snew = 0.0, sold = 0.0;
-      if (on) {
-        __syncthreads();
-        // stage: (entry k, line l) of the tile <- element xx + A (k + n y) of the input,
-        // line l0 + l = xx + A y
-        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
-          int k, l;
-          if (a == 0) { l = e / n; k = e - l * n; }  // consecutive entries of one line are adjacent
-          else { k = e / nl; l = e - k * nl; }       // consecutive lines are adjacent
-          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
-          const long long g = xx + A * (k + (long long)n * y);
-          T u;
-          if (a == 0) u = (T)(Pp.r[v * N + g] * Pp.scale[g]);
-          else u = tin[v * N + g];
-          sb[k * kPLS + l] = u;
-        }
-        __syncthreads();
-        switch (p) {
-          case 2: solve_lines<2, T>(sb, sF, sG, n, nl); break;
-          case 3: solve_lines<3, T>(sb, sF, sG, n, nl); break;
-          case 4: solve_lines<4, T>(sb, sF, sG, n, nl); break;
-          default: solve_lines<1, T>(sb, sF, sG, n, nl); break;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
-          int k, l;
-          if (a == 0) { l = e / n; k = e - l * n; }
-          else { k = e / nl; l = e - k * nl; }
-          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
-          const long long g = xx + A * (k + (long long)n * y);
-          if (a == 2) {
-            const double zn = (double)sb[k * kPLS + l] * Pp.scale[g];
-            const double rg = Pp.r[v * N + g];
-            sold = fma(rg, Pp.z[v * N + g], sold);
-            snew = fma(rg, zn, snew);
-            Pp.z[v * N + g] = zn;
-          } else {
-            tout[v * N + g] = sb[k * kPLS + l];
-          }
-        }
+      if (!(act >> v & 1)) continue;
+      T* sv = sb + (size_t)v * n * kPLS;
+      const double* rv = Pp.r + v * N;
+      const T* iv = tin + v * N;
+      if (a == 0) tile_walk(t, [&](int k, int l, long long g) { sv[k * kPLS + l] = (T)(rv[g] * Pp.scale[g]); });
+      else tile_walk(t, [&](int k, int l, long long g) { sv[k * kPLS + l] = iv[g]; });
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < K && (act >> w & 1) && lane < t.nl) {
+      T* sv = sb + (size_t)w * n * kPLS;
+      switch (p) {
+        case 2: solve_lines<2, T>(sv, sF, sG, n, lane); break;
+        case 3: solve_lines<3, T>(sv, sF, sG, n, lane); break;
+        case 4: solve_lines<4, T>(sv, sF, sG, n, lane); break;
+        default: solve_lines<1, T>(sv, sF, sG, n, lane); break;
       }
+    }
+    __syncthreads();
+    double snew[K], sold[K];
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+      snew[v] = sold[v] = 0.0;
+      if (!(act >> v & 1)) continue;
+      const T* sv = sb + (size_t)v * n * kPLS;
       if (a == 2) {
-        const double s1 = pblock_sum(snew), s2 = pblock_sum(sold);
+        double* zv = Pp.z + v * N;
+        const double* rv = Pp.r + v * N;
+        double s1 = 0.0, s2 = 0.0;
+        tile_walk(t, [&](int k, int l, long long g) {
+          const double zn = (double)sv[k * kPLS + l] * Pp.scale[g];
+          const double rg = rv[g];
+          s2 = fma(rg, zv[g], s2);
+          s1 = fma(rg, zn, s1);
+          zv[g] = zn;
+        });
+        snew[v] = s1;
+        sold[v] = s2;
+      } else {
+        T* ov = tout + v * N;
+        tile_walk(t, [&](int k, int l, long long g) { ov[g] = sv[k * kPLS + l]; });
+      }
+    }
+    if (a == 2) {
+#pragma unroll
+      for (int v = 0; v < K; ++v) {
+        const double s1 = pblock_sum(snew[v]), s2 = pblock_sum(sold[v]);
         if (threadIdx.x == 0) {
           B.lpart[(long long)it * K + v] = s1;
           B.lpart[(long long)(B.nrzt + it) * K + v] = s2;
@@ -411,71 +500,115 @@ __device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
 // stage 1: t1 -> t2 (axis 1, U^T); stage 2: t2 -> t1 (axis 2, U^T) times 1 / Lambda
 // stage 3: t1 -> t2 (axis 2, U); stage 4: t2 -> t1 (axis 1, U)
 // stage 5: t1 -> z (axis 0, U) times D^-1/2 Dhat^1/2, with the partials of r.z (new, old).
-// Thread (warp w, lane l): line l of the tile, outputs i = w, w + 8, ...; the warp reads
-// one matrix row (a broadcast) and 32 lines' staged entries (consecutive banks).
+// Mat is staged transposed (row j holds Mat(., j), rows padded to nP = 4 ceil(n / 4)), the
+// inputs of every active system as in the axis phase. Thread (warp w, lane l): line l,
+// outputs i0 .. i0 + 3 for i0 = 4 w, 4 w + 32, ...; per input index j one broadcast
+// 16-byte read of Mat^T(j, i0 .. i0 + 3) and one staged entry per system, four
+// multiply-adds per system, summed over j in order.
 template <int K>
 __device__ void ph_fd(const PBatch& B, int stage, unsigned char* smem) {
   const int a = stage < 3 ? stage : 5 - stage;
   const int tr = stage < 3 ? 1 : 0;
   for (int it = blockIdx.x; it < B.nlt[a]; it += gridDim.x) {
     const int2 tl = B.ltile[a][it];
+    const int act = patch_active<K>(B, tl.x);
+    if (!act) {
+      if (stage == 5 && threadIdx.x < K) {
+        B.lpart[(long long)it * K + threadIdx.x] = 0.0;
+        B.lpart[(long long)(B.nrzt + it) * K + threadIdx.x] = 0.0;
+      }
+      continue;
+    }
     const PPatch& Pp = B.pt[tl.x];
-    const int n = Pp.n[a];
-    const long long N = Pp.N;
-    const long long A = a == 0 ? 1 : (a == 1 ? (long long)Pp.n[0] : (long long)Pp.n[0] * Pp.n[1]);
-    const long long Rl = N / n;
-    const long long l0 = (long long)tl.y * kPLines;
-    const int nl = (int)min((long long)kPLines, Rl - l0);
-    float* sb = reinterpret_cast<float*>(smem);
-    const float* Mat = Pp.Ub[a][tr];
+    const LineTile t = line_tile(Pp, a, tl.y);
+    const int n = t.n, nP = (n + 3) & ~3;
+    const long long N = t.N;
+    float* sM = reinterpret_cast<float*>(smem);
+    float* sb = sM + (size_t)n * nP;
+    const float* MT = Pp.Ub[a][1 - tr];  // Mat(i, j) = MT[j n + i]
     // stages 1, 3, 5 read t1 and 2, 4 read t2; stages 1, 3 write t2 and 0, 2, 4 write t1
     const float* tin = (stage == 2 || stage == 4) ? static_cast<const float*>(Pp.t2) : static_cast<const float*>(Pp.t1);
     float* tout = (stage == 1 || stage == 3) ? static_cast<float*>(Pp.t2) : static_cast<float*>(Pp.t1);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();  // the previous item's shared data is consumed
+    for (int e = threadIdx.x; e < n * nP; e += kPThreads) {
+      const int j = e / nP, i = e - j * nP;
+      sM[e] = i < n ? MT[(size_t)j * n + i] : 0.0f;
+    }
+#pragma unroll
     for (int v = 0; v < K; ++v) {
-      const int s = tl.x * K + v;
-      const bool on = B.active[s] != 0;  // uniform over the block
-      double snew = 0.0, sold = 0.0;
-      if (on) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < nl * n; e += kPThreads) {
-          int k, l;
-          if (a == 0) { l = e / n; k = e - l * n; }
-          else { k = e / nl; l = e - k * nl; }
-          const long long rr = l0 + l, y = rr / A, xx = rr - y * A;
-          const long long g = xx + A * (k + (long long)n * y);
-          const float u = stage == 0 ? (float)(Pp.r[v * N + g] * Pp.scale[g]) : tin[v * N + g];
-          sb[k * kPLS + l] = __bfloat162float(__float2bfloat16(u));
-        }
-        __syncthreads();
-        if (lane < nl) {
-          const long long rr = l0 + lane, y = rr / A, xx = rr - y * A;
-          // the line's other two indices, for 1 / Lambda (stage 2: along axis 2, the line is (i0, i1))
-          float lam01 = 1.0f;
-          if (stage == 2) {
-            const int i0 = (int)(xx % Pp.n[0]), i1 = (int)(xx / Pp.n[0]);
-            lam01 = Pp.lam[0][i0] * Pp.lam[1][i1];
+      if (!(act >> v & 1)) continue;
+      float* sv = sb + (size_t)v * n * kPLS;
+      const double* rv = Pp.r + v * N;
+      const float* iv = tin + v * N;
+      if (stage == 0)
+        tile_walk(t, [&](int k, int l, long long g) {
+          sv[k * kPLS + l] = __bfloat162float(__float2bfloat16((float)(rv[g] * Pp.scale[g])));
+        });
+      else
+        tile_walk(t, [&](int k, int l, long long g) {
+          sv[k * kPLS + l] = __bfloat162float(__float2bfloat16(iv[g]));
+        });
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double snew[K], sold[K];
+#pragma unroll
+    for (int v = 0; v < K; ++v) snew[v] = sold[v] = 0.0;
+    if (lane < t.nl) {
+      // 1 / Lambda of the line's two other indices (stage 2: along axis 2, the line is (i0, i1))
+      float lam01 = 1.0f;
+      if (stage == 2) {
+        const long long xx = t.l0 + lane;
+        lam01 = Pp.lam[0][(int)(xx % Pp.n[0])] * Pp.lam[1][(int)(xx / Pp.n[0])];
+      }
+      const long long gl = a == 0 ? (t.l0 + lane) * n : t.base;  // element of entry 0 of the line
+      const long long ga = a == 0 ? 1 : t.A;                      // element stride along the line
+      for (int i0 = 4 * w; i0 < n; i0 += 4 * (kPThreads / 32)) {
+        float acc[K][4];
+#pragma unroll
+        for (int v = 0; v < K; ++v)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[v][q] = 0.0f;
+        const float* mj = sM + i0;
+        const float* uj = sb + lane;
+        for (int j = 0; j < n; ++j) {
+          const float4 m = *reinterpret_cast<const float4*>(mj + (size_t)j * nP);
+#pragma unroll
+          for (int v = 0; v < K; ++v) {
+            if (!(act >> v & 1)) continue;
+            const float u = uj[((size_t)v * n + j) * kPLS];
+            acc[v][0] = fmaf(m.x, u, acc[v][0]);
+            acc[v][1] = fmaf(m.y, u, acc[v][1]);
+            acc[v][2] = fmaf(m.z, u, acc[v][2]);
+            acc[v][3] = fmaf(m.w, u, acc[v][3]);
           }
-          for (int i = w; i < n; i += kPThreads / 32) {
-            const float* Mi = Mat + (size_t)i * n;
-            float acc = 0.0f;
-            for (int j = 0; j < n; ++j) acc = fmaf(Mi[j], sb[j * kPLS + lane], acc);
-            const long long g = xx + A * (i + (long long)n * y);
-            if (stage == 2) acc *= lam01 * Pp.lam[2][i];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = i0 + q;
+          if (i >= n) break;
+          const long long g = gl + ga * i;
+          const float li = stage == 2 ? lam01 * Pp.lam[2][i] : 1.0f;
+#pragma unroll
+          for (int v = 0; v < K; ++v) {
+            if (!(act >> v & 1)) continue;
             if (stage == 5) {
-              const double zn = (double)acc * Pp.scale[g];
+              const double zn = (double)acc[v][q] * Pp.scale[g];
               const double rg = Pp.r[v * N + g];
-              sold = fma(rg, Pp.z[v * N + g], sold);
-              snew = fma(rg, zn, snew);
+              sold[v] = fma(rg, Pp.z[v * N + g], sold[v]);
+              snew[v] = fma(rg, zn, snew[v]);
               Pp.z[v * N + g] = zn;
             } else {
-              tout[v * N + g] = acc;
+              tout[v * N + g] = stage == 2 ? acc[v][q] * li : acc[v][q];
             }
           }
         }
       }
-      if (stage == 5) {
-        const double s1 = pblock_sum(snew), s2 = pblock_sum(sold);
+    }
+    if (stage == 5) {
+#pragma unroll
+      for (int v = 0; v < K; ++v) {
+        const double s1 = pblock_sum(snew[v]), s2 = pblock_sum(sold[v]);
         if (threadIdx.x == 0) {
           B.lpart[(long long)it * K + v] = s1;
           B.lpart[(long long)(B.nrzt + it) * K + v] = s2;
@@ -564,53 +697,84 @@ __device__ void lead_stats(const PBatch& B) {
   }
 }
 
+// Phase clock: block 0 adds the time since its previous mark to B.ptime[cat] once a
+// phase's grid barrier has passed (the barrier passes when the last block arrives, so
+// the interval is the phase's duration on the whole grid, barrier included).
+enum PhaseCat { kPhPredict, kPhKProduct, kPhScalars, kPhPrecond, kPhDirection, kPhMProduct, kPhXr, kPhUpdate };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void pmark(const PBatch& B, int cat, unsigned long long& last) {
+  if (B.ptime && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long now = gtimer();
+    B.ptime[cat] += now - last;
+    last = now;
+  }
+}
+
 // the preconditioner z = P^-1 r (three axis phases) and the r.z scalars
 template <int K, typename T>
-__device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first) {
+__device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first, unsigned long long& clk) {
   if (B.fd) {
     for (int st = 0; st < 6; ++st) {
       ph_fd<K>(B, st, smem);
       if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+      pmark(B, kPhPrecond, clk);
     }
   } else {
     for (int a = 0; a < 3; ++a) {
       ph_axis<K, T>(B, a, smem);
       if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+      pmark(B, kPhPrecond, clk);
     }
   }
   if (blockIdx.x == 0) lead_rz(B, first);
-  return pgrid_sync(B.bar, B.bar_limit, B.err);
+  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
+  pmark(B, kPhScalars, clk);
+  return true;
 }
 
 template <int K, typename T>
 __global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
   extern __shared__ __align__(16) unsigned char psmem[];
+  unsigned long long clk = (B.ptime && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ULL;
+#define IGA_PSYNC(cat)                                         \
+  do {                                                         \
+    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;        \
+    pmark(B, cat, clk);                                        \
+  } while (0)
   ph_predict<K>(B);
-  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+  IGA_PSYNC(kPhPredict);
   // b = K (-Y) into r (x0 = 0: r = b), partials of b.b
   ph_band<K>(B, true, B.Yp, B.rp, 2, B.part);
-  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+  IGA_PSYNC(kPhKProduct);
   if (blockIdx.x == 0) lead_start(B);
-  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
-  if (!pprecond<K, T>(B, psmem, true)) return;
+  IGA_PSYNC(kPhScalars);
+  if (!pprecond<K, T>(B, psmem, true, clk)) return;
   bool first = true;
   for (int iter = 0;; ++iter) {
     ph_dir<K>(B, first);
     first = false;
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    IGA_PSYNC(kPhDirection);
     ph_band<K>(B, false, B.pp, B.qp, 1, B.part);  // q = M p, partials of p.q
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    IGA_PSYNC(kPhMProduct);
     if (blockIdx.x == 0) lead_alpha(B);
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    IGA_PSYNC(kPhScalars);
     ph_xr<K>(B);
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    IGA_PSYNC(kPhXr);
     if (blockIdx.x == 0) lead_check(B);
-    if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return;
+    IGA_PSYNC(kPhScalars);
     if (*(volatile int*)&B.flags[0] == 0) break;  // the same value in every block
-    if (!pprecond<K, T>(B, psmem, false)) return;
+    if (!pprecond<K, T>(B, psmem, false, clk)) return;
   }
+#undef IGA_PSYNC
   ph_update<K>(B);
   if (blockIdx.x == 0) lead_stats(B);
+  pmark(B, kPhUpdate, clk);  // block 0's own end
 }
 
 template <int K, typename T>
@@ -641,9 +805,9 @@ cudaError_t batch_go(cudaStream_t s, const PBatch& B, size_t smem, int sms, int*
 
 int batch_row_tiles(long long N) { return (int)((N + kPRows - 1) / kPRows); }
 int batch_line_tiles(long long N, int n) { return (int)((N / n + kPLines - 1) / kPLines); }
-size_t batch_smem_bytes(int nmax, int pmax, bool f32, bool fd) {
-  if (fd) return (size_t)nmax * kPLS * sizeof(float) + 64;
-  return (size_t)nmax * (kPLS + 2 * (pmax + 1)) * (f32 ? sizeof(float) : sizeof(double)) + 64;
+size_t batch_smem_bytes(int nmax, int pmax, int k, bool f32, bool fd) {
+  if (fd) return ((size_t)nmax * ((nmax + 3) & ~3) + (size_t)k * nmax * kPLS) * sizeof(float) + 64;
+  return (size_t)nmax * (2 * (pmax + 1) + (size_t)k * kPLS) * (f32 ? sizeof(float) : sizeof(double)) + 64;
 }
 
 cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid) {

@@ -12,6 +12,8 @@ operators; band-Cholesky Kronecker or BF16 fast-diagonalisation preconditioner).
   * the BF16 fast diagonalisation (flexible PCG) at tol 1e-10: within 1e-8 of the oracle
     and of the patches stepped alone with the tensor-core BF16 preconditioner;
   * a second persistent run equals the first bit for bit (fixed-order reductions);
+  * the phase clock (iga_batch_phase_times): the products and the preconditioner are timed,
+    the times add up to no more than the call, and a batch without a persistent step has none;
   * refusals: a form the persistent step does not compute gives IGA_EINVAL and the batch
     keeps its graph path.
 """
@@ -80,9 +82,25 @@ def test_persistent_batch_matches_oracle_and_patches_alone():
     for g, st, (u0, v0) in zip(pats, states, inits):
         g.state_init(k, u0, v0, st)
     b = iga.Batch(pats)
+    with pytest.raises(iga.IgaError) as e:  # no persistent step yet
+        b.phase_times()
+    assert e.value.status == iga.EINVAL
     b.set_persistent(True)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
     stats = b.step(states, k, rho, dts, nsteps)
+    t1.record()
+    t1.synchronize()
     assert stats[0].launches == nsteps  # one launch per batch step
+    # the device-side phase clock: every kind of phase ran, and the phases add up to the call
+    ph = b.phase_times()
+    total = sum(ph.values())
+    print("persistent batch phases (ms over %d steps): %s; call %.3f ms" % (
+        nsteps, ", ".join("%s %.3f" % kv for kv in ph.items()), t0.elapsed_time(t1)))
+    assert all(v >= 0.0 for v in ph.values()) and ph["M product"] > 0.0 and ph["preconditioner"] > 0.0, ph
+    assert total <= t0.elapsed_time(t1) * 1.01 + 0.05
     batched = [s.cpu().numpy().reshape(3 * k, -1) for s in states]
     for i, (g, st, (u0, v0), dt) in enumerate(zip(pats, states, inits, dts)):
         assert stats[i].steps == nsteps and stats[i].solves == k * nsteps and stats[i].max_relres <= 1e-13
