@@ -86,6 +86,11 @@ StepCoefs step_coefs(int k, double rho, double dt) {
     sc.c[m] = std::pow(dt, m) / fact;
   }
   galpha_params(k, rho, sc.alpha, sc.beta, sc.gamma);
+  for (int j = 0; j < k; ++j) {  // the update's per-stage factors, once per step instead of per entry
+    sc.ralpha[j] = 1.0 / sc.alpha[j];
+    sc.gtau[j] = sc.gamma[j] * dt;
+    sc.btau2[j] = sc.beta[j] * dt * dt;
+  }
   return sc;
 }
 
@@ -273,13 +278,14 @@ int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double
                          f32 ? (const void*)d[2].cdinv32 : d[2].cdinv};
     const int mid = f32 ? 0 : 1;  // intermediates are FP64 only in the FP64 form
     const double* sc = h->scale;
+    const float* s32 = f32 ? h->scale32 : nullptr;  // the FP32 form scales in FP32
     if (d3) {
-      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n12}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
+      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n12}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr, nullptr, nullptr, nullptr, s32));
       LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], n[2]}, nvec, active, f32, L[1], Di[1], t1, mid, t2, mid, N, nullptr, nullptr));
-      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz));
+      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz, s32));
     } else {
-      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n[1]}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr));
-      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz));
+      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n[1]}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr, nullptr, nullptr, nullptr, s32));
+      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz, s32));
     }
     return IGA_OK;
   }
@@ -1230,6 +1236,8 @@ int create_handle(int dim, const int* degree, const int* nknots, const double* c
       sc[i] = std::sqrt(dh / D[i]);
     }
     CKS(upload(h, &h->scale, sc));
+    std::vector<float> sc32(sc.begin(), sc.end());
+    CKS(upload(h, &h->scale32, sc32));
     return IGA_OK;
   };
   rc = setup();
@@ -1320,7 +1328,7 @@ void iga_destroy(iga_handle* h) {
     for (int t = 0; t < 2; ++t)
       if (d.Btc16[t]) { cudaFree(d.Btc16[t]); d.Btc16[t] = nullptr; }
   }
-  dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->dflag);
+  dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->scale32); dfree(h->dflag);
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
   dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);

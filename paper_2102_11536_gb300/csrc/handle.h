@@ -26,6 +26,7 @@ struct iga_handle {
   long long gstride = 0;
   double* Dm = nullptr;     // diag(M)
   double* scale = nullptr;  // D^{-1/2} Dhat^{1/2}
+  float* scale32 = nullptr; // the same rounded to FP32 (the FP32 band-Cholesky solve scales in FP32)
   int* dflag = nullptr;     // device scratch flag
   // assembled form
   double* Mband = nullptr;

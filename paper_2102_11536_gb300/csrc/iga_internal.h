@@ -213,6 +213,7 @@ struct StepCoefs {
   int k;
   double c[kMaxRows];          // tau^m / m!
   double alpha[kMaxK], beta[kMaxK], gamma[kMaxK];
+  double ralpha[kMaxK], gtau[kMaxK], btau2[kMaxK];  // 1 / alpha_j, gamma_j tau, beta_j tau^2
   double tau;
   int damped;                  // Rayleigh damping C = aM M + aK K present
   double aM, aK;
@@ -428,7 +429,8 @@ cudaError_t launch_ws_target(cudaStream_t s, long long N, int k, const double* Z
 cudaError_t launch_kron_axis(cudaStream_t s, int n, int p, AxisShape sh, int nvec, const int* active, int f32,
                              const void* L, const void* dinv, const void* in, int in_is_double, void* out,
                              int out_is_double, long long vs, const double* pre, const double* post,
-                             const double* rdot = nullptr, double* part = nullptr, int* npart = nullptr);
+                             const double* rdot = nullptr, double* part = nullptr, int* npart = nullptr,
+                             const float* scale32 = nullptr);
 
 // Fixed scratch of the allocation-free preconditioner entry point: values per buffer.
 constexpr long long kNoAllocMaxElems = 1LL << 20;

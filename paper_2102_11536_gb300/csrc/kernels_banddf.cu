@@ -150,7 +150,8 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
     out[i] = df_split_entry(x[v * vs + i], E, sc);
 }
 
-// The two passes of a vector split in one cooperative launch (every block resident):
+// The two passes of a vector split in one cooperative launch (two blocks per SM; four
+// entries per thread and pass with their loads issued together):
 // block maxima, a grid barrier, then every block reduces the maxima and splits its
 // grid-stride share. With z (and beta), the first pass also forms the PCG direction
 // x = z + beta x (active systems; the same operation as k_cg_update_p) before taking
@@ -168,19 +169,41 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
                                                        unsigned int* bar, int* err, long long limit) {
   const int G = gridDim.x;
   const long long stride = (long long)G * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int U = 4;  // entries per thread and pass, their loads issued together
   for (int v = 0; v < nvec; ++v) {
     unsigned long long m = 0;
     if (!active || active[v]) {
+      double* xv = x + v * vs;
       if (z) {
         const double b = beta[v];
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-          const double pn = fma(b, x[v * vs + i], z[v * vs + i]);
-          x[v * vs + i] = pn;
-          m = max(m, abs_bits(pn));
+        const double* zv = z + v * vs;
+        for (long long i = i0; i < n; i += U * stride) {
+          double xa[U], za[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long iu = i + u * stride;
+            xa[u] = iu < n ? xv[iu] : 0.0;
+            za[u] = iu < n ? zv[iu] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long iu = i + u * stride;
+            if (iu < n) {
+              const double pn = fma(b, xa[u], za[u]);
+              xv[iu] = pn;
+              m = max(m, abs_bits(pn));
+            }
+          }
         }
       } else {
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-          m = max(m, abs_bits(x[v * vs + i]));
+        for (long long i = i0; i < n; i += U * stride) {
+          double xa[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) xa[u] = i + u * stride < n ? xv[i + u * stride] : 0.0;
+#pragma unroll
+          for (int u = 0; u < U; ++u) m = max(m, abs_bits(xa[u]));
+        }
       }
     }
     m = block_max(m);
@@ -216,8 +239,15 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
     if (blockIdx.x == 0 && threadIdx.x == 0) Eout[v] = E;
     const double sc = ldexp(1.0, -E);
     float2* out = xs + (long long)v * xvs + kDfPad;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-      out[i] = df_split_entry(x[v * vs + i], E, sc);
+    const double* xv = x + v * vs;
+    for (long long i = i0; i < n; i += U * stride) {
+      double xa[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xa[u] = i + u * stride < n ? xv[i + u * stride] : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (i + u * stride < n) out[i + u * stride] = df_split_entry(xa[u], E, sc);
+    }
   }
 }
 
@@ -1369,6 +1399,7 @@ cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nv
   }
   const int sm = dev < 64 ? nsm[dev] : -1;
   if (sm <= 0) return cudaErrorNotSupported;
+  // two blocks per SM: co-resident with the kernels of other patches' graph branches
   const long long G = std::min<long long>(std::min<long long>(2LL * sm, kDfBlocks), std::max<long long>(1, (N + 255) / 256));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);

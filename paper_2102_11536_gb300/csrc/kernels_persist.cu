@@ -294,14 +294,13 @@ __device__ void ph_update(const PBatch& B) {
       for (int r = R - 1; r >= q; --r) s = fma(P.sc.c[r - q], xr[r], s);
       t[q] = s;
     }
-    const double tau = P.sc.tau;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int row = 3 * j + 2;
-      const double Pj = (P.x[j * N + i] - t[row]) / P.sc.alpha[j];
+      const double Pj = (P.x[j * N + i] - t[row]) * P.sc.ralpha[j];
       P.X[row * N + i] = t[row] + Pj;
-      P.X[(row - 1) * N + i] = fma(P.sc.gamma[j] * tau, Pj, t[row - 1]);
-      P.X[(row - 2) * N + i] = fma(P.sc.beta[j] * tau * tau, Pj, t[row - 2]);
+      P.X[(row - 1) * N + i] = fma(P.sc.gtau[j], Pj, t[row - 1]);
+      P.X[(row - 2) * N + i] = fma(P.sc.btau2[j], Pj, t[row - 2]);
     }
   }
 }

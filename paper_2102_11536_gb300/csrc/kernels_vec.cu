@@ -58,7 +58,7 @@ __device__ __forceinline__ void reduce_partials(int nvec, const double* partial,
   const int v = w / per, q = w - v * per;
   if (v < nvec) {
     double s = 0.0;
-#pragma unroll 4
+#pragma unroll 8
     for (int b = q * 32 + lane; b < np; b += per * 32) s += partial[(long long)v * np + b];
     s = warp_sum(s);
     if (lane == 0) wsum[w] = s;
@@ -134,7 +134,10 @@ cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, 
 }
 
 // alpha = r.z / p.q; breakdown (p.q <= 0 or not finite) stops the system with IGA_ENUMERIC.
-__global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double* ppq, int np, CgScalars c) {
+// p.q comes from the band product's per-block partials (N / 128 of them per vector), so
+// this reduction takes a block of 32 warps.
+constexpr int kEpiWide = 1024;
+__global__ void __launch_bounds__(kEpiWide) k_cg_alpha(int nvec, const double* ppq, int np, CgScalars c) {
   __shared__ double sq[kMaxVec];
   reduce_partials(nvec, ppq, sq, np);
   const int v = threadIdx.x;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_cg_alpha(int nvec, const double
 }
 
 cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int np, CgScalars c) {
-  k_cg_alpha<<<1, kEpiThreads, 0, s>>>(nvec, partial, np, c);
+  k_cg_alpha<<<1, kEpiWide, 0, s>>>(nvec, partial, np, c);
   return cudaGetLastError();
 }
 
@@ -345,14 +348,13 @@ __global__ void __launch_bounds__(256) k_update(long long N, StepCoefs sc, doubl
     for (int r = R - 1; r >= q; --r) s = fma(sc.c[r - q], x[r], s);
     t[q] = s;
   }
-  const double tau = sc.tau;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int row = 3 * j + 2;
-    const double P = (Z[j * N + i] - t[row]) / sc.alpha[j];
+    const double P = (Z[j * N + i] - t[row]) * sc.ralpha[j];
     X[row * N + i] = t[row] + P;
-    X[(row - 1) * N + i] = fma(sc.gamma[j] * tau, P, t[row - 1]);
-    X[(row - 2) * N + i] = fma(sc.beta[j] * tau * tau, P, t[row - 2]);
+    X[(row - 1) * N + i] = fma(sc.gtau[j], P, t[row - 1]);
+    X[(row - 2) * N + i] = fma(sc.btau2[j], P, t[row - 2]);
   }
 }
 
