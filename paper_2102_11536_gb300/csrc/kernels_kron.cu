@@ -71,11 +71,13 @@ __device__ __forceinline__ T kron_in(const TI* x, long long g, const double* pre
   if constexpr (std::is_same<T, TI>::value) {
     if (!pre) return x[g];
   }
-  if constexpr (std::is_same<T, float>::value) {
-    if (pre && s32) return as_f32(x[g]) * s32[g];
+  if constexpr (std::is_same<T, float>::value) {  // the FP32 form scales by s32 (never null with pre)
+    if (pre) return as_f32(x[g]) * s32[g];
+    return as_f32(x[g]);
+  } else {
+    if (pre) return as_f64(x[g]) * pre[g];
+    return as_f64(x[g]);
   }
-  if (pre) return narrow<T>(as_f64(x[g]) * pre[g]);
-  return narrow<T>(as_f64(x[g]));
 }
 
 // one output entry: u scaled by post[g] (FP64, or with s32 in FP32 and widened), the
@@ -90,9 +92,8 @@ __device__ __forceinline__ void kron_out(T u, TO* o, long long g, const double* 
     }
   }
   double w;
-  if (post && s32) w = as_f64((float)u * s32[g]);
-  else if (post) w = as_f64(u) * post[g];
-  else w = as_f64(u);
+  if constexpr (std::is_same<T, float>::value) w = post ? as_f64(u * s32[g]) : as_f64(u);
+  else w = post ? u * post[g] : u;
   if (rv) {
     const double rr = rv[g];
     sold = fma(rr, as_f64(o[g]), sold);
@@ -234,11 +235,45 @@ __global__ void __launch_bounds__(kThreads) k_kron_axis(int n, long long A, long
       }
     }
   } else if (nl == kLines) {
+    // four entries at a time: every load of the four (r, the previous output, the scaling)
+    // is issued before their stores, which the compiler may not move loads across; the
+    // entries are then finished in order (the same order as one at a time)
     const int line = t & (kLines - 1);
-#pragma unroll 4
-    for (int k = t / kLines; k < n; k += kThreads / kLines) {
-      const long long g = gline + A * k;
-      kron_out<T>(sb[k * kLS + line], o, g, post, s32, rv, snew, sold);
+    constexpr int KS = kThreads / kLines;
+    for (int kb = t / kLines; kb < n; kb += 4 * KS) {
+      T u[4], ps[4];  // the entry and its scaling (the FP32 form's s32, or post)
+      double rr[4], zo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kb + q * KS;
+        rr[q] = zo[q] = 0.0;
+        u[q] = ps[q] = T(0);
+        if (k < n) {
+          const long long g = gline + A * k;
+          u[q] = sb[k * kLS + line];
+          if (post) {
+            if constexpr (std::is_same<T, float>::value) ps[q] = s32[g];
+            else ps[q] = post[g];
+          }
+          if (rv) {
+            rr[q] = rv[g];
+            zo[q] = as_f64(o[g]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kb + q * KS;
+        if (k < n) {
+          const long long g = gline + A * k;
+          const double w = post ? as_f64(u[q] * ps[q]) : as_f64(u[q]);
+          if (rv) {
+            sold = fma(rr[q], zo[q], sold);
+            snew = fma(rr[q], w, snew);
+          }
+          o[g] = (TO)narrow<TO>(w);
+        }
+      }
     }
   } else {
     for (int e = t; e < cnt; e += kThreads) {
@@ -301,6 +336,7 @@ cudaError_t kron_go(cudaStream_t s, int n, AxisShape sh, int nvec, const int* ac
                     const void* dinv, const void* in, void* out, long long vs, const double* pre,
                     const double* post, const double* rdot, double* part, int* npart, const float* s32) {
   const int mode = (pre ? 1 : 0) | (post ? 2 : 0);
+  if (std::is_same<T, float>::value && mode && !s32) return cudaErrorInvalidValue;  // FP32 scaling needs s32
 #define IGA_KGO(M) kron_go_m<P, T, TI, TO, M>(s, n, sh, nvec, active, L, dinv, in, out, vs, pre, post, rdot, part, npart, s32)
   constexpr bool in_d = std::is_same<TI, double>::value, out_d = std::is_same<TO, double>::value;
   constexpr bool fp64 = std::is_same<T, double>::value;  // the FP64 form: every axis in every mode

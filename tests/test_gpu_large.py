@@ -162,7 +162,7 @@ def test_multipatch_batch_48():
     """The 48-patch batch (sizes 16^3..96^3 elements, p in {2, 3, 4}, per-patch
     deformations): FP64 assembled operators, BF16 preconditioner, autotuned band
     launches; the batched graph steps equal every patch stepped alone, and the
-    largest and smallest patches' operators match oracle rows."""
+    operators of the largest patch and of the 16 smallest match oracle rows."""
     ws = W.multipatch_batch()
     k, rho, nsteps = 2, 0.5, 3
     pats, states, dts, inits = [], [], [], []
@@ -186,11 +186,13 @@ def test_multipatch_batch_48():
         sa = g.step(st, k, rho, dt, nsteps)
         assert np.array_equal(st.cpu().numpy(), batched[i]), i
         assert sa.iters == stb[i].iters
-    sizes = [g.N for g in pats]
-    for i in (int(np.argmax(sizes)), int(np.argmin(sizes))):
+    # operator rows against the oracle: the largest patch (30 rows) and the 16 smallest (6 rows
+    # each: every degree, many shapes; the oracle's geometry at every Gauss point bounds the count)
+    order = sorted(range(len(pats)), key=lambda i: pats[i].N)
+    for i in [order[-1]] + order[:16]:
         w, g = ws[i], pats[i]
         P = oracle.Patch(w.p, w.knots, w.ctrl())
-        rows = W.sample_indices(P.N, 30, seed=i)
+        rows = W.sample_indices(P.N, 30 if i == order[-1] else 6, seed=i)
         Mr, Kr = P.assemble(rows)
         X = np.random.default_rng(i).standard_normal(P.N)
         x = torch.from_numpy(X).to(DEV)
