@@ -546,6 +546,23 @@ int iga_batch_set_persistent(iga_batch* b, int on);
 int iga_batch_phase_times(iga_batch* b, double* ms, int n);
 
 /*
+ * iga_batch_set_persistent_variant / iga_batch_persistent_variant -- the launch variant
+ * of the persistent step: 0 = three blocks of 256 threads per SM (80 registers per
+ * thread), the band products loading two stored slots per pass; 1 = two blocks per SM
+ * (128 registers), four slots per pass (k <= 2 only; with k > 2 variant 0 runs). Both
+ * compute every term, reduction and update in the same order, so they give bitwise the
+ * same results; they differ in speed. variant = -1 (the default): the batch times its
+ * first persistent steps, each variant twice, alternating, and keeps the faster one for
+ * the batch's life (the choice survives changes of k, rho, dt or states); 0 or 1 forces
+ * that variant. iga_batch_persistent_variant returns in *variant the variant in use
+ * (forced, chosen, or -1 while still timing) and in ms[0..1] (host, may be NULL) the
+ * fastest timed step of each variant (-1 if never timed). IGA_EINVAL for another variant
+ * number. The paper has no counterpart.
+ */
+int iga_batch_set_persistent_variant(iga_batch* b, int variant);
+int iga_batch_persistent_variant(iga_batch* b, int* variant, double* ms);
+
+/*
  * iga_probe_fp64_fma -- measured FP64 FMA throughput of `device` (no counterpart in
  * the paper; measurement aid): 8 independent FMA chains per thread, 4 blocks of 256
  * threads per SM, 2^14 iterations, averaged over 5 timed launches after 2

@@ -112,6 +112,8 @@ def lib():
                                           ctypes.POINTER(Stats)]),
         "iga_batch_set_persistent": (ctypes.c_int, [H, ctypes.c_int]),
         "iga_batch_phase_times": (ctypes.c_int, [H, dp, ctypes.c_int]),
+        "iga_batch_set_persistent_variant": (ctypes.c_int, [H, ctypes.c_int]),
+        "iga_batch_persistent_variant": (ctypes.c_int, [H, ip, dp]),
         "iga_mp_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                          ctypes.c_double, ip, ip, ctypes.POINTER(ctypes.c_longlong), ip,
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]),
@@ -146,7 +148,8 @@ def exported_symbols():
             "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
             "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
-            "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent", "iga_batch_phase_times"]
+            "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent", "iga_batch_phase_times",
+            "iga_batch_set_persistent_variant", "iga_batch_persistent_variant"]
 
 
 def multipatch_layout(patches, tol=0.0):
@@ -663,6 +666,22 @@ class Batch:
         if rc != OK:
             raise IgaError(rc, "iga_batch_phase_times: " + lib().iga_batch_last_error(self.b).decode())
         return dict(zip(self.PHASES, list(ms)))
+
+    def set_persistent_variant(self, variant=-1):
+        """Launch variant of the persistent step (iga_batch_set_persistent_variant): -1 chooses
+        by timing the first steps, 0 or 1 forces one."""
+        rc = lib().iga_batch_set_persistent_variant(self.b, int(variant))
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_set_persistent_variant: " + lib().iga_batch_last_error(self.b).decode())
+
+    def persistent_variant(self):
+        """(variant in use or -1, (fastest timed ms of variant 0, of variant 1) or -1 each)."""
+        v = ctypes.c_int(0)
+        ms = (ctypes.c_double * 2)()
+        rc = lib().iga_batch_persistent_variant(self.b, ctypes.byref(v), ms)
+        if rc != OK:
+            raise IgaError(rc, "iga_batch_persistent_variant: " + lib().iga_batch_last_error(self.b).decode())
+        return v.value, (ms[0], ms[1])
 
     def close(self):
         if getattr(self, "b", None):

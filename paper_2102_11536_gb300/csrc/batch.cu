@@ -20,19 +20,32 @@ struct PersistState {
   std::vector<double*> states;
   bool f32 = false;
   size_t smem = 0;
-  int grid = 0;
+  int grid[kPersistVariants] = {};
   PBatch B{};
   std::vector<void*> allocs;  // every device allocation, freed together
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph[kPersistVariants] = {};
+  cudaGraphExec_t gexec[kPersistVariants] = {};
+  int nvariants = 1;                        // variants built (the second only for k <= 2)
   double phase_ms[kPersistPhases] = {};  // of the last iga_batch_step, summed over its steps
   bool have_phases = false;
+};
+
+// Launch variant of the persistent step (kernels_persist.cu: blocks per SM and slots per
+// band pass): forced, or chosen by timing the first steps of the batch -- each variant
+// twice, alternating -- and taking the faster one. Kept across rebuilds of the state.
+struct PersistTuning {
+  int force = -1;            // -1: choose by timing
+  int chosen = -1;           // the variant in use once chosen
+  double ms[kPersistVariants] = {-1.0, -1.0};  // best timed step per variant
+  int samples[kPersistVariants] = {0, 0};
+  cudaEvent_t ev[2 * kPersistVariants] = {};
 };
 
 struct iga_batch {
   std::vector<iga_handle*> p;
   bool persistent = false;
   PersistState* ps = nullptr;
+  PersistTuning tune;
   int device = 0;
   cudaStream_t s0 = nullptr;
   cudaEvent_t fork = nullptr, done = nullptr;
@@ -68,8 +81,10 @@ void drop_batch_graph(iga_batch* b) {
 
 void free_persist(PersistState* ps) {
   if (!ps) return;
-  if (ps->gexec) cudaGraphExecDestroy(ps->gexec);
-  if (ps->graph) cudaGraphDestroy(ps->graph);
+  for (int v = 0; v < kPersistVariants; ++v) {
+    if (ps->gexec[v]) cudaGraphExecDestroy(ps->gexec[v]);
+    if (ps->graph[v]) cudaGraphDestroy(ps->graph[v]);
+  }
   for (void* a : ps->allocs) cudaFree(a);
   delete ps;
 }
@@ -266,30 +281,33 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
       cudaMemsetAsync(B.beta, 0, sizeof(double) * S, b->s0) != cudaSuccess)
     return bfail(b, IGA_ECUDA, "persistent batch: cudaMemsetAsync");
   ps->smem = batch_smem_bytes(nmax, pmax, k, ps->f32, fd);
-  // the graph holding the one cooperative launch of a batch step
-  cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-  const cudaError_t le = launch_batch_step(b->s0, B, ps->f32, ps->smem, &ps->grid);
-  cudaGraph_t g = nullptr;
-  const cudaError_t ee = cudaStreamEndCapture(b->s0, &g);
-  if (le != cudaSuccess || ee != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();
-    return bfail(b, IGA_ECUDA, std::string("persistent batch launch: ") +
-                                   cudaGetErrorString(le != cudaSuccess ? le : ee));
-  }
-  e = cudaGraphInstantiate(&ps->gexec, g, 0);
-  ps->graph = g;
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return bfail(b, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  // one graph per launch variant, each holding the one cooperative launch of a batch step
+  ps->nvariants = k <= 2 ? kPersistVariants : 1;
+  for (int v = 0; v < ps->nvariants; ++v) {
+    cudaError_t e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    const cudaError_t le = launch_batch_step(b->s0, B, ps->f32, ps->smem, v, &ps->grid[v]);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->s0, &g);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return bfail(b, IGA_ECUDA, std::string("persistent batch launch: ") +
+                                     cudaGetErrorString(le != cudaSuccess ? le : ee));
+    }
+    ps->graph[v] = g;
+    e = cudaGraphInstantiate(&ps->gexec[v], g, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, IGA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
   }
   return IGA_OK;
 }
 
 bool persist_current(const iga_batch* b, double* const* states, int k, double rho, const double* dt) {
   const PersistState* ps = b->ps;
-  if (!ps || !ps->gexec || ps->k != k || ps->rho != rho) return false;
+  if (!ps || !ps->gexec[0] || ps->k != k || ps->rho != rho) return false;
   for (size_t i = 0; i < b->p.size(); ++i)
     if (ps->states[i] != states[i] || ps->dt[i] != dt[i] || b->p[i]->ws_gen < 0) return false;
   return true;
@@ -312,7 +330,31 @@ int persist_steps(iga_batch* b, double* const* states, int k, double rho, const 
   if (e == cudaSuccess) e = cudaMemsetAsync(B.max_iters, 0, sizeof(int) * S, b->s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.flags, 0, sizeof(int) * 2, b->s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.ptime, 0, sizeof(unsigned long long) * kPersistPhases, b->s0);
-  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) e = cudaGraphLaunch(ps->gexec, b->s0);
+  // the variant of every launch; the timed ones (at most one per variant per call) between events
+  PersistTuning& tu = b->tune;
+  int timed[kPersistVariants] = {0, 0};
+  for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
+    int v = tu.force >= 0 ? tu.force : tu.chosen;
+    bool time_it = false;
+    if (v < 0) {  // still choosing: the variant with the fewest samples (two each), alternating
+      v = 0;
+      for (int q = 1; q < ps->nvariants; ++q)
+        if (tu.samples[q] < tu.samples[v]) v = q;
+      time_it = timed[v] == 0;
+    }
+    if (v >= ps->nvariants) v = 0;
+    if (time_it) {
+      for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+        if (!tu.ev[2 * v + q]) e = cudaEventCreate(&tu.ev[2 * v + q]);
+      if (e == cudaSuccess) e = cudaEventRecord(tu.ev[2 * v], b->s0);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(ps->gexec[v], b->s0);
+    if (time_it && e == cudaSuccess) {
+      e = cudaEventRecord(tu.ev[2 * v + 1], b->s0);
+      timed[v] = 1;
+      ++tu.samples[v];  // counted when launched, read after the synchronisation below
+    }
+  }
   std::vector<long long> tot(S);
   std::vector<int> mx(S), st(S);
   std::vector<double> rel(S);
@@ -332,6 +374,24 @@ int persist_steps(iga_batch* b, double* const* states, int k, double rho, const 
   if (e != cudaSuccess) return bfail(b, IGA_ECUDA, std::string("persistent batch step: ") + cudaGetErrorString(e));
   for (int c = 0; c < kPersistPhases; ++c) ps->phase_ms[c] = 1e-6 * (double)pns[c];
   ps->have_phases = !err;
+  for (int v = 0; v < kPersistVariants && !err; ++v) {
+    if (!timed[v]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, tu.ev[2 * v], tu.ev[2 * v + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (tu.ms[v] < 0.0 || ms < tu.ms[v]) tu.ms[v] = ms;
+  }
+  if (tu.chosen < 0 && tu.force < 0) {  // every variant sampled twice: keep the faster
+    bool done = true;
+    for (int v = 0; v < ps->nvariants; ++v) done = done && tu.samples[v] >= 2 && tu.ms[v] >= 0.0;
+    if (done) {
+      tu.chosen = 0;
+      for (int v = 1; v < ps->nvariants; ++v)
+        if (tu.ms[v] < tu.ms[tu.chosen]) tu.chosen = v;
+    }
+  }
   if (err) {  // a barrier wait ran out: the step's results are not to be used; start the words afresh
     cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), b->s0);
     cudaMemsetAsync(B.err, 0, sizeof(int), b->s0);
@@ -462,6 +522,8 @@ void iga_batch_destroy(iga_batch* b) {
   if (b->s0) cudaStreamSynchronize(b->s0);
   drop_batch_graph(b);
   free_persist(b->ps);
+  for (auto e : b->tune.ev)
+    if (e) cudaEventDestroy(e);
   for (auto e : b->join)
     if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -481,6 +543,23 @@ int iga_batch_set_persistent(iga_batch* b, int on) {
     free_persist(b->ps);
     b->ps = nullptr;
   }
+  return IGA_OK;
+}
+
+int iga_batch_set_persistent_variant(iga_batch* b, int variant) {
+  if (!b) return IGA_EINVAL;
+  b->err.clear();
+  if (variant < -1 || variant >= kPersistVariants) return bfail(b, IGA_EINVAL, "variant must be -1, 0 or 1");
+  b->tune.force = variant;
+  return IGA_OK;
+}
+
+int iga_batch_persistent_variant(iga_batch* b, int* variant, double* ms) {
+  if (!b) return IGA_EINVAL;
+  b->err.clear();
+  if (variant) *variant = b->tune.force >= 0 ? b->tune.force : b->tune.chosen;
+  if (ms)
+    for (int v = 0; v < kPersistVariants; ++v) ms[v] = b->tune.ms[v];
   return IGA_OK;
 }
 

@@ -381,7 +381,10 @@ constexpr int kPersistPhases = 8;     // predictor, K product, PCG scalars, prec
 int batch_row_tiles(long long N);
 int batch_line_tiles(long long N, int n);
 size_t batch_smem_bytes(int nmax, int pmax, int k, bool f32, bool fd);
-cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid);
+// variant 0: three blocks per SM, two slots per band pass; 1: two blocks per SM, four slots
+// (k <= 2); both give bitwise the same results
+constexpr int kPersistVariants = 2;
+cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int variant, int* grid);
 
 cudaError_t launch_probe_gen(cudaStream_t s, long long N, const int* n, const int* p, int first, int ncol, int nvec,
                              double* x, long long vs);

@@ -132,11 +132,11 @@ __device__ void ph_predict(const PBatch& B) {
 
 // y[j] = A x[j] for the patch's active systems (mask act), one row per thread; with
 // dot, the per-tile partials of x[j].y[j] (dot = 1) or y[j].y[j] (dot = 2) into part.
-// Two slots per pass: both slots' coefficients and x values are loaded before their
-// multiply-adds (twice the loads in flight; the phase is bound by the FP64 units once
-// enough loads are in flight); the terms are added in slot order, the upper term before
-// the lower one, as in the single-patch band product.
-template <int K>
+// SLOTS slots per pass: their coefficients and x values are all loaded before their
+// multiply-adds (SLOTS times the loads in flight; the phase is bound by the FP64 units
+// once enough loads are in flight); the terms are added in slot order, the upper term
+// before the lower one, as in the single-patch band product, whatever SLOTS is.
+template <int K, int SLOTS>
 __device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, double* const* ys, int dot,
                         double* part) {
   for (int it = blockIdx.x; it < B.nrt; it += gridDim.x) {
@@ -168,11 +168,11 @@ __device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, do
       i1 = (int)(t % n1);
       i2 = (int)(t / n1);
     }
-    for (int h = 1; h < H; h += 2) {
-      bool up[2], dn[2];
-      double au[2], ad[2], xu[2][K], xd[2][K];
+    for (int h = 1; h < H; h += SLOTS) {
+      bool up[SLOTS], dn[SLOTS];
+      double au[SLOTS], ad[SLOTS], xu[SLOTS][K], xd[SLOTS][K];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < SLOTS; ++u) {
         const int hh = h + u;
         up[u] = dn[u] = false;
         long long jp = 0, jm = 0;
@@ -194,9 +194,12 @@ __device__ void ph_band(const PBatch& B, bool stiff, const double* const* xs, do
           xd[u][v] = dn[u] && (on >> v & 1) ? x[v * N + jm] : 0.0;
         }
       }
-      if (!__any_sync(0xffffffffu, up[0] || dn[0] || up[1] || dn[1])) continue;
+      bool any = false;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < SLOTS; ++u) any = any || up[u] || dn[u];
+      if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+      for (int u = 0; u < SLOTS; ++u) {
         if (up[u]) {
 #pragma unroll
           for (int v = 0; v < K; ++v)
@@ -737,8 +740,8 @@ __device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first, unsig
   return true;
 }
 
-template <int K, typename T>
-__global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
+template <int K, typename T, int SLOTS, int MINB>
+__global__ void __launch_bounds__(kPThreads, MINB) k_batch_step(const PBatch B) {
   extern __shared__ __align__(16) unsigned char psmem[];
   unsigned long long clk = (B.ptime && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ULL;
 #define IGA_PSYNC(cat)                                         \
@@ -749,7 +752,7 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
   ph_predict<K>(B);
   IGA_PSYNC(kPhPredict);
   // b = K (-Y) into r (x0 = 0: r = b), partials of b.b
-  ph_band<K>(B, true, B.Yp, B.rp, 2, B.part);
+  ph_band<K, SLOTS>(B, true, B.Yp, B.rp, 2, B.part);
   IGA_PSYNC(kPhKProduct);
   if (blockIdx.x == 0) lead_start(B);
   IGA_PSYNC(kPhScalars);
@@ -759,7 +762,7 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
     ph_dir<K>(B, first);
     first = false;
     IGA_PSYNC(kPhDirection);
-    ph_band<K>(B, false, B.pp, B.qp, 1, B.part);  // q = M p, partials of p.q
+    ph_band<K, SLOTS>(B, false, B.pp, B.qp, 1, B.part);  // q = M p, partials of p.q
     IGA_PSYNC(kPhMProduct);
     if (blockIdx.x == 0) lead_alpha(B);
     IGA_PSYNC(kPhScalars);
@@ -776,9 +779,9 @@ __global__ void __launch_bounds__(kPThreads, 3) k_batch_step(const PBatch B) {
   pmark(B, kPhUpdate, clk);  // block 0's own end
 }
 
-template <int K, typename T>
+template <int K, typename T, int SLOTS, int MINB>
 cudaError_t batch_go(cudaStream_t s, const PBatch& B, size_t smem, int sms, int* grid_out) {
-  auto kern = k_batch_step<K, T>;
+  auto kern = k_batch_step<K, T, SLOTS, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per = 0;
@@ -809,22 +812,29 @@ size_t batch_smem_bytes(int nmax, int pmax, int k, bool f32, bool fd) {
   return (size_t)nmax * (2 * (pmax + 1) + (size_t)k * kPLS) * (f32 ? sizeof(float) : sizeof(double)) + 64;
 }
 
-cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int* grid) {
+cudaError_t launch_batch_step(cudaStream_t s, const PBatch& B, bool f32, size_t smem, int variant, int* grid) {
   int dev = 0, sms = 0, coop = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e != cudaSuccess) return e;
   if (!coop) return cudaErrorNotSupported;
-#define IGA_BG(KK) return f32 ? batch_go<KK, float>(s, B, smem, sms, grid) : batch_go<KK, double>(s, B, smem, sms, grid)
+  // variant 0: three blocks per SM (80 registers), two slots per band pass; variant 1: two
+  // blocks per SM (128 registers), four slots per band pass (k <= 2; else as variant 0)
+#define IGA_BGV(KK, S, M) \
+  return f32 ? batch_go<KK, float, S, M>(s, B, smem, sms, grid) : batch_go<KK, double, S, M>(s, B, smem, sms, grid)
   switch (B.k) {
-    case 1: IGA_BG(1);
-    case 2: IGA_BG(2);
-    case 3: IGA_BG(3);
-    case 4: IGA_BG(4);
+    case 1:
+      if (variant == 1) IGA_BGV(1, 4, 2);
+      IGA_BGV(1, 2, 3);
+    case 2:
+      if (variant == 1) IGA_BGV(2, 4, 2);
+      IGA_BGV(2, 2, 3);
+    case 3: IGA_BGV(3, 2, 3);
+    case 4: IGA_BGV(4, 2, 3);
     default: return cudaErrorInvalidValue;
   }
-#undef IGA_BG
+#undef IGA_BGV
 }
 
 }  // namespace iga

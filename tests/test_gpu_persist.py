@@ -12,6 +12,8 @@ operators; band-Cholesky Kronecker or BF16 fast-diagonalisation preconditioner).
   * the BF16 fast diagonalisation (flexible PCG) at tol 1e-10: within 1e-8 of the oracle
     and of the patches stepped alone with the tensor-core BF16 preconditioner;
   * a second persistent run equals the first bit for bit (fixed-order reductions);
+  * the launch variants (three blocks per SM and two slots per band pass, or two blocks and
+    four slots) give bitwise the same states, and the automatic choice times both;
   * the phase clock (iga_batch_phase_times): the products and the preconditioner are timed,
     the times add up to no more than the call, and a batch without a persistent step has none;
   * refusals: a form the persistent step does not compute gives IGA_EINVAL and the batch
@@ -217,6 +219,43 @@ def test_persistent_batch_bf16_fast_diagonalisation():
             e_a = _rel(batched[i][row], alone[row])
             print("  %s: vs oracle %.3e, vs alone %.3e" % (var, e_o, e_a))
             assert e_o <= 1e-8 and e_a <= 1e-8, (i, var, e_o, e_a)
+    b.close()
+    for g in pats:
+        g.close()
+
+
+def test_persistent_variants_agree_bitwise_and_are_timed():
+    ws = _small_patches()
+    k, rho, nsteps = 2, 0.5, 4
+    pats, states, inits = _setup(ws, "banded", 1e-12)
+    dts = [0.5 * g.cfl(rho, iters=60)[1] for g in pats]
+    b = iga.Batch(pats)
+    b.set_persistent(True)
+    runs = []
+    for v in (0, 1):
+        b.set_persistent_variant(v)
+        for g, st, (u0, v0) in zip(pats, states, inits):
+            g.state_init(k, u0, v0, st)
+        stats = b.step(states, k, rho, dts, nsteps)
+        assert stats[0].launches == nsteps
+        assert b.persistent_variant()[0] == v
+        runs.append([s.cpu().numpy() for s in states])
+    for i in range(len(pats)):
+        assert np.array_equal(runs[0][i], runs[1][i]), i
+    # the automatic choice: each variant timed twice over the first single steps
+    b.set_persistent_variant(-1)
+    for g, st, (u0, v0) in zip(pats, states, inits):
+        g.state_init(k, u0, v0, st)
+    for _ in range(4):
+        b.step(states, k, rho, dts, 1)
+    v, ms = b.persistent_variant()
+    print("persistent variants: chosen %d, fastest step %.3f / %.3f ms" % (v, ms[0], ms[1]))
+    assert v in (0, 1) and ms[0] > 0.0 and ms[1] > 0.0 and ms[v] == min(ms)
+    for i, st in enumerate(states):  # the steps taken while timing are the same steps
+        assert np.array_equal(st.cpu().numpy(), runs[0][i]), i
+    with pytest.raises(iga.IgaError) as e:
+        b.set_persistent_variant(2)
+    assert e.value.status == iga.EINVAL
     b.close()
     for g in pats:
         g.close()
