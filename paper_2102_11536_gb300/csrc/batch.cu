@@ -191,22 +191,24 @@ int build_persist(iga_batch* b, double* const* states, int k, double rho, const 
     P.sc = handle_coefs(h, k, rho, dt[i]);
     for (int a = 0; a < 3; ++a) {
       P.lam[a] = h->dd[a].lam32;
-      P.Ub[a][0] = P.Ub[a][1] = nullptr;
+      P.Ubf[a][0] = P.Ubf[a][1] = nullptr;
       if (!fd) continue;
-      // U_a (column c = eigenvector c of the parametric mass matrix) and U_a^T, rounded to BF16
-      const int n = h->tab[a].n;
+      // U_a (column c = eigenvector c of the parametric mass matrix) and U_a^T in BF16, each as
+      // the image the mode products copy into shared memory: ceil16(n) rows of ceil16(n) +
+      // kPersistFdPad entries, zero beyond n
+      const int n = h->tab[a].n, n16 = (n + 15) & ~15, ld = n16 + kPersistFdPad;
       const std::vector<double>& ev = h->tab[a].evec;
-      std::vector<float> mu((size_t)n * n), mt((size_t)n * n);
+      std::vector<__nv_bfloat16> mu((size_t)n16 * ld, __float2bfloat16(0.0f)), mt((size_t)n16 * ld, __float2bfloat16(0.0f));
       for (int r = 0; r < n; ++r)
         for (int c = 0; c < n; ++c) {
-          mu[(size_t)r * n + c] = __bfloat162float(__float2bfloat16((float)ev[(size_t)r * n + c]));
-          mt[(size_t)r * n + c] = __bfloat162float(__float2bfloat16((float)ev[(size_t)c * n + r]));
+          mu[(size_t)r * ld + c] = __float2bfloat16((float)ev[(size_t)r * n + c]);
+          mt[(size_t)r * ld + c] = __float2bfloat16((float)ev[(size_t)c * n + r]);
         }
-      float *du = nullptr, *dt_ = nullptr;
+      __nv_bfloat16 *du = nullptr, *dt_ = nullptr;
       CKB(pupload(b, ps, &du, mu));
       CKB(pupload(b, ps, &dt_, mt));
-      P.Ub[a][0] = du;
-      P.Ub[a][1] = dt_;
+      P.Ubf[a][0] = du;
+      P.Ubf[a][1] = dt_;
     }
     rt0[i] = (int)rtile.size();
     nrt[i] = batch_row_tiles(h->N);

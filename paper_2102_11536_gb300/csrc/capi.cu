@@ -662,8 +662,8 @@ int solve_iter_a(iga_handle* h, int nvec, double* x) {
     LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
     LK(launch_cg_alpha(s, nvec, pA, kRedBlocks, c));
   }
-  LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB));
-  LK(launch_cg_check(s, nvec, pB, c, h->opt.tol * h->opt.tol));
+  // the convergence test runs in the update's last block
+  LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB, 1, h->opt.tol * h->opt.tol));
   return IGA_OK;
 }
 
@@ -678,22 +678,33 @@ int solve_iter_b(iga_handle* h, int nvec) {
   const bool flexible = h->opt.precond != IGA_PREC_FP64 && h->opt.precond != IGA_PREC_BANDED;
   const bool fused = h->opt.precond == IGA_PREC_BANDED || h->opt.precond == IGA_PREC_BANDED32;
   int nrz = 0;
+  const double* rzA = pA;  // r.z partials, [nvec][nrzp], and r.z_old for the flexible beta
+  const double* rzB = pC;
+  int nrzp = kRedBlocks;
   if (fused) {  // r.z and r.z_old come with the preconditioner's last pass
     CKS(apply_Pinv(h, nvec, c.active, h->r, h->z, h->rz_part, &nrz));
     if (nrz <= 0) return fail(h, IGA_ECUDA, "fused inner products missing");
-    LK(launch_cg_beta(s, nvec, h->rz_part, h->rz_part + (size_t)nvec * nrz, nrz, c, flexible ? 1 : 0));
+    rzA = h->rz_part;
+    rzB = h->rz_part + (size_t)nvec * nrz;
+    nrzp = nrz;
   } else {
     if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
     CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
     LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-    LK(launch_cg_beta(s, nvec, pA, pC, kRedBlocks, c, flexible ? 1 : 0));
   }
-  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // p = z + beta p and its split for the next product, one launch
+  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
+    // beta, p = z + beta p and its split for the next product, one launch (the fused r.z
+    // partials are laid out [2][nvec][nrz], as BetaArgs reads them)
     float2* xs = h->df_xs + h->df_slack;
-    cudaError_t e = launch_df_update_split(s, N, c.active, nvec, h->p, h->z, c.beta, N, xs, h->band_Np, h->df_E,
-                                           h->df_part, h->df_bar, h->dflag + 2, h->bar_limit);
+    cudaError_t e = cudaErrorNotSupported;
+    if (fused) {
+      const BetaArgs ba{rzA, nrzp, flexible ? 1 : 0, c};
+      e = launch_df_update_split(s, N, c.active, nvec, h->p, h->z, ba, N, xs, h->band_Np, h->df_E, h->df_part,
+                                 h->df_bar, h->dflag + 2, h->bar_limit);
+    }
     if (e == cudaErrorNotSupported) {
       cudaGetLastError();
+      LK(launch_cg_beta(s, nvec, rzA, rzB, nrzp, c, flexible ? 1 : 0));
       LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
       e = launch_df_split(s, N, c.active, nvec, h->p, N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar,
                           h->dflag + 2, h->bar_limit);
@@ -701,6 +712,7 @@ int solve_iter_b(iga_handle* h, int nvec) {
     LK(e);
     return IGA_OK;
   }
+  LK(launch_cg_beta(s, nvec, rzA, rzB, nrzp, c, flexible ? 1 : 0));
   LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
   return IGA_OK;
 }
@@ -1211,6 +1223,8 @@ int create_handle(int dim, const int* degree, const int* nknots, const double* c
     CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
     CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
     CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
+    CKS(dalloc(h, &h->cs.ticket, 1));
+    CK(cudaMemset(h->cs.ticket, 0, sizeof(unsigned int)));
     CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
     // diag(M): D = (B_0^2)^T (B_1^2)^T (B_2^2)^T W (transposed passes with squared tables)
     CKS(ensure_op_ws(h, 1));
@@ -1335,7 +1349,7 @@ void iga_destroy(iga_handle* h) {
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
   dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
-  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive);
+  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive); dfree(h->cs.ticket);
   if (h->h_nactive) cudaFreeHost(h->h_nactive);
   for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
@@ -1701,6 +1715,8 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
     CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
     CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
     CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
+    CKS(dalloc(h, &h->cs.ticket, 1));
+    CK(cudaMemset(h->cs.ticket, 0, sizeof(unsigned int)));
     CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
     CK(cudaStreamSynchronize(h->stream));
     return IGA_OK;

@@ -187,7 +187,42 @@ struct CgScalars {  // device arrays, one entry per system
   int* iters;
   int* status;     // 0 ok, IGA_ENUMERIC on breakdown
   int* nactive;    // single counter
+  unsigned int* ticket;  // arrival counter of the x, r update (its last block tests convergence); 0 between launches
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// out[v] = sum of partial[v][0..np) for v < nvec, by the whole block (blockDim.x a
+// multiple of 32 with at least nvec warps): each vector gets blockDim.x / 32 / nvec
+// warps, which sum fixed strided shares (lane stride 32), then their warp sums are added
+// in order -- a fixed order, so the result is reproducible. The partials are read from
+// L2 (they may come from other blocks of the same launch).
+__device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out, int np) {
+  __shared__ double wsum[32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = (int)(blockDim.x >> 5), per = nw / nvec;  // warps per vector
+  const int v = w / per, q = w - v * per;
+  if (v < nvec) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int b = q * 32 + lane; b < np; b += per * 32) s += __ldcg(&partial[(long long)v * np + b]);
+    s = warp_sum(s);
+    if (lane == 0) wsum[w] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int i = 0; i < per; ++i) s += wsum[threadIdx.x * per + i];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+#endif
 // Reduction epilogues of PCG (one thread per system, tiny kernels).
 // partials [nvec][np]
 cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int np, CgScalars c);
@@ -197,9 +232,11 @@ cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, cons
 cudaError_t launch_cg_init(cudaStream_t s, int nvec, const double* partial_bb, const double* partial_rr,
                            CgScalars c, double tol2);
 cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, int np, CgScalars c);
-// x += alpha p; r -= alpha q; partial ||r||^2
+// x += alpha p; r -= alpha q; partial ||r||^2; with check != 0 the launch's last block also
+// runs the convergence test (launch_cg_check's work) on those partials
 cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
-                                const double* p, const double* q, long long vs, double* partial);
+                                const double* p, const double* q, long long vs, double* partial, int check,
+                                double tol2);
 // p = z + beta p
 cudaError_t launch_cg_update_p(cudaStream_t s, long long N, int nvec, CgScalars c, double* p, const double* z,
                                long long vs);
@@ -293,10 +330,19 @@ cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const dou
 cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int nvec, const double* x, long long vs,
                             float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err,
                             long long bar_limit = -1);
+// The PCG beta of the direction update: rzp == nullptr: c.beta as computed; else every
+// block computes it from the preconditioner's per-block partials rzp[0][v][nrz] (r.z) and,
+// flexible, rzp[1][v][nrz] (r with the previous z), as launch_cg_beta does, and block 0
+// stores beta and r.z into c after the launch's grid barrier (launch_cg_beta's work).
+struct BetaArgs {
+  const double* rzp;
+  int nrz, flexible;
+  CgScalars c;
+};
 // p = z + beta p (active systems, the PCG direction update) and the split of the new p in
 // one cooperative launch; cudaErrorNotSupported without cooperative launch (nothing done)
 cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
-                                   const double* z, const double* beta, long long vs, float2* xs, long long Np,
+                                   const double* z, const BetaArgs& ba, long long vs, float2* xs, long long Np,
                                    int* Ex, unsigned long long* part, unsigned int* bar, int* err,
                                    long long bar_limit = -1);
 // y = A x from the split copies (xs, Ex from launch_df_split; EA the band's exponent);
@@ -334,6 +380,7 @@ cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* r
 // Persistent batch step (kernels_persist.cu): one cooperative launch advances every
 // patch of a batch by one time step with FP64 band operators and the band-Cholesky
 // Kronecker preconditioner (FP32 or FP64). Device tables, built by the host.
+constexpr int kPersistFdPad = 8;  // BF16 entries added to each staged row of the persistent mode products
 struct PPatch {
   long long N;
   int n[3], deg[3], H;
@@ -342,8 +389,10 @@ struct PPatch {
   const int* o12;               // [H] packed offsets along directions 1, 2
   const double* scale;          // [N] D^-1/2 Dhat^1/2
   const void *L[3], *dinv[3];   // band Cholesky factors per axis ([n][p+1], [n]), FP32 or FP64
-  const float* Ub[3][2];        // fast diagonalisation: U_a (0) and U_a^T (1) rounded to BF16, as FP32,
-                                // row-major [n][n] (Mat(i, j) at i n + j, i the output)
+  const void* Ubf[3][2];        // fast diagonalisation: U_a (0) and U_a^T (1) in BF16, row-major, rows of
+                                // ceil16(n) + kPersistFdPad entries, ceil16(n) rows, zero beyond n
+                                // (Mat(i, j) at i (ceil16(n) + kPersistFdPad) + j, i the output): the
+                                // shared-memory image the mode products copy
   const float* lam[3];          // 1 / Lambda_a, FP32
   double* X;                    // state [3k][N] (the caller's)
   double *Y, *T, *r, *x, *z, *p, *q;  // [k][N] work vectors

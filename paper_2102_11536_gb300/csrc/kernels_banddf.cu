@@ -153,8 +153,9 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
 // The two passes of a vector split in one cooperative launch (two blocks per SM; four
 // entries per thread and pass with their loads issued together):
 // block maxima, a grid barrier, then every block reduces the maxima and splits its
-// grid-stride share. With z (and beta), the first pass also forms the PCG direction
-// x = z + beta x (active systems; the same operation as k_cg_update_p) before taking
+// grid-stride share. With z, the first pass also forms the PCG direction x = z + beta x
+// (active systems; the same operation as k_cg_update_p; beta given, or computed by every
+// block from the r.z partials, BetaArgs) before taking
 // the maxima, and the second pass splits what the same thread wrote. bar[0] counts
 // arrivals, bar[1] is the barrier's generation; the wait is bounded by `limit` polls of
 // at least 64 ns (err = 1 if it runs out; the results are then not to be used). Every
@@ -163,11 +164,27 @@ constexpr long long kBarLimit = 1LL << 22;  // default poll limit (about 0.3 s o
 
 __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, const int* __restrict__ active,
                                                        double* __restrict__ x, const double* __restrict__ z,
-                                                       const double* __restrict__ beta, long long vs,
+                                                       const BetaArgs ba, long long vs,
                                                        unsigned long long* __restrict__ part,
                                                        float2* __restrict__ xs, long long xvs, int* __restrict__ Eout,
                                                        unsigned int* bar, int* err, long long limit) {
   const int G = gridDim.x;
+  // beta per system: from c, or computed here by every block from the r.z partials
+  __shared__ double sbeta[kMaxVec], srz[kMaxVec], srz2[kMaxVec];
+  if (z) {
+    if (ba.rzp) {
+      reduce_partials(nvec, ba.rzp, srz, ba.nrz);
+      if (ba.flexible) reduce_partials(nvec, ba.rzp + (long long)nvec * ba.nrz, srz2, ba.nrz);
+      const int v = threadIdx.x;
+      if (v < nvec) {
+        sbeta[v] = 0.0;
+        if (!active || active[v]) sbeta[v] = (ba.flexible ? srz[v] - srz2[v] : srz[v]) / ba.c.rz[v];
+      }
+    } else if ((int)threadIdx.x < nvec) {
+      sbeta[threadIdx.x] = ba.c.beta[threadIdx.x];
+    }
+    __syncthreads();
+  }
   const long long stride = (long long)G * blockDim.x;
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int U = 4;  // entries per thread and pass, their loads issued together
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
     if (!active || active[v]) {
       double* xv = x + v * vs;
       if (z) {
-        const double b = beta[v];
+        const double b = sbeta[v];
         const double* zv = z + v * vs;
         for (long long i = i0; i < n; i += U * stride) {
           double xa[U], za[U];
@@ -231,6 +248,11 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
     __threadfence();
   }
   __syncthreads();
+  // every block has read c.rz (above): block 0 records beta and the new r.z
+  if (z && ba.rzp && blockIdx.x == 0 && (int)threadIdx.x < nvec && (!active || active[threadIdx.x])) {
+    ba.c.beta[threadIdx.x] = sbeta[threadIdx.x];
+    ba.c.rz[threadIdx.x] = srz[threadIdx.x];
+  }
   for (int v = 0; v < nvec; ++v) {
     if (active && !active[v]) continue;  // uniform over the block
     unsigned long long m = 0;
@@ -1385,7 +1407,7 @@ namespace {
 // the cooperative split (z: with the direction update x = z + beta x first); returns
 // cudaErrorNotSupported when the device has no cooperative launch
 cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nvec, double* x, const double* z,
-                          const double* beta, long long vs, float2* xs, long long Np, int* Ex,
+                          const BetaArgs& ba, long long vs, float2* xs, long long Np, int* Ex,
                           unsigned long long* part, unsigned int* bar, int* err, long long limit) {
   static int nsm[64] = {0};
   int dev = 0;
@@ -1412,7 +1434,7 @@ cudaError_t df_split_coop(cudaStream_t s, long long N, const int* active, int nv
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (limit < 0) limit = kBarLimit;
-  return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, z, beta, vs, part, xs, Np, Ex, bar, err,
+  return cudaLaunchKernelEx(&cfg, k_df_split_coop, N, nvec, active, x, z, ba, vs, part, xs, Np, Ex, bar, err,
                             limit);
 }
 }  // namespace
@@ -1421,8 +1443,8 @@ cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int 
                             float2* xs, long long Np, int* Ex, unsigned long long* part, unsigned int* bar, int* err,
                             long long bar_limit) {
   if (bar && err) {  // one cooperative launch, two blocks per SM
-    const cudaError_t e = df_split_coop(s, N, active, nvec, const_cast<double*>(x), nullptr, nullptr, vs, xs, Np,
-                                        Ex, part, bar, err, bar_limit);
+    const cudaError_t e = df_split_coop(s, N, active, nvec, const_cast<double*>(x), nullptr, BetaArgs{}, vs, xs,
+                                        Np, Ex, part, bar, err, bar_limit);
     if (e != cudaErrorNotSupported) return e;
   }
   k_df_absmax<<<dim3(kDfBlocks, nvec), 256, 0, s>>>(N, active, x, vs, part);
@@ -1432,10 +1454,10 @@ cudaError_t launch_df_split(cudaStream_t s, long long N, const int* active, int 
 }
 
 cudaError_t launch_df_update_split(cudaStream_t s, long long N, const int* active, int nvec, double* p,
-                                   const double* z, const double* beta, long long vs, float2* xs, long long Np,
+                                   const double* z, const BetaArgs& ba, long long vs, float2* xs, long long Np,
                                    int* Ex, unsigned long long* part, unsigned int* bar, int* err,
                                    long long bar_limit) {
-  return df_split_coop(s, N, active, nvec, p, z, beta, vs, xs, Np, Ex, part, bar, err, bar_limit);
+  return df_split_coop(s, N, active, nvec, p, z, ba, vs, xs, Np, Ex, part, bar, err, bar_limit);
 }
 
 cudaError_t launch_band_df(cudaStream_t s, long long N, int nruns, const int4* runs, const int* n, int p0, int p2,

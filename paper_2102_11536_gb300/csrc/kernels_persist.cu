@@ -502,15 +502,32 @@ __device__ void ph_axis(const PBatch& B, int a, unsigned char* smem) {
 // stage 1: t1 -> t2 (axis 1, U^T); stage 2: t2 -> t1 (axis 2, U^T) times 1 / Lambda
 // stage 3: t1 -> t2 (axis 2, U); stage 4: t2 -> t1 (axis 1, U)
 // stage 5: t1 -> z (axis 0, U) times D^-1/2 Dhat^1/2, with the partials of r.z (new, old).
-// Mat is staged transposed (row j holds Mat(., j), rows padded to nP = 4 ceil(n / 4)), the
-// inputs of every active system as in the axis phase. Thread (warp w, lane l): line l,
-// outputs i0 .. i0 + 3 for i0 = 4 w, 4 w + 32, ...; per input index j one broadcast
-// 16-byte read of Mat^T(j, i0 .. i0 + 3) and one staged entry per system, four
-// multiply-adds per system, summed over j in order.
+// On the tensor cores by warp-level BF16 MMA (m16n8k16, FP32 accumulation): the block's
+// product is out (n x 32K) = Mat (n x n) . in (n x 32K), 32K = 32 lines per active-or-not
+// system. Shared memory holds Mat as BF16 rows sA[i][j] (copied from its padded image in
+// HBM by 16-byte loads) and the inputs as BF16 rows per line sB[line][j], both padded
+// with zeros to multiples of 16 and with a row stride of ceil16(n) + 8 elements
+// (fragment loads free of bank conflicts), then per line the
+// element of entry 0 and (stage 2) 1 / (Lambda_0 Lambda_1). Warp w takes the 16 x 8
+// output tiles w, w + 8, ...; fragments are read with 4-byte loads.
+constexpr int kFdPad = kPersistFdPad;  // BF16 elements added to each staged row
+
+__host__ __device__ __forceinline__ int fd_round16(int n) { return (n + 15) & ~15; }
+
+__device__ __forceinline__ void mma_bf16_16x8x16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                                 unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 template <int K>
 __device__ void ph_fd(const PBatch& B, int stage, unsigned char* smem) {
   const int a = stage < 3 ? stage : 5 - stage;
   const int tr = stage < 3 ? 1 : 0;
+  constexpr int NL = 32 * K;  // staged lines: 32 per system
   for (int it = blockIdx.x; it < B.nlt[a]; it += gridDim.x) {
     const int2 tl = B.ltile[a][it];
     const int act = patch_active<K>(B, tl.x);
@@ -523,87 +540,99 @@ __device__ void ph_fd(const PBatch& B, int stage, unsigned char* smem) {
     }
     const PPatch& Pp = B.pt[tl.x];
     const LineTile t = line_tile(Pp, a, tl.y);
-    const int n = t.n, nP = (n + 3) & ~3;
+    const int n = t.n, n16 = fd_round16(n), ld = n16 + kFdPad;
     const long long N = t.N;
-    float* sM = reinterpret_cast<float*>(smem);
-    float* sb = sM + (size_t)n * nP;
-    const float* MT = Pp.Ub[a][1 - tr];  // Mat(i, j) = MT[j n + i]
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem);
+    __nv_bfloat16* sB = sA + (size_t)n16 * ld;
+    long long* sbase = reinterpret_cast<long long*>(sB + (size_t)NL * ld);
+    float* slam = reinterpret_cast<float*>(sbase + kPLines);
+    const uint4* Mat = static_cast<const uint4*>(Pp.Ubf[a][tr]);  // the shared-memory image of sA
     // stages 1, 3, 5 read t1 and 2, 4 read t2; stages 1, 3 write t2 and 0, 2, 4 write t1
     const float* tin = (stage == 2 || stage == 4) ? static_cast<const float*>(Pp.t2) : static_cast<const float*>(Pp.t1);
     float* tout = (stage == 1 || stage == 3) ? static_cast<float*>(Pp.t2) : static_cast<float*>(Pp.t1);
     __syncthreads();  // the previous item's shared data is consumed
-    for (int e = threadIdx.x; e < n * nP; e += kPThreads) {
-      const int j = e / nP, i = e - j * nP;
-      sM[e] = i < n ? MT[(size_t)j * n + i] : 0.0f;
+    {  // Mat: 16-byte copies of its padded image (n16 ld BF16 = a multiple of 16 bytes)
+      uint4* dA = reinterpret_cast<uint4*>(sA);
+      const int nq = n16 * ld * (int)sizeof(__nv_bfloat16) / 16;
+      for (int e = threadIdx.x; e < nq; e += kPThreads) dA[e] = Mat[e];
+    }
+    for (int e = threadIdx.x; e < NL * (n16 - n); e += kPThreads) {  // the padding entries j >= n
+      const int l = e / (n16 - n), j = n + (e - l * (n16 - n));
+      sB[(size_t)l * ld + j] = __float2bfloat16(0.0f);
+    }
+    if (threadIdx.x < kPLines) {  // per line: the element of entry 0, 1 / (Lambda_0 Lambda_1)
+      const int l = threadIdx.x;
+      const long long rr = t.l0 + l;
+      long long g0 = 0;
+      float lam = 1.0f;
+      if (l < t.nl) {
+        if (a == 0) {
+          g0 = rr * n;
+        } else {
+          const long long y = rr / t.A;
+          g0 = (rr - y * t.A) + t.A * (long long)n * y;
+        }
+        if (stage == 2) lam = Pp.lam[0][(int)(rr % Pp.n[0])] * Pp.lam[1][(int)(rr / Pp.n[0])];
+      }
+      sbase[l] = g0;
+      slam[l] = lam;
     }
 #pragma unroll
     for (int v = 0; v < K; ++v) {
       if (!(act >> v & 1)) continue;
-      float* sv = sb + (size_t)v * n * kPLS;
+      __nv_bfloat16* sv = sB + (size_t)v * kPLines * ld;
       const double* rv = Pp.r + v * N;
       const float* iv = tin + v * N;
       if (stage == 0)
         tile_walk(t, [&](int k, int l, long long g) {
-          sv[k * kPLS + l] = __bfloat162float(__float2bfloat16((float)(rv[g] * Pp.scale[g])));
+          sv[(size_t)l * ld + k] = __float2bfloat16((float)(rv[g] * Pp.scale[g]));
         });
       else
-        tile_walk(t, [&](int k, int l, long long g) {
-          sv[k * kPLS + l] = __bfloat162float(__float2bfloat16(iv[g]));
-        });
+        tile_walk(t, [&](int k, int l, long long g) { sv[(size_t)l * ld + k] = __float2bfloat16(iv[g]); });
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
     double snew[K], sold[K];
 #pragma unroll
     for (int v = 0; v < K; ++v) snew[v] = sold[v] = 0.0;
-    if (lane < t.nl) {
-      // 1 / Lambda of the line's two other indices (stage 2: along axis 2, the line is (i0, i1))
-      float lam01 = 1.0f;
-      if (stage == 2) {
-        const long long xx = t.l0 + lane;
-        lam01 = Pp.lam[0][(int)(xx % Pp.n[0])] * Pp.lam[1][(int)(xx / Pp.n[0])];
+    const int mt = n16 / 16, ntiles = mt * (NL / 8);
+    for (int tile = w; tile < ntiles; tile += kPThreads / 32) {
+      const int i0 = (tile % mt) * 16, c0 = (tile / mt) * 8;  // output rows i0.., lines c0..
+      const int v = c0 / kPLines;
+      if (!(act >> v & 1)) continue;  // warp-uniform
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const __nv_bfloat16* ar0 = sA + (size_t)(i0 + gid) * ld + 2 * tig;
+      const __nv_bfloat16* ar1 = ar0 + 8 * ld;
+      const __nv_bfloat16* br = sB + (size_t)(c0 + gid) * ld + 2 * tig;
+      for (int k0 = 0; k0 < n16; k0 += 16) {
+        const unsigned a0 = *reinterpret_cast<const unsigned*>(ar0 + k0);
+        const unsigned a1 = *reinterpret_cast<const unsigned*>(ar1 + k0);
+        const unsigned a2 = *reinterpret_cast<const unsigned*>(ar0 + k0 + 8);
+        const unsigned a3 = *reinterpret_cast<const unsigned*>(ar1 + k0 + 8);
+        const unsigned b0 = *reinterpret_cast<const unsigned*>(br + k0);
+        const unsigned b1 = *reinterpret_cast<const unsigned*>(br + k0 + 8);
+        mma_bf16_16x8x16(acc, a0, a1, a2, a3, b0, b1);
       }
-      const long long gl = a == 0 ? (t.l0 + lane) * n : t.base;  // element of entry 0 of the line
-      const long long ga = a == 0 ? 1 : t.A;                      // element stride along the line
-      for (int i0 = 4 * w; i0 < n; i0 += 4 * (kPThreads / 32)) {
-        float acc[K][4];
+      // acc[q]: output row i0 + gid (+ 8 for q >= 2), line c0 + 2 tig (+ 1 for odd q)
 #pragma unroll
-        for (int v = 0; v < K; ++v)
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + gid + (q >= 2 ? 8 : 0);
+        const int l = (c0 + 2 * tig + (q & 1)) - v * kPLines;
+        if (i >= n || l >= t.nl) continue;
+        const long long g = sbase[l] + (a == 0 ? 1LL : t.A) * i;
+        if (stage == 5) {
+          const double zn = (double)acc[q] * Pp.scale[g];
+          const double rg = Pp.r[v * N + g];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[v][q] = 0.0f;
-        const float* mj = sM + i0;
-        const float* uj = sb + lane;
-        for (int j = 0; j < n; ++j) {
-          const float4 m = *reinterpret_cast<const float4*>(mj + (size_t)j * nP);
-#pragma unroll
-          for (int v = 0; v < K; ++v) {
-            if (!(act >> v & 1)) continue;
-            const float u = uj[((size_t)v * n + j) * kPLS];
-            acc[v][0] = fmaf(m.x, u, acc[v][0]);
-            acc[v][1] = fmaf(m.y, u, acc[v][1]);
-            acc[v][2] = fmaf(m.z, u, acc[v][2]);
-            acc[v][3] = fmaf(m.w, u, acc[v][3]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + q;
-          if (i >= n) break;
-          const long long g = gl + ga * i;
-          const float li = stage == 2 ? lam01 * Pp.lam[2][i] : 1.0f;
-#pragma unroll
-          for (int v = 0; v < K; ++v) {
-            if (!(act >> v & 1)) continue;
-            if (stage == 5) {
-              const double zn = (double)acc[v][q] * Pp.scale[g];
-              const double rg = Pp.r[v * N + g];
-              sold[v] = fma(rg, Pp.z[v * N + g], sold[v]);
-              snew[v] = fma(rg, zn, snew[v]);
-              Pp.z[v * N + g] = zn;
-            } else {
-              tout[v * N + g] = stage == 2 ? acc[v][q] * li : acc[v][q];
+          for (int u = 0; u < K; ++u)
+            if (u == v) {
+              sold[u] = fma(rg, Pp.z[v * N + g], sold[u]);
+              snew[u] = fma(rg, zn, snew[u]);
             }
-          }
+          Pp.z[v * N + g] = zn;
+        } else {
+          tout[v * N + g] = stage == 2 ? acc[q] * (slam[l] * Pp.lam[2][i]) : acc[q];
         }
       }
     }
@@ -808,7 +837,9 @@ cudaError_t batch_go(cudaStream_t s, const PBatch& B, size_t smem, int sms, int*
 int batch_row_tiles(long long N) { return (int)((N + kPRows - 1) / kPRows); }
 int batch_line_tiles(long long N, int n) { return (int)((N / n + kPLines - 1) / kPLines); }
 size_t batch_smem_bytes(int nmax, int pmax, int k, bool f32, bool fd) {
-  if (fd) return ((size_t)nmax * ((nmax + 3) & ~3) + (size_t)k * nmax * kPLS) * sizeof(float) + 64;
+  if (fd)  // Mat and the lines as BF16 rows, then the per-line bases and 1 / Lambda
+    return ((size_t)fd_round16(nmax) + 32 * (size_t)k) * (fd_round16(nmax) + kFdPad) * sizeof(__nv_bfloat16) +
+           kPLines * (sizeof(long long) + sizeof(float)) + 64;
   return (size_t)nmax * (2 * (pmax + 1) + (size_t)k * kPLS) * (f32 ? sizeof(float) : sizeof(double)) + 64;
 }
 

@@ -5,12 +5,6 @@
 
 namespace iga {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // block of 256 threads -> one value (valid in thread 0)
 __device__ __forceinline__ double block_sum256(double v) {
   __shared__ double sh[8];
@@ -45,38 +39,11 @@ cudaError_t launch_dot(cudaStream_t s, long long N, int nvec, const double* a, c
   return cudaGetLastError();
 }
 
-// Warp w of a 256-thread block sums vector w's np partials (layout [v][np]; lane
-// stride 32, then a shuffle tree): a fixed order, so the result is reproducible, and
-// 32 lanes instead of one serial FP64 chain.
-// out[v] = sum of partial[v][0..np) for v < nvec, by the whole block (blockDim.x a
-// multiple of 32 with at least nvec warps): each vector gets blockDim.x / 32 / nvec
-// warps, which sum fixed strided shares, then their warp sums are added in order.
-__device__ __forceinline__ void reduce_partials(int nvec, const double* partial, double* out, int np = kRedBlocks) {
-  __shared__ double wsum[32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = (int)(blockDim.x >> 5), per = nw / nvec;  // warps per vector
-  const int v = w / per, q = w - v * per;
-  if (v < nvec) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int b = q * 32 + lane; b < np; b += per * 32) s += partial[(long long)v * np + b];
-    s = warp_sum(s);
-    if (lane == 0) wsum[w] = s;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < nvec) {
-    double s = 0.0;
-    for (int i = 0; i < per; ++i) s += wsum[threadIdx.x * per + i];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
 constexpr int kEpiThreads = 32 * kMaxVec;
 
 __global__ void __launch_bounds__(kEpiThreads) k_reduce(int nvec, const double* partial, double* result) {
   __shared__ double sa[kMaxVec];
-  reduce_partials(nvec, partial, sa);
+  reduce_partials(nvec, partial, sa, kRedBlocks);
   const int v = threadIdx.x;
   if (v < nvec) result[v] = sa[v];
 }
@@ -90,8 +57,8 @@ cudaError_t launch_reduce(cudaStream_t s, int nvec, const double* partial, doubl
 __global__ void __launch_bounds__(kEpiThreads) k_cg_init(int nvec, const double* pbb, const double* prr, CgScalars c,
                                                          double tol2) {
   __shared__ double sb[kMaxVec], sr[kMaxVec];
-  reduce_partials(nvec, pbb, sb);
-  reduce_partials(nvec, prr, sr);
+  reduce_partials(nvec, pbb, sb, kRedBlocks);
+  reduce_partials(nvec, prr, sr, kRedBlocks);
   const int v = threadIdx.x;
   if (v < nvec) {
     const double bb = sb[v], rr = sr[v];
@@ -161,10 +128,11 @@ cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int
   return cudaGetLastError();
 }
 
-// After x/r update: count the iteration, test ||r||^2 <= tol^2 ||b||^2.
-__global__ void __launch_bounds__(kEpiThreads) k_cg_check(int nvec, const double* prr, CgScalars c, double tol2) {
+// After x/r update: count the iteration, test ||r||^2 <= tol^2 ||b||^2 (by one block of
+// kEpiThreads threads: a kernel of its own, or the last block of the x, r update).
+__device__ void cg_check_block(int nvec, const double* prr, CgScalars c, double tol2) {
   __shared__ double sr[kMaxVec];
-  reduce_partials(nvec, prr, sr);
+  reduce_partials(nvec, prr, sr, kRedBlocks);
   const int v = threadIdx.x;
   if (v < nvec && c.active[v]) {
     const double rr = sr[v];
@@ -183,6 +151,10 @@ __global__ void __launch_bounds__(kEpiThreads) k_cg_check(int nvec, const double
     for (int i = 0; i < nvec; ++i) na += c.active[i];
     *c.nactive = na;
   }
+}
+
+__global__ void __launch_bounds__(kEpiThreads) k_cg_check(int nvec, const double* prr, CgScalars c, double tol2) {
+  cg_check_block(nvec, prr, c, tol2);
 }
 
 cudaError_t launch_cg_check(cudaStream_t s, int nvec, const double* partial, CgScalars c, double tol2) {
@@ -212,10 +184,12 @@ cudaError_t launch_cg_beta(cudaStream_t s, int nvec, const double* partial, cons
   return cudaGetLastError();
 }
 
+// x += alpha p, r -= alpha q (active systems), per-block partials of r.r; with check, the
+// last block to finish (arrival counter c.ticket) runs the convergence test on them.
 __global__ void __launch_bounds__(256) k_cg_update_xr(long long N, CgScalars c, double* __restrict__ x,
                                                       double* __restrict__ r, const double* __restrict__ p,
                                                       const double* __restrict__ q, long long vs,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial, int check, double tol2) {
   const int v = blockIdx.y;
   const double a = c.alpha[v];
   const bool act = c.active[v] != 0;
@@ -232,11 +206,24 @@ __global__ void __launch_bounds__(256) k_cg_update_xr(long long N, CgScalars c, 
   }
   s = block_sum256(s);
   if (threadIdx.x == 0) partial[v * kRedBlocks + blockIdx.x] = s;
+  if (!check) return;
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // the partial is visible before the arrival
+    last = atomicAdd(c.ticket, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  cg_check_block((int)gridDim.y, partial, c, tol2);
+  if (threadIdx.x == 0) atomicExch(c.ticket, 0u);  // ready for the next launch
 }
 
 cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
-                                const double* p, const double* q, long long vs, double* partial) {
-  k_cg_update_xr<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, c, x, r, p, q, vs, partial);
+                                const double* p, const double* q, long long vs, double* partial, int check,
+                                double tol2) {
+  static_assert(kEpiThreads == 256, "the fused convergence test runs in a 256-thread block");
+  k_cg_update_xr<<<dim3(kRedBlocks, nvec), 256, 0, s>>>(N, c, x, r, p, q, vs, partial, check, tol2);
   return cudaGetLastError();
 }
 
