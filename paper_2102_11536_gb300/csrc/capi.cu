@@ -1223,8 +1223,9 @@ int create_handle(int dim, const int* degree, const int* nknots, const double* c
     CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
     CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
     CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
-    CKS(dalloc(h, &h->cs.ticket, 1));
-    CK(cudaMemset(h->cs.ticket, 0, sizeof(unsigned int)));
+    CKS(dalloc(h, &h->cs.ticket, 2));
+    CK(cudaMemset(h->cs.ticket, 0, 2 * sizeof(unsigned int)));
+    CKS(dalloc(h, &h->cs.red, (size_t)kMaxVec * 64));
     CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
     // diag(M): D = (B_0^2)^T (B_1^2)^T (B_2^2)^T W (transposed passes with squared tables)
     CKS(ensure_op_ws(h, 1));
@@ -1349,7 +1350,7 @@ void iga_destroy(iga_handle* h) {
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
   dfree(h->cs.bb); dfree(h->cs.rz); dfree(h->cs.rr); dfree(h->cs.rr0); dfree(h->cs.alpha); dfree(h->cs.beta);
-  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive); dfree(h->cs.ticket);
+  dfree(h->cs.active); dfree(h->cs.iters); dfree(h->cs.status); dfree(h->cs.nactive); dfree(h->cs.ticket); dfree(h->cs.red);
   if (h->h_nactive) cudaFreeHost(h->h_nactive);
   for (auto& pr : h->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
@@ -1715,8 +1716,9 @@ int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, con
     CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
     CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
     CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
-    CKS(dalloc(h, &h->cs.ticket, 1));
-    CK(cudaMemset(h->cs.ticket, 0, sizeof(unsigned int)));
+    CKS(dalloc(h, &h->cs.ticket, 2));
+    CK(cudaMemset(h->cs.ticket, 0, 2 * sizeof(unsigned int)));
+    CKS(dalloc(h, &h->cs.red, (size_t)kMaxVec * 64));
     CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
     CK(cudaStreamSynchronize(h->stream));
     return IGA_OK;

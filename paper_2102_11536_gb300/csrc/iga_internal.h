@@ -187,7 +187,9 @@ struct CgScalars {  // device arrays, one entry per system
   int* iters;
   int* status;     // 0 ok, IGA_ENUMERIC on breakdown
   int* nactive;    // single counter
-  unsigned int* ticket;  // arrival counter of the x, r update (its last block tests convergence); 0 between launches
+  unsigned int* ticket;  // [2] arrival counters: the x, r update (its last block tests convergence) and
+                         // the alpha reduction (its last block sets alpha); 0 between launches
+  double* red;           // [kMaxVec][64] chunk sums of the alpha reduction
 };
 
 #ifdef __CUDACC__

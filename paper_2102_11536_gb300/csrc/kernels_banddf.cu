@@ -150,7 +150,7 @@ __global__ void k_df_split(long long n, int G, const int* __restrict__ active, c
     out[i] = df_split_entry(x[v * vs + i], E, sc);
 }
 
-// The two passes of a vector split in one cooperative launch (two blocks per SM; four
+// The two passes of a vector split in one cooperative launch (two blocks per SM; eight
 // entries per thread and pass with their loads issued together):
 // block maxima, a grid barrier, then every block reduces the maxima and splits its
 // grid-stride share. With z, the first pass also forms the PCG direction x = z + beta x
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_df_split_coop(long long n, int nvec, co
   }
   const long long stride = (long long)G * blockDim.x;
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  constexpr int U = 4;  // entries per thread and pass, their loads issued together
+  constexpr int U = 8;  // entries per thread and pass, their loads issued together
   for (int v = 0; v < nvec; ++v) {
     unsigned long long m = 0;
     if (!active || active[v]) {

@@ -101,30 +101,47 @@ cudaError_t launch_cg_start(cudaStream_t s, int nvec, const double* partial_rz, 
 }
 
 // alpha = r.z / p.q; breakdown (p.q <= 0 or not finite) stops the system with IGA_ENUMERIC.
-// p.q comes from the band product's per-block partials (N / 128 of them per vector), so
-// this reduction takes a block of 32 warps.
-constexpr int kEpiWide = 1024;
-__global__ void __launch_bounds__(kEpiWide) k_cg_alpha(int nvec, const double* ppq, int np, CgScalars c) {
-  __shared__ double sq[kMaxVec];
-  reduce_partials(nvec, ppq, sq, np);
-  const int v = threadIdx.x;
-  if (v >= nvec) return;
-  if (!c.active[v]) {
-    c.alpha[v] = 0.0;
-    return;
+// p.q comes from the band product's per-block partials (N / 128 of them per vector): block
+// (b, v) sums the b-th of kAlphaBlocks contiguous chunks of vector v's partials (a fixed
+// strided share per thread, then the block tree), and the last block to finish (arrival
+// counter c.ticket[1]) adds the chunks' sums in chunk order and sets alpha.
+constexpr int kAlphaBlocks = 64;
+__global__ void __launch_bounds__(256) k_cg_alpha(int nvec, const double* ppq, int np, CgScalars c) {
+  const int v = blockIdx.y, b = blockIdx.x;
+  const int chunk = (np + kAlphaBlocks - 1) / kAlphaBlocks;
+  const int lo = b * chunk, hi = min(np, lo + chunk);
+  double s = 0.0;
+#pragma unroll 4
+  for (int i = lo + threadIdx.x; i < hi; i += 256) s += __ldcg(&ppq[(long long)v * np + i]);
+  s = block_sum256(s);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    c.red[v * kAlphaBlocks + b] = s;
+    __threadfence();
+    last = atomicAdd(&c.ticket[1], 1u) == gridDim.x * gridDim.y - 1;
   }
-  const double pq = sq[v];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    c.status[v] = IGA_ENUMERIC;
-    c.active[v] = 0;
-    c.alpha[v] = 0.0;
-    return;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int u = threadIdx.x;
+  if (u < nvec) {
+    double pq = 0.0;
+    for (int q = 0; q < kAlphaBlocks; ++q) pq += __ldcg(&c.red[u * kAlphaBlocks + q]);
+    if (!c.active[u]) {
+      c.alpha[u] = 0.0;
+    } else if (!(pq > 0.0) || !isfinite(pq)) {
+      c.status[u] = IGA_ENUMERIC;
+      c.active[u] = 0;
+      c.alpha[u] = 0.0;
+    } else {
+      c.alpha[u] = c.rz[u] / pq;
+    }
   }
-  c.alpha[v] = c.rz[v] / pq;
+  if (threadIdx.x == 0) atomicExch(&c.ticket[1], 0u);  // ready for the next launch
 }
 
 cudaError_t launch_cg_alpha(cudaStream_t s, int nvec, const double* partial, int np, CgScalars c) {
-  k_cg_alpha<<<1, kEpiWide, 0, s>>>(nvec, partial, np, c);
+  k_cg_alpha<<<dim3(kAlphaBlocks, nvec), 256, 0, s>>>(nvec, partial, np, c);
   return cudaGetLastError();
 }
 
@@ -210,13 +227,13 @@ __global__ void __launch_bounds__(256) k_cg_update_xr(long long N, CgScalars c, 
   __shared__ bool last;
   if (threadIdx.x == 0) {
     __threadfence();  // the partial is visible before the arrival
-    last = atomicAdd(c.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    last = atomicAdd(&c.ticket[0], 1u) == gridDim.x * gridDim.y - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   cg_check_block((int)gridDim.y, partial, c, tol2);
-  if (threadIdx.x == 0) atomicExch(c.ticket, 0u);  // ready for the next launch
+  if (threadIdx.x == 0) atomicExch(&c.ticket[0], 0u);  // ready for the next launch
 }
 
 cudaError_t launch_cg_update_xr(cudaStream_t s, long long N, int nvec, CgScalars c, double* x, double* r,
