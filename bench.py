@@ -46,6 +46,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -495,8 +496,11 @@ def timed_steps(patch, iga, torch, state, w, dt, nsteps, warmup, stream, flush):
 
 
 def run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts):
-    """The 64^3 p = 3 k = 2 configuration with the headline form and the two FP64 forms,
-    each from the same initial state; errors of U and V against the fp64_paper run."""
+    """The 64^3 p = 3 k = 2 configuration with the headline form, the two FP64 forms and
+    the tensor-core BF16 / FP16 mode-product preconditioners (the configuration's
+    comparison), each from the same initial state; errors of U and V against the fp64_paper
+    run. Then the FP64 and headline forms at the configuration's other rho_inf values (0, 1),
+    each with its own critical step."""
     import numpy as np
     w = workloads.config(args.secondary)
     w.rho = args.rho
@@ -510,8 +514,10 @@ def run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts):
     state = torch.empty(3 * w.k * g.N, dtype=torch.float64, device=dev)
     cfgs, out, finals = {}, {}, {}
     forms = [("fp64_paper", dict(op_form="matrix_free", precond="fp64", guess="zero")),
-             ("fp64_banded", dict(op_form="assembled", precond="banded", guess="zero"))]
-    if head not in ("fp64_paper", "fp64_banded"):
+             ("fp64_banded", dict(op_form="assembled", precond="banded", guess="zero")),
+             ("mixed_bf16", dict(op_form="assembled", precond="bf16", guess="zero")),
+             ("mixed_fp16", dict(op_form="assembled", precond="fp16", guess="zero"))]
+    if head not in [f for f, _ in forms]:
         forms.append((head, hopts))
     for name, opts in forms:
         select_form(g, opts, cfgs, w.k)
@@ -526,9 +532,31 @@ def run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts):
     for name in out:
         out[name]["rel_err_vs_fp64_paper"] = {
             v: float(np.linalg.norm(finals[name][r] - ref[r]) / np.linalg.norm(ref[r])) for r, v in ((0, "U"), (1, "V"))}
+    # the other rho_inf values of the configuration: the FP64 band form and the headline form
+    by_rho = {}
+    for rho in (0.0, 1.0):
+        lam_r, tc_r = g.cfl(rho, iters=args.cfl_iters)
+        dt_r = w.cfl_fraction * tc_r
+        wr = copy.copy(w)
+        wr.rho = rho
+        res, fin = {}, {}
+        for name, opts in [("fp64_banded", dict(op_form="assembled", precond="banded", guess="zero")), (head, hopts)]:
+            if name in res:
+                continue
+            select_form(g, opts, cfgs, w.k)
+            g.set_graphs(opts.get("graphs", True) and not args.no_graphs)
+            g.state_init(w.k, u0, v0, state)
+            ms, st = timed_steps(g, iga, torch, state, wr, dt_r, args.steps, args.warmup, stream, flush)
+            fin[name] = state.view(3 * w.k, g.N)[:2].cpu().numpy()
+            res[name] = {"value": args.steps / (ms / 1e3), "unit": "steps/s", "pcg_iters_per_solve": st.iters / max(st.solves, 1)}
+        for name in res:
+            res[name]["rel_err_vs_fp64_banded"] = {
+                v: float(np.linalg.norm(fin[name][r] - fin["fp64_banded"][r]) / np.linalg.norm(fin["fp64_banded"][r]))
+                for r, v in ((0, "U"), (1, "V"))}
+        by_rho["%g" % rho] = {"dt": dt_r, "forms": res}
     g.close()
     return {"workload": workload_desc(w), "ndof": w.ndof, "dt": dt, "lambda_max": lam, "steps": args.steps,
-            "forms": out}
+            "forms": out, "other_rho_inf": by_rho}
 
 
 def run_learned(args, iga, torch, workloads, dev, stream, flush):
