@@ -155,6 +155,8 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
+    ap.add_argument("--error-steps", type=int, default=10,
+                    help="steps of the headline form's per-step error trace against the FP64 form (0 = skip)")
     ap.add_argument("--multipatch-steps", type=int, default=20,
                     help="timed steps of the conforming multi-patch system (2 x 2 x 2 glued patches, additive "
                          "Schwarz preconditioner; 0 = skip)")
@@ -1008,6 +1010,28 @@ def run_ours(args):
                 "headline_speedup": results[head]["value"] / results[n]["value"]}
             for n in ("fp64_paper", "fp64_banded", "fp64_assembled") if n in results}
 
+    # the headline form's error per step against the FP64 form (the paper's method) from the same
+    # initial state: both stepped by the host-driven loop (the same kernels), one step at a time
+    err_trace = None
+    if "fp64_paper" in results and head != "fp64_paper" and args.error_steps > 0:
+        ref_opts = results["fp64_paper"]["options"]
+        st_ref = torch.empty_like(state)
+        patch.set_graphs(False)
+        select_form(patch, ref_opts, band_cfgs, k)
+        patch.state_init(k, u0, v0, st_ref)
+        select_form(patch, hopts, band_cfgs, k)
+        patch.state_init(k, u0, v0, state)
+        err_trace = []
+        for n in range(args.error_steps):
+            select_form(patch, ref_opts, band_cfgs, k)
+            patch.step(st_ref, k, w.rho, dt, 1)
+            select_form(patch, hopts, band_cfgs, k)
+            patch.step(state, k, w.rho, dt, 1)
+            a, b = state.view(3 * k, N), st_ref.view(3 * k, N)
+            err_trace.append({"step": n + 1, **{v: float(torch.linalg.norm(a[r] - b[r]) / torch.linalg.norm(b[r]))
+                                                for r, v in ((0, "U"), (1, "V"))}})
+        del st_ref
+
     # end to end through the public C API on host memory, headline form: every step
     # copies the state in from pinned host memory and the new state back out.
     select_form(patch, hopts, band_cfgs, k)
@@ -1079,6 +1103,7 @@ def run_ours(args):
         "pcg_iters_per_solve": h["pcg_iters_per_solve"],
         "dof_updates_per_s": h["value"] * N,
         "rel_err_vs_fp64_paper": h.get("rel_err_vs_fp64_paper"),
+        "error_per_step_vs_fp64_paper": err_trace,
         "fp64": fp64,
         "gpu_launches": h["gpu_launches"],
         "roofline": h["roofline"],
