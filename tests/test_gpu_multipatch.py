@@ -3,8 +3,8 @@ additive Schwarz preconditioner, Sec. 5.4) with the multi-patch oracle on the sa
 layouts: three deformed quadratic patches in a row (N_adj = 2), an L of three patches (a
 re-entrant corner), a 2 x 2 grid of cubic patches (N_adj = 4) and a 2 x 2 x 2 grid of
 quadratic patches (N_adj = 8); every operator form, PCG, the critical step, the time
-steps (initial data and k = 2 steps) from the host loop, the captured step and the
-patches on concurrent streams.
+steps (initial data and k = 2 steps) from the host loop, the captured step, the
+patches on concurrent streams, and the per-patch access, tuning and profiling calls.
 
 Tolerances: FP64 forms as for one patch (operators 1e-12 of max|y| for M and P_ad^{-1},
 1e-11 for K; solves at tol 1e-13 within 1e-10 relative, iteration counts within 1 of the
@@ -168,3 +168,42 @@ def test_captured_and_concurrent_steps_equal_the_host_loop(layout):
             sys_.close()
     for name in ("graph", "concurrent", "graph_concurrent"):
         assert np.array_equal(finals[name], finals["host"]), name
+
+
+def test_per_patch_access_and_tuning(layout):
+    """iga_mp_patch / iga_mp_patch_io against the layout's global ids: the gather copies each
+    box entry's global value (zero where the entry is no degree of freedom), the adds sum
+    the patches' copies in patch order; a lent patch handle has its box's size; the
+    system's autotune and profile calls run through every patch."""
+    patches, _ = layout
+    lay = iga.multipatch_layout(patches)
+    sys_ = iga.MultiPatch(patches, op_form="assembled", precond="fp64")
+    try:
+        N = sys_.N
+        rng = np.random.default_rng(5)
+        x = rng.standard_normal(N)
+        y = torch.zeros(N, dtype=torch.float64, device=DEV)
+        want_y = np.zeros(N)
+        for r in range(len(patches)):
+            gid = np.asarray(lay["gid"][r]).reshape(-1)
+            assert sys_.patch(r).N == gid.size
+            box = torch.full((gid.size,), np.nan, dtype=torch.float64, device=DEV)
+            sys_.patch_gather(r, _t(x), box)
+            want = np.where(gid >= 0, x[np.maximum(gid, 0)], 0.0)
+            assert np.array_equal(_np(box), want), r
+            b = rng.standard_normal(gid.size)
+            sys_.patch_scatter_add(r, _t(b), y)
+            for e in np.nonzero(gid >= 0)[0]:  # the patch's copies, in the order of the patches
+                want_y[gid[e]] += b[e]
+        torch.cuda.synchronize()
+        assert np.array_equal(_np(y), want_y)
+        cfg = sys_.autotune(nvec=2, reps=1)
+        assert len(cfg) == 2 and cfg[0] > 0
+        out = torch.empty_like(y)
+        sys_.profile("band_mass")
+        sys_.apply_M(_t(x), out)
+        ms, launches, _, _ = sys_.profile_read()
+        sys_.profile("off")
+        assert launches >= len(patches) and ms > 0.0
+    finally:
+        sys_.close()
