@@ -126,7 +126,7 @@ NCU_TRAFFIC = {
     ("band_mass", "6428c7f922f0f6eb", "cube64_p3", 2): 373.9e6,   # k_band_spmv<2, 64>
     ("band_mass_df", "089aa6988b2aaa18", "cube64_p3", 2): 390.2e6,  # k_band_df_tm<3, 2>
     # k_band_df_tm<4, 3>, 128 rows per block, strips of 26 lines, one buffer
-    ("band_mass_df", "317f917d7321d430", "cube128_p4", 3): 8.377e9,
+    ("band_mass_df", "c8eb1a52520170d7", "cube128_p4", 3): 8.392e9,
     # k_mid_mass<4>, captured at file hash 618d068dc16a5b19; the file's later edit touched
     # only launch_geometry's host code (k_mid_mass byte-identical), hence the new key
     ("mass", "2b7c940689f4c144", "cube64_p3", 1): 186.69e6,
@@ -155,6 +155,8 @@ def parse_args():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--train-lr", type=float, default=2e-3)
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the 48-patch batch (0 = skip)")
+    ap.add_argument("--batch-patches", type=int, default=0,
+                    help="the first N patches of the batch only (0 = all 48; for small profiling captures)")
     ap.add_argument("--error-steps", type=int, default=10,
                     help="steps of the headline form's per-step error trace against the FP64 form (0 = skip)")
     ap.add_argument("--multipatch-steps", type=int, default=20,
@@ -637,6 +639,8 @@ def run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg):
     maximum over ranks."""
     t0 = time.perf_counter()
     allw = workloads.multipatch_batch()
+    if args.batch_patches > 0:
+        allw = allw[:args.batch_patches]
     k, rho = 2, 0.5
     shards = iga.shard_patches([iga.patch_work(w.ndof, w.p[0]) for w in allw], world)
     ws = [allw[i] for i in shards[rank]]
