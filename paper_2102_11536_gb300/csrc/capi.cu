@@ -1,4 +1,10 @@
-// C ABI of the GB300 explicit generalized-alpha IGA library (include/iga_galpha.h).
+// C ABI of the GB300 explicit generalized-alpha IGA library (include/iga_galpha.h): handle
+// creation and set-up (tables, geometry, diagonal scaling), options, the step-parameter
+// helpers, the time step (predictor, stage right-hand sides, the k PCG solves, update) in the
+// host-driven loop or as a captured CUDA graph with the PCG loop on the device, initial
+// data, fields at the Gauss points, the critical step, profiling and launch tuning. The
+// operators are in operators.cu, PCG in pcg.cu, the learned guess in warmstart.cu, the
+// multi-patch system in multipatch.cu, batches in batch.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -108,9 +114,6 @@ double theta_crit(double rho) { return 12.0 * (1.0 + rho) * (2.0 - rho) / (rho *
 // A captured step graph holds workspace addresses: every workspace reallocation
 // below drops it, and the next step captures again.
 void drop_step_graph(iga_handle* h);
-inline bool is_assembled(const iga_handle* h) {
-  return h->opt.op_form == IGA_OP_ASSEMBLED || h->opt.op_form == IGA_OP_ASSEMBLED_DF;
-}
 
 int ensure_op_ws(iga_handle* h, int nvec) {
   if (h->ws_vec >= nvec) return IGA_OK;
@@ -147,625 +150,6 @@ int ensure_cg_ws(iga_handle* h, int nvec) {
   CKS(dalloc(h, &h->pq_part, (size_t)nvec * (size_t)df_max_blocks(h->N, h->n)));
   CKS(dalloc(h, &h->rz_part, (size_t)2 * nvec * (size_t)(h->N / 32 + 2)));
   h->cg_vec = nvec;
-  return IGA_OK;
-}
-
-// ---------------------------------------------------------------------------
-// operators
-// ---------------------------------------------------------------------------
-// Algorithmic work of the last-axis kernels per vector (FMA = 2 flops):
-// mass: interpolate (p+1 FMA), scale by W (1 mul), integrate (p+1 FMA) per point;
-// stiffness: 3 interpolations, the symmetric 3x3 product (9 mul + 6 add), 3 integrations.
-double mass_last_flops(const iga_handle* h) { return (4.0 * h->dd[h->dim - 1].P + 1.0) * (double)h->Qt; }
-double stiff_last_flops(const iga_handle* h) {
-  const double P = h->dd[h->dim - 1].P;
-  return h->dim == 3 ? (12.0 * P + 15.0) * (double)h->Qt : (8.0 * P + 6.0) * (double)h->Qt;
-}
-// whole mass application: banded passes of every axis, forward and transposed
-double mass_apply_flops(const iga_handle* h) {
-  const int *n = h->n, *Q = h->Q;
-  double f = mass_last_flops(h);
-  if (h->dim == 3) {
-    f += 2 * 2.0 * h->dd[0].P * (double)Q[0] * n[1] * n[2];
-    f += 2 * 2.0 * h->dd[1].P * (double)Q[0] * Q[1] * n[2];
-  } else {
-    f += 2 * 2.0 * h->dd[0].P * (double)Q[0] * n[1];
-  }
-  return f;
-}
-
-int apply_M_mf(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
-  CKS(ensure_op_ws(h, nvec));
-  cudaStream_t s = h->stream;
-  const int *n = h->n, *Q = h->Q;
-  const DirDev* d = h->dd;
-  const int nact = active ? h->cur_active : nvec;
-  cudaEvent_t ea = nullptr, em = nullptr;
-  CKS(prof_begin(h, IGA_PROF_MASS_APPLY, &ea));
-  if (h->dim == 3) {
-    LK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
-    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, nullptr, nullptr, h->st));
-    CKS(prof_begin(h, IGA_PROF_MASS, &em));
-    LK(launch_mid_mass(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->W, h->ta, h->ta, h->st));
-    CKS(prof_end(h, em, nact * mass_last_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->st)));
-    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, nullptr, nullptr, h->st, h->u0, h->su));
-    LK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
-  } else {
-    LK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, nullptr, nullptr, h->su));
-    CKS(prof_begin(h, IGA_PROF_MASS, &em));
-    LK(launch_mid_mass(s, d[1], Q[0], nvec, active, h->W, h->u0, h->u0, h->su));
-    CKS(prof_end(h, em, nact * mass_last_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->su)));
-    LK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, nullptr, nullptr, h->su, y, h->N));
-  }
-  CKS(prof_end(h, ea, nact * mass_apply_flops(h), 8.0 * (h->Qt + 2.0 * nact * h->N)));
-  return IGA_OK;
-}
-
-int apply_K_mf(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
-  CKS(ensure_op_ws(h, nvec));
-  cudaStream_t s = h->stream;
-  const int *n = h->n, *Q = h->Q;
-  const DirDev* d = h->dd;
-  const int nact = active ? h->cur_active : nvec;
-  cudaEvent_t ek = nullptr;
-  if (h->dim == 3) {
-    LK(launch_fwd(s, d[0], {1, n[0], Q[0], (long long)n[1] * n[2]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
-    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u0, h->su, d[1].val, h->ta, d[1].der, h->tb, h->st));
-    LK(launch_fwd(s, d[1], {Q[0], n[1], Q[1], n[2]}, nvec, active, h->u1, h->su, d[1].val, h->tc, nullptr, nullptr, h->st));
-    CKS(prof_begin(h, IGA_PROF_STIFF, &ek));
-    LK(launch_mid_stiff3(s, d[2], (long long)Q[0] * Q[1], nvec, active, h->G, h->gstride, h->ta, h->tb, h->tc, h->st));
-    CKS(prof_end(h, ek, nact * stiff_last_flops(h), 8.0 * (6.0 * h->Qt + 6.0 * nact * h->st)));
-    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->ta, d[1].val, h->tb, d[1].der, h->st, h->u0, h->su));
-    LK(launch_tr(s, d[1], {Q[0], Q[1], n[1], n[2]}, nvec, active, h->tc, d[1].val, nullptr, nullptr, h->st, h->u1, h->su));
-    LK(launch_tr(s, d[0], {1, Q[0], n[0], (long long)n[1] * n[2]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
-  } else {
-    LK(launch_fwd(s, d[0], {1, n[0], Q[0], n[1]}, nvec, active, x, h->N, d[0].val, h->u0, d[0].der, h->u1, h->su));
-    CKS(prof_begin(h, IGA_PROF_STIFF, &ek));
-    LK(launch_mid_stiff2(s, d[1], Q[0], nvec, active, h->G, h->gstride, h->u0, h->u1, h->su));
-    CKS(prof_end(h, ek, nact * stiff_last_flops(h), 8.0 * (3.0 * h->Qt + 4.0 * nact * h->su)));
-    LK(launch_tr(s, d[0], {1, Q[0], n[0], n[1]}, nvec, active, h->u0, d[0].val, h->u1, d[0].der, h->su, y, h->N));
-  }
-  return IGA_OK;
-}
-
-// The preconditioner of Sec. 5.3 by fast diagonalisation with scratch t1, t2
-// (nvec*N doubles each): t = S r (S = D^{-1/2} Dhat^{1/2}), then U^T along each
-// axis, division by Lambda_0(i0) Lambda_1(i1) Lambda_2(i2), U along each axis, S.
-// FP64 form: all in FP64. FP32 form: the scaled residual is rounded to FP32,
-// mode products and Lambda in FP32, final rescale in FP64.
-// rzp (nullable): with the band-Cholesky forms, per-block partials of r.z and r.z_old
-// (z's previous content) come out of the last axis, [2][nvec][*nrz]; *nrz = 0 otherwise.
-int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* t1, double* t2,
-             double* rzp = nullptr, int* nrz = nullptr) {
-  if (nrz) *nrz = 0;
-  cudaStream_t s = h->stream;
-  const int* n = h->n;
-  const DirDev* d = h->dd;
-  const long long N = h->N;
-  const long long n01 = (long long)n[0] * n[1];
-  const long long n12 = (long long)n[1] * n[2];
-  const bool d3 = h->dim == 3;
-  if (h->opt.precond == IGA_PREC_FP64) {
-    FdEpilogue none{}, lam{}, post{};
-    lam.lam[0] = d[0].lam64;
-    lam.lam[1] = d[1].lam64;
-    lam.lam[2] = d3 ? d[2].lam64 : nullptr;
-    lam.n[0] = n[0]; lam.n[1] = n[1]; lam.n[2] = n[2];
-    post.post = h->scale;
-    const double* sc = h->scale;
-    if (d3) {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 1, r, t1, N, sc, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 1, t2, t1, N, nullptr, lam));
-      LK(launch_fd_mode64(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U64, 0, t1, t2, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
-    } else {
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 1, r, t1, N, sc, none));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 1, t1, t2, N, nullptr, lam));
-      LK(launch_fd_mode64(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U64, 0, t2, t1, N, nullptr, none));
-      LK(launch_fd_mode64(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U64, 0, t1, z, N, nullptr, post));
-    }
-    return IGA_OK;
-  }
-  if (h->opt.precond == IGA_PREC_BANDED || h->opt.precond == IGA_PREC_BANDED32) {
-    // (Mhat_1 x Mhat_2 x Mhat_3)^{-1} by band Cholesky along each axis, FP64 or FP32
-    // (FP32 intermediates between the axes)
-    const int f32 = h->opt.precond == IGA_PREC_BANDED32;
-    const void* L[3] = {f32 ? (const void*)d[0].chol32 : d[0].chol, f32 ? (const void*)d[1].chol32 : d[1].chol,
-                        f32 ? (const void*)d[2].chol32 : d[2].chol};
-    const void* Di[3] = {f32 ? (const void*)d[0].cdinv32 : d[0].cdinv, f32 ? (const void*)d[1].cdinv32 : d[1].cdinv,
-                         f32 ? (const void*)d[2].cdinv32 : d[2].cdinv};
-    const int mid = f32 ? 0 : 1;  // intermediates are FP64 only in the FP64 form
-    const double* sc = h->scale;
-    const float* s32 = f32 ? h->scale32 : nullptr;  // the FP32 form scales in FP32
-    if (d3) {
-      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n12}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr, nullptr, nullptr, nullptr, s32));
-      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], n[2]}, nvec, active, f32, L[1], Di[1], t1, mid, t2, mid, N, nullptr, nullptr));
-      LK(launch_kron_axis(s, n[2], d[2].p, {n01, n[2], n[2], 1}, nvec, active, f32, L[2], Di[2], t2, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz, s32));
-    } else {
-      LK(launch_kron_axis(s, n[0], d[0].p, {1, n[0], n[0], n[1]}, nvec, active, f32, L[0], Di[0], r, 1, t1, mid, N, sc, nullptr, nullptr, nullptr, nullptr, s32));
-      LK(launch_kron_axis(s, n[1], d[1].p, {n[0], n[1], n[1], 1}, nvec, active, f32, L[1], Di[1], t1, mid, z, 1, N, nullptr, sc, rzp ? r : nullptr, rzp, nrz, s32));
-    }
-    return IGA_OK;
-  }
-  if (h->opt.precond == IGA_PREC_FP32) {
-    float* f1 = reinterpret_cast<float*>(t1);
-    float* f2 = reinterpret_cast<float*>(t2);
-    const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
-    const double* sc = h->scale;
-    if (d3) {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 1, r, 1, f1, 0, N, sc, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 1, f2, 0, f1, 0, N, nullptr, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[2], {n01, n[2], n[2], 1}, nvec, active, d[2].U32, 0, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], n[2]}, nvec, active, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n12}, nvec, active, d[0].U32, 0, f1, 0, z, 1, N, nullptr, sc, nullptr, n));
-    } else {
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 1, r, 1, f1, 0, N, sc, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 1, f1, 0, f2, 0, N, nullptr, nullptr, lam, n));
-      LK(launch_fd_mode32(s, n[1], {n[0], n[1], n[1], 1}, nvec, active, d[1].U32, 0, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n));
-      LK(launch_fd_mode32(s, n[0], {1, n[0], n[0], n[1]}, nvec, active, d[0].U32, 0, f1, 0, z, 1, N, nullptr, sc, nullptr, n));
-    }
-    return IGA_OK;
-  }
-  if (h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16) {
-    // the same sequence on the tensor cores: 16-bit operands, FP32 accumulation and intermediates
-    const int f16 = h->opt.precond == IGA_PREC_FP16;
-    for (int a = 0; a < h->dim; ++a)
-      if (!d[a].Btc[0])
-        return fail(h, IGA_EINVAL, "tensor-core preconditioner needs at most 256 interior functions per direction");
-    void* const* B[3] = {f16 ? d[0].Btc16 : d[0].Btc, f16 ? d[1].Btc16 : d[1].Btc,
-                         f16 ? d[2].Btc16 : d[2].Btc};
-    float* f1 = reinterpret_cast<float*>(t1);
-    float* f2 = reinterpret_cast<float*>(t2);
-    const float* lam[3] = {d[0].lam32, d[1].lam32, d3 ? d[2].lam32 : nullptr};
-    const double* sc = h->scale;
-    int* err = h->dflag + 1;
-    if (d3) {
-      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n12}, nvec, active, B[0][1], f16, r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], n[2]}, nvec, active, B[1][1], f16, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[2], 2, {n01, n[2], n[2], 1}, nvec, active, B[2][1], f16, f2, 0, f1, 0, N, nullptr, nullptr, lam, n, err));
-      LK(launch_fd_mode_tc(s, n[2], 2, {n01, n[2], n[2], 1}, nvec, active, B[2][0], f16, f1, 0, f2, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], n[2]}, nvec, active, B[1][0], f16, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n12}, nvec, active, B[0][0], f16, f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
-    } else {
-      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n[1]}, nvec, active, B[0][1], f16, r, 1, f1, 0, N, sc, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], 1}, nvec, active, B[1][1], f16, f1, 0, f2, 0, N, nullptr, nullptr, lam, n, err));
-      LK(launch_fd_mode_tc(s, n[1], 1, {n[0], n[1], n[1], 1}, nvec, active, B[1][0], f16, f2, 0, f1, 0, N, nullptr, nullptr, nullptr, n, err));
-      LK(launch_fd_mode_tc(s, n[0], 0, {1, n[0], n[0], n[1]}, nvec, active, B[0][0], f16, f1, 0, z, 1, N, nullptr, sc, nullptr, n, err));
-    }
-    return IGA_OK;
-  }
-  return fail(h, IGA_EINVAL, "preconditioner arithmetic not available in this build");
-}
-
-// The tensor-core kernels set dflag[1], the TMA-staged band product and the cooperative
-// split dflag[2], when an mbarrier or grid-barrier wait runs out.
-int check_tc_error(iga_handle* h) {
-  if (h->mp) {
-    for (size_t r = 0; r < h->mp->patch.size(); ++r) {
-      iga_handle* p = h->mp->patch[r];
-      p->stream = h->stream;
-      const int rc = check_tc_error(p);
-      if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
-    }
-    return IGA_OK;
-  }
-  const bool tc = h->opt.precond == IGA_PREC_BF16 || h->opt.precond == IGA_PREC_FP16;
-  const bool df = h->opt.op_form == IGA_OP_ASSEMBLED_DF;
-  if (!tc && !df) return IGA_OK;
-  int e[2] = {0, 0};
-  CK(cudaMemcpyAsync(e, h->dflag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  if (e[0] || e[1]) {
-    CK(cudaMemsetAsync(h->dflag + 1, 0, 2 * sizeof(int), h->stream));
-    // a grid barrier that ran out may have left its arrival count behind: start afresh
-    if (e[1] && h->df_bar) CK(cudaMemsetAsync(h->df_bar, 0, 2 * sizeof(unsigned int), h->stream));
-    return fail(h, IGA_ECUDA, e[0] ? "tensor-core mode product: mbarrier wait timed out"
-                                   : "double-FP32 band product or split: a bounded wait (mbarrier or grid "
-                                     "barrier) timed out");
-  }
-  return IGA_OK;
-}
-
-// Assembled band rows of M and K by probing the matrix-free operators with the
-// (2p+1)^d colour vectors, 8 colours per application (kernels_band.cu).
-int assemble_band64(iga_handle* h) {
-  if (h->band_ready) return IGA_OK;
-  drop_step_graph(h);  // new addresses
-  cudaStream_t s = h->stream;
-  int p3[3] = {0, 0, 0};
-  for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
-  int S = 1;
-  for (int a = 0; a < 3; ++a) S *= 2 * p3[a] + 1;
-  const int centre = S / 2, H = S - centre;
-  std::vector<long long> off(H);
-  std::vector<int> o12(H);
-  for (int hh = 0; hh < H; ++hh) {
-    const int sl = centre + hh;
-    const int m0 = 2 * p3[0] + 1, m1 = 2 * p3[1] + 1;
-    const int o0 = sl % m0 - p3[0], o1 = (sl / m0) % m1 - p3[1], o2 = sl / (m0 * m1) - p3[2];
-    off[hh] = o0 + (long long)h->n[0] * (o1 + (long long)h->n[1] * o2);
-    o12[hh] = (o1 + 64) | ((o2 + 64) << 8);
-  }
-  CKS(upload(h, &h->band_o12, o12));
-  double nnz = 1.0;
-  for (int a = 0; a < 3; ++a) nnz *= (double)h->n[a] * (2 * p3[a] + 1) - (double)p3[a] * (p3[a] + 1);
-  CKS(upload(h, &h->band_off, off));
-  CKS(dalloc(h, &h->Mband, (size_t)H * h->N));
-  CKS(dalloc(h, &h->Kband, (size_t)H * h->N));
-  CK(cudaMemsetAsync(h->Mband, 0, sizeof(double) * H * h->N, s));
-  CK(cudaMemsetAsync(h->Kband, 0, sizeof(double) * H * h->N, s));
-  // Probe vectors in buffers of their own: the assembly may run lazily inside an
-  // operator call whose caller holds pointers into the PCG workspace, so it must
-  // not resize that workspace.
-  constexpr int kBatch = 8;
-  struct ProbeBufs {
-    double* x = nullptr;
-    double* y = nullptr;
-    ~ProbeBufs() {
-      if (x) cudaFree(x);
-      if (y) cudaFree(y);
-    }
-  } pb;
-  CKS(dalloc(h, &pb.x, (size_t)kBatch * h->N));
-  CKS(dalloc(h, &pb.y, (size_t)kBatch * h->N));
-  for (int first = 0; first < S; first += kBatch) {
-    const int nv = std::min(kBatch, S - first);
-    LK(launch_probe_gen(s, h->N, h->n, p3, first, S, nv, pb.x, h->N));
-    CKS(apply_M_mf(h, nv, nullptr, pb.x, pb.y));
-    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, pb.y, h->N, h->Mband));
-    CKS(apply_K_mf(h, nv, nullptr, pb.x, pb.y));
-    LK(launch_probe_extract(s, h->N, h->n, p3, first, S, nv, pb.y, h->N, h->Kband));
-  }
-  CK(cudaStreamSynchronize(s));
-  h->band_H = H;
-  h->band_nnz = nnz;
-  h->band_ready = true;
-  return IGA_OK;
-}
-
-// The double-FP32 copies of the assembled band (kernels_banddf.cu): split once from
-// the FP64 band, which is then released.
-int assemble_band_df(iga_handle* h) {
-  if (h->df_ready) return IGA_OK;
-  CKS(assemble_band64(h));
-  drop_step_graph(h);
-  cudaStream_t s = h->stream;
-  const int H = h->band_H;
-  const long long N = h->N, Np = df_row_stride(N);
-  int p3[3] = {0, 0, 0};
-  for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
-  const std::vector<int> runs = band_df_runs(h->n, p3);
-  CKS(upload(h, &h->band_runs, runs));
-  h->band_nruns = (int)runs.size() / 4;
-  long long maxL = 0;  // reach of a run's staged copies beyond its rows
-  for (size_t q = 0; q < runs.size(); q += 4) maxL = std::max(maxL, (long long)std::abs(runs[q + 3]) + runs[q + 1]);
-  const long long sl = df_slack(maxL);
-  h->df_slack = sl;
-  const size_t nA = (size_t)H * Np + 2 * sl, nX = (size_t)kMaxVec * Np + 2 * sl;
-  CKS(dalloc(h, &h->Mdf, nA));
-  CKS(dalloc(h, &h->Kdf, nA));
-  CKS(dalloc(h, &h->df_xs, nX));
-  CKS(dalloc(h, &h->df_E, (size_t)2 * kMaxVec));
-  CKS(dalloc(h, &h->df_part, (size_t)kMaxVec * kDfBlocks));
-  CKS(dalloc(h, &h->df_bar, 2));
-  CK(cudaMemsetAsync(h->df_bar, 0, 2 * sizeof(unsigned int), s));
-  CK(cudaMemsetAsync(h->Mdf, 0, sizeof(float2) * nA, s));
-  CK(cudaMemsetAsync(h->Kdf, 0, sizeof(float2) * nA, s));
-  CK(cudaMemsetAsync(h->df_xs, 0, sizeof(float2) * nX, s));
-  int* dE = h->df_E + kMaxVec;
-  int EA[2] = {0, 0};
-  LK(launch_df_split_matrix(s, N, H, h->Mband, h->Mdf + sl, Np, h->df_part, dE));
-  CK(cudaMemcpyAsync(&EA[0], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  LK(launch_df_split_matrix(s, N, H, h->Kband, h->Kdf + sl, Np, h->df_part, dE));
-  CK(cudaMemcpyAsync(&EA[1], dE, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  h->EAm = EA[0];
-  h->EAk = EA[1];
-  h->band_Np = Np;
-  df_encode_maps(h->Mdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmM);
-  df_encode_maps(h->Kdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmK);
-  dfree(h->Mband);
-  dfree(h->Kband);
-  h->band_ready = false;
-  h->df_ready = true;
-  return IGA_OK;
-}
-
-// the band rows of the handle's assembled form
-int assemble_band(iga_handle* h) {
-  return h->opt.op_form == IGA_OP_ASSEMBLED_DF ? assemble_band_df(h) : assemble_band64(h);
-}
-
-// one band product y = A x in the handle's assembled form (FP64, or double-FP32 with
-// the split of x first -- unless presplit: the split copy already holds x, as the PCG
-// direction's producers leave it); cls selects the matrix (IGA_PROF_BAND_MASS / _STIFF)
-cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const int* active, const double* x,
-                        double* y, int threads, int nv, double* pq, int* npq, bool presplit = false) {
-  const bool mass = cls == IGA_PROF_BAND_MASS;
-  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
-    float2* xs = h->df_xs + h->df_slack;
-    if (!presplit) {
-      const cudaError_t e = launch_df_split(s, h->N, active, nvec, x, h->N, xs, h->band_Np, h->df_E, h->df_part,
-                                            h->df_bar, h->dflag + 2, h->bar_limit);
-      if (e != cudaSuccess) return e;
-    }
-    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
-                          h->dim == 3 ? h->dd[2].p : 0, h->band_H, (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
-                          xs, h->df_E, x, y, h->N, threads, nv, pq, npq, h->dflag + 2, mass ? &h->tmM : &h->tmK);
-  }
-  return launch_band_spmv(s, h->N, h->band_H, h->band_off, h->band_o12, h->n, mass ? h->Mband : h->Kband, active,
-                          nvec, x, y, h->N, threads, nv, pq, npq);
-}
-
-int apply_band(iga_handle* h, int cls, int nvec, const int* active, const double* x, double* y,
-               double* pq = nullptr, int* npq = nullptr, bool presplit = false) {
-  const int nact = active ? h->cur_active : nvec;
-  cudaEvent_t e = nullptr;
-  CKS(prof_begin(h, cls, &e));
-  LK(launch_band(h, h->stream, cls, nvec, active, x, y, h->band_threads, h->band_nv, pq, npq, presplit));
-  CKS(prof_end(h, e, 2.0 * h->band_nnz * nact, 8.0 * ((double)h->band_H * h->N + 2.0 * nact * h->N)));
-  return IGA_OK;
-}
-
-// y = M x; with pq, the assembled form also leaves per-block partials of x . y in pq
-// ([nvec][*npq]); *npq = 0 when they were not computed (matrix-free form).
-// presplit (double-FP32 form): the split copy of x is already in place
-int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double* x, double* y);
-
-int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
-            int* npq = nullptr, bool presplit = false) {
-  if (npq) *npq = 0;
-  if (h->mp) return mp_apply(h, 0, nvec, active, x, y);
-  if (is_assembled(h)) {
-    CKS(assemble_band(h));
-    return apply_band(h, IGA_PROF_BAND_MASS, nvec, active, x, y, pq, npq,
-                      presplit && h->opt.op_form == IGA_OP_ASSEMBLED_DF);
-  }
-  return apply_M_mf(h, nvec, active, x, y);
-}
-int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y) {
-  if (h->mp) return mp_apply(h, 1, nvec, active, x, y);
-  if (is_assembled(h)) {
-    CKS(assemble_band(h));
-    return apply_band(h, IGA_PROF_BAND_STIFF, nvec, active, x, y);
-  }
-  return apply_K_mf(h, nvec, active, x, y);
-}
-int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* rzp = nullptr,
-               int* nrz = nullptr) {
-  if (h->mp) {
-    if (nrz) *nrz = 0;
-    return mp_apply(h, 2, nvec, active, r, z);
-  }
-  const int nact = active ? h->cur_active : nvec;
-  double modes = 0.0;  // sum_a n_a: one mode product costs 2 n_a flops per entry, done twice
-  for (int a = 0; a < h->dim; ++a) modes += h->n[a];
-  cudaEvent_t e = nullptr;
-  CKS(prof_begin(h, IGA_PROF_PRECOND, &e));
-  CKS(ensure_cg_ws(h, nvec));
-  CKS(fd_apply(h, nvec, active, r, z, h->f1, h->f2, rzp, nrz));
-  CKS(prof_end(h, e, nact * (4.0 * modes + 3.0) * (double)h->N, 8.0 * (2.0 * nact + 1.0) * (double)h->N));
-  return IGA_OK;
-}
-
-// Multi-patch operators (Sec. 5.1, 5.4): the global vectors are gathered into every
-// patch's box (zero where a box entry is no degree of freedom), the patch's own operator
-// acts on its box -- M^(r), K^(r), or the local preconditioner P^(r)^{-1}
-// (def:loc_forms2) -- and the local results are summed into the global vector:
-// which = 0: M = sum_r R^(r)T M^(r) R^(r); 1: K likewise; 2: P_ad^{-1} (def:asp).
-int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double* x, double* y) {
-  MpState& mp = *h->mp;
-  if (nvec > mp.vec_cap) {
-    drop_step_graph(h);
-    CKS(dalloc(h, &mp.xl, (size_t)nvec * mp.nloc));
-    CKS(dalloc(h, &mp.yl, (size_t)nvec * mp.nloc));
-    mp.vec_cap = nvec;
-  }
-  cudaStream_t s = h->stream;
-  // Patches on streams of their own in the host-driven loop only: inside a step capture
-  // (s is the capture or loop-body stream) they run in order on s, because the patch
-  // streams, once joined to the step's capture, cannot also join the loop body's.
-  const bool conc = mp.concurrent && s != h->gs && s != h->gbody;
-  LK(launch_mp_gather(s, mp.maps, nvec, active, x, mp.xl));
-  if (conc) CK(cudaEventRecord(mp.fork, s));
-  for (size_t r = 0; r < mp.patch.size(); ++r) {
-    iga_handle* p = mp.patch[r];
-    p->stream = s;
-    if (conc) {
-      CK(cudaStreamWaitEvent(mp.ps[r], mp.fork, 0));
-      p->stream = mp.ps[r];
-    }
-    p->cur_active = h->cur_active;
-    const long long l0 = p->nlaunch;
-    double* xr = mp.xl + nvec * mp.off[r];
-    double* yr = mp.yl + nvec * mp.off[r];
-    const int rc = which == 0   ? apply_M(p, nvec, active, xr, yr)
-                   : which == 1 ? apply_K(p, nvec, active, xr, yr)
-                                : apply_Pinv(p, nvec, active, xr, yr);
-    h->nlaunch += p->nlaunch - l0;
-    if (rc != IGA_OK) return fail(h, rc, "patch " + std::to_string(r) + ": " + p->err);
-    if (conc) {
-      CK(cudaEventRecord(mp.join[r], mp.ps[r]));
-      CK(cudaStreamWaitEvent(s, mp.join[r], 0));
-      p->stream = s;
-    }
-  }
-  LK(launch_mp_scatter(s, mp.maps, nvec, active, mp.yl, y));
-  return IGA_OK;
-}
-
-// ---------------------------------------------------------------------------
-// batched PCG
-// ---------------------------------------------------------------------------
-// PCG (Sec. 5.5), split into launch-only pieces so that the same kernels serve the
-// host-driven loop and the captured graph (whose loop runs on the device).
-// solve_begin: r = b - M x0 (or x = 0, r = b), ||b||^2, ||r||^2, activity flags.
-int solve_begin(iga_handle* h, int nvec, const double* b, double* x, bool use_x0) {
-  cudaStream_t s = h->stream;
-  const long long N = h->N;
-  CgScalars& c = h->cs;
-  double* pA = h->partial;
-  double* pB = h->partial + kMaxVec * kRedBlocks;
-  const double tol2 = h->opt.tol * h->opt.tol;
-  if (use_x0) {
-    CKS(apply_M(h, nvec, nullptr, x, h->q));
-    LK(launch_sub(s, N, nvec, b, h->q, h->r, N));
-  } else {
-    CK(cudaMemsetAsync(x, 0, sizeof(double) * nvec * N, s));
-    CK(cudaMemcpyAsync(h->r, b, sizeof(double) * nvec * N, cudaMemcpyDeviceToDevice, s));
-  }
-  LK(launch_dot(s, N, nvec, b, b, N, pA));
-  LK(launch_dot(s, N, nvec, h->r, h->r, N, pB));
-  LK(launch_cg_init(s, nvec, pA, pB, c, tol2));
-  return IGA_OK;
-}
-
-// solve_prime: z = P^{-1} r, r.z, p = z (active systems).
-int solve_prime(iga_handle* h, int nvec) {
-  cudaStream_t s = h->stream;
-  const long long N = h->N;
-  CgScalars& c = h->cs;
-  int nrz = 0;
-  CKS(apply_Pinv(h, nvec, c.active, h->r, h->z, h->rz_part, &nrz));
-  if (nrz > 0) {  // r.z came with the preconditioner's last pass
-    LK(launch_cg_start(s, nvec, h->rz_part, nrz, c));
-  } else {
-    LK(launch_dot(s, N, nvec, h->r, h->z, N, h->partial));
-    LK(launch_cg_start(s, nvec, h->partial, kRedBlocks, c));
-  }
-  LK(launch_copy_active(s, N, nvec, c.active, h->z, h->p, N));
-  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {  // the first product's split, made here (see solve_iter_a)
-    CKS(assemble_band(h));
-    LK(launch_df_split(s, N, c.active, nvec, h->p, N, h->df_xs + h->df_slack, h->band_Np, h->df_E, h->df_part,
-                       h->df_bar, h->dflag + 2, h->bar_limit));
-  }
-  return IGA_OK;
-}
-
-// solve_iter_a: q = M p, alpha = r.z / p.q, x += alpha p, r -= alpha q, convergence test.
-int solve_iter_a(iga_handle* h, int nvec, double* x) {
-  cudaStream_t s = h->stream;
-  const long long N = h->N;
-  CgScalars& c = h->cs;
-  double* pA = h->partial;
-  double* pB = h->partial + kMaxVec * kRedBlocks;
-  int npq = 0;
-  // double-FP32 form: p's split copy was made where p was (solve_prime, solve_iter_b)
-  CKS(apply_M(h, nvec, c.active, h->p, h->q, h->pq_part, &npq, true));
-  if (npq > 0) {  // p.q came with the band product
-    LK(launch_cg_alpha(s, nvec, h->pq_part, npq, c));
-  } else {
-    LK(launch_dot(s, N, nvec, h->p, h->q, N, pA));
-    LK(launch_cg_alpha(s, nvec, pA, kRedBlocks, c));
-  }
-  // the convergence test runs in the update's last block
-  LK(launch_cg_update_xr(s, N, nvec, c, x, h->r, h->p, h->q, N, pB, 1, h->opt.tol * h->opt.tol));
-  return IGA_OK;
-}
-
-// solve_iter_b: [flexible: r.z_old] z = P^{-1} r, beta, p = z + beta p.
-int solve_iter_b(iga_handle* h, int nvec) {
-  cudaStream_t s = h->stream;
-  const long long N = h->N;
-  CgScalars& c = h->cs;
-  double* pA = h->partial;
-  double* pC = h->partial + 2 * kMaxVec * kRedBlocks;
-  // the FP64 preconditioners are symmetric and linear to rounding: plain CG
-  const bool flexible = h->opt.precond != IGA_PREC_FP64 && h->opt.precond != IGA_PREC_BANDED;
-  const bool fused = h->opt.precond == IGA_PREC_BANDED || h->opt.precond == IGA_PREC_BANDED32;
-  int nrz = 0;
-  const double* rzA = pA;  // r.z partials, [nvec][nrzp], and r.z_old for the flexible beta
-  const double* rzB = pC;
-  int nrzp = kRedBlocks;
-  if (fused) {  // r.z and r.z_old come with the preconditioner's last pass
-    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z, h->rz_part, &nrz));
-    if (nrz <= 0) return fail(h, IGA_ECUDA, "fused inner products missing");
-    rzA = h->rz_part;
-    rzB = h->rz_part + (size_t)nvec * nrz;
-    nrzp = nrz;
-  } else {
-    if (flexible) LK(launch_dot(s, N, nvec, h->r, h->z, N, pC));  // z still holds the previous z
-    CKS(apply_Pinv(h, nvec, c.active, h->r, h->z));
-    LK(launch_dot(s, N, nvec, h->r, h->z, N, pA));
-  }
-  if (h->opt.op_form == IGA_OP_ASSEMBLED_DF) {
-    // beta, p = z + beta p and its split for the next product, one launch (the fused r.z
-    // partials are laid out [2][nvec][nrz], as BetaArgs reads them)
-    float2* xs = h->df_xs + h->df_slack;
-    cudaError_t e = cudaErrorNotSupported;
-    if (fused) {
-      const BetaArgs ba{rzA, nrzp, flexible ? 1 : 0, c};
-      e = launch_df_update_split(s, N, c.active, nvec, h->p, h->z, ba, N, xs, h->band_Np, h->df_E, h->df_part,
-                                 h->df_bar, h->dflag + 2, h->bar_limit);
-    }
-    if (e == cudaErrorNotSupported) {
-      cudaGetLastError();
-      LK(launch_cg_beta(s, nvec, rzA, rzB, nrzp, c, flexible ? 1 : 0));
-      LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
-      e = launch_df_split(s, N, c.active, nvec, h->p, N, xs, h->band_Np, h->df_E, h->df_part, h->df_bar,
-                          h->dflag + 2, h->bar_limit);
-    }
-    LK(e);
-    return IGA_OK;
-  }
-  LK(launch_cg_beta(s, nvec, rzA, rzB, nrzp, c, flexible ? 1 : 0));
-  LK(launch_cg_update_p(s, N, nvec, c, h->p, h->z, N));
-  return IGA_OK;
-}
-
-int read_nactive(iga_handle* h, int* nact) {
-  CK(cudaMemcpyAsync(h->h_nactive, h->cs.nactive, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  *nact = *h->h_nactive;
-  h->cur_active = *nact;
-  return IGA_OK;
-}
-
-// Host-driven batched PCG: one host synchronisation per iteration to test convergence.
-int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int* iters, double* relres) {
-  CKS(ensure_cg_ws(h, nvec));
-  CKS(ensure_op_ws(h, nvec));
-  cudaStream_t s = h->stream;
-  CgScalars& c = h->cs;
-  CKS(solve_begin(h, nvec, b, x, use_x0));
-  int nact = 0;
-  CKS(read_nactive(h, &nact));
-  if (nact > 0) CKS(solve_prime(h, nvec));
-  int it = 0;
-  while (nact > 0 && it < h->opt.max_iter) {
-    CKS(solve_iter_a(h, nvec, x));
-    CKS(read_nactive(h, &nact));
-    ++it;
-    if (nact == 0) break;
-    CKS(solve_iter_b(h, nvec));
-  }
-  int hit[kMaxVec], hst[kMaxVec];
-  double hrr[kMaxVec], hbb[kMaxVec], hr0[kMaxVec];
-  CK(cudaMemcpyAsync(hr0, c.rr0, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hit, c.iters, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hst, c.status, sizeof(int) * nvec, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hrr, c.rr, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hbb, c.bb, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int status = IGA_OK;
-  for (int v = 0; v < nvec; ++v) {
-    const double rel = hbb[v] > 0 ? std::sqrt(hrr[v] / hbb[v]) : 0.0;
-    h->last_init[v] = hbb[v] > 0 ? std::sqrt(hr0[v] / hbb[v]) : 0.0;
-    if (iters) iters[v] = hit[v];
-    if (relres) relres[v] = rel;
-    if (hst[v] != 0) status = IGA_ENUMERIC;
-  }
-  CKS(check_tc_error(h));
-  if (status != IGA_OK) return fail(h, status, "PCG breakdown (non-positive curvature or non-finite values)");
-  if (nact > 0) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "PCG did not reach tol %.3g in %d iterations", h->opt.tol, h->opt.max_iter);
-    return fail(h, IGA_ENOT_CONVERGED, buf);
-  }
   return IGA_OK;
 }
 
@@ -1593,203 +977,6 @@ int iga_galpha_params(int k, double rho_inf, double* alpha, double* beta, double
   return IGA_OK;
 }
 
-int iga_mp_layout(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
-                  const double* const* ctrl, double tol, int* lo, int* hi, long long* nglob, int* n_adj,
-                  long long* gid, long long gid_len) {
-  std::string msg;
-  const int rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo, hi, nglob, n_adj, gid, gid_len, msg);
-  return rc == IGA_OK ? IGA_OK : fail(nullptr, rc, msg);
-}
-
-int iga_mp_create(int npatch, int dim, const int* degree, const int* nknots, const double* const* knots,
-                  const double* const* ctrl, double tol, const iga_options* opt, iga_handle** out) {
-  g_create_err.clear();
-  if (!out) return fail(nullptr, IGA_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (npatch < 1 || (dim != 2 && dim != 3) || !degree || !nknots || !knots || !ctrl)
-    return fail(nullptr, IGA_EINVAL, "iga_mp_create: npatch >= 1, dim 2 or 3 and non-null arrays required");
-  iga_options o;
-  if (opt) o = *opt;
-  else iga_options_default(&o);
-  if (!(o.tol >= 0.0) || o.max_iter < 1 || o.precond < 0 || o.precond > IGA_PREC_BANDED32 || o.op_form < 0 ||
-      o.op_form > IGA_OP_ASSEMBLED_DF || o.guess < 0 || o.guess > IGA_GUESS_TAYLOR)
-    return fail(nullptr, IGA_EINVAL, "invalid options (the learned guess is not available on a multi-patch handle)");
-  // gluing: boxes first, then the global id of every box entry
-  std::vector<int> lo((size_t)npatch * dim), hi((size_t)npatch * dim);
-  long long nglob = 0;
-  int n_adj = 0;
-  std::string err;
-  int rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo.data(), hi.data(), &nglob, &n_adj, nullptr, 0,
-                     err);
-  if (rc != IGA_OK) return fail(nullptr, rc, err);
-  std::vector<long long> off(npatch), nr(npatch);
-  long long nloc = 0;
-  for (int r = 0; r < npatch; ++r) {
-    long long c = 1;
-    for (int a = 0; a < dim; ++a) c *= hi[(size_t)r * dim + a] - lo[(size_t)r * dim + a] + 1;
-    off[r] = nloc;
-    nr[r] = c;
-    nloc += c;
-  }
-  std::vector<long long> gid((size_t)nloc);
-  rc = mp_layout(npatch, dim, degree, nknots, knots, ctrl, tol, lo.data(), hi.data(), &nglob, &n_adj, gid.data(),
-                 nloc, err);
-  if (rc != IGA_OK) return fail(nullptr, rc, err);
-  if (nglob < 1) return fail(nullptr, IGA_EINVAL, "iga_mp_create: no degrees of freedom");
-  // global -> entries (CSR, entries ascending) and entry -> patch
-  std::vector<long long> crow((size_t)nglob + 1, 0), cent;
-  std::vector<int> epatch((size_t)nloc);
-  for (int r = 0; r < npatch; ++r)
-    for (long long i = 0; i < nr[r]; ++i) epatch[(size_t)(off[r] + i)] = r;
-  for (long long e = 0; e < nloc; ++e)
-    if (gid[(size_t)e] >= 0) ++crow[(size_t)gid[(size_t)e] + 1];
-  for (long long g = 0; g < nglob; ++g) crow[(size_t)g + 1] += crow[(size_t)g];
-  cent.assign((size_t)crow[(size_t)nglob], 0);
-  {
-    std::vector<long long> fill(crow.begin(), crow.end() - 1);
-    for (long long e = 0; e < nloc; ++e)
-      if (gid[(size_t)e] >= 0) cent[(size_t)fill[(size_t)gid[(size_t)e]]++] = e;
-  }
-  iga_handle* h = new (std::nothrow) iga_handle();
-  if (!h) return fail(nullptr, IGA_ENOMEM, "host allocation failed");
-  h->mp = new (std::nothrow) MpState();
-  if (!h->mp) {
-    delete h;
-    return fail(nullptr, IGA_ENOMEM, "host allocation failed");
-  }
-  MpState& mp = *h->mp;
-  h->opt = o;
-  h->dim = dim;
-  h->stream = (cudaStream_t)o.stream;
-  h->N = nglob;
-  h->Qt = 1;
-  // host-driven loop unless iga_set_graphs(h, 1): a captured step reaches the patches through
-  // the stream they are handed on every call, and prepare_capture sizes their workspaces
-  h->use_graphs = false;
-  // the composite runs the PCG of its preconditioner's class: plain CG for the FP64 forms,
-  // flexible CG otherwise; its own operator form is the dispatch through the patches
-  mp.op_form = o.op_form;
-  mp.precond = o.precond;
-  h->opt.op_form = IGA_OP_MATRIX_FREE;
-  h->opt.precond = (o.precond == IGA_PREC_FP64 || o.precond == IGA_PREC_BANDED) ? IGA_PREC_FP64 : IGA_PREC_FP32;
-  mp.off = off;
-  mp.nr = nr;
-  mp.nloc = nloc;
-  mp.n_adj = n_adj;
-  if (cudaSetDevice(o.device) != cudaSuccess) {
-    cudaGetLastError();
-    iga_destroy(h);
-    return fail(nullptr, IGA_ECUDA, "cudaSetDevice failed");
-  }
-  iga_options po = o;
-  po.guess = IGA_GUESS_ZERO;
-  for (int r = 0; r < npatch; ++r) {
-    iga_handle* p = nullptr;
-    rc = create_handle(dim, degree + (size_t)r * dim, nknots + (size_t)r * dim, knots + (size_t)r * dim, ctrl[r],
-                       lo.data() + (size_t)r * dim, hi.data() + (size_t)r * dim, &po, &p);
-    if (rc != IGA_OK) {
-      const std::string msg = "patch " + std::to_string(r) + ": " + g_create_err;
-      iga_destroy(h);
-      return fail(nullptr, rc, msg);
-    }
-    mp.patch.push_back(p);
-  }
-  auto setup = [&]() -> int {
-    CKS(upload(h, &mp.d_gid, gid));
-    CKS(upload(h, &mp.d_off, off));
-    CKS(upload(h, &mp.d_nr, nr));
-    CKS(upload(h, &mp.d_crow, crow));
-    CKS(upload(h, &mp.d_cent, cent));
-    CKS(upload(h, &mp.d_epatch, epatch));
-    mp.maps.nloc = nloc;
-    mp.maps.nglob = nglob;
-    mp.maps.gid = mp.d_gid;
-    mp.maps.epatch = mp.d_epatch;
-    mp.maps.off = mp.d_off;
-    mp.maps.nr = mp.d_nr;
-    mp.maps.crow = mp.d_crow;
-    mp.maps.cent = mp.d_cent;
-    CKS(dalloc(h, &h->dflag, 4));
-    CK(cudaMemsetAsync(h->dflag, 0, sizeof(int) * 4, h->stream));
-    CKS(dalloc(h, &h->partial, (size_t)3 * kMaxVec * kRedBlocks));
-    CKS(dalloc(h, &h->cs.bb, kMaxVec)); CKS(dalloc(h, &h->cs.rz, kMaxVec)); CKS(dalloc(h, &h->cs.rr, kMaxVec)); CKS(dalloc(h, &h->cs.rr0, kMaxVec));
-    CKS(dalloc(h, &h->cs.alpha, kMaxVec)); CKS(dalloc(h, &h->cs.beta, kMaxVec));
-    CKS(dalloc(h, &h->cs.active, kMaxVec)); CKS(dalloc(h, &h->cs.iters, kMaxVec));
-    CKS(dalloc(h, &h->cs.status, kMaxVec)); CKS(dalloc(h, &h->cs.nactive, 1));
-    CKS(dalloc(h, &h->cs.ticket, 2));
-    CK(cudaMemset(h->cs.ticket, 0, 2 * sizeof(unsigned int)));
-    CKS(dalloc(h, &h->cs.red, (size_t)kMaxVec * 64));
-    CK(cudaMallocHost((void**)&h->h_nactive, sizeof(int) * 4));
-    CK(cudaStreamSynchronize(h->stream));
-    return IGA_OK;
-  };
-  rc = setup();
-  if (rc != IGA_OK) {
-    const std::string msg = h->err;
-    iga_destroy(h);
-    return fail(nullptr, rc, msg);
-  }
-  *out = h;
-  return IGA_OK;
-}
-
-int iga_mp_set_concurrent(iga_handle* h, int on) {
-  CKS(check_handle(h));
-  if (!h->mp) return fail(h, IGA_EINVAL, "not a multi-patch handle");
-  MpState& mp = *h->mp;
-  if (on && mp.ps.empty()) {  // all or nothing: the vectors stay empty if a creation fails
-    std::vector<cudaStream_t> ps;
-    std::vector<cudaEvent_t> join;
-    cudaEvent_t fork = nullptr;
-    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    for (size_t r = 0; e == cudaSuccess && r < mp.patch.size(); ++r) {
-      cudaStream_t st = nullptr;
-      cudaEvent_t ev = nullptr;
-      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-      if (e == cudaSuccess) ps.push_back(st);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (e == cudaSuccess) join.push_back(ev);
-    }
-    if (e != cudaSuccess) {
-      for (cudaStream_t st : ps) cudaStreamDestroy(st);
-      for (cudaEvent_t ev : join) cudaEventDestroy(ev);
-      if (fork) cudaEventDestroy(fork);
-      cudaGetLastError();
-      return fail(h, IGA_ECUDA, std::string("iga_mp_set_concurrent: ") + cudaGetErrorString(e));
-    }
-    mp.ps = ps;
-    mp.join = join;
-    mp.fork = fork;
-  }
-  mp.concurrent = on != 0;
-  drop_step_graph(h);
-  return IGA_OK;
-}
-
-int iga_mp_patch(iga_handle* h, int r, iga_handle** patch) {
-  if (!h || !h->mp || !patch || r < 0 || r >= (int)h->mp->patch.size()) return IGA_EINVAL;
-  *patch = h->mp->patch[(size_t)r];
-  (*patch)->stream = h->stream;
-  return IGA_OK;
-}
-
-int iga_mp_patch_io(iga_handle* h, int r, int nvec, int add, const double* in, double* out) {
-  CKS(check_handle(h));
-  if (!h->mp || r < 0 || r >= (int)h->mp->patch.size() || nvec < 1 || nvec > kMaxVec || !in || !out)
-    return fail(h, IGA_EINVAL, "bad arguments");
-  const MpState& mp = *h->mp;
-  LK(launch_mp_patch_io(h->stream, mp.maps, mp.off[(size_t)r], mp.nr[(size_t)r], nvec, add != 0, in, out));
-  return IGA_OK;
-}
-
-int iga_mp_info(const iga_handle* h, int* npatch, int* n_adj, long long* nloc) {
-  if (!h || !h->mp) return IGA_EINVAL;
-  if (npatch) *npatch = (int)h->mp->patch.size();
-  if (n_adj) *n_adj = h->mp->n_adj;
-  if (nloc) *nloc = h->mp->nloc;
-  return IGA_OK;
-}
-
 int iga_state_init(iga_handle* h, int k, const double* U0, const double* V0, double* state) {
   CKS(check_handle(h));
   if (k < 1 || k > kMaxK || !U0 || !V0 || !state) return fail(h, IGA_EINVAL, "bad arguments");
@@ -2076,200 +1263,6 @@ int iga_cfl(iga_handle* h, double rho_inf, int iters, double* lambda_max, double
   *lambda_max = est;
   *tau_crit = std::sqrt(theta_crit(rho_inf) / est);
   return IGA_OK;
-}
-
-
-// ---------------------------------------------------------------------------
-// learned warm start
-// ---------------------------------------------------------------------------
-namespace {
-
-uint64_t splitmix64(uint64_t& state) {
-  uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-
-double uniform01(uint64_t& state) { return (double)(splitmix64(state) >> 11) * (1.0 / 9007199254740992.0); }
-
-int ws_upload_params(iga_handle* h, const float* theta) {
-  CKS(ensure_ws_step(h, 1));
-  CK(cudaMemcpy(h->ws_theta, theta, sizeof(float) * IGA_NET_NPARAM, cudaMemcpyHostToDevice));
-  CK(cudaMemset(h->ws_m, 0, sizeof(float) * IGA_NET_NPARAM));
-  CK(cudaMemset(h->ws_v, 0, sizeof(float) * IGA_NET_NPARAM));
-  h->ws_adam_t = 0;
-  h->ws_params = true;
-  return IGA_OK;
-}
-
-int net_args_ok(int n1, int n2, int n3, int nb) { return net_grid_ok(NetGrid{n1, n2, n3}, nb); }
-
-}  // namespace
-
-int iga_ws_init_params(iga_handle* h, unsigned long long seed) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_init_params"));
-  std::vector<float> th(IGA_NET_NPARAM, 0.0f);
-  uint64_t st = seed;
-  const double b1 = 1.0 / std::sqrt(81.0), b2 = 1.0 / std::sqrt(432.0);
-  for (int i = 0; i < 1296; ++i) th[i] = (float)((2.0 * uniform01(st) - 1.0) * b1);
-  for (int i = 1312; i < 1744; ++i) th[i] = (float)((2.0 * uniform01(st) - 1.0) * b2);
-  CKS(ws_upload_params(h, th.data()));
-  h->ws_trained = false;
-  drop_step_graph(h);
-  return IGA_OK;
-}
-
-int iga_ws_set_params(iga_handle* h, const float* theta_host) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_set_params"));
-  if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
-  CKS(ws_upload_params(h, theta_host));
-  h->ws_trained = true;
-  drop_step_graph(h);
-  return IGA_OK;
-}
-
-int iga_ws_get_params(iga_handle* h, float* theta_host) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_get_params"));
-  if (!theta_host) return fail(h, IGA_EINVAL, "theta is NULL");
-  if (!h->ws_params) return fail(h, IGA_EINVAL, "no parameters yet (iga_ws_init_params, iga_ws_train or iga_ws_set_params)");
-  CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpy(theta_host, h->ws_theta, sizeof(float) * IGA_NET_NPARAM, cudaMemcpyDeviceToHost));
-  return IGA_OK;
-}
-
-int iga_ws_collect(iga_handle* h, int capacity) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_collect"));
-  if (capacity < 0) return fail(h, IGA_EINVAL, "capacity < 0");
-  CK(cudaStreamSynchronize(h->stream));
-  dfree(h->ws_sx);
-  dfree(h->ws_st);
-  h->ws_cap = h->ws_count = 0;
-  if (capacity == 0) return IGA_OK;
-  CKS(dalloc(h, &h->ws_sx, (size_t)capacity * 3 * h->N));
-  CKS(dalloc(h, &h->ws_st, (size_t)capacity * h->N));
-  h->ws_cap = capacity;
-  return IGA_OK;
-}
-
-int iga_ws_samples(iga_handle* h, int* count) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_samples"));
-  if (!count) return fail(h, IGA_EINVAL, "count is NULL");
-  *count = h->ws_count;
-  return IGA_OK;
-}
-
-int iga_ws_train(iga_handle* h, int epochs, double lr, unsigned long long seed, double* epoch_loss) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_train"));
-  if (epochs < 1 || !(lr > 0.0)) return fail(h, IGA_EINVAL, "epochs < 1 or lr <= 0");
-  if (h->ws_count < 1) return fail(h, IGA_EINVAL, "no recorded samples (iga_ws_collect, then iga_step)");
-  const NetGrid g = net_grid_of(h);
-  if (!net_grid_ok(g, 1)) return fail(h, IGA_EINVAL, "grid beyond the network kernels' launch limits");
-  if (!h->ws_params) CKS(iga_ws_init_params(h, seed));
-  const long long N = h->N;
-  const int ns = h->ws_count;
-  const long long nupd = (long long)epochs * ns;
-  if (!h->ws_y) {
-    CKS(dalloc(h, &h->ws_y, (size_t)N));
-    CKS(dalloc(h, &h->ws_dy, (size_t)N));
-    CKS(dalloc(h, &h->ws_lpart, (size_t)kRedBlocks));
-    void* w = nullptr;
-    const cudaError_t e = cudaMalloc(&w, net_workspace_bytes(g, 1));
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, IGA_ENOMEM, "network workspace"); }
-    h->ws_work = w;
-  }
-  if (h->ws_loss_cap < nupd) {
-    CKS(dalloc(h, &h->ws_loss, (size_t)nupd));
-    h->ws_loss_cap = nupd;
-  }
-  cudaStream_t s = h->stream;
-  std::vector<int> order(ns);
-  uint64_t st = seed ^ 0xA0761D6478BD642FULL;
-  long long u = 0;
-  for (int e = 0; e < epochs; ++e) {
-    for (int i = 0; i < ns; ++i) order[i] = i;
-    for (int i = ns - 1; i > 0; --i) {  // Fisher-Yates
-      const int j = (int)(splitmix64(st) % (uint64_t)(i + 1));
-      std::swap(order[i], order[j]);
-    }
-    for (int i = 0; i < ns; ++i, ++u) {
-      const __nv_bfloat16* x = h->ws_sx + (size_t)order[i] * 3 * N;
-      const float* t = h->ws_st + (size_t)order[i] * N;
-      CK(launch_net_forward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_y, nullptr, nullptr, nullptr, &h->nlaunch));
-      CK(launch_net_loss(s, N, h->ws_y, t, h->ws_dy, h->ws_lpart, h->ws_loss + u, &h->nlaunch));
-      CK(launch_net_backward(s, g, 1, x, h->ws_theta, h->ws_act, h->ws_dy, h->ws_grad, h->ws_work, &h->nlaunch));
-      const double lr_u = lr * 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)u / (double)nupd));
-      CK(launch_net_adam(s, IGA_NET_NPARAM, h->ws_theta, h->ws_grad, h->ws_m, h->ws_v, ++h->ws_adam_t, lr_u,
-                         &h->nlaunch));
-    }
-  }
-  std::vector<double> L((size_t)nupd);
-  CK(cudaMemcpyAsync(L.data(), h->ws_loss, sizeof(double) * nupd, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (epoch_loss)
-    for (int e = 0; e < epochs; ++e) {
-      double m = 0.0;
-      for (int i = 0; i < ns; ++i) m += L[(size_t)e * ns + i];
-      epoch_loss[e] = m / ns;
-    }
-  h->ws_trained = true;
-  drop_step_graph(h);
-  return IGA_OK;
-}
-
-int iga_ws_features(iga_handle* h, int k, const double* b, double* b1, double* b2, double* z1, double* z2,
-                    unsigned short* x, double* E, double* scales) {
-  CKS(check_handle(h));
-  CKS(single_patch(h, "iga_ws_features"));
-  if (k < 1 || k > kMaxVec || !b || !b1 || !b2 || !z1 || !z2 || !x || !E || !scales)
-    return fail(h, IGA_EINVAL, "bad arguments");
-  CKS(ensure_ws_step(h, 1));
-  cudaStream_t s = h->stream;
-  CK(launch_ws_features(s, h->N, k, b, b1, b2, h->Dm, z1, z2, reinterpret_cast<__nv_bfloat16*>(x), E, h->ws_part,
-                        h->ws_sc, &h->nlaunch));
-  CK(cudaMemcpyAsync(scales, h->ws_sc, sizeof(double) * 2 * k, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
-  return IGA_OK;
-}
-
-int iga_net_forward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
-                    unsigned short* act, float* y, void* stream) {
-  if (!net_args_ok(n1, n2, n3, nb) || !x || !theta || !act || !y) return IGA_EINVAL;
-  long long nl = 0;
-  const cudaError_t e = launch_net_forward((cudaStream_t)stream, NetGrid{n1, n2, n3}, nb,
-                                           reinterpret_cast<const __nv_bfloat16*>(x), theta,
-                                           reinterpret_cast<__nv_bfloat16*>(act), y, nullptr, nullptr, nullptr, &nl);
-  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
-}
-
-unsigned long long iga_net_workspace_bytes(int n1, int n2, int n3, int nb) {
-  if (!net_args_ok(n1, n2, n3, nb)) return 0;
-  return net_workspace_bytes(NetGrid{n1, n2, n3}, nb);
-}
-
-int iga_net_backward(int n1, int n2, int n3, int nb, const unsigned short* x, const float* theta,
-                     const unsigned short* act, const float* dy, float* grad, void* work,
-                     unsigned long long work_bytes, void* stream) {
-  if (!net_args_ok(n1, n2, n3, nb) || !x || !theta || !act || !dy || !grad || !work) return IGA_EINVAL;
-  const NetGrid g{n1, n2, n3};
-  if (work_bytes < net_workspace_bytes(g, nb)) return IGA_EINVAL;
-  long long nl = 0;
-  const cudaError_t e = launch_net_backward((cudaStream_t)stream, g, nb, reinterpret_cast<const __nv_bfloat16*>(x),
-                                            theta, reinterpret_cast<const __nv_bfloat16*>(act), dy, grad, work, &nl);
-  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
-}
-
-int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int step, double lr, void* stream) {
-  if (n < 1 || step < 1 || !(lr > 0.0) || !theta || !grad || !m || !v) return IGA_EINVAL;
-  long long nl = 0;
-  const cudaError_t e = launch_net_adam((cudaStream_t)stream, n, theta, grad, m, v, step, lr, &nl);
-  return e == cudaSuccess ? IGA_OK : IGA_ECUDA;
 }
 
 

@@ -206,7 +206,54 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
-// internal routines of capi.cu used elsewhere (batch.cu)
+inline bool is_assembled(const iga_handle* h) {
+  return h->opt.op_form == IGA_OP_ASSEMBLED || h->opt.op_form == IGA_OP_ASSEMBLED_DF;
+}
+
+// operators.cu: the handle's operators. pq / npq: the band product's per-block partials of
+// x.y ([nvec][*npq]; *npq = 0 when not computed); presplit (double-FP32 form): the split copy
+// of x is already in place; rzp / nrz: the preconditioner's last pass's partials of r.z and
+// r.z_old ([2][nvec][*nrz]).
+double mass_last_flops(const iga_handle* h);
+double stiff_last_flops(const iga_handle* h);
+double mass_apply_flops(const iga_handle* h);
+int fd_apply(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* t1, double* t2,
+             double* rzp = nullptr, int* nrz = nullptr);
+int assemble_band64(iga_handle* h);
+int assemble_band_df(iga_handle* h);
+cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const int* active, const double* x,
+                        double* y, int threads, int nv, double* pq, int* npq, bool presplit = false);
+int apply_band(iga_handle* h, int cls, int nvec, const int* active, const double* x, double* y,
+               double* pq = nullptr, int* npq = nullptr, bool presplit = false);
+int mp_apply(iga_handle* h, int which, int nvec, const int* active, const double* x, double* y);
+int apply_M(iga_handle* h, int nvec, const int* active, const double* x, double* y, double* pq = nullptr,
+            int* npq = nullptr, bool presplit = false);
+int apply_K(iga_handle* h, int nvec, const int* active, const double* x, double* y);
+int apply_Pinv(iga_handle* h, int nvec, const int* active, const double* r, double* z, double* rzp = nullptr,
+               int* nrz = nullptr);
+
+// pcg.cu: batched PCG (launch-only pieces and the host-driven loop)
+int solve_begin(iga_handle* h, int nvec, const double* b, double* x, bool use_x0);
+int solve_prime(iga_handle* h, int nvec);
+int solve_iter_a(iga_handle* h, int nvec, double* x);
+int solve_iter_b(iga_handle* h, int nvec);
+int read_nactive(iga_handle* h, int* nact);
+int solve(iga_handle* h, int nvec, const double* b, double* x, bool use_x0, int* iters, double* relres);
+
+// internal routines of capi.cu used elsewhere (batch.cu, warmstart.cu, multipatch.cu, operators.cu, pcg.cu)
+int fail(iga_handle* h, int code, const std::string& msg);
+int prof_begin(iga_handle* h, int cls, cudaEvent_t* e1);
+int prof_end(iga_handle* h, cudaEvent_t e1, double flops, double bytes);
+int ensure_op_ws(iga_handle* h, int nvec);
+double theta_crit(double rho);
+extern thread_local std::string g_create_err;  // message of the last failed handle creation
+// a handle over the index box lo..hi of a patch (nullptr: the whole patch)
+int create_handle(int dim, const int* degree, const int* nknots, const double* const* knots, const double* ctrl,
+                  const int* lo, const int* hi, const iga_options* opt, iga_handle** out);
+int check_handle(iga_handle* h);
+int single_patch(iga_handle* h, const char* what);
+int ensure_ws_step(iga_handle* h, int k);
+NetGrid net_grid_of(const iga_handle* h);
 StepCoefs handle_coefs(const iga_handle* h, int k, double rho, double dt);
 void drop_step_graph(iga_handle* h);
 int ensure_cg_ws(iga_handle* h, int nvec);
