@@ -4,7 +4,7 @@ operators; band-Cholesky Kronecker or BF16 fast-diagonalisation preconditioner).
 
   * three small patches of degrees 2, 3, 4 at PCG tol 1e-13: every patch after 6 steps
     within 1e-10 (relative L2 of U and V) of the oracle's Stepper on the same inputs,
-    and of the patch stepped alone through the library;
+    and of the patch stepped alone through the library; the same for k = 1 and k = 3;
   * the FP32 Kronecker solve (flexible PCG) at tol 1e-10: within 1e-8 of the same patches
     stepped alone with it;
   * the 48-patch batch (16^3..96^3 elements, p in {2, 3, 4}) for 3 steps: every patch
@@ -114,6 +114,54 @@ def test_persistent_batch_matches_oracle_and_patches_alone():
             e_a = _rel(batched[i][row], alone[row])
             print("persistent batch, patch %d (p=%d), %s: vs oracle %.3e, vs alone %.3e" % (i, ws[i].p[0], var, e_o, e_a))
             assert e_o <= 1e-10 and e_a <= 1e-10, (i, var, e_o, e_a)
+    b.close()
+    for g in pats:
+        g.close()
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_persistent_batch_other_orders_match_oracle(k):
+    """The persistent step for k = 1 (second order) and k = 3 (sixth order): every patch
+    within 1e-10 of the oracle's Stepper and of the patch stepped alone (FP64 Kronecker
+    solve, tol 1e-13)."""
+    ws = _small_patches()
+    rho, nsteps = 0.5, 4
+    pats, states, inits = [], [], []
+    for w in ws:
+        g = iga.Patch(w.p, w.knots, w.ctrl(), tol=1e-13, op_form="assembled", precond="banded")
+        U0, V0 = w.initial()
+        pats.append(g)
+        inits.append((_t(U0), _t(V0)))
+        states.append(torch.zeros(3 * k * g.N, dtype=torch.float64, device=DEV))
+    dts, refs = [], []
+    for w in ws:
+        ops = oracle.Operators(oracle.Patch(w.p, w.knots, w.ctrl()))
+        lam = oracle.lambda_max_dense(ops.patch.band_to_dense(ops.M), ops.patch.band_to_dense(ops.K))
+        dt = 0.5 * math.sqrt(oracle.theta_crit(rho) / lam)
+        st = oracle.Stepper(ops, k, rho, tol=1e-13)
+        U0, V0 = w.initial()
+        X = st.init(U0, V0)
+        for _ in range(nsteps):
+            X = st.step(X, dt)
+        dts.append(dt)
+        refs.append(X)
+    for g, st, (u0, v0) in zip(pats, states, inits):
+        g.state_init(k, u0, v0, st)
+    b = iga.Batch(pats)
+    b.set_persistent(True)
+    stats = b.step(states, k, rho, dts, nsteps)
+    assert stats[0].launches == nsteps
+    batched = [s.cpu().numpy().reshape(3 * k, -1) for s in states]
+    for i, (g, st, (u0, v0), dt) in enumerate(zip(pats, states, inits, dts)):
+        assert stats[i].solves == k * nsteps and stats[i].max_relres <= 1e-13
+        g.state_init(k, u0, v0, st)
+        g.step(st, k, rho, dt, nsteps)
+        alone = st.cpu().numpy().reshape(3 * k, -1)
+        for row, var in ((0, "U"), (1, "V")):
+            e_o = _rel(batched[i][row], refs[i][row])
+            e_a = _rel(batched[i][row], alone[row])
+            print("persistent batch k=%d, patch %d, %s: vs oracle %.3e, vs alone %.3e" % (k, i, var, e_o, e_a))
+            assert e_o <= 1e-10 and e_a <= 1e-10, (k, i, var, e_o, e_a)
     b.close()
     for g in pats:
         g.close()
