@@ -332,7 +332,7 @@ class Operators:
 def pcg(apply_A, apply_Pinv, b, x0=None, tol=1e-10, max_iter=500):
     """Preconditioned conjugate gradients (Sec. 5.5). Stops when ||r||_2 <= tol ||b||_2
     (the paper's relative tolerance; the denominator is ||b||, so that a warm start is
-    judged against the same target as the null guess). Returns (x, iterations, ||r||/||b||).
+    held to the same target as the null guess). Returns (x, iterations, ||r||/||b||).
     One iteration = one product A p."""
     bn = float(np.linalg.norm(b))
     if bn == 0.0:

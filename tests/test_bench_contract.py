@@ -25,7 +25,7 @@ def _band_prof(w, launches, vectors, ms):
 
 
 def test_method_bytes_of_the_mass_product():
-    # 64^3 elements, p = 3: 256^3 Gauss points, W in FP64 (the survey's 134 MB), 16 B per dof and vector
+    # 64^3 elements, p = 3: 256^3 Gauss points, W in FP64 (134 MB), 16 B per dof and vector
     fac, per_vec = bench.method_bytes(C2, mass=True)
     assert fac == 256 ** 3 * 8 and per_vec == 16 * C2.ndof
     fac_k, _ = bench.method_bytes(C2, mass=False)
