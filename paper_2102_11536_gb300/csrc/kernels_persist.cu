@@ -6,8 +6,9 @@
 // kPRows rows for the band products and vector updates, tiles of kPLines lines for the
 // axis solves -- which the resident blocks take in turn; phases are separated by a grid
 // barrier whose wait is bounded (a time-out sets the error word and every block
-// returns). The per-system scalars of PCG (one system per patch and stage) are summed by
-// one block from per-tile partials in a fixed order, so a run is reproducible.
+// returns). The per-system scalars of PCG (one system per patch and stage) are summed from
+// per-tile partials in a phase of their own (block b sums systems b, b + G, ... in a fixed
+// order), then updated by block 0, so a run is reproducible.
 //
 // Arithmetic per row and line as in the single-patch kernels: the FP64 band product
 // (diagonal, then per stored slot the upper and the lower term), the band-Cholesky
@@ -65,22 +66,23 @@ __device__ bool pgrid_sync(unsigned int* bar, long long limit, int* err) {
   return gave_up == 0;
 }
 
-// out[s] = sum over the patch's tiles t of part[(t0 + t) k + j], s = patch k + j, by the
-// block's warps (lanes take fixed strided shares, then a shuffle tree): a fixed order
-__device__ void psum_systems(const PBatch& B, const double* part, const int* t0, const int* nt, double* out) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// fixed-order block sum of one value per thread (valid in thread 0)
+__device__ double pblock_sum(double v);
+
+// out[s] = sum over the patch's tiles t of part[(t0 + t) k + j], s = patch k + j: a phase of
+// its own, block b summing systems b, b + G, ... (a fixed strided share per thread, then the
+// block tree: a fixed order), so that one block does not sum every system's partials
+__device__ void psum_phase(const PBatch& B, const double* part, const int* t0, const int* nt, double* out) {
   const int S = B.np * B.k;
-  for (int s = w; s < S; s += kPThreads / 32) {
+  for (int s = blockIdx.x; s < S; s += gridDim.x) {  // uniform over the block
     const int pi = s / B.k, j = s - pi * B.k;
     double a = 0.0;
-    for (int t = lane; t < nt[pi]; t += 32) a += __ldcg(&part[(long long)(t0[pi] + t) * B.k + j]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) out[s] = a;
+    for (int t = threadIdx.x; t < nt[pi]; t += kPThreads) a += __ldcg(&part[(long long)(t0[pi] + t) * B.k + j]);
+    a = pblock_sum(a);
+    if (threadIdx.x == 0) out[s] = a;
   }
 }
 
-// fixed-order block sum of one value per thread (valid in thread 0)
 __device__ double pblock_sum(double v) {
   __shared__ double red[kPThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -652,8 +654,6 @@ __device__ void ph_fd(const PBatch& B, int stage, unsigned char* smem) {
 // ---------------------------------------------------------------- scalar updates (block 0)
 // start: ||b||^2, ||r||^2 = ||b||^2, activity, counters
 __device__ void lead_start(const PBatch& B) {
-  psum_systems(B, B.part, B.rt0, B.nrt_p, B.bb);
-  __syncthreads();
   for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
     B.rr[s] = B.bb[s];
     B.active[s] = B.bb[s] > 0.0 ? 1 : 0;
@@ -663,9 +663,6 @@ __device__ void lead_start(const PBatch& B) {
 
 // after the preconditioner: r.z, and beta for the next direction (plain or flexible)
 __device__ void lead_rz(const PBatch& B, bool first) {
-  psum_systems(B, B.lpart, B.lt2, B.nlt2_p, B.rznew);
-  psum_systems(B, B.lpart + (long long)B.nrzt * B.k, B.lt2, B.nlt2_p, B.rzold);
-  __syncthreads();
   for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
     if (!B.active[s]) continue;
     if (!first) {
@@ -678,8 +675,6 @@ __device__ void lead_rz(const PBatch& B, bool first) {
 
 // after q = M p: alpha = r.z / p.q (breakdown stops the system)
 __device__ void lead_alpha(const PBatch& B) {
-  psum_systems(B, B.part, B.rt0, B.nrt_p, B.pq);
-  __syncthreads();
   for (int s = threadIdx.x; s < B.np * B.k; s += kPThreads) {
     if (!B.active[s]) continue;
     const double pq = B.pq[s];
@@ -695,8 +690,6 @@ __device__ void lead_alpha(const PBatch& B) {
 
 // after the x, r update: ||r||^2, iteration count, convergence; flags[0] = any active
 __device__ void lead_check(const PBatch& B) {
-  psum_systems(B, B.part, B.rt0, B.nrt_p, B.rr);
-  __syncthreads();
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -763,6 +756,9 @@ __device__ bool pprecond(const PBatch& B, unsigned char* smem, bool first, unsig
       pmark(B, kPhPrecond, clk);
     }
   }
+  psum_phase(B, B.lpart, B.lt2, B.nlt2_p, B.rznew);
+  psum_phase(B, B.lpart + (long long)B.nrzt * B.k, B.lt2, B.nlt2_p, B.rzold);
+  if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
   if (blockIdx.x == 0) lead_rz(B, first);
   if (!pgrid_sync(B.bar, B.bar_limit, B.err)) return false;
   pmark(B, kPhScalars, clk);
@@ -783,6 +779,8 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_batch_step(const PBatch B) 
   // b = K (-Y) into r (x0 = 0: r = b), partials of b.b
   ph_band<K, SLOTS>(B, true, B.Yp, B.rp, 2, B.part);
   IGA_PSYNC(kPhKProduct);
+  psum_phase(B, B.part, B.rt0, B.nrt_p, B.bb);
+  IGA_PSYNC(kPhScalars);
   if (blockIdx.x == 0) lead_start(B);
   IGA_PSYNC(kPhScalars);
   if (!pprecond<K, T>(B, psmem, true, clk)) return;
@@ -793,10 +791,14 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_batch_step(const PBatch B) 
     IGA_PSYNC(kPhDirection);
     ph_band<K, SLOTS>(B, false, B.pp, B.qp, 1, B.part);  // q = M p, partials of p.q
     IGA_PSYNC(kPhMProduct);
+    psum_phase(B, B.part, B.rt0, B.nrt_p, B.pq);
+    IGA_PSYNC(kPhScalars);
     if (blockIdx.x == 0) lead_alpha(B);
     IGA_PSYNC(kPhScalars);
     ph_xr<K>(B);
     IGA_PSYNC(kPhXr);
+    psum_phase(B, B.part, B.rt0, B.nrt_p, B.rr);
+    IGA_PSYNC(kPhScalars);
     if (blockIdx.x == 0) lead_check(B);
     IGA_PSYNC(kPhScalars);
     if (*(volatile int*)&B.flags[0] == 0) break;  // the same value in every block
