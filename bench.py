@@ -1014,10 +1014,22 @@ def run_ours(args):
                 "headline_speedup": results[head]["value"] / results[n]["value"]}
             for n in ("fp64_paper", "fp64_banded", "fp64_assembled") if n in results}
 
+    # the secondary legs: a failure in one is recorded in the line (leg_errors) instead of
+    # ending the run; the batch leg's collectives under torchrun leave it unguarded there
+    leg_errors = {}
+
+    def guarded(name, fn, on=True):
+        if not on:
+            return fn()
+        try:
+            return fn()
+        except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
+            leg_errors[name] = "%s: %s" % (type(exc).__name__, exc)
+            return None
+
     # the headline form's error per step against the FP64 form (the paper's method) from the same
     # initial state: both stepped by the host-driven loop (the same kernels), one step at a time
-    err_trace = None
-    if "fp64_paper" in results and head != "fp64_paper" and args.error_steps > 0:
+    def error_trace():
         ref_opts = results["fp64_paper"]["options"]
         st_ref = torch.empty_like(state)
         patch.set_graphs(False)
@@ -1025,16 +1037,20 @@ def run_ours(args):
         patch.state_init(k, u0, v0, st_ref)
         select_form(patch, hopts, band_cfgs, k)
         patch.state_init(k, u0, v0, state)
-        err_trace = []
+        trace = []
         for n in range(args.error_steps):
             select_form(patch, ref_opts, band_cfgs, k)
             patch.step(st_ref, k, w.rho, dt, 1)
             select_form(patch, hopts, band_cfgs, k)
             patch.step(state, k, w.rho, dt, 1)
             a, b = state.view(3 * k, N), st_ref.view(3 * k, N)
-            err_trace.append({"step": n + 1, **{v: float(torch.linalg.norm(a[r] - b[r]) / torch.linalg.norm(b[r]))
-                                                for r, v in ((0, "U"), (1, "V"))}})
+            trace.append({"step": n + 1, **{v: float(torch.linalg.norm(a[r] - b[r]) / torch.linalg.norm(b[r]))
+                                            for r, v in ((0, "U"), (1, "V"))}})
         del st_ref
+        return trace
+
+    err_trace = (guarded("error_per_step", error_trace)
+                 if "fp64_paper" in results and head != "fp64_paper" and args.error_steps > 0 else None)
 
     # end to end through the public C API on host memory, headline form: every step
     # copies the state in from pinned host memory and the new state back out.
@@ -1054,16 +1070,19 @@ def run_ours(args):
     if pg:
         pg.barrier()
     e2e_rate = world * args.steps / e2e_s
-    general = run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream, flush, hopts,
-                          band_cfgs) if args.general else None
+    general = guarded("general_model", lambda: run_general(args, iga, torch, patch, w, dt, u0, v0, state, stream,
+                                                            flush, hopts, band_cfgs)) if args.general else None
     patch.close()
     del state, host
     torch.cuda.empty_cache()
-    secondary = (run_secondary(args, iga, torch, workloads, dev, stream, flush, head, hopts)
+    secondary = (guarded("secondary_workload", lambda: run_secondary(args, iga, torch, workloads, dev, stream, flush,
+                                                                      head, hopts))
                  if args.secondary and rank == 0 else None)
-    learned = run_learned(args, iga, torch, workloads, dev, stream, flush) if args.learned_config and rank == 0 else None
-    batch_res = run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg) if args.batch_steps > 0 else None
-    mp_res = (run_multipatch(args, iga, torch, dev, flush, stream)
+    learned = (guarded("learned_warm_start", lambda: run_learned(args, iga, torch, workloads, dev, stream, flush))
+               if args.learned_config and rank == 0 else None)
+    batch_res = (guarded("multipatch_batch", lambda: run_batch(args, iga, torch, workloads, dev, flush, rank, world, pg),
+                         on=world == 1) if args.batch_steps > 0 else None)
+    mp_res = (guarded("multipatch_system", lambda: run_multipatch(args, iga, torch, dev, flush, stream))
               if args.multipatch_steps > 0 and world == 1 else None)
 
     if rank != 0:
@@ -1132,11 +1151,16 @@ def run_ours(args):
     if mp_res is not None:
         result["multipatch_system"] = mp_res
     if not args.no_cpu_baseline and world == 1:
-        ws = sample_workload(w, args.sample_nel)
-        base, Xo, nst = run_cpu_baseline(w, ws, dt, args.cpu_seconds)
-        result["cpu_baseline"] = base
-        forms = [(head, hopts)] + [(n, o) for n, o, _, _ in FORMS if n in ("fp64_paper", "fp64_banded") and n != head]
-        result["parity_vs_oracle"] = sample_parity(args, iga, torch, dev, ws, dt, nst, Xo, forms)
+        def baseline_and_parity():
+            ws = sample_workload(w, args.sample_nel)
+            base, Xo, nst = run_cpu_baseline(w, ws, dt, args.cpu_seconds)
+            result["cpu_baseline"] = base
+            forms = [(head, hopts)] + [(n, o) for n, o, _, _ in FORMS
+                                       if n in ("fp64_paper", "fp64_banded") and n != head]
+            result["parity_vs_oracle"] = sample_parity(args, iga, torch, dev, ws, dt, nst, Xo, forms)
+        guarded("cpu_baseline", baseline_and_parity)
+    if leg_errors:
+        result["leg_errors"] = leg_errors
     print(json.dumps(result), flush=True)
     if pg:
         pg.destroy_process_group()
