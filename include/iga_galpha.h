@@ -53,7 +53,10 @@ extern "C" {
                                  vector); products in double-FP32 arithmetic: error-free FP32
                                  products and TwoSum accumulation, a few 2^-48 of sum |a||x|,
                                  plus, for entries below about 2^-130 of the vector's largest,
-                                 an absolute error of that order */
+                                 an absolute error of that order; the terms of tiny slots
+                                 (every coefficient below 2^-24 of the matrix's largest) are
+                                 one FP32 multiply-add each, within 2^-23 |a x| < 2^-47
+                                 max|A| |x| (iga_band_df_tiny) */
 
 /* Arithmetic of the preconditioner's fast-diagonalisation mode products. */
 #define IGA_PREC_FP64 0       /* FP64 (default); plain CG */
@@ -464,6 +467,18 @@ int iga_net_adam(int n, float* theta, const float* grad, float* m, float* v, int
  * out). Every configuration computes each row with the same operations in the same
  * order, so results are bitwise equal. IGA_EINVAL for other values. */
 int iga_set_band_config(iga_handle* h, int threads, int nv);
+
+/*
+ * iga_band_df_tiny -- the share of the terms of an interior row that the
+ * IGA_OP_ASSEMBLED_DF products form as one FP32 multiply-add (the tiny slots: every
+ * coefficient of the slot, after the matrix's power-of-two scaling, below 2^-24 of
+ * its largest; taken at the two ends of each run of slots sharing their offsets along
+ * directions 1 and 2), for M (frac_m) and K (frac_k); the other terms cost 12 FP32
+ * operations. Host outputs, either may be NULL. Assembles the double-FP32 band first
+ * if needed. IGA_EINVAL unless h's form is IGA_OP_ASSEMBLED_DF. A numerical choice of
+ * this library: the paper has no counterpart.
+ */
+int iga_band_df_tiny(iga_handle* h, double* frac_m, double* frac_k);
 
 /*
  * iga_autotune -- time every band-product configuration (threads 64/128/256/512 x

@@ -100,6 +100,7 @@ def lib():
         "iga_net_backward": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp, vp, vp, vp, ctypes.c_ulonglong, vp]),
         "iga_net_adam": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]),
         "iga_set_band_config": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
+        "iga_band_df_tiny": (ctypes.c_int, [H, dp, dp]),
         "iga_set_damping": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_double]),
         "iga_set_forcing": (ctypes.c_int, [H, ctypes.c_int, vp, dp, dp]),
         "iga_set_time": (ctypes.c_int, [H, ctypes.c_double]),
@@ -145,7 +146,7 @@ def exported_symbols():
             "iga_apply_Pinv_noalloc", "iga_probe_fp64_fma", "iga_set_graphs", "iga_ws_collect",
             "iga_ws_samples", "iga_ws_train", "iga_ws_init_params", "iga_ws_get_params", "iga_ws_set_params",
             "iga_ws_features", "iga_net_forward", "iga_net_workspace_bytes", "iga_net_backward", "iga_net_adam",
-            "iga_set_band_config", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
+            "iga_set_band_config", "iga_band_df_tiny", "iga_autotune", "iga_batch_create", "iga_batch_destroy", "iga_batch_last_error",
             "iga_batch_step", "iga_set_damping", "iga_set_forcing", "iga_set_time", "iga_get_time",
             "iga_mp_layout", "iga_mp_create", "iga_mp_info", "iga_mp_patch", "iga_mp_patch_io", "iga_mp_set_concurrent", "iga_npoints", "iga_gauss_points", "iga_evaluate",
             "iga_integrate", "iga_set_barrier_limit", "iga_batch_set_persistent", "iga_batch_phase_times",
@@ -492,6 +493,13 @@ class Patch:
     def set_band_config(self, threads=0, nv=0):
         """Band-product launch configuration (threads per block, vectors per thread; 0 = default)."""
         self._chk(lib().iga_set_band_config(self.h, threads, nv), "iga_set_band_config")
+
+    def band_df_tiny(self):
+        """(frac_m, frac_k): the share of an interior row's terms that the double-FP32
+        products form as one FP32 multiply-add (iga_band_df_tiny)."""
+        fm, fk = ctypes.c_double(), ctypes.c_double()
+        self._chk(lib().iga_band_df_tiny(self.h, ctypes.byref(fm), ctypes.byref(fk)), "iga_band_df_tiny")
+        return fm.value, fk.value
 
     def autotune(self, nvec=2, reps=5):
         """Time the band-product configurations on nvec vectors, keep the fastest; returns (threads, nv)."""

@@ -729,7 +729,7 @@ void iga_destroy(iga_handle* h) {
   }
   dfree(h->ctrl); dfree(h->W); dfree(h->G); dfree(h->Dm); dfree(h->scale); dfree(h->scale32); dfree(h->dflag);
   dfree(h->Mband); dfree(h->Kband); dfree(h->band_off); dfree(h->band_o12);
-  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
+  dfree(h->Mdf); dfree(h->Kdf); dfree(h->band_runs); dfree(h->band_runs_k); dfree(h->df_xs); dfree(h->df_E); dfree(h->df_part); dfree(h->df_bar);
   dfree(h->u0); dfree(h->u1); dfree(h->ta); dfree(h->tb); dfree(h->tc);
   dfree(h->r); dfree(h->z); dfree(h->zold); dfree(h->p); dfree(h->q); dfree(h->f1); dfree(h->f2);
   dfree(h->partial); dfree(h->pq_part); dfree(h->rz_part);
@@ -1282,6 +1282,16 @@ int iga_set_band_config(iga_handle* h, int threads, int nv) {
   h->band_threads = threads;
   h->band_nv = nv;
   drop_step_graph(h);
+  return IGA_OK;
+}
+
+int iga_band_df_tiny(iga_handle* h, double* frac_m, double* frac_k) {
+  CKS(check_handle(h));
+  if (h->mp) return fail(h, IGA_EINVAL, "iga_band_df_tiny takes a single patch (iga_mp_patch lends one)");
+  if (h->opt.op_form != IGA_OP_ASSEMBLED_DF) return fail(h, IGA_EINVAL, "the handle's form is not IGA_OP_ASSEMBLED_DF");
+  CKS(assemble_band(h));
+  if (frac_m) *frac_m = h->df_tiny_m;
+  if (frac_k) *frac_k = h->df_tiny_k;
   return IGA_OK;
 }
 

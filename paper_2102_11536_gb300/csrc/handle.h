@@ -42,7 +42,9 @@ struct iga_handle {
   float2* Mdf = nullptr;
   float2* Kdf = nullptr;
   int EAm = 0, EAk = 0;           // power-of-two exponents of the split bands
-  int* band_runs = nullptr;       // [nruns][4] runs of the upper half
+  int* band_runs = nullptr;       // [nruns][4] runs of the upper half, with M's tiny slots
+  int* band_runs_k = nullptr;     // the same runs with K's tiny slots
+  double df_tiny_m = 0.0, df_tiny_k = 0.0;  // share of an interior row's terms that are tiny
   int band_nruns = 0;
   long long band_Np = 0;          // row stride of the split bands and vectors
   long long df_slack = 0;         // zeroed elements before and after each split array

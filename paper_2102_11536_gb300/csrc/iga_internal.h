@@ -320,8 +320,14 @@ constexpr int kDfPad = 16;
 constexpr int kDfBlocks = 512;
 inline long long df_row_stride(long long N) { return (N + 2 * kDfPad + 15) / 16 * 16; }
 inline long long df_slack(long long maxL) { return (maxL + 1024 + 15) / 16 * 16; }
-// the runs of the upper half: per run {first slot, length, (o1 + 64) | (o2 + 64) << 8, linear offset}
-std::vector<int> band_df_runs(const int* n, const int* p);
+// the runs of the upper half: per run {first slot, length, (o1 + 64) | (o2 + 64) << 8 | m << 16,
+// linear offset}, the centre run (o1 = o2 = 0) first and the others ordered by m. m is the
+// number of tiny slots at each end of the run (slots t < m and t >= length - m): with
+// tiny (nullable, one flag per stored slot) the products form those terms as one FP32
+// multiply-add of the high parts; without it m = 0.
+std::vector<int> band_df_runs(const int* n, const int* p, const unsigned char* tiny);
+// out[h] = largest |hi| of stored slot h over the N rows of a split band, as FP32 bits
+cudaError_t launch_df_slot_absmax(cudaStream_t s, long long N, int H, const float2* A, long long Np, unsigned* out);
 // Adf = split(A 2^-E) with one exponent E (left in dE[0]) for the whole [H][N] band
 cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const double* A, float2* Adf, long long Np,
                                    unsigned long long* part, int* dE);

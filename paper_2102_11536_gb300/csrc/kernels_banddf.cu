@@ -39,6 +39,7 @@
 // DRAM. A block owns the rows of one strip-plane that fall in its window of R rows
 // (window starts even, for the tensor copies' 16-byte alignment).
 #include <algorithm>
+#include <array>
 
 #include "iga_internal.h"
 
@@ -286,6 +287,26 @@ __device__ __forceinline__ void df_term(float& s, float& c, const float2 a, cons
   s = S;
 }
 
+// A term of a tiny slot -- a slot whose coefficients all lie below 2^-24 after the
+// matrix's scaling (its largest coefficient in [1, 2)) -- is one FP32 multiply-add of
+// the high parts into c. Its error, at most 2^-23 |a x| < 2^-47 max|A| |x|, is of the
+// order of the (hi, lo) representation error of the matrix's largest coefficients, so
+// the exact product and the low parts would add nothing the result keeps.
+__device__ __forceinline__ void df_term_tiny(float& c, const float2 a, const float2 x) {
+  c = __fmaf_rn(a.x, x.x, c);
+}
+
+// slot t of a run of len slots whose m first and m last slots are tiny
+__device__ __forceinline__ bool df_is_tiny(int t, int len, int m) { return t < m || t >= len - m; }
+
+__device__ __forceinline__ void df_term_m(float& s, float& c, const float2 a, const float2 x, bool tiny) {
+  if (tiny) df_term_tiny(c, a, x);
+  else df_term(s, c, a, x);
+}
+
+// the tiny-end count m of a run (bits 16..19 of its packed offsets; 0 for run 0)
+__device__ __forceinline__ int df_run_m(const int4& R) { return (R.z >> 16) & 15; }
+
 // Fast2Sum renormalisation of (s, c): |c| is at most a few ulps of s; only for rows
 // that computed a term of the run (on)
 template <int NV>
@@ -303,9 +324,9 @@ __device__ __forceinline__ void df_renorm(float (&s)[NV], float (&c)[NV], bool o
 // the neighbour lines exist: up) and A[h0 + t][i - L0 - t] x[i - L0 - t] (lower: dn).
 // au = &A[h0][i], ad = &A[h0][i - L0], xu[v] = &x_v[i + L0], xd[v] = &x_v[i - L0].
 // LEN > 0: a compile-time length (the loads of the run can all be issued at once);
-// LEN == 0: the runtime length len.
+// LEN == 0: the runtime length len. m: the run's tiny-end count (df_is_tiny).
 template <int LEN, int NV>
-__device__ __forceinline__ void df_run(int len, bool up, bool dn, const float2* __restrict__ au,
+__device__ __forceinline__ void df_run(int len, int m, bool up, bool dn, const float2* __restrict__ au,
                                        const float2* __restrict__ ad, long long Np, const float2* const (&xu)[NV],
                                        const float2* const (&xd)[NV], float (&s)[NV], float (&c)[NV]) {
   // the upper terms of the run, then the lower ones
@@ -314,16 +335,18 @@ __device__ __forceinline__ void df_run(int len, bool up, bool dn, const float2* 
 #pragma unroll
       for (int t = 0; t < LEN; ++t) {
         const float2 a = au[t * Np];
+        const bool tn = df_is_tiny(t, LEN > 0 ? LEN : len, m);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v][t]);
+        for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xu[v][t], tn);
       }
     }
     if (dn) {
 #pragma unroll
       for (int t = 0; t < LEN; ++t) {
         const float2 a = ad[t * (Np - 1)];
+        const bool tn = df_is_tiny(t, LEN > 0 ? LEN : len, m);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v][-t]);
+        for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xd[v][-t], tn);
       }
     }
   } else {
@@ -331,16 +354,18 @@ __device__ __forceinline__ void df_run(int len, bool up, bool dn, const float2* 
 #pragma unroll 1
       for (int t = 0; t < len; ++t) {
         const float2 a = au[t * Np];
+        const bool tn = df_is_tiny(t, LEN > 0 ? LEN : len, m);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v][t]);
+        for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xu[v][t], tn);
       }
     }
     if (dn) {
 #pragma unroll 1
       for (int t = 0; t < len; ++t) {
         const float2 a = ad[t * (Np - 1)];
+        const bool tn = df_is_tiny(t, LEN > 0 ? LEN : len, m);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v][-t]);
+        for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xd[v][-t], tn);
       }
     }
   }
@@ -425,11 +450,12 @@ __global__ void __launch_bounds__(BS) k_band_df(long long N, int nruns, const in
       xu[v] = xv[v] + R.w;
       xd[v] = xv[v] - R.w;
     }
+    const int m = df_run_m(R);
     if (P0 > 0) {
-      if (r == 0) df_run<P0, NV>(0, up, dn, au, ad, Np, xu, xd, s, c);
-      else df_run<2 * P0 + 1, NV>(0, up, dn, au, ad, Np, xu, xd, s, c);
+      if (r == 0) df_run<P0, NV>(0, 0, up, dn, au, ad, Np, xu, xd, s, c);
+      else df_run<2 * P0 + 1, NV>(0, m, up, dn, au, ad, Np, xu, xd, s, c);
     } else {
-      df_run<0, NV>(R.y, up, dn, au, ad, Np, xu, xd, s, c);
+      df_run<0, NV>(R.y, m, up, dn, au, ad, Np, xu, xd, s, c);
     }
     df_renorm<NV>(s, c, up || dn);
   }
@@ -551,7 +577,7 @@ __device__ __forceinline__ void df_issue(const int4 R4, float2* buf, uint32_t mb
 // the terms of run (LEN slots) from buffer buf for row j of the block: the upper
 // terms, then the lower ones, as in df_run
 template <int P0, int NV, int R, int LEN>
-__device__ __forceinline__ void df_run_smem(const float2* buf, int j, int L0, bool up, bool dn, float (&s)[NV],
+__device__ __forceinline__ void df_run_smem(const float2* buf, int j, int L0, int m, bool up, bool dn, float (&s)[NV],
                                             float (&c)[NV]) {
   using St = DfStage<P0, NV, R>;
   if (up) {
@@ -559,8 +585,9 @@ __device__ __forceinline__ void df_run_smem(const float2* buf, int j, int L0, bo
 #pragma unroll
     for (int t = 0; t < LEN; ++t) {
       const float2 a = buf[St::CU + t * R + j];
+      const bool tn = df_is_tiny(t, LEN, m);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xu[v * St::W + t]);
+      for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xu[v * St::W + t], tn);
     }
   }
   if (dn) {
@@ -570,8 +597,9 @@ __device__ __forceinline__ void df_run_smem(const float2* buf, int j, int L0, bo
 #pragma unroll
     for (int t = 0; t < LEN; ++t) {
       const float2 a = ((t & 1) ? cd1 : cd0)[t * (R + 2)];
+      const bool tn = df_is_tiny(t, LEN, m);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) df_term(s[v], c[v], a, xd[v * St::W - t]);
+      for (int v = 0; v < NV; ++v) df_term_m(s[v], c[v], a, xd[v * St::W - t], tn);
     }
   }
 }
@@ -662,8 +690,8 @@ __global__ void __launch_bounds__(R + 32) k_band_df_tma(long long N, int nruns, 
       }
       if (ok && warp_on) {
         const float2* buf = dsm + (size_t)b * St::ELEMS;
-        if (r == 0) df_run_smem<P0, NV, R, P0>(buf, j, R4.w, up, dn, s, c);
-        else df_run_smem<P0, NV, R, M0>(buf, j, R4.w, up, dn, s, c);
+        if (r == 0) df_run_smem<P0, NV, R, P0>(buf, j, R4.w, 0, up, dn, s, c);
+        else df_run_smem<P0, NV, R, M0>(buf, j, R4.w, df_run_m(R4), up, dn, s, c);
         df_renorm<NV>(s, c, up || dn);
       }
       __syncwarp();
@@ -781,35 +809,55 @@ constexpr int kTmStages = 1;     // ring buffers of the one-row tensor-map kerne
 constexpr int kTm2Stages = 1;    // ring buffers of the two-row tensor-map kernel (measured: 1 beats 2)
 
 // The terms of run (LEN slots) for row j, both sides (the common case), every vector
-// (ALL) or the vectors with act[v] (uniform tests over the block)
-template <int P0, int NV, int LEN, bool ALL>
-__device__ __forceinline__ void df_run_tm(const float2* buf, int j, int o, const bool (&act)[NV], float (&s)[NV],
-                                          float (&c)[NV]) {
+// (ALL) or the vectors with act[v] (uniform tests over the block). MT >= 0: the run's
+// tiny-end count at compile time (the tiny terms' code is then all that is emitted for
+// them); MT < 0: the runtime count m.
+template <int P0, int NV, int LEN, bool ALL, int MT>
+__device__ __forceinline__ void df_run_tm(const float2* buf, int j, int o, int m, const bool (&act)[NV],
+                                          float (&s)[NV], float (&c)[NV]) {
   using St = DfTmStage<P0, NV>;
   constexpr int R = St::R, M0 = St::M0, W = St::W;
+  const int mm = MT >= 0 ? MT : m;
   const float2* xu = buf + St::XU + o + j;
 #pragma unroll
   for (int t = 0; t < LEN; ++t) {
     const float2 a = buf[St::CU + t * R + j];
+    const bool tn = df_is_tiny(t, LEN, mm);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      if (ALL || act[v]) df_term(s[v], c[v], a, xu[v * W + t]);
+      if (ALL || act[v]) df_term_m(s[v], c[v], a, xu[v * W + t], tn);
   }
   const float2* cd = buf + St::CD + o + j + (M0 - 1);
   const float2* xd = buf + St::XD + o + j + (M0 - 1);
 #pragma unroll
   for (int t = 0; t < LEN; ++t) {
     const float2 a = cd[t * W - t];
+    const bool tn = df_is_tiny(t, LEN, mm);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      if (ALL || act[v]) df_term(s[v], c[v], a, xd[v * W - t]);
+      if (ALL || act[v]) df_term_m(s[v], c[v], a, xd[v * W - t], tn);
   }
+}
+
+// a full run (2 P0 + 1 slots) of the common case with every vector: the tiny-end count
+// chosen at compile time (m >= P0 + 1: every slot tiny)
+template <int P0, int NV>
+__device__ __forceinline__ void df_run_tm_full(const float2* buf, int j, int o, int m, const bool (&act)[NV],
+                                               float (&s)[NV], float (&c)[NV]) {
+  constexpr int M0 = 2 * P0 + 1;
+  constexpr int MA = P0 + 1;
+  if (m <= 0) df_run_tm<P0, NV, M0, true, 0>(buf, j, o, 0, act, s, c);
+  else if (m == 1) df_run_tm<P0, NV, M0, true, 1>(buf, j, o, 1, act, s, c);
+  else if (m == 2) df_run_tm<P0, NV, M0, true, 2>(buf, j, o, 2, act, s, c);
+  else if (m == 3) df_run_tm<P0, NV, M0, true, (3 < MA ? 3 : MA)>(buf, j, o, 3, act, s, c);
+  else if (m == 4) df_run_tm<P0, NV, M0, true, (4 < MA ? 4 : MA)>(buf, j, o, 4, act, s, c);
+  else df_run_tm<P0, NV, M0, true, MA>(buf, j, o, m, act, s, c);
 }
 
 // the same for any sides and vectors (rows next to the grid's faces, converged systems):
 // the same operations per row and vector in the same order, compact code
 template <int P0, int NV>
-__device__ __forceinline__ void df_run_tm_any(const float2* buf, int j, int o, int len, bool up, bool dn,
+__device__ __forceinline__ void df_run_tm_any(const float2* buf, int j, int o, int len, int m, bool up, bool dn,
                                               const bool (&act)[NV], float (&s)[NV], float (&c)[NV]) {
   using St = DfTmStage<P0, NV>;
   constexpr int R = St::R, M0 = St::M0, W = St::W;
@@ -818,9 +866,10 @@ __device__ __forceinline__ void df_run_tm_any(const float2* buf, int j, int o, i
 #pragma unroll 1
     for (int t = 0; t < len; ++t) {
       const float2 a = buf[St::CU + t * R + j];
+      const bool tn = df_is_tiny(t, len, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v)
-        if (act[v]) df_term(s[v], c[v], a, xu[v * W + t]);
+        if (act[v]) df_term_m(s[v], c[v], a, xu[v * W + t], tn);
     }
   }
   if (dn) {
@@ -829,9 +878,10 @@ __device__ __forceinline__ void df_run_tm_any(const float2* buf, int j, int o, i
 #pragma unroll 1
     for (int t = 0; t < len; ++t) {
       const float2 a = cd[t * W - t];
+      const bool tn = df_is_tiny(t, len, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v)
-        if (act[v]) df_term(s[v], c[v], a, xd[v * W - t]);
+        if (act[v]) df_term_m(s[v], c[v], a, xd[v * W - t], tn);
     }
   }
 }
@@ -941,14 +991,15 @@ __global__ void __launch_bounds__(kTmRows + 32) k_band_df_tm(long long N, int nr
       if (ok && warp_on) {
         const float2* buf = dsm + (size_t)b * St::ELEMS;
         const int o = R4.w & 1;
+        const int m = r == 0 ? 0 : df_run_m(R4);
         if (up && dn && all) {
-          if (r == 0) df_run_tm<P0, NV, P0, true>(buf, j, o, act, s, c);
-          else df_run_tm<P0, NV, M0, true>(buf, j, o, act, s, c);
+          if (r == 0) df_run_tm<P0, NV, P0, true, 0>(buf, j, o, 0, act, s, c);
+          else df_run_tm_full<P0, NV>(buf, j, o, m, act, s, c);
         } else if (up && dn) {
-          if (r == 0) df_run_tm<P0, NV, P0, false>(buf, j, o, act, s, c);
-          else df_run_tm<P0, NV, M0, false>(buf, j, o, act, s, c);
+          if (r == 0) df_run_tm<P0, NV, P0, false, 0>(buf, j, o, 0, act, s, c);
+          else df_run_tm<P0, NV, M0, false, -1>(buf, j, o, m, act, s, c);
         } else {
-          df_run_tm_any<P0, NV>(buf, j, o, r == 0 ? P0 : M0, up, dn, act, s, c);
+          df_run_tm_any<P0, NV>(buf, j, o, r == 0 ? P0 : M0, m, up, dn, act, s, c);
         }
         df_renorm<NV>(s, c, up || dn);
       }
@@ -1032,7 +1083,7 @@ cudaError_t band_df_tm_go(cudaStream_t s, long long N, int nruns, const int4* ru
 // common case): one coefficient load per term serves both rows (a 16-byte pair for the
 // upper terms; for the lower terms on every other term), and the x loads slide
 template <int P0, int NV, int LEN, bool ALL>
-__device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, const bool (&act)[NV],
+__device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, int m, const bool (&act)[NV],
                                            float (&s)[2][NV], float (&c)[2][NV]) {
   using St = DfTmStage<P0, NV>;
   constexpr int R = St::R, M0 = St::M0, W = St::W;
@@ -1045,12 +1096,13 @@ __device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, con
 #pragma unroll
     for (int t = 0; t < LEN; ++t) {
       const float4 a2 = *reinterpret_cast<const float4*>(cu + t * R);
+      const bool tn = df_is_tiny(t, LEN, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         if (!ALL && !act[v]) continue;
         const float2 xb = xu[v * W + t + 1];
-        df_term(s[0][v], c[0][v], make_float2(a2.x, a2.y), xa[v]);
-        df_term(s[1][v], c[1][v], make_float2(a2.z, a2.w), xb);
+        df_term_m(s[0][v], c[0][v], make_float2(a2.x, a2.y), xa[v], tn);
+        df_term_m(s[1][v], c[1][v], make_float2(a2.z, a2.w), xb, tn);
         xa[v] = xb;
       }
     }
@@ -1074,12 +1126,13 @@ __device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, con
         a0 = buf[off];
         a1 = buf[off + 1];
       }
+      const bool tn = df_is_tiny(t, LEN, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         if (!ALL && !act[v]) continue;
         const float2 xa = xd[v * W - t];
-        df_term(s[0][v], c[0][v], a0, xa);
-        df_term(s[1][v], c[1][v], a1, xb[v]);
+        df_term_m(s[0][v], c[0][v], a0, xa, tn);
+        df_term_m(s[1][v], c[1][v], a1, xb[v], tn);
         xb[v] = xa;
       }
     }
@@ -1089,7 +1142,7 @@ __device__ __forceinline__ void df_run_tm2(const float2* buf, int jj, int o, con
 // the same for any rows, sides and vectors (rows next to the grid's faces, converged
 // systems): per row and vector the same operations in the same order, compact code
 template <int P0, int NV>
-__device__ __forceinline__ void df_run_tm2_any(const float2* buf, int jj, int o, int len, bool up0, bool up1,
+__device__ __forceinline__ void df_run_tm2_any(const float2* buf, int jj, int o, int len, int m, bool up0, bool up1,
                                                bool dn0, bool dn1, const bool (&act)[NV], float (&s)[2][NV],
                                                float (&c)[2][NV]) {
   using St = DfTmStage<P0, NV>;
@@ -1100,11 +1153,12 @@ __device__ __forceinline__ void df_run_tm2_any(const float2* buf, int jj, int o,
 #pragma unroll 1
     for (int t = 0; t < len; ++t) {
       const float2 a0 = cu[t * R], a1 = cu[t * R + 1];
+      const bool tn = df_is_tiny(t, len, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         if (!act[v]) continue;
-        if (up0) df_term(s[0][v], c[0][v], a0, xu[v * W + t]);
-        if (up1) df_term(s[1][v], c[1][v], a1, xu[v * W + t + 1]);
+        if (up0) df_term_m(s[0][v], c[0][v], a0, xu[v * W + t], tn);
+        if (up1) df_term_m(s[1][v], c[1][v], a1, xu[v * W + t + 1], tn);
       }
     }
   }
@@ -1114,11 +1168,12 @@ __device__ __forceinline__ void df_run_tm2_any(const float2* buf, int jj, int o,
 #pragma unroll 1
     for (int t = 0; t < len; ++t) {
       const float2 a0 = cd[t * (W - 1)], a1 = cd[t * (W - 1) + 1];
+      const bool tn = df_is_tiny(t, len, m);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         if (!act[v]) continue;
-        if (dn0) df_term(s[0][v], c[0][v], a0, xd[v * W - t]);
-        if (dn1) df_term(s[1][v], c[1][v], a1, xd[v * W - t + 1]);
+        if (dn0) df_term_m(s[0][v], c[0][v], a0, xd[v * W - t], tn);
+        if (dn1) df_term_m(s[1][v], c[1][v], a1, xd[v * W - t + 1], tn);
       }
     }
   }
@@ -1240,14 +1295,15 @@ __global__ void __launch_bounds__(kTmRows / 2 + 32) k_band_df_tm2(
       if (ok && warp_on) {
         const float2* buf = dsm + (size_t)b * St::ELEMS;
         const int o = R4.w & 1;
+        const int m = r == 0 ? 0 : df_run_m(R4);
         if (up0 && up1 && dn0 && dn1 && all) {
-          if (r == 0) df_run_tm2<P0, NV, P0, true>(buf, jj, o, act, s, c);
-          else df_run_tm2<P0, NV, M0, true>(buf, jj, o, act, s, c);
+          if (r == 0) df_run_tm2<P0, NV, P0, true>(buf, jj, o, 0, act, s, c);
+          else df_run_tm2<P0, NV, M0, true>(buf, jj, o, m, act, s, c);
         } else if (up0 && up1 && dn0 && dn1) {
-          if (r == 0) df_run_tm2<P0, NV, P0, false>(buf, jj, o, act, s, c);
-          else df_run_tm2<P0, NV, M0, false>(buf, jj, o, act, s, c);
+          if (r == 0) df_run_tm2<P0, NV, P0, false>(buf, jj, o, 0, act, s, c);
+          else df_run_tm2<P0, NV, M0, false>(buf, jj, o, m, act, s, c);
         } else {
-          df_run_tm2_any<P0, NV>(buf, jj, o, r == 0 ? P0 : M0, up0, up1, dn0, dn1, act, s, c);
+          df_run_tm2_any<P0, NV>(buf, jj, o, r == 0 ? P0 : M0, m, up0, up1, dn0, dn1, act, s, c);
         }
         df_renorm<NV>(s[0], c[0], up0 || dn0);
         df_renorm<NV>(s[1], c[1], up1 || dn1);
@@ -1374,11 +1430,11 @@ long long df_strip_blocks(const DfStrips& g) {
   return (long long)(g.S - 1) * g.n2 * g.nb0 + (long long)g.n2 * g.nbl;
 }
 
-std::vector<int> band_df_runs(const int* n, const int* p) {
+std::vector<int> band_df_runs(const int* n, const int* p, const unsigned char* tiny) {
   const int m0 = 2 * p[0] + 1, m1 = 2 * p[1] + 1, m2 = 2 * p[2] + 1;
   const int centre = m0 * m1 * m2 / 2;
   const int qc = centre / m0;  // (o1, o2) = (0, 0)
-  std::vector<int> out;
+  std::vector<std::array<int, 4>> runs;
   for (int q = qc; q < m1 * m2; ++q) {
     const int o1 = q % m1 - p[1], o2 = q / m1 - p[2];
     const int first_o0 = q == qc ? 1 : -p[0];
@@ -1386,12 +1442,37 @@ std::vector<int> band_df_runs(const int* n, const int* p) {
     if (len == 0) continue;
     const int h0 = m0 * q + (first_o0 + p[0]) - centre;
     const long long L0 = first_o0 + (long long)n[0] * (o1 + (long long)n[1] * o2);
-    out.push_back(h0);
-    out.push_back(len);
-    out.push_back((o1 + 64) | ((o2 + 64) << 8));
-    out.push_back((int)L0);
+    int m = 0;  // tiny slots at each end of the run (the centre run keeps every slot exact)
+    if (tiny && q != qc)
+      while (m < (len + 1) / 2 && tiny[h0 + m] && tiny[h0 + len - 1 - m]) ++m;
+    runs.push_back({h0, len, (o1 + 64) | ((o2 + 64) << 8) | (m << 16), (int)L0});
   }
+  // the centre run first (the kernels take run 0 as the row's own lines), the others by
+  // their tiny-end count, so that consecutive runs share one compiled form of the terms
+  std::stable_sort(runs.begin() + (runs.empty() ? 0 : 1), runs.end(),
+                   [](const std::array<int, 4>& a, const std::array<int, 4>& b) { return (a[2] >> 16) < (b[2] >> 16); });
+  std::vector<int> out;
+  for (const auto& r : runs) out.insert(out.end(), r.begin(), r.end());
   return out;
+}
+
+// per stored slot h, the largest |hi| over the rows of a split band (FP32 bits, which
+// order as the magnitudes do): out[h] must be zero on entry
+__global__ void k_df_slot_absmax(long long N, const float2* __restrict__ A, long long Np, unsigned* __restrict__ out) {
+  const float2* row = A + (long long)blockIdx.y * Np + kDfPad;
+  unsigned m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(row[i].x) & 0x7fffffffu);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, m);
+}
+
+cudaError_t launch_df_slot_absmax(cudaStream_t s, long long N, int H, const float2* A, long long Np, unsigned* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned) * H, s);
+  if (e != cudaSuccess) return e;
+  const unsigned gx = (unsigned)std::min<long long>((N + 255) / 256, 64);
+  k_df_slot_absmax<<<dim3(gx, (unsigned)H), 256, 0, s>>>(N, A, Np, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_df_split_matrix(cudaStream_t s, long long N, int H, const double* A, float2* Adf, long long Np,

@@ -298,8 +298,7 @@ int assemble_band_df(iga_handle* h) {
   const long long N = h->N, Np = df_row_stride(N);
   int p3[3] = {0, 0, 0};
   for (int a = 0; a < h->dim; ++a) p3[a] = h->dd[a].p;
-  const std::vector<int> runs = band_df_runs(h->n, p3);
-  CKS(upload(h, &h->band_runs, runs));
+  const std::vector<int> runs = band_df_runs(h->n, p3, nullptr);  // the geometry of the runs
   h->band_nruns = (int)runs.size() / 4;
   long long maxL = 0;  // reach of a run's staged copies beyond its rows
   for (size_t q = 0; q < runs.size(); q += 4) maxL = std::max(maxL, (long long)std::abs(runs[q + 3]) + runs[q + 1]);
@@ -327,6 +326,40 @@ int assemble_band_df(iga_handle* h) {
   h->EAm = EA[0];
   h->EAk = EA[1];
   h->band_Np = Np;
+  // each matrix's tiny slots (every coefficient below 2^-24 after the scaling, which puts the
+  // largest in [1, 2)): their terms take one FP32 multiply-add (band_df_runs)
+  {
+    struct Tmp {
+      unsigned* p = nullptr;
+      ~Tmp() {
+        if (p) cudaFree(p);
+      }
+    } smax;
+    CKS(dalloc(h, &smax.p, (size_t)2 * H));
+    LK(launch_df_slot_absmax(s, N, H, h->Mdf + sl, Np, smax.p));
+    LK(launch_df_slot_absmax(s, N, H, h->Kdf + sl, Np, smax.p + H));
+    std::vector<unsigned> hmax((size_t)2 * H);
+    CK(cudaMemcpyAsync(hmax.data(), smax.p, sizeof(unsigned) * 2 * H, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    constexpr unsigned kTinyBits = 0x33800000u;  // 2^-24 as FP32 bits
+    std::vector<unsigned char> tiny((size_t)2 * H);
+    for (size_t q = 0; q < tiny.size(); ++q) tiny[q] = hmax[q] < kTinyBits;
+    const std::vector<int> rm = band_df_runs(h->n, p3, tiny.data()), rk = band_df_runs(h->n, p3, tiny.data() + H);
+    CKS(upload(h, &h->band_runs, rm));
+    CKS(upload(h, &h->band_runs_k, rk));
+    // the share of an interior row's terms that are tiny: per run 2 min(2 m, len) of 2 len
+    auto share = [](const std::vector<int>& r) {
+      long long all = 1, cheap = 0;
+      for (size_t q = 0; q < r.size(); q += 4) {
+        const int len = r[q + 1], m = (r[q + 2] >> 16) & 15;
+        all += 2LL * len;
+        cheap += 2LL * std::min(2 * m, len);
+      }
+      return (double)cheap / (double)all;
+    };
+    h->df_tiny_m = share(rm);
+    h->df_tiny_k = share(rk);
+  }
   df_encode_maps(h->Mdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmM);
   df_encode_maps(h->Kdf + sl, H, h->df_xs + sl, kMaxVec, Np, p3[0], &h->tmK);
   dfree(h->Mband);
@@ -354,7 +387,8 @@ cudaError_t launch_band(iga_handle* h, cudaStream_t s, int cls, int nvec, const 
                                             h->df_bar, h->dflag + 2, h->bar_limit);
       if (e != cudaSuccess) return e;
     }
-    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(h->band_runs), h->n, h->dd[0].p,
+    return launch_band_df(s, h->N, h->band_nruns, reinterpret_cast<const int4*>(mass ? h->band_runs : h->band_runs_k),
+                          h->n, h->dd[0].p,
                           h->dim == 3 ? h->dd[2].p : 0, h->band_H, (mass ? h->Mdf : h->Kdf) + h->df_slack, h->band_Np, mass ? h->EAm : h->EAk, active, nvec,
                           xs, h->df_E, x, y, h->N, threads, nv, pq, npq, h->dflag + 2, mass ? &h->tmM : &h->tmK);
   }

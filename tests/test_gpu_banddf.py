@@ -6,7 +6,10 @@ replay, batches and the full-size patch.
 Error bound: coefficients and inputs are held to 48 significant bits and every
 product and addition of a row is error-free up to the rounding of the second FP32
 accumulator, so |y_i - (A x)_i| <= C 2^-48 sum_j |A_ij| |x_j| with C a small
-multiple of the number of terms' rounding steps seen in practice; C = 64 below."""
+multiple of the number of terms' rounding steps seen in practice; C = 64 below.
+Terms of tiny slots (every coefficient of the slot below 2^-24 of the matrix's
+largest) are one FP32 multiply-add of the high parts, each within 2^-23 |A_ij x_j|
+(2^-22 below, as slack), which adds 2^-22 sum over those slots of |A_ij| |x_j|."""
 import math
 
 import numpy as np
@@ -23,6 +26,20 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 C_BOUND = 64 * 2.0 ** -48
+TINY_BOUND = 2.0 ** -22
+
+
+def _tiny_slots(A, cut=2.0 ** -23):
+    """The slots the library may treat as tiny, as a superset: its cut is 2^-24 on the FP32
+    high parts of its own band (assembled by probing, scaled so that the largest entry lies
+    in [1, 2)); cut > 2^-24 here keeps every such slot whatever the roundoff of either band."""
+    scale = 2.0 ** np.floor(np.log2(np.abs(A).max()))
+    return (np.abs(A).max(axis=0) / scale < cut).astype(np.float64)
+
+
+def _bound(P, rows, A, X, tiny):
+    return (C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X))
+            + TINY_BOUND * P.band_rows_times(rows, np.abs(A) * tiny[None, :], np.abs(X)))
 
 CASES = {
     "2d_p23": W.Workload("t", 2, (4, 5), (2, 3), 0.1, 1, 0.5, 1),
@@ -60,9 +77,10 @@ def test_df_operators_within_the_arithmetic_bound(name):
     for A, apply in ((Mr, g.apply_M), (Kr, g.apply_K)):
         apply(_t(X.ravel()), y, 3)
         Y = _np(y).reshape(3, P.N)
+        tiny = _tiny_slots(A)
         for v in range(3):
             ref = P.band_rows_times(rows, A, X[v])
-            bound = C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X[v]))
+            bound = _bound(P, rows, A, X[v], tiny)
             assert np.all(np.abs(Y[v] - ref) <= bound), (v, np.max(np.abs(Y[v] - ref) / bound))
     g.close()
 
@@ -232,9 +250,10 @@ def test_df_cube64_sampled_rows():
     for A, apply in ((Mr, g.apply_M), (Kr, g.apply_K)):
         apply(_t(X.ravel()), y, 2)
         Y = _np(y).reshape(2, P.N)
+        tiny = _tiny_slots(A, cut=2.0 ** -20)  # sampled rows: their largest entry may be below the band's
         for v in range(2):
             ref = P.band_rows_times(rows, A, X[v])
-            bound = C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X[v]))
+            bound = _bound(P, rows, A, X[v], tiny)
             assert np.all(np.abs(Y[v][rows] - ref) <= bound)
     g.close()
 
@@ -267,7 +286,7 @@ def test_df_split_paths_wide_dynamic_range(decades):
         adf(_t(X), y)
         a64(_t(X), y64)
         absA = P.band_rows_times(rows, np.abs(A), np.ones(P.N))
-        bound = C_BOUND * P.band_rows_times(rows, np.abs(A), np.abs(X)) + 343 * 2.0 ** -130 * np.abs(X).max() * absA
+        bound = _bound(P, rows, A, X, _tiny_slots(A)) + 343 * 2.0 ** -130 * np.abs(X).max() * absA
         assert np.all(np.abs(_np(y) - _np(y64)) <= bound)
         if decades <= 15:
             assert np.all(np.abs(_np(y) - P.band_rows_times(rows, A, X)) <= bound)
@@ -327,3 +346,50 @@ def test_df_strips_cover_every_row():
                     first[name] = Y
                 assert np.array_equal(Y, first[name]), (threads, nv, name)
     g.close()
+
+
+def _tiny_share(P, A):
+    """The share of an interior row's terms in tiny slots as the library forms them:
+    slots whose largest coefficient is below 2^-24 after the power-of-two scaling that
+    puts the matrix's largest in [1, 2), taken at the two ends of each run of slots with
+    equal offsets along directions 1 and 2 (both ends tiny, working inwards)."""
+    offs = P.slot_offsets()
+    p = P.p
+    smax = np.abs(A).max(axis=0) / 2.0 ** np.floor(np.log2(np.abs(A).max()))
+    ratio = smax / 2.0 ** -24
+    assert not np.any(np.abs(ratio - 1.0) < 1e-6)  # no slot at the cut (the probed band may round either way)
+    tiny = smax < 2.0 ** -24
+    m0 = 2 * p[0] + 1
+    cheap, total = 0, 1
+    for o2 in range(0, p[2] + 1):
+        for o1 in range(-p[1], p[1] + 1):
+            if (o2, o1) < (0, 0):
+                continue
+            o0s = list(range(1, p[0] + 1)) if (o1, o2) == (0, 0) else list(range(-p[0], p[0] + 1))
+            total += 2 * len(o0s)
+            if (o1, o2) == (0, 0):
+                continue
+            sl = [int(np.where((offs[:, 0] == a) & (offs[:, 1] == o1) & (offs[:, 2] == o2))[0][0]) for a in o0s]
+            m = 0
+            while m < (m0 + 1) // 2 and tiny[sl[m]] and tiny[sl[m0 - 1 - m]]:
+                m += 1
+            cheap += 2 * min(2 * m, m0)
+    return cheap / total
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_df_tiny_share_matches_the_slot_magnitudes(p):
+    """iga_band_df_tiny against the oracle band's slot magnitudes: none at p = 2, about a
+    fifth of M's terms at p = 4."""
+    w = W.small(d=3, nel=(8, 7, 6), p=p, amp=0.1)
+    P = oracle.Patch(w.p, w.knots, w.ctrl())
+    Mr, Kr = P.assemble()
+    g = _gpu(w, op_form="assembled_df")
+    fm, fk = g.band_df_tiny()
+    g.close()
+    assert fm == pytest.approx(_tiny_share(P, Mr), abs=1e-12)
+    assert fk == pytest.approx(_tiny_share(P, Kr), abs=1e-12)
+    if p == 2:
+        assert fm == 0.0 and fk == 0.0
+    if p == 4:
+        assert fm > 0.15 and fk > 0.1
