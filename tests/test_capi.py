@@ -101,6 +101,7 @@ def test_tuning_and_batch_entry_points_validate(lib):
     assert lib.iga_batch_last_error(None) == b""
     assert lib.iga_set_band_config(None, 256, 2) == iga.EINVAL
     assert lib.iga_autotune(None, 2, 3, None, None) == iga.EINVAL
+    assert lib.iga_band_df_tiny(None, None, None) == iga.EINVAL
 
 
 def test_create_rejects_patches_without_interior_dofs(lib):
