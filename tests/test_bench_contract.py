@@ -48,6 +48,19 @@ def test_band_roofline_counts_the_methods_bytes():
     assert r["band_view"]["frac"] == pytest.approx(8 * band / 1e-3 / 1e9 / 6800.0)
 
 
+def test_alu_view_counts_the_tiny_slots_terms():
+    """The double-FP32 view counts 12 FP32 operations per exact term and 1 per tiny slot's
+    term (the profiler's flops count 2 per term)."""
+    prof = (2.0, 4, 4 * 1.0e9, 4 * 400e6)  # 4 launches of 0.5 G terms in 2 ms
+    r0 = bench.roofline("band_mass", DF, "k", prof, 6800.0, "measured", C2)
+    r = bench.roofline("band_mass", DF, "k", prof, 6800.0, "measured", C2, tiny=0.25)
+    assert r0["alu_view"]["fp32_ops_per_term"] == 12.0
+    assert r["alu_view"]["fp32_ops_per_term"] == pytest.approx(12.0 * 0.75 + 0.25)
+    assert r["alu_view"]["achieved_tops"] == pytest.approx((12.0 * 0.75 + 0.25) * 2.0e9 / 2e-3 / 1e12)
+    assert r["alu_view"]["frac"] == pytest.approx(r["alu_view"]["achieved_tops"] / r["alu_view"]["peak_tops"])
+    assert r["frac"] == pytest.approx(r0["frac"])  # the HBM view does not depend on the arithmetic
+
+
 def test_traffic_scaled_from_the_capture_while_the_source_matches(monkeypatch):
     monkeypatch.setattr(bench, "source_sha", lambda name: "feedfacefeedface")
     monkeypatch.setitem(bench.NCU_TRAFFIC, ("band_mass_df", "feedfacefeedface", C2.name, 2), 400e6)
